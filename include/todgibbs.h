@@ -1,0 +1,237 @@
+/*
+ * todgibbs.h -- C ABI of the GB300 Gibbs TOD step library (libtodgibbs.so).
+ *
+ * The library implements the data-parallel per-scan time-ordered-data (TOD)
+ * step of the Commander3 Gibbs sampler (BeyondPlanck, arXiv 2201.03509):
+ * Huffman decode of the pointing streams (Sect. 4.1), projection of the TQU
+ * sky (Eq. `todmodel`), the gain and correlated-noise conditionals
+ * (Eq. `gibbsstart`, first two lines; Sect. 5 on CG gap filling), binning
+ * into per-pixel normal equations and their solution (Sect. 5 table, rows
+ * "TOD binning" and "Map solution").
+ *
+ * Conventions for every entry point
+ *  - A band holds ndet detectors x nscan scans.  A "detscan" q = scan*ndet+det
+ *    owns samples [off[q], off[q+1]) of every per-sample array (the
+ *    comm_scan / comm_detscan hierarchy of Listing `tod`).
+ *  - Sample counts are FFT lengths: even 2^a 3^b 5^c numbers (Sect. 4.2);
+ *    use tod_fft_length() when ingesting.
+ *  - Unless stated otherwise, array arguments of compute calls are DEVICE
+ *    pointers owned by the caller; the library never frees them.  Calls are
+ *    asynchronous on the given stream (0 = legacy default stream), return
+ *    after enqueueing, and only argument errors are reported immediately.
+ *    Faults found on the device (corrupt stream, CG not converged, bounded
+ *    wait timed out) are recorded per detscan and read with
+ *    tod_plan_status() after the stream is synchronised.  No call traps the
+ *    GPU.
+ *  - flags: bit (t & 31) of word (t >> 5) is 1 when sample t (global index)
+ *    is flagged (excluded: M_t = 0).
+ *  - psd: double[ndet][3] = (sigma0 [data units], f_knee [Hz], alpha < 0).
+ *    Noise model P(f) = sigma0^2 (1 + (f/f_knee)^alpha) at DCT frequencies
+ *    f_k = k f_samp / (2 n) (the mirrored array of Sect. 4.2 has period 2n).
+ *  - Not thread-safe per plan: calls on one plan must not run concurrently
+ *    from several host threads.  Calls on one plan in different streams race.
+ */
+#ifndef TODGIBBS_H
+#define TODGIBBS_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t tod_status;
+
+#define TOD_OK                 0
+#define TOD_ERR_ARG           -1   /* bad argument; nothing was enqueued */
+#define TOD_ERR_CORRUPT_STREAM -2  /* a Huffman stream did not decode */
+#define TOD_ERR_NOT_CONVERGED -3   /* CG gap filling hit its iteration cap */
+#define TOD_ERR_TIMEOUT       -4   /* a bounded device-side wait gave up */
+#define TOD_ERR_CUDA          -5   /* a CUDA runtime call failed */
+#define TOD_ERR_OOM           -6   /* device or host allocation failed */
+#define TOD_ERR_UNIMPLEMENTED -7
+
+#define TOD_MODE_DRAW 0   /* sample from the conditional */
+#define TOD_MODE_MEAN 1   /* conditional mean: all normals set to zero */
+
+#define TOD_N_PSI 4096    /* polarisation-angle bins over [0, 2pi) (Sect. 4.1) */
+#define TOD_CKPT_BLOCK 512
+#define TOD_HUFF_MAXLEN 24
+
+/* Short, static description of a status code.  Never NULL. */
+const char *tod_status_string(tod_status s);
+
+/* Largest even 2^a 3^b 5^c not above n (0 if n < 2).  Sect. 4.2: chunks are
+ * truncated at read-in to lengths that are cheap to transform; a detscan
+ * keeps its first tod_fft_length(n) samples. */
+int64_t tod_fft_length(int64_t n);
+
+/* ---------------------------------------------------------------------------
+ * Compressed pointing stream of one kind (HEALPix RING pixel, or psi bin) for
+ * a whole band (Sect. 4.1: samples differenced, x(i) - x(i-1) with x(-1) = 0,
+ * then Huffman coded; Listing `tod`: pix/psi stored as bytes).  Format:
+ *   - one canonical Huffman code per (scan, kind), shared by the scan's
+ *     detectors; code lengths <= TOD_HUFF_MAXLEN; symbols of each code listed
+ *     in ascending value with their lengths (codes follow canonically:
+ *     ordered by (length, value), consecutive, first code all zeros);
+ *   - bits most-significant first in 32-bit words; each detscan's stream
+ *     starts on a word boundary;
+ *   - a checkpoint every TOD_CKPT_BLOCK samples: the bit offset of the block
+ *     (relative to the detscan's first word) and the value preceding it.
+ * All pointers HOST, read during the call only.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    const uint32_t *words;      int64_t nwords;
+    const int64_t  *word_off;   /* [ndetscan+1] first word of each detscan  */
+    const int64_t  *nbits;      /* [ndetscan]   payload bits per detscan    */
+    const int64_t  *blk_off;    /* [ndetscan+1] first checkpoint per detscan */
+    const uint32_t *ckpt_bit;   /* [nblk] */
+    const int32_t  *ckpt_val;   /* [nblk] */
+    int64_t         nblk;
+    const int64_t  *sym_off;    /* [nscan+1] first symbol of each scan's code */
+    const int32_t  *sym_vals;   /* [nsym] ascending per scan */
+    const uint8_t  *sym_len;    /* [nsym] */
+    int64_t         nsym;
+} tod_huff_streams;
+
+/* Library-allocated output of tod_huff_encode (host memory). */
+typedef struct {
+    uint32_t *words;    int64_t nwords;
+    int64_t  *word_off; int64_t *nbits; int64_t *blk_off;
+    uint32_t *ckpt_bit; int32_t *ckpt_val; int64_t nblk;
+    int64_t  *sym_off;  int32_t *sym_vals; uint8_t *sym_len; int64_t nsym;
+} tod_huff_buffers;
+
+/* Ingest (host, not on the per-step path): compress one stream kind of a
+ * band.  values: HOST int32[offsets[ndetscan]] (pixel indices or psi bins);
+ * offsets: HOST int64[ndet*nscan+1].  Fills *out with malloc'd arrays that
+ * the caller releases with tod_huff_free.  Tie rules of the Huffman build:
+ * leaves ordered by (count, value); two-queue merge taking the leaf on equal
+ * counts; lengths above TOD_HUFF_MAXLEN trigger count halving ((c+1)/2) and
+ * a rebuild.  A code with one symbol gets the 1-bit code 0.  Uses host
+ * threads.  Returns TOD_ERR_ARG on bad sizes, TOD_ERR_OOM on allocation
+ * failure. */
+tod_status tod_huff_encode(int32_t ndet, int32_t nscan, const int64_t *offsets,
+                           const int32_t *values, tod_huff_buffers *out);
+void tod_huff_free(tod_huff_buffers *b);
+
+/* ---------------------------------------------------------------------------
+ * Plan = the band's TOD object (Listing `tod`: comm_tod -> comm_scan ->
+ * comm_detscan): device copies of the compressed pointing streams, decode
+ * tables, the per-detscan transform plans, the pixel-sorted binning
+ * structure (pointing is fixed during the run, Sect. 2.1, so it is built
+ * once) and scratch.  tod_plan_create decodes the pointing on the host to
+ * build the binning structure.
+ * ------------------------------------------------------------------------- */
+typedef struct tod_plan tod_plan;
+
+typedef struct {
+    int32_t nside;          /* HEALPix Nside; npix = 12 nside^2 */
+    int32_t ndet;
+    int32_t nscan;
+    int32_t n_psi;          /* must be TOD_N_PSI */
+    double  fsamp;          /* sample rate [Hz] */
+    const int64_t *offsets; /* HOST [ndet*nscan+1]; every length an FFT length */
+    tod_huff_streams pix;   /* HOST compressed pixel stream */
+    tod_huff_streams psi;   /* HOST compressed psi-bin stream */
+    int32_t cluster_size;   /* 0 = choose; else 1, 2, 4, 8 or 16 CTAs per detscan transform */
+    int32_t device;         /* CUDA device ordinal the plan lives on */
+} tod_band_desc;
+
+/* Counter-based random streams: Philox4x64-10 (Salmon et al. 2011) with key
+ * (seed, band) and counter (block, detscan, purpose, gibbs_iter); purposes
+ * 0 = gain, 1 = white-noise term, 2 = prior term of the n_corr draw. */
+typedef struct {
+    uint64_t seed;
+    uint64_t band;
+    uint64_t gibbs_iter;
+} tod_rng;
+
+tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band);
+tod_status tod_plan_destroy(tod_plan *p);
+/* Sizes of the plan (host scalars; any pointer may be NULL). */
+tod_status tod_plan_info(const tod_plan *p, int64_t *nsamples, int32_t *ndetscan,
+                         int32_t *npix, int32_t *cluster_size, int64_t *device_bytes);
+/* Synchronises the device, copies the per-detscan status words
+ * (TOD_OK or an error code) into HOST int32[ndetscan] (may be NULL), clears
+ * them, and returns the first error found (TOD_OK if none). */
+tod_status tod_plan_status(tod_plan *p, int32_t *detscan_status);
+
+/* A1 -- Huffman decode + undo differencing (Sect. 4.1).
+ * pix_out int32[N], psi_out uint16[N] (device).  Bit-exact; a stream that
+ * does not decode marks its detscan TOD_ERR_CORRUPT_STREAM. */
+tod_status tod_decode(tod_plan *p, int32_t *pix_out, uint16_t *psi_out, cudaStream_t stream);
+
+/* A2 -- projection (Eq. `todmodel`, the g P m term):
+ * s_t = g_q (T_p + Q_p cos 2psi_t + U_p sin 2psi_t), p = pix_t,
+ * psi_t = (bin + 1/2) 2pi / TOD_N_PSI, cos/sin tabulated in FP32.
+ * map_tqu: float4[npix] (T, Q, U, unused).  gain: double[ndetscan] or NULL
+ * for unit gain.  s_out float32[N].  FP32 arithmetic. */
+tod_status tod_project(tod_plan *p, const void *map_tqu, const int32_t *pix,
+                       const uint16_t *psi, const double *gain, float *s_out,
+                       cudaStream_t stream);
+
+/* A4 -- gain draw (Eq. `gibbsstart`, first line; n_corr marginalised, so
+ * the full noise PSD weights the fit).  Per detscan, with shat = C(M s),
+ * dhat = C(M d) the orthonormal DCT-II (the mirrored FFT of Sect. 4.2):
+ *   a = sum_{k>=1} shat_k^2 / P_k,  b = sum_{k>=1} shat_k dhat_k / P_k,
+ *   mu = b/a, sigma = a^(-1/2), g = mu + z sigma (z = 0 in TOD_MODE_MEAN).
+ * d, s: float32[N] (s at unit gain).  Outputs double[ndetscan].
+ * Transforms in FP32, sums in FP64. */
+tod_status tod_sample_gain(tod_plan *p, const float *d, const float *s,
+                           const uint32_t *flags, const double *psd, tod_rng rng,
+                           int32_t mode, double *gain_out, double *mu_out,
+                           double *sigma_out, cudaStream_t stream);
+
+/* A5 -- correlated-noise draw with flagged samples inpainted (Eq.
+ * `gibbsstart`, second line; Sect. 5: CG gap filling).  Per detscan,
+ * r = d - g s and x solves
+ *   (C^T diag(phi) C + M / sigma0^2) x = M r / sigma0^2 + M w1 / sigma0
+ *                                        + C^T (sqrt(phi) w2),
+ * phi_k = 1 / (sigma0^2 (f_k/f_knee)^alpha) for k >= 1, phi_0 = 0.
+ * w1[t] is normal i(t) of the NC_W1 stream (i(t) = t/2 for even t,
+ * n-1-(t-1)/2 for odd t); w2[k] is normal 2k (k < n/2), 2(n-k)+1 (k > n/2),
+ * 0 (k = 0) or 1 (k = n/2) of the NC_W2 stream.  Gap-free detscans are solved
+ * exactly in the DCT basis; flagged ones by conjugate gradients on the
+ * flagged samples (Woodbury form), stopping at relative residual cg_tol
+ * (<= 0: 1e-6) or cg_maxiter (<= 0: 500) iterations (then
+ * TOD_ERR_NOT_CONVERGED).  ncorr_out float32[N]; cg_iters_out int32[ndetscan]
+ * or NULL. */
+tod_status tod_sample_ncorr(tod_plan *p, const float *d, const float *s,
+                            const double *gain, const uint32_t *flags,
+                            const double *psd, tod_rng rng, int32_t mode,
+                            double cg_tol, int32_t cg_maxiter,
+                            float *ncorr_out, int32_t *cg_iters_out,
+                            cudaStream_t stream);
+
+/* A6 -- binning (Sect. 5 table, "TOD binning"; Sect. 2.4: coadded during
+ * the pass over chunks).  With r'_t = d_t - ncorr_t, w_t = M_t / sigma0^2:
+ *   A_p = sum_t w_t g_q^2 u_t u_t^T,  b_p = sum_t w_t g_q u_t r'_t,
+ *   u_t = (1, cos 2psi_t, sin 2psi_t),  hits_p = sum_t M_t.
+ * A_out double[npix][6] (TT,TQ,TU,QQ,QU,UU), b_out double[npix][3],
+ * hits_out int32[npix]; all overwritten.  Deterministic: samples are summed
+ * per (detscan, pixel) run of the pixel-sorted order fixed at plan
+ * creation, runs in ascending detscan order, with products and partial sums
+ * carried at FP64 accuracy. */
+tod_status tod_bin(tod_plan *p, const uint16_t *psi, const float *d,
+                   const float *ncorr, const double *gain, const uint32_t *flags,
+                   const double *psd, double *A_out, double *b_out,
+                   int32_t *hits_out, cudaStream_t stream);
+
+/* A7 -- per-pixel solve (Sect. 5 table, "Map solution (Ax=b for each
+ * pixel)"): m_p = A_p^{-1} b_p by FP64 3x3 Cholesky.  A pixel is valid iff
+ * hits_p >= 3 and its Hadamard ratio det(A_p)/(A_TT A_QQ A_UU) >= rcond_min;
+ * invalid pixels get m_p = 0.  map_out double[3][npix]; map_f32_out
+ * float4[npix] (T,Q,U,0) or NULL (next step's projection input);
+ * rcond_out double[npix] (the Hadamard ratio) or NULL; valid_out
+ * uint8[npix] or NULL. */
+tod_status tod_solve_maps(tod_plan *p, const double *A, const double *b,
+                          const int32_t *hits, double rcond_min, double *map_out,
+                          void *map_f32_out, double *rcond_out, uint8_t *valid_out,
+                          cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TODGIBBS_H */

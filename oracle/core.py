@@ -240,7 +240,7 @@ def stream_normals(seed: int, band: int, q: int, purpose: int, it: int, n: int) 
 
     Normal i comes from Philox block i//8 (counter (i//8, q, purpose, it)),
     whose four 64-bit words split into eight 32-bit halves, low half first;
-    pair j = (i%8)//2 takes halves 2j, 2j+1 as uniforms u = (h>>8 + 1/2) 2^-24
+    pair j = (i%8)//2 takes halves 2j, 2j+1 as uniforms u = (h>>9 + 1/2) 2^-23
     and gives sqrt(-2 ln u1) cos(2 pi u2) (even i) or ... sin(2 pi u2) (odd i).
     Evaluated here in FP64."""
     nb = (n + 7) // 8
@@ -249,13 +249,38 @@ def stream_normals(seed: int, band: int, q: int, purpose: int, it: int, n: int) 
     halves = np.empty((nb, 8), dtype=np.uint64)
     halves[:, 0::2] = w & _MASK32
     halves[:, 1::2] = w >> np.uint64(32)
-    u = ((halves >> np.uint64(8)).astype(np.float64) + 0.5) * 2.0 ** -24
+    u = ((halves >> np.uint64(9)).astype(np.float64) + 0.5) * 2.0 ** -23
     u1, u2 = u[:, 0::2], u[:, 1::2]
     r = np.sqrt(-2.0 * np.log(u1))
     z = np.empty((nb, 8))
     z[:, 0::2] = r * np.cos(2.0 * np.pi * u2)
     z[:, 1::2] = r * np.sin(2.0 * np.pi * u2)
     return z.reshape(-1)[:n]
+
+
+def omega1(seed: int, band: int, q: int, it: int, n: int) -> np.ndarray:
+    """White-noise normals of the correlated-noise right-hand side, one per
+    sample.  Convention (the paper does not fix one): sample t takes normal
+    number i(t) of stream (q, NC_W1, it), where i(t) is t's position in the
+    even-then-reversed-odd order (x_0, x_2, ..., x_3, x_1): i = t/2 for even
+    t, n-1-(t-1)/2 for odd t."""
+    z = stream_normals(seed, band, q, PURPOSE_NC_W1, it, n)
+    t = np.arange(n)
+    i = np.where(t % 2 == 0, t // 2, n - 1 - (t - 1) // 2)
+    return z[i]
+
+
+def omega2(seed: int, band: int, q: int, it: int, n: int) -> np.ndarray:
+    """Normals of the prior term, one per DCT mode kappa.  Convention: modes
+    kappa and n-kappa (1 <= kappa < n/2) take normals 2 kappa and 2 kappa+1 of
+    stream (q, NC_W2, it); mode 0 takes normal 0 and mode n/2 normal 1."""
+    z = stream_normals(seed, band, q, PURPOSE_NC_W2, it, n)
+    m = n // 2
+    k = np.arange(n)
+    nu = np.where(k < m, 2 * k, 2 * (n - k) + 1)
+    nu[0] = 0
+    nu[m] = 1
+    return z[nu]
 
 
 # ============================================================================
@@ -572,8 +597,8 @@ def gibbs_tod_step(ing: dict, band_cfg, npix: int, map_tqu: np.ndarray, psd: np.
         z = gain_normal(seed, band_id, q, it)
         gain[q], mu[q], sig[q] = sample_gain(s, d, M, P, z, mode)
         if mode == MODE_DRAW:
-            w1 = stream_normals(seed, band_id, q, PURPOSE_NC_W1, it, n)
-            w2 = stream_normals(seed, band_id, q, PURPOSE_NC_W2, it, n)
+            w1 = omega1(seed, band_id, q, it, n)
+            w2 = omega2(seed, band_id, q, it, n)
         else:
             w1 = np.zeros(n)
             w2 = np.zeros(n)

@@ -1,0 +1,286 @@
+"""GB300 Gibbs TOD step (Commander3 / BeyondPlanck, arXiv 2201.03509).
+
+Thin Python binding over the C ABI in ``include/todgibbs.h`` (library
+``_build/libtodgibbs.so``, built by ``build()``): argument marshalling only.
+Every step of the TOD path runs in the library's CUDA kernels; device arrays
+are torch tensors, streams are torch streams.  There is no CPU fallback: if
+the library is missing the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from ._build import LIB as _LIB_PATH, build as _build_lib
+
+__all__ = ["build", "lib", "fft_length", "huff_encode", "ingest", "pack_flags", "Plan", "Rng",
+           "TodError", "MODE_DRAW", "MODE_MEAN", "N_PSI", "CKPT_BLOCK"]
+
+MODE_DRAW = 0
+MODE_MEAN = 1
+N_PSI = 4096
+CKPT_BLOCK = 512
+
+_P = ctypes.c_void_p
+_i32, _i64, _u64, _f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+
+
+class TodError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        msg = lib().tod_status_string(code).decode() if _lib is not None else str(code)
+        super().__init__("%s: %s (%d)" % (what, msg, code))
+        self.code = code
+
+
+class _HuffStreams(ctypes.Structure):
+    _fields_ = [("words", _P), ("nwords", _i64), ("word_off", _P), ("nbits", _P), ("blk_off", _P),
+                ("ckpt_bit", _P), ("ckpt_val", _P), ("nblk", _i64), ("sym_off", _P), ("sym_vals", _P),
+                ("sym_len", _P), ("nsym", _i64)]
+
+
+class _HuffBuffers(ctypes.Structure):
+    _fields_ = [("words", ctypes.POINTER(ctypes.c_uint32)), ("nwords", _i64),
+                ("word_off", ctypes.POINTER(_i64)), ("nbits", ctypes.POINTER(_i64)),
+                ("blk_off", ctypes.POINTER(_i64)), ("ckpt_bit", ctypes.POINTER(ctypes.c_uint32)),
+                ("ckpt_val", ctypes.POINTER(_i32)), ("nblk", _i64),
+                ("sym_off", ctypes.POINTER(_i64)), ("sym_vals", ctypes.POINTER(_i32)),
+                ("sym_len", ctypes.POINTER(ctypes.c_uint8)), ("nsym", _i64)]
+
+
+class _BandDesc(ctypes.Structure):
+    _fields_ = [("nside", _i32), ("ndet", _i32), ("nscan", _i32), ("n_psi", _i32), ("fsamp", _f64),
+                ("offsets", _P), ("pix", _HuffStreams), ("psi", _HuffStreams),
+                ("cluster_size", _i32), ("device", _i32)]
+
+
+class Rng(ctypes.Structure):
+    """Counter-based random streams: key (seed, band), counter carries the
+    Gibbs iteration."""
+    _fields_ = [("seed", _u64), ("band", _u64), ("gibbs_iter", _u64)]
+
+
+_lib = None
+
+SYMBOLS = ["tod_status_string", "tod_fft_length", "tod_huff_encode", "tod_huff_free",
+           "tod_plan_create", "tod_plan_destroy", "tod_plan_info", "tod_plan_status",
+           "tod_decode", "tod_project", "tod_sample_gain", "tod_sample_ncorr", "tod_bin",
+           "tod_solve_maps"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the CUDA library for sm_103a into the package's _build/."""
+    global _lib
+    _lib = None
+    return _build_lib(force=force)
+
+
+def lib():
+    """The loaded C library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError("libtodgibbs.so is not built: call paper_2201_03509_gb300.build()")
+        L = ctypes.CDLL(_LIB_PATH)
+        L.tod_status_string.argtypes = [_i32]
+        L.tod_status_string.restype = ctypes.c_char_p
+        L.tod_fft_length.argtypes = [_i64]
+        L.tod_fft_length.restype = _i64
+        L.tod_huff_encode.argtypes = [_i32, _i32, _P, _P, ctypes.POINTER(_HuffBuffers)]
+        L.tod_huff_free.argtypes = [ctypes.POINTER(_HuffBuffers)]
+        L.tod_huff_free.restype = None
+        L.tod_plan_create.argtypes = [ctypes.POINTER(_P), ctypes.POINTER(_BandDesc)]
+        L.tod_plan_destroy.argtypes = [_P]
+        L.tod_plan_info.argtypes = [_P, _P, _P, _P, _P, _P]
+        L.tod_plan_status.argtypes = [_P, _P]
+        L.tod_decode.argtypes = [_P, _P, _P, _P]
+        L.tod_project.argtypes = [_P, _P, _P, _P, _P, _P, _P]
+        L.tod_sample_gain.argtypes = [_P, _P, _P, _P, _P, Rng, _i32, _P, _P, _P, _P]
+        L.tod_sample_ncorr.argtypes = [_P, _P, _P, _P, _P, _P, Rng, _i32, _f64, _i32, _P, _P, _P]
+        L.tod_bin.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
+        L.tod_solve_maps.argtypes = [_P, _P, _P, _P, _f64, _P, _P, _P, _P, _P]
+        for name in SYMBOLS:
+            if name not in ("tod_status_string", "tod_fft_length", "tod_huff_free"):
+                getattr(L, name).restype = _i32
+        _lib = L
+    return _lib
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise TodError(code, what)
+
+
+def fft_length(n: int) -> int:
+    return int(lib().tod_fft_length(int(n)))
+
+
+def _arr(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def huff_encode(ndet: int, nscan: int, offsets: np.ndarray, values: np.ndarray) -> dict:
+    """Compress one pointing stream kind (host).  Returns numpy arrays with
+    the stream layout documented in todgibbs.h."""
+    offsets = _arr(offsets, np.int64)
+    values = _arr(values, np.int32)
+    buf = _HuffBuffers()
+    _check(lib().tod_huff_encode(ndet, nscan, offsets.ctypes.data, values.ctypes.data,
+                                 ctypes.byref(buf)), "tod_huff_encode")
+    nq = ndet * nscan
+
+    def take(ptr, n, dt):
+        return np.ctypeslib.as_array(ptr, shape=(n,)).astype(dt, copy=True) if n else np.zeros(0, dt)
+
+    try:
+        out = dict(words=take(buf.words, buf.nwords, np.uint32),
+                   word_off=take(buf.word_off, nq + 1, np.int64),
+                   nbits=take(buf.nbits, nq, np.int64),
+                   blk_off=take(buf.blk_off, nq + 1, np.int64),
+                   ckpt_bit=take(buf.ckpt_bit, buf.nblk, np.uint32),
+                   ckpt_val=take(buf.ckpt_val, buf.nblk, np.int32),
+                   sym_off=take(buf.sym_off, nscan + 1, np.int64),
+                   sym_vals=take(buf.sym_vals, buf.nsym, np.int32),
+                   sym_len=take(buf.sym_len, buf.nsym, np.uint8))
+    finally:
+        lib().tod_huff_free(ctypes.byref(buf))
+    return out
+
+
+def pack_flags(flagged: np.ndarray) -> np.ndarray:
+    """Bool per sample (True = flagged) -> uint32 words, bit t&31 of word t>>5."""
+    f = np.asarray(flagged, dtype=bool)
+    pad = (-len(f)) % 32
+    if pad:
+        f = np.concatenate([f, np.zeros(pad, bool)])
+    return np.packbits(f, bitorder="little").view("<u4").copy()
+
+
+def ingest(band) -> dict:
+    """Ingest of a synthetic band (not on the per-step path): truncate each
+    scan to its FFT length (paper Sect. 4.2) and compress its pixel and psi
+    streams (Sect. 4.1)."""
+    ndet, nscan = band.cfg.ndet, band.cfg.nscan
+    nq = ndet * nscan
+    nlen = np.array([fft_length(int(band.scan_len[q // ndet])) for q in range(nq)], dtype=np.int64)
+    off = np.zeros(nq + 1, dtype=np.int64)
+    off[1:] = np.cumsum(nlen)
+    pix = np.concatenate([band.pix[q][:nlen[q]] for q in range(nq)]).astype(np.int32)
+    psi = np.concatenate([band.psi[q][:nlen[q]] for q in range(nq)]).astype(np.int32)
+    flags = np.concatenate([band.flags[q][:nlen[q]] for q in range(nq)])
+    return dict(offsets=off,
+                pix_streams=huff_encode(ndet, nscan, off, pix),
+                psi_streams=huff_encode(ndet, nscan, off, psi),
+                tod=np.concatenate([band.tod[q][:nlen[q]] for q in range(nq)]).astype(np.float32),
+                flags=flags, flag_words=pack_flags(flags))
+
+
+def _streams(d: dict, keep: list) -> _HuffStreams:
+    arrs = {k: _arr(d[k], dt) for k, dt in (("words", np.uint32), ("word_off", np.int64),
+                                             ("nbits", np.int64), ("blk_off", np.int64),
+                                             ("ckpt_bit", np.uint32), ("ckpt_val", np.int32),
+                                             ("sym_off", np.int64), ("sym_vals", np.int32),
+                                             ("sym_len", np.uint8))}
+    keep.append(arrs)
+    return _HuffStreams(arrs["words"].ctypes.data, len(arrs["words"]), arrs["word_off"].ctypes.data,
+                        arrs["nbits"].ctypes.data, arrs["blk_off"].ctypes.data,
+                        arrs["ckpt_bit"].ctypes.data, arrs["ckpt_val"].ctypes.data,
+                        len(arrs["ckpt_bit"]), arrs["sym_off"].ctypes.data,
+                        arrs["sym_vals"].ctypes.data, arrs["sym_len"].ctypes.data,
+                        len(arrs["sym_vals"]))
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor (or None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("device tensor expected")
+    if not t.is_contiguous():
+        raise ValueError("contiguous tensor expected")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+class Plan:
+    """The band's TOD object on the GPU (todgibbs.h: tod_plan)."""
+
+    def __init__(self, nside: int, ndet: int, nscan: int, fsamp: float, offsets: np.ndarray,
+                 pix_streams: dict, psi_streams: dict, cluster_size: int = 0, device: int = 0):
+        keep = []
+        off = _arr(offsets, np.int64)
+        keep.append(off)
+        desc = _BandDesc(nside, ndet, nscan, N_PSI, float(fsamp), off.ctypes.data,
+                         _streams(pix_streams, keep), _streams(psi_streams, keep),
+                         int(cluster_size), int(device))
+        h = _P()
+        _check(lib().tod_plan_create(ctypes.byref(h), ctypes.byref(desc)), "tod_plan_create")
+        self._h = h
+        self.ndet, self.nscan, self.nq = ndet, nscan, ndet * nscan
+        self.offsets = off.copy()
+        self.nside = nside
+        self.npix = 12 * nside * nside
+        self.N = int(off[-1])
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().tod_plan_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        ns, nq, npix, cs, nb = _i64(), _i32(), _i32(), _i32(), _i64()
+        _check(lib().tod_plan_info(self._h, ctypes.byref(ns), ctypes.byref(nq), ctypes.byref(npix),
+                                   ctypes.byref(cs), ctypes.byref(nb)), "tod_plan_info")
+        return dict(nsamples=ns.value, ndetscan=nq.value, npix=npix.value, cluster_size=cs.value,
+                    device_bytes=nb.value)
+
+    def status(self, raise_on_error: bool = True) -> np.ndarray:
+        st = np.zeros(self.nq, dtype=np.int32)
+        code = lib().tod_plan_status(self._h, st.ctypes.data)
+        if raise_on_error and code != 0:
+            raise TodError(code, "device status")
+        return st
+
+    # --- A1..A7 -------------------------------------------------------------
+    def decode(self, pix_out, psi_out, stream=None):
+        _check(lib().tod_decode(self._h, _ptr(pix_out), _ptr(psi_out), _stream(stream)), "tod_decode")
+
+    def project(self, map_tqu4, pix, psi, gain, s_out, stream=None):
+        _check(lib().tod_project(self._h, _ptr(map_tqu4), _ptr(pix), _ptr(psi), _ptr(gain),
+                                 _ptr(s_out), _stream(stream)), "tod_project")
+
+    def sample_gain(self, d, s, flags, psd, rng: Rng, mode, gain_out, mu_out=None, sigma_out=None,
+                    stream=None):
+        _check(lib().tod_sample_gain(self._h, _ptr(d), _ptr(s), _ptr(flags), _ptr(psd), rng, mode,
+                                     _ptr(gain_out), _ptr(mu_out), _ptr(sigma_out), _stream(stream)),
+               "tod_sample_gain")
+
+    def sample_ncorr(self, d, s, gain, flags, psd, rng: Rng, mode, ncorr_out, cg_iters_out=None,
+                     cg_tol: float = 0.0, cg_maxiter: int = 0, stream=None):
+        _check(lib().tod_sample_ncorr(self._h, _ptr(d), _ptr(s), _ptr(gain), _ptr(flags), _ptr(psd),
+                                      rng, mode, float(cg_tol), int(cg_maxiter), _ptr(ncorr_out),
+                                      _ptr(cg_iters_out), _stream(stream)), "tod_sample_ncorr")
+
+    def bin(self, psi, d, ncorr, gain, flags, psd, A_out, b_out, hits_out, stream=None):
+        _check(lib().tod_bin(self._h, _ptr(psi), _ptr(d), _ptr(ncorr), _ptr(gain), _ptr(flags),
+                             _ptr(psd), _ptr(A_out), _ptr(b_out), _ptr(hits_out), _stream(stream)),
+               "tod_bin")
+
+    def solve_maps(self, A, b, hits, rcond_min, map_out, map_f32_out=None, rcond_out=None,
+                   valid_out=None, stream=None):
+        _check(lib().tod_solve_maps(self._h, _ptr(A), _ptr(b), _ptr(hits), float(rcond_min),
+                                    _ptr(map_out), _ptr(map_f32_out), _ptr(rcond_out),
+                                    _ptr(valid_out), _stream(stream)), "tod_solve_maps")

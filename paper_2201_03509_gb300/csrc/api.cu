@@ -1,0 +1,810 @@
+// C ABI of libtodgibbs: ingest (FFT lengths, Huffman encoding), plan
+// construction (the band's TOD object) and the six step entry points.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <functional>
+#include <new>
+#include <numeric>
+#include <thread>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace tg;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// ---------------------------------------------------------------------------
+// host helpers
+// ---------------------------------------------------------------------------
+void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)> &f)
+{
+    unsigned hw = std::thread::hardware_concurrency();
+    int64_t nt = std::max<int64_t>(1, std::min<int64_t>(hw ? hw : 4, 64));
+    nt = std::min<int64_t>(nt, std::max<int64_t>(1, n));
+    if (nt <= 1) { f(0, n); return; }
+    std::vector<std::thread> th;
+    std::atomic<int64_t> next(0);
+    const int64_t grain = std::max<int64_t>(1, n / (nt * 8));
+    for (int64_t i = 0; i < nt; ++i)
+        th.emplace_back([&]() {
+            for (;;) {
+                const int64_t a = next.fetch_add(grain);
+                if (a >= n) break;
+                f(a, std::min(n, a + grain));
+            }
+        });
+    for (auto &t : th) t.join();
+}
+
+// Code lengths of symbols (ascending value) from counts: two-queue Huffman
+// merge over leaves ordered by (count, value), a leaf winning ties against a
+// merged node; lengths over TOD_HUFF_MAXLEN halve every count ((c+1)/2) and
+// rebuild.  The format (and so these rules) is shared with every reader of
+// the streams.
+std::vector<uint8_t> huffman_lengths(const std::vector<int64_t> &counts_in)
+{
+    const size_t k = counts_in.size();
+    std::vector<uint8_t> len(k, 0);
+    if (k == 1) { len[0] = 1; return len; }
+    std::vector<int64_t> cnt(counts_in);
+    for (auto &c : cnt) c = std::max<int64_t>(c, 1);
+    for (;;) {
+        std::vector<uint32_t> order(k);
+        std::iota(order.begin(), order.end(), 0u);
+        std::stable_sort(order.begin(), order.end(),
+                         [&](uint32_t a, uint32_t b) { return cnt[a] < cnt[b]; });
+        // node weights: [0,k) leaves in 'order', [k, 2k-1) merged nodes
+        std::vector<int64_t> wt(2 * k - 1);
+        std::vector<int32_t> up(2 * k - 1, -1);
+        for (size_t i = 0; i < k; ++i) wt[i] = cnt[order[i]];
+        size_t leaf = 0, mhead = k, mtail = k;
+        auto pop = [&]() -> size_t {
+            const bool use_leaf = leaf < k && (mhead == mtail || wt[leaf] <= wt[mhead]);
+            return use_leaf ? leaf++ : mhead++;
+        };
+        while (mtail < 2 * k - 1) {
+            const size_t a = pop(), b = pop();
+            wt[mtail] = wt[a] + wt[b];
+            up[a] = static_cast<int32_t>(mtail);
+            up[b] = static_cast<int32_t>(mtail);
+            ++mtail;
+        }
+        // depths top-down: a parent is always created after its children
+        std::vector<int32_t> depth(2 * k - 1, 0);
+        for (size_t i = 2 * k - 2; i-- > 0;) depth[i] = depth[up[i]] + 1;
+        int maxd = 0;
+        for (size_t i = 0; i < k; ++i) {
+            len[order[i]] = static_cast<uint8_t>(std::min(depth[i], 255));
+            maxd = std::max(maxd, depth[i]);
+        }
+        if (maxd <= TOD_HUFF_MAXLEN) break;
+        for (auto &c : cnt) c = (c + 1) / 2;
+    }
+    return len;
+}
+
+// Canonical code words: ordered by (length, value), consecutive, shifted at
+// each length increase.
+std::vector<uint32_t> canonical_codes(const std::vector<uint8_t> &len)
+{
+    const size_t k = len.size();
+    std::vector<uint32_t> idx(k), code(k, 0);
+    std::iota(idx.begin(), idx.end(), 0u);
+    std::stable_sort(idx.begin(), idx.end(), [&](uint32_t a, uint32_t b) { return len[a] < len[b]; });
+    uint32_t c = 0;
+    for (size_t i = 0; i < k; ++i) {
+        if (i) c = (c + 1) << (len[idx[i]] - len[idx[i - 1]]);
+        code[idx[i]] = c;
+    }
+    return code;
+}
+
+// canonical decode tables of one code (symbols ascending with lengths)
+struct DecTab {
+    std::vector<int2> lut;                  // 1 << DEC_LUTB
+    unsigned long long lim[26];
+    int32_t base[26];
+    std::vector<int32_t> canon;
+};
+
+DecTab build_dectab(const int32_t *vals, const uint8_t *len, int64_t k)
+{
+    DecTab t;
+    std::vector<int64_t> count(33, 0);
+    for (int64_t i = 0; i < k; ++i) count[len[i]]++;
+    // canonical order
+    std::vector<int64_t> idx(k);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) { return len[a] < len[b]; });
+    t.canon.resize(k);
+    for (int64_t i = 0; i < k; ++i) t.canon[i] = vals[idx[i]];
+    uint64_t first = 0;
+    int64_t index = 0;
+    for (int L = 0; L < 26; ++L) { t.lim[L] = 0; t.base[L] = 0; }
+    for (int L = 1; L <= TOD_HUFF_MAXLEN; ++L) {
+        if (L > 1) first = (first + count[L - 1]) << 1;
+        t.base[L] = static_cast<int32_t>(index - static_cast<int64_t>(first));
+        t.lim[L] = (first + count[L]) << (32 - L);
+        index += count[L];
+    }
+    t.lim[25] = ~0ull;
+    t.lut.assign(1 << DEC_LUTB, make_int2(0, 0));
+    for (uint32_t v = 0; v < (1u << DEC_LUTB); ++v) {
+        const uint64_t peek = static_cast<uint64_t>(v) << (32 - DEC_LUTB);
+        for (int L = 1; L <= DEC_LUTB; ++L) {
+            if (peek < t.lim[L]) {
+                const int64_t ci = t.base[L] + static_cast<int64_t>(peek >> (32 - L));
+                if (ci >= 0 && ci < k) t.lut[v] = make_int2(t.canon[ci], L);
+                break;
+            }
+        }
+    }
+    return t;
+}
+
+// decode one detscan on the host (plan construction only)
+bool host_decode(const tod_huff_streams &h, const DecTab &t, int64_t q, int64_t n, int32_t *out)
+{
+    const int64_t w0 = h.word_off[q], w1 = h.word_off[q + 1];
+    const int64_t nb = h.nbits[q];
+    int64_t pos = 0;
+    int32_t x = 0;
+    auto bit_window = [&](int64_t p) -> uint32_t {   // 32 bits starting at p (zero past the end)
+        const int64_t w = p >> 5;
+        const int sh = static_cast<int>(p & 31);
+        const uint64_t a = (w0 + w < w1) ? h.words[w0 + w] : 0u;
+        const uint64_t b = (w0 + w + 1 < w1) ? h.words[w0 + w + 1] : 0u;
+        return static_cast<uint32_t>((((a << 32) | b) << sh) >> 32);
+    };
+    const int64_t k = static_cast<int64_t>(t.canon.size());
+    for (int64_t i = 0; i < n; ++i) {
+        const uint32_t peek = bit_window(pos);
+        int L = 1;
+        while (L <= TOD_HUFF_MAXLEN && static_cast<uint64_t>(peek) >= t.lim[L]) ++L;
+        if (L > TOD_HUFF_MAXLEN) return false;
+        const int64_t ci = t.base[L] + static_cast<int64_t>(peek >> (32 - L));
+        if (ci < 0 || ci >= k) return false;
+        x += t.canon[ci];
+        out[i] = x;
+        pos += L;
+        if (pos > nb) return false;
+    }
+    return pos == nb;
+}
+
+template <class T>
+cudaError_t dev_upload(Plan &p, T *&dst, const T *src, size_t count)
+{
+    dst = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&dst), count * sizeof(T));
+    if (e != cudaSuccess) return e;
+    p.allocs.push_back(dst);
+    p.device_bytes += static_cast<int64_t>(count * sizeof(T));
+    if (src) return cudaMemcpy(dst, src, count * sizeof(T), cudaMemcpyHostToDevice);
+    return cudaMemset(dst, 0, count * sizeof(T));
+}
+
+void free_plan(Plan *p)
+{
+    if (!p) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(p->device);
+    for (void *a : p->allocs) cudaFree(a);
+    cudaSetDevice(cur);
+    delete p;
+}
+
+int64_t fft_length_impl(int64_t n)
+{
+    if (n < 2) return 0;
+    int64_t best = 0;
+    for (int64_t a = 2; a <= n; a *= 2)
+        for (int64_t b = a; b <= n; b *= 3)
+            for (int64_t c = b; c <= n; c *= 5) best = std::max(best, c);
+    return best;
+}
+
+std::vector<int8_t> radix_plan(int L)
+{
+    std::vector<int8_t> r;
+    while (L % 4 == 0) { r.push_back(4); L /= 4; }
+    while (L % 2 == 0) { r.push_back(2); L /= 2; }
+    while (L % 3 == 0) { r.push_back(3); L /= 3; }
+    while (L % 5 == 0) { r.push_back(5); L /= 5; }
+    if (L != 1) r.clear();
+    return r;
+}
+
+bool has5(const std::vector<int8_t> &r) { return std::find(r.begin(), r.end(), 5) != r.end(); }
+
+// Choose m1 x m2 for one length with C CTAs; returns false if none fits.
+bool choose_factor(int n, int C, DctPlan &out, int &sz)
+{
+    const int m = n / 2;
+    int best = -1, bestm1 = 0;
+    for (int m1 = 2; m1 <= m; ++m1) {
+        if (m % m1) continue;
+        const int m2 = m / m1;
+        if (m2 < 2) continue;
+        const auto r1 = radix_plan(m1), r2 = radix_plan(m2);
+        if (r1.empty() || r2.empty() || r1.size() > DCT_MAXR || r2.size() > DCT_MAXR) continue;
+        const int ncolmax = (m2 + C - 1) / C;
+        const int P = m1 / 2 + 1;
+        const int npmax = (P + C - 1) / C;
+        const int asz = m1 * ncolmax, bsz = 2 * npmax * m2;
+        const int acap = has5(r1) ? 20 * DCT_T : DCT_EMAX * DCT_T;
+        const int bcap = has5(r2) ? 20 * DCT_T : DCT_EMAX * DCT_T;
+        if (asz > acap || bsz > bcap) continue;
+        const int s = std::max(asz, bsz);
+        if (best < 0 || s < best || (s == best && std::abs(m1 - m2) < std::abs(bestm1 - m / bestm1))) {
+            best = s;
+            bestm1 = m1;
+        }
+    }
+    if (best < 0) return false;
+    const int m1 = bestm1, m2 = m / m1;
+    const auto r1 = radix_plan(m1), r2 = radix_plan(m2);
+    std::memset(&out, 0, sizeof(out));
+    out.n = n; out.m = m; out.m1 = m1; out.m2 = m2;
+    out.ncolmax = (m2 + C - 1) / C;
+    out.P = m1 / 2 + 1;
+    out.npmax = (out.P + C - 1) / C;
+    out.nr1 = static_cast<int32_t>(r1.size());
+    out.nr2 = static_cast<int32_t>(r2.size());
+    for (size_t i = 0; i < r1.size(); ++i) out.r1[i] = r1[i];
+    for (size_t i = 0; i < r2.size(); ++i) out.r2[i] = r2[i];
+    sz = best;
+    return true;
+}
+
+tod_status to_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return TOD_OK;
+    if (e == cudaErrorMemoryAllocation) return TOD_ERR_OOM;
+    return TOD_ERR_CUDA;
+}
+
+struct DeviceGuard {
+    int prev = 0;
+    explicit DeviceGuard(int dev) { cudaGetDevice(&prev); if (prev != dev) cudaSetDevice(dev); }
+    ~DeviceGuard() { int cur = 0; cudaGetDevice(&cur); if (cur != prev) cudaSetDevice(prev); }
+};
+
+bool valid_streams(const tod_huff_streams &h, int64_t nq, int64_t nscan, const std::vector<int64_t> &off)
+{
+    if (!h.words || !h.word_off || !h.nbits || !h.blk_off || !h.ckpt_bit || !h.ckpt_val ||
+        !h.sym_off || !h.sym_vals || !h.sym_len)
+        return false;
+    if (h.word_off[0] != 0 || h.word_off[nq] != h.nwords || h.blk_off[0] != 0 || h.blk_off[nq] != h.nblk)
+        return false;
+    if (h.sym_off[0] != 0 || h.sym_off[nscan] != h.nsym) return false;
+    for (int64_t q = 0; q < nq; ++q) {
+        const int64_t n = off[q + 1] - off[q];
+        if (h.word_off[q + 1] < h.word_off[q]) return false;
+        if (h.nbits[q] < 0 || h.nbits[q] > 32 * (h.word_off[q + 1] - h.word_off[q])) return false;
+        if (h.blk_off[q + 1] - h.blk_off[q] != (n + TOD_CKPT_BLOCK - 1) / TOD_CKPT_BLOCK) return false;
+        for (int64_t b = h.blk_off[q]; b < h.blk_off[q + 1]; ++b)
+            if (static_cast<int64_t>(h.ckpt_bit[b]) > h.nbits[q]) return false;
+    }
+    for (int64_t s = 0; s < nscan; ++s) {
+        if (h.sym_off[s + 1] <= h.sym_off[s]) return false;
+        for (int64_t i = h.sym_off[s]; i < h.sym_off[s + 1]; ++i)
+            if (h.sym_len[i] < 1 || h.sym_len[i] > TOD_HUFF_MAXLEN) return false;
+    }
+    return true;
+}
+
+cudaError_t build_huff(Plan &p, HuffDev &d, const tod_huff_streams &h)
+{
+    cudaError_t e;
+    std::vector<uint32_t> words(h.nwords + 4, 0u);
+    std::memcpy(words.data(), h.words, sizeof(uint32_t) * h.nwords);
+    if ((e = dev_upload(p, d.words, words.data(), words.size()))) return e;
+    if ((e = dev_upload(p, d.word_off, h.word_off, p.nq + 1))) return e;
+    if ((e = dev_upload(p, d.nbits, h.nbits, p.nq))) return e;
+    if ((e = dev_upload(p, d.blk_off, h.blk_off, p.nq + 1))) return e;
+    if ((e = dev_upload(p, d.ckpt_bit, h.ckpt_bit, h.nblk))) return e;
+    if ((e = dev_upload(p, d.ckpt_val, h.ckpt_val, h.nblk))) return e;
+    std::vector<int32_t> blk_q(h.nblk);
+    for (int64_t q = 0; q < p.nq; ++q)
+        for (int64_t b = h.blk_off[q]; b < h.blk_off[q + 1]; ++b) blk_q[b] = static_cast<int32_t>(q);
+    if ((e = dev_upload(p, d.blk_q, blk_q.data(), blk_q.size()))) return e;
+    d.nblk = h.nblk;
+    std::vector<int2> lut(static_cast<size_t>(p.nscan) << DEC_LUTB);
+    std::vector<unsigned long long> lim(static_cast<size_t>(p.nscan) * 26);
+    std::vector<int32_t> base(static_cast<size_t>(p.nscan) * 26);
+    std::vector<int32_t> canon_off(p.nscan + 1, 0), canon;
+    std::vector<int32_t> cta_scan;
+    std::vector<int64_t> cta_blk0;
+    std::vector<int32_t> cta_nblk;
+    for (int s = 0; s < p.nscan; ++s) {
+        const int64_t a = h.sym_off[s], k = h.sym_off[s + 1] - a;
+        DecTab t = build_dectab(h.sym_vals + a, h.sym_len + a, k);
+        std::copy(t.lut.begin(), t.lut.end(), lut.begin() + (static_cast<size_t>(s) << DEC_LUTB));
+        for (int L = 0; L < 26; ++L) { lim[s * 26 + L] = t.lim[L]; base[s * 26 + L] = t.base[L]; }
+        canon.insert(canon.end(), t.canon.begin(), t.canon.end());
+        canon_off[s + 1] = static_cast<int32_t>(canon.size());
+        d.max_canon = std::max<int32_t>(d.max_canon, static_cast<int32_t>(k));
+        const int64_t b0 = h.blk_off[static_cast<int64_t>(s) * p.ndet];
+        const int64_t b1 = h.blk_off[static_cast<int64_t>(s + 1) * p.ndet];
+        for (int64_t b = b0; b < b1; b += DEC_T) {
+            cta_scan.push_back(s);
+            cta_blk0.push_back(b);
+            cta_nblk.push_back(static_cast<int32_t>(std::min<int64_t>(DEC_T, b1 - b)));
+        }
+    }
+    if ((e = dev_upload(p, d.lut, lut.data(), lut.size()))) return e;
+    if ((e = dev_upload(p, d.lim, lim.data(), lim.size()))) return e;
+    if ((e = dev_upload(p, d.base, base.data(), base.size()))) return e;
+    if ((e = dev_upload(p, d.canon_off, canon_off.data(), canon_off.size()))) return e;
+    if ((e = dev_upload(p, d.canon_vals, canon.data(), canon.size()))) return e;
+    if ((e = dev_upload(p, d.cta_scan, cta_scan.data(), cta_scan.size()))) return e;
+    if ((e = dev_upload(p, d.cta_blk0, cta_blk0.data(), cta_blk0.size()))) return e;
+    if ((e = dev_upload(p, d.cta_nblk, cta_nblk.data(), cta_nblk.size()))) return e;
+    d.ncta = static_cast<int32_t>(cta_scan.size());
+    return cudaSuccess;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char *tod_status_string(tod_status s)
+{
+    switch (s) {
+    case TOD_OK: return "ok";
+    case TOD_ERR_ARG: return "invalid argument";
+    case TOD_ERR_CORRUPT_STREAM: return "corrupt Huffman stream";
+    case TOD_ERR_NOT_CONVERGED: return "conjugate gradients did not converge";
+    case TOD_ERR_TIMEOUT: return "bounded device wait timed out";
+    case TOD_ERR_CUDA: return "CUDA runtime error";
+    case TOD_ERR_OOM: return "out of memory";
+    case TOD_ERR_UNIMPLEMENTED: return "not implemented";
+    default: return "unknown status";
+    }
+}
+
+int64_t tod_fft_length(int64_t n) { return fft_length_impl(n); }
+
+void tod_huff_free(tod_huff_buffers *b)
+{
+    if (!b) return;
+    std::free(b->words); std::free(b->word_off); std::free(b->nbits); std::free(b->blk_off);
+    std::free(b->ckpt_bit); std::free(b->ckpt_val); std::free(b->sym_off); std::free(b->sym_vals);
+    std::free(b->sym_len);
+    std::memset(b, 0, sizeof(*b));
+}
+
+tod_status tod_huff_encode(int32_t ndet, int32_t nscan, const int64_t *offsets, const int32_t *values,
+                           tod_huff_buffers *out)
+{
+    if (!out || !offsets || ndet <= 0 || nscan <= 0) return TOD_ERR_ARG;
+    std::memset(out, 0, sizeof(*out));
+    const int64_t nq = static_cast<int64_t>(ndet) * nscan;
+    for (int64_t q = 0; q < nq; ++q)
+        if (offsets[q + 1] < offsets[q]) return TOD_ERR_ARG;
+    if (offsets[0] != 0 || (offsets[nq] > 0 && !values)) return TOD_ERR_ARG;
+    try {
+        // per scan: code over the deltas of all its detectors
+        std::vector<std::vector<int32_t>> svals(nscan);
+        std::vector<std::vector<uint8_t>> slen(nscan);
+        std::vector<std::vector<uint32_t>> scode(nscan);
+        parallel_for(nscan, [&](int64_t a, int64_t b) {
+            for (int64_t s = a; s < b; ++s) {
+                std::vector<int32_t> dl;
+                for (int64_t q = s * ndet; q < (s + 1) * ndet; ++q) {
+                    int32_t prev = 0;
+                    for (int64_t t = offsets[q]; t < offsets[q + 1]; ++t) {
+                        dl.push_back(values[t] - prev);
+                        prev = values[t];
+                    }
+                }
+                std::sort(dl.begin(), dl.end());
+                std::vector<int32_t> v;
+                std::vector<int64_t> c;
+                for (size_t i = 0; i < dl.size();) {
+                    size_t j = i;
+                    while (j < dl.size() && dl[j] == dl[i]) ++j;
+                    v.push_back(dl[i]);
+                    c.push_back(static_cast<int64_t>(j - i));
+                    i = j;
+                }
+                if (v.empty()) { v.push_back(0); c.push_back(1); }
+                slen[s] = huffman_lengths(c);
+                scode[s] = canonical_codes(slen[s]);
+                svals[s] = std::move(v);
+            }
+        });
+        // bit lengths per detscan
+        std::vector<int64_t> nbits(nq, 0), nblk(nq, 0);
+        parallel_for(nq, [&](int64_t a, int64_t b) {
+            for (int64_t q = a; q < b; ++q) {
+                const auto &v = svals[q / ndet];
+                const auto &L = slen[q / ndet];
+                int32_t prev = 0;
+                int64_t bits = 0;
+                for (int64_t t = offsets[q]; t < offsets[q + 1]; ++t) {
+                    const int32_t dv = values[t] - prev;
+                    prev = values[t];
+                    bits += L[std::lower_bound(v.begin(), v.end(), dv) - v.begin()];
+                }
+                nbits[q] = bits;
+                nblk[q] = (offsets[q + 1] - offsets[q] + TOD_CKPT_BLOCK - 1) / TOD_CKPT_BLOCK;
+            }
+        });
+        const auto alloc = [](size_t bytes) { void *p = std::calloc(bytes ? bytes : 1, 1); if (!p) throw std::bad_alloc(); return p; };
+        out->word_off = static_cast<int64_t *>(alloc(sizeof(int64_t) * (nq + 1)));
+        out->nbits = static_cast<int64_t *>(alloc(sizeof(int64_t) * nq));
+        out->blk_off = static_cast<int64_t *>(alloc(sizeof(int64_t) * (nq + 1)));
+        for (int64_t q = 0; q < nq; ++q) {
+            out->word_off[q + 1] = out->word_off[q] + (nbits[q] + 31) / 32;
+            out->blk_off[q + 1] = out->blk_off[q] + nblk[q];
+            out->nbits[q] = nbits[q];
+        }
+        out->nwords = out->word_off[nq];
+        out->nblk = out->blk_off[nq];
+        out->words = static_cast<uint32_t *>(alloc(sizeof(uint32_t) * out->nwords));
+        out->ckpt_bit = static_cast<uint32_t *>(alloc(sizeof(uint32_t) * out->nblk));
+        out->ckpt_val = static_cast<int32_t *>(alloc(sizeof(int32_t) * out->nblk));
+        parallel_for(nq, [&](int64_t a, int64_t b) {
+            for (int64_t q = a; q < b; ++q) {
+                const auto &v = svals[q / ndet];
+                const auto &L = slen[q / ndet];
+                const auto &cw = scode[q / ndet];
+                uint32_t *w = out->words + out->word_off[q];
+                uint64_t acc = 0;          // pending bits, left-aligned in the low 'fill' bits
+                int fill = 0;
+                int64_t wi = 0, bitpos = 0;
+                int32_t prev = 0;
+                for (int64_t t = offsets[q], i = 0; t < offsets[q + 1]; ++t, ++i) {
+                    if (i % TOD_CKPT_BLOCK == 0) {
+                        const int64_t blk = out->blk_off[q] + i / TOD_CKPT_BLOCK;
+                        out->ckpt_bit[blk] = static_cast<uint32_t>(bitpos);
+                        out->ckpt_val[blk] = prev;
+                    }
+                    const int32_t dv = values[t] - prev;
+                    prev = values[t];
+                    const size_t si = std::lower_bound(v.begin(), v.end(), dv) - v.begin();
+                    const int l = L[si];
+                    acc = (acc << l) | cw[si];
+                    fill += l;
+                    bitpos += l;
+                    while (fill >= 32) {
+                        w[wi++] = static_cast<uint32_t>(acc >> (fill - 32));
+                        fill -= 32;
+                    }
+                }
+                if (fill > 0) w[wi++] = static_cast<uint32_t>(acc << (32 - fill));
+            }
+        });
+        // code tables
+        int64_t nsym = 0;
+        for (int s = 0; s < nscan; ++s) nsym += static_cast<int64_t>(svals[s].size());
+        out->nsym = nsym;
+        out->sym_off = static_cast<int64_t *>(alloc(sizeof(int64_t) * (nscan + 1)));
+        out->sym_vals = static_cast<int32_t *>(alloc(sizeof(int32_t) * nsym));
+        out->sym_len = static_cast<uint8_t *>(alloc(nsym));
+        for (int s = 0; s < nscan; ++s) {
+            out->sym_off[s + 1] = out->sym_off[s] + static_cast<int64_t>(svals[s].size());
+            std::copy(svals[s].begin(), svals[s].end(), out->sym_vals + out->sym_off[s]);
+            std::copy(slen[s].begin(), slen[s].end(), out->sym_len + out->sym_off[s]);
+        }
+    } catch (const std::bad_alloc &) {
+        tod_huff_free(out);
+        return TOD_ERR_OOM;
+    }
+    return TOD_OK;
+}
+
+tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
+{
+    if (!out || !band) return TOD_ERR_ARG;
+    *out = nullptr;
+    if (band->nside <= 0 || band->nside > 8192 || band->ndet <= 0 || band->nscan <= 0 ||
+        band->n_psi != TOD_N_PSI || !(band->fsamp > 0) || !band->offsets)
+        return TOD_ERR_ARG;
+    const int cs = band->cluster_size;
+    if (cs != 0 && cs != 1 && cs != 2 && cs != 4 && cs != 8 && cs != 16) return TOD_ERR_ARG;
+    Plan *p = new (std::nothrow) Plan();
+    if (!p) return TOD_ERR_OOM;
+    p->device = band->device;
+    DeviceGuard dg(p->device);
+    p->nside = band->nside;
+    p->npix = 12 * band->nside * band->nside;
+    p->ndet = band->ndet;
+    p->nscan = band->nscan;
+    p->nq = band->ndet * band->nscan;
+    p->fsamp = band->fsamp;
+    p->h_off.assign(band->offsets, band->offsets + p->nq + 1);
+    if (p->h_off[0] != 0) { delete p; return TOD_ERR_ARG; }
+    for (int q = 0; q < p->nq; ++q) {
+        const int64_t n = p->h_off[q + 1] - p->h_off[q];
+        if (n < 4 || n != fft_length_impl(n) || n > (int64_t(1) << 24)) { delete p; return TOD_ERR_ARG; }
+        if (q % p->ndet && n != p->h_off[q] - p->h_off[q - 1]) { delete p; return TOD_ERR_ARG; }
+    }
+    p->N = p->h_off[p->nq];
+    if (p->N >= (int64_t(1) << 32)) { delete p; return TOD_ERR_ARG; }
+    if (!valid_streams(band->pix, p->nq, p->nscan, p->h_off) ||
+        !valid_streams(band->psi, p->nq, p->nscan, p->h_off)) {
+        delete p;
+        return TOD_ERR_ARG;
+    }
+    cudaError_t e = cudaSetDevice(p->device);
+    if (e != cudaSuccess) { delete p; return TOD_ERR_CUDA; }
+    const auto fail = [&](cudaError_t err) { const tod_status s = to_status(err); free_plan(p); return s; };
+
+    if ((e = dev_upload(*p, p->off, p->h_off.data(), p->h_off.size()))) return fail(e);
+    if ((e = dev_upload(*p, p->status, static_cast<int32_t *>(nullptr), p->nq))) return fail(e);
+    if ((e = build_huff(*p, p->hpix, band->pix))) return fail(e);
+    if ((e = build_huff(*p, p->hpsi, band->psi))) return fail(e);
+
+    // element-wise tiles
+    {
+        std::vector<int32_t> tq;
+        std::vector<int64_t> t0;
+        for (int q = 0; q < p->nq; ++q)
+            for (int64_t t = p->h_off[q]; t < p->h_off[q + 1]; t += ELEM_TILE) { tq.push_back(q); t0.push_back(t); }
+        p->ntile = static_cast<int32_t>(tq.size());
+        if ((e = dev_upload(*p, p->tile_q, tq.data(), tq.size()))) return fail(e);
+        if ((e = dev_upload(*p, p->tile_t0, t0.data(), t0.size()))) return fail(e);
+    }
+    // psi table: FP32 values of cos 2psi, sin 2psi at the bin centres
+    {
+        std::vector<float2> trig(TOD_N_PSI);
+        for (int b = 0; b < TOD_N_PSI; ++b) {
+            const double psi = (b + 0.5) * (2.0 * kPi / TOD_N_PSI);
+            trig[b] = make_float2(static_cast<float>(std::cos(2.0 * psi)), static_cast<float>(std::sin(2.0 * psi)));
+        }
+        if ((e = dev_upload(*p, p->trig, trig.data(), trig.size()))) return fail(e);
+    }
+    // work list: decreasing length
+    {
+        std::vector<int32_t> w(p->nq);
+        std::iota(w.begin(), w.end(), 0);
+        std::stable_sort(w.begin(), w.end(), [&](int a, int b) {
+            return p->h_off[a + 1] - p->h_off[a] > p->h_off[b + 1] - p->h_off[b];
+        });
+        if ((e = dev_upload(*p, p->work, w.data(), w.size()))) return fail(e);
+    }
+    // transform plans
+    {
+        std::vector<int> lens;
+        for (int q = 0; q < p->nq; ++q) lens.push_back(static_cast<int>(p->h_off[q + 1] - p->h_off[q]));
+        std::vector<int> uniq(lens);
+        std::sort(uniq.begin(), uniq.end());
+        uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+        std::vector<DctPlan> plans;
+        int chosenC = 0;
+        const int cands[5] = {1, 2, 4, 8, 16};
+        for (int ci = 0; ci < 5 && !chosenC; ++ci) {
+            const int C = cands[ci];
+            if (cs && C != cs) continue;
+            plans.clear();
+            int sz = 0, m1max = 0, m2max = 0;
+            bool ok = true;
+            for (int n : uniq) {
+                DctPlan dp;
+                int s = 0;
+                if (!choose_factor(n, C, dp, s)) { ok = false; break; }
+                plans.push_back(dp);
+                sz = std::max(sz, s);
+                m1max = std::max(m1max, dp.m1);
+                m2max = std::max(m2max, dp.m2);
+            }
+            if (!ok) continue;
+            const size_t smem = sizeof(float2) * (2 * static_cast<size_t>(sz) + m1max + m2max) +
+                                static_cast<size_t>(CG_KCAP) * 20 + 4096;
+            if (smem > 227 * 1024) continue;
+            chosenC = C;
+            p->sz = sz; p->m1max = m1max; p->m2max = m2max;
+        }
+        if (!chosenC) { free_plan(p); return TOD_ERR_ARG; }
+        p->C = chosenC;
+        // twiddle tables per plan
+        std::vector<float2> tw;
+        for (auto &dp : plans) {
+            for (int which = 0; which < 2; ++which) {
+                const int L = which ? dp.m2 : dp.m1;
+                (which ? dp.tw2 : dp.tw1) = static_cast<int32_t>(tw.size());
+                for (int i = 0; i < L; ++i) {
+                    const double ang = -2.0 * kPi * i / L;
+                    tw.push_back(make_float2(static_cast<float>(std::cos(ang)), static_cast<float>(std::sin(ang))));
+                }
+            }
+        }
+        std::vector<int32_t> qp(p->nq);
+        for (int q = 0; q < p->nq; ++q)
+            qp[q] = static_cast<int32_t>(std::lower_bound(uniq.begin(), uniq.end(), lens[q]) - uniq.begin());
+        p->nplans = static_cast<int32_t>(plans.size());
+        if ((e = dev_upload(*p, p->plans, plans.data(), plans.size()))) return fail(e);
+        if ((e = dev_upload(*p, p->q_plan, qp.data(), qp.size()))) return fail(e);
+        if ((e = dev_upload(*p, p->tw, tw.data(), tw.size()))) return fail(e);
+        if ((e = setup_dct_kernels(*p))) return fail(e);
+    }
+    // binning structure from the pointing (fixed during the run)
+    {
+        std::vector<int32_t> pix(p->N);
+        std::vector<DecTab> tabs(p->nscan);
+        for (int s = 0; s < p->nscan; ++s) {
+            const int64_t a = band->pix.sym_off[s];
+            tabs[s] = build_dectab(band->pix.sym_vals + a, band->pix.sym_len + a, band->pix.sym_off[s + 1] - a);
+        }
+        std::atomic<bool> bad(false);
+        std::vector<uint32_t> lp(p->N);
+        std::vector<std::vector<int32_t>> rpix(p->nq), rlen(p->nq);
+        std::vector<std::vector<int64_t>> rstart(p->nq);
+        parallel_for(p->nq, [&](int64_t a, int64_t b) {
+            std::vector<uint64_t> key;
+            for (int64_t q = a; q < b; ++q) {
+                const int64_t o = p->h_off[q], n = p->h_off[q + 1] - o;
+                if (!host_decode(band->pix, tabs[q / p->ndet], q, n, pix.data() + o)) { bad = true; continue; }
+                key.resize(n);
+                for (int64_t t = 0; t < n; ++t) {
+                    const int32_t px = pix[o + t];
+                    if (px < 0 || px >= p->npix) { bad = true; break; }
+                    key[t] = (static_cast<uint64_t>(px) << 32) | static_cast<uint64_t>(t);
+                }
+                if (bad) continue;
+                std::sort(key.begin(), key.end());
+                for (int64_t i = 0; i < n; ++i) {
+                    lp[o + i] = static_cast<uint32_t>(key[i] & 0xFFFFFFFFu);
+                    const int32_t px = static_cast<int32_t>(key[i] >> 32);
+                    if (i == 0 || px != static_cast<int32_t>(key[i - 1] >> 32)) {
+                        rpix[q].push_back(px);
+                        rstart[q].push_back(o + i);
+                        rlen[q].push_back(1);
+                    } else {
+                        rlen[q].back()++;
+                    }
+                }
+            }
+        });
+        if (bad) { free_plan(p); return TOD_ERR_CORRUPT_STREAM; }
+        std::vector<int64_t> pair_off(p->nq + 1, 0);
+        for (int q = 0; q < p->nq; ++q) pair_off[q + 1] = pair_off[q] + static_cast<int64_t>(rpix[q].size());
+        p->npairs = pair_off[p->nq];
+        std::vector<int64_t> pstart(p->npairs), pslot_off(static_cast<size_t>(p->npix) + 1, 0);
+        std::vector<int32_t> plen(p->npairs), pslot(p->npairs);
+        for (int q = 0; q < p->nq; ++q)
+            for (size_t i = 0; i < rpix[q].size(); ++i) pslot_off[rpix[q][i] + 1]++;
+        for (int px = 0; px < p->npix; ++px) pslot_off[px + 1] += pslot_off[px];
+        std::vector<int64_t> fillc(pslot_off.begin(), pslot_off.end() - 1);
+        for (int q = 0; q < p->nq; ++q)
+            for (size_t i = 0; i < rpix[q].size(); ++i) {
+                const int64_t pr = pair_off[q] + static_cast<int64_t>(i);
+                pstart[pr] = rstart[q][i];
+                plen[pr] = rlen[q][i];
+                pslot[pr] = static_cast<int32_t>(fillc[rpix[q][i]]++);
+            }
+        if (p->npairs >= (int64_t(1) << 31)) { free_plan(p); return TOD_ERR_ARG; }
+        if ((e = dev_upload(*p, p->lp, lp.data(), lp.size()))) return fail(e);
+        if ((e = dev_upload(*p, p->pair_off, pair_off.data(), pair_off.size()))) return fail(e);
+        if ((e = dev_upload(*p, p->pair_start, pstart.data(), pstart.size()))) return fail(e);
+        if ((e = dev_upload(*p, p->pair_len, plen.data(), plen.size()))) return fail(e);
+        if ((e = dev_upload(*p, p->pair_slot, pslot.data(), pslot.size()))) return fail(e);
+        if ((e = dev_upload(*p, p->pix_slot_off, pslot_off.data(), pslot_off.size()))) return fail(e);
+        if ((e = dev_upload(*p, p->rec, static_cast<double *>(nullptr), static_cast<size_t>(p->npairs) * 10))) return fail(e);
+    }
+    if ((e = cudaDeviceSynchronize())) return fail(e);
+    *out = reinterpret_cast<tod_plan *>(p);
+    return TOD_OK;
+}
+
+tod_status tod_plan_destroy(tod_plan *pl)
+{
+    if (!pl) return TOD_ERR_ARG;
+    free_plan(reinterpret_cast<Plan *>(pl));
+    return TOD_OK;
+}
+
+tod_status tod_plan_info(const tod_plan *pl, int64_t *nsamples, int32_t *ndetscan, int32_t *npix,
+                         int32_t *cluster_size, int64_t *device_bytes)
+{
+    if (!pl) return TOD_ERR_ARG;
+    const Plan *p = reinterpret_cast<const Plan *>(pl);
+    if (nsamples) *nsamples = p->N;
+    if (ndetscan) *ndetscan = p->nq;
+    if (npix) *npix = p->npix;
+    if (cluster_size) *cluster_size = p->C;
+    if (device_bytes) *device_bytes = p->device_bytes;
+    return TOD_OK;
+}
+
+tod_status tod_plan_status(tod_plan *pl, int32_t *detscan_status)
+{
+    if (!pl) return TOD_ERR_ARG;
+    Plan *p = reinterpret_cast<Plan *>(pl);
+    DeviceGuard dg(p->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return TOD_ERR_CUDA;
+    std::vector<int32_t> st(p->nq);
+    e = cudaMemcpy(st.data(), p->status, sizeof(int32_t) * p->nq, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return TOD_ERR_CUDA;
+    e = cudaMemset(p->status, 0, sizeof(int32_t) * p->nq);
+    if (e != cudaSuccess) return TOD_ERR_CUDA;
+    if (detscan_status) std::memcpy(detscan_status, st.data(), sizeof(int32_t) * p->nq);
+    for (int32_t s : st)
+        if (s != TOD_OK) return s;
+    return TOD_OK;
+}
+
+tod_status tod_decode(tod_plan *pl, int32_t *pix_out, uint16_t *psi_out, cudaStream_t stream)
+{
+    if (!pl || (!pix_out && !psi_out)) return TOD_ERR_ARG;
+    Plan *p = reinterpret_cast<Plan *>(pl);
+    DeviceGuard dg(p->device);
+    cudaError_t e = cudaSuccess;
+    if (pix_out) e = launch_decode(*p, p->hpix, pix_out, nullptr, stream);
+    if (e == cudaSuccess && psi_out) e = launch_decode(*p, p->hpsi, nullptr, psi_out, stream);
+    return to_status(e);
+}
+
+tod_status tod_project(tod_plan *pl, const void *map_tqu, const int32_t *pix, const uint16_t *psi,
+                       const double *gain, float *s_out, cudaStream_t stream)
+{
+    if (!pl || !map_tqu || !pix || !psi || !s_out) return TOD_ERR_ARG;
+    Plan *p = reinterpret_cast<Plan *>(pl);
+    DeviceGuard dg(p->device);
+    return to_status(launch_project(*p, static_cast<const float4 *>(map_tqu), pix, psi, gain, s_out, stream));
+}
+
+tod_status tod_sample_gain(tod_plan *pl, const float *d, const float *s, const uint32_t *flags,
+                           const double *psd, tod_rng rng, int32_t mode, double *gain_out,
+                           double *mu_out, double *sigma_out, cudaStream_t stream)
+{
+    if (!pl || !d || !s || !flags || !psd || !gain_out) return TOD_ERR_ARG;
+    if (mode != TOD_MODE_DRAW && mode != TOD_MODE_MEAN) return TOD_ERR_ARG;
+    Plan *p = reinterpret_cast<Plan *>(pl);
+    DeviceGuard dg(p->device);
+    return to_status(launch_gain(*p, d, s, flags, psd, rng, mode, gain_out, mu_out, sigma_out, stream, 0, p->nq));
+}
+
+tod_status tod_sample_ncorr(tod_plan *pl, const float *d, const float *s, const double *gain,
+                            const uint32_t *flags, const double *psd, tod_rng rng, int32_t mode,
+                            double cg_tol, int32_t cg_maxiter, float *ncorr_out, int32_t *cg_iters_out,
+                            cudaStream_t stream)
+{
+    if (!pl || !d || !s || !gain || !flags || !psd || !ncorr_out) return TOD_ERR_ARG;
+    if (mode != TOD_MODE_DRAW && mode != TOD_MODE_MEAN) return TOD_ERR_ARG;
+    Plan *p = reinterpret_cast<Plan *>(pl);
+    DeviceGuard dg(p->device);
+    const float tol = cg_tol > 0 ? static_cast<float>(cg_tol) : 1e-6f;
+    const int maxit = cg_maxiter > 0 ? cg_maxiter : 500;
+    return to_status(launch_ncorr(*p, d, s, gain, flags, psd, rng, mode, tol, maxit, ncorr_out,
+                                  cg_iters_out, stream, 0, p->nq));
+}
+
+tod_status tod_bin(tod_plan *pl, const uint16_t *psi, const float *d, const float *ncorr,
+                   const double *gain, const uint32_t *flags, const double *psd, double *A_out,
+                   double *b_out, int32_t *hits_out, cudaStream_t stream)
+{
+    if (!pl || !psi || !d || !ncorr || !gain || !flags || !psd || !A_out || !b_out || !hits_out)
+        return TOD_ERR_ARG;
+    Plan *p = reinterpret_cast<Plan *>(pl);
+    DeviceGuard dg(p->device);
+    return to_status(launch_bin(*p, psi, d, ncorr, gain, flags, psd, A_out, b_out, hits_out, stream));
+}
+
+tod_status tod_solve_maps(tod_plan *pl, const double *A, const double *b, const int32_t *hits,
+                          double rcond_min, double *map_out, void *map_f32_out, double *rcond_out,
+                          uint8_t *valid_out, cudaStream_t stream)
+{
+    if (!pl || !A || !b || !hits || !map_out) return TOD_ERR_ARG;
+    Plan *p = reinterpret_cast<Plan *>(pl);
+    DeviceGuard dg(p->device);
+    return to_status(launch_solve(*p, A, b, hits, rcond_min, map_out, static_cast<float4 *>(map_f32_out),
+                                  rcond_out, valid_out, stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,108 @@
+// Internal plan layout and kernel-launcher prototypes of libtodgibbs.
+#pragma once
+#include <cstdint>
+#include <vector>
+#include <cuda_runtime.h>
+#include "../../include/todgibbs.h"
+
+namespace tg {
+
+constexpr int DEC_LUTB = 10;          // first-level decode table: 2^10 entries
+constexpr int DEC_T = 256;            // decode threads per CTA (one checkpoint block each)
+constexpr int DEC_ROUND = 16;         // symbols staged per thread before a coalesced write
+constexpr int ELEM_TILE = 4096;       // samples per tile of the element-wise kernels
+constexpr int DCT_T = 512;            // threads per CTA of the cluster transform kernels
+constexpr int DCT_EMAX = 24;          // complex values per thread in one FFT stage
+constexpr int DCT_MAXR = 20;          // maximum number of radix stages per sub-transform
+constexpr int CG_KCAP = 1536;         // flagged samples per CTA held by the CG
+
+// Compressed stream kind, device copy + decode tables.
+struct HuffDev {
+    uint32_t *words = nullptr;       // + 2 zero pad words
+    int64_t *word_off = nullptr;     // [nq+1]
+    int64_t *nbits = nullptr;        // [nq]
+    int64_t *blk_off = nullptr;      // [nq+1]
+    uint32_t *ckpt_bit = nullptr;    // [nblk]
+    int32_t *ckpt_val = nullptr;     // [nblk]
+    int32_t *blk_q = nullptr;        // [nblk] detscan of each block
+    int2 *lut = nullptr;             // [nscan][1<<DEC_LUTB] (value, length) ; length 0 = long code
+    unsigned long long *lim = nullptr;  // [nscan][26] left-justified limits, index = length
+    int32_t *base = nullptr;         // [nscan][26]
+    int32_t *canon_off = nullptr;    // [nscan+1]
+    int32_t *canon_vals = nullptr;   // symbols in canonical order
+    int32_t *cta_scan = nullptr;     // decode work list: one entry per CTA
+    int64_t *cta_blk0 = nullptr;
+    int32_t *cta_nblk = nullptr;
+    int32_t ncta = 0;
+    int32_t max_canon = 0;           // largest code of any scan (symbols)
+    int64_t nblk = 0;
+};
+
+// Per-length transform plan (real DCT-II of length n via an m = n/2 complex
+// FFT split as m1 x m2 across a cluster of C CTAs).
+struct DctPlan {
+    int32_t n, m, m1, m2, ncolmax, npmax, P;
+    int32_t nr1, nr2;
+    int32_t tw1, tw2;                // offsets of the W_{m1}^i and W_{m2}^i tables
+    int8_t r1[DCT_MAXR], r2[DCT_MAXR];
+};
+
+struct Plan {
+    int device = 0;
+    int32_t nside = 0, npix = 0, ndet = 0, nscan = 0, nq = 0;
+    double fsamp = 0;
+    int64_t N = 0;
+    std::vector<int64_t> h_off;      // host copy of offsets
+    int64_t *off = nullptr;          // [nq+1] device
+    int32_t *status = nullptr;       // [nq] device
+    HuffDev hpix, hpsi;
+    // element-wise tiles
+    int32_t ntile = 0;
+    int32_t *tile_q = nullptr;
+    int64_t *tile_t0 = nullptr;
+    float2 *trig = nullptr;          // [TOD_N_PSI] (cos 2psi, sin 2psi) at bin centres, FP32
+    // transforms
+    int32_t C = 1;                   // CTAs per cluster
+    int32_t sz = 0;                  // complex values per CTA buffer (max over plans)
+    int32_t m1max = 0, m2max = 0;
+    int32_t nplans = 0;
+    DctPlan *plans = nullptr;        // device
+    int32_t *q_plan = nullptr;       // [nq] plan index of each detscan
+    float2 *tw = nullptr;            // twiddle tables
+    int32_t *work = nullptr;         // [nq] detscans sorted by decreasing length
+    int32_t nclusters_gain = 1, nclusters_ncorr = 1;
+    size_t smem_gain = 0, smem_ncorr = 0;
+    // binning
+    uint32_t *lp = nullptr;          // [N] per-detscan pixel-sorted local order
+    int64_t npairs = 0;
+    int64_t *pair_off = nullptr;     // [nq+1] runs of each detscan
+    int64_t *pair_start = nullptr;   // [npairs] first lp index (global) of the run
+    int32_t *pair_len = nullptr;     // [npairs]
+    int32_t *pair_slot = nullptr;    // [npairs] position in pixel-sorted run order
+    int64_t *pix_slot_off = nullptr; // [npix+1]
+    double *rec = nullptr;           // [npairs][10] per-run partial sums (scratch)
+    int64_t device_bytes = 0;
+    std::vector<void *> allocs;
+};
+
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_decode(const Plan &p, const HuffDev &h, int32_t *pix_out, uint16_t *psi_out,
+                          cudaStream_t st);
+cudaError_t launch_project(const Plan &p, const float4 *map, const int32_t *pix, const uint16_t *psi,
+                           const double *gain, float *s_out, cudaStream_t st);
+cudaError_t setup_dct_kernels(Plan &p);
+cudaError_t launch_gain(const Plan &p, const float *d, const float *s, const uint32_t *flags,
+                        const double *psd, tod_rng rng, int mode, double *g, double *mu,
+                        double *sig, cudaStream_t st, int work_begin, int work_count);
+cudaError_t launch_ncorr(const Plan &p, const float *d, const float *s, const double *gain,
+                         const uint32_t *flags, const double *psd, tod_rng rng, int mode,
+                         float tol, int maxit, float *x, int32_t *iters, cudaStream_t st,
+                         int work_begin, int work_count);
+cudaError_t launch_bin(const Plan &p, const uint16_t *psi, const float *d, const float *ncorr,
+                       const double *gain, const uint32_t *flags, const double *psd, double *A,
+                       double *b, int32_t *hits, cudaStream_t st);
+cudaError_t launch_solve(const Plan &p, const double *A, const double *b, const int32_t *hits,
+                         double rcond_min, double *map, float4 *map32, double *rcond,
+                         uint8_t *valid, cudaStream_t st);
+
+}  // namespace tg

@@ -1,0 +1,180 @@
+// A1 Huffman decode (paper Sect. 4.1) and A2 projection (Eq. `todmodel`).
+//
+// Decode: every checkpoint block (TOD_CKPT_BLOCK symbols of one detscan) is
+// decoded by one thread, starting from the block's bit offset and the value
+// preceding it, so a band's ~10^6 blocks decode in parallel.  One CTA takes
+// up to DEC_T consecutive blocks of one scan and stages that scan's code
+// (a 2^DEC_LUTB-entry first-level table, per-length limits for the long
+// codes, symbols in canonical order) in shared memory.  Values are undone
+// from their differences on the fly and staged DEC_ROUND at a time per
+// thread in shared memory, then written with coalesced stores.
+#include "common.cuh"
+#include "internal.cuh"
+
+namespace tg {
+
+template <typename OutT>
+__global__ void __launch_bounds__(DEC_T)
+k_decode(const uint32_t *__restrict__ words, const int64_t *__restrict__ word_off,
+         const int64_t *__restrict__ nbits, const int64_t *__restrict__ blk_off,
+         const uint32_t *__restrict__ ckpt_bit, const int32_t *__restrict__ ckpt_val,
+         const int32_t *__restrict__ blk_q, const int2 *__restrict__ lut,
+         const unsigned long long *__restrict__ lim_g, const int32_t *__restrict__ base_g,
+         const int32_t *__restrict__ canon_off, const int32_t *__restrict__ canon_vals,
+         const int32_t *__restrict__ cta_scan, const int64_t *__restrict__ cta_blk0,
+         const int32_t *__restrict__ cta_nblk, const int64_t *__restrict__ off,
+         OutT *__restrict__ out, int32_t *status)
+{
+    __shared__ int2 s_lut[1 << DEC_LUTB];
+    __shared__ unsigned long long s_lim[26];
+    __shared__ int32_t s_base[26];
+    __shared__ OutT s_tile[DEC_T][DEC_ROUND + 1];
+    __shared__ int64_t s_out0[DEC_T];
+    __shared__ int32_t s_cnt[DEC_T];
+
+    const int tid = threadIdx.x;
+    const int scan = cta_scan[blockIdx.x];
+    const int64_t b0 = cta_blk0[blockIdx.x];
+    const int nb = cta_nblk[blockIdx.x];
+
+    for (int i = tid; i < (1 << DEC_LUTB); i += DEC_T) s_lut[i] = lut[(int64_t)scan * (1 << DEC_LUTB) + i];
+    if (tid < 26) { s_lim[tid] = lim_g[scan * 26 + tid]; s_base[tid] = base_g[scan * 26 + tid]; }
+    // long codes (longer than DEC_LUTB bits) are rare: their symbols are read
+    // from global memory through the cache
+    const int c0 = canon_off[scan], nc = canon_off[scan + 1] - c0;
+
+    // this thread's block
+    const bool active = tid < nb;
+    int q = 0, cnt = 0;
+    int64_t pos = 0, end = 0, wptr = 0;
+    int32_t x = 0;
+    unsigned long long buf = 0;
+    int have = 0;                       // valid bits in buf (left-aligned)
+    bool ok = true;
+    if (active) {
+        const int64_t b = b0 + tid;
+        q = blk_q[b];
+        const int64_t j = b - blk_off[q];
+        const int64_t n = off[q + 1] - off[q];
+        cnt = static_cast<int>((n - j * TOD_CKPT_BLOCK < TOD_CKPT_BLOCK ? n - j * TOD_CKPT_BLOCK : TOD_CKPT_BLOCK));
+        s_out0[tid] = off[q] + j * TOD_CKPT_BLOCK;
+        s_cnt[tid] = cnt;
+        const int64_t w0 = word_off[q];
+        pos = w0 * 32 + ckpt_bit[b];
+        end = w0 * 32 + nbits[q];
+        x = ckpt_val[b];
+        wptr = pos >> 5;
+        const int sh = static_cast<int>(pos & 31);
+        buf = ((static_cast<unsigned long long>(words[wptr]) << 32) | words[wptr + 1]) << sh;
+        have = 64 - sh;
+        wptr += 2;
+    } else {
+        s_cnt[tid] = 0;
+        s_out0[tid] = 0;
+    }
+    __syncthreads();
+
+    for (int round = 0; round < TOD_CKPT_BLOCK / DEC_ROUND; ++round) {
+#pragma unroll 4
+        for (int i = 0; i < DEC_ROUND; ++i) {
+            const int idx = round * DEC_ROUND + i;
+            if (active && ok && idx < cnt) {
+                const uint32_t peek = static_cast<uint32_t>(buf >> 32);
+                const int2 e = s_lut[peek >> (32 - DEC_LUTB)];
+                int len = e.y;
+                int32_t v = e.x;
+                if (len == 0) {
+                    int L = DEC_LUTB + 1;
+                    while (L <= TOD_HUFF_MAXLEN && static_cast<unsigned long long>(peek) >= s_lim[L]) ++L;
+                    if (L > TOD_HUFF_MAXLEN) { ok = false; len = 1; v = 0; }
+                    else {
+                        const int ci = s_base[L] + static_cast<int>(peek >> (32 - L));
+                        if (ci < 0 || ci >= nc) { ok = false; v = 0; }
+                        else v = __ldg(canon_vals + c0 + ci);
+                        len = L;
+                    }
+                }
+                x += v;
+                buf <<= len;
+                have -= len;
+                pos += len;
+                if (pos > end) ok = false;       // never read past the stream (+pad)
+                if (ok && have < 32) {
+                    buf |= static_cast<unsigned long long>(words[wptr]) << (32 - have);
+                    ++wptr;
+                    have += 32;
+                }
+                s_tile[tid][i] = static_cast<OutT>(x);
+            }
+        }
+        __syncthreads();
+        // coalesced write-out: consecutive threads take consecutive values of a block
+        for (int e = tid; e < DEC_T * DEC_ROUND; e += DEC_T) {
+            const int bl = e / DEC_ROUND, i = e % DEC_ROUND;
+            const int idx = round * DEC_ROUND + i;
+            if (idx < s_cnt[bl]) out[s_out0[bl] + idx] = s_tile[bl][i];
+        }
+        __syncthreads();
+    }
+    if (active && (!ok || pos > end)) set_status(status, q, TOD_ERR_CORRUPT_STREAM);
+}
+
+cudaError_t launch_decode(const Plan &p, const HuffDev &h, int32_t *pix_out, uint16_t *psi_out,
+                          cudaStream_t st)
+{
+    if (h.ncta == 0) return cudaSuccess;
+    const size_t smem = 0;
+    if (pix_out) {
+        k_decode<int32_t><<<h.ncta, DEC_T, smem, st>>>(
+            h.words, h.word_off, h.nbits, h.blk_off, h.ckpt_bit, h.ckpt_val, h.blk_q, h.lut, h.lim,
+            h.base, h.canon_off, h.canon_vals, h.cta_scan, h.cta_blk0, h.cta_nblk, p.off, pix_out,
+            p.status);
+    } else {
+        k_decode<uint16_t><<<h.ncta, DEC_T, smem, st>>>(
+            h.words, h.word_off, h.nbits, h.blk_off, h.ckpt_bit, h.ckpt_val, h.blk_q, h.lut, h.lim,
+            h.base, h.canon_off, h.canon_vals, h.cta_scan, h.cta_blk0, h.cta_nblk, p.off, psi_out,
+            p.status);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// A2 projection: one 16-byte map gather per sample, psi angle from the FP32
+// table (L1-resident), gain per detscan.  Tiles of ELEM_TILE samples never
+// cross a detscan.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_project(const float4 *__restrict__ map, const int32_t *__restrict__ pix,
+          const uint16_t *__restrict__ psi, const double *__restrict__ gain,
+          const float2 *__restrict__ trig, const int32_t *__restrict__ tile_q,
+          const int64_t *__restrict__ tile_t0, const int64_t *__restrict__ off,
+          int32_t npix, float *__restrict__ s_out, int32_t *status)
+{
+    const int q = tile_q[blockIdx.x];
+    const int64_t t0 = tile_t0[blockIdx.x];
+    const int64_t t1 = (t0 + ELEM_TILE < off[q + 1]) ? t0 + ELEM_TILE : off[q + 1];
+    const float g = gain ? static_cast<float>(gain[q]) : 1.0f;
+    for (int64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+        const int32_t pp = pix[t];
+        const uint32_t b = psi[t];
+        if (static_cast<uint32_t>(pp) >= static_cast<uint32_t>(npix) || b >= TOD_N_PSI) {
+            set_status(status, q, TOD_ERR_ARG);      // out-of-range pointing: no gather
+            s_out[t] = 0.0f;
+            continue;
+        }
+        const float4 m = __ldg(map + pp);
+        const float2 cs = __ldg(trig + b);
+        s_out[t] = g * fmaf(m.z, cs.y, fmaf(m.y, cs.x, m.x));
+    }
+}
+
+cudaError_t launch_project(const Plan &p, const float4 *map, const int32_t *pix, const uint16_t *psi,
+                           const double *gain, float *s_out, cudaStream_t st)
+{
+    if (p.ntile == 0) return cudaSuccess;
+    k_project<<<p.ntile, 256, 0, st>>>(map, pix, psi, gain, p.trig, p.tile_q, p.tile_t0, p.off, p.npix,
+                                       s_out, p.status);
+    return cudaGetLastError();
+}
+
+}  // namespace tg

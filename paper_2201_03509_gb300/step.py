@@ -1,0 +1,60 @@
+"""One Gibbs TOD step on the GPU (paper Listing `code:gibbs`, step 1):
+decode -> project -> sample gain -> sample n_corr -> bin -> solve, as a
+sequence of the C-ABI calls on one stream.  Holds the device buffers."""
+from __future__ import annotations
+
+import numpy as np
+
+from . import MODE_DRAW, Plan, Rng
+
+
+class GibbsTODStep:
+    def __init__(self, plan: Plan, psd: np.ndarray, flag_words: np.ndarray, rcond_min: float = 1e-6,
+                 cg_tol: float = 1e-6, cg_maxiter: int = 500):
+        import torch
+        dev = torch.device("cuda", plan.device)
+        N, nq, npix = plan.N, plan.nq, plan.npix
+        self.plan = plan
+        self.rcond_min, self.cg_tol, self.cg_maxiter = rcond_min, cg_tol, cg_maxiter
+        f32, f64, i32 = torch.float32, torch.float64, torch.int32
+        self.psd = torch.from_numpy(np.ascontiguousarray(psd, np.float64)).to(dev)
+        self.flags = torch.from_numpy(np.ascontiguousarray(flag_words, np.uint32).view(np.int32)).to(dev)
+        self.d = torch.empty(N, dtype=f32, device=dev)
+        self.pix = torch.empty(N, dtype=i32, device=dev)
+        self.psi = torch.empty(N, dtype=torch.int16, device=dev)
+        self.s = torch.empty(N, dtype=f32, device=dev)
+        self.ncorr = torch.empty(N, dtype=f32, device=dev)
+        self.gain = torch.zeros(nq, dtype=f64, device=dev)
+        self.mu = torch.zeros(nq, dtype=f64, device=dev)
+        self.sigma = torch.zeros(nq, dtype=f64, device=dev)
+        self.cg_iters = torch.zeros(nq, dtype=i32, device=dev)
+        self.A = torch.zeros((npix, 6), dtype=f64, device=dev)
+        self.b = torch.zeros((npix, 3), dtype=f64, device=dev)
+        self.hits = torch.zeros(npix, dtype=i32, device=dev)
+        self.map = torch.zeros((3, npix), dtype=f64, device=dev)
+        self.map32 = torch.zeros((npix, 4), dtype=f32, device=dev)
+        self.rcond = torch.zeros(npix, dtype=f64, device=dev)
+        self.valid = torch.zeros(npix, dtype=torch.uint8, device=dev)
+
+    def set_tod(self, d, stream=None):
+        """Copy this band's detector data (host numpy float32 or a tensor)."""
+        import torch
+        if isinstance(d, np.ndarray):
+            d = torch.from_numpy(np.ascontiguousarray(d, np.float32))
+        self.d.copy_(d, non_blocking=True)
+
+    def run(self, map32_in, rng: Rng, mode: int = MODE_DRAW, stream=None):
+        """Enqueue one step; the new map lands in self.map / self.map32."""
+        p = self.plan
+        p.decode(self.pix, self.psi, stream)
+        p.project(map32_in, self.pix, self.psi, None, self.s, stream)
+        p.sample_gain(self.d, self.s, self.flags, self.psd, rng, mode, self.gain, self.mu, self.sigma,
+                      stream)
+        p.sample_ncorr(self.d, self.s, self.gain, self.flags, self.psd, rng, mode, self.ncorr,
+                       self.cg_iters, self.cg_tol, self.cg_maxiter, stream)
+        p.bin(self.psi, self.d, self.ncorr, self.gain, self.flags, self.psd, self.A, self.b, self.hits,
+              stream)
+        p.solve_maps(self.A, self.b, self.hits, self.rcond_min, self.map, self.map32, self.rcond,
+                     self.valid, stream)
+
+    LAUNCHES_PER_STEP = 8   # decode x2, project, gain, ncorr, bin + reduce, solve

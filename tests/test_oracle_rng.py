@@ -42,8 +42,8 @@ def test_stream_normals_layout():
     z = oracle.stream_normals(5, 1, 12, oracle.PURPOSE_NC_W1, 3, 20)
     w = _numpy_block((2, 12, oracle.PURPOSE_NC_W1, 3), (5, 1))
     h = [int(w[1]) & 0xFFFFFFFF, int(w[1]) >> 32]          # pair 1 of block 2 = normals 18, 19
-    u1 = ((h[0] >> 8) + 0.5) / 2 ** 24
-    u2 = ((h[1] >> 8) + 0.5) / 2 ** 24
+    u1 = ((h[0] >> 9) + 0.5) / 2 ** 23
+    u2 = ((h[1] >> 9) + 0.5) / 2 ** 23
     r = math.sqrt(-2 * math.log(u1))
     assert z[18] == pytest.approx(r * math.cos(2 * math.pi * u2), rel=1e-15)
     assert z[19] == pytest.approx(r * math.sin(2 * math.pi * u2), rel=1e-15)
@@ -61,3 +61,14 @@ def test_stream_normals_are_standard_normal():
 def test_gain_normals_are_standard_normal():
     z = np.array([oracle.gain_normal(3, 0, q, 0) for q in range(5000)])
     assert stats.kstest(z, "norm").pvalue > 1e-3
+
+
+def test_omega_conventions_are_permutations():
+    n = 96
+    z1 = oracle.stream_normals(4, 2, 7, oracle.PURPOSE_NC_W1, 1, n)
+    z2 = oracle.stream_normals(4, 2, 7, oracle.PURPOSE_NC_W2, 1, n)
+    w1 = oracle.omega1(4, 2, 7, 1, n)
+    w2 = oracle.omega2(4, 2, 7, 1, n)
+    assert np.array_equal(np.sort(w1), np.sort(z1)) and np.array_equal(np.sort(w2), np.sort(z2))
+    assert w1[0] == z1[0] and w1[1] == z1[n - 1] and w1[2] == z1[1] and w1[3] == z1[n - 2]
+    assert w2[0] == z2[0] and w2[n // 2] == z2[1] and w2[5] == z2[10] and w2[n - 5] == z2[11]
