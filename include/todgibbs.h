@@ -146,6 +146,11 @@ typedef struct {
     uint64_t seed;
     uint64_t band;
     uint64_t gibbs_iter;
+    /* Optional DEVICE pointer: when non-NULL the kernels read the Gibbs
+     * iteration from this word when they run (gibbs_iter is ignored), so a
+     * captured CUDA graph replays with a new iteration after the caller
+     * updates the word. */
+    const uint64_t *gibbs_iter_dev;
 } tod_rng;
 
 tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band);
@@ -157,6 +162,15 @@ tod_status tod_plan_info(const tod_plan *p, int64_t *nsamples, int32_t *ndetscan
  * (TOD_OK or an error code) into HOST int32[ndetscan] (may be NULL), clears
  * them, and returns the first error found (TOD_OK if none). */
 tod_status tod_plan_status(tod_plan *p, int32_t *detscan_status);
+
+/* Launch schedule of the transform stages (gain, n_corr):
+ * TOD_SCHED_PERSISTENT (default): one persistent cluster launch per stage
+ * over the work list sorted by decreasing length;
+ * TOD_SCHED_PER_SCAN: one launch of one cluster per detscan (the plain
+ * per-scan path, kept for comparison).  Results are identical. */
+#define TOD_SCHED_PERSISTENT 0
+#define TOD_SCHED_PER_SCAN   1
+tod_status tod_plan_set_schedule(tod_plan *p, int32_t schedule);
 
 /* A1 -- Huffman decode + undo differencing (Sect. 4.1).
  * pix_out int32[N], psi_out uint16[N] (device).  Bit-exact; a stream that

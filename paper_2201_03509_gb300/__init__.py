@@ -58,14 +58,14 @@ class _BandDesc(ctypes.Structure):
 class Rng(ctypes.Structure):
     """Counter-based random streams: key (seed, band), counter carries the
     Gibbs iteration."""
-    _fields_ = [("seed", _u64), ("band", _u64), ("gibbs_iter", _u64)]
+    _fields_ = [("seed", _u64), ("band", _u64), ("gibbs_iter", _u64), ("gibbs_iter_dev", _P)]
 
 
 _lib = None
 
 SYMBOLS = ["tod_status_string", "tod_fft_length", "tod_huff_encode", "tod_huff_free",
            "tod_plan_create", "tod_plan_destroy", "tod_plan_info", "tod_plan_status",
-           "tod_decode", "tod_project", "tod_sample_gain", "tod_sample_ncorr", "tod_bin",
+           "tod_plan_set_schedule", "tod_decode", "tod_project", "tod_sample_gain", "tod_sample_ncorr", "tod_bin",
            "tod_solve_maps"]
 
 
@@ -94,6 +94,7 @@ def lib():
         L.tod_plan_destroy.argtypes = [_P]
         L.tod_plan_info.argtypes = [_P, _P, _P, _P, _P, _P]
         L.tod_plan_status.argtypes = [_P, _P]
+        L.tod_plan_set_schedule.argtypes = [_P, _i32]
         L.tod_decode.argtypes = [_P, _P, _P, _P]
         L.tod_project.argtypes = [_P, _P, _P, _P, _P, _P, _P]
         L.tod_sample_gain.argtypes = [_P, _P, _P, _P, _P, Rng, _i32, _P, _P, _P, _P]
@@ -246,6 +247,12 @@ class Plan:
                                    ctypes.byref(cs), ctypes.byref(nb)), "tod_plan_info")
         return dict(nsamples=ns.value, ndetscan=nq.value, npix=npix.value, cluster_size=cs.value,
                     device_bytes=nb.value)
+
+    SCHED_PERSISTENT = 0
+    SCHED_PER_SCAN = 1
+
+    def set_schedule(self, schedule: int):
+        _check(lib().tod_plan_set_schedule(self._h, int(schedule)), "tod_plan_set_schedule")
 
     def status(self, raise_on_error: bool = True) -> np.ndarray:
         st = np.zeros(self.nq, dtype=np.int32)

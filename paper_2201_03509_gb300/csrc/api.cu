@@ -695,6 +695,7 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
         if ((e = dev_upload(*p, p->pair_slot, pslot.data(), pslot.size()))) return fail(e);
         if ((e = dev_upload(*p, p->pix_slot_off, pslot_off.data(), pslot_off.size()))) return fail(e);
         if ((e = dev_upload(*p, p->rec, static_cast<double *>(nullptr), static_cast<size_t>(p->npairs) * 10))) return fail(e);
+        if ((e = setup_bin_kernel(*p))) return fail(e);
     }
     if ((e = cudaDeviceSynchronize())) return fail(e);
     *out = reinterpret_cast<tod_plan *>(p);
@@ -736,6 +737,13 @@ tod_status tod_plan_status(tod_plan *pl, int32_t *detscan_status)
     if (detscan_status) std::memcpy(detscan_status, st.data(), sizeof(int32_t) * p->nq);
     for (int32_t s : st)
         if (s != TOD_OK) return s;
+    return TOD_OK;
+}
+
+tod_status tod_plan_set_schedule(tod_plan *pl, int32_t schedule)
+{
+    if (!pl || (schedule != TOD_SCHED_PERSISTENT && schedule != TOD_SCHED_PER_SCAN)) return TOD_ERR_ARG;
+    reinterpret_cast<Plan *>(pl)->schedule = schedule;
     return TOD_OK;
 }
 

@@ -71,6 +71,9 @@ struct Plan {
     float2 *tw = nullptr;            // twiddle tables
     int32_t *work = nullptr;         // [nq] detscans sorted by decreasing length
     int32_t nclusters_gain = 1, nclusters_ncorr = 1;
+    int32_t schedule = TOD_SCHED_PERSISTENT;
+    int32_t bin_C = 1, bin_cap = 0, bin_nclusters = 1;
+    size_t smem_bin = 0;
     size_t smem_gain = 0, smem_ncorr = 0;
     // binning
     uint32_t *lp = nullptr;          // [N] per-detscan pixel-sorted local order
@@ -98,6 +101,7 @@ cudaError_t launch_ncorr(const Plan &p, const float *d, const float *s, const do
                          const uint32_t *flags, const double *psd, tod_rng rng, int mode,
                          float tol, int maxit, float *x, int32_t *iters, cudaStream_t st,
                          int work_begin, int work_count);
+cudaError_t setup_bin_kernel(Plan &p);
 cudaError_t launch_bin(const Plan &p, const uint16_t *psi, const float *d, const float *ncorr,
                        const double *gain, const uint32_t *flags, const double *psd, double *A,
                        double *b, int32_t *hits, cudaStream_t st);

@@ -184,58 +184,60 @@ k_solve(const double *__restrict__ A, const double *__restrict__ b, const int32_
 }
 
 // ---------------------------------------------------------------------------
-static int bin_cluster(const Plan &p) { return p.C < 8 ? p.C : 8; }
+// Cluster size and staging capacity are fixed at plan creation (the longest
+// detscan over the cluster, <= 200 KB per CTA), so tod_bin only launches.
+cudaError_t setup_bin_kernel(Plan &p)
+{
+    int64_t nmax = 0;
+    for (int q = 0; q < p.nq; ++q) nmax = std::max<int64_t>(nmax, p.h_off[q + 1] - p.h_off[q]);
+    int C = 1;
+    while (C < 16 && (nmax + C - 1) / C * 10 > 200 * 1024) C *= 2;
+    p.bin_C = C;
+    p.bin_cap = static_cast<int>((nmax + C - 1) / C);
+    p.smem_bin = static_cast<size_t>(p.bin_cap) * 10 + 16;
+    cudaError_t e = cudaFuncSetAttribute(k_bin, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(p.smem_bin));
+    if (e != cudaSuccess) return e;
+    if (C > 8) {
+        e = cudaFuncSetAttribute(k_bin, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(C * 64));
+    cfg.blockDim = dim3(BIN_T);
+    cfg.dynamicSmemBytes = p.smem_bin;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr; cfg.numAttrs = 1;
+    int ncl = 0;
+    e = cudaOccupancyMaxActiveClusters(&ncl, k_bin, &cfg);
+    if (e != cudaSuccess) return e;
+    p.bin_nclusters = std::max(1, std::min(ncl, p.nq));
+    return cudaSuccess;
+}
 
 cudaError_t launch_bin(const Plan &p, const uint16_t *psi, const float *d, const float *ncorr,
                        const double *gain, const uint32_t *flags, const double *psd, double *A,
                        double *b, int32_t *hits, cudaStream_t st)
 {
     if (p.nq == 0) return cudaSuccess;
-    // staging capacity: the longest detscan over the cluster
-    int64_t nmax = 0;
-    for (int q = 0; q < p.nq; ++q) nmax = std::max<int64_t>(nmax, p.h_off[q + 1] - p.h_off[q]);
-    int C = 1;
-    while (C < 16 && (nmax + C - 1) / C * 10 > 200 * 1024) C *= 2;
-    const int cap = static_cast<int>((nmax + C - 1) / C);
-    const size_t smem = static_cast<size_t>(cap) * 10 + 16;
-    cudaError_t e = cudaFuncSetAttribute(k_bin, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    if (C > 8) {
-        e = cudaFuncSetAttribute(k_bin, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-    }
     BinArgs a;
     a.psi = psi; a.d = d; a.x = ncorr; a.gain = gain; a.flags = flags; a.psd = psd; a.off = p.off;
     a.lp = p.lp; a.pair_off = p.pair_off; a.pair_start = p.pair_start; a.pair_len = p.pair_len;
     a.pair_slot = p.pair_slot; a.trig = p.trig; a.work = p.work; a.nq = p.nq; a.ndet = p.ndet;
-    a.chunk_cap = cap; a.rec = p.rec; a.status = p.status;
-    // clusters: enough to fill the GPU
-    int ncl = 0;
-    {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(static_cast<unsigned>(C * 64));
-        cfg.blockDim = dim3(BIN_T);
-        cfg.dynamicSmemBytes = smem;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = C; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr; cfg.numAttrs = 1;
-        e = cudaOccupancyMaxActiveClusters(&ncl, k_bin, &cfg);
-        if (e != cudaSuccess) return e;
-        if (ncl < 1) ncl = 1;
-    }
-    ncl = std::min(ncl, p.nq);
+    a.chunk_cap = p.bin_cap; a.rec = p.rec; a.status = p.status;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(static_cast<unsigned>(ncl * C));
+    cfg.gridDim = dim3(static_cast<unsigned>(p.bin_nclusters * p.bin_C));
     cfg.blockDim = dim3(BIN_T);
-    cfg.dynamicSmemBytes = smem;
+    cfg.dynamicSmemBytes = p.smem_bin;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = C; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
+    attr[0].val.clusterDim.x = p.bin_C; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr; cfg.numAttrs = 1;
     void *argv[1] = {&a};
-    e = cudaLaunchKernelExC(&cfg, reinterpret_cast<const void *>(k_bin), argv);
+    cudaError_t e = cudaLaunchKernelExC(&cfg, reinterpret_cast<const void *>(k_bin), argv);
     if (e != cudaSuccess) return e;
     const int nb = (p.npix + 255) / 256;
     k_reduce<<<nb, 256, 0, st>>>(p.rec, p.pix_slot_off, p.npix, A, b, hits);

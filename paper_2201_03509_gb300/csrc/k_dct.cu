@@ -505,7 +505,8 @@ __global__ void __launch_bounds__(DCT_T, 1) k_gain(GainArgs a)
                 const double mu = B / A, sg = 1.0 / sqrt(A);
                 double z = 0.0;
                 if (a.mode == TOD_MODE_DRAW) {
-                    const u64x4 wv = philox4x64(0, static_cast<uint64_t>(q), 0, a.rng.gibbs_iter,
+                    const uint64_t it = a.rng.gibbs_iter_dev ? *a.rng.gibbs_iter_dev : a.rng.gibbs_iter;
+                    const u64x4 wv = philox4x64(0, static_cast<uint64_t>(q), 0, it,
                                                 a.rng.seed, a.rng.band);
                     const double u1 = (static_cast<double>(wv.x[0] >> 11) + 0.5) * 1.1102230246251565e-16;
                     const double u2 = (static_cast<double>(wv.x[1] >> 11) + 0.5) * 1.1102230246251565e-16;
@@ -522,8 +523,9 @@ __global__ void __launch_bounds__(DCT_T, 1) k_gain(GainArgs a)
 // ---------------------------------------------------------------------------
 // A5: correlated noise.  x0 = B^{-1} b (B = C^T diag(phi + 1/sigma0^2) C) in
 // U1; flagged detscans then solve the Schur complement
-//   S y = E^T x0,  S = sigma0^2 I - E^T B^{-1} E   (E: flagged samples)
-// by CG and add B^{-1} E y (Woodbury): x = A^{-1} b exactly.
+//   S y = E^T x0,  S = sigma0^2 I - E^T B^{-1} E = E^T C^T diag(gamma) C E
+// (E: flagged samples; C^T C = I) by CG and add B^{-1} E y (Woodbury):
+// x = A^{-1} b exactly, A = B - E E^T / sigma0^2.
 // ---------------------------------------------------------------------------
 struct NcorrArgs {
     const float *d, *s;
@@ -548,8 +550,14 @@ struct NcorrArgs {
     int sz, m1max, m2max;
 };
 
-// Multiply the packed spectrum in U by beta_kappa = 1/(phi_kappa + 1/sigma0^2).
-__device__ __noinline__ void apply_beta(const Ctx &X, float2 *U, float fscale, float alpha, float s2, float inv_s2)
+// Multiply the packed spectrum in U by a per-mode weight:
+//   beta_kappa  = 1/(phi_kappa + 1/sigma0^2) = s2/(1 + r)          (hp = false)
+//   gamma_kappa = sigma0^2 - beta_kappa     = s2 r/(1 + r)         (hp = true)
+// with r = sigma0^2 phi = (f/f_knee)^-alpha (r = 0 at kappa = 0).  gamma is
+// evaluated directly, so the Schur operator sigma0^2 I - E^T B^{-1} E =
+// E^T C^T diag(gamma) C E carries no FP32 cancellation on its small modes.
+__device__ __noinline__ void apply_filter(const Ctx &X, float2 *U, float fscale, float alpha, float s2,
+                                          bool hp)
 {
     const int total = 2 * X.npl * X.m2;
     for (int e = threadIdx.x; e < total; e += DCT_T) {
@@ -558,12 +566,13 @@ __device__ __noinline__ void apply_beta(const Ctx &X, float2 *U, float fscale, f
         if (k1 < 0) continue;
         const int k = k1 + X.m1 * k2;
         const int ka = k, kb = (k == 0) ? X.m : X.n - k;
-        // beta = 1/(phi + 1/s2) = s2 / (1 + s2 phi), s2 phi = (f/fk)^{-alpha}
-        const float ba = (ka == 0) ? s2 : s2 / (1.0f + fratio_pow(ka, fscale, -alpha));
-        const float bb = s2 / (1.0f + fratio_pow(kb, fscale, -alpha));
+        const float ra = (ka == 0) ? 0.f : fratio_pow(ka, fscale, -alpha);
+        const float rb = fratio_pow(kb, fscale, -alpha);
+        const float wa = hp ? s2 * ra / (1.0f + ra) : s2 / (1.0f + ra);
+        const float wb = hp ? s2 * rb / (1.0f + rb) : s2 / (1.0f + rb);
         float2 v = U[e];
-        v.x *= ba;
-        v.y *= bb;
+        v.x *= wa;
+        v.y *= wb;
         U[e] = v;
     }
     __syncthreads();
@@ -581,7 +590,10 @@ __device__ __forceinline__ void elem_samples(const Ctx &X, int e, int &t0, int &
 // sample t -> (owner CTA, element, part)
 __device__ __forceinline__ void sample_loc(const Ctx &X, int t, int &owner, int &loc)
 {
-    const int i = (t & 1) ? X.n - 1 - ((t - 1) >> 1) : (t >> 1);
+    // position of sample t in the even-then-reversed-odd order: t/2 for even
+    // t, n-1-(t-1)/2 = n-1-floor(t/2) for odd t
+    const int h = t >> 1;
+    const int i = (t & 1) ? (X.n - 1) - h : h;
     const int j = i >> 1;
     const int j1 = j / X.m2, j2 = j - j1 * X.m2;
     owner = j2 / X.ncolmax;
@@ -625,11 +637,12 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
         const float *dq = a.d + o, *sq = a.s + o;
         const uint32_t *fl = a.flags;
         const tod_rng rng = a.rng;
+        const uint64_t gi = rng.gibbs_iter_dev ? *rng.gibbs_iter_dev : rng.gibbs_iter;
         // right-hand side, time-domain part: M (r/s2 + w1/s)
         load_time(X, sm.U1, [&](int j) {
             const int t0 = vpos_t(2 * j, n, m), t1 = vpos_t(2 * j + 1, n, m);
             float2 w1 = make_float2(0.f, 0.f);
-            if (draw) w1 = stream_normal_pair(rng.seed, rng.band, q, 1, rng.gibbs_iter, 2 * j);
+            if (draw) w1 = stream_normal_pair(rng.seed, rng.band, q, 1, gi, 2 * j);
             const float r0 = flagged(fl, o + t0) ? 0.f
                                                   : fmaf(dq[t0] - g * sq[t0], inv_s2, w1.x * inv_s);
             const float r1 = flagged(fl, o + t1) ? 0.f
@@ -650,7 +663,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                 const float pb = fratio_pow(kb, fscale, -alpha) * inv_s2;
                 float2 v = sm.U1[e];
                 if (draw) {
-                    const float2 w2 = stream_normal_pair(rng.seed, rng.band, q, 2, rng.gibbs_iter, 2 * k);
+                    const float2 w2 = stream_normal_pair(rng.seed, rng.band, q, 2, gi, 2 * k);
                     v.x += sqrtf(pa) * w2.x;
                     v.y += sqrtf(pb) * w2.y;
                 }
@@ -672,7 +685,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             if (wi >= nw) break;
             uint32_t bits = fl[wb0 + wi];
             while (bits) {
-                const int b = __ffs(bits) - 1;
+                const int b = __popc((bits & (0u - bits)) - 1u);   // index of the lowest set bit
                 bits &= bits - 1;
                 const int64_t tl = ((wb0 + wi) << 5) + b - o;
                 if (tl < 0 || tl >= n) continue;
@@ -697,7 +710,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             if (wi >= nw) break;
             uint32_t bits = fl[wb0 + wi];
             while (bits) {
-                const int b = __ffs(bits) - 1;
+                const int b = __popc((bits & (0u - bits)) - 1u);   // index of the lowest set bit
                 bits &= bits - 1;
                 const int64_t tl = ((wb0 + wi) << 5) + b - o;
                 if (tl < 0 || tl >= n) continue;
@@ -738,11 +751,11 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                 for (int i = threadIdx.x; i < kc; i += DCT_T) U0f[c_loc[i]] = c_p[i];
                 __syncthreads();
                 dct_forward_inplace(X, sm.U0, sm.tw1, sm.tw2, cl);
-                apply_beta(X, sm.U0, fscale, alpha, s2, inv_s2);
+                apply_filter(X, sm.U0, fscale, alpha, s2, true);
                 dct_inverse_inplace(X, sm.U0, sm.tw1, sm.tw2, cl);
                 double pq_loc = 0.0;
                 for (int i = threadIdx.x; i < kc; i += DCT_T) {
-                    const float v = fmaf(s2, c_p[i], -U0f[c_loc[i]]);
+                    const float v = U0f[c_loc[i]];
                     c_q[i] = v;
                     pq_loc += static_cast<double>(c_p[i]) * v;
                 }
@@ -770,7 +783,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             for (int i = threadIdx.x; i < kc; i += DCT_T) U0f[c_loc[i]] = c_y[i];
             __syncthreads();
             dct_forward_inplace(X, sm.U0, sm.tw1, sm.tw2, cl);
-            apply_beta(X, sm.U0, fscale, alpha, s2, inv_s2);
+            apply_filter(X, sm.U0, fscale, alpha, s2, false);
             dct_inverse_inplace(X, sm.U0, sm.tw1, sm.tw2, cl);
             for (int e = threadIdx.x; e < tot; e += DCT_T)
                 sm.U1[e] = cadd(sm.U1[e], sm.U0[e]);
@@ -879,6 +892,15 @@ cudaError_t launch_gain(const Plan &p, const float *d, const float *s, const uin
     a.work_count = work_count; a.ndet = p.ndet; a.fsamp = p.fsamp; a.rng = rng; a.mode = mode;
     a.g_out = g; a.mu_out = mu; a.sig_out = sig; a.status = p.status; a.sz = p.sz;
     a.m1max = p.m1max; a.m2max = p.m2max;
+    if (p.schedule == TOD_SCHED_PER_SCAN) {
+        for (int w = 0; w < work_count; ++w) {
+            a.work_begin = work_begin + w;
+            a.work_count = 1;
+            cudaError_t e = launch_cluster(reinterpret_cast<const void *>(k_gain), &a, p.C, 1, p.smem_gain, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     const int ncl = std::min(work_count, p.nclusters_gain);
     return launch_cluster(reinterpret_cast<const void *>(k_gain), &a, p.C, ncl, p.smem_gain, st);
 }
@@ -895,6 +917,15 @@ cudaError_t launch_ncorr(const Plan &p, const float *d, const float *s, const do
     a.work_count = work_count; a.ndet = p.ndet; a.fsamp = p.fsamp; a.rng = rng; a.mode = mode;
     a.tol = tol; a.maxit = maxit; a.x_out = x; a.iters = iters; a.status = p.status; a.sz = p.sz;
     a.m1max = p.m1max; a.m2max = p.m2max;
+    if (p.schedule == TOD_SCHED_PER_SCAN) {
+        for (int w = 0; w < work_count; ++w) {
+            a.work_begin = work_begin + w;
+            a.work_count = 1;
+            cudaError_t e = launch_cluster(reinterpret_cast<const void *>(k_ncorr), &a, p.C, 1, p.smem_ncorr, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     const int ncl = std::min(work_count, p.nclusters_ncorr);
     return launch_cluster(reinterpret_cast<const void *>(k_ncorr), &a, p.C, ncl, p.smem_ncorr, st);
 }
