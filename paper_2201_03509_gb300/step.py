@@ -58,3 +58,25 @@ class GibbsTODStep:
                      self.valid, stream)
 
     LAUNCHES_PER_STEP = 8   # decode x2, project, gain, ncorr, bin + reduce, solve
+
+    def capture(self, map32_in, seed: int, band: int = 0, mode: int = MODE_DRAW):
+        """Capture one step into a CUDA graph.  The Gibbs iteration is read by
+        the kernels from a device word, so replay(it) draws fresh numbers."""
+        import torch
+        self.iter_dev = torch.zeros(1, dtype=torch.int64, device=self.d.device)
+        self._rng_graph = Rng(seed, band, 0, self.iter_dev.data_ptr())
+        self._map_graph = map32_in
+        side = torch.cuda.Stream(device=self.d.device)
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.run(map32_in, self._rng_graph, mode)          # untimed first run off the capture
+        torch.cuda.current_stream().wait_stream(side)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.run(map32_in, self._rng_graph, mode)
+        return self.graph
+
+    def replay(self, it: int):
+        """Run the captured step at Gibbs iteration ``it`` (current stream)."""
+        self.iter_dev.fill_(int(it))
+        self.graph.replay()
