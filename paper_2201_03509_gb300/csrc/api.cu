@@ -215,6 +215,7 @@ int64_t fft_length_impl(int64_t n)
 std::vector<int8_t> radix_plan(int L)
 {
     std::vector<int8_t> r;
+    while (L % 8 == 0) { r.push_back(8); L /= 8; }
     while (L % 4 == 0) { r.push_back(4); L /= 4; }
     while (L % 2 == 0) { r.push_back(2); L /= 2; }
     while (L % 3 == 0) { r.push_back(3); L /= 3; }
@@ -223,7 +224,17 @@ std::vector<int8_t> radix_plan(int L)
     return r;
 }
 
-bool has5(const std::vector<int8_t> &r) { return std::find(r.begin(), r.end(), 5) != r.end(); }
+void fill_stages(DctStage *st, const std::vector<int8_t> &r, int L)
+{
+    int Ns = 1;
+    for (size_t i = 0; i < r.size(); ++i) {
+        st[i].R = r[i];
+        st[i].Ns = Ns;
+        st[i].fLR = make_fastdiv(static_cast<uint32_t>(L / r[i]));
+        st[i].fNs = make_fastdiv(static_cast<uint32_t>(Ns));
+        Ns *= r[i];
+    }
+}
 
 // Choose m1 x m2 for one length with C CTAs; returns false if none fits.
 bool choose_factor(int n, int C, DctPlan &out, int &sz)
@@ -240,14 +251,19 @@ bool choose_factor(int n, int C, DctPlan &out, int &sz)
         const int P = m1 / 2 + 1;
         const int npmax = (P + C - 1) / C;
         const int asz = m1 * ncolmax, bsz = 2 * npmax * m2;
-        const int acap = has5(r1) ? 20 * DCT_T : DCT_EMAX * DCT_T;
-        const int bcap = has5(r2) ? 20 * DCT_T : DCT_EMAX * DCT_T;
-        if (asz > acap || bsz > bcap) continue;
+        if (asz > DCT_SZ_MAX || bsz > DCT_SZ_MAX) continue;               // shared-memory budget
+        // smallest per-CTA buffer; within 5 % of it, the most balanced split
         const int s = std::max(asz, bsz);
-        if (best < 0 || s < best || (s == best && std::abs(m1 - m2) < std::abs(bestm1 - m / bestm1))) {
+        const bool better = best < 0 || s * 20 < best * 19 ||
+                            (s * 20 <= best * 21 && std::max(m1, m2) < std::max(bestm1, m / bestm1));
+        if (better) {
             best = s;
             bestm1 = m1;
         }
+    }
+    if (best >= 0) {   // best holds the buffer size of the chosen split
+        const int m2b = m / bestm1;
+        best = std::max(bestm1 * ((m2b + C - 1) / C), 2 * (((bestm1 / 2 + 1) + C - 1) / C) * m2b);
     }
     if (best < 0) return false;
     const int m1 = bestm1, m2 = m / m1;
@@ -259,8 +275,11 @@ bool choose_factor(int n, int C, DctPlan &out, int &sz)
     out.npmax = (out.P + C - 1) / C;
     out.nr1 = static_cast<int32_t>(r1.size());
     out.nr2 = static_cast<int32_t>(r2.size());
-    for (size_t i = 0; i < r1.size(); ++i) out.r1[i] = r1[i];
-    for (size_t i = 0; i < r2.size(); ++i) out.r2[i] = r2[i];
+    fill_stages(out.s1, r1, m1);
+    fill_stages(out.s2, r2, m2);
+    out.f_ncolmax = make_fastdiv(static_cast<uint32_t>(out.ncolmax));
+    out.f_m2 = make_fastdiv(static_cast<uint32_t>(m2));
+    out.f_npmax = make_fastdiv(static_cast<uint32_t>(out.npmax));
     sz = best;
     return true;
 }
@@ -603,25 +622,33 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
                 m2max = std::max(m2max, dp.m2);
             }
             if (!ok) continue;
-            const size_t smem = sizeof(float2) * (2 * static_cast<size_t>(sz) + m1max + m2max) +
-                                static_cast<size_t>(CG_KCAP) * 20 + 4096;
+            const size_t smem = sizeof(float2) * (2 * static_cast<size_t>(sz)) +
+                                static_cast<size_t>(CG_KCAP) * 28 + sizeof(int) * GMAP_CAP +
+                                sizeof(float) * 4 * TOEP_LMAX + 12288;
             if (smem > 227 * 1024) continue;
             chosenC = C;
             p->sz = sz; p->m1max = m1max; p->m2max = m2max;
         }
         if (!chosenC) { free_plan(p); return TOD_ERR_ARG; }
         p->C = chosenC;
-        // twiddle tables per plan
+        // twiddle tables per plan: W_{m1}^i, W_{m2}^i, and the four-step
+        // factors W_m^{64 i} (i <= m/64) and W_m^i (i < 64), from FP64
         std::vector<float2> tw;
+        const auto push_w = [&](int L, int64_t i) {
+            const double ang = -2.0 * kPi * static_cast<double>(i) / L;
+            tw.push_back(make_float2(static_cast<float>(std::cos(ang)), static_cast<float>(std::sin(ang))));
+        };
         for (auto &dp : plans) {
-            for (int which = 0; which < 2; ++which) {
-                const int L = which ? dp.m2 : dp.m1;
-                (which ? dp.tw2 : dp.tw1) = static_cast<int32_t>(tw.size());
-                for (int i = 0; i < L; ++i) {
-                    const double ang = -2.0 * kPi * i / L;
-                    tw.push_back(make_float2(static_cast<float>(std::cos(ang)), static_cast<float>(std::sin(ang))));
-                }
-            }
+            dp.tw1 = static_cast<int32_t>(tw.size());
+            for (int i = 0; i < dp.m1; ++i) push_w(dp.m1, i);
+            dp.tw2 = static_cast<int32_t>(tw.size());
+            for (int i = 0; i < dp.m2; ++i) push_w(dp.m2, i);
+            dp.tw4 = static_cast<int32_t>(tw.size());
+            for (int i = 0; i <= dp.m / 64; ++i) push_w(dp.m, 64 * static_cast<int64_t>(i));
+            for (int i = 0; i < 64; ++i) push_w(dp.m, i);
+            dp.tws = static_cast<int32_t>(tw.size());
+            for (int i = 0; i <= (4 * dp.n) / 64; ++i) push_w(4 * dp.n, 64 * static_cast<int64_t>(i));
+            for (int i = 0; i < 64; ++i) push_w(4 * dp.n, i);
         }
         std::vector<int32_t> qp(p->nq);
         for (int q = 0; q < p->nq; ++q)
@@ -631,6 +658,22 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
         if ((e = dev_upload(*p, p->q_plan, qp.data(), qp.size()))) return fail(e);
         if ((e = dev_upload(*p, p->tw, tw.data(), tw.size()))) return fail(e);
         if ((e = setup_dct_kernels(*p))) return fail(e);
+        // Toeplitz preconditioner tables (per detector)
+        p->toep_nref = 0;
+        for (int q = 0; q < p->nq; ++q)
+            p->toep_nref = std::max<int32_t>(p->toep_nref, static_cast<int32_t>(p->h_off[q + 1] - p->h_off[q]));
+        if ((e = dev_upload(*p, p->htab, static_cast<float *>(nullptr), static_cast<size_t>(p->ndet) * TOEP_LMAX)))
+            return fail(e);
+        if ((e = dev_upload(*p, p->xtab, static_cast<float *>(nullptr),
+                            static_cast<size_t>(p->ndet) * (TOEP_LMAX * (TOEP_LMAX + 1) / 2))))
+            return fail(e);
+        if ((e = dev_upload(*p, p->lvalid, static_cast<int32_t *>(nullptr), static_cast<size_t>(p->ndet))))
+            return fail(e);
+        // filter-weight scratch: one slot per CTA of every resident cluster
+        p->wscratch_per_cluster = static_cast<int64_t>(p->C) * p->sz;
+        if ((e = dev_upload(*p, p->wscratch, static_cast<float4 *>(nullptr),
+                            static_cast<size_t>(std::max(1, p->nclusters_ncorr)) * p->wscratch_per_cluster)))
+            return fail(e);
     }
     // binning structure from the pointing (fixed during the run)
     {

@@ -8,6 +8,27 @@
 namespace tg {
 
 // ---------------------------------------------------------------------------
+// division by a runtime constant: q = (umulhi(x, mul) + x) >> shift, exact for
+// 0 <= x < 2^31 (round-up multiplier method, Granlund & Montgomery 1994)
+// ---------------------------------------------------------------------------
+struct FastDiv {
+    uint32_t d, mul, shift;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+    FastDiv f;
+    f.d = d;
+    uint32_t s = 0;
+    while ((1ull << s) < d) ++s;
+    f.shift = s;
+    f.mul = static_cast<uint32_t>((((1ull << 32) * ((1ull << s) - d)) / d) + 1);
+    return f;
+}
+__device__ __forceinline__ int fdiv(int x, const FastDiv &f) {
+    const uint32_t ux = static_cast<uint32_t>(x);
+    return static_cast<int>((__umulhi(ux, f.mul) + ux) >> f.shift);
+}
+
+// ---------------------------------------------------------------------------
 // per-detscan status words (device): first error wins, never a trap
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void set_status(int32_t *status, int q, int32_t code) {

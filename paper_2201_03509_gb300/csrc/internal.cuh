@@ -4,6 +4,7 @@
 #include <vector>
 #include <cuda_runtime.h>
 #include "../../include/todgibbs.h"
+#include "common.cuh"
 
 namespace tg {
 
@@ -12,9 +13,12 @@ constexpr int DEC_T = 256;            // decode threads per CTA (one checkpoint 
 constexpr int DEC_ROUND = 16;         // symbols staged per thread before a coalesced write
 constexpr int ELEM_TILE = 4096;       // samples per tile of the element-wise kernels
 constexpr int DCT_T = 512;            // threads per CTA of the cluster transform kernels
-constexpr int DCT_EMAX = 24;          // complex values per thread in one FFT stage
+constexpr int DCT_SZ_MAX = 11776;     // complex values per CTA buffer (two buffers + CG fit in 227 KB)
 constexpr int DCT_MAXR = 20;          // maximum number of radix stages per sub-transform
-constexpr int CG_KCAP = 1536;         // flagged samples per CTA held by the CG
+constexpr int CG_KCAP = 1024;         // flagged samples per CTA held by the CG
+constexpr int TOEP_LMAX = 512;        // longest gap block of the Toeplitz preconditioner
+constexpr int GAP_CAP = 256;          // gap blocks per detscan handled by the preconditioner
+constexpr int GMAP_CAP = 2048;        // gap-block elements mapped per CTA
 
 // Compressed stream kind, device copy + decode tables.
 struct HuffDev {
@@ -38,13 +42,22 @@ struct HuffDev {
     int64_t nblk = 0;
 };
 
+// One Stockham pass of a sub-transform: radix R after Ns points are done.
+struct DctStage {
+    int32_t R, Ns;
+    FastDiv fLR, fNs;                // divisions by L/R and Ns
+};
+
 // Per-length transform plan (real DCT-II of length n via an m = n/2 complex
 // FFT split as m1 x m2 across a cluster of C CTAs).
 struct DctPlan {
     int32_t n, m, m1, m2, ncolmax, npmax, P;
     int32_t nr1, nr2;
     int32_t tw1, tw2;                // offsets of the W_{m1}^i and W_{m2}^i tables
-    int8_t r1[DCT_MAXR], r2[DCT_MAXR];
+    int32_t tw4;                     // offset of W_m^{64 i} (m/64+1 entries) then W_m^i (64)
+    int32_t tws;                     // offset of W_{4n}^{64 i} (4n/64+1 entries) then W_{4n}^i (64)
+    FastDiv f_ncolmax, f_m2, f_npmax;
+    DctStage s1[DCT_MAXR], s2[DCT_MAXR];
 };
 
 struct Plan {
@@ -71,6 +84,13 @@ struct Plan {
     float2 *tw = nullptr;            // twiddle tables
     int32_t *work = nullptr;         // [nq] detscans sorted by decreasing length
     int32_t nclusters_gain = 1, nclusters_ncorr = 1;
+    float4 *wscratch = nullptr;      // per-cluster filter weights (beta, gamma) in packed layout
+    float *htab = nullptr;           // [ndet][TOEP_LMAX] gap-kernel h(d)
+    float *xtab = nullptr;           // [ndet][TOEP_LMAX (TOEP_LMAX+1)/2] T_L^{-1} e_1 per order
+    int32_t *lvalid = nullptr;       // [ndet]
+    int32_t toep_nref = 0;
+    bool use_prec = true;
+    int64_t wscratch_per_cluster = 0;
     int32_t schedule = TOD_SCHED_PERSISTENT;
     int32_t bin_C = 1, bin_cap = 0, bin_nclusters = 1;
     size_t smem_bin = 0;
@@ -102,6 +122,7 @@ cudaError_t launch_ncorr(const Plan &p, const float *d, const float *s, const do
                          float tol, int maxit, float *x, int32_t *iters, cudaStream_t st,
                          int work_begin, int work_count);
 cudaError_t setup_bin_kernel(Plan &p);
+cudaError_t launch_toeplitz_prep(const Plan &p, const double *psd, cudaStream_t st);
 cudaError_t launch_bin(const Plan &p, const uint16_t *psi, const float *d, const float *ncorr,
                        const double *gain, const uint32_t *flags, const double *psd, double *A,
                        double *b, int32_t *hits, cudaStream_t st);

@@ -57,6 +57,26 @@ template <bool INV> struct Dft<4, INV> {
         v[3] = csub(d0, d1);
     }
 };
+// 8 = 2 x 4: a_r = v_r + v_{r+4}, b_r = (v_r - v_{r+4}) W8^r; even outputs
+// are DFT4(a), odd outputs DFT4(b).
+template <bool INV> struct Dft<8, INV> {
+    static __device__ __forceinline__ void run(float2 *v) {
+        const float c = 0.70710678118654752f;
+        float2 a[4], b[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) { a[r] = cadd(v[r], v[r + 4]); b[r] = csub(v[r], v[r + 4]); }
+        // W8^1 = (c, -+c), W8^2 = -+i, W8^3 = (-c, -+c)
+        b[1] = INV ? make_float2(c * (b[1].x - b[1].y), c * (b[1].x + b[1].y))
+                   : make_float2(c * (b[1].x + b[1].y), c * (b[1].y - b[1].x));
+        b[2] = mul_i(b[2], INV);
+        b[3] = INV ? make_float2(-c * (b[3].x + b[3].y), c * (b[3].x - b[3].y))
+                   : make_float2(c * (b[3].y - b[3].x), -c * (b[3].x + b[3].y));
+        Dft<4, INV>::run(a);
+        Dft<4, INV>::run(b);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { v[2 * u] = a[u]; v[2 * u + 1] = b[u]; }
+    }
+};
 template <bool INV> struct Dft<3, INV> {
     static __device__ __forceinline__ void run(float2 *v) {
         const float S3 = INV ? 0.86602540378443865f : -0.86602540378443865f;   // sin(-+2pi/3)
@@ -90,68 +110,60 @@ template <bool INV> struct Dft<5, INV> {
 };
 
 // One Stockham radix-R pass (Govindaraju et al. 2008 formulation) over nvec
-// vectors of length L held in shared memory (element stride es, vector
-// stride vs).  All reads complete before the barrier, all writes follow it,
-// so the pass is in place.  vfast: consecutive threads take consecutive
-// vectors (column FFTs) instead of consecutive elements (row FFTs).
+// vectors of length L, out of place from src to dst in shared memory
+// (element stride es, vector stride vs).  Each thread loops over whole
+// butterflies; one barrier per pass.  vfast: consecutive threads take
+// consecutive vectors (column FFTs) instead of consecutive elements (row
+// FFTs).  Index arithmetic uses precomputed multiply-shift divisions.
 template <int R, bool INV>
-__device__ __noinline__ void fft_pass(float2 *__restrict__ buf, int L, int Ns, int nvec, int es,
-                                         int vs, bool vfast, const float2 *__restrict__ tw)
+__device__ __noinline__ void fft_pass(const float2 *__restrict__ src, float2 *__restrict__ dst, int L,
+                                      const DctStage st, int nvec, const FastDiv fnvec, int es, int vs,
+                                      bool vfast, const float2 *__restrict__ tw)
 {
-    constexpr int NB = DCT_EMAX / R;
     const int LR = L / R;
+    const int Ns = st.Ns;
     const int total = nvec * LR;
-    float2 v[NB][R];
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-        const int w = threadIdx.x + b * DCT_T;
-        if (w < total) {
-            int vec, j;
-            if (vfast) { j = w / nvec; vec = w - j * nvec; }
-            else { vec = w / LR; j = w - vec * LR; }
-            const float2 *p = buf + vec * vs + j * es;
-#pragma unroll
-            for (int r = 0; r < R; ++r) v[b][r] = p[r * LR * es];
-        }
-    }
-    __syncthreads();
     const int tstep = L / (Ns * R);
+    for (int w = threadIdx.x; w < total; w += DCT_T) {
+        int vec, j;
+        if (vfast) { j = fdiv(w, fnvec); vec = w - j * nvec; }
+        else { vec = fdiv(w, st.fLR); j = w - vec * LR; }
+        const float2 *p = src + vec * vs + j * es;
+        float2 v[R];
 #pragma unroll
-    for (int b = 0; b < NB; ++b) {
-        const int w = threadIdx.x + b * DCT_T;
-        if (w < total) {
-            int vec, j;
-            if (vfast) { j = w / nvec; vec = w - j * nvec; }
-            else { vec = w / LR; j = w - vec * LR; }
-            const int k = j % Ns;
+        for (int r = 0; r < R; ++r) v[r] = p[r * LR * es];
+        const int jq = fdiv(j, st.fNs);
+        const int k = j - jq * Ns;
+        if (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                float2 t = tw[r * k * tstep];
+                float2 t = __ldg(tw + r * k * tstep);
                 if (INV) t.y = -t.y;
-                v[b][r] = cmul(v[b][r], t);
+                v[r] = cmul(v[r], t);
             }
-            Dft<R, INV>::run(v[b]);
-            const int idxD = (j / Ns) * Ns * R + k;
-            float2 *p = buf + vec * vs + idxD * es;
-#pragma unroll
-            for (int r = 0; r < R; ++r) p[r * Ns * es] = v[b][r];
         }
+        Dft<R, INV>::run(v);
+        float2 *q = dst + vec * vs + (jq * Ns * R + k) * es;
+#pragma unroll
+        for (int r = 0; r < R; ++r) q[r * Ns * es] = v[r];
     }
     __syncthreads();
 }
 
+// All passes of one sub-transform, ping-ponging between cur and oth; on
+// return cur holds the result.
 template <bool INV>
-__device__ void fft_smem(float2 *buf, int L, const int8_t *rad, int nr, int nvec, int es, int vs,
-                         bool vfast, const float2 *tw)
+__device__ void fft_seq(float2 *&cur, float2 *&oth, int L, const DctStage *stages, int nr, int nvec,
+                        FastDiv fnvec, int es, int vs, bool vfast, const float2 *tw)
 {
-    int Ns = 1;
     for (int s = 0; s < nr; ++s) {
-        const int R = rad[s];
-        if (R == 4) fft_pass<4, INV>(buf, L, Ns, nvec, es, vs, vfast, tw);
-        else if (R == 2) fft_pass<2, INV>(buf, L, Ns, nvec, es, vs, vfast, tw);
-        else if (R == 3) fft_pass<3, INV>(buf, L, Ns, nvec, es, vs, vfast, tw);
-        else fft_pass<5, INV>(buf, L, Ns, nvec, es, vs, vfast, tw);
-        Ns *= R;
+        const DctStage st = stages[s];
+        if (st.R == 8) fft_pass<8, INV>(cur, oth, L, st, nvec, fnvec, es, vs, vfast, tw);
+        else if (st.R == 4) fft_pass<4, INV>(cur, oth, L, st, nvec, fnvec, es, vs, vfast, tw);
+        else if (st.R == 2) fft_pass<2, INV>(cur, oth, L, st, nvec, fnvec, es, vs, vfast, tw);
+        else if (st.R == 3) fft_pass<3, INV>(cur, oth, L, st, nvec, fnvec, es, vs, vfast, tw);
+        else fft_pass<5, INV>(cur, oth, L, st, nvec, fnvec, es, vs, vfast, tw);
+        float2 *t = cur; cur = oth; oth = t;
     }
 }
 
@@ -165,7 +177,10 @@ struct Ctx {
     int c, C;
     int ncol;    // valid local columns
     int p0, npl; // local row pairs
-    int8_t r1[DCT_MAXR], r2[DCT_MAXR];
+    FastDiv f_ncolmax, f_m2, f_npmax;
+    const float2 *tw4;   // W_m^{64 i} (m/64 + 1 entries) followed by W_m^i (64 entries)
+    const float2 *tws;   // W_{4n}^{64 i} (4n/64 + 1 entries) followed by W_{4n}^i (64 entries)
+    DctStage s1[DCT_MAXR], s2[DCT_MAXR];
 };
 
 __device__ __forceinline__ int slot_row(const Ctx &X, int slot) {
@@ -180,25 +195,41 @@ __device__ __forceinline__ int slot_row(const Ctx &X, int slot) {
 // sample index of position i of the even/odd-reordered sequence v
 __device__ __forceinline__ int vpos_t(int i, int n, int m) { return i < m ? 2 * i : 2 * n - 1 - 2 * i; }
 
-// Forward half-split: packed orthonormal coefficients of slot k from Z_k, Z_{m-k}.
-__device__ __forceinline__ float2 split_fwd_one(float2 a, float2 b, int k, int n, float sq) {
+// W_m^{r}, 0 <= r < m, from the two-level table (one complex multiply)
+__device__ __forceinline__ float2 tw4_lookup(const float2 *__restrict__ t4, int m, int r) {
+    const float2 hi = __ldg(t4 + (r >> 6));
+    const float2 lo = __ldg(t4 + (m >> 6) + 1 + (r & 63));
+    return cmul(hi, lo);
+}
+
+// W_{4n}^{r} = e^{-i pi r/(2n)}, 0 <= r < 4n, from the two-level table
+__device__ __forceinline__ float2 tws_lookup(const float2 *__restrict__ ts, int n4, int r) {
+    const float2 hi = __ldg(ts + (r >> 6));
+    const float2 lo = __ldg(ts + (n4 >> 6) + 1 + (r & 63));
+    return cmul(hi, lo);
+}
+
+// Forward half-split: packed orthonormal coefficients of slot k from Z_k,
+// Z_{m-k}: W = e^{-i pi k/2n} A + e^{-i 5 pi k/2n} B.
+__device__ __forceinline__ float2 split_fwd_one(float2 a, float2 b, int k, int n, float sq,
+                                                const float2 *ts) {
     const float2 cb = cconj(b);
     const float2 A = cscale(cadd(a, cb), 0.5f);
     const float2 d = csub(a, cb);
     const float2 Bv = make_float2(0.5f * d.y, -0.5f * d.x);                     // -i/2 (a - conj b)
-    const float xk = static_cast<float>(k) / static_cast<float>(2 * n);
-    const float2 e1 = cexpi_pi(-xk), e5 = cexpi_pi(-5.0f * xk);
+    const float2 e1 = tws_lookup(ts, 4 * n, k), e5 = tws_lookup(ts, 4 * n, 5 * k);
     const float2 W = cadd(cmul(e1, A), cmul(e5, Bv));
     return make_float2(sq * W.x, -sq * W.y);
 }
 // Inverse of the half-split: Z_k from the packed slots k and m-k.
-__device__ __forceinline__ float2 split_inv_one(float2 yk, float2 yp, int k, int kp, int n, float sq) {
+__device__ __forceinline__ float2 split_inv_one(float2 yk, float2 yp, int k, int kp, int n, float sq,
+                                                const float2 *ts) {
     // V_k = sqrt(n/2) e^{i pi k/2n} conj(Y_k)   (sq carries sqrt(n/2)/m)
-    const float2 Vk = cscale(cmul(cexpi_pi(static_cast<float>(k) / static_cast<float>(2 * n)), cconj(yk)), sq);
-    const float2 Vp = cscale(cmul(cexpi_pi(static_cast<float>(kp) / static_cast<float>(2 * n)), cconj(yp)), sq);
+    const float2 Vk = cscale(cmulc(cconj(yk), tws_lookup(ts, 4 * n, k)), sq);
+    const float2 Vp = cscale(cmulc(cconj(yp), tws_lookup(ts, 4 * n, kp)), sq);
     const float2 cVp = cconj(Vp);
     const float2 A = cscale(cadd(Vk, cVp), 0.5f);
-    const float2 Bv = cscale(cmul(cexpi_pi(static_cast<float>(2 * k) / static_cast<float>(n)), csub(Vk, cVp)), 0.5f);
+    const float2 Bv = cscale(cmulc(csub(Vk, cVp), tws_lookup(ts, 4 * n, 4 * k)), 0.5f);  // e^{+2 pi i k/n}
     return make_float2(A.x - Bv.y, A.y + Bv.x);                                 // A + i B
 }
 
@@ -206,22 +237,24 @@ __device__ __forceinline__ float2 split_inv_one(float2 yk, float2 yp, int k, int
 template <bool INV>
 __device__ __noinline__ void split_pass(const Ctx &X, float2 *U)
 {
-    const int m2 = X.m2, m1 = X.m1, m = X.m, n = X.n;
+    const int m2 = X.m2, m1 = X.m1, m = X.m, n = X.n, p0 = X.p0;
     const float sq = INV ? static_cast<float>(sqrt(0.5 * n) / m) : static_cast<float>(sqrt(2.0 / n));
     const float s0 = INV ? static_cast<float>(sqrt(static_cast<double>(n)) / m)
                          : static_cast<float>(1.0 / sqrt(static_cast<double>(n)));
     const int total = X.npl * m2;
+    const FastDiv fm2 = X.f_m2;
+    const float2 *ts = X.tws;
     for (int e = threadIdx.x; e < total; e += DCT_T) {
-        const int pl = e / m2, k2 = e - pl * m2;
-        const int p = X.p0 + pl;
+        const int pl = fdiv(e, fm2), k2 = e - pl * m2;
+        const int p = p0 + pl;
         const int cnt = (p == 0) ? (m2 / 2 + 1) : ((2 * p == m1) ? (m2 + 1) / 2 : m2);
         if (k2 >= cnt) continue;
         const int k = p + m1 * k2;
         int ib, k2p;
-        if (p == 0) { k2p = (m2 - k2) % m2; ib = 2 * pl * m2 + k2p; }
+        if (p == 0) { k2p = (k2 == 0) ? 0 : m2 - k2; ib = 2 * pl * m2 + k2p; }
         else { k2p = m2 - 1 - k2; ib = ((m1 - p == p) ? 2 * pl : 2 * pl + 1) * m2 + k2p; }
         const int ia = 2 * pl * m2 + k2;
-        const int kp = (m - k) % m;
+        const int kp = (k == 0) ? 0 : m - k;
         const float2 Za = U[ia], Zb = U[ib];
         if (k == 0) {
             if (!INV) {
@@ -234,110 +267,133 @@ __device__ __noinline__ void split_pass(const Ctx &X, float2 *U)
             continue;
         }
         if (!INV) {
-            const float2 Ya = split_fwd_one(Za, Zb, k, n, sq);
-            if (ib != ia) U[ib] = split_fwd_one(Zb, Za, kp, n, sq);
+            const float2 Ya = split_fwd_one(Za, Zb, k, n, sq, ts);
+            if (ib != ia) U[ib] = split_fwd_one(Zb, Za, kp, n, sq, ts);
             U[ia] = Ya;
         } else {
-            const float2 Ya = split_inv_one(Za, Zb, k, kp, n, sq);
-            if (ib != ia) U[ib] = split_inv_one(Zb, Za, kp, k, n, sq);
+            const float2 Ya = split_inv_one(Za, Zb, k, kp, n, sq, ts);
+            if (ib != ia) U[ib] = split_inv_one(Zb, Za, kp, k, n, sq, ts);
             U[ia] = Ya;
         }
     }
     __syncthreads();
 }
 
-// Time layout -> freq layout (forward) or back (inverse) through registers:
-// remote reads, cluster barrier, local writes.  The four-step twiddle
-// W_m^{-+ j2 k1} is applied on the way.
+// Time layout (src, every CTA) -> freq layout (dst, local), or back.  The
+// four-step twiddle W_m^{-+ j2 k1} comes from the two-level table.  The
+// first cluster barrier makes every CTA's src complete; the second keeps
+// src alive until every remote read of it has finished.
 template <bool INV>
-__device__ __noinline__ void transpose(const Ctx &X, float2 *U, cg::cluster_group &cl)
+__device__ __noinline__ void transpose(const Ctx &X, const float2 *src, float2 *dst, cg::cluster_group &cl)
 {
-    constexpr int NE = DCT_EMAX;
-    float2 tmp[NE];
-    cl.sync();   // every CTA finished its local passes
-    const float inv_m = 2.0f / static_cast<float>(X.m);
+    constexpr int U = 4;     // independent remote reads in flight per thread
+    const int m = X.m, m1 = X.m1, m2 = X.m2, ncolmax = X.ncolmax, npmax = X.npmax;
+    const float2 *t4 = X.tw4;
+    cl.sync();
     if (!INV) {
-        const int total = 2 * X.npl * X.m2;
+        const int total = 2 * X.npl * m2;
+        const FastDiv fm2 = X.f_m2, fnc = X.f_ncolmax;
+        for (int e0 = threadIdx.x; e0 < total; e0 += U * DCT_T) {
+            float2 v[U], w[U];
 #pragma unroll
-        for (int b = 0; b < NE; ++b) {
-            const int e = threadIdx.x + b * DCT_T;
-            float2 v = make_float2(0.f, 0.f);
-            if (e < total) {
-                const int slot = e / X.m2, j2 = e - slot * X.m2;
-                const int k1 = slot_row(X, slot);
-                if (k1 >= 0) {
-                    const int o = j2 / X.ncolmax, lc = j2 - o * X.ncolmax;
-                    const float2 *rT = cl.map_shared_rank(U, o);
-                    v = cmul(rT[k1 * X.ncolmax + lc], cexpi_pi(-static_cast<float>(j2 * k1) * inv_m));
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * DCT_T;
+                v[u] = make_float2(0.f, 0.f);
+                w[u] = make_float2(1.f, 0.f);
+                if (e < total) {
+                    const int slot = fdiv(e, fm2), j2 = e - slot * m2;
+                    const int k1 = slot_row(X, slot);
+                    if (k1 >= 0) {
+                        const int o = fdiv(j2, fnc), lc = j2 - o * ncolmax;
+                        v[u] = cl.map_shared_rank(src, o)[k1 * ncolmax + lc];
+                        w[u] = tw4_lookup(t4, m, j2 * k1);
+                    }
                 }
             }
-            tmp[b] = v;
-        }
-        cl.sync();   // all remote reads done before anyone overwrites
 #pragma unroll
-        for (int b = 0; b < NE; ++b) {
-            const int e = threadIdx.x + b * DCT_T;
-            if (e < total) U[e] = tmp[b];
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * DCT_T;
+                if (e < total) dst[e] = cmul(v[u], w[u]);
+            }
         }
     } else {
-        const int total = X.m1 * X.ncolmax;
+        const int total = m1 * ncolmax;
+        const FastDiv fnc = X.f_ncolmax, fnp = X.f_npmax;
+        for (int e0 = threadIdx.x; e0 < total; e0 += U * DCT_T) {
+            float2 v[U], w[U];
 #pragma unroll
-        for (int b = 0; b < NE; ++b) {
-            const int e = threadIdx.x + b * DCT_T;
-            float2 v = make_float2(0.f, 0.f);
-            if (e < total) {
-                const int k1 = e / X.ncolmax, lc = e - k1 * X.ncolmax;
-                if (lc < X.ncol) {
-                    const int j2 = X.c * X.ncolmax + lc;
-                    const int p = min(k1, X.m1 - k1);
-                    const int o = p / X.npmax;
-                    const int slot = 2 * (p - o * X.npmax) + (k1 == p ? 0 : 1);
-                    const float2 *rF = cl.map_shared_rank(U, o);
-                    v = cmul(rF[slot * X.m2 + j2], cexpi_pi(static_cast<float>(j2 * k1) * inv_m));
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * DCT_T;
+                v[u] = make_float2(0.f, 0.f);
+                w[u] = make_float2(1.f, 0.f);
+                if (e < total) {
+                    const int k1 = fdiv(e, fnc), lc = e - k1 * ncolmax;
+                    if (lc < X.ncol) {
+                        const int j2 = X.c * ncolmax + lc;
+                        const int p = min(k1, m1 - k1);
+                        const int o = fdiv(p, fnp);
+                        const int slot = 2 * (p - o * npmax) + (k1 == p ? 0 : 1);
+                        v[u] = cl.map_shared_rank(src, o)[slot * m2 + j2];
+                        w[u] = tw4_lookup(t4, m, j2 * k1);
+                    }
                 }
             }
-            tmp[b] = v;
-        }
-        cl.sync();
 #pragma unroll
-        for (int b = 0; b < NE; ++b) {
-            const int e = threadIdx.x + b * DCT_T;
-            if (e < total) U[e] = tmp[b];
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * DCT_T;
+                if (e < total) dst[e] = cmulc(v[u], w[u]);
+            }
         }
     }
-    __syncthreads();
+    cl.sync();
 }
 
-// Forward DCT of the time-layout data already in U (packed spectrum -> U).
-__device__ __noinline__ void dct_forward_inplace(const Ctx &X, float2 *U, const float2 *tw1, const float2 *tw2,
-                                    cg::cluster_group &cl)
+// Forward DCT: time layout in cur -> packed spectrum in cur (the two
+// buffers may swap roles).
+__device__ __noinline__ void dct_forward(const Ctx &X, float2 *&cur, float2 *&oth, const float2 *tw1,
+                                         const float2 *tw2, cg::cluster_group &cl)
 {
-    fft_smem<false>(U, X.m1, X.r1, X.nr1, X.ncol, X.ncolmax, 1, true, tw1);
-    transpose<false>(X, U, cl);
-    fft_smem<false>(U, X.m2, X.r2, X.nr2, 2 * X.npl, 1, X.m2, false, tw2);
-    split_pass<false>(X, U);
+    fft_seq<false>(cur, oth, X.m1, X.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, tw1);
+    transpose<false>(X, cur, oth, cl);
+    { float2 *t = cur; cur = oth; oth = t; }
+    fft_seq<false>(cur, oth, X.m2, X.s2, X.nr2, 2 * X.npl, X.f_m2, 1, X.m2, false, tw2);
+    split_pass<false>(X, cur);
 }
-// Inverse (transpose of the orthonormal DCT-II): packed spectrum in U ->
-// time layout in U, scaled.
-__device__ __noinline__ void dct_inverse_inplace(const Ctx &X, float2 *U, const float2 *tw1, const float2 *tw2,
-                                    cg::cluster_group &cl)
+// Inverse (transpose of the orthonormal DCT-II): packed spectrum in cur ->
+// time layout in cur, scaled.
+__device__ __noinline__ void dct_inverse(const Ctx &X, float2 *&cur, float2 *&oth, const float2 *tw1,
+                                         const float2 *tw2, cg::cluster_group &cl)
 {
-    split_pass<true>(X, U);
-    fft_smem<true>(U, X.m2, X.r2, X.nr2, 2 * X.npl, 1, X.m2, false, tw2);
-    transpose<true>(X, U, cl);
-    fft_smem<true>(U, X.m1, X.r1, X.nr1, X.ncol, X.ncolmax, 1, true, tw1);
+    split_pass<true>(X, cur);
+    fft_seq<true>(cur, oth, X.m2, X.s2, X.nr2, 2 * X.npl, X.f_m2, 1, X.m2, false, tw2);
+    transpose<true>(X, cur, oth, cl);
+    { float2 *t = cur; cur = oth; oth = t; }
+    fft_seq<true>(cur, oth, X.m1, X.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, tw1);
 }
 
 // Fill U (time layout) with f(j) = (x_{t(2j)}, x_{t(2j+1)}) for own columns.
 template <class F>
 __device__ void load_time(const Ctx &X, float2 *U, F f)
 {
+    constexpr int UB = 4;
     const int total = X.m1 * X.ncolmax;
-    for (int e = threadIdx.x; e < total; e += DCT_T) {
-        const int j1 = e / X.ncolmax, lc = e - j1 * X.ncolmax;
-        float2 z = make_float2(0.f, 0.f);
-        if (lc < X.ncol) z = f(j1 * X.m2 + X.c * X.ncolmax + lc);
-        U[e] = z;
+    const FastDiv fnc = X.f_ncolmax;
+    for (int e0 = threadIdx.x; e0 < total; e0 += UB * DCT_T) {
+        float2 z[UB];
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            const int e = e0 + u * DCT_T;
+            z[u] = make_float2(0.f, 0.f);
+            if (e < total) {
+                const int j1 = fdiv(e, fnc), lc = e - j1 * X.ncolmax;
+                if (lc < X.ncol) z[u] = f(j1 * X.m2 + X.c * X.ncolmax + lc);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            const int e = e0 + u * DCT_T;
+            if (e < total) U[e] = z[u];
+        }
     }
     __syncthreads();
 }
@@ -370,14 +426,17 @@ __device__ double2 cluster_sum2(double2 v, double2 *s_red, double2 *s_part, int 
     return tot;
 }
 
-__device__ void load_ctx(Ctx &X, const DctPlan &P, int c, int C)
+__device__ void load_ctx(Ctx &X, const DctPlan &P, const float2 *tw, int c, int C)
 {
     X.n = P.n; X.m = P.m; X.m1 = P.m1; X.m2 = P.m2; X.ncolmax = P.ncolmax; X.npmax = P.npmax;
     X.P = P.P; X.nr1 = P.nr1; X.nr2 = P.nr2; X.c = c; X.C = C;
     X.ncol = max(0, min(P.ncolmax, P.m2 - c * P.ncolmax));
     X.p0 = c * P.npmax;
     X.npl = max(0, min(P.npmax, P.P - X.p0));
-    for (int i = 0; i < DCT_MAXR; ++i) { X.r1[i] = P.r1[i]; X.r2[i] = P.r2[i]; }
+    X.f_ncolmax = P.f_ncolmax; X.f_m2 = P.f_m2; X.f_npmax = P.f_npmax;
+    X.tw4 = tw + P.tw4;
+    X.tws = tw + P.tws;
+    for (int i = 0; i < DCT_MAXR; ++i) { X.s1[i] = P.s1[i]; X.s2[i] = P.s2[i]; }
 }
 
 __device__ __forceinline__ bool flagged(const uint32_t *flags, int64_t t) {
@@ -389,36 +448,102 @@ __device__ __forceinline__ float fratio_pow(int kappa, float fscale, float alpha
     return exp2f(alpha * log2f(static_cast<float>(kappa) * fscale));
 }
 
-// shared-memory carve-up common to both kernels
+// shared-memory carve-up common to both kernels; tw1/tw2 point at the
+// plan's twiddle tables in global memory (read through L1)
 struct Smem {
-    float2 *U0, *U1, *tw1, *tw2;
+    float2 *U0, *U1;
+    const float2 *tw1, *tw2;
+    void *tail;
 };
-__device__ __forceinline__ Smem carve(void *raw, int sz, int m1max, int m2max)
+__device__ __forceinline__ Smem carve(void *raw, int sz)
 {
     Smem s;
     float2 *p = static_cast<float2 *>(raw);
     s.U0 = p; p += sz;
     s.U1 = p; p += sz;
-    s.tw1 = p; p += m1max;
-    s.tw2 = p; p += m2max;
+    s.tw1 = nullptr;
+    s.tw2 = nullptr;
+    s.tail = p;
     return s;
 }
 
-__device__ void load_plan(Ctx *sX, const DctPlan *plans, int pi, const float2 *tw,
-                          float2 *tw1, float2 *tw2, int c, int C)
+__device__ void load_plan(Ctx *sX, const DctPlan *plans, int pi, const float2 *tw, Smem &sm, int c, int C)
 {
     __syncthreads();      // previous users of sX are done
-    if (threadIdx.x == 0) load_ctx(*sX, plans[pi], c, C);
+    if (threadIdx.x == 0) load_ctx(*sX, plans[pi], tw, c, C);
     __syncthreads();
-    const Ctx &X = *sX;
-    const DctPlan &P = plans[pi];
-    for (int i = threadIdx.x; i < X.m1; i += DCT_T) tw1[i] = tw[P.tw1 + i];
-    for (int i = threadIdx.x; i < X.m2; i += DCT_T) tw2[i] = tw[P.tw2 + i];
+    sm.tw1 = tw + plans[pi].tw1;
+    sm.tw2 = tw + plans[pi].tw2;
+}
+
+// element e of the time layout -> (t0, t1) samples
+__device__ __forceinline__ void elem_samples(const Ctx &X, int e, int &t0, int &t1, bool &valid)
+{
+    const int j1 = fdiv(e, X.f_ncolmax), lc = e - j1 * X.ncolmax;
+    valid = lc < X.ncol;
+    const int j = j1 * X.m2 + X.c * X.ncolmax + lc;
+    t0 = vpos_t(2 * j, X.n, X.m);
+    t1 = vpos_t(2 * j + 1, X.n, X.m);
+}
+// sample t -> (owner CTA, element, part)
+__device__ __forceinline__ void sample_loc(const Ctx &X, int t, int &owner, int &loc)
+{
+    // position of sample t in the even-then-reversed-odd order: t/2 for even
+    // t, n-1-(t-1)/2 = n-1-floor(t/2) for odd t
+    const int h = t >> 1;
+    const int i = (t & 1) ? (X.n - 1) - h : h;
+    const int j = i >> 1;
+    const int j1 = fdiv(j, X.f_m2), j2 = j - j1 * X.m2;
+    owner = fdiv(j2, X.f_ncolmax);
+    const int lc = j2 - owner * X.ncolmax;
+    loc = 2 * (j1 * X.ncolmax + lc) + (i & 1);
+}
+
+// Multiply the packed spectrum in U by a per-mode weight:
+//   kind 0: beta_kappa  = 1/(phi_kappa + 1/sigma0^2) = s2/(1 + r)
+//   kind 1: gamma_kappa = sigma0^2 - beta_kappa     = s2 r/(1 + r)
+//   kind 2: 1/P_kappa = 1/(s2 (1 + (f/f_knee)^alpha)),  0 at kappa = 0
+// with r = sigma0^2 phi = (f/f_knee)^-alpha (r = 0 at kappa = 0).  gamma is
+// evaluated directly, so the Schur operator sigma0^2 I - E^T B^{-1} E =
+// E^T C^T diag(gamma) C E carries no FP32 cancellation on its small modes.
+// Kinds 0 and 1 read (beta_a, beta_b, gamma_a, gamma_b) per packed element
+// from wt, filled once per detscan by fill_weights.
+__device__ __noinline__ void apply_filter(const Ctx &X, float2 *U, float fscale, float alpha, float s2,
+                                          int kind, const float4 *__restrict__ wt)
+{
+    const int total = 2 * X.npl * X.m2;
+    const FastDiv fm2 = X.f_m2;
+    if (kind != 2) {
+        for (int e = threadIdx.x; e < total; e += DCT_T) {
+            const float4 w = wt[e];
+            float2 v = U[e];
+            v.x *= kind ? w.z : w.x;
+            v.y *= kind ? w.w : w.y;
+            U[e] = v;
+        }
+        __syncthreads();
+        return;
+    }
+    for (int e = threadIdx.x; e < total; e += DCT_T) {
+        const int slot = fdiv(e, fm2), k2 = e - slot * X.m2;
+        const int k1 = slot_row(X, slot);
+        if (k1 < 0) continue;
+        const int k = k1 + X.m1 * k2;
+        const int ka = k, kb = (k == 0) ? X.m : X.n - k;
+        const float wa = (ka == 0) ? 0.f : 1.0f / (s2 * (1.0f + fratio_pow(ka, fscale, alpha)));
+        const float wb = 1.0f / (s2 * (1.0f + fratio_pow(kb, fscale, alpha)));
+        float2 v = U[e];
+        v.x *= wa;
+        v.y *= wb;
+        U[e] = v;
+    }
     __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
-// A4: gain.  shat = C(M s) in U0, dhat = C(M d) in U1, sums over k >= 1.
+// A4: gain.  a = sum_{k>=1} shat_k^2 / P_k from the forward transform of
+// M s; b = sum_k shat_k dhat_k / P_k = <M s, C^T diag(1/P) C (M d)> in the
+// time domain, so two buffers suffice.
 // ---------------------------------------------------------------------------
 struct GainArgs {
     const float *d, *s;
@@ -448,49 +573,62 @@ __global__ void __launch_bounds__(DCT_T, 1) k_gain(GainArgs a)
     cg::cluster_group cl = cg::this_cluster();
     const int C = static_cast<int>(cl.num_blocks()), c = static_cast<int>(cl.block_rank());
     const int cid = blockIdx.x / C, ncl = gridDim.x / C;
-    Smem sm = carve(smem_raw, a.sz, a.m1max, a.m2max);
+    Smem sm = carve(smem_raw, a.sz);
     int parity = 0;
     for (int w = cid; w < a.work_count; w += ncl) {
         const int q = a.work[a.work_begin + w];
         const int det = q % a.ndet;
         const int64_t o = a.off[q];
-        load_plan(&sX, a.plans, a.q_plan[q], a.tw, sm.tw1, sm.tw2, c, C);
+        load_plan(&sX, a.plans, a.q_plan[q], a.tw, sm, c, C);
         const Ctx &X = sX;
         const int n = X.n, m = X.m;
         const float *sq = a.s + o, *dq = a.d + o;
         const uint32_t *fl = a.flags;
-        load_time(X, sm.U0, [&](int j) {
-            const int t0 = vpos_t(2 * j, n, m), t1 = vpos_t(2 * j + 1, n, m);
-            return make_float2(flagged(fl, o + t0) ? 0.f : sq[t0], flagged(fl, o + t1) ? 0.f : sq[t1]);
-        });
-        dct_forward_inplace(X, sm.U0, sm.tw1, sm.tw2, cl);
-        load_time(X, sm.U1, [&](int j) {
-            const int t0 = vpos_t(2 * j, n, m), t1 = vpos_t(2 * j + 1, n, m);
-            return make_float2(flagged(fl, o + t0) ? 0.f : dq[t0], flagged(fl, o + t1) ? 0.f : dq[t1]);
-        });
-        dct_forward_inplace(X, sm.U1, sm.tw1, sm.tw2, cl);
-        // sums over this CTA's packed coefficients
         const double sig0 = a.psd[3 * det], fk = a.psd[3 * det + 1], al = a.psd[3 * det + 2];
         const float fscale = static_cast<float>(a.fsamp / (2.0 * n * fk));
         const float alpha = static_cast<float>(al);
-        const float inv_s2 = static_cast<float>(1.0 / (sig0 * sig0));
+        const float s2 = static_cast<float>(sig0 * sig0);
+        float2 *cur = sm.U0, *oth = sm.U1;
+        // a from C(M s)
+        load_time(X, cur, [&](int j) {
+            const int t0 = vpos_t(2 * j, n, m), t1 = vpos_t(2 * j + 1, n, m);
+            return make_float2(flagged(fl, o + t0) ? 0.f : sq[t0], flagged(fl, o + t1) ? 0.f : sq[t1]);
+        });
+        dct_forward(X, cur, oth, sm.tw1, sm.tw2, cl);
         Acc2 sa = {0.f, 0.f}, sb = {0.f, 0.f};
-        const int total = 2 * X.npl * X.m2;
-        for (int e = threadIdx.x; e < total; e += DCT_T) {
-            const int slot = e / X.m2, k2 = e - slot * X.m2;
-            const int k1 = slot_row(X, slot);
-            if (k1 < 0) continue;
-            const int k = k1 + X.m1 * k2;
-            const float2 S = sm.U0[e], D = sm.U1[e];
-            const int ka = k, kb = (k == 0) ? m : n - k;
-            if (ka != 0) {
-                const float wa = inv_s2 / (1.0f + fratio_pow(ka, fscale, alpha));
-                acc_add(sa, S.x * S.x * wa);
-                acc_add(sb, S.x * D.x * wa);
+        {
+            const int total = 2 * X.npl * X.m2;
+            for (int e = threadIdx.x; e < total; e += DCT_T) {
+                const int slot = fdiv(e, X.f_m2), k2 = e - slot * X.m2;
+                const int k1 = slot_row(X, slot);
+                if (k1 < 0) continue;
+                const int k = k1 + X.m1 * k2;
+                const float2 S = cur[e];
+                const int ka = k, kb = (k == 0) ? m : n - k;
+                if (ka != 0) acc_add(sa, S.x * S.x / (s2 * (1.0f + fratio_pow(ka, fscale, alpha))));
+                acc_add(sa, S.y * S.y / (s2 * (1.0f + fratio_pow(kb, fscale, alpha))));
             }
-            const float wb = inv_s2 / (1.0f + fratio_pow(kb, fscale, alpha));
-            acc_add(sa, S.y * S.y * wb);
-            acc_add(sb, S.y * D.y * wb);
+        }
+        __syncthreads();
+        // b from <M s, C^T diag(1/P) C M d>
+        load_time(X, cur, [&](int j) {
+            const int t0 = vpos_t(2 * j, n, m), t1 = vpos_t(2 * j + 1, n, m);
+            return make_float2(flagged(fl, o + t0) ? 0.f : dq[t0], flagged(fl, o + t1) ? 0.f : dq[t1]);
+        });
+        dct_forward(X, cur, oth, sm.tw1, sm.tw2, cl);
+        apply_filter(X, cur, fscale, alpha, s2, 2, nullptr);
+        dct_inverse(X, cur, oth, sm.tw1, sm.tw2, cl);
+        {
+            const int tot = X.m1 * X.ncolmax;
+            for (int e = threadIdx.x; e < tot; e += DCT_T) {
+                int t0, t1;
+                bool valid;
+                elem_samples(X, e, t0, t1, valid);
+                if (!valid) continue;
+                const float2 v = cur[e];
+                if (!flagged(fl, o + t0)) acc_add_prod(sb, sq[t0], v.x);
+                if (!flagged(fl, o + t1)) acc_add_prod(sb, sq[t1], v.y);
+            }
         }
         const double2 ab = cluster_sum2(make_double2(acc_value(sa), acc_value(sb)), s_red, s_part,
                                         parity, cl);
@@ -521,8 +659,8 @@ __global__ void __launch_bounds__(DCT_T, 1) k_gain(GainArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// A5: correlated noise.  x0 = B^{-1} b (B = C^T diag(phi + 1/sigma0^2) C) in
-// U1; flagged detscans then solve the Schur complement
+// A5: correlated noise.  x0 = B^{-1} b (B = C^T diag(phi + 1/sigma0^2) C)
+// is written to x_out; flagged detscans then solve the Schur complement
 //   S y = E^T x0,  S = sigma0^2 I - E^T B^{-1} E = E^T C^T diag(gamma) C E
 // (E: flagged samples; C^T C = I) by CG and add B^{-1} E y (Woodbury):
 // x = A^{-1} b exactly, A = B - E E^T / sigma0^2.
@@ -547,59 +685,11 @@ struct NcorrArgs {
     float *x_out;
     int32_t *iters;
     int32_t *status;
+    float4 *wscratch;
+    const float *xtab;       // Toeplitz inverses' first columns per detector (NULL: no preconditioner)
+    const int32_t *lvalid;
     int sz, m1max, m2max;
 };
-
-// Multiply the packed spectrum in U by a per-mode weight:
-//   beta_kappa  = 1/(phi_kappa + 1/sigma0^2) = s2/(1 + r)          (hp = false)
-//   gamma_kappa = sigma0^2 - beta_kappa     = s2 r/(1 + r)         (hp = true)
-// with r = sigma0^2 phi = (f/f_knee)^-alpha (r = 0 at kappa = 0).  gamma is
-// evaluated directly, so the Schur operator sigma0^2 I - E^T B^{-1} E =
-// E^T C^T diag(gamma) C E carries no FP32 cancellation on its small modes.
-__device__ __noinline__ void apply_filter(const Ctx &X, float2 *U, float fscale, float alpha, float s2,
-                                          bool hp)
-{
-    const int total = 2 * X.npl * X.m2;
-    for (int e = threadIdx.x; e < total; e += DCT_T) {
-        const int slot = e / X.m2, k2 = e - slot * X.m2;
-        const int k1 = slot_row(X, slot);
-        if (k1 < 0) continue;
-        const int k = k1 + X.m1 * k2;
-        const int ka = k, kb = (k == 0) ? X.m : X.n - k;
-        const float ra = (ka == 0) ? 0.f : fratio_pow(ka, fscale, -alpha);
-        const float rb = fratio_pow(kb, fscale, -alpha);
-        const float wa = hp ? s2 * ra / (1.0f + ra) : s2 / (1.0f + ra);
-        const float wb = hp ? s2 * rb / (1.0f + rb) : s2 / (1.0f + rb);
-        float2 v = U[e];
-        v.x *= wa;
-        v.y *= wb;
-        U[e] = v;
-    }
-    __syncthreads();
-}
-
-// element e of the time layout -> (t0, t1) samples
-__device__ __forceinline__ void elem_samples(const Ctx &X, int e, int &t0, int &t1, bool &valid)
-{
-    const int j1 = e / X.ncolmax, lc = e - j1 * X.ncolmax;
-    valid = lc < X.ncol;
-    const int j = j1 * X.m2 + X.c * X.ncolmax + lc;
-    t0 = vpos_t(2 * j, X.n, X.m);
-    t1 = vpos_t(2 * j + 1, X.n, X.m);
-}
-// sample t -> (owner CTA, element, part)
-__device__ __forceinline__ void sample_loc(const Ctx &X, int t, int &owner, int &loc)
-{
-    // position of sample t in the even-then-reversed-odd order: t/2 for even
-    // t, n-1-(t-1)/2 = n-1-floor(t/2) for odd t
-    const int h = t >> 1;
-    const int i = (t & 1) ? (X.n - 1) - h : h;
-    const int j = i >> 1;
-    const int j1 = j / X.m2, j2 = j - j1 * X.m2;
-    owner = j2 / X.ncolmax;
-    const int lc = j2 - owner * X.ncolmax;
-    loc = 2 * (j1 * X.ncolmax + lc) + (i & 1);
-}
 
 __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
 {
@@ -608,22 +698,35 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
     __shared__ double2 s_red[DCT_T / 32];
     __shared__ double2 s_part[2];
     __shared__ int s_scan[DCT_T];
+    __shared__ int s_gscan[DCT_T];
+    __shared__ int s_escan[DCT_T];
+    __shared__ int s_kc, s_ngap, s_nown, s_ovf;
+    __shared__ int g_beg[GAP_CAP], g_end[GAP_CAP];
+    __shared__ int o_beg[GAP_CAP], o_len[GAP_CAP], o_off[GAP_CAP];
     cg::cluster_group cl = cg::this_cluster();
     const int C = static_cast<int>(cl.num_blocks()), c = static_cast<int>(cl.block_rank());
     const int cid = blockIdx.x / C, ncl = gridDim.x / C;
-    Smem sm = carve(smem_raw, a.sz, a.m1max, a.m2max);
-    // CG vectors after the twiddle tables
-    int *c_loc = reinterpret_cast<int *>(sm.tw2 + a.m2max);
-    float *c_y = reinterpret_cast<float *>(c_loc + CG_KCAP);
+    Smem sm = carve(smem_raw, a.sz);
+    // CG vectors and preconditioner work areas after the two buffers
+    int *c_loc = reinterpret_cast<int *>(sm.tail);
+    int *c_t = c_loc + CG_KCAP;
+    float *c_y = reinterpret_cast<float *>(c_t + CG_KCAP);
     float *c_r = c_y + CG_KCAP;
     float *c_p = c_r + CG_KCAP;
     float *c_q = c_p + CG_KCAP;
+    float *c_z = c_q + CG_KCAP;
+    int *g_map = reinterpret_cast<int *>(c_z + CG_KCAP);
+    float *gb_r = reinterpret_cast<float *>(g_map + GMAP_CAP);
+    float *gb_x = gb_r + TOEP_LMAX;
+    float *gb_u1 = gb_x + TOEP_LMAX;
+    float *gb_u2 = gb_u1 + TOEP_LMAX;
     int parity = 0;
     for (int w = cid; w < a.work_count; w += ncl) {
         const int q = a.work[a.work_begin + w];
         const int det = q % a.ndet;
         const int64_t o = a.off[q];
-        load_plan(&sX, a.plans, a.q_plan[q], a.tw, sm.tw1, sm.tw2, c, C);
+        load_plan(&sX, a.plans, a.q_plan[q], a.tw, sm, c, C);
+        if (threadIdx.x == 0) s_nown = 0;
         const Ctx &X = sX;
         const int n = X.n, m = X.m;
         const double sig0 = a.psd[3 * det], fk = a.psd[3 * det + 1], al = a.psd[3 * det + 2];
@@ -638,8 +741,11 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
         const uint32_t *fl = a.flags;
         const tod_rng rng = a.rng;
         const uint64_t gi = rng.gibbs_iter_dev ? *rng.gibbs_iter_dev : rng.gibbs_iter;
+        float *xq = a.x_out + o;
+        float4 *wt = a.wscratch + (static_cast<int64_t>(cid) * C + c) * a.sz;
+        float2 *cur = sm.U0, *oth = sm.U1;
         // right-hand side, time-domain part: M (r/s2 + w1/s)
-        load_time(X, sm.U1, [&](int j) {
+        load_time(X, cur, [&](int j) {
             const int t0 = vpos_t(2 * j, n, m), t1 = vpos_t(2 * j + 1, n, m);
             float2 w1 = make_float2(0.f, 0.f);
             if (draw) w1 = stream_normal_pair(rng.seed, rng.band, q, 1, gi, 2 * j);
@@ -649,165 +755,319 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                                                   : fmaf(dq[t1] - g * sq[t1], inv_s2, w1.y * inv_s);
             return make_float2(r0, r1);
         });
-        dct_forward_inplace(X, sm.U1, sm.tw1, sm.tw2, cl);
-        // + sqrt(phi) w2, times beta
+        dct_forward(X, cur, oth, sm.tw1, sm.tw2, cl);
+        // + sqrt(phi) w2, times beta; the filter weights of this detscan
+        // (beta, gamma for both modes of each packed slot) go to wt once
         {
             const int total = 2 * X.npl * X.m2;
             for (int e = threadIdx.x; e < total; e += DCT_T) {
-                const int slot = e / X.m2, k2 = e - slot * X.m2;
+                const int slot = fdiv(e, X.f_m2), k2 = e - slot * X.m2;
                 const int k1 = slot_row(X, slot);
-                if (k1 < 0) continue;
+                if (k1 < 0) { wt[e] = make_float4(0.f, 0.f, 0.f, 0.f); continue; }
                 const int k = k1 + X.m1 * k2;
                 const int ka = k, kb = (k == 0) ? m : n - k;
-                const float pa = (ka == 0) ? 0.f : fratio_pow(ka, fscale, -alpha) * inv_s2;  // phi
-                const float pb = fratio_pow(kb, fscale, -alpha) * inv_s2;
-                float2 v = sm.U1[e];
+                const float ra = (ka == 0) ? 0.f : fratio_pow(ka, fscale, -alpha);   // s2 phi
+                const float rb = fratio_pow(kb, fscale, -alpha);
+                const float ba = s2 / (1.0f + ra), bb = s2 / (1.0f + rb);
+                wt[e] = make_float4(ba, bb, ra * ba, rb * bb);
+                float2 v = cur[e];
                 if (draw) {
                     const float2 w2 = stream_normal_pair(rng.seed, rng.band, q, 2, gi, 2 * k);
-                    v.x += sqrtf(pa) * w2.x;
-                    v.y += sqrtf(pb) * w2.y;
+                    v.x += sqrtf(ra * inv_s2) * w2.x;
+                    v.y += sqrtf(rb * inv_s2) * w2.y;
                 }
-                v.x /= (pa + inv_s2);
-                v.y /= (pb + inv_s2);
-                sm.U1[e] = v;
+                v.x *= ba;
+                v.y *= bb;
+                cur[e] = v;
             }
             __syncthreads();
         }
-        dct_inverse_inplace(X, sm.U1, sm.tw1, sm.tw2, cl);      // U1 = x0 (time layout)
-
-        // flagged samples owned by this CTA, in sample order (deterministic)
-        const int64_t wb0 = o >> 5, wb1 = (o + n - 1) >> 5;
-        const int nw = static_cast<int>(wb1 - wb0 + 1);
-        const int per = (nw + DCT_T - 1) / DCT_T;
-        int mycnt = 0;
-        for (int i = 0; i < per; ++i) {
-            const int wi = threadIdx.x * per + i;
-            if (wi >= nw) break;
-            uint32_t bits = fl[wb0 + wi];
-            while (bits) {
-                const int b = __popc((bits & (0u - bits)) - 1u);   // index of the lowest set bit
-                bits &= bits - 1;
-                const int64_t tl = ((wb0 + wi) << 5) + b - o;
-                if (tl < 0 || tl >= n) continue;
-                int ow, loc;
-                sample_loc(X, static_cast<int>(tl), ow, loc);
-                if (ow == c) ++mycnt;
-            }
-        }
-        s_scan[threadIdx.x] = mycnt;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int acc = 0;
-            for (int i = 0; i < DCT_T; ++i) { const int v = s_scan[i]; s_scan[i] = acc; acc += v; }
-            s_red[0].x = static_cast<double>(acc);
-        }
-        __syncthreads();
-        const int kc = static_cast<int>(s_red[0].x);
-        int pos = s_scan[threadIdx.x];
-        __syncthreads();
-        for (int i = 0; i < per; ++i) {
-            const int wi = threadIdx.x * per + i;
-            if (wi >= nw) break;
-            uint32_t bits = fl[wb0 + wi];
-            while (bits) {
-                const int b = __popc((bits & (0u - bits)) - 1u);   // index of the lowest set bit
-                bits &= bits - 1;
-                const int64_t tl = ((wb0 + wi) << 5) + b - o;
-                if (tl < 0 || tl >= n) continue;
-                int ow, loc;
-                sample_loc(X, static_cast<int>(tl), ow, loc);
-                if (ow == c) {
-                    if (pos < CG_KCAP) c_loc[pos] = loc;
-                    ++pos;
-                }
-            }
-        }
-        __syncthreads();
-        const double2 kt = cluster_sum2(make_double2(static_cast<double>(kc),
-                                                     kc > CG_KCAP ? 1.0 : 0.0), s_red, s_part, parity, cl);
-        int it = 0;
-        bool conv = true;
-        if (kt.x > 0.0 && kt.y > 0.0) {
-            conv = false;      // too many flagged samples for the CG buffers: left as x0
-            set_status(a.status, q, TOD_ERR_NOT_CONVERGED);
-        } else if (kt.x > 0.0) {
-            float *U1f = reinterpret_cast<float *>(sm.U1);
-            float *U0f = reinterpret_cast<float *>(sm.U0);
-            // rhs = E^T x0 ; y = 0 ; r = p = rhs
-            double rr_loc = 0.0;
-            for (int i = threadIdx.x; i < kc; i += DCT_T) {
-                const float v = U1f[c_loc[i]];
-                c_y[i] = 0.f; c_r[i] = v; c_p[i] = v;
-                rr_loc += static_cast<double>(v) * v;
-            }
-            double rr = cluster_sum2(make_double2(rr_loc, 0.0), s_red, s_part, parity, cl).x;
-            const double stop = static_cast<double>(a.tol) * a.tol * rr;
-            conv = rr == 0.0;
-            while (!conv && it < a.maxit) {
-                // U0 <- E p ; U0 <- B^{-1} U0
-                const int tot = X.m1 * X.ncolmax;
-                for (int e = threadIdx.x; e < tot; e += DCT_T) sm.U0[e] = make_float2(0.f, 0.f);
-                __syncthreads();
-                for (int i = threadIdx.x; i < kc; i += DCT_T) U0f[c_loc[i]] = c_p[i];
-                __syncthreads();
-                dct_forward_inplace(X, sm.U0, sm.tw1, sm.tw2, cl);
-                apply_filter(X, sm.U0, fscale, alpha, s2, true);
-                dct_inverse_inplace(X, sm.U0, sm.tw1, sm.tw2, cl);
-                double pq_loc = 0.0;
-                for (int i = threadIdx.x; i < kc; i += DCT_T) {
-                    const float v = U0f[c_loc[i]];
-                    c_q[i] = v;
-                    pq_loc += static_cast<double>(c_p[i]) * v;
-                }
-                const double pq = cluster_sum2(make_double2(pq_loc, 0.0), s_red, s_part, parity, cl).x;
-                const float alp = static_cast<float>(rr / pq);
-                double rn_loc = 0.0;
-                for (int i = threadIdx.x; i < kc; i += DCT_T) {
-                    c_y[i] = fmaf(alp, c_p[i], c_y[i]);
-                    const float rv = fmaf(-alp, c_q[i], c_r[i]);
-                    c_r[i] = rv;
-                    rn_loc += static_cast<double>(rv) * rv;
-                }
-                const double rn = cluster_sum2(make_double2(rn_loc, 0.0), s_red, s_part, parity, cl).x;
-                ++it;
-                if (rn <= stop) { conv = true; break; }
-                const float beta = static_cast<float>(rn / rr);
-                for (int i = threadIdx.x; i < kc; i += DCT_T) c_p[i] = fmaf(beta, c_p[i], c_r[i]);
-                __syncthreads();
-                rr = rn;
-            }
-            // x = x0 + B^{-1} E y
-            const int tot = X.m1 * X.ncolmax;
-            for (int e = threadIdx.x; e < tot; e += DCT_T) sm.U0[e] = make_float2(0.f, 0.f);
-            __syncthreads();
-            for (int i = threadIdx.x; i < kc; i += DCT_T) U0f[c_loc[i]] = c_y[i];
-            __syncthreads();
-            dct_forward_inplace(X, sm.U0, sm.tw1, sm.tw2, cl);
-            apply_filter(X, sm.U0, fscale, alpha, s2, false);
-            dct_inverse_inplace(X, sm.U0, sm.tw1, sm.tw2, cl);
-            for (int e = threadIdx.x; e < tot; e += DCT_T)
-                sm.U1[e] = cadd(sm.U1[e], sm.U0[e]);
-            __syncthreads();
-            if (!conv) set_status(a.status, q, TOD_ERR_NOT_CONVERGED);
-        }
-        // store x (time layout -> samples)
+        dct_inverse(X, cur, oth, sm.tw1, sm.tw2, cl);      // cur = x0 (time layout)
+        // x0 -> x_out
         {
             const int tot = X.m1 * X.ncolmax;
-            float *xq = a.x_out + o;
             for (int e = threadIdx.x; e < tot; e += DCT_T) {
                 int t0, t1;
                 bool valid;
                 elem_samples(X, e, t0, t1, valid);
                 if (!valid) continue;
-                const float2 v = sm.U1[e];
+                const float2 v = cur[e];
                 xq[t0] = v.x;
                 xq[t1] = v.y;
             }
         }
+
+        // flagged samples owned by this CTA, in sample order (deterministic),
+        // and the gaps (runs of flagged samples) of the detscan
+        const int64_t wb0 = o >> 5, wb1 = (o + n - 1) >> 5;
+        const int nw = static_cast<int>(wb1 - wb0 + 1);
+        const int per = (nw + DCT_T - 1) / DCT_T;
+        // bits of word wi restricted to this detscan
+        auto word_bits = [&](int wi) -> uint32_t {
+            if (wi < 0 || wi >= nw) return 0u;
+            uint32_t bits = fl[wb0 + wi];
+            const int64_t base = ((wb0 + wi) << 5) - o;             // sample of bit 0
+            if (base < 0) bits &= ~0u << static_cast<int>(-base);
+            if (base + 32 > n) bits &= (n - base >= 32) ? ~0u : ((1u << static_cast<int>(n - base)) - 1u);
+            return bits;
+        };
+        int mycnt = 0, mygaps = 0, myends = 0;
+        for (int i = 0; i < per; ++i) {
+            const int wi = threadIdx.x * per + i;
+            if (wi >= nw) break;
+            const uint32_t bits = word_bits(wi);
+            const uint32_t prev = word_bits(wi - 1) >> 31;
+            const uint32_t next = word_bits(wi + 1) & 1u;
+            mygaps += __popc(bits & ~((bits << 1) | prev));
+            myends += __popc(bits & ~((bits >> 1) | (next << 31)));
+            uint32_t bb = bits;
+            while (bb) {
+                const int b = __popc((bb & (0u - bb)) - 1u);   // index of the lowest set bit
+                bb &= bb - 1;
+                int ow, loc;
+                sample_loc(X, static_cast<int>(((wb0 + wi) << 5) + b - o), ow, loc);
+                if (ow == c) ++mycnt;
+            }
+        }
+        s_scan[threadIdx.x] = mycnt;
+        s_gscan[threadIdx.x] = mygaps;
+        s_escan[threadIdx.x] = myends;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int acc = 0, gacc = 0, eacc = 0;
+            for (int i = 0; i < DCT_T; ++i) {
+                const int v = s_scan[i]; s_scan[i] = acc; acc += v;
+                const int g2 = s_gscan[i]; s_gscan[i] = gacc; gacc += g2;
+                const int e2 = s_escan[i]; s_escan[i] = eacc; eacc += e2;
+            }
+            s_kc = acc;
+            s_ngap = gacc;
+        }
+        __syncthreads();
+        const int kc = s_kc, ngap = s_ngap;
+        {
+            int pos = s_scan[threadIdx.x], gpos = s_gscan[threadIdx.x], epos = s_escan[threadIdx.x];
+            for (int i = 0; i < per; ++i) {
+                const int wi = threadIdx.x * per + i;
+                if (wi >= nw) break;
+                const uint32_t bits = word_bits(wi);
+                const uint32_t prev = word_bits(wi - 1) >> 31;
+                const uint32_t next = word_bits(wi + 1) & 1u;
+                uint32_t st = bits & ~((bits << 1) | prev);
+                uint32_t en = bits & ~((bits >> 1) | (next << 31));
+                const int64_t base = ((wb0 + wi) << 5) - o;
+                while (st) {
+                    const int b = __popc((st & (0u - st)) - 1u);
+                    st &= st - 1;
+                    if (gpos < GAP_CAP) g_beg[gpos] = static_cast<int>(base + b);
+                    ++gpos;
+                }
+                while (en) {
+                    const int b = __popc((en & (0u - en)) - 1u);
+                    en &= en - 1;
+                    if (epos < GAP_CAP) g_end[epos] = static_cast<int>(base + b + 1);
+                    ++epos;
+                }
+                uint32_t bb = bits;
+                while (bb) {
+                    const int b = __popc((bb & (0u - bb)) - 1u);
+                    bb &= bb - 1;
+                    int ow, loc;
+                    const int tl = static_cast<int>(base + b);
+                    sample_loc(X, tl, ow, loc);
+                    if (ow == c) {
+                        if (pos < CG_KCAP) { c_loc[pos] = loc; c_t[pos] = tl; }
+                        ++pos;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // a gap that starts in one thread's words and ends in another's is
+        // matched by index: starts and ends alternate in sample order
+        const bool prec = a.xtab != nullptr && ngap <= GAP_CAP;
+        if (prec && threadIdx.x == 0) {
+            // split gaps into blocks of at most lmax samples; block b goes to
+            // CTA b mod C; own blocks get consecutive map offsets
+            const int lmax = min(TOEP_LMAX, a.lvalid[det]);
+            int nb = 0, own = 0, ovf = 0;
+            for (int g2 = 0; g2 < ngap; ++g2) {
+                for (int b0 = g_beg[g2]; b0 < g_end[g2]; b0 += lmax) {
+                    const int len = min(lmax, g_end[g2] - b0);
+                    if ((nb % C) == c) {
+                        if (own + len <= GMAP_CAP && s_nown < GAP_CAP) {
+                            o_beg[s_nown] = b0; o_len[s_nown] = len; o_off[s_nown] = own; ++s_nown;
+                            own += len;
+                        } else {
+                            ovf = 1;
+                        }
+                    }
+                    ++nb;
+                }
+            }
+            s_ovf = ovf;
+        }
+        if (!prec && threadIdx.x == 0) s_ovf = 1;
+        __syncthreads();
+        const double2 kt = cluster_sum2(make_double2(threadIdx.x == 0 ? static_cast<double>(kc) : 0.0,
+                                                     threadIdx.x == 0 ? ((kc > CG_KCAP ? 1.0 : 0.0) +
+                                                                         (s_ovf ? 1e6 : 0.0)) : 0.0),
+                                        s_red, s_part, parity, cl);
+        const bool use_prec = kt.y < 1e6 - 1.0 ? true : false;
+        const bool cap_ovf = (kt.y - (use_prec ? 0.0 : 1e6)) > 0.5;
+        int it = 0;
+        bool conv = true;
+        if (kt.x > 0.0 && cap_ovf) {
+            conv = false;      // too many flagged samples for the CG buffers: left as x0
+            set_status(a.status, q, TOD_ERR_NOT_CONVERGED);
+        } else if (kt.x > 0.0) {
+            // map of own preconditioner blocks: element -> (owner, index); the
+            // owners' sample lists are complete (cluster barrier above)
+            if (use_prec) {
+                for (int bi = 0; bi < s_nown; ++bi) {
+                    const int b0 = o_beg[bi], len = o_len[bi], off = o_off[bi];
+                    for (int u = threadIdx.x; u < len; u += DCT_T) {
+                        const int tl = b0 + u;
+                        int ow, loc;
+                        sample_loc(X, tl, ow, loc);
+                        const int *rt = cl.map_shared_rank(c_t, ow);
+                        int lo = 0, hi = *cl.map_shared_rank(&s_kc, ow);
+                        hi = min(hi, CG_KCAP);
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (rt[mid] < tl) lo = mid + 1; else hi = mid;
+                        }
+                        g_map[off + u] = (ow << 20) | lo;
+                    }
+                }
+                __syncthreads();
+            }
+            float *curf = reinterpret_cast<float *>(cur);
+            const float *xt_det = a.xtab ? a.xtab + static_cast<int64_t>(det) * (TOEP_LMAX * (TOEP_LMAX + 1) / 2)
+                                         : nullptr;
+            // z = M^{-1} r: Gohberg-Semencul per own block, scattered to owners
+            auto precond = [&]() {
+                if (!use_prec) {
+                    for (int i = threadIdx.x; i < kc; i += DCT_T) c_z[i] = c_r[i];
+                    __syncthreads();
+                    return;
+                }
+                cl.sync();     // every CTA's residual is complete before the gathers
+                for (int bi = 0; bi < s_nown; ++bi) {
+                    const int len = o_len[bi], off = o_off[bi];
+                    const float *xv = xt_det + static_cast<int64_t>(len) * (len - 1) / 2;
+                    for (int u = threadIdx.x; u < len; u += DCT_T) {
+                        const int gm = g_map[off + u];
+                        gb_r[u] = *cl.map_shared_rank(c_r + (gm & 0xFFFFF), gm >> 20);
+                        gb_x[u] = xv[u];
+                    }
+                    __syncthreads();
+                    // u1 = L(x)^T r, u2 = L(w)^T r, w_0 = 0, w_j = x_{L-j}
+                    for (int i = threadIdx.x; i < len; i += DCT_T) {
+                        float s1 = 0.f, s2v = 0.f;
+                        for (int j = i; j < len; ++j) {
+                            const float rj = gb_r[j];
+                            s1 = fmaf(gb_x[j - i], rj, s1);
+                            if (j > i) s2v = fmaf(gb_x[len - (j - i)], rj, s2v);
+                        }
+                        gb_u1[i] = s1;
+                        gb_u2[i] = s2v;
+                    }
+                    __syncthreads();
+                    const float inv_x0 = 1.0f / gb_x[0];
+                    for (int i = threadIdx.x; i < len; i += DCT_T) {
+                        float z1 = 0.f, z2 = 0.f;
+                        for (int j = 0; j <= i; ++j) {
+                            z1 = fmaf(gb_x[i - j], gb_u1[j], z1);
+                            if (j < i) z2 = fmaf(gb_x[len - (i - j)], gb_u2[j], z2);
+                        }
+                        const int gm = g_map[off + i];
+                        *cl.map_shared_rank(c_z + (gm & 0xFFFFF), gm >> 20) = (z1 - z2) * inv_x0;
+                    }
+                    __syncthreads();
+                }
+                cl.sync();     // every scatter into every CTA's c_z is done
+            };
+            // rhs = E^T x0 ; y = 0 ; r = rhs ; z = M^{-1} r ; p = z
+            double rr_loc = 0.0;
+            for (int i = threadIdx.x; i < kc; i += DCT_T) {
+                const float v = curf[c_loc[i]];
+                c_y[i] = 0.f; c_r[i] = v;
+                rr_loc += static_cast<double>(v) * v;
+            }
+            __syncthreads();
+            precond();
+            double rz_loc = 0.0;
+            for (int i = threadIdx.x; i < kc; i += DCT_T) {
+                c_p[i] = c_z[i];
+                rz_loc += static_cast<double>(c_r[i]) * c_z[i];
+            }
+            const double2 rr2 = cluster_sum2(make_double2(rr_loc, rz_loc), s_red, s_part, parity, cl);
+            double rz = rr2.y;
+            const double stop = static_cast<double>(a.tol) * a.tol * rr2.x;
+            conv = rr2.x == 0.0;
+            const int tot = X.m1 * X.ncolmax;
+            while (!conv && it < a.maxit) {
+                // cur <- C^T diag(gamma) C E p
+                for (int e = threadIdx.x; e < tot; e += DCT_T) cur[e] = make_float2(0.f, 0.f);
+                __syncthreads();
+                curf = reinterpret_cast<float *>(cur);
+                for (int i = threadIdx.x; i < kc; i += DCT_T) curf[c_loc[i]] = c_p[i];
+                __syncthreads();
+                dct_forward(X, cur, oth, sm.tw1, sm.tw2, cl);
+                apply_filter(X, cur, fscale, alpha, s2, 1, wt);
+                dct_inverse(X, cur, oth, sm.tw1, sm.tw2, cl);
+                curf = reinterpret_cast<float *>(cur);
+                double pq_loc = 0.0;
+                for (int i = threadIdx.x; i < kc; i += DCT_T) {
+                    const float v = curf[c_loc[i]];
+                    c_q[i] = v;
+                    pq_loc += static_cast<double>(c_p[i]) * v;
+                }
+                const double pq = cluster_sum2(make_double2(pq_loc, 0.0), s_red, s_part, parity, cl).x;
+                const float alp = static_cast<float>(rz / pq);
+                for (int i = threadIdx.x; i < kc; i += DCT_T) {
+                    c_y[i] = fmaf(alp, c_p[i], c_y[i]);
+                    c_r[i] = fmaf(-alp, c_q[i], c_r[i]);
+                }
+                __syncthreads();
+                ++it;
+                precond();
+                double rn_loc = 0.0, rzn_loc = 0.0;
+                for (int i = threadIdx.x; i < kc; i += DCT_T) {
+                    rn_loc += static_cast<double>(c_r[i]) * c_r[i];
+                    rzn_loc += static_cast<double>(c_r[i]) * c_z[i];
+                }
+                const double2 rn2 = cluster_sum2(make_double2(rn_loc, rzn_loc), s_red, s_part, parity, cl);
+                if (rn2.x <= stop) { conv = true; break; }
+                const float beta = static_cast<float>(rn2.y / rz);
+                for (int i = threadIdx.x; i < kc; i += DCT_T) c_p[i] = fmaf(beta, c_p[i], c_z[i]);
+                __syncthreads();
+                rz = rn2.y;
+            }
+            // x = x0 + B^{-1} E y
+            for (int e = threadIdx.x; e < tot; e += DCT_T) cur[e] = make_float2(0.f, 0.f);
+            __syncthreads();
+            curf = reinterpret_cast<float *>(cur);
+            for (int i = threadIdx.x; i < kc; i += DCT_T) curf[c_loc[i]] = c_y[i];
+            __syncthreads();
+            dct_forward(X, cur, oth, sm.tw1, sm.tw2, cl);
+            apply_filter(X, cur, fscale, alpha, s2, 0, wt);
+            dct_inverse(X, cur, oth, sm.tw1, sm.tw2, cl);
+            for (int e = threadIdx.x; e < tot; e += DCT_T) {
+                int t0, t1;
+                bool valid;
+                elem_samples(X, e, t0, t1, valid);
+                if (!valid) continue;
+                const float2 v = cur[e];
+                xq[t0] += v.x;
+                xq[t1] += v.y;
+            }
+            if (!conv) set_status(a.status, q, TOD_ERR_NOT_CONVERGED);
+        }
         if (a.iters && c == 0 && threadIdx.x == 0) a.iters[q] = it;
-        // U0/U1 of this CTA may still be read remotely by the last transpose of
-        // a sibling: the next detscan starts with load_plan + local writes only
-        // after this barrier.
+        // the buffers of this CTA may still be read remotely by a sibling's
+        // last transpose: start the next detscan only after this barrier
         cl.sync();
     }
 }
@@ -817,8 +1077,9 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
 // ---------------------------------------------------------------------------
 static size_t smem_bytes(const Plan &p, bool ncorr)
 {
-    size_t b = sizeof(float2) * (2 * static_cast<size_t>(p.sz) + p.m1max + p.m2max);
-    if (ncorr) b += static_cast<size_t>(CG_KCAP) * (sizeof(int) + 4 * sizeof(float));
+    size_t b = sizeof(float2) * (2 * static_cast<size_t>(p.sz));
+    if (ncorr) b += static_cast<size_t>(CG_KCAP) * (2 * sizeof(int) + 5 * sizeof(float)) +
+                    sizeof(int) * GMAP_CAP + sizeof(float) * 4 * TOEP_LMAX;
     return b;
 }
 
@@ -916,6 +1177,13 @@ cudaError_t launch_ncorr(const Plan &p, const float *d, const float *s, const do
     a.q_plan = p.q_plan; a.tw = p.tw; a.work = p.work; a.work_begin = work_begin;
     a.work_count = work_count; a.ndet = p.ndet; a.fsamp = p.fsamp; a.rng = rng; a.mode = mode;
     a.tol = tol; a.maxit = maxit; a.x_out = x; a.iters = iters; a.status = p.status; a.sz = p.sz;
+    a.wscratch = p.wscratch;
+    a.xtab = p.use_prec ? p.xtab : nullptr;
+    a.lvalid = p.lvalid;
+    if (p.use_prec) {
+        cudaError_t e = launch_toeplitz_prep(p, psd, st);
+        if (e != cudaSuccess) return e;
+    }
     a.m1max = p.m1max; a.m2max = p.m2max;
     if (p.schedule == TOD_SCHED_PER_SCAN) {
         for (int w = 0; w < work_count; ++w) {
