@@ -613,3 +613,64 @@ def gibbs_tod_step(ing: dict, band_cfg, npix: int, map_tqu: np.ndarray, psd: np.
     m, had, valid = solve_maps(A, b, hits, rcond_min)
     return dict(gain=gain, mu=mu, sigma=sig, cg_iters=iters, ncorr=ncorr,
                 A=A, b=b, hits=hits, map=m, rcond=had, valid=valid)
+
+
+# ============================================================================
+# A8. TOD chi^2 of the correlated-noise-marginalised likelihood and its
+# gradients (the adjoint of the projection is the binning)
+# ============================================================================
+
+def chi2_detscan(d, s, gain, mask, sigma0, fknee, alpha, fsamp) -> dict:
+    """L = 1/2 sum_{k>=1} [ rhat_k^2 / P_k + ln P_k ],  rhat = C(M (d - g s)),
+    the negative log-likelihood of one detscan under the noise model
+    P_k = sigma0^2 (1 + (f_k/fknee)^alpha) with n_corr marginalised (the
+    gain conditional's likelihood, paper Eq. `gibbsstart` first line, as a
+    function of the map, the gain and xi_n).  Returns L and the gradients
+    dL/dg, dL/d(sigma0, fknee, alpha), and the per-sample vector
+    v = M C^T (rhat / P) with dL/ds = -g v (so dL/dm = -g P^T v)."""
+    n = len(d)
+    M = np.asarray(mask, np.float64)
+    f = dct_freqs(n, fsamp)
+    r = M * (np.asarray(d, np.float64) - gain * np.asarray(s, np.float64))
+    rh = dct(r)
+    k = slice(1, n)
+    x = (f[k] / fknee) ** alpha
+    P = sigma0 ** 2 * (1.0 + x)
+    L = 0.5 * float(np.sum(rh[k] ** 2 / P + np.log(P)))
+    w = np.zeros(n)
+    w[k] = rh[k] / P
+    v = M * idct(w)
+    dLdg = -float(np.dot(M * np.asarray(s, np.float64), v))
+    c = 0.5 * (1.0 / P - rh[k] ** 2 / P ** 2)
+    dP_ds = 2.0 * P / sigma0
+    dP_dfk = -sigma0 ** 2 * alpha * x / fknee
+    dP_da = sigma0 ** 2 * x * np.log(f[k] / fknee)
+    return dict(L=L, dg=dLdg, dpsd=np.array([np.sum(c * dP_ds), np.sum(c * dP_dfk), np.sum(c * dP_da)]),
+                v=v)
+
+
+def chi2_band(map_tqu, pix, psi, d, gains, mask, psd, offsets, ndet, fsamp) -> dict:
+    """Sum over detscans of chi2_detscan, with s = P m (unit gain) and the map
+    gradient dL/dm = -P^T(g v) accumulated by binning (the adjoint of
+    ``project``).  Returns L, dm (3, npix), dg (ndetscan), dpsd (ndet, 3)."""
+    npix = map_tqu.shape[1]
+    s = project(map_tqu, pix, psi)
+    L = 0.0
+    dg = np.zeros(len(offsets) - 1)
+    dpsd = np.zeros((ndet, 3))
+    gv = np.zeros(len(d))
+    for q in range(len(offsets) - 1):
+        a, b = int(offsets[q]), int(offsets[q + 1])
+        det = q % ndet
+        res = chi2_detscan(d[a:b], s[a:b], gains[q], mask[a:b], *psd[det], fsamp)
+        L += res["L"]
+        dg[q] = res["dg"]
+        dpsd[det] += res["dpsd"]
+        gv[a:b] = gains[q] * res["v"]
+    c, sn = psi_trig_table()
+    pix = np.asarray(pix, np.int64)
+    b_ = np.asarray(psi, np.int64)
+    dm = -np.stack([np.bincount(pix, weights=gv, minlength=npix),
+                    np.bincount(pix, weights=gv * c[b_], minlength=npix),
+                    np.bincount(pix, weights=gv * sn[b_], minlength=npix)])
+    return dict(L=L, dm=dm, dg=dg, dpsd=dpsd)
