@@ -210,6 +210,37 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         elapsed = float(t.item())
 
+    # the same step captured in a CUDA graph (iteration read on the device)
+    graph_ms = None
+    try:
+        step.capture(map_in, args.seed, 0, tg.MODE_DRAW)
+        for k in range(2):
+            step.replay(30_000 + k)
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for k in range(args.steps):
+            step.replay(40_000 + k)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        graph_ms = g0.elapsed_time(g1) / args.steps
+    except Exception as ex:          # report, do not hide
+        graph_ms = "capture failed: %s" % ex
+    # the plain per-scan path: one cluster launch per detscan per stage
+    plain_ms = None
+    if not args.no_plain:
+        plan.set_schedule(plan.SCHED_PER_SCAN)
+        torch.cuda.synchronize()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        step.run(map_in, tg.Rng(args.seed, 0, 50_000), tg.MODE_DRAW)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = p0.elapsed_time(p1)
+        plan.set_schedule(plan.SCHED_PERSISTENT)
+
     # end to end through the public API with host buffers
     d_host = torch.from_numpy(ing["tod"]).pin_memory()
     map_host = torch.empty((3, npix), dtype=torch.float64).pin_memory()
@@ -270,6 +301,11 @@ def run_ours(args):
         "gpu_launches": GibbsTODStep.LAUNCHES_PER_STEP * args.steps,
         "stage_ms": stage_ms, "stage_gbs": stage_gbs,
         "cg_iters": {"mean": float(iters.mean()), "max": int(iters.max()), "min": int(iters.min())},
+        "graph": ({"ms_per_step": graph_ms, "value": ws * N / (graph_ms / 1e3)}
+                  if isinstance(graph_ms, float) else graph_ms),
+        "plain_per_scan": ({"ms_per_step": plain_ms, "value": N / (plain_ms / 1e3),
+                            "speedup_batched": plain_ms / (1e3 * elapsed / args.steps)}
+                           if plain_ms else None),
         "device_status_errors": int(np.count_nonzero(st)),
         "roofline": roof, "clocks": clocks, "setup_s": setup_s,
     }
@@ -368,6 +404,7 @@ def main():
     ap.add_argument("--cpu-detscans", type=int, default=8)
     ap.add_argument("--ref-detscans-per-step", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the per-scan comparison step")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

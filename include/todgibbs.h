@@ -245,6 +245,21 @@ tod_status tod_solve_maps(tod_plan *p, const double *A, const double *b,
                           void *map_f32_out, double *rcond_out, uint8_t *valid_out,
                           cudaStream_t stream);
 
+/* A8 -- TOD chi^2 with the correlated noise marginalised, and its
+ * gradients (the likelihood of the gain conditional, Eq. `gibbsstart`
+ * first line, as a function of map, gains and noise parameters).  Per
+ * detscan, with rhat = C(M(d - g s)) and P_k the noise PSD:
+ *   chi2_out[q]  = 1/2 sum_{k>=1} [ rhat_k^2 / P_k + ln P_k ],
+ *   dgain_out[q] = dL/dg_q = -<M s, v>,
+ *   dpsd_out[q][3] = dL/d(sigma0, f_knee, alpha) of this detscan's terms,
+ *   v_out[t] = M_t (C^T(rhat/P))_t (NULL to skip), so dL/ds = -g v and the
+ *   map gradient is -P^T(g v): tod_bin of d = v, n_corr = 0 with every
+ *   sigma0 = 1 returns it in b_out (negated).
+ * s is the unit-gain projection.  Transforms in FP32, sums in FP64. */
+tod_status tod_chi2(tod_plan *p, const float *d, const float *s, const double *gain,
+                    const uint32_t *flags, const double *psd, double *chi2_out,
+                    double *dgain_out, double *dpsd_out, float *v_out, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

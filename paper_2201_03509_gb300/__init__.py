@@ -65,7 +65,7 @@ _lib = None
 
 SYMBOLS = ["tod_status_string", "tod_fft_length", "tod_huff_encode", "tod_huff_free",
            "tod_plan_create", "tod_plan_destroy", "tod_plan_info", "tod_plan_status",
-           "tod_plan_set_schedule", "tod_decode", "tod_project", "tod_sample_gain", "tod_sample_ncorr", "tod_bin",
+           "tod_plan_set_schedule", "tod_chi2", "tod_decode", "tod_project", "tod_sample_gain", "tod_sample_ncorr", "tod_bin",
            "tod_solve_maps"]
 
 
@@ -101,6 +101,7 @@ def lib():
         L.tod_sample_ncorr.argtypes = [_P, _P, _P, _P, _P, _P, Rng, _i32, _f64, _i32, _P, _P, _P]
         L.tod_bin.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
         L.tod_solve_maps.argtypes = [_P, _P, _P, _P, _f64, _P, _P, _P, _P, _P]
+        L.tod_chi2.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
         for name in SYMBOLS:
             if name not in ("tod_status_string", "tod_fft_length", "tod_huff_free"):
                 getattr(L, name).restype = _i32
@@ -285,6 +286,11 @@ class Plan:
         _check(lib().tod_bin(self._h, _ptr(psi), _ptr(d), _ptr(ncorr), _ptr(gain), _ptr(flags),
                              _ptr(psd), _ptr(A_out), _ptr(b_out), _ptr(hits_out), _stream(stream)),
                "tod_bin")
+
+    def chi2(self, d, s, gain, flags, psd, chi2_out, dgain_out, dpsd_out, v_out=None, stream=None):
+        _check(lib().tod_chi2(self._h, _ptr(d), _ptr(s), _ptr(gain), _ptr(flags), _ptr(psd),
+                              _ptr(chi2_out), _ptr(dgain_out), _ptr(dpsd_out), _ptr(v_out),
+                              _stream(stream)), "tod_chi2")
 
     def solve_maps(self, A, b, hits, rcond_min, map_out, map_f32_out=None, rcond_out=None,
                    valid_out=None, stream=None):

@@ -565,6 +565,7 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
 
     if ((e = dev_upload(*p, p->off, p->h_off.data(), p->h_off.size()))) return fail(e);
     if ((e = dev_upload(*p, p->status, static_cast<int32_t *>(nullptr), p->nq))) return fail(e);
+    if ((e = setup_decode_kernel())) return fail(e);
     if ((e = build_huff(*p, p->hpix, band->pix))) return fail(e);
     if ((e = build_huff(*p, p->hpsi, band->psi))) return fail(e);
 
@@ -622,7 +623,10 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
                 m2max = std::max(m2max, dp.m2);
             }
             if (!ok) continue;
-            const size_t smem = sizeof(float2) * (2 * static_cast<size_t>(sz)) +
+            // twiddle block: 3 (m1 + m2) + m/64 + 65 complex values
+            int twmax = 0;
+            for (auto &dp : plans) twmax = std::max(twmax, 3 * (dp.m1 + dp.m2) + dp.m / 64 + 65);
+            const size_t smem = sizeof(float2) * (2 * static_cast<size_t>(sz) + twmax) +
                                 static_cast<size_t>(CG_KCAP) * 28 + sizeof(int) * GMAP_CAP +
                                 sizeof(float) * 4 * TOEP_LMAX + 12288;
             if (smem > 227 * 1024) continue;
@@ -631,26 +635,30 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
         }
         if (!chosenC) { free_plan(p); return TOD_ERR_ARG; }
         p->C = chosenC;
-        // twiddle tables per plan: W_{m1}^i, W_{m2}^i, and the four-step
-        // factors W_m^{64 i} (i <= m/64) and W_m^i (i < 64), from FP64
+        // twiddle block per length, FP64-generated: W_{m1}^i (m1), W_{m2}^i (m2),
+        // real-split factors W_{4n}^{k1}, W_{4n}^{m1 k2}, W_{4n}^{5 k1},
+        // W_{4n}^{5 m1 k2} (m1, m2, m1, m2), four-step factors W_m^{64 i}
+        // (m/64 + 1) and W_m^i (64); staged in shared memory per detscan
         std::vector<float2> tw;
-        const auto push_w = [&](int L, int64_t i) {
-            const double ang = -2.0 * kPi * static_cast<double>(i) / L;
+        const auto push_w = [&](int64_t L, int64_t i) {
+            const double ang = -2.0 * kPi * static_cast<double>(i % L) / static_cast<double>(L);
             tw.push_back(make_float2(static_cast<float>(std::cos(ang)), static_cast<float>(std::sin(ang))));
         };
+        int twsz = 0;
         for (auto &dp : plans) {
-            dp.tw1 = static_cast<int32_t>(tw.size());
+            dp.twb = static_cast<int32_t>(tw.size());
+            const int64_t n4 = 4 * static_cast<int64_t>(dp.n);
             for (int i = 0; i < dp.m1; ++i) push_w(dp.m1, i);
-            dp.tw2 = static_cast<int32_t>(tw.size());
             for (int i = 0; i < dp.m2; ++i) push_w(dp.m2, i);
-            dp.tw4 = static_cast<int32_t>(tw.size());
+            for (int i = 0; i < dp.m1; ++i) push_w(n4, i);
+            for (int i = 0; i < dp.m2; ++i) push_w(n4, static_cast<int64_t>(dp.m1) * i);
+            for (int i = 0; i < dp.m1; ++i) push_w(n4, 5 * static_cast<int64_t>(i));
+            for (int i = 0; i < dp.m2; ++i) push_w(n4, 5 * static_cast<int64_t>(dp.m1) * i);
             for (int i = 0; i <= dp.m / 64; ++i) push_w(dp.m, 64 * static_cast<int64_t>(i));
             for (int i = 0; i < 64; ++i) push_w(dp.m, i);
-            dp.tws = static_cast<int32_t>(tw.size());
-            for (int i = 0; i <= (4 * dp.n) / 64; ++i) push_w(4 * dp.n, 64 * static_cast<int64_t>(i));
-            for (int i = 0; i < 64; ++i) push_w(4 * dp.n, i);
+            twsz = std::max(twsz, static_cast<int>(tw.size()) - dp.twb);
         }
-        std::vector<int32_t> qp(p->nq);
+        p->twsz = twsz;        std::vector<int32_t> qp(p->nq);
         for (int q = 0; q < p->nq; ++q)
             qp[q] = static_cast<int32_t>(std::lower_bound(uniq.begin(), uniq.end(), lens[q]) - uniq.begin());
         p->nplans = static_cast<int32_t>(plans.size());
@@ -701,7 +709,8 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
                 if (bad) continue;
                 std::sort(key.begin(), key.end());
                 for (int64_t i = 0; i < n; ++i) {
-                    lp[o + i] = static_cast<uint32_t>(key[i] & 0xFFFFFFFFu);
+                    // sample -> its position in the pixel-sorted order of the detscan
+                    lp[o + static_cast<int64_t>(key[i] & 0xFFFFFFFFu)] = static_cast<uint32_t>(i);
                     const int32_t px = static_cast<int32_t>(key[i] >> 32);
                     if (i == 0 || px != static_cast<int32_t>(key[i - 1] >> 32)) {
                         rpix[q].push_back(px);
@@ -845,6 +854,17 @@ tod_status tod_bin(tod_plan *pl, const uint16_t *psi, const float *d, const floa
     Plan *p = reinterpret_cast<Plan *>(pl);
     DeviceGuard dg(p->device);
     return to_status(launch_bin(*p, psi, d, ncorr, gain, flags, psd, A_out, b_out, hits_out, stream));
+}
+
+tod_status tod_chi2(tod_plan *pl, const float *d, const float *s, const double *gain,
+                    const uint32_t *flags, const double *psd, double *chi2_out, double *dgain_out,
+                    double *dpsd_out, float *v_out, cudaStream_t stream)
+{
+    if (!pl || !d || !s || !gain || !flags || !psd || !chi2_out || !dgain_out || !dpsd_out)
+        return TOD_ERR_ARG;
+    Plan *p = reinterpret_cast<Plan *>(pl);
+    DeviceGuard dg(p->device);
+    return to_status(launch_chi2(*p, d, s, gain, flags, psd, chi2_out, dgain_out, dpsd_out, v_out, stream));
 }
 
 tod_status tod_solve_maps(tod_plan *pl, const double *A, const double *b, const int32_t *hits,

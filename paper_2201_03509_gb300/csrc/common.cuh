@@ -23,6 +23,15 @@ inline FastDiv make_fastdiv(uint32_t d) {
     f.mul = static_cast<uint32_t>((((1ull << 32) * ((1ull << s) - d)) / d) + 1);
     return f;
 }
+__device__ __forceinline__ FastDiv make_fastdiv_dev(uint32_t d) {
+    FastDiv f;
+    f.d = d;
+    uint32_t s = 0;
+    while ((1ull << s) < d) ++s;
+    f.shift = s;
+    f.mul = static_cast<uint32_t>((((1ull << 32) * ((1ull << s) - d)) / d) + 1);
+    return f;
+}
 __device__ __forceinline__ int fdiv(int x, const FastDiv &f) {
     const uint32_t ux = static_cast<uint32_t>(x);
     return static_cast<int>((__umulhi(ux, f.mul) + ux) >> f.shift);

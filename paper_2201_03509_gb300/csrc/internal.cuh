@@ -8,17 +8,18 @@
 
 namespace tg {
 
-constexpr int DEC_LUTB = 10;          // first-level decode table: 2^10 entries
+constexpr int DEC_LUTB = 12;          // first-level decode table: 2^12 entries
+constexpr int DEC_CANON_SMEM = 4096;  // symbols of one code staged in shared memory
 constexpr int DEC_T = 256;            // decode threads per CTA (one checkpoint block each)
 constexpr int DEC_ROUND = 16;         // symbols staged per thread before a coalesced write
 constexpr int ELEM_TILE = 4096;       // samples per tile of the element-wise kernels
 constexpr int DCT_T = 512;            // threads per CTA of the cluster transform kernels
 constexpr int DCT_SZ_MAX = 11776;     // complex values per CTA buffer (two buffers + CG fit in 227 KB)
 constexpr int DCT_MAXR = 20;          // maximum number of radix stages per sub-transform
-constexpr int CG_KCAP = 1024;         // flagged samples per CTA held by the CG
+constexpr int CG_KCAP = 768;          // flagged samples per CTA held by the CG
 constexpr int TOEP_LMAX = 512;        // longest gap block of the Toeplitz preconditioner
 constexpr int GAP_CAP = 256;          // gap blocks per detscan handled by the preconditioner
-constexpr int GMAP_CAP = 2048;        // gap-block elements mapped per CTA
+constexpr int GMAP_CAP = 1024;        // gap-block elements mapped per CTA
 
 // Compressed stream kind, device copy + decode tables.
 struct HuffDev {
@@ -54,8 +55,7 @@ struct DctPlan {
     int32_t n, m, m1, m2, ncolmax, npmax, P;
     int32_t nr1, nr2;
     int32_t tw1, tw2;                // offsets of the W_{m1}^i and W_{m2}^i tables
-    int32_t tw4;                     // offset of W_m^{64 i} (m/64+1 entries) then W_m^i (64)
-    int32_t tws;                     // offset of W_{4n}^{64 i} (4n/64+1 entries) then W_{4n}^i (64)
+    int32_t twb;                     // offset of this length's twiddle block (see k_dct.cu)
     FastDiv f_ncolmax, f_m2, f_npmax;
     DctStage s1[DCT_MAXR], s2[DCT_MAXR];
 };
@@ -77,6 +77,7 @@ struct Plan {
     // transforms
     int32_t C = 1;                   // CTAs per cluster
     int32_t sz = 0;                  // complex values per CTA buffer (max over plans)
+    int32_t twsz = 0;                // complex values of the largest twiddle block
     int32_t m1max = 0, m2max = 0;
     int32_t nplans = 0;
     DctPlan *plans = nullptr;        // device
@@ -96,7 +97,7 @@ struct Plan {
     size_t smem_bin = 0;
     size_t smem_gain = 0, smem_ncorr = 0;
     // binning
-    uint32_t *lp = nullptr;          // [N] per-detscan pixel-sorted local order
+    uint32_t *lp = nullptr;          // [N] position of each sample in its detscan's pixel-sorted order
     int64_t npairs = 0;
     int64_t *pair_off = nullptr;     // [nq+1] runs of each detscan
     int64_t *pair_start = nullptr;   // [npairs] first lp index (global) of the run
@@ -109,6 +110,7 @@ struct Plan {
 };
 
 // launchers (return cudaError_t of the launch)
+cudaError_t setup_decode_kernel();
 cudaError_t launch_decode(const Plan &p, const HuffDev &h, int32_t *pix_out, uint16_t *psi_out,
                           cudaStream_t st);
 cudaError_t launch_project(const Plan &p, const float4 *map, const int32_t *pix, const uint16_t *psi,
@@ -121,6 +123,9 @@ cudaError_t launch_ncorr(const Plan &p, const float *d, const float *s, const do
                          const uint32_t *flags, const double *psd, tod_rng rng, int mode,
                          float tol, int maxit, float *x, int32_t *iters, cudaStream_t st,
                          int work_begin, int work_count);
+cudaError_t launch_chi2(const Plan &p, const float *d, const float *s, const double *gain,
+                        const uint32_t *flags, const double *psd, double *chi2, double *dgain,
+                        double *dpsd, float *v, cudaStream_t st);
 cudaError_t setup_bin_kernel(Plan &p);
 cudaError_t launch_toeplitz_prep(const Plan &p, const double *psd, cudaStream_t st);
 cudaError_t launch_bin(const Plan &p, const uint16_t *psi, const float *d, const float *ncorr,

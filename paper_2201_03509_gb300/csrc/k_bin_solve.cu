@@ -33,7 +33,7 @@ struct BinArgs {
     const uint32_t *flags;
     const double *psd;
     const int64_t *off;
-    const uint32_t *lp;
+    const uint32_t *inv;          // sample -> position in the detscan's pixel-sorted order
     const int64_t *pair_off, *pair_start;
     const int32_t *pair_len, *pair_slot;
     const float2 *trig;
@@ -44,15 +44,32 @@ struct BinArgs {
     int32_t *status;
 };
 
+// sum of two double-words (two-sum on the heads, tails added)
+__device__ __forceinline__ Acc2 acc_merge(const Acc2 &a, const Acc2 &b) {
+    Acc2 r = a;
+    acc_add(r, b.s);
+    r.c = __fadd_rn(r.c, b.c);
+    return r;
+}
+__device__ __forceinline__ Acc2 acc_shfl_down(const Acc2 &a, int o) {
+    Acc2 r;
+    r.s = __shfl_down_sync(0xffffffffu, a.s, o);
+    r.c = __shfl_down_sync(0xffffffffu, a.c, o);
+    return r;
+}
+
 __global__ void __launch_bounds__(BIN_T, 1) k_bin(BinArgs a)
 {
     extern __shared__ __align__(16) unsigned char bin_raw[];
+    __shared__ FastDiv s_fchunk;
+    __shared__ int s_ra, s_rb;
     cg::cluster_group cl = cg::this_cluster();
     const int C = static_cast<int>(cl.num_blocks()), c = static_cast<int>(cl.block_rank());
     const int cid = blockIdx.x / C, ncl = gridDim.x / C;
     float *s_d = reinterpret_cast<float *>(bin_raw);
     float *s_x = s_d + a.chunk_cap;
     uint16_t *s_pf = reinterpret_cast<uint16_t *>(s_x + a.chunk_cap);   // psi | flag << 15
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     for (int w = cid; w < a.nq; w += ncl) {
         const int q = a.work[w];
@@ -64,59 +81,89 @@ __global__ void __launch_bounds__(BIN_T, 1) k_bin(BinArgs a)
             cl.sync();
             continue;
         }
+        const int64_t pr0 = a.pair_off[q], pr1 = a.pair_off[q + 1];
+        if (threadIdx.x == 0) {
+            s_fchunk = make_fastdiv_dev(static_cast<uint32_t>(chunk));
+            // runs whose first sorted position lies in this CTA's chunk
+            int64_t lo = pr0, hi = pr1;
+            while (lo < hi) { const int64_t mid = (lo + hi) >> 1; if (a.pair_start[mid] - o < static_cast<int64_t>(c) * chunk) lo = mid + 1; else hi = mid; }
+            s_ra = static_cast<int>(lo - pr0);
+            lo = pr0; hi = pr1;
+            while (lo < hi) { const int64_t mid = (lo + hi) >> 1; if (a.pair_start[mid] - o < static_cast<int64_t>(c + 1) * chunk) lo = mid + 1; else hi = mid; }
+            s_rb = static_cast<int>(lo - pr0);
+        }
+        __syncthreads();
+        const FastDiv fch = s_fchunk;
+        // stage: coalesced reads in time order, stores to the sorted position
         const int t0 = c * chunk, t1 = min(n, t0 + chunk);
         for (int t = t0 + threadIdx.x; t < t1; t += BIN_T) {
             const int64_t tg = o + t;
-            s_d[t - t0] = a.d[tg];
-            s_x[t - t0] = a.x[tg];
+            const int sp = static_cast<int>(a.inv[tg]);
+            const int ow = fdiv(sp, fch), ls = sp - ow * chunk;
             const uint32_t fb = (a.flags[tg >> 5] >> (tg & 31)) & 1u;
-            s_pf[t - t0] = static_cast<uint16_t>((a.psi[tg] & 0x0FFF) | (fb << 15));
+            *cl.map_shared_rank(s_d + ls, ow) = a.d[tg];
+            *cl.map_shared_rank(s_x + ls, ow) = a.x[tg];
+            *cl.map_shared_rank(s_pf + ls, ow) = static_cast<uint16_t>((a.psi[tg] & 0x0FFF) | (fb << 15));
         }
         cl.sync();
         const int det = q % a.ndet;
         const double sig0 = a.psd[3 * det];
         const double gq = a.gain[q];
         const double wA = gq * gq / (sig0 * sig0), wb = gq / (sig0 * sig0);
-        const int64_t pr0 = a.pair_off[q], pr1 = a.pair_off[q + 1];
-        for (int64_t pr = pr0 + c * BIN_T + threadIdx.x; pr < pr1; pr += static_cast<int64_t>(C) * BIN_T) {
-            const int64_t st = a.pair_start[pr];
+        for (int r = s_ra + warp; r < s_rb; r += BIN_T / 32) {
+            const int64_t pr = pr0 + r;
+            const int st = static_cast<int>(a.pair_start[pr] - o);
             const int len = a.pair_len[pr];
-            Acc2 ac = {0.f, 0.f}, as_ = {0.f, 0.f}, acc = {0.f, 0.f}, acs = {0.f, 0.f}, ass = {0.f, 0.f};
-            Acc2 bd = {0.f, 0.f}, bcd = {0.f, 0.f}, bsd = {0.f, 0.f};
-            Acc2 bx = {0.f, 0.f}, bcx = {0.f, 0.f}, bsx = {0.f, 0.f};
+            Acc2 acc[11];
+#pragma unroll
+            for (int i = 0; i < 11; ++i) acc[i] = Acc2{0.f, 0.f};
             int hits = 0;
-            for (int i = 0; i < len; ++i) {
-                const int t = static_cast<int>(a.lp[st + i]);
-                const int ow = t / chunk, lt = t - ow * chunk;
-                const uint16_t pf = *cl.map_shared_rank(s_pf + lt, ow);
+            for (int i = lane; i < len; i += 32) {
+                const int sp = st + i;
+                const int ow = fdiv(sp, fch), ls = sp - ow * chunk;
+                uint16_t pf;
+                float dv, xv;
+                if (ow == c) { pf = s_pf[ls]; dv = s_d[ls]; xv = s_x[ls]; }
+                else {
+                    pf = *cl.map_shared_rank(s_pf + ls, ow);
+                    dv = *cl.map_shared_rank(s_d + ls, ow);
+                    xv = *cl.map_shared_rank(s_x + ls, ow);
+                }
                 if (pf >> 15) continue;
-                const float dv = *cl.map_shared_rank(s_d + lt, ow);
-                const float xv = *cl.map_shared_rank(s_x + lt, ow);
                 const float2 cs = __ldg(a.trig + (pf & 0x0FFF));
                 ++hits;
-                acc_add(ac, cs.x);
-                acc_add(as_, cs.y);
-                acc_add_prod(acc, cs.x, cs.x);
-                acc_add_prod(acs, cs.x, cs.y);
-                acc_add_prod(ass, cs.y, cs.y);
-                acc_add(bd, dv);
-                acc_add_prod(bcd, cs.x, dv);
-                acc_add_prod(bsd, cs.y, dv);
-                acc_add(bx, xv);
-                acc_add_prod(bcx, cs.x, xv);
-                acc_add_prod(bsx, cs.y, xv);
+                acc_add(acc[0], cs.x);
+                acc_add(acc[1], cs.y);
+                acc_add_prod(acc[2], cs.x, cs.x);
+                acc_add_prod(acc[3], cs.x, cs.y);
+                acc_add_prod(acc[4], cs.y, cs.y);
+                acc_add(acc[5], dv);
+                acc_add_prod(acc[6], cs.x, dv);
+                acc_add_prod(acc[7], cs.y, dv);
+                acc_add(acc[8], xv);
+                acc_add_prod(acc[9], cs.x, xv);
+                acc_add_prod(acc[10], cs.y, xv);
             }
-            double *r = a.rec + static_cast<int64_t>(a.pair_slot[pr]) * 10;
-            r[0] = wA * hits;
-            r[1] = wA * acc_value(ac);
-            r[2] = wA * acc_value(as_);
-            r[3] = wA * acc_value(acc);
-            r[4] = wA * acc_value(acs);
-            r[5] = wA * acc_value(ass);
-            r[6] = wb * (acc_value(bd) - acc_value(bx));
-            r[7] = wb * (acc_value(bcd) - acc_value(bcx));
-            r[8] = wb * (acc_value(bsd) - acc_value(bsx));
-            r[9] = static_cast<double>(hits);
+            // warp tree in a fixed order (deterministic)
+#pragma unroll
+            for (int ofs = 16; ofs; ofs >>= 1) {
+#pragma unroll
+                for (int i = 0; i < 11; ++i) acc[i] = acc_merge(acc[i], acc_shfl_down(acc[i], ofs));
+                hits += __shfl_down_sync(0xffffffffu, hits, ofs);
+            }
+            if (lane == 0) {
+                double *rr = a.rec + static_cast<int64_t>(a.pair_slot[pr]) * 10;
+                rr[0] = wA * hits;
+                rr[1] = wA * acc_value(acc[0]);
+                rr[2] = wA * acc_value(acc[1]);
+                rr[3] = wA * acc_value(acc[2]);
+                rr[4] = wA * acc_value(acc[3]);
+                rr[5] = wA * acc_value(acc[4]);
+                rr[6] = wb * (acc_value(acc[5]) - acc_value(acc[8]));
+                rr[7] = wb * (acc_value(acc[6]) - acc_value(acc[9]));
+                rr[8] = wb * (acc_value(acc[7]) - acc_value(acc[10]));
+                rr[9] = static_cast<double>(hits);
+            }
         }
         cl.sync();      // staging buffers are reused by the next detscan
     }
@@ -224,7 +271,7 @@ cudaError_t launch_bin(const Plan &p, const uint16_t *psi, const float *d, const
     if (p.nq == 0) return cudaSuccess;
     BinArgs a;
     a.psi = psi; a.d = d; a.x = ncorr; a.gain = gain; a.flags = flags; a.psd = psd; a.off = p.off;
-    a.lp = p.lp; a.pair_off = p.pair_off; a.pair_start = p.pair_start; a.pair_len = p.pair_len;
+    a.inv = p.lp; a.pair_off = p.pair_off; a.pair_start = p.pair_start; a.pair_len = p.pair_len;
     a.pair_slot = p.pair_slot; a.trig = p.trig; a.work = p.work; a.nq = p.nq; a.ndet = p.ndet;
     a.chunk_cap = p.bin_cap; a.rec = p.rec; a.status = p.status;
     cudaLaunchConfig_t cfg = {};

@@ -137,7 +137,7 @@ __device__ __noinline__ void fft_pass(const float2 *__restrict__ src, float2 *__
         if (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                float2 t = __ldg(tw + r * k * tstep);
+                float2 t = tw[r * k * tstep];
                 if (INV) t.y = -t.y;
                 v[r] = cmul(v[r], t);
             }
@@ -178,8 +178,10 @@ struct Ctx {
     int ncol;    // valid local columns
     int p0, npl; // local row pairs
     FastDiv f_ncolmax, f_m2, f_npmax;
-    const float2 *tw4;   // W_m^{64 i} (m/64 + 1 entries) followed by W_m^i (64 entries)
-    const float2 *tws;   // W_{4n}^{64 i} (4n/64 + 1 entries) followed by W_{4n}^i (64 entries)
+    // twiddles staged in shared memory (see load_plan)
+    const float2 *tw1, *tw2;            // W_{m1}^i, W_{m2}^i
+    const float2 *sa1, *sb1, *sa5, *sb5;// W_{4n}^{k1}, W_{4n}^{m1 k2}, W_{4n}^{5 k1}, W_{4n}^{5 m1 k2}
+    const float2 *t4hi, *t4lo;          // W_m^{64 i}, W_m^i (i < 64)
     DctStage s1[DCT_MAXR], s2[DCT_MAXR];
 };
 
@@ -196,40 +198,32 @@ __device__ __forceinline__ int slot_row(const Ctx &X, int slot) {
 __device__ __forceinline__ int vpos_t(int i, int n, int m) { return i < m ? 2 * i : 2 * n - 1 - 2 * i; }
 
 // W_m^{r}, 0 <= r < m, from the two-level table (one complex multiply)
-__device__ __forceinline__ float2 tw4_lookup(const float2 *__restrict__ t4, int m, int r) {
-    const float2 hi = __ldg(t4 + (r >> 6));
-    const float2 lo = __ldg(t4 + (m >> 6) + 1 + (r & 63));
-    return cmul(hi, lo);
-}
-
-// W_{4n}^{r} = e^{-i pi r/(2n)}, 0 <= r < 4n, from the two-level table
-__device__ __forceinline__ float2 tws_lookup(const float2 *__restrict__ ts, int n4, int r) {
-    const float2 hi = __ldg(ts + (r >> 6));
-    const float2 lo = __ldg(ts + (n4 >> 6) + 1 + (r & 63));
-    return cmul(hi, lo);
+__device__ __forceinline__ float2 tw4_lookup(const Ctx &X, int r) {
+    return cmul(X.t4hi[r >> 6], X.t4lo[r & 63]);
 }
 
 // Forward half-split: packed orthonormal coefficients of slot k from Z_k,
-// Z_{m-k}: W = e^{-i pi k/2n} A + e^{-i 5 pi k/2n} B.
-__device__ __forceinline__ float2 split_fwd_one(float2 a, float2 b, int k, int n, float sq,
-                                                const float2 *ts) {
+// Z_{m-k}: W = e^{-i pi k/2n} A + e^{-i 5 pi k/2n} B, with k = k1 + m1 k2.
+__device__ __forceinline__ float2 split_fwd_one(const Ctx &X, float2 a, float2 b, int k1, int k2, float sq) {
     const float2 cb = cconj(b);
     const float2 A = cscale(cadd(a, cb), 0.5f);
     const float2 d = csub(a, cb);
     const float2 Bv = make_float2(0.5f * d.y, -0.5f * d.x);                     // -i/2 (a - conj b)
-    const float2 e1 = tws_lookup(ts, 4 * n, k), e5 = tws_lookup(ts, 4 * n, 5 * k);
+    const float2 e1 = cmul(X.sa1[k1], X.sb1[k2]), e5 = cmul(X.sa5[k1], X.sb5[k2]);
     const float2 W = cadd(cmul(e1, A), cmul(e5, Bv));
     return make_float2(sq * W.x, -sq * W.y);
 }
 // Inverse of the half-split: Z_k from the packed slots k and m-k.
-__device__ __forceinline__ float2 split_inv_one(float2 yk, float2 yp, int k, int kp, int n, float sq,
-                                                const float2 *ts) {
+__device__ __forceinline__ float2 split_inv_one(const Ctx &X, float2 yk, float2 yp, int k1, int k2, int q1,
+                                                int q2, float sq) {
     // V_k = sqrt(n/2) e^{i pi k/2n} conj(Y_k)   (sq carries sqrt(n/2)/m)
-    const float2 Vk = cscale(cmulc(cconj(yk), tws_lookup(ts, 4 * n, k)), sq);
-    const float2 Vp = cscale(cmulc(cconj(yp), tws_lookup(ts, 4 * n, kp)), sq);
+    const float2 ek = cmul(X.sa1[k1], X.sb1[k2]), ep = cmul(X.sa1[q1], X.sb1[q2]);
+    const float2 Vk = cscale(cmulc(cconj(yk), ek), sq);
+    const float2 Vp = cscale(cmulc(cconj(yp), ep), sq);
     const float2 cVp = cconj(Vp);
     const float2 A = cscale(cadd(Vk, cVp), 0.5f);
-    const float2 Bv = cscale(cmulc(csub(Vk, cVp), tws_lookup(ts, 4 * n, 4 * k)), 0.5f);  // e^{+2 pi i k/n}
+    const float2 e4 = cmulc(cmul(X.sa5[k1], X.sb5[k2]), ek);                  // W_{4n}^{4k} = e^{-2 pi i k/n}
+    const float2 Bv = cscale(cmulc(csub(Vk, cVp), e4), 0.5f);                  // e^{+2 pi i k/n} (...)
     return make_float2(A.x - Bv.y, A.y + Bv.x);                                 // A + i B
 }
 
@@ -243,20 +237,18 @@ __device__ __noinline__ void split_pass(const Ctx &X, float2 *U)
                          : static_cast<float>(1.0 / sqrt(static_cast<double>(n)));
     const int total = X.npl * m2;
     const FastDiv fm2 = X.f_m2;
-    const float2 *ts = X.tws;
     for (int e = threadIdx.x; e < total; e += DCT_T) {
         const int pl = fdiv(e, fm2), k2 = e - pl * m2;
         const int p = p0 + pl;
         const int cnt = (p == 0) ? (m2 / 2 + 1) : ((2 * p == m1) ? (m2 + 1) / 2 : m2);
         if (k2 >= cnt) continue;
-        const int k = p + m1 * k2;
-        int ib, k2p;
-        if (p == 0) { k2p = (k2 == 0) ? 0 : m2 - k2; ib = 2 * pl * m2 + k2p; }
-        else { k2p = m2 - 1 - k2; ib = ((m1 - p == p) ? 2 * pl : 2 * pl + 1) * m2 + k2p; }
+        // partner m - k: row (m1 - p) mod m1, column m2-1-k2 (p > 0) or (m2-k2) mod m2 (p = 0)
+        int ib, q1, q2;
+        if (p == 0) { q1 = 0; q2 = (k2 == 0) ? 0 : m2 - k2; ib = 2 * pl * m2 + q2; }
+        else { q1 = m1 - p; q2 = m2 - 1 - k2; ib = ((q1 == p) ? 2 * pl : 2 * pl + 1) * m2 + q2; }
         const int ia = 2 * pl * m2 + k2;
-        const int kp = (k == 0) ? 0 : m - k;
         const float2 Za = U[ia], Zb = U[ib];
-        if (k == 0) {
+        if (p == 0 && k2 == 0) {
             if (!INV) {
                 const float V0 = Za.x + Za.y, Vm = Za.x - Za.y;
                 U[ia] = make_float2(V0 * s0, Vm * s0);
@@ -267,12 +259,12 @@ __device__ __noinline__ void split_pass(const Ctx &X, float2 *U)
             continue;
         }
         if (!INV) {
-            const float2 Ya = split_fwd_one(Za, Zb, k, n, sq, ts);
-            if (ib != ia) U[ib] = split_fwd_one(Zb, Za, kp, n, sq, ts);
+            const float2 Ya = split_fwd_one(X, Za, Zb, p, k2, sq);
+            if (ib != ia) U[ib] = split_fwd_one(X, Zb, Za, q1, q2, sq);
             U[ia] = Ya;
         } else {
-            const float2 Ya = split_inv_one(Za, Zb, k, kp, n, sq, ts);
-            if (ib != ia) U[ib] = split_inv_one(Zb, Za, kp, k, n, sq, ts);
+            const float2 Ya = split_inv_one(X, Za, Zb, p, k2, q1, q2, sq);
+            if (ib != ia) U[ib] = split_inv_one(X, Zb, Za, q1, q2, p, k2, sq);
             U[ia] = Ya;
         }
     }
@@ -288,7 +280,6 @@ __device__ __noinline__ void transpose(const Ctx &X, const float2 *src, float2 *
 {
     constexpr int U = 4;     // independent remote reads in flight per thread
     const int m = X.m, m1 = X.m1, m2 = X.m2, ncolmax = X.ncolmax, npmax = X.npmax;
-    const float2 *t4 = X.tw4;
     cl.sync();
     if (!INV) {
         const int total = 2 * X.npl * m2;
@@ -306,7 +297,7 @@ __device__ __noinline__ void transpose(const Ctx &X, const float2 *src, float2 *
                     if (k1 >= 0) {
                         const int o = fdiv(j2, fnc), lc = j2 - o * ncolmax;
                         v[u] = cl.map_shared_rank(src, o)[k1 * ncolmax + lc];
-                        w[u] = tw4_lookup(t4, m, j2 * k1);
+                        w[u] = tw4_lookup(X, j2 * k1);
                     }
                 }
             }
@@ -334,7 +325,7 @@ __device__ __noinline__ void transpose(const Ctx &X, const float2 *src, float2 *
                         const int o = fdiv(p, fnp);
                         const int slot = 2 * (p - o * npmax) + (k1 == p ? 0 : 1);
                         v[u] = cl.map_shared_rank(src, o)[slot * m2 + j2];
-                        w[u] = tw4_lookup(t4, m, j2 * k1);
+                        w[u] = tw4_lookup(X, j2 * k1);
                     }
                 }
             }
@@ -350,9 +341,10 @@ __device__ __noinline__ void transpose(const Ctx &X, const float2 *src, float2 *
 
 // Forward DCT: time layout in cur -> packed spectrum in cur (the two
 // buffers may swap roles).
-__device__ __noinline__ void dct_forward(const Ctx &X, float2 *&cur, float2 *&oth, const float2 *tw1,
-                                         const float2 *tw2, cg::cluster_group &cl)
+__device__ __noinline__ void dct_forward(const Ctx &X, float2 *&cur, float2 *&oth, const float2 *,
+                                         const float2 *, cg::cluster_group &cl)
 {
+    const float2 *tw1 = X.tw1, *tw2 = X.tw2;
     fft_seq<false>(cur, oth, X.m1, X.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, tw1);
     transpose<false>(X, cur, oth, cl);
     { float2 *t = cur; cur = oth; oth = t; }
@@ -361,9 +353,10 @@ __device__ __noinline__ void dct_forward(const Ctx &X, float2 *&cur, float2 *&ot
 }
 // Inverse (transpose of the orthonormal DCT-II): packed spectrum in cur ->
 // time layout in cur, scaled.
-__device__ __noinline__ void dct_inverse(const Ctx &X, float2 *&cur, float2 *&oth, const float2 *tw1,
-                                         const float2 *tw2, cg::cluster_group &cl)
+__device__ __noinline__ void dct_inverse(const Ctx &X, float2 *&cur, float2 *&oth, const float2 *,
+                                         const float2 *, cg::cluster_group &cl)
 {
+    const float2 *tw1 = X.tw1, *tw2 = X.tw2;
     split_pass<true>(X, cur);
     fft_seq<true>(cur, oth, X.m2, X.s2, X.nr2, 2 * X.npl, X.f_m2, 1, X.m2, false, tw2);
     transpose<true>(X, cur, oth, cl);
@@ -426,19 +419,6 @@ __device__ double2 cluster_sum2(double2 v, double2 *s_red, double2 *s_part, int 
     return tot;
 }
 
-__device__ void load_ctx(Ctx &X, const DctPlan &P, const float2 *tw, int c, int C)
-{
-    X.n = P.n; X.m = P.m; X.m1 = P.m1; X.m2 = P.m2; X.ncolmax = P.ncolmax; X.npmax = P.npmax;
-    X.P = P.P; X.nr1 = P.nr1; X.nr2 = P.nr2; X.c = c; X.C = C;
-    X.ncol = max(0, min(P.ncolmax, P.m2 - c * P.ncolmax));
-    X.p0 = c * P.npmax;
-    X.npl = max(0, min(P.npmax, P.P - X.p0));
-    X.f_ncolmax = P.f_ncolmax; X.f_m2 = P.f_m2; X.f_npmax = P.f_npmax;
-    X.tw4 = tw + P.tw4;
-    X.tws = tw + P.tws;
-    for (int i = 0; i < DCT_MAXR; ++i) { X.s1[i] = P.s1[i]; X.s2[i] = P.s2[i]; }
-}
-
 __device__ __forceinline__ bool flagged(const uint32_t *flags, int64_t t) {
     return (flags[t >> 5] >> (t & 31)) & 1u;
 }
@@ -448,32 +428,59 @@ __device__ __forceinline__ float fratio_pow(int kappa, float fscale, float alpha
     return exp2f(alpha * log2f(static_cast<float>(kappa) * fscale));
 }
 
-// shared-memory carve-up common to both kernels; tw1/tw2 point at the
-// plan's twiddle tables in global memory (read through L1)
+// shared-memory carve-up common to both kernels: two transform buffers,
+// then the twiddle block of the current length, then kernel-specific areas
 struct Smem {
-    float2 *U0, *U1;
+    float2 *U0, *U1, *twb;
     const float2 *tw1, *tw2;
     void *tail;
 };
-__device__ __forceinline__ Smem carve(void *raw, int sz)
+__device__ __forceinline__ Smem carve(void *raw, int sz, int twsz)
 {
     Smem s;
     float2 *p = static_cast<float2 *>(raw);
     s.U0 = p; p += sz;
     s.U1 = p; p += sz;
+    s.twb = p; p += twsz;
     s.tw1 = nullptr;
     s.tw2 = nullptr;
     s.tail = p;
     return s;
 }
 
+// Stage plan pi in shared memory: scalars and stage tables into sX, the
+// length's twiddle block into sm.twb (all threads copy).
 __device__ void load_plan(Ctx *sX, const DctPlan *plans, int pi, const float2 *tw, Smem &sm, int c, int C)
 {
-    __syncthreads();      // previous users of sX are done
-    if (threadIdx.x == 0) load_ctx(*sX, plans[pi], tw, c, C);
+    __syncthreads();      // previous users of sX and the twiddle block are done
+    const DctPlan &P = plans[pi];
+    const int t = threadIdx.x;
+    if (t >= 32 && t < 32 + DCT_MAXR) sX->s1[t - 32] = P.s1[t - 32];
+    else if (t >= 64 && t < 64 + DCT_MAXR) sX->s2[t - 64] = P.s2[t - 64];
+    else if (t == 0) {
+        Ctx &X = *sX;
+        X.n = P.n; X.m = P.m; X.m1 = P.m1; X.m2 = P.m2; X.ncolmax = P.ncolmax; X.npmax = P.npmax;
+        X.P = P.P; X.nr1 = P.nr1; X.nr2 = P.nr2; X.c = c; X.C = C;
+        X.ncol = max(0, min(P.ncolmax, P.m2 - c * P.ncolmax));
+        X.p0 = c * P.npmax;
+        X.npl = max(0, min(P.npmax, P.P - X.p0));
+        X.f_ncolmax = P.f_ncolmax; X.f_m2 = P.f_m2; X.f_npmax = P.f_npmax;
+        const float2 *b = sm.twb;
+        X.tw1 = b; b += P.m1;
+        X.tw2 = b; b += P.m2;
+        X.sa1 = b; b += P.m1;
+        X.sb1 = b; b += P.m2;
+        X.sa5 = b; b += P.m1;
+        X.sb5 = b; b += P.m2;
+        X.t4hi = b; b += P.m / 64 + 1;
+        X.t4lo = b;
+    }
+    const int cnt = 3 * (P.m1 + P.m2) + P.m / 64 + 65;
+    const float2 *src = tw + P.twb;
+    for (int i = t; i < cnt; i += DCT_T) sm.twb[i] = __ldg(src + i);
     __syncthreads();
-    sm.tw1 = tw + plans[pi].tw1;
-    sm.tw2 = tw + plans[pi].tw2;
+    sm.tw1 = sX->tw1;
+    sm.tw2 = sX->tw2;
 }
 
 // element e of the time layout -> (t0, t1) samples
@@ -561,7 +568,7 @@ struct GainArgs {
     int mode;
     double *g_out, *mu_out, *sig_out;
     int32_t *status;
-    int sz, m1max, m2max;
+    int sz, m1max, m2max, twsz;
 };
 
 __global__ void __launch_bounds__(DCT_T, 1) k_gain(GainArgs a)
@@ -573,7 +580,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_gain(GainArgs a)
     cg::cluster_group cl = cg::this_cluster();
     const int C = static_cast<int>(cl.num_blocks()), c = static_cast<int>(cl.block_rank());
     const int cid = blockIdx.x / C, ncl = gridDim.x / C;
-    Smem sm = carve(smem_raw, a.sz);
+    Smem sm = carve(smem_raw, a.sz, a.twsz);
     int parity = 0;
     for (int w = cid; w < a.work_count; w += ncl) {
         const int q = a.work[a.work_begin + w];
@@ -592,7 +599,8 @@ __global__ void __launch_bounds__(DCT_T, 1) k_gain(GainArgs a)
         // a from C(M s)
         load_time(X, cur, [&](int j) {
             const int t0 = vpos_t(2 * j, n, m), t1 = vpos_t(2 * j + 1, n, m);
-            return make_float2(flagged(fl, o + t0) ? 0.f : sq[t0], flagged(fl, o + t1) ? 0.f : sq[t1]);
+            const float v0 = __ldg(sq + t0), v1 = __ldg(sq + t1);      // independent of the flags
+            return make_float2(flagged(fl, o + t0) ? 0.f : v0, flagged(fl, o + t1) ? 0.f : v1);
         });
         dct_forward(X, cur, oth, sm.tw1, sm.tw2, cl);
         Acc2 sa = {0.f, 0.f}, sb = {0.f, 0.f};
@@ -613,7 +621,8 @@ __global__ void __launch_bounds__(DCT_T, 1) k_gain(GainArgs a)
         // b from <M s, C^T diag(1/P) C M d>
         load_time(X, cur, [&](int j) {
             const int t0 = vpos_t(2 * j, n, m), t1 = vpos_t(2 * j + 1, n, m);
-            return make_float2(flagged(fl, o + t0) ? 0.f : dq[t0], flagged(fl, o + t1) ? 0.f : dq[t1]);
+            const float v0 = __ldg(dq + t0), v1 = __ldg(dq + t1);
+            return make_float2(flagged(fl, o + t0) ? 0.f : v0, flagged(fl, o + t1) ? 0.f : v1);
         });
         dct_forward(X, cur, oth, sm.tw1, sm.tw2, cl);
         apply_filter(X, cur, fscale, alpha, s2, 2, nullptr);
@@ -688,7 +697,7 @@ struct NcorrArgs {
     float4 *wscratch;
     const float *xtab;       // Toeplitz inverses' first columns per detector (NULL: no preconditioner)
     const int32_t *lvalid;
-    int sz, m1max, m2max;
+    int sz, m1max, m2max, twsz;
 };
 
 __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
@@ -706,7 +715,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
     cg::cluster_group cl = cg::this_cluster();
     const int C = static_cast<int>(cl.num_blocks()), c = static_cast<int>(cl.block_rank());
     const int cid = blockIdx.x / C, ncl = gridDim.x / C;
-    Smem sm = carve(smem_raw, a.sz);
+    Smem sm = carve(smem_raw, a.sz, a.twsz);
     // CG vectors and preconditioner work areas after the two buffers
     int *c_loc = reinterpret_cast<int *>(sm.tail);
     int *c_t = c_loc + CG_KCAP;
@@ -749,10 +758,9 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             const int t0 = vpos_t(2 * j, n, m), t1 = vpos_t(2 * j + 1, n, m);
             float2 w1 = make_float2(0.f, 0.f);
             if (draw) w1 = stream_normal_pair(rng.seed, rng.band, q, 1, gi, 2 * j);
-            const float r0 = flagged(fl, o + t0) ? 0.f
-                                                  : fmaf(dq[t0] - g * sq[t0], inv_s2, w1.x * inv_s);
-            const float r1 = flagged(fl, o + t1) ? 0.f
-                                                  : fmaf(dq[t1] - g * sq[t1], inv_s2, w1.y * inv_s);
+            const float d0 = __ldg(dq + t0), d1 = __ldg(dq + t1), s0v = __ldg(sq + t0), s1v = __ldg(sq + t1);
+            const float r0 = flagged(fl, o + t0) ? 0.f : fmaf(d0 - g * s0v, inv_s2, w1.x * inv_s);
+            const float r1 = flagged(fl, o + t1) ? 0.f : fmaf(d1 - g * s1v, inv_s2, w1.y * inv_s);
             return make_float2(r0, r1);
         });
         dct_forward(X, cur, oth, sm.tw1, sm.tw2, cl);
@@ -1073,11 +1081,132 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
 }
 
 // ---------------------------------------------------------------------------
+// A8: TOD chi^2 with n_corr marginalised and its gradients.  Per detscan,
+// rhat = C(M(d - g s)); L = 1/2 sum_{k>=1} [rhat^2/P + ln P];
+// v = M C^T(rhat/P) (written out: dL/ds = -g v, so the map gradient is
+// -P^T(g v), a binning); dL/dg = -<M s, v>; dL/dtheta for the PSD
+// parameters from sum_k 1/2 (1/P - rhat^2/P^2) dP/dtheta.
+// ---------------------------------------------------------------------------
+struct Chi2Args {
+    const float *d, *s;
+    const double *gain;
+    const uint32_t *flags;
+    const double *psd;
+    const int64_t *off;
+    const DctPlan *plans;
+    const int32_t *q_plan;
+    const float2 *tw;
+    const int32_t *work;
+    int work_count;
+    int ndet;
+    double fsamp;
+    double *chi2, *dgain, *dpsd;
+    float *v_out;
+    int sz, twsz;
+};
+
+__global__ void __launch_bounds__(DCT_T, 1) k_chi2(Chi2Args a)
+{
+    extern __shared__ __align__(16) float2 smem_raw[];
+    __shared__ Ctx sX;
+    __shared__ double2 s_red[DCT_T / 32];
+    __shared__ double2 s_part[2];
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = static_cast<int>(cl.num_blocks()), c = static_cast<int>(cl.block_rank());
+    const int cid = blockIdx.x / C, ncl = gridDim.x / C;
+    Smem sm = carve(smem_raw, a.sz, a.twsz);
+    int parity = 0;
+    for (int w = cid; w < a.work_count; w += ncl) {
+        const int q = a.work[w];
+        const int det = q % a.ndet;
+        const int64_t o = a.off[q];
+        load_plan(&sX, a.plans, a.q_plan[q], a.tw, sm, c, C);
+        const Ctx &X = sX;
+        const int n = X.n, m = X.m;
+        const float *sq = a.s + o, *dq = a.d + o;
+        const uint32_t *fl = a.flags;
+        const double sig0 = a.psd[3 * det], fk = a.psd[3 * det + 1], al = a.psd[3 * det + 2];
+        const float fscale = static_cast<float>(a.fsamp / (2.0 * n * fk));
+        const float alpha = static_cast<float>(al);
+        const float s2 = static_cast<float>(sig0 * sig0);
+        const float g = static_cast<float>(a.gain[q]);
+        float2 *cur = sm.U0, *oth = sm.U1;
+        load_time(X, cur, [&](int j) {
+            const int t0 = vpos_t(2 * j, n, m), t1 = vpos_t(2 * j + 1, n, m);
+            const float d0 = __ldg(dq + t0), d1 = __ldg(dq + t1), s0v = __ldg(sq + t0), s1v = __ldg(sq + t1);
+            return make_float2(flagged(fl, o + t0) ? 0.f : d0 - g * s0v, flagged(fl, o + t1) ? 0.f : d1 - g * s1v);
+        });
+        dct_forward(X, cur, oth, X.tw1, X.tw2, cl);
+        // per mode: rhat^2/P, ln(1+x), and the f_knee / alpha gradient terms
+        Acc2 aq = {0.f, 0.f}, al1 = {0.f, 0.f}, afk = {0.f, 0.f}, aal = {0.f, 0.f};
+        {
+            const int total = 2 * X.npl * X.m2;
+            for (int e = threadIdx.x; e < total; e += DCT_T) {
+                const int slot = fdiv(e, X.f_m2), k2 = e - slot * X.m2;
+                const int k1 = slot_row(X, slot);
+                if (k1 < 0) continue;
+                const int k = k1 + X.m1 * k2;
+                float2 v = cur[e];
+                float wv[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int kap = h ? ((k == 0) ? m : n - k) : k;
+                    const float rh = h ? v.y : v.x;
+                    if (kap == 0) { wv[h] = 0.f; continue; }
+                    const float lf = log2f(static_cast<float>(kap) * fscale);     // log2(f/fk)
+                    const float x = exp2f(alpha * lf);
+                    const float P = s2 * (1.0f + x);
+                    const float q2 = rh * rh / P;                                    // rhat^2 / P
+                    acc_add(aq, q2);
+                    acc_add(al1, log1pf(x));
+                    // 1/2 (1/P - rhat^2/P^2) dP/dtheta = 1/2 (1 - q2) (dP/dtheta) / P
+                    const float cpre = 0.5f * (1.0f - q2) * s2 * x / P;
+                    acc_add(afk, -cpre * alpha);                                     // times 1/fk on the host side
+                    acc_add(aal, cpre * lf * 0.69314718055994531f);
+                    wv[h] = rh / P;
+                }
+                cur[e] = make_float2(wv[0], wv[1]);
+            }
+            __syncthreads();
+        }
+        dct_inverse(X, cur, oth, X.tw1, X.tw2, cl);
+        Acc2 ag = {0.f, 0.f};
+        {
+            const int tot = X.m1 * X.ncolmax;
+            float *vq = a.v_out ? a.v_out + o : nullptr;
+            for (int e = threadIdx.x; e < tot; e += DCT_T) {
+                int t0, t1;
+                bool valid;
+                elem_samples(X, e, t0, t1, valid);
+                if (!valid) continue;
+                const float2 v = cur[e];
+                const bool f0 = flagged(fl, o + t0), f1 = flagged(fl, o + t1);
+                const float v0 = f0 ? 0.f : v.x, v1 = f1 ? 0.f : v.y;
+                if (vq) { vq[t0] = v0; vq[t1] = v1; }
+                acc_add_prod(ag, __ldg(sq + t0), v0);
+                acc_add_prod(ag, __ldg(sq + t1), v1);
+            }
+        }
+        const double2 r1 = cluster_sum2(make_double2(acc_value(aq), acc_value(al1)), s_red, s_part, parity, cl);
+        const double2 r2 = cluster_sum2(make_double2(acc_value(afk), acc_value(aal)), s_red, s_part, parity, cl);
+        const double2 r3 = cluster_sum2(make_double2(acc_value(ag), 0.0), s_red, s_part, parity, cl);
+        if (c == 0 && threadIdx.x == 0) {
+            const double nm1 = static_cast<double>(n - 1);
+            a.chi2[q] = 0.5 * (r1.x + r1.y + nm1 * log(sig0 * sig0));
+            a.dgain[q] = -r3.x;
+            a.dpsd[3 * q + 0] = (nm1 - r1.x) / sig0;
+            a.dpsd[3 * q + 1] = r2.x / fk;
+            a.dpsd[3 * q + 2] = r2.y;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 static size_t smem_bytes(const Plan &p, bool ncorr)
 {
-    size_t b = sizeof(float2) * (2 * static_cast<size_t>(p.sz));
+    size_t b = sizeof(float2) * (2 * static_cast<size_t>(p.sz) + p.twsz);
     if (ncorr) b += static_cast<size_t>(CG_KCAP) * (2 * sizeof(int) + 5 * sizeof(float)) +
                     sizeof(int) * GMAP_CAP + sizeof(float) * 4 * TOEP_LMAX;
     return b;
@@ -1130,10 +1259,14 @@ cudaError_t setup_dct_kernels(Plan &p)
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_ncorr, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(p.smem_ncorr));
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_chi2, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(p.smem_gain));
+    if (e != cudaSuccess) return e;
     if (p.C > 8) {
         e = cudaFuncSetAttribute(k_gain, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(k_ncorr, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_chi2, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
     }
     e = max_clusters(reinterpret_cast<const void *>(k_gain), p.C, p.smem_gain, &p.nclusters_gain);
@@ -1152,7 +1285,7 @@ cudaError_t launch_gain(const Plan &p, const float *d, const float *s, const uin
     a.q_plan = p.q_plan; a.tw = p.tw; a.work = p.work; a.work_begin = work_begin;
     a.work_count = work_count; a.ndet = p.ndet; a.fsamp = p.fsamp; a.rng = rng; a.mode = mode;
     a.g_out = g; a.mu_out = mu; a.sig_out = sig; a.status = p.status; a.sz = p.sz;
-    a.m1max = p.m1max; a.m2max = p.m2max;
+    a.m1max = p.m1max; a.m2max = p.m2max; a.twsz = p.twsz;
     if (p.schedule == TOD_SCHED_PER_SCAN) {
         for (int w = 0; w < work_count; ++w) {
             a.work_begin = work_begin + w;
@@ -1184,7 +1317,7 @@ cudaError_t launch_ncorr(const Plan &p, const float *d, const float *s, const do
         cudaError_t e = launch_toeplitz_prep(p, psd, st);
         if (e != cudaSuccess) return e;
     }
-    a.m1max = p.m1max; a.m2max = p.m2max;
+    a.m1max = p.m1max; a.m2max = p.m2max; a.twsz = p.twsz;
     if (p.schedule == TOD_SCHED_PER_SCAN) {
         for (int w = 0; w < work_count; ++w) {
             a.work_begin = work_begin + w;
@@ -1196,6 +1329,25 @@ cudaError_t launch_ncorr(const Plan &p, const float *d, const float *s, const do
     }
     const int ncl = std::min(work_count, p.nclusters_ncorr);
     return launch_cluster(reinterpret_cast<const void *>(k_ncorr), &a, p.C, ncl, p.smem_ncorr, st);
+}
+
+}  // namespace tg
+
+namespace tg {
+
+cudaError_t launch_chi2(const Plan &p, const float *d, const float *s, const double *gain,
+                        const uint32_t *flags, const double *psd, double *chi2, double *dgain,
+                        double *dpsd, float *v, cudaStream_t st)
+{
+    if (p.nq == 0) return cudaSuccess;
+    static_assert(sizeof(Chi2Args) < 4096, "kernel parameters");
+    Chi2Args a;
+    a.d = d; a.s = s; a.gain = gain; a.flags = flags; a.psd = psd; a.off = p.off; a.plans = p.plans;
+    a.q_plan = p.q_plan; a.tw = p.tw; a.work = p.work; a.work_count = p.nq; a.ndet = p.ndet;
+    a.fsamp = p.fsamp; a.chi2 = chi2; a.dgain = dgain; a.dpsd = dpsd; a.v_out = v; a.sz = p.sz;
+    a.twsz = p.twsz;
+    const int ncl = std::min(p.nq, p.nclusters_gain);
+    return launch_cluster(reinterpret_cast<const void *>(k_chi2), &a, p.C, ncl, p.smem_gain, st);
 }
 
 }  // namespace tg

@@ -25,7 +25,8 @@ k_decode(const uint32_t *__restrict__ words, const int64_t *__restrict__ word_of
          const int32_t *__restrict__ cta_nblk, const int64_t *__restrict__ off,
          OutT *__restrict__ out, int32_t *status)
 {
-    __shared__ int2 s_lut[1 << DEC_LUTB];
+    extern __shared__ int2 s_lut[];                        // [1 << DEC_LUTB] then canonical symbols
+    int32_t *s_canon = reinterpret_cast<int32_t *>(s_lut + (1 << DEC_LUTB));
     __shared__ unsigned long long s_lim[26];
     __shared__ int32_t s_base[26];
     __shared__ OutT s_tile[DEC_T][DEC_ROUND + 1];
@@ -39,9 +40,12 @@ k_decode(const uint32_t *__restrict__ words, const int64_t *__restrict__ word_of
 
     for (int i = tid; i < (1 << DEC_LUTB); i += DEC_T) s_lut[i] = lut[(int64_t)scan * (1 << DEC_LUTB) + i];
     if (tid < 26) { s_lim[tid] = lim_g[scan * 26 + tid]; s_base[tid] = base_g[scan * 26 + tid]; }
-    // long codes (longer than DEC_LUTB bits) are rare: their symbols are read
-    // from global memory through the cache
+    // symbols of long codes (longer than DEC_LUTB bits) from shared memory
+    // when the code is small enough, else through the cache
     const int c0 = canon_off[scan], nc = canon_off[scan + 1] - c0;
+    const bool canon_smem = nc <= DEC_CANON_SMEM;
+    if (canon_smem)
+        for (int i = tid; i < nc; i += DEC_T) s_canon[i] = canon_vals[c0 + i];
 
     // this thread's block
     const bool active = tid < nb;
@@ -90,7 +94,7 @@ k_decode(const uint32_t *__restrict__ words, const int64_t *__restrict__ word_of
                     else {
                         const int ci = s_base[L] + static_cast<int>(peek >> (32 - L));
                         if (ci < 0 || ci >= nc) { ok = false; v = 0; }
-                        else v = __ldg(canon_vals + c0 + ci);
+                        else v = canon_smem ? s_canon[ci] : __ldg(canon_vals + c0 + ci);
                         len = L;
                     }
                 }
@@ -119,11 +123,19 @@ k_decode(const uint32_t *__restrict__ words, const int64_t *__restrict__ word_of
     if (active && (!ok || pos > end)) set_status(status, q, TOD_ERR_CORRUPT_STREAM);
 }
 
+cudaError_t setup_decode_kernel()
+{
+    const int smem = static_cast<int>(sizeof(int2) * (1 << DEC_LUTB) + sizeof(int32_t) * DEC_CANON_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_decode<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_decode<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
 cudaError_t launch_decode(const Plan &p, const HuffDev &h, int32_t *pix_out, uint16_t *psi_out,
                           cudaStream_t st)
 {
     if (h.ncta == 0) return cudaSuccess;
-    const size_t smem = 0;
+    const size_t smem = sizeof(int2) * (1 << DEC_LUTB) + sizeof(int32_t) * DEC_CANON_SMEM;
     if (pix_out) {
         k_decode<int32_t><<<h.ncta, DEC_T, smem, st>>>(
             h.words, h.word_off, h.nbits, h.blk_off, h.ckpt_bit, h.ckpt_val, h.blk_q, h.lut, h.lim,
