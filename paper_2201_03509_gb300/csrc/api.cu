@@ -252,8 +252,9 @@ bool choose_factor(int n, int C, DctPlan &out, int &sz)
         const int npmax = (P + C - 1) / C;
         const int asz = m1 * ncolmax, bsz = 2 * npmax * m2;
         if (asz > DCT_SZ_MAX || bsz > DCT_SZ_MAX) continue;               // shared-memory budget
-        // smallest per-CTA buffer; within 5 % of it, the most balanced split
-        const int s = std::max(asz, bsz);
+        // smallest shared-memory footprint (two buffers plus the length's
+        // twiddle tables); within 5 % of it, the most balanced split
+        const int s = 2 * std::max(asz, bsz) + 3 * (m1 + m2);
         const bool better = best < 0 || s * 20 < best * 19 ||
                             (s * 20 <= best * 21 && std::max(m1, m2) < std::max(bestm1, m / bestm1));
         if (better) {
@@ -261,7 +262,7 @@ bool choose_factor(int n, int C, DctPlan &out, int &sz)
             bestm1 = m1;
         }
     }
-    if (best >= 0) {   // best holds the buffer size of the chosen split
+    if (best >= 0) {   // best now holds the buffer size of the chosen split
         const int m2b = m / bestm1;
         best = std::max(bestm1 * ((m2b + C - 1) / C), 2 * (((bestm1 / 2 + 1) + C - 1) / C) * m2b);
     }
@@ -627,8 +628,7 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
             int twmax = 0;
             for (auto &dp : plans) twmax = std::max(twmax, 3 * (dp.m1 + dp.m2) + dp.m / 64 + 65);
             const size_t smem = sizeof(float2) * (2 * static_cast<size_t>(sz) + twmax) +
-                                static_cast<size_t>(CG_KCAP) * 28 + sizeof(int) * GMAP_CAP +
-                                sizeof(float) * 4 * TOEP_LMAX + 12288;
+                                static_cast<size_t>(CG_KCAP) * 24 + sizeof(float) * 4 * TOEP_LMAX + 12288;
             if (smem > 227 * 1024) continue;
             chosenC = C;
             p->sz = sz; p->m1max = m1max; p->m2max = m2max;
@@ -692,7 +692,7 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
             tabs[s] = build_dectab(band->pix.sym_vals + a, band->pix.sym_len + a, band->pix.sym_off[s + 1] - a);
         }
         std::atomic<bool> bad(false);
-        std::vector<uint32_t> lp(p->N);
+        std::vector<uint32_t> srt(p->N);
         std::vector<std::vector<int32_t>> rpix(p->nq), rlen(p->nq);
         std::vector<std::vector<int64_t>> rstart(p->nq);
         parallel_for(p->nq, [&](int64_t a, int64_t b) {
@@ -709,8 +709,8 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
                 if (bad) continue;
                 std::sort(key.begin(), key.end());
                 for (int64_t i = 0; i < n; ++i) {
-                    // sample -> its position in the pixel-sorted order of the detscan
-                    lp[o + static_cast<int64_t>(key[i] & 0xFFFFFFFFu)] = static_cast<uint32_t>(i);
+                    // pixel-sorted position -> time index within the detscan
+                    srt[o + i] = static_cast<uint32_t>(key[i] & 0xFFFFFFFFu);
                     const int32_t px = static_cast<int32_t>(key[i] >> 32);
                     if (i == 0 || px != static_cast<int32_t>(key[i - 1] >> 32)) {
                         rpix[q].push_back(px);
@@ -740,7 +740,26 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
                 pslot[pr] = static_cast<int32_t>(fillc[rpix[q][i]]++);
             }
         if (p->npairs >= (int64_t(1) << 31)) { free_plan(p); return TOD_ERR_ARG; }
-        if ((e = dev_upload(*p, p->lp, lp.data(), lp.size()))) return fail(e);
+        // binning tiles: consecutive whole runs of one detscan, at most
+        // BIN_TILE samples, or a single longer run on its own
+        std::vector<int32_t> tq, tr0;
+        for (int q = 0; q < p->nq; ++q) {
+            int64_t cnt = 0;
+            for (int64_t pr = pair_off[q]; pr < pair_off[q + 1]; ++pr) {
+                const int64_t len = plen[pr];
+                if (pr == pair_off[q] || cnt + len > BIN_TILE) {
+                    tq.push_back(q);
+                    tr0.push_back(static_cast<int32_t>(pr));
+                    cnt = 0;
+                }
+                cnt += len;
+            }
+        }
+        tr0.push_back(static_cast<int32_t>(p->npairs));
+        p->nbin_tiles = static_cast<int32_t>(tq.size());
+        if ((e = dev_upload(*p, p->srt, srt.data(), srt.size()))) return fail(e);
+        if ((e = dev_upload(*p, p->bin_tile_q, tq.data(), tq.size()))) return fail(e);
+        if ((e = dev_upload(*p, p->bin_tile_r0, tr0.data(), tr0.size()))) return fail(e);
         if ((e = dev_upload(*p, p->pair_off, pair_off.data(), pair_off.size()))) return fail(e);
         if ((e = dev_upload(*p, p->pair_start, pstart.data(), pstart.size()))) return fail(e);
         if ((e = dev_upload(*p, p->pair_len, plen.data(), plen.size()))) return fail(e);

@@ -18,8 +18,8 @@ constexpr int DCT_SZ_MAX = 11776;     // complex values per CTA buffer (two buff
 constexpr int DCT_MAXR = 20;          // maximum number of radix stages per sub-transform
 constexpr int CG_KCAP = 768;          // flagged samples per CTA held by the CG
 constexpr int TOEP_LMAX = 512;        // longest gap block of the Toeplitz preconditioner
+constexpr int BIN_TILE = 4096;        // sorted samples staged per binning tile
 constexpr int GAP_CAP = 256;          // gap blocks per detscan handled by the preconditioner
-constexpr int GMAP_CAP = 1024;        // gap-block elements mapped per CTA
 
 // Compressed stream kind, device copy + decode tables.
 struct HuffDev {
@@ -93,14 +93,15 @@ struct Plan {
     bool use_prec = true;
     int64_t wscratch_per_cluster = 0;
     int32_t schedule = TOD_SCHED_PERSISTENT;
-    int32_t bin_C = 1, bin_cap = 0, bin_nclusters = 1;
-    size_t smem_bin = 0;
+    int32_t nbin_tiles = 0;          // binning tiles (whole runs of one detscan)
     size_t smem_gain = 0, smem_ncorr = 0;
     // binning
-    uint32_t *lp = nullptr;          // [N] position of each sample in its detscan's pixel-sorted order
+    uint32_t *srt = nullptr;         // [N] pixel-sorted order of each detscan: time index within the detscan
+    int32_t *bin_tile_q = nullptr;   // [nbin_tiles] detscan of the tile
+    int32_t *bin_tile_r0 = nullptr;  // [nbin_tiles + 1] first run (global run index); last entry = npairs
     int64_t npairs = 0;
     int64_t *pair_off = nullptr;     // [nq+1] runs of each detscan
-    int64_t *pair_start = nullptr;   // [npairs] first lp index (global) of the run
+    int64_t *pair_start = nullptr;   // [npairs] first srt index (global) of the run
     int32_t *pair_len = nullptr;     // [npairs]
     int32_t *pair_slot = nullptr;    // [npairs] position in pixel-sorted run order
     int64_t *pix_slot_off = nullptr; // [npix+1]
@@ -123,6 +124,12 @@ cudaError_t launch_ncorr(const Plan &p, const float *d, const float *s, const do
                          const uint32_t *flags, const double *psd, tod_rng rng, int mode,
                          float tol, int maxit, float *x, int32_t *iters, cudaStream_t st,
                          int work_begin, int work_count);
+// the same draw with caller-provided filter-weight scratch: at most
+// nclusters_max clusters, each using C x sz float4 of it
+cudaError_t launch_ncorr_scratch(const Plan &p, const float *d, const float *s, const double *gain,
+                                 const uint32_t *flags, const double *psd, tod_rng rng, int mode,
+                                 float tol, int maxit, float *x, int32_t *iters, cudaStream_t st,
+                                 int work_begin, int work_count, float4 *scratch, int nclusters_max);
 cudaError_t launch_chi2(const Plan &p, const float *d, const float *s, const double *gain,
                         const uint32_t *flags, const double *psd, double *chi2, double *dgain,
                         double *dpsd, float *v, cudaStream_t st);

@@ -3,28 +3,29 @@
 // pixel)"; Sect. 2.4: coadded on the fly, synchronised once).
 //
 // Binning is a deterministic two-level segmented reduction.  The plan holds,
-// for every detscan, its samples sorted by pixel (stable in time) and the
-// runs of equal pixel ("pairs" of detscan and pixel); the runs of the whole
-// band are ranked by (pixel, detscan).
-//   k_bin:    one cluster per detscan stages the detscan's data, residual and
-//             psi/flag words in distributed shared memory (coalesced HBM
-//             reads), then each thread sums whole runs, gathering from DSMEM.
-//             Products of FP32 values are formed exactly and summed as FP32
-//             double-words (FP64 accuracy at FP32 issue rate); each run's
-//             sums are scaled by the detscan's g^2/sigma0^2, g/sigma0^2 in
-//             FP64 and written at the run's rank.
+// for every detscan, its pixel-sorted order (stable in time), the runs of
+// equal pixel ("pairs" of detscan and pixel) ranked over the band by (pixel,
+// detscan), and tiles of consecutive whole runs of one detscan (at most
+// BIN_TILE samples, or one longer run alone).
+//   k_bin:    one CTA per tile gathers the tile's data, residual and
+//             psi/flag words in sorted order into shared memory (the
+//             detscan's samples stay in L2 while its tiles run), then one
+//             thread sums each run.  Products of FP32 values are formed
+//             exactly and summed as FP32 double-words (FP64 accuracy at FP32
+//             issue rate); each run's sums are scaled by the detscan's
+//             g^2/sigma0^2, g/sigma0^2 in FP64 and written at the run's rank.
+//             A run longer than a tile is summed by the whole CTA with a
+//             fixed-order tree.
 //   k_reduce: one thread per pixel adds its contiguous runs in FP64, in
 //             ascending detscan order.
 #include <algorithm>
-#include <cooperative_groups.h>
 #include "common.cuh"
 #include "internal.cuh"
 
-namespace cg = cooperative_groups;
 
 namespace tg {
 
-constexpr int BIN_T = 512;
+constexpr int BIN_T = 256;
 
 struct BinArgs {
     const uint16_t *psi;
@@ -33,15 +34,13 @@ struct BinArgs {
     const uint32_t *flags;
     const double *psd;
     const int64_t *off;
-    const uint32_t *inv;          // sample -> position in the detscan's pixel-sorted order
-    const int64_t *pair_off, *pair_start;
+    const uint32_t *srt;          // sorted position -> time index within the detscan
+    const int64_t *pair_start;
     const int32_t *pair_len, *pair_slot;
+    const int32_t *tile_q, *tile_r0;
     const float2 *trig;
-    const int32_t *work;
-    int nq, ndet;
-    int chunk_cap;     // samples staged per CTA
+    int ndet;
     double *rec;
-    int32_t *status;
 };
 
 // sum of two double-words (two-sum on the heads, tails added)
@@ -51,121 +50,136 @@ __device__ __forceinline__ Acc2 acc_merge(const Acc2 &a, const Acc2 &b) {
     r.c = __fadd_rn(r.c, b.c);
     return r;
 }
-__device__ __forceinline__ Acc2 acc_shfl_down(const Acc2 &a, int o) {
-    Acc2 r;
-    r.s = __shfl_down_sync(0xffffffffu, a.s, o);
-    r.c = __shfl_down_sync(0xffffffffu, a.c, o);
-    return r;
+
+// the eleven per-run sums: 1 (as hits), c, s, cc, cs, ss, d, cd, sd, x, cx, sx
+struct RunSums {
+    Acc2 a[11];
+    int hits;
+};
+__device__ __forceinline__ void sums_zero(RunSums &r) {
+#pragma unroll
+    for (int i = 0; i < 11; ++i) r.a[i] = Acc2{0.f, 0.f};
+    r.hits = 0;
+}
+__device__ __forceinline__ void sums_add(RunSums &r, float2 cs, float dv, float xv) {
+    ++r.hits;
+    acc_add(r.a[0], cs.x);
+    acc_add(r.a[1], cs.y);
+    acc_add_prod(r.a[2], cs.x, cs.x);
+    acc_add_prod(r.a[3], cs.x, cs.y);
+    acc_add_prod(r.a[4], cs.y, cs.y);
+    acc_add(r.a[5], dv);
+    acc_add_prod(r.a[6], cs.x, dv);
+    acc_add_prod(r.a[7], cs.y, dv);
+    acc_add(r.a[8], xv);
+    acc_add_prod(r.a[9], cs.x, xv);
+    acc_add_prod(r.a[10], cs.y, xv);
+}
+__device__ __forceinline__ void sums_store(const RunSums &r, double wA, double wb, double *rr) {
+    rr[0] = wA * r.hits;
+    rr[1] = wA * acc_value(r.a[0]);
+    rr[2] = wA * acc_value(r.a[1]);
+    rr[3] = wA * acc_value(r.a[2]);
+    rr[4] = wA * acc_value(r.a[3]);
+    rr[5] = wA * acc_value(r.a[4]);
+    rr[6] = wb * (acc_value(r.a[5]) - acc_value(r.a[8]));
+    rr[7] = wb * (acc_value(r.a[6]) - acc_value(r.a[9]));
+    rr[8] = wb * (acc_value(r.a[7]) - acc_value(r.a[10]));
+    rr[9] = static_cast<double>(r.hits);
 }
 
-__global__ void __launch_bounds__(BIN_T, 1) k_bin(BinArgs a)
-{
-    extern __shared__ __align__(16) unsigned char bin_raw[];
-    __shared__ FastDiv s_fchunk;
-    __shared__ int s_ra, s_rb;
-    cg::cluster_group cl = cg::this_cluster();
-    const int C = static_cast<int>(cl.num_blocks()), c = static_cast<int>(cl.block_rank());
-    const int cid = blockIdx.x / C, ncl = gridDim.x / C;
-    float *s_d = reinterpret_cast<float *>(bin_raw);
-    float *s_x = s_d + a.chunk_cap;
-    uint16_t *s_pf = reinterpret_cast<uint16_t *>(s_x + a.chunk_cap);   // psi | flag << 15
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+__device__ __forceinline__ uint16_t psi_flag(const BinArgs &a, int64_t tg) {
+    const uint32_t fb = (__ldg(a.flags + (tg >> 5)) >> (tg & 31)) & 1u;
+    return static_cast<uint16_t>((__ldg(a.psi + tg) & 0x0FFF) | (fb << 15));
+}
 
-    for (int w = cid; w < a.nq; w += ncl) {
-        const int q = a.work[w];
-        const int64_t o = a.off[q];
-        const int n = static_cast<int>(a.off[q + 1] - o);
-        const int chunk = (n + C - 1) / C;
-        if (chunk > a.chunk_cap) {                   // plan guarantees this never happens
-            if (c == 0 && threadIdx.x == 0) set_status(a.status, q, TOD_ERR_ARG);
-            cl.sync();
-            continue;
+__global__ void __launch_bounds__(BIN_T) k_bin(BinArgs a)
+{
+    __shared__ float s_d[BIN_TILE], s_x[BIN_TILE];
+    __shared__ uint16_t s_pf[BIN_TILE];
+    __shared__ Acc2 s_red[BIN_T / 32][11];
+    __shared__ int s_hits[BIN_T / 32];
+    const int tile = blockIdx.x;
+    const int q = a.tile_q[tile];
+    const int r0 = a.tile_r0[tile], nr = a.tile_r0[tile + 1] - r0;
+    const int64_t o = a.off[q];
+    const int64_t s0 = a.pair_start[r0];
+    const int cnt = static_cast<int>(a.pair_start[r0 + nr - 1] + a.pair_len[r0 + nr - 1] - s0);
+    const int det = q % a.ndet;
+    const double sig0 = a.psd[3 * det];
+    const double gq = a.gain[q];
+    const double wA = gq * gq / (sig0 * sig0), wb = gq / (sig0 * sig0);
+
+    if (cnt > BIN_TILE) {
+        // one run longer than a tile: strided partial sums, then a fixed-order tree
+        RunSums r;
+        sums_zero(r);
+        for (int i = threadIdx.x; i < cnt; i += BIN_T) {
+            const int64_t tg = o + __ldg(a.srt + s0 + i);
+            const uint16_t pf = psi_flag(a, tg);
+            if (pf >> 15) continue;
+            sums_add(r, __ldg(a.trig + (pf & 0x0FFF)), __ldg(a.d + tg), __ldg(a.x + tg));
         }
-        const int64_t pr0 = a.pair_off[q], pr1 = a.pair_off[q + 1];
-        if (threadIdx.x == 0) {
-            s_fchunk = make_fastdiv_dev(static_cast<uint32_t>(chunk));
-            // runs whose first sorted position lies in this CTA's chunk
-            int64_t lo = pr0, hi = pr1;
-            while (lo < hi) { const int64_t mid = (lo + hi) >> 1; if (a.pair_start[mid] - o < static_cast<int64_t>(c) * chunk) lo = mid + 1; else hi = mid; }
-            s_ra = static_cast<int>(lo - pr0);
-            lo = pr0; hi = pr1;
-            while (lo < hi) { const int64_t mid = (lo + hi) >> 1; if (a.pair_start[mid] - o < static_cast<int64_t>(c + 1) * chunk) lo = mid + 1; else hi = mid; }
-            s_rb = static_cast<int>(lo - pr0);
+#pragma unroll
+        for (int ofs = 16; ofs; ofs >>= 1) {
+#pragma unroll
+            for (int k = 0; k < 11; ++k) {
+                Acc2 o2;
+                o2.s = __shfl_down_sync(0xffffffffu, r.a[k].s, ofs);
+                o2.c = __shfl_down_sync(0xffffffffu, r.a[k].c, ofs);
+                r.a[k] = acc_merge(r.a[k], o2);
+            }
+            r.hits += __shfl_down_sync(0xffffffffu, r.hits, ofs);
+        }
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < 11; ++k) s_red[warp][k] = r.a[k];
+            s_hits[warp] = r.hits;
         }
         __syncthreads();
-        const FastDiv fch = s_fchunk;
-        // stage: coalesced reads in time order, stores to the sorted position
-        const int t0 = c * chunk, t1 = min(n, t0 + chunk);
-        for (int t = t0 + threadIdx.x; t < t1; t += BIN_T) {
-            const int64_t tg = o + t;
-            const int sp = static_cast<int>(a.inv[tg]);
-            const int ow = fdiv(sp, fch), ls = sp - ow * chunk;
-            const uint32_t fb = (a.flags[tg >> 5] >> (tg & 31)) & 1u;
-            *cl.map_shared_rank(s_d + ls, ow) = a.d[tg];
-            *cl.map_shared_rank(s_x + ls, ow) = a.x[tg];
-            *cl.map_shared_rank(s_pf + ls, ow) = static_cast<uint16_t>((a.psi[tg] & 0x0FFF) | (fb << 15));
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < BIN_T / 32; ++w) {
+#pragma unroll
+                for (int k = 0; k < 11; ++k) r.a[k] = acc_merge(r.a[k], s_red[w][k]);
+                r.hits += s_hits[w];
+            }
+            sums_store(r, wA, wb, a.rec + static_cast<int64_t>(a.pair_slot[r0]) * 10);
         }
-        cl.sync();
-        const int det = q % a.ndet;
-        const double sig0 = a.psd[3 * det];
-        const double gq = a.gain[q];
-        const double wA = gq * gq / (sig0 * sig0), wb = gq / (sig0 * sig0);
-        for (int r = s_ra + warp; r < s_rb; r += BIN_T / 32) {
-            const int64_t pr = pr0 + r;
-            const int st = static_cast<int>(a.pair_start[pr] - o);
-            const int len = a.pair_len[pr];
-            Acc2 acc[11];
+        return;
+    }
+
+    // gather in sorted order: four independent loads in flight per thread
+    for (int i0 = threadIdx.x; i0 < cnt; i0 += 4 * BIN_T) {
+        int64_t tg[4];
 #pragma unroll
-            for (int i = 0; i < 11; ++i) acc[i] = Acc2{0.f, 0.f};
-            int hits = 0;
-            for (int i = lane; i < len; i += 32) {
-                const int sp = st + i;
-                const int ow = fdiv(sp, fch), ls = sp - ow * chunk;
-                uint16_t pf;
-                float dv, xv;
-                if (ow == c) { pf = s_pf[ls]; dv = s_d[ls]; xv = s_x[ls]; }
-                else {
-                    pf = *cl.map_shared_rank(s_pf + ls, ow);
-                    dv = *cl.map_shared_rank(s_d + ls, ow);
-                    xv = *cl.map_shared_rank(s_x + ls, ow);
-                }
-                if (pf >> 15) continue;
-                const float2 cs = __ldg(a.trig + (pf & 0x0FFF));
-                ++hits;
-                acc_add(acc[0], cs.x);
-                acc_add(acc[1], cs.y);
-                acc_add_prod(acc[2], cs.x, cs.x);
-                acc_add_prod(acc[3], cs.x, cs.y);
-                acc_add_prod(acc[4], cs.y, cs.y);
-                acc_add(acc[5], dv);
-                acc_add_prod(acc[6], cs.x, dv);
-                acc_add_prod(acc[7], cs.y, dv);
-                acc_add(acc[8], xv);
-                acc_add_prod(acc[9], cs.x, xv);
-                acc_add_prod(acc[10], cs.y, xv);
-            }
-            // warp tree in a fixed order (deterministic)
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * BIN_T;
+            tg[u] = i < cnt ? o + __ldg(a.srt + s0 + i) : -1;
+        }
 #pragma unroll
-            for (int ofs = 16; ofs; ofs >>= 1) {
-#pragma unroll
-                for (int i = 0; i < 11; ++i) acc[i] = acc_merge(acc[i], acc_shfl_down(acc[i], ofs));
-                hits += __shfl_down_sync(0xffffffffu, hits, ofs);
-            }
-            if (lane == 0) {
-                double *rr = a.rec + static_cast<int64_t>(a.pair_slot[pr]) * 10;
-                rr[0] = wA * hits;
-                rr[1] = wA * acc_value(acc[0]);
-                rr[2] = wA * acc_value(acc[1]);
-                rr[3] = wA * acc_value(acc[2]);
-                rr[4] = wA * acc_value(acc[3]);
-                rr[5] = wA * acc_value(acc[4]);
-                rr[6] = wb * (acc_value(acc[5]) - acc_value(acc[8]));
-                rr[7] = wb * (acc_value(acc[6]) - acc_value(acc[9]));
-                rr[8] = wb * (acc_value(acc[7]) - acc_value(acc[10]));
-                rr[9] = static_cast<double>(hits);
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * BIN_T;
+            if (tg[u] >= 0) {
+                s_d[i] = __ldg(a.d + tg[u]);
+                s_x[i] = __ldg(a.x + tg[u]);
+                s_pf[i] = psi_flag(a, tg[u]);
             }
         }
-        cl.sync();      // staging buffers are reused by the next detscan
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < nr; r += BIN_T) {
+        const int pr = r0 + r;
+        const int st = static_cast<int>(a.pair_start[pr] - s0);
+        const int len = a.pair_len[pr];
+        RunSums rs;
+        sums_zero(rs);
+        for (int i = st; i < st + len; ++i) {
+            const uint16_t pf = s_pf[i];
+            if (pf >> 15) continue;
+            sums_add(rs, __ldg(a.trig + (pf & 0x0FFF)), s_d[i], s_x[i]);
+        }
+        sums_store(rs, wA, wb, a.rec + static_cast<int64_t>(a.pair_slot[pr]) * 10);
     }
 }
 
@@ -230,37 +244,8 @@ k_solve(const double *__restrict__ A, const double *__restrict__ b, const int32_
     if (valid) valid[p] = ok ? 1 : 0;
 }
 
-// ---------------------------------------------------------------------------
-// Cluster size and staging capacity are fixed at plan creation (the longest
-// detscan over the cluster, <= 200 KB per CTA), so tod_bin only launches.
-cudaError_t setup_bin_kernel(Plan &p)
+cudaError_t setup_bin_kernel(Plan &)
 {
-    int64_t nmax = 0;
-    for (int q = 0; q < p.nq; ++q) nmax = std::max<int64_t>(nmax, p.h_off[q + 1] - p.h_off[q]);
-    int C = 1;
-    while (C < 16 && (nmax + C - 1) / C * 10 > 200 * 1024) C *= 2;
-    p.bin_C = C;
-    p.bin_cap = static_cast<int>((nmax + C - 1) / C);
-    p.smem_bin = static_cast<size_t>(p.bin_cap) * 10 + 16;
-    cudaError_t e = cudaFuncSetAttribute(k_bin, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(p.smem_bin));
-    if (e != cudaSuccess) return e;
-    if (C > 8) {
-        e = cudaFuncSetAttribute(k_bin, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(static_cast<unsigned>(C * 64));
-    cfg.blockDim = dim3(BIN_T);
-    cfg.dynamicSmemBytes = p.smem_bin;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = C; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr; cfg.numAttrs = 1;
-    int ncl = 0;
-    e = cudaOccupancyMaxActiveClusters(&ncl, k_bin, &cfg);
-    if (e != cudaSuccess) return e;
-    p.bin_nclusters = std::max(1, std::min(ncl, p.nq));
     return cudaSuccess;
 }
 
@@ -271,20 +256,10 @@ cudaError_t launch_bin(const Plan &p, const uint16_t *psi, const float *d, const
     if (p.nq == 0) return cudaSuccess;
     BinArgs a;
     a.psi = psi; a.d = d; a.x = ncorr; a.gain = gain; a.flags = flags; a.psd = psd; a.off = p.off;
-    a.inv = p.lp; a.pair_off = p.pair_off; a.pair_start = p.pair_start; a.pair_len = p.pair_len;
-    a.pair_slot = p.pair_slot; a.trig = p.trig; a.work = p.work; a.nq = p.nq; a.ndet = p.ndet;
-    a.chunk_cap = p.bin_cap; a.rec = p.rec; a.status = p.status;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(static_cast<unsigned>(p.bin_nclusters * p.bin_C));
-    cfg.blockDim = dim3(BIN_T);
-    cfg.dynamicSmemBytes = p.smem_bin;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = p.bin_C; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr; cfg.numAttrs = 1;
-    void *argv[1] = {&a};
-    cudaError_t e = cudaLaunchKernelExC(&cfg, reinterpret_cast<const void *>(k_bin), argv);
+    a.srt = p.srt; a.pair_start = p.pair_start; a.pair_len = p.pair_len; a.pair_slot = p.pair_slot;
+    a.tile_q = p.bin_tile_q; a.tile_r0 = p.bin_tile_r0; a.trig = p.trig; a.ndet = p.ndet; a.rec = p.rec;
+    if (p.nbin_tiles > 0) k_bin<<<p.nbin_tiles, BIN_T, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int nb = (p.npix + 255) / 256;
     k_reduce<<<nb, 256, 0, st>>>(p.rec, p.pix_slot_off, p.npix, A, b, hits);

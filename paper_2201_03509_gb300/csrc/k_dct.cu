@@ -674,6 +674,43 @@ __global__ void __launch_bounds__(DCT_T, 1) k_gain(GainArgs a)
 // (E: flagged samples; C^T C = I) by CG and add B^{-1} E y (Woodbury):
 // x = A^{-1} b exactly, A = B - E E^T / sigma0^2.
 // ---------------------------------------------------------------------------
+// Exclusive scan of one int3 per thread over the CTA (warp shuffles, then
+// the warp totals); total gets the CTA-wide sum.  s_w holds DCT_T/32 + 1.
+__device__ int3 block_exscan3(int3 v, int3 *s_w, int3 &total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int3 inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int x = __shfl_up_sync(0xffffffffu, inc.x, d);
+        const int y = __shfl_up_sync(0xffffffffu, inc.y, d);
+        const int z = __shfl_up_sync(0xffffffffu, inc.z, d);
+        if (lane >= d) { inc.x += x; inc.y += y; inc.z += z; }
+    }
+    if (lane == 31) s_w[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        constexpr int NW = DCT_T / 32;
+        const int3 w = lane < NW ? s_w[lane] : make_int3(0, 0, 0);
+        int3 wi = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, wi.x, d);
+            const int y = __shfl_up_sync(0xffffffffu, wi.y, d);
+            const int z = __shfl_up_sync(0xffffffffu, wi.z, d);
+            if (lane >= d) { wi.x += x; wi.y += y; wi.z += z; }
+        }
+        __syncwarp();
+        if (lane < NW) s_w[lane] = make_int3(wi.x - w.x, wi.y - w.y, wi.z - w.z);
+        if (lane == NW - 1) s_w[NW] = wi;
+    }
+    __syncthreads();
+    const int3 b = s_w[warp];
+    total = s_w[DCT_T / 32];
+    __syncthreads();       // s_w may be reused after this
+    return make_int3(b.x + inc.x - v.x, b.y + inc.y - v.y, b.z + inc.z - v.z);
+}
+
 struct NcorrArgs {
     const float *d, *s;
     const double *gain;
@@ -706,26 +743,22 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
     __shared__ Ctx sX;
     __shared__ double2 s_red[DCT_T / 32];
     __shared__ double2 s_part[2];
-    __shared__ int s_scan[DCT_T];
-    __shared__ int s_gscan[DCT_T];
-    __shared__ int s_escan[DCT_T];
-    __shared__ int s_kc, s_ngap, s_nown, s_ovf;
+    __shared__ int3 s_wscan[DCT_T / 32 + 1];
+    __shared__ int s_nown, s_ovf;
     __shared__ int g_beg[GAP_CAP], g_end[GAP_CAP];
-    __shared__ int o_beg[GAP_CAP], o_len[GAP_CAP], o_off[GAP_CAP];
+    __shared__ int o_len[GAP_CAP], o_rank[GAP_CAP];
     cg::cluster_group cl = cg::this_cluster();
     const int C = static_cast<int>(cl.num_blocks()), c = static_cast<int>(cl.block_rank());
     const int cid = blockIdx.x / C, ncl = gridDim.x / C;
     Smem sm = carve(smem_raw, a.sz, a.twsz);
     // CG vectors and preconditioner work areas after the two buffers
     int *c_loc = reinterpret_cast<int *>(sm.tail);
-    int *c_t = c_loc + CG_KCAP;
-    float *c_y = reinterpret_cast<float *>(c_t + CG_KCAP);
+    float *c_y = reinterpret_cast<float *>(c_loc + CG_KCAP);
     float *c_r = c_y + CG_KCAP;
     float *c_p = c_r + CG_KCAP;
     float *c_q = c_p + CG_KCAP;
     float *c_z = c_q + CG_KCAP;
-    int *g_map = reinterpret_cast<int *>(c_z + CG_KCAP);
-    float *gb_r = reinterpret_cast<float *>(g_map + GMAP_CAP);
+    float *gb_r = c_z + CG_KCAP;
     float *gb_x = gb_r + TOEP_LMAX;
     float *gb_u1 = gb_x + TOEP_LMAX;
     float *gb_u2 = gb_u1 + TOEP_LMAX;
@@ -805,8 +838,11 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             }
         }
 
-        // flagged samples owned by this CTA, in sample order (deterministic),
-        // and the gaps (runs of flagged samples) of the detscan
+        // Flagged samples of the detscan, ranked in time order.  The CG
+        // vectors are spread evenly over the cluster: CTA c holds ranks
+        // [c kper, (c+1) kper), each entry with the (owner CTA, element) of
+        // its sample in the transform layout (E and E^T go through DSMEM).
+        // Gaps (runs of flagged samples) are listed in time order.
         const int64_t wb0 = o >> 5, wb1 = (o + n - 1) >> 5;
         const int nw = static_cast<int>(wb1 - wb0 + 1);
         const int per = (nw + DCT_T - 1) / DCT_T;
@@ -819,42 +855,26 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             if (base + 32 > n) bits &= (n - base >= 32) ? ~0u : ((1u << static_cast<int>(n - base)) - 1u);
             return bits;
         };
-        int mycnt = 0, mygaps = 0, myends = 0;
+        int3 mine = make_int3(0, 0, 0);     // flagged samples, gap starts, gap ends
         for (int i = 0; i < per; ++i) {
             const int wi = threadIdx.x * per + i;
             if (wi >= nw) break;
             const uint32_t bits = word_bits(wi);
             const uint32_t prev = word_bits(wi - 1) >> 31;
             const uint32_t next = word_bits(wi + 1) & 1u;
-            mygaps += __popc(bits & ~((bits << 1) | prev));
-            myends += __popc(bits & ~((bits >> 1) | (next << 31)));
-            uint32_t bb = bits;
-            while (bb) {
-                const int b = __popc((bb & (0u - bb)) - 1u);   // index of the lowest set bit
-                bb &= bb - 1;
-                int ow, loc;
-                sample_loc(X, static_cast<int>(((wb0 + wi) << 5) + b - o), ow, loc);
-                if (ow == c) ++mycnt;
-            }
+            mine.x += __popc(bits);
+            mine.y += __popc(bits & ~((bits << 1) | prev));
+            mine.z += __popc(bits & ~((bits >> 1) | (next << 31)));
         }
-        s_scan[threadIdx.x] = mycnt;
-        s_gscan[threadIdx.x] = mygaps;
-        s_escan[threadIdx.x] = myends;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int acc = 0, gacc = 0, eacc = 0;
-            for (int i = 0; i < DCT_T; ++i) {
-                const int v = s_scan[i]; s_scan[i] = acc; acc += v;
-                const int g2 = s_gscan[i]; s_gscan[i] = gacc; gacc += g2;
-                const int e2 = s_escan[i]; s_escan[i] = eacc; eacc += e2;
-            }
-            s_kc = acc;
-            s_ngap = gacc;
-        }
-        __syncthreads();
-        const int kc = s_kc, ngap = s_ngap;
+        int3 tot3;
+        const int3 ex = block_exscan3(mine, s_wscan, tot3);
+        const int kc_all = tot3.x, ngap = tot3.y;
+        const int kper = (kc_all + C - 1) / C;
+        const int k0 = min(kc_all, c * kper);
+        const int kc = min(kc_all, k0 + kper) - k0;     // entries held by this CTA
+        const bool cap_ovf = kper > CG_KCAP;
         {
-            int pos = s_scan[threadIdx.x], gpos = s_gscan[threadIdx.x], epos = s_escan[threadIdx.x];
+            int pos = ex.x, gpos = ex.y, epos = ex.z;
             for (int i = 0; i < per; ++i) {
                 const int wi = threadIdx.x * per + i;
                 if (wi >= nw) break;
@@ -865,7 +885,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                 uint32_t en = bits & ~((bits >> 1) | (next << 31));
                 const int64_t base = ((wb0 + wi) << 5) - o;
                 while (st) {
-                    const int b = __popc((st & (0u - st)) - 1u);
+                    const int b = __popc((st & (0u - st)) - 1u);     // index of the lowest set bit
                     st &= st - 1;
                     if (gpos < GAP_CAP) g_beg[gpos] = static_cast<int>(base + b);
                     ++gpos;
@@ -876,17 +896,18 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                     if (epos < GAP_CAP) g_end[epos] = static_cast<int>(base + b + 1);
                     ++epos;
                 }
+                const int nb = __popc(bits);
+                if (cap_ovf || pos + nb <= k0 || pos >= k0 + kc) { pos += nb; continue; }
                 uint32_t bb = bits;
                 while (bb) {
                     const int b = __popc((bb & (0u - bb)) - 1u);
                     bb &= bb - 1;
-                    int ow, loc;
-                    const int tl = static_cast<int>(base + b);
-                    sample_loc(X, tl, ow, loc);
-                    if (ow == c) {
-                        if (pos < CG_KCAP) { c_loc[pos] = loc; c_t[pos] = tl; }
-                        ++pos;
+                    if (pos >= k0 && pos < k0 + kc) {
+                        int ow, loc;
+                        sample_loc(X, static_cast<int>(base + b), ow, loc);
+                        c_loc[pos - k0] = (ow << 20) | loc;
                     }
+                    ++pos;
                 }
             }
         }
@@ -896,20 +917,20 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
         const bool prec = a.xtab != nullptr && ngap <= GAP_CAP;
         if (prec && threadIdx.x == 0) {
             // split gaps into blocks of at most lmax samples; block b goes to
-            // CTA b mod C; own blocks get consecutive map offsets
-            const int lmax = min(TOEP_LMAX, a.lvalid[det]);
-            int nb = 0, own = 0, ovf = 0;
+            // CTA b mod C with the rank of its first sample
+            const int lmax = max(1, min(TOEP_LMAX, a.lvalid[det]));
+            int nb = 0, ovf = 0, rank = 0;
             for (int g2 = 0; g2 < ngap; ++g2) {
                 for (int b0 = g_beg[g2]; b0 < g_end[g2]; b0 += lmax) {
                     const int len = min(lmax, g_end[g2] - b0);
                     if ((nb % C) == c) {
-                        if (own + len <= GMAP_CAP && s_nown < GAP_CAP) {
-                            o_beg[s_nown] = b0; o_len[s_nown] = len; o_off[s_nown] = own; ++s_nown;
-                            own += len;
+                        if (s_nown < GAP_CAP) {
+                            o_len[s_nown] = len; o_rank[s_nown] = rank; ++s_nown;
                         } else {
                             ovf = 1;
                         }
                     }
+                    rank += len;
                     ++nb;
                 }
             }
@@ -917,40 +938,27 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
         }
         if (!prec && threadIdx.x == 0) s_ovf = 1;
         __syncthreads();
-        const double2 kt = cluster_sum2(make_double2(threadIdx.x == 0 ? static_cast<double>(kc) : 0.0,
-                                                     threadIdx.x == 0 ? ((kc > CG_KCAP ? 1.0 : 0.0) +
-                                                                         (s_ovf ? 1e6 : 0.0)) : 0.0),
-                                        s_red, s_part, parity, cl);
-        const bool use_prec = kt.y < 1e6 - 1.0 ? true : false;
-        const bool cap_ovf = (kt.y - (use_prec ? 0.0 : 1e6)) > 0.5;
+        const double ovf_all = cluster_sum2(make_double2(threadIdx.x == 0 && s_ovf ? 1.0 : 0.0, 0.0),
+                                            s_red, s_part, parity, cl).x;
+        const bool use_prec = ovf_all < 0.5;
         int it = 0;
         bool conv = true;
-        if (kt.x > 0.0 && cap_ovf) {
+        // element i of the CG vectors of this CTA: its sample's value in the
+        // transform buffer U of CTA (c_loc >> 20)
+        auto at = [&](float2 *U, int i) -> float * {
+            const int cl_i = c_loc[i];
+            float *uf = reinterpret_cast<float *>(U) + (cl_i & 0xFFFFF);
+            return cl.map_shared_rank(uf, cl_i >> 20);
+        };
+        // CG vector rank k: (CTA, index)
+        auto rank_ref = [&](float *vec, int k) -> float * {
+            const int ow = k / kper;
+            return cl.map_shared_rank(vec + (k - ow * kper), ow);
+        };
+        if (kc_all > 0 && cap_ovf) {
             conv = false;      // too many flagged samples for the CG buffers: left as x0
             set_status(a.status, q, TOD_ERR_NOT_CONVERGED);
-        } else if (kt.x > 0.0) {
-            // map of own preconditioner blocks: element -> (owner, index); the
-            // owners' sample lists are complete (cluster barrier above)
-            if (use_prec) {
-                for (int bi = 0; bi < s_nown; ++bi) {
-                    const int b0 = o_beg[bi], len = o_len[bi], off = o_off[bi];
-                    for (int u = threadIdx.x; u < len; u += DCT_T) {
-                        const int tl = b0 + u;
-                        int ow, loc;
-                        sample_loc(X, tl, ow, loc);
-                        const int *rt = cl.map_shared_rank(c_t, ow);
-                        int lo = 0, hi = *cl.map_shared_rank(&s_kc, ow);
-                        hi = min(hi, CG_KCAP);
-                        while (lo < hi) {
-                            const int mid = (lo + hi) >> 1;
-                            if (rt[mid] < tl) lo = mid + 1; else hi = mid;
-                        }
-                        g_map[off + u] = (ow << 20) | lo;
-                    }
-                }
-                __syncthreads();
-            }
-            float *curf = reinterpret_cast<float *>(cur);
+        } else if (kc_all > 0) {
             const float *xt_det = a.xtab ? a.xtab + static_cast<int64_t>(det) * (TOEP_LMAX * (TOEP_LMAX + 1) / 2)
                                          : nullptr;
             // z = M^{-1} r: Gohberg-Semencul per own block, scattered to owners
@@ -962,11 +970,10 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                 }
                 cl.sync();     // every CTA's residual is complete before the gathers
                 for (int bi = 0; bi < s_nown; ++bi) {
-                    const int len = o_len[bi], off = o_off[bi];
+                    const int len = o_len[bi], r0 = o_rank[bi];
                     const float *xv = xt_det + static_cast<int64_t>(len) * (len - 1) / 2;
                     for (int u = threadIdx.x; u < len; u += DCT_T) {
-                        const int gm = g_map[off + u];
-                        gb_r[u] = *cl.map_shared_rank(c_r + (gm & 0xFFFFF), gm >> 20);
+                        gb_r[u] = *rank_ref(c_r, r0 + u);
                         gb_x[u] = xv[u];
                     }
                     __syncthreads();
@@ -989,17 +996,17 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                             z1 = fmaf(gb_x[i - j], gb_u1[j], z1);
                             if (j < i) z2 = fmaf(gb_x[len - (i - j)], gb_u2[j], z2);
                         }
-                        const int gm = g_map[off + i];
-                        *cl.map_shared_rank(c_z + (gm & 0xFFFFF), gm >> 20) = (z1 - z2) * inv_x0;
+                        *rank_ref(c_z, r0 + i) = (z1 - z2) * inv_x0;
                     }
                     __syncthreads();
                 }
                 cl.sync();     // every scatter into every CTA's c_z is done
             };
             // rhs = E^T x0 ; y = 0 ; r = rhs ; z = M^{-1} r ; p = z
+            cl.sync();         // x0 is complete in every CTA before the gathers
             double rr_loc = 0.0;
             for (int i = threadIdx.x; i < kc; i += DCT_T) {
-                const float v = curf[c_loc[i]];
+                const float v = *at(cur, i);
                 c_y[i] = 0.f; c_r[i] = v;
                 rr_loc += static_cast<double>(v) * v;
             }
@@ -1018,17 +1025,16 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             while (!conv && it < a.maxit) {
                 // cur <- C^T diag(gamma) C E p
                 for (int e = threadIdx.x; e < tot; e += DCT_T) cur[e] = make_float2(0.f, 0.f);
-                __syncthreads();
-                curf = reinterpret_cast<float *>(cur);
-                for (int i = threadIdx.x; i < kc; i += DCT_T) curf[c_loc[i]] = c_p[i];
-                __syncthreads();
+                cl.sync();     // every buffer is zero before the scatters
+                for (int i = threadIdx.x; i < kc; i += DCT_T) *at(cur, i) = c_p[i];
+                cl.sync();     // every scatter has landed
                 dct_forward(X, cur, oth, sm.tw1, sm.tw2, cl);
                 apply_filter(X, cur, fscale, alpha, s2, 1, wt);
                 dct_inverse(X, cur, oth, sm.tw1, sm.tw2, cl);
-                curf = reinterpret_cast<float *>(cur);
+                cl.sync();     // every CTA's result is complete before the gathers
                 double pq_loc = 0.0;
                 for (int i = threadIdx.x; i < kc; i += DCT_T) {
-                    const float v = curf[c_loc[i]];
+                    const float v = *at(cur, i);
                     c_q[i] = v;
                     pq_loc += static_cast<double>(c_p[i]) * v;
                 }
@@ -1055,10 +1061,9 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             }
             // x = x0 + B^{-1} E y
             for (int e = threadIdx.x; e < tot; e += DCT_T) cur[e] = make_float2(0.f, 0.f);
-            __syncthreads();
-            curf = reinterpret_cast<float *>(cur);
-            for (int i = threadIdx.x; i < kc; i += DCT_T) curf[c_loc[i]] = c_y[i];
-            __syncthreads();
+            cl.sync();
+            for (int i = threadIdx.x; i < kc; i += DCT_T) *at(cur, i) = c_y[i];
+            cl.sync();
             dct_forward(X, cur, oth, sm.tw1, sm.tw2, cl);
             apply_filter(X, cur, fscale, alpha, s2, 0, wt);
             dct_inverse(X, cur, oth, sm.tw1, sm.tw2, cl);
@@ -1207,8 +1212,8 @@ __global__ void __launch_bounds__(DCT_T, 1) k_chi2(Chi2Args a)
 static size_t smem_bytes(const Plan &p, bool ncorr)
 {
     size_t b = sizeof(float2) * (2 * static_cast<size_t>(p.sz) + p.twsz);
-    if (ncorr) b += static_cast<size_t>(CG_KCAP) * (2 * sizeof(int) + 5 * sizeof(float)) +
-                    sizeof(int) * GMAP_CAP + sizeof(float) * 4 * TOEP_LMAX;
+    if (ncorr) b += static_cast<size_t>(CG_KCAP) * (sizeof(int) + 5 * sizeof(float)) +
+                    sizeof(float) * 4 * TOEP_LMAX;
     return b;
 }
 
@@ -1304,13 +1309,23 @@ cudaError_t launch_ncorr(const Plan &p, const float *d, const float *s, const do
                          float tol, int maxit, float *x, int32_t *iters, cudaStream_t st,
                          int work_begin, int work_count)
 {
+    return launch_ncorr_scratch(p, d, s, gain, flags, psd, rng, mode, tol, maxit, x, iters, st,
+                                work_begin, work_count, p.wscratch, p.nclusters_ncorr);
+}
+
+cudaError_t launch_ncorr_scratch(const Plan &p, const float *d, const float *s, const double *gain,
+                                 const uint32_t *flags, const double *psd, tod_rng rng, int mode,
+                                 float tol, int maxit, float *x, int32_t *iters, cudaStream_t st,
+                                 int work_begin, int work_count, float4 *scratch, int nclusters_max)
+{
     if (work_count <= 0) return cudaSuccess;
+    if (nclusters_max < 1) return cudaErrorInvalidValue;
     NcorrArgs a;
     a.d = d; a.s = s; a.gain = gain; a.flags = flags; a.psd = psd; a.off = p.off; a.plans = p.plans;
     a.q_plan = p.q_plan; a.tw = p.tw; a.work = p.work; a.work_begin = work_begin;
     a.work_count = work_count; a.ndet = p.ndet; a.fsamp = p.fsamp; a.rng = rng; a.mode = mode;
     a.tol = tol; a.maxit = maxit; a.x_out = x; a.iters = iters; a.status = p.status; a.sz = p.sz;
-    a.wscratch = p.wscratch;
+    a.wscratch = scratch;
     a.xtab = p.use_prec ? p.xtab : nullptr;
     a.lvalid = p.lvalid;
     if (p.use_prec) {
@@ -1327,7 +1342,7 @@ cudaError_t launch_ncorr(const Plan &p, const float *d, const float *s, const do
         }
         return cudaSuccess;
     }
-    const int ncl = std::min(work_count, p.nclusters_ncorr);
+    const int ncl = std::min(work_count, std::min(p.nclusters_ncorr, nclusters_max));
     return launch_cluster(reinterpret_cast<const void *>(k_ncorr), &a, p.C, ncl, p.smem_ncorr, st);
 }
 

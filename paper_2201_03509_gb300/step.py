@@ -57,7 +57,7 @@ class GibbsTODStep:
         p.solve_maps(self.A, self.b, self.hits, self.rcond_min, self.map, self.map32, self.rcond,
                      self.valid, stream)
 
-    LAUNCHES_PER_STEP = 8   # decode x2, project, gain, ncorr, bin + reduce, solve
+    LAUNCHES_PER_STEP = 10  # decode x2, project, gain, Toeplitz prep x2, ncorr, bin + reduce, solve
 
     def capture(self, map32_in, seed: int, band: int = 0, mode: int = MODE_DRAW):
         """Capture one step into a CUDA graph.  The Gibbs iteration is read by
