@@ -51,6 +51,7 @@ typedef int32_t tod_status;
 #define TOD_ERR_CUDA          -5   /* a CUDA runtime call failed */
 #define TOD_ERR_OOM           -6   /* device or host allocation failed */
 #define TOD_ERR_UNIMPLEMENTED -7
+#define TOD_ERR_SCRATCH       -8   /* the plan needs more scratch than a fixed array holds */
 
 #define TOD_MODE_DRAW 0   /* sample from the conditional */
 #define TOD_MODE_MEAN 1   /* conditional mean: all normals set to zero */
@@ -218,6 +219,41 @@ tod_status tod_sample_ncorr(tod_plan *p, const float *d, const float *s,
                             double cg_tol, int32_t cg_maxiter,
                             float *ncorr_out, int32_t *cg_iters_out,
                             cudaStream_t stream);
+
+/* tod_sample_ncorr_static -- tod_sample_ncorr with nothing allocated.
+ * The paper has no counterpart: it is a library convenience.  Same
+ * arguments, results and errors as tod_sample_ncorr, except that the
+ * per-cluster filter-weight scratch comes from one fixed device array
+ * compiled into the library (TOD_NCORR_STATIC_SCRATCH_BYTES per device)
+ * instead of the plan's buffer.  It is for callers that must not allocate
+ * device memory once they run: a process whose free device memory is all
+ * held by another allocator's pool (so a new allocation fails or forces that
+ * pool to release), or a pipeline whose policy forbids allocation after
+ * start-up.  The call never calls an allocating routine.
+ *   Set-up: call tod_ncorr_static_setup once per device, with the plan, on
+ *   the host before the first draw and before any stream capture; it looks
+ *   up the array's device address (cudaGetSymbolAddress on the plan's
+ *   device) and caches it.  A first draw without it does the lookup itself.
+ *   Size: each cluster of the draw needs C x sz x 16 bytes (C the cluster
+ *   size, sz the plan's per-CTA transform buffer); the draw runs with as
+ *   many clusters as fit (fewer than tod_sample_ncorr may use, so it can be
+ *   slower) and returns TOD_ERR_SCRATCH, enqueuing nothing, when not even
+ *   one cluster fits.  The setup call reports the cluster count that fits
+ *   in *max_clusters_out (may be NULL) and returns TOD_ERR_SCRATCH likewise.
+ *   Contents: every cluster writes its weights before it reads them, so no
+ *   part of the array must start at zero.
+ *   Concurrency: all plans and streams on one device share the array; two
+ *   calls that can overlap on the device (different streams, or host
+ *   threads without ordering) race on it and give wrong results.  Serialise
+ *   them on one stream. */
+#define TOD_NCORR_STATIC_SCRATCH_BYTES (32u << 20)
+tod_status tod_ncorr_static_setup(tod_plan *p, int32_t *max_clusters_out);
+tod_status tod_sample_ncorr_static(tod_plan *p, const float *d, const float *s,
+                                   const double *gain, const uint32_t *flags,
+                                   const double *psd, tod_rng rng, int32_t mode,
+                                   double cg_tol, int32_t cg_maxiter,
+                                   float *ncorr_out, int32_t *cg_iters_out,
+                                   cudaStream_t stream);
 
 /* A6 -- binning (Sect. 5 table, "TOD binning"; Sect. 2.4: coadded during
  * the pass over chunks).  With r'_t = d_t - ncorr_t, w_t = M_t / sigma0^2:

@@ -66,7 +66,7 @@ _lib = None
 SYMBOLS = ["tod_status_string", "tod_fft_length", "tod_huff_encode", "tod_huff_free",
            "tod_plan_create", "tod_plan_destroy", "tod_plan_info", "tod_plan_status",
            "tod_plan_set_schedule", "tod_chi2", "tod_decode", "tod_project", "tod_sample_gain", "tod_sample_ncorr", "tod_bin",
-           "tod_solve_maps"]
+           "tod_solve_maps", "tod_ncorr_static_setup", "tod_sample_ncorr_static"]
 
 
 def build(force: bool = False) -> str:
@@ -102,6 +102,8 @@ def lib():
         L.tod_bin.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
         L.tod_solve_maps.argtypes = [_P, _P, _P, _P, _f64, _P, _P, _P, _P, _P]
         L.tod_chi2.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
+        L.tod_ncorr_static_setup.argtypes = [_P, _P]
+        L.tod_sample_ncorr_static.argtypes = [_P, _P, _P, _P, _P, _P, Rng, _i32, _f64, _i32, _P, _P, _P]
         for name in SYMBOLS:
             if name not in ("tod_status_string", "tod_fft_length", "tod_huff_free"):
                 getattr(L, name).restype = _i32
@@ -281,6 +283,21 @@ class Plan:
         _check(lib().tod_sample_ncorr(self._h, _ptr(d), _ptr(s), _ptr(gain), _ptr(flags), _ptr(psd),
                                       rng, mode, float(cg_tol), int(cg_maxiter), _ptr(ncorr_out),
                                       _ptr(cg_iters_out), _stream(stream)), "tod_sample_ncorr")
+
+    def ncorr_static_setup(self) -> int:
+        """Look up the fixed scratch array of sample_ncorr_static on this
+        plan's device; returns how many clusters fit in it."""
+        n = _i32()
+        _check(lib().tod_ncorr_static_setup(self._h, ctypes.byref(n)), "tod_ncorr_static_setup")
+        return n.value
+
+    def sample_ncorr_static(self, d, s, gain, flags, psd, rng: Rng, mode, ncorr_out, cg_iters_out=None,
+                            cg_tol: float = 0.0, cg_maxiter: int = 0, stream=None):
+        """sample_ncorr with its scratch in the library's fixed device array
+        (allocates nothing; calls on one device must not overlap)."""
+        _check(lib().tod_sample_ncorr_static(self._h, _ptr(d), _ptr(s), _ptr(gain), _ptr(flags), _ptr(psd),
+                                             rng, mode, float(cg_tol), int(cg_maxiter), _ptr(ncorr_out),
+                                             _ptr(cg_iters_out), _stream(stream)), "tod_sample_ncorr_static")
 
     def bin(self, psi, d, ncorr, gain, flags, psd, A_out, b_out, hits_out, stream=None):
         _check(lib().tod_bin(self._h, _ptr(psi), _ptr(d), _ptr(ncorr), _ptr(gain), _ptr(flags),

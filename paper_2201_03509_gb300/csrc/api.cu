@@ -391,6 +391,7 @@ const char *tod_status_string(tod_status s)
     case TOD_ERR_CUDA: return "CUDA runtime error";
     case TOD_ERR_OOM: return "out of memory";
     case TOD_ERR_UNIMPLEMENTED: return "not implemented";
+    case TOD_ERR_SCRATCH: return "fixed scratch array too small for this plan";
     default: return "unknown status";
     }
 }
