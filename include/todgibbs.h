@@ -136,7 +136,7 @@ typedef struct {
     const int64_t *offsets; /* HOST [ndet*nscan+1]; every length an FFT length */
     tod_huff_streams pix;   /* HOST compressed pixel stream */
     tod_huff_streams psi;   /* HOST compressed psi-bin stream */
-    int32_t cluster_size;   /* 0 = choose; else 1, 2, 4, 8 or 16 CTAs per detscan transform */
+    int32_t cluster_size;   /* 0 = choose (most SMs busy); else 1..16 CTAs per detscan transform */
     int32_t device;         /* CUDA device ordinal the plan lives on */
 } tod_band_desc;
 

@@ -536,7 +536,7 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
         band->n_psi != TOD_N_PSI || !(band->fsamp > 0) || !band->offsets)
         return TOD_ERR_ARG;
     const int cs = band->cluster_size;
-    if (cs != 0 && cs != 1 && cs != 2 && cs != 4 && cs != 8 && cs != 16) return TOD_ERR_ARG;
+    if (cs < 0 || cs > 16) return TOD_ERR_ARG;
     Plan *p = new (std::nothrow) Plan();
     if (!p) return TOD_ERR_OOM;
     p->device = band->device;
@@ -606,20 +606,22 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
         std::vector<int> uniq(lens);
         std::sort(uniq.begin(), uniq.end());
         uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+        // Cluster size: every C in 1..16 whose per-CTA buffers, twiddle block
+        // and CG areas fit in shared memory is scored by the SMs it keeps
+        // busy (C x co-resident clusters, which depends on how clusters pack
+        // into the GPCs); the best score wins, ties to the smaller C.
         std::vector<DctPlan> plans;
-        int chosenC = 0;
-        const int cands[5] = {1, 2, 4, 8, 16};
-        for (int ci = 0; ci < 5 && !chosenC; ++ci) {
-            const int C = cands[ci];
+        int chosenC = 0, best_sms = 0;
+        for (int C = 1; C <= 16; ++C) {
             if (cs && C != cs) continue;
-            plans.clear();
+            std::vector<DctPlan> cand;
             int sz = 0, m1max = 0, m2max = 0;
             bool ok = true;
             for (int n : uniq) {
                 DctPlan dp;
                 int s = 0;
                 if (!choose_factor(n, C, dp, s)) { ok = false; break; }
-                plans.push_back(dp);
+                cand.push_back(dp);
                 sz = std::max(sz, s);
                 m1max = std::max(m1max, dp.m1);
                 m2max = std::max(m2max, dp.m2);
@@ -627,12 +629,19 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
             if (!ok) continue;
             // twiddle block: 3 (m1 + m2) + m/64 + 65 complex values
             int twmax = 0;
-            for (auto &dp : plans) twmax = std::max(twmax, 3 * (dp.m1 + dp.m2) + dp.m / 64 + 65);
-            const size_t smem = sizeof(float2) * (2 * static_cast<size_t>(sz) + twmax) +
-                                static_cast<size_t>(CG_KCAP) * 24 + sizeof(float) * 4 * TOEP_LMAX + 12288;
-            if (smem > 227 * 1024) continue;
-            chosenC = C;
-            p->sz = sz; p->m1max = m1max; p->m2max = m2max;
+            for (auto &dp : cand) twmax = std::max(twmax, 3 * (dp.m1 + dp.m2) + dp.m / 64 + 65);
+            const size_t smem_dyn = sizeof(float2) * (2 * static_cast<size_t>(sz) + twmax) +
+                                    static_cast<size_t>(CG_KCAP) * 24 + sizeof(float) * 4 * TOEP_LMAX;
+            if (smem_dyn + 12288 > 227 * 1024) continue;
+            int ncl = 0;
+            if ((e = transform_cluster_occupancy(C, smem_dyn, &ncl))) return fail(e);
+            if (ncl < 1) continue;
+            if (C * ncl > best_sms) {
+                best_sms = C * ncl;
+                chosenC = C;
+                plans.swap(cand);
+                p->sz = sz; p->m1max = m1max; p->m2max = m2max;
+            }
         }
         if (!chosenC) { free_plan(p); return TOD_ERR_ARG; }
         p->C = chosenC;

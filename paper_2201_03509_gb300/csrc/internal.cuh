@@ -117,6 +117,9 @@ cudaError_t launch_decode(const Plan &p, const HuffDev &h, int32_t *pix_out, uin
 cudaError_t launch_project(const Plan &p, const float4 *map, const int32_t *pix, const uint16_t *psi,
                            const double *gain, float *s_out, cudaStream_t st);
 cudaError_t setup_dct_kernels(Plan &p);
+// co-resident clusters of C CTAs of the n_corr kernel with smem_dyn bytes of
+// dynamic shared memory each (0 if none fits)
+cudaError_t transform_cluster_occupancy(int C, size_t smem_dyn, int *nclusters);
 cudaError_t launch_gain(const Plan &p, const float *d, const float *s, const uint32_t *flags,
                         const double *psd, tod_rng rng, int mode, double *g, double *mu,
                         double *sig, cudaStream_t st, int work_begin, int work_count);

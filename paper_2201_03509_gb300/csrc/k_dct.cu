@@ -171,7 +171,7 @@ __device__ void fft_seq(float2 *&cur, float2 *&oth, int L, const DctStage *stage
 // per-detscan transform context (shared memory copy of the plan + this CTA's
 // share of it)
 // ---------------------------------------------------------------------------
-struct Ctx {
+struct Geo {
     int n, m, m1, m2, ncolmax, npmax, P;
     int nr1, nr2;
     int c, C;
@@ -182,10 +182,15 @@ struct Ctx {
     const float2 *tw1, *tw2;            // W_{m1}^i, W_{m2}^i
     const float2 *sa1, *sb1, *sa5, *sb5;// W_{4n}^{k1}, W_{4n}^{m1 k2}, W_{4n}^{5 k1}, W_{4n}^{5 m1 k2}
     const float2 *t4hi, *t4lo;          // W_m^{64 i}, W_m^i (i < 64)
+};
+// The shared-memory copy adds the radix stages.  Device code copies the
+// Geo part into registers (a local value) before its loops, so stores to
+// the transform buffers cannot force the scalars to be reloaded.
+struct Ctx : Geo {
     DctStage s1[DCT_MAXR], s2[DCT_MAXR];
 };
 
-__device__ __forceinline__ int slot_row(const Ctx &X, int slot) {
+__device__ __forceinline__ int slot_row(const Geo &X, int slot) {
     const int p = X.p0 + (slot >> 1);
     if (p >= X.P) return -1;
     if ((slot & 1) == 0) return p;
@@ -198,13 +203,13 @@ __device__ __forceinline__ int slot_row(const Ctx &X, int slot) {
 __device__ __forceinline__ int vpos_t(int i, int n, int m) { return i < m ? 2 * i : 2 * n - 1 - 2 * i; }
 
 // W_m^{r}, 0 <= r < m, from the two-level table (one complex multiply)
-__device__ __forceinline__ float2 tw4_lookup(const Ctx &X, int r) {
+__device__ __forceinline__ float2 tw4_lookup(const Geo &X, int r) {
     return cmul(X.t4hi[r >> 6], X.t4lo[r & 63]);
 }
 
 // Forward half-split: packed orthonormal coefficients of slot k from Z_k,
 // Z_{m-k}: W = e^{-i pi k/2n} A + e^{-i 5 pi k/2n} B, with k = k1 + m1 k2.
-__device__ __forceinline__ float2 split_fwd_one(const Ctx &X, float2 a, float2 b, int k1, int k2, float sq) {
+__device__ __forceinline__ float2 split_fwd_one(const Geo &X, float2 a, float2 b, int k1, int k2, float sq) {
     const float2 cb = cconj(b);
     const float2 A = cscale(cadd(a, cb), 0.5f);
     const float2 d = csub(a, cb);
@@ -214,7 +219,7 @@ __device__ __forceinline__ float2 split_fwd_one(const Ctx &X, float2 a, float2 b
     return make_float2(sq * W.x, -sq * W.y);
 }
 // Inverse of the half-split: Z_k from the packed slots k and m-k.
-__device__ __forceinline__ float2 split_inv_one(const Ctx &X, float2 yk, float2 yp, int k1, int k2, int q1,
+__device__ __forceinline__ float2 split_inv_one(const Geo &X, float2 yk, float2 yp, int k1, int k2, int q1,
                                                 int q2, float sq) {
     // V_k = sqrt(n/2) e^{i pi k/2n} conj(Y_k)   (sq carries sqrt(n/2)/m)
     const float2 ek = cmul(X.sa1[k1], X.sb1[k2]), ep = cmul(X.sa1[q1], X.sb1[q2]);
@@ -229,7 +234,7 @@ __device__ __forceinline__ float2 split_inv_one(const Ctx &X, float2 yk, float2 
 
 // Real split over this CTA's row pairs, in place (forward or inverse).
 template <bool INV>
-__device__ __noinline__ void split_pass(const Ctx &X, float2 *U)
+__device__ __noinline__ void split_pass(const Geo X, float2 *__restrict__ U)
 {
     const int m2 = X.m2, m1 = X.m1, m = X.m, n = X.n, p0 = X.p0;
     const float sq = INV ? static_cast<float>(sqrt(0.5 * n) / m) : static_cast<float>(sqrt(2.0 / n));
@@ -276,7 +281,8 @@ __device__ __noinline__ void split_pass(const Ctx &X, float2 *U)
 // first cluster barrier makes every CTA's src complete; the second keeps
 // src alive until every remote read of it has finished.
 template <bool INV>
-__device__ __noinline__ void transpose(const Ctx &X, const float2 *src, float2 *dst, cg::cluster_group &cl)
+__device__ __noinline__ void transpose(const Geo X, const float2 *src, float2 *__restrict__ dst,
+                                       cg::cluster_group &cl)
 {
     constexpr int U = 4;     // independent remote reads in flight per thread
     const int m = X.m, m1 = X.m1, m2 = X.m2, ncolmax = X.ncolmax, npmax = X.npmax;
@@ -341,32 +347,34 @@ __device__ __noinline__ void transpose(const Ctx &X, const float2 *src, float2 *
 
 // Forward DCT: time layout in cur -> packed spectrum in cur (the two
 // buffers may swap roles).
-__device__ __noinline__ void dct_forward(const Ctx &X, float2 *&cur, float2 *&oth, const float2 *,
+__device__ __noinline__ void dct_forward(const Ctx &XS, float2 *&cur, float2 *&oth, const float2 *,
                                          const float2 *, cg::cluster_group &cl)
 {
+    const Geo X = XS;
     const float2 *tw1 = X.tw1, *tw2 = X.tw2;
-    fft_seq<false>(cur, oth, X.m1, X.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, tw1);
+    fft_seq<false>(cur, oth, X.m1, XS.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, tw1);
     transpose<false>(X, cur, oth, cl);
     { float2 *t = cur; cur = oth; oth = t; }
-    fft_seq<false>(cur, oth, X.m2, X.s2, X.nr2, 2 * X.npl, X.f_m2, 1, X.m2, false, tw2);
+    fft_seq<false>(cur, oth, X.m2, XS.s2, X.nr2, 2 * X.npl, X.f_m2, 1, X.m2, false, tw2);
     split_pass<false>(X, cur);
 }
 // Inverse (transpose of the orthonormal DCT-II): packed spectrum in cur ->
 // time layout in cur, scaled.
-__device__ __noinline__ void dct_inverse(const Ctx &X, float2 *&cur, float2 *&oth, const float2 *,
+__device__ __noinline__ void dct_inverse(const Ctx &XS, float2 *&cur, float2 *&oth, const float2 *,
                                          const float2 *, cg::cluster_group &cl)
 {
+    const Geo X = XS;
     const float2 *tw1 = X.tw1, *tw2 = X.tw2;
     split_pass<true>(X, cur);
-    fft_seq<true>(cur, oth, X.m2, X.s2, X.nr2, 2 * X.npl, X.f_m2, 1, X.m2, false, tw2);
+    fft_seq<true>(cur, oth, X.m2, XS.s2, X.nr2, 2 * X.npl, X.f_m2, 1, X.m2, false, tw2);
     transpose<true>(X, cur, oth, cl);
     { float2 *t = cur; cur = oth; oth = t; }
-    fft_seq<true>(cur, oth, X.m1, X.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, tw1);
+    fft_seq<true>(cur, oth, X.m1, XS.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, tw1);
 }
 
 // Fill U (time layout) with f(j) = (x_{t(2j)}, x_{t(2j+1)}) for own columns.
 template <class F>
-__device__ void load_time(const Ctx &X, float2 *U, F f)
+__device__ void load_time(const Geo &X, float2 *__restrict__ U, F f)
 {
     constexpr int UB = 4;
     const int total = X.m1 * X.ncolmax;
@@ -484,7 +492,7 @@ __device__ void load_plan(Ctx *sX, const DctPlan *plans, int pi, const float2 *t
 }
 
 // element e of the time layout -> (t0, t1) samples
-__device__ __forceinline__ void elem_samples(const Ctx &X, int e, int &t0, int &t1, bool &valid)
+__device__ __forceinline__ void elem_samples(const Geo &X, int e, int &t0, int &t1, bool &valid)
 {
     const int j1 = fdiv(e, X.f_ncolmax), lc = e - j1 * X.ncolmax;
     valid = lc < X.ncol;
@@ -493,7 +501,7 @@ __device__ __forceinline__ void elem_samples(const Ctx &X, int e, int &t0, int &
     t1 = vpos_t(2 * j + 1, X.n, X.m);
 }
 // sample t -> (owner CTA, element, part)
-__device__ __forceinline__ void sample_loc(const Ctx &X, int t, int &owner, int &loc)
+__device__ __forceinline__ void sample_loc(const Geo &X, int t, int &owner, int &loc)
 {
     // position of sample t in the even-then-reversed-odd order: t/2 for even
     // t, n-1-(t-1)/2 = n-1-floor(t/2) for odd t
@@ -515,7 +523,7 @@ __device__ __forceinline__ void sample_loc(const Ctx &X, int t, int &owner, int 
 // E^T C^T diag(gamma) C E carries no FP32 cancellation on its small modes.
 // Kinds 0 and 1 read (beta_a, beta_b, gamma_a, gamma_b) per packed element
 // from wt, filled once per detscan by fill_weights.
-__device__ __noinline__ void apply_filter(const Ctx &X, float2 *U, float fscale, float alpha, float s2,
+__device__ __noinline__ void apply_filter(const Geo X, float2 *__restrict__ U, float fscale, float alpha, float s2,
                                           int kind, const float4 *__restrict__ wt)
 {
     const int total = 2 * X.npl * X.m2;
@@ -587,7 +595,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_gain(GainArgs a)
         const int det = q % a.ndet;
         const int64_t o = a.off[q];
         load_plan(&sX, a.plans, a.q_plan[q], a.tw, sm, c, C);
-        const Ctx &X = sX;
+        const Geo X = sX;
         const int n = X.n, m = X.m;
         const float *sq = a.s + o, *dq = a.d + o;
         const uint32_t *fl = a.flags;
@@ -596,13 +604,14 @@ __global__ void __launch_bounds__(DCT_T, 1) k_gain(GainArgs a)
         const float alpha = static_cast<float>(al);
         const float s2 = static_cast<float>(sig0 * sig0);
         float2 *cur = sm.U0, *oth = sm.U1;
-        // a from C(M s)
+        // shat = C(M s); a = sum_k shat_k^2 / P_k; then u = C^T(shat / P) and
+        // b = sum_t M_t d_t u_t = sum_k shat_k dhat_k / P_k (two transforms)
         load_time(X, cur, [&](int j) {
             const int t0 = vpos_t(2 * j, n, m), t1 = vpos_t(2 * j + 1, n, m);
             const float v0 = __ldg(sq + t0), v1 = __ldg(sq + t1);      // independent of the flags
             return make_float2(flagged(fl, o + t0) ? 0.f : v0, flagged(fl, o + t1) ? 0.f : v1);
         });
-        dct_forward(X, cur, oth, sm.tw1, sm.tw2, cl);
+        dct_forward(sX, cur, oth, sm.tw1, sm.tw2, cl);
         Acc2 sa = {0.f, 0.f}, sb = {0.f, 0.f};
         {
             const int total = 2 * X.npl * X.m2;
@@ -613,20 +622,16 @@ __global__ void __launch_bounds__(DCT_T, 1) k_gain(GainArgs a)
                 const int k = k1 + X.m1 * k2;
                 const float2 S = cur[e];
                 const int ka = k, kb = (k == 0) ? m : n - k;
-                if (ka != 0) acc_add(sa, S.x * S.x / (s2 * (1.0f + fratio_pow(ka, fscale, alpha))));
-                acc_add(sa, S.y * S.y / (s2 * (1.0f + fratio_pow(kb, fscale, alpha))));
+                const float wa = ka == 0 ? 0.f : 1.0f / (s2 * (1.0f + fratio_pow(ka, fscale, alpha)));
+                const float wb = 1.0f / (s2 * (1.0f + fratio_pow(kb, fscale, alpha)));
+                const float2 W = make_float2(S.x * wa, S.y * wb);
+                acc_add_prod(sa, S.x, W.x);
+                acc_add_prod(sa, S.y, W.y);
+                cur[e] = W;
             }
         }
         __syncthreads();
-        // b from <M s, C^T diag(1/P) C M d>
-        load_time(X, cur, [&](int j) {
-            const int t0 = vpos_t(2 * j, n, m), t1 = vpos_t(2 * j + 1, n, m);
-            const float v0 = __ldg(dq + t0), v1 = __ldg(dq + t1);
-            return make_float2(flagged(fl, o + t0) ? 0.f : v0, flagged(fl, o + t1) ? 0.f : v1);
-        });
-        dct_forward(X, cur, oth, sm.tw1, sm.tw2, cl);
-        apply_filter(X, cur, fscale, alpha, s2, 2, nullptr);
-        dct_inverse(X, cur, oth, sm.tw1, sm.tw2, cl);
+        dct_inverse(sX, cur, oth, sm.tw1, sm.tw2, cl);
         {
             const int tot = X.m1 * X.ncolmax;
             for (int e = threadIdx.x; e < tot; e += DCT_T) {
@@ -635,8 +640,8 @@ __global__ void __launch_bounds__(DCT_T, 1) k_gain(GainArgs a)
                 elem_samples(X, e, t0, t1, valid);
                 if (!valid) continue;
                 const float2 v = cur[e];
-                if (!flagged(fl, o + t0)) acc_add_prod(sb, sq[t0], v.x);
-                if (!flagged(fl, o + t1)) acc_add_prod(sb, sq[t1], v.y);
+                if (!flagged(fl, o + t0)) acc_add_prod(sb, __ldg(dq + t0), v.x);
+                if (!flagged(fl, o + t1)) acc_add_prod(sb, __ldg(dq + t1), v.y);
             }
         }
         const double2 ab = cluster_sum2(make_double2(acc_value(sa), acc_value(sb)), s_red, s_part,
@@ -769,7 +774,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
         const int64_t o = a.off[q];
         load_plan(&sX, a.plans, a.q_plan[q], a.tw, sm, c, C);
         if (threadIdx.x == 0) s_nown = 0;
-        const Ctx &X = sX;
+        const Ctx &X = sX;     // read from shared memory: registers are scarce here
         const int n = X.n, m = X.m;
         const double sig0 = a.psd[3 * det], fk = a.psd[3 * det + 1], al = a.psd[3 * det + 2];
         const float fscale = static_cast<float>(a.fsamp / (2.0 * n * fk));
@@ -796,7 +801,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             const float r1 = flagged(fl, o + t1) ? 0.f : fmaf(d1 - g * s1v, inv_s2, w1.y * inv_s);
             return make_float2(r0, r1);
         });
-        dct_forward(X, cur, oth, sm.tw1, sm.tw2, cl);
+        dct_forward(sX, cur, oth, sm.tw1, sm.tw2, cl);
         // + sqrt(phi) w2, times beta; the filter weights of this detscan
         // (beta, gamma for both modes of each packed slot) go to wt once
         {
@@ -823,7 +828,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             }
             __syncthreads();
         }
-        dct_inverse(X, cur, oth, sm.tw1, sm.tw2, cl);      // cur = x0 (time layout)
+        dct_inverse(sX, cur, oth, sm.tw1, sm.tw2, cl);      // cur = x0 (time layout)
         // x0 -> x_out
         {
             const int tot = X.m1 * X.ncolmax;
@@ -1028,9 +1033,9 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                 cl.sync();     // every buffer is zero before the scatters
                 for (int i = threadIdx.x; i < kc; i += DCT_T) *at(cur, i) = c_p[i];
                 cl.sync();     // every scatter has landed
-                dct_forward(X, cur, oth, sm.tw1, sm.tw2, cl);
+                dct_forward(sX, cur, oth, sm.tw1, sm.tw2, cl);
                 apply_filter(X, cur, fscale, alpha, s2, 1, wt);
-                dct_inverse(X, cur, oth, sm.tw1, sm.tw2, cl);
+                dct_inverse(sX, cur, oth, sm.tw1, sm.tw2, cl);
                 cl.sync();     // every CTA's result is complete before the gathers
                 double pq_loc = 0.0;
                 for (int i = threadIdx.x; i < kc; i += DCT_T) {
@@ -1064,9 +1069,9 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             cl.sync();
             for (int i = threadIdx.x; i < kc; i += DCT_T) *at(cur, i) = c_y[i];
             cl.sync();
-            dct_forward(X, cur, oth, sm.tw1, sm.tw2, cl);
+            dct_forward(sX, cur, oth, sm.tw1, sm.tw2, cl);
             apply_filter(X, cur, fscale, alpha, s2, 0, wt);
-            dct_inverse(X, cur, oth, sm.tw1, sm.tw2, cl);
+            dct_inverse(sX, cur, oth, sm.tw1, sm.tw2, cl);
             for (int e = threadIdx.x; e < tot; e += DCT_T) {
                 int t0, t1;
                 bool valid;
@@ -1126,7 +1131,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_chi2(Chi2Args a)
         const int det = q % a.ndet;
         const int64_t o = a.off[q];
         load_plan(&sX, a.plans, a.q_plan[q], a.tw, sm, c, C);
-        const Ctx &X = sX;
+        const Geo X = sX;
         const int n = X.n, m = X.m;
         const float *sq = a.s + o, *dq = a.d + o;
         const uint32_t *fl = a.flags;
@@ -1141,7 +1146,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_chi2(Chi2Args a)
             const float d0 = __ldg(dq + t0), d1 = __ldg(dq + t1), s0v = __ldg(sq + t0), s1v = __ldg(sq + t1);
             return make_float2(flagged(fl, o + t0) ? 0.f : d0 - g * s0v, flagged(fl, o + t1) ? 0.f : d1 - g * s1v);
         });
-        dct_forward(X, cur, oth, X.tw1, X.tw2, cl);
+        dct_forward(sX, cur, oth, X.tw1, X.tw2, cl);
         // per mode: rhat^2/P, ln(1+x), and the f_knee / alpha gradient terms
         Acc2 aq = {0.f, 0.f}, al1 = {0.f, 0.f}, afk = {0.f, 0.f}, aal = {0.f, 0.f};
         {
@@ -1174,7 +1179,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_chi2(Chi2Args a)
             }
             __syncthreads();
         }
-        dct_inverse(X, cur, oth, X.tw1, X.tw2, cl);
+        dct_inverse(sX, cur, oth, X.tw1, X.tw2, cl);
         Acc2 ag = {0.f, 0.f};
         {
             const int tot = X.m1 * X.ncolmax;
@@ -1255,25 +1260,56 @@ static cudaError_t max_clusters(const void *fn, int C, size_t smem, int *out)
     return e;
 }
 
+// Function attributes that do not depend on a plan: the largest dynamic
+// shared memory the device allows next to each kernel's static part, and
+// cluster sizes above the portable 8.  Set for the current device.
+static cudaError_t init_transform_kernels()
+{
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const void *fns[3] = {reinterpret_cast<const void *>(k_gain), reinterpret_cast<const void *>(k_ncorr),
+                          reinterpret_cast<const void *>(k_chi2)};
+    for (const void *fn : fns) {
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, fn);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - static_cast<int>(fa.sharedSizeBytes));
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t transform_cluster_occupancy(int C, size_t smem_dyn, int *nclusters)
+{
+    cudaError_t e = init_transform_kernels();
+    if (e != cudaSuccess) return e;
+    *nclusters = 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(C * 64));
+    cfg.blockDim = dim3(DCT_T);
+    cfg.dynamicSmemBytes = smem_dyn;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(nclusters, reinterpret_cast<const void *>(k_ncorr), &cfg);
+}
+
 cudaError_t setup_dct_kernels(Plan &p)
 {
     p.smem_gain = smem_bytes(p, false);
     p.smem_ncorr = smem_bytes(p, true);
-    cudaError_t e;
-    e = cudaFuncSetAttribute(k_gain, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(p.smem_gain));
+    cudaError_t e = init_transform_kernels();
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_ncorr, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(p.smem_ncorr));
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_chi2, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(p.smem_gain));
-    if (e != cudaSuccess) return e;
-    if (p.C > 8) {
-        e = cudaFuncSetAttribute(k_gain, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_ncorr, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_chi2, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-    }
     e = max_clusters(reinterpret_cast<const void *>(k_gain), p.C, p.smem_gain, &p.nclusters_gain);
     if (e != cudaSuccess) return e;
     e = max_clusters(reinterpret_cast<const void *>(k_ncorr), p.C, p.smem_ncorr, &p.nclusters_ncorr);

@@ -58,58 +58,71 @@ k_toep_h(const double *__restrict__ psd, int ndet, int nref, double fsamp, float
     }
 }
 
-// One warp per detector.  xtab[det] holds, at offset L(L-1)/2, the L values
-// of T_L^{-1} e_1 for L = 1..TOEP_LMAX; lvalid[det] is the largest order
-// the recursion reached with a positive pivot.
-__global__ void __launch_bounds__(32)
+// One CTA per detector (FP64 issue is the bound, so the dot products use
+// all four SM sub-partitions).  xtab[det] holds, at offset L(L-1)/2, the L
+// values of T_L^{-1} e_1 for L = 1..TOEP_LMAX; lvalid[det] is the largest
+// order the recursion reached with a positive pivot.
+constexpr int DT = 256;
+
+__global__ void __launch_bounds__(DT)
 k_toep_durbin(const float *__restrict__ htab, float *__restrict__ xtab, int32_t *__restrict__ lvalid)
 {
     const int det = blockIdx.x;
-    const int lane = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     __shared__ double y[TOEP_LMAX];
     __shared__ double r[TOEP_LMAX];
+    __shared__ double2 part[2][DT / 32];
     const float *h = htab + det * TOEP_LMAX;
     float *xt = xtab + static_cast<int64_t>(det) * (TOEP_LMAX * (TOEP_LMAX + 1) / 2);
     const double t0 = h[0];
-    for (int i = lane; i < TOEP_LMAX; i += 32) r[i] = (i + 1 < TOEP_LMAX ? h[i + 1] : 0.0f) / t0;
-    __syncwarp();
-    if (!(t0 > 0.0)) { if (lane == 0) lvalid[det] = 0; return; }
+    if (!(t0 > 0.0)) { if (tid == 0) lvalid[det] = 0; return; }
+    for (int i = tid; i < TOEP_LMAX; i += DT) r[i] = (i + 1 < TOEP_LMAX ? h[i + 1] : 0.0f) / t0;
+    __syncthreads();
     // order 1
-    if (lane == 0) { xt[0] = static_cast<float>(1.0 / t0); y[0] = -r[0]; }
-    __syncwarp();
+    if (tid == 0) { xt[0] = static_cast<float>(1.0 / t0); y[0] = -r[0]; }
+    __syncthreads();
     double beta = 1.0, alpha = -r[0];
     int valid = 1;
     for (int k = 1; k < TOEP_LMAX; ++k) {
-        // x for order k+1 uses y^(k) (length k): gamma = 1/(1 + r[0..k) . y)
-        double dot = 0.0;
-        for (int i = lane; i < k; i += 32) dot += r[i] * y[i];
-        for (int o = 16; o; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-        const double gam = 1.0 / (1.0 + dot);
+        // with y^(k) (length k): D1 = r[0..k) . y, D2 = sum_j r[k-1-j] y[j]
+        double d1 = 0.0, d2 = 0.0;
+        for (int j = tid; j < k; j += DT) {
+            const double yj = y[j];
+            d1 += r[j] * yj;
+            d2 += r[k - 1 - j] * yj;
+        }
+        for (int o = 16; o; o >>= 1) {
+            d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+            d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+        }
+        if (lane == 0) part[k & 1][warp] = make_double2(d1, d2);
+        __syncthreads();
+        double D1 = 0.0, D2 = 0.0;
+        for (int w = 0; w < DT / 32; ++w) { D1 += part[k & 1][w].x; D2 += part[k & 1][w].y; }
+        // x for order k+1: gamma = 1/(1 + D1), x = gamma (1, y) / t0
+        const double gam = 1.0 / (1.0 + D1);
         if (!(gam > 0.0) || !isfinite(gam)) break;
         float *xk = xt + static_cast<int64_t>(k + 1) * k / 2;       // order L = k+1
-        if (lane == 0) xk[0] = static_cast<float>(gam / t0);
-        for (int i = lane; i < k; i += 32) xk[i + 1] = static_cast<float>(gam * y[i] / t0);
+        if (tid == 0) xk[0] = static_cast<float>(gam / t0);
+        for (int i = tid; i < k; i += DT) xk[i + 1] = static_cast<float>(gam * y[i] / t0);
         valid = k + 1;
         if (k + 1 >= TOEP_LMAX) break;
         // Durbin step to y^(k+1)
         beta = (1.0 - alpha * alpha) * beta;
         if (!(beta > 0.0)) break;
-        double s = 0.0;
-        for (int i = lane; i < k; i += 32) s += r[i] * y[k - 1 - i];
-        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        alpha = -(r[k] + s) / beta;
-        // y[i] += alpha y[k-1-i] for i < k, pairs (i, k-1-i) by one lane
-        for (int i = lane; i < (k + 1) / 2; i += 32) {
+        alpha = -(r[k] + D2) / beta;
+        __syncthreads();      // every read of y^(k) is done
+        // y[i] += alpha y[k-1-i] for i < k, pairs (i, k-1-i) by one thread
+        for (int i = tid; i < (k + 1) / 2; i += DT) {
             const int jj = k - 1 - i;
             const double yi = y[i], yj = y[jj];
             y[i] = yi + alpha * yj;
             if (jj != i) y[jj] = yj + alpha * yi;
         }
-        __syncwarp();
-        if (lane == 0) y[k] = alpha;
-        __syncwarp();
+        if (tid == 0) y[k] = alpha;
+        __syncthreads();
     }
-    if (lane == 0) lvalid[det] = valid;
+    if (tid == 0) lvalid[det] = valid;
 }
 
 cudaError_t launch_toeplitz_prep(const Plan &p, const double *psd, cudaStream_t st)
@@ -118,7 +131,7 @@ cudaError_t launch_toeplitz_prep(const Plan &p, const double *psd, cudaStream_t 
     k_toep_h<<<g, HT, 0, st>>>(psd, p.ndet, p.toep_nref, p.fsamp, p.htab);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_toep_durbin<<<p.ndet, 32, 0, st>>>(p.htab, p.xtab, p.lvalid);
+    k_toep_durbin<<<p.ndet, DT, 0, st>>>(p.htab, p.xtab, p.lvalid);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,147 @@
+"""Parity at the full 30 GHz-like workload (4 detectors x 1000 scans of
+U[90k, 140k] samples at 32.5 Hz, Nside 512: 4.6e8 samples), in the launch
+configuration the benchmark times (default cluster size, persistent
+schedule, one Gibbs step through GibbsTODStep).
+
+The oracle cannot redo the whole band in a test, so:
+  * decode, gain and n_corr are checked on sampled detscans (the longest,
+    the shortest, the most flagged, and fixed others), each against the
+    oracle run on that detscan alone;
+  * hits are checked for every pixel against a bincount of the synthetic
+    pointing;
+  * binning and the 3x3 solve are checked on sampled pixels, with gains and
+    an n_corr timeline chosen by the test, against the oracle's normal
+    equations built from exactly the samples that hit those pixels.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+SEED, BAND, IT = 5, 0, 7
+CG_TOL = 1e-6          # the benchmark's setting
+
+
+@pytest.fixture(scope="module")
+def full():
+    import torch
+    import paper_2201_03509_gb300 as tg
+    from paper_2201_03509_gb300.step import GibbsTODStep
+    cfg = synth.CONFIGS["lfi30"]
+    band = synth.make_band(cfg)
+    ing = tg.ingest(band)
+    off = ing["offsets"]
+    plan = tg.Plan(cfg.nside, cfg.ndet, cfg.nscan, cfg.fsamp, off, ing["pix_streams"], ing["psi_streams"])
+    step = GibbsTODStep(plan, band.psd, ing["flag_words"], cg_tol=CG_TOL)
+    step.set_tod(ing["tod"])
+    m4 = np.zeros((band.npix, 4), np.float32)
+    m4[:, :3] = band.map_tqu.T
+    map_in = torch.from_numpy(m4).cuda()
+    step.run(map_in, tg.Rng(SEED, BAND, IT), tg.MODE_DRAW)
+    torch.cuda.synchronize()
+    plan.status()
+    nq = len(off) - 1
+    lens = np.diff(off)
+    flagfrac = np.array([ing["flags"][off[q]:off[q + 1]].mean() for q in range(nq)])
+    qs = sorted({int(np.argmax(lens)), int(np.argmin(lens)), int(np.argmax(flagfrac)), 0, 1234, nq - 1})
+    return dict(cfg=cfg, band=band, ing=ing, off=off, plan=plan, step=step, map32=m4[:, :3].T.astype(np.float64),
+                qs=qs, torch=torch, tg=tg)
+
+
+def _sl(F, q):
+    return slice(int(F["off"][q]), int(F["off"][q + 1]))
+
+
+@pytest.mark.gpu
+def test_full_decode_sampled(full):
+    F = full
+    for q in F["qs"]:
+        sl = _sl(F, q)
+        n = sl.stop - sl.start
+        pix = F["step"].pix[sl].cpu().numpy()
+        psi = F["step"].psi[sl].cpu().numpy().view(np.uint16)
+        assert np.array_equal(pix, F["band"].pix[q][:n]), q
+        assert np.array_equal(psi, F["band"].psi[q][:n]), q
+
+
+@pytest.mark.gpu
+def test_full_gain_and_ncorr_sampled(full):
+    F = full
+    cfg, band, ing = F["cfg"], F["band"], F["ing"]
+    g_gpu = F["step"].gain.cpu().numpy()
+    for q in F["qs"]:
+        sl = _sl(F, q)
+        n = sl.stop - sl.start
+        det = q % cfg.ndet
+        s0, fk, al = band.psd[det]
+        d = ing["tod"][sl].astype(np.float64)
+        mask = (~ing["flags"][sl]).astype(np.float64)
+        s = oracle.project(F["map32"], band.pix[q][:n].astype(np.int64), band.psi[q][:n].astype(np.int64))
+        P = oracle.noise_psd(n, cfg.fsamp, s0, fk, al)
+        rg, rmu, rsg = oracle.sample_gain(s, d, mask, P, oracle.gain_normal(SEED, BAND, q, IT), oracle.MODE_DRAW)
+        assert g_gpu[q] == pytest.approx(rg, rel=1e-5, abs=1e-5 * rsg), q
+        w1 = oracle.omega1(SEED, BAND, q, IT, n)
+        w2 = oracle.omega2(SEED, BAND, q, IT, n)
+        ref, _ = oracle.sample_ncorr(d, s, rg, mask, s0, fk, al, cfg.fsamp, w1, w2)
+        x = F["step"].ncorr[sl].cpu().numpy().astype(np.float64)
+        err = np.linalg.norm(x - ref) / np.linalg.norm(ref)
+        assert err < 1e-5, (q, err)
+
+
+@pytest.mark.gpu
+def test_full_hits_bin_and_solve_sampled(full):
+    F = full
+    torch, cfg, band, ing = F["torch"], F["cfg"], F["band"], F["ing"]
+    off, plan = F["off"], F["plan"]
+    nq, npix, N = len(off) - 1, band.npix, int(off[-1])
+    pix = np.concatenate([band.pix[q][:off[q + 1] - off[q]] for q in range(nq)]).astype(np.int32)
+    mask = ~ing["flags"]
+    # hits of every pixel, from the step just run
+    rh = np.bincount(pix, weights=mask, minlength=npix).astype(np.int64)
+    assert np.array_equal(F["step"].hits.cpu().numpy(), rh)
+    # binning with test-chosen gains and n_corr, on sampled pixels
+    gains = band.gain.copy()
+    x32 = (1e-4 * np.random.default_rng(3).standard_normal(N)).astype(np.float32)
+    dev = F["step"].d.device
+    t_x = torch.from_numpy(x32).to(dev)
+    t_g = torch.from_numpy(gains).to(dev)
+    A = torch.zeros((npix, 6), dtype=torch.float64, device=dev)
+    b = torch.zeros((npix, 3), dtype=torch.float64, device=dev)
+    hits = torch.zeros(npix, dtype=torch.int32, device=dev)
+    plan.bin(F["step"].psi, F["step"].d, t_x, t_g, F["step"].flags, F["step"].psd, A, b, hits)
+    plan.status()
+    hit_pix = np.nonzero(rh >= 3)[0]
+    sp = np.sort(np.random.default_rng(4).choice(hit_pix, 2000, replace=False))
+    sel = np.nonzero(np.isin(pix, sp))[0]
+    psi = np.concatenate([band.psi[q][:off[q + 1] - off[q]] for q in range(nq)])[sel].astype(np.int64)
+    qsel = np.searchsorted(off, sel, side="right") - 1
+    gs = gains[qsel]
+    s0 = band.psd[qsel % cfg.ndet, 0]
+    msel = mask[sel].astype(np.float64)
+    resid = ing["tod"][sel].astype(np.float64) - x32[sel].astype(np.float64)
+    rA, rb = oracle.bin_maps(npix, pix[sel].astype(np.int64), psi, resid,
+                             (msel * gs ** 2 / s0 ** 2, msel * gs / s0 ** 2))
+    gA, gb = A.cpu().numpy()[sp], b.cpu().numpy()[sp]
+    for i in range(6):
+        assert np.abs(gA[:, i] - rA[sp, i]).max() <= 1e-10 * np.abs(rA[sp, i]).max()
+    for i in range(3):
+        assert np.abs(gb[:, i] - rb[sp, i]).max() <= 1e-10 * np.abs(rb[sp, i]).max()
+    # solve at full size on the oracle's normal equations of the sampled pixels
+    rA_full = np.zeros((npix, 6))
+    rb_full = np.zeros((npix, 3))
+    rh_full = np.zeros(npix, np.int64)
+    rA_full[sp], rb_full[sp], rh_full[sp] = rA[sp], rb[sp], rh[sp]
+    m = torch.zeros((3, npix), dtype=torch.float64, device=dev)
+    m32 = torch.zeros((npix, 4), dtype=torch.float32, device=dev)
+    rc = torch.zeros(npix, dtype=torch.float64, device=dev)
+    va = torch.zeros(npix, dtype=torch.uint8, device=dev)
+    plan.solve_maps(torch.from_numpy(rA_full).to(dev), torch.from_numpy(rb_full).to(dev),
+                    torch.from_numpy(rh_full.astype(np.int32)).to(dev), 1e-6, m, m32, rc, va)
+    rm, _, rvalid = oracle.solve_maps(rA_full[sp], rb_full[sp], rh_full[sp], 1e-6)
+    gm, gv = m.cpu().numpy()[:, sp], va.cpu().numpy()
+    assert np.array_equal(gv[sp], rvalid)
+    assert gv.sum() == rvalid.sum()          # nothing outside the sample is valid
+    ok = rvalid > 0
+    for i in range(3):
+        assert np.abs(gm[i, ok] - rm[i, ok]).max() <= 1e-10 * np.abs(rm[i, ok]).max()

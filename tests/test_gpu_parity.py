@@ -17,8 +17,8 @@ def _cfgs():
     tiny = synth.CONFIGS["tiny"]
     # a few LFI-30-like detscans, short enough for the oracle, with flags
     l30 = synth.scaled(synth.CONFIGS["lfi30"], nscan=3, len_lo=9000, len_hi=30000)
-    return {"tiny_c1": (tiny, 1), "tiny_c4": (tiny, 4), "lfi30_small_c2": (l30, 2),
-            "lfi30_small_c8": (l30, 8)}
+    return {"tiny_c1": (tiny, 1), "tiny_c4": (tiny, 4), "tiny_c3": (tiny, 3), "lfi30_small_c2": (l30, 2),
+            "lfi30_small_c8": (l30, 8), "lfi30_small_c9": (l30, 9), "lfi30_small_auto": (l30, 0)}
 
 
 @pytest.fixture(scope="module", params=list(_cfgs().keys()))
