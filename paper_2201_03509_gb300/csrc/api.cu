@@ -281,6 +281,10 @@ bool choose_factor(int n, int C, DctPlan &out, int &sz)
     out.f_ncolmax = make_fastdiv(static_cast<uint32_t>(out.ncolmax));
     out.f_m2 = make_fastdiv(static_cast<uint32_t>(m2));
     out.f_npmax = make_fastdiv(static_cast<uint32_t>(out.npmax));
+    out.sq_fwd = static_cast<float>(std::sqrt(2.0 / n));
+    out.s0_fwd = static_cast<float>(1.0 / std::sqrt(static_cast<double>(n)));
+    out.sq_inv = static_cast<float>(std::sqrt(0.5 * n) / m);
+    out.s0_inv = static_cast<float>(std::sqrt(static_cast<double>(n)) / m);
     sz = best;
     return true;
 }

@@ -57,6 +57,7 @@ struct DctPlan {
     int32_t tw1, tw2;                // offsets of the W_{m1}^i and W_{m2}^i tables
     int32_t twb;                     // offset of this length's twiddle block (see k_dct.cu)
     FastDiv f_ncolmax, f_m2, f_npmax;
+    float sq_fwd, s0_fwd, sq_inv, s0_inv;   // real-split scales (FP64-computed on the host)
     DctStage s1[DCT_MAXR], s2[DCT_MAXR];
 };
 

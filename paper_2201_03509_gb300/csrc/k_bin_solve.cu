@@ -105,10 +105,17 @@ __global__ void __launch_bounds__(BIN_T) k_bin(BinArgs a)
     const int64_t o = a.off[q];
     const int64_t s0 = a.pair_start[r0];
     const int cnt = static_cast<int>(a.pair_start[r0 + nr - 1] + a.pair_len[r0 + nr - 1] - s0);
-    const int det = q % a.ndet;
-    const double sig0 = a.psd[3 * det];
-    const double gq = a.gain[q];
-    const double wA = gq * gq / (sig0 * sig0), wb = gq / (sig0 * sig0);
+    // the detscan's weights g^2/sigma0^2 and g/sigma0^2: FP64 divisions once,
+    // by thread 0 (FP64 issues at 1/64 of the FP32 rate on this part)
+    __shared__ double s_w[2];
+    if (threadIdx.x == 0) {
+        const double sig0 = a.psd[3 * (q % a.ndet)];
+        const double gq = a.gain[q];
+        s_w[0] = gq * gq / (sig0 * sig0);
+        s_w[1] = gq / (sig0 * sig0);
+    }
+    __syncthreads();
+    const double wA = s_w[0], wb = s_w[1];
 
     if (cnt > BIN_TILE) {
         // one run longer than a tile: strided partial sums, then a fixed-order tree

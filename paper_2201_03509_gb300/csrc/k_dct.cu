@@ -178,6 +178,7 @@ struct Geo {
     int ncol;    // valid local columns
     int p0, npl; // local row pairs
     FastDiv f_ncolmax, f_m2, f_npmax;
+    float sq_fwd, s0_fwd, sq_inv, s0_inv;   // real-split scales
     // twiddles staged in shared memory (see load_plan)
     const float2 *tw1, *tw2;            // W_{m1}^i, W_{m2}^i
     const float2 *sa1, *sb1, *sa5, *sb5;// W_{4n}^{k1}, W_{4n}^{m1 k2}, W_{4n}^{5 k1}, W_{4n}^{5 m1 k2}
@@ -237,9 +238,8 @@ template <bool INV>
 __device__ __noinline__ void split_pass(const Geo X, float2 *__restrict__ U)
 {
     const int m2 = X.m2, m1 = X.m1, m = X.m, n = X.n, p0 = X.p0;
-    const float sq = INV ? static_cast<float>(sqrt(0.5 * n) / m) : static_cast<float>(sqrt(2.0 / n));
-    const float s0 = INV ? static_cast<float>(sqrt(static_cast<double>(n)) / m)
-                         : static_cast<float>(1.0 / sqrt(static_cast<double>(n)));
+    const float sq = INV ? X.sq_inv : X.sq_fwd;
+    const float s0 = INV ? X.s0_inv : X.s0_fwd;
     const int total = X.npl * m2;
     const FastDiv fm2 = X.f_m2;
     for (int e = threadIdx.x; e < total; e += DCT_T) {
@@ -399,17 +399,31 @@ __device__ void load_time(const Geo &X, float2 *__restrict__ U, F f)
     __syncthreads();
 }
 
-// Cluster-wide sum of two doubles in a fixed order (identical in every CTA).
-__device__ double2 cluster_sum2(double2 v, double2 *s_red, double2 *s_part, int &parity,
-                                cg::cluster_group &cl)
+// Cluster-wide sums of two FP32 double-words in a fixed order (identical in
+// every CTA): warp trees in double-word FP32, the 16 warp partials and the C
+// CTA partials added in FP64 by thread 0 only (FP64 issues at 1/64 of the
+// FP32 rate on this part), the result broadcast through shared memory.
+__device__ __forceinline__ Acc2 acc_merge2(const Acc2 &a, const Acc2 &b) {
+    Acc2 r = a;
+    acc_add(r, b.s);
+    r.c = __fadd_rn(r.c, b.c);
+    return r;
+}
+__device__ double2 cluster_sum_acc(Acc2 x, Acc2 y, double2 *s_red, double2 *s_part, int &parity,
+                                   cg::cluster_group &cl)
 {
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
-        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+        Acc2 ox, oy;
+        ox.s = __shfl_xor_sync(0xffffffffu, x.s, o);
+        ox.c = __shfl_xor_sync(0xffffffffu, x.c, o);
+        oy.s = __shfl_xor_sync(0xffffffffu, y.s, o);
+        oy.c = __shfl_xor_sync(0xffffffffu, y.c, o);
+        x = acc_merge2(x, ox);
+        y = acc_merge2(y, oy);
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) s_red[warp] = v;
+    if (lane == 0) s_red[warp] = make_double2(acc_value(x), acc_value(y));
     __syncthreads();
     if (threadIdx.x == 0) {
         double2 t = make_double2(0.0, 0.0);
@@ -417,14 +431,40 @@ __device__ double2 cluster_sum2(double2 v, double2 *s_red, double2 *s_part, int 
         s_part[parity] = t;
     }
     cl.sync();
-    double2 tot = make_double2(0.0, 0.0);
-    for (int r = 0; r < static_cast<int>(cl.num_blocks()); ++r) {
-        const double2 pr = *cl.map_shared_rank(&s_part[parity], r);
-        tot.x += pr.x;
-        tot.y += pr.y;
+    if (threadIdx.x == 0) {
+        double2 tot = make_double2(0.0, 0.0);
+        for (int r = 0; r < static_cast<int>(cl.num_blocks()); ++r) {
+            const double2 pr = *cl.map_shared_rank(&s_part[parity], r);
+            tot.x += pr.x;
+            tot.y += pr.y;
+        }
+        s_red[DCT_T / 32] = tot;
     }
+    __syncthreads();
+    const double2 tot = s_red[DCT_T / 32];
     parity ^= 1;
     return tot;
+}
+
+// Per-detscan scalars: FP64 arithmetic (1/64 of the FP32 rate on this
+// part) done once by thread 0 and broadcast through shared memory.
+struct DetScal { float fscale, alpha, s2, inv_s2, inv_s, g; };
+__device__ __forceinline__ DetScal det_scalars(DetScal *sh, const double *psd, int det, int n, double fsamp,
+                                               const double *gain, int q)
+{
+    if (threadIdx.x == 0) {
+        const double sig0 = psd[3 * det], fk = psd[3 * det + 1], al = psd[3 * det + 2];
+        DetScal v;
+        v.fscale = static_cast<float>(fsamp / (2.0 * n * fk));
+        v.alpha = static_cast<float>(al);
+        v.s2 = static_cast<float>(sig0 * sig0);
+        v.inv_s2 = static_cast<float>(1.0 / (sig0 * sig0));
+        v.inv_s = static_cast<float>(1.0 / sig0);
+        v.g = gain ? static_cast<float>(gain[q]) : 1.0f;
+        *sh = v;
+    }
+    __syncthreads();
+    return *sh;
 }
 
 __device__ __forceinline__ bool flagged(const uint32_t *flags, int64_t t) {
@@ -473,6 +513,7 @@ __device__ void load_plan(Ctx *sX, const DctPlan *plans, int pi, const float2 *t
         X.p0 = c * P.npmax;
         X.npl = max(0, min(P.npmax, P.P - X.p0));
         X.f_ncolmax = P.f_ncolmax; X.f_m2 = P.f_m2; X.f_npmax = P.f_npmax;
+        X.sq_fwd = P.sq_fwd; X.s0_fwd = P.s0_fwd; X.sq_inv = P.sq_inv; X.s0_inv = P.s0_inv;
         const float2 *b = sm.twb;
         X.tw1 = b; b += P.m1;
         X.tw2 = b; b += P.m2;
@@ -583,7 +624,8 @@ __global__ void __launch_bounds__(DCT_T, 1) k_gain(GainArgs a)
 {
     extern __shared__ __align__(16) float2 smem_raw[];
     __shared__ Ctx sX;
-    __shared__ double2 s_red[DCT_T / 32];
+    __shared__ DetScal s_sc;
+    __shared__ double2 s_red[DCT_T / 32 + 1];
     __shared__ double2 s_part[2];
     cg::cluster_group cl = cg::this_cluster();
     const int C = static_cast<int>(cl.num_blocks()), c = static_cast<int>(cl.block_rank());
@@ -599,10 +641,8 @@ __global__ void __launch_bounds__(DCT_T, 1) k_gain(GainArgs a)
         const int n = X.n, m = X.m;
         const float *sq = a.s + o, *dq = a.d + o;
         const uint32_t *fl = a.flags;
-        const double sig0 = a.psd[3 * det], fk = a.psd[3 * det + 1], al = a.psd[3 * det + 2];
-        const float fscale = static_cast<float>(a.fsamp / (2.0 * n * fk));
-        const float alpha = static_cast<float>(al);
-        const float s2 = static_cast<float>(sig0 * sig0);
+        const DetScal sc = det_scalars(&s_sc, a.psd, det, n, a.fsamp, nullptr, q);
+        const float fscale = sc.fscale, alpha = sc.alpha, s2 = sc.s2;
         float2 *cur = sm.U0, *oth = sm.U1;
         // shat = C(M s); a = sum_k shat_k^2 / P_k; then u = C^T(shat / P) and
         // b = sum_t M_t d_t u_t = sum_k shat_k dhat_k / P_k (two transforms)
@@ -644,7 +684,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_gain(GainArgs a)
                 if (!flagged(fl, o + t1)) acc_add_prod(sb, __ldg(dq + t1), v.y);
             }
         }
-        const double2 ab = cluster_sum2(make_double2(acc_value(sa), acc_value(sb)), s_red, s_part,
+        const double2 ab = cluster_sum_acc(sa, sb, s_red, s_part,
                                         parity, cl);
         if (c == 0 && threadIdx.x == 0) {
             const double A = ab.x, B = ab.y;
@@ -746,7 +786,8 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
 {
     extern __shared__ __align__(16) float2 smem_raw[];
     __shared__ Ctx sX;
-    __shared__ double2 s_red[DCT_T / 32];
+    __shared__ DetScal s_sc;
+    __shared__ double2 s_red[DCT_T / 32 + 1];
     __shared__ double2 s_part[2];
     __shared__ int3 s_wscan[DCT_T / 32 + 1];
     __shared__ int s_nown, s_ovf;
@@ -776,13 +817,9 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
         if (threadIdx.x == 0) s_nown = 0;
         const Ctx &X = sX;     // read from shared memory: registers are scarce here
         const int n = X.n, m = X.m;
-        const double sig0 = a.psd[3 * det], fk = a.psd[3 * det + 1], al = a.psd[3 * det + 2];
-        const float fscale = static_cast<float>(a.fsamp / (2.0 * n * fk));
-        const float alpha = static_cast<float>(al);
-        const float s2 = static_cast<float>(sig0 * sig0);
-        const float inv_s2 = static_cast<float>(1.0 / (sig0 * sig0));
-        const float inv_s = static_cast<float>(1.0 / sig0);
-        const float g = static_cast<float>(a.gain[q]);
+        const DetScal sc = det_scalars(&s_sc, a.psd, det, n, a.fsamp, a.gain, q);
+        const float fscale = sc.fscale, alpha = sc.alpha, s2 = sc.s2;
+        const float inv_s2 = sc.inv_s2, inv_s = sc.inv_s, g = sc.g;
         const bool draw = a.mode == TOD_MODE_DRAW;
         const float *dq = a.d + o, *sq = a.s + o;
         const uint32_t *fl = a.flags;
@@ -943,8 +980,8 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
         }
         if (!prec && threadIdx.x == 0) s_ovf = 1;
         __syncthreads();
-        const double ovf_all = cluster_sum2(make_double2(threadIdx.x == 0 && s_ovf ? 1.0 : 0.0, 0.0),
-                                            s_red, s_part, parity, cl).x;
+        const double ovf_all = cluster_sum_acc(Acc2{threadIdx.x == 0 && s_ovf ? 1.0f : 0.0f, 0.0f},
+                                               Acc2{0.f, 0.f}, s_red, s_part, parity, cl).x;
         const bool use_prec = ovf_all < 0.5;
         int it = 0;
         bool conv = true;
@@ -1009,20 +1046,20 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             };
             // rhs = E^T x0 ; y = 0 ; r = rhs ; z = M^{-1} r ; p = z
             cl.sync();         // x0 is complete in every CTA before the gathers
-            double rr_loc = 0.0;
+            Acc2 rr_loc = {0.f, 0.f};
             for (int i = threadIdx.x; i < kc; i += DCT_T) {
                 const float v = *at(cur, i);
                 c_y[i] = 0.f; c_r[i] = v;
-                rr_loc += static_cast<double>(v) * v;
+                acc_add_prod(rr_loc, v, v);
             }
             __syncthreads();
             precond();
-            double rz_loc = 0.0;
+            Acc2 rz_loc = {0.f, 0.f};
             for (int i = threadIdx.x; i < kc; i += DCT_T) {
                 c_p[i] = c_z[i];
-                rz_loc += static_cast<double>(c_r[i]) * c_z[i];
+                acc_add_prod(rz_loc, c_r[i], c_z[i]);
             }
-            const double2 rr2 = cluster_sum2(make_double2(rr_loc, rz_loc), s_red, s_part, parity, cl);
+            const double2 rr2 = cluster_sum_acc(rr_loc, rz_loc, s_red, s_part, parity, cl);
             double rz = rr2.y;
             const double stop = static_cast<double>(a.tol) * a.tol * rr2.x;
             conv = rr2.x == 0.0;
@@ -1037,14 +1074,16 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                 apply_filter(X, cur, fscale, alpha, s2, 1, wt);
                 dct_inverse(sX, cur, oth, sm.tw1, sm.tw2, cl);
                 cl.sync();     // every CTA's result is complete before the gathers
-                double pq_loc = 0.0;
+                Acc2 pq_loc = {0.f, 0.f};
                 for (int i = threadIdx.x; i < kc; i += DCT_T) {
                     const float v = *at(cur, i);
                     c_q[i] = v;
-                    pq_loc += static_cast<double>(c_p[i]) * v;
+                    acc_add_prod(pq_loc, c_p[i], v);
                 }
-                const double pq = cluster_sum2(make_double2(pq_loc, 0.0), s_red, s_part, parity, cl).x;
-                const float alp = static_cast<float>(rz / pq);
+                const double pq = cluster_sum_acc(pq_loc, Acc2{0.f, 0.f}, s_red, s_part, parity, cl).x;
+                // step lengths in FP32 (the vectors are FP32); FP64 division
+                // by every thread would cost more than the update itself
+                const float alp = static_cast<float>(rz) / static_cast<float>(pq);
                 for (int i = threadIdx.x; i < kc; i += DCT_T) {
                     c_y[i] = fmaf(alp, c_p[i], c_y[i]);
                     c_r[i] = fmaf(-alp, c_q[i], c_r[i]);
@@ -1052,14 +1091,14 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                 __syncthreads();
                 ++it;
                 precond();
-                double rn_loc = 0.0, rzn_loc = 0.0;
+                Acc2 rn_loc = {0.f, 0.f}, rzn_loc = {0.f, 0.f};
                 for (int i = threadIdx.x; i < kc; i += DCT_T) {
-                    rn_loc += static_cast<double>(c_r[i]) * c_r[i];
-                    rzn_loc += static_cast<double>(c_r[i]) * c_z[i];
+                    acc_add_prod(rn_loc, c_r[i], c_r[i]);
+                    acc_add_prod(rzn_loc, c_r[i], c_z[i]);
                 }
-                const double2 rn2 = cluster_sum2(make_double2(rn_loc, rzn_loc), s_red, s_part, parity, cl);
+                const double2 rn2 = cluster_sum_acc(rn_loc, rzn_loc, s_red, s_part, parity, cl);
                 if (rn2.x <= stop) { conv = true; break; }
-                const float beta = static_cast<float>(rn2.y / rz);
+                const float beta = static_cast<float>(rn2.y) / static_cast<float>(rz);
                 for (int i = threadIdx.x; i < kc; i += DCT_T) c_p[i] = fmaf(beta, c_p[i], c_z[i]);
                 __syncthreads();
                 rz = rn2.y;
@@ -1119,7 +1158,8 @@ __global__ void __launch_bounds__(DCT_T, 1) k_chi2(Chi2Args a)
 {
     extern __shared__ __align__(16) float2 smem_raw[];
     __shared__ Ctx sX;
-    __shared__ double2 s_red[DCT_T / 32];
+    __shared__ DetScal s_sc;
+    __shared__ double2 s_red[DCT_T / 32 + 1];
     __shared__ double2 s_part[2];
     cg::cluster_group cl = cg::this_cluster();
     const int C = static_cast<int>(cl.num_blocks()), c = static_cast<int>(cl.block_rank());
@@ -1135,11 +1175,8 @@ __global__ void __launch_bounds__(DCT_T, 1) k_chi2(Chi2Args a)
         const int n = X.n, m = X.m;
         const float *sq = a.s + o, *dq = a.d + o;
         const uint32_t *fl = a.flags;
-        const double sig0 = a.psd[3 * det], fk = a.psd[3 * det + 1], al = a.psd[3 * det + 2];
-        const float fscale = static_cast<float>(a.fsamp / (2.0 * n * fk));
-        const float alpha = static_cast<float>(al);
-        const float s2 = static_cast<float>(sig0 * sig0);
-        const float g = static_cast<float>(a.gain[q]);
+        const DetScal sc = det_scalars(&s_sc, a.psd, det, n, a.fsamp, a.gain, q);
+        const float fscale = sc.fscale, alpha = sc.alpha, s2 = sc.s2, g = sc.g;
         float2 *cur = sm.U0, *oth = sm.U1;
         load_time(X, cur, [&](int j) {
             const int t0 = vpos_t(2 * j, n, m), t1 = vpos_t(2 * j + 1, n, m);
@@ -1197,10 +1234,11 @@ __global__ void __launch_bounds__(DCT_T, 1) k_chi2(Chi2Args a)
                 acc_add_prod(ag, __ldg(sq + t1), v1);
             }
         }
-        const double2 r1 = cluster_sum2(make_double2(acc_value(aq), acc_value(al1)), s_red, s_part, parity, cl);
-        const double2 r2 = cluster_sum2(make_double2(acc_value(afk), acc_value(aal)), s_red, s_part, parity, cl);
-        const double2 r3 = cluster_sum2(make_double2(acc_value(ag), 0.0), s_red, s_part, parity, cl);
+        const double2 r1 = cluster_sum_acc(aq, al1, s_red, s_part, parity, cl);
+        const double2 r2 = cluster_sum_acc(afk, aal, s_red, s_part, parity, cl);
+        const double2 r3 = cluster_sum_acc(ag, Acc2{0.f, 0.f}, s_red, s_part, parity, cl);
         if (c == 0 && threadIdx.x == 0) {
+            const double sig0 = a.psd[3 * det], fk = a.psd[3 * det + 1];
             const double nm1 = static_cast<double>(n - 1);
             a.chi2[q] = 0.5 * (r1.x + r1.y + nm1 * log(sig0 * sig0));
             a.dgain[q] = -r3.x;
