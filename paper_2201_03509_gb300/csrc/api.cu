@@ -634,8 +634,9 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
             // twiddle block: 3 (m1 + m2) + m/64 + 65 complex values
             int twmax = 0;
             for (auto &dp : cand) twmax = std::max(twmax, 3 * (dp.m1 + dp.m2) + dp.m / 64 + 65);
+            twmax = (twmax + 1) & ~1;
             const size_t smem_dyn = sizeof(float2) * (2 * static_cast<size_t>(sz) + twmax) +
-                                    static_cast<size_t>(CG_KCAP) * 24 + sizeof(float) * 4 * TOEP_LMAX;
+                                    static_cast<size_t>(CG_KCAP) * 24 + sizeof(float) * 5 * GB_CAP;
             if (smem_dyn + 12288 > 227 * 1024) continue;
             int ncl = 0;
             if ((e = transform_cluster_occupancy(C, smem_dyn, &ncl))) return fail(e);
@@ -672,7 +673,8 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
             for (int i = 0; i < 64; ++i) push_w(dp.m, i);
             twsz = std::max(twsz, static_cast<int>(tw.size()) - dp.twb);
         }
-        p->twsz = twsz;        std::vector<int32_t> qp(p->nq);
+        p->twsz = (twsz + 1) & ~1;      // keeps the areas after the block 16-byte aligned
+        std::vector<int32_t> qp(p->nq);
         for (int q = 0; q < p->nq; ++q)
             qp[q] = static_cast<int32_t>(std::lower_bound(uniq.begin(), uniq.end(), lens[q]) - uniq.begin());
         p->nplans = static_cast<int32_t>(plans.size());

@@ -276,6 +276,50 @@ __device__ __noinline__ void split_pass(const Geo X, float2 *__restrict__ U)
     __syncthreads();
 }
 
+// Forward split, a per-mode filter and the inverse split in one pass over
+// this CTA's row pairs, in place: Z -> Y (packed orthonormal coefficients)
+// -> f(e, k, Y) -> Z'.  f gets the element index e and the mode k of Y.x
+// (Y.y is mode n - k, or m when k = 0).  Equivalent to split_pass<false>,
+// a filter pass and split_pass<true>, with one load and one store.
+template <class F>
+__device__ __forceinline__ void split_roundtrip(const Geo &XS, float2 *__restrict__ U, F f)
+{
+    const Geo X = XS;       // registers: the stores to U cannot alias it
+    const int m2 = X.m2, m1 = X.m1, p0 = X.p0;
+    const float sqf = X.sq_fwd, s0f = X.s0_fwd, sqi = X.sq_inv, s0i = X.s0_inv;
+    const int total = X.npl * m2;
+    const FastDiv fm2 = X.f_m2;
+    for (int e = threadIdx.x; e < total; e += DCT_T) {
+        const int pl = fdiv(e, fm2), k2 = e - pl * m2;
+        const int p = p0 + pl;
+        const int cnt = (p == 0) ? (m2 / 2 + 1) : ((2 * p == m1) ? (m2 + 1) / 2 : m2);
+        if (k2 >= cnt) continue;
+        int ib, q1, q2;
+        if (p == 0) { q1 = 0; q2 = (k2 == 0) ? 0 : m2 - k2; ib = 2 * pl * m2 + q2; }
+        else { q1 = m1 - p; q2 = m2 - 1 - k2; ib = ((q1 == p) ? 2 * pl : 2 * pl + 1) * m2 + q2; }
+        const int ia = 2 * pl * m2 + k2;
+        const float2 Za = U[ia], Zb = U[ib];
+        if (p == 0 && k2 == 0) {
+            float2 Y = make_float2((Za.x + Za.y) * s0f, (Za.x - Za.y) * s0f);
+            Y = f(ia, 0, Y);
+            const float V0 = Y.x * s0i, Vm = Y.y * s0i;
+            U[ia] = make_float2(0.5f * (V0 + Vm), 0.5f * (V0 - Vm));
+            continue;
+        }
+        float2 Ya = split_fwd_one(X, Za, Zb, p, k2, sqf);
+        Ya = f(ia, p + m1 * k2, Ya);
+        if (ib != ia) {
+            float2 Yb = split_fwd_one(X, Zb, Za, q1, q2, sqf);
+            Yb = f(ib, q1 + m1 * q2, Yb);
+            U[ib] = split_inv_one(X, Yb, Ya, q1, q2, p, k2, sqi);
+            U[ia] = split_inv_one(X, Ya, Yb, p, k2, q1, q2, sqi);
+        } else {
+            U[ia] = split_inv_one(X, Ya, Ya, p, k2, q1, q2, sqi);
+        }
+    }
+    __syncthreads();
+}
+
 // Time layout (src, every CTA) -> freq layout (dst, local), or back.  The
 // four-step twiddle W_m^{-+ j2 k1} comes from the two-level table.  The
 // first cluster barrier makes every CTA's src complete; the second keeps
@@ -370,6 +414,25 @@ __device__ __noinline__ void dct_inverse(const Ctx &XS, float2 *&cur, float2 *&o
     transpose<true>(X, cur, oth, cl);
     { float2 *t = cur; cur = oth; oth = t; }
     fft_seq<true>(cur, oth, X.m1, XS.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, tw1);
+}
+
+// The two halves of a filter round trip: time layout -> row-FFT output
+// (split not applied), and back.
+__device__ __noinline__ void dct_forward_pre(const Ctx &XS, float2 *&cur, float2 *&oth, cg::cluster_group &cl)
+{
+    const Geo X = XS;
+    fft_seq<false>(cur, oth, X.m1, XS.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, X.tw1);
+    transpose<false>(X, cur, oth, cl);
+    { float2 *t = cur; cur = oth; oth = t; }
+    fft_seq<false>(cur, oth, X.m2, XS.s2, X.nr2, 2 * X.npl, X.f_m2, 1, X.m2, false, X.tw2);
+}
+__device__ __noinline__ void dct_inverse_post(const Ctx &XS, float2 *&cur, float2 *&oth, cg::cluster_group &cl)
+{
+    const Geo X = XS;
+    fft_seq<true>(cur, oth, X.m2, XS.s2, X.nr2, 2 * X.npl, X.f_m2, 1, X.m2, false, X.tw2);
+    transpose<true>(X, cur, oth, cl);
+    { float2 *t = cur; cur = oth; oth = t; }
+    fft_seq<true>(cur, oth, X.m1, XS.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, X.tw1);
 }
 
 // Fill U (time layout) with f(j) = (x_{t(2j)}, x_{t(2j+1)}) for own columns.
@@ -651,27 +714,18 @@ __global__ void __launch_bounds__(DCT_T, 1) k_gain(GainArgs a)
             const float v0 = __ldg(sq + t0), v1 = __ldg(sq + t1);      // independent of the flags
             return make_float2(flagged(fl, o + t0) ? 0.f : v0, flagged(fl, o + t1) ? 0.f : v1);
         });
-        dct_forward(sX, cur, oth, sm.tw1, sm.tw2, cl);
+        dct_forward_pre(sX, cur, oth, cl);
         Acc2 sa = {0.f, 0.f}, sb = {0.f, 0.f};
-        {
-            const int total = 2 * X.npl * X.m2;
-            for (int e = threadIdx.x; e < total; e += DCT_T) {
-                const int slot = fdiv(e, X.f_m2), k2 = e - slot * X.m2;
-                const int k1 = slot_row(X, slot);
-                if (k1 < 0) continue;
-                const int k = k1 + X.m1 * k2;
-                const float2 S = cur[e];
-                const int ka = k, kb = (k == 0) ? m : n - k;
-                const float wa = ka == 0 ? 0.f : 1.0f / (s2 * (1.0f + fratio_pow(ka, fscale, alpha)));
-                const float wb = 1.0f / (s2 * (1.0f + fratio_pow(kb, fscale, alpha)));
-                const float2 W = make_float2(S.x * wa, S.y * wb);
-                acc_add_prod(sa, S.x, W.x);
-                acc_add_prod(sa, S.y, W.y);
-                cur[e] = W;
-            }
-        }
-        __syncthreads();
-        dct_inverse(sX, cur, oth, sm.tw1, sm.tw2, cl);
+        split_roundtrip(X, cur, [&](int, int k, float2 S) {
+            const int ka = k, kb = (k == 0) ? m : n - k;
+            const float wa = ka == 0 ? 0.f : 1.0f / (s2 * (1.0f + fratio_pow(ka, fscale, alpha)));
+            const float wb = 1.0f / (s2 * (1.0f + fratio_pow(kb, fscale, alpha)));
+            const float2 W = make_float2(S.x * wa, S.y * wb);
+            acc_add_prod(sa, S.x, W.x);
+            acc_add_prod(sa, S.y, W.y);
+            return W;
+        });
+        dct_inverse_post(sX, cur, oth, cl);
         {
             const int tot = X.m1 * X.ncolmax;
             for (int e = threadIdx.x; e < tot; e += DCT_T) {
@@ -792,7 +846,8 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
     __shared__ int3 s_wscan[DCT_T / 32 + 1];
     __shared__ int s_nown, s_ovf;
     __shared__ int g_beg[GAP_CAP], g_end[GAP_CAP];
-    __shared__ int o_len[GAP_CAP], o_rank[GAP_CAP];
+    __shared__ int o_len[GAP_CAP], o_rank[GAP_CAP], o_off[GAP_CAP], o_q[GAP_CAP];
+    __shared__ int o_rnd[GAP_CAP + 1], s_nrnd;    // rounds of own blocks, <= GB_CAP elements each
     cg::cluster_group cl = cg::this_cluster();
     const int C = static_cast<int>(cl.num_blocks()), c = static_cast<int>(cl.block_rank());
     const int cid = blockIdx.x / C, ncl = gridDim.x / C;
@@ -805,16 +860,17 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
     float *c_q = c_p + CG_KCAP;
     float *c_z = c_q + CG_KCAP;
     float *gb_r = c_z + CG_KCAP;
-    float *gb_x = gb_r + TOEP_LMAX;
-    float *gb_u1 = gb_x + TOEP_LMAX;
-    float *gb_u2 = gb_u1 + TOEP_LMAX;
+    float *gb_x = gb_r + GB_CAP;
+    float *gb_w = gb_x + GB_CAP;
+    float *gb_u1 = gb_w + GB_CAP;
+    float *gb_u2 = gb_u1 + GB_CAP;
     int parity = 0;
     for (int w = cid; w < a.work_count; w += ncl) {
         const int q = a.work[a.work_begin + w];
         const int det = q % a.ndet;
         const int64_t o = a.off[q];
         load_plan(&sX, a.plans, a.q_plan[q], a.tw, sm, c, C);
-        if (threadIdx.x == 0) s_nown = 0;
+        if (threadIdx.x == 0) { s_nown = 0; s_nrnd = 0; }
         const Ctx &X = sX;     // read from shared memory: registers are scarce here
         const int n = X.n, m = X.m;
         const DetScal sc = det_scalars(&s_sc, a.psd, det, n, a.fsamp, a.gain, q);
@@ -828,44 +884,94 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
         float *xq = a.x_out + o;
         float4 *wt = a.wscratch + (static_cast<int64_t>(cid) * C + c) * a.sz;
         float2 *cur = sm.U0, *oth = sm.U1;
-        // right-hand side, time-domain part: M (r/s2 + w1/s)
-        load_time(X, cur, [&](int j) {
-            const int t0 = vpos_t(2 * j, n, m), t1 = vpos_t(2 * j + 1, n, m);
-            float2 w1 = make_float2(0.f, 0.f);
-            if (draw) w1 = stream_normal_pair(rng.seed, rng.band, q, 1, gi, 2 * j);
-            const float d0 = __ldg(dq + t0), d1 = __ldg(dq + t1), s0v = __ldg(sq + t0), s1v = __ldg(sq + t1);
-            const float r0 = flagged(fl, o + t0) ? 0.f : fmaf(d0 - g * s0v, inv_s2, w1.x * inv_s);
-            const float r1 = flagged(fl, o + t1) ? 0.f : fmaf(d1 - g * s1v, inv_s2, w1.y * inv_s);
-            return make_float2(r0, r1);
-        });
-        dct_forward(sX, cur, oth, sm.tw1, sm.tw2, cl);
-        // + sqrt(phi) w2, times beta; the filter weights of this detscan
-        // (beta, gamma for both modes of each packed slot) go to wt once
+        // right-hand side, time-domain part: M (r/s2 + w1/s).  Element j takes
+        // normals 2j, 2j+1, i.e. pair j mod 4 of Philox block j/4: one thread
+        // per block of four consecutive elements of a row draws it once.
         {
-            const int total = 2 * X.npl * X.m2;
-            for (int e = threadIdx.x; e < total; e += DCT_T) {
-                const int slot = fdiv(e, X.f_m2), k2 = e - slot * X.m2;
-                const int k1 = slot_row(X, slot);
-                if (k1 < 0) { wt[e] = make_float4(0.f, 0.f, 0.f, 0.f); continue; }
-                const int k = k1 + X.m1 * k2;
-                const int ka = k, kb = (k == 0) ? m : n - k;
-                const float ra = (ka == 0) ? 0.f : fratio_pow(ka, fscale, -alpha);   // s2 phi
-                const float rb = fratio_pow(kb, fscale, -alpha);
-                const float ba = s2 / (1.0f + ra), bb = s2 / (1.0f + rb);
-                wt[e] = make_float4(ba, bb, ra * ba, rb * bb);
-                float2 v = cur[e];
-                if (draw) {
-                    const float2 w2 = stream_normal_pair(rng.seed, rng.band, q, 2, gi, 2 * k);
-                    v.x += sqrtf(ra * inv_s2) * w2.x;
-                    v.y += sqrtf(rb * inv_s2) * w2.y;
+            const int ncol = X.ncol, nbr = (ncol + 3) / 4 + 1;     // blocks touching a row
+            const int items = X.m1 * nbr;
+            for (int w = threadIdx.x; w < items; w += DCT_T) {
+                const int j1 = w / nbr, bi = w - j1 * nbr;
+                const int js = j1 * X.m2 + X.c * X.ncolmax;          // first element of the row
+                const int b = (js >> 2) + bi;
+                if (4 * b >= js + ncol) continue;
+                u64x4 rw;
+                if (draw) rw = philox4x64(static_cast<uint64_t>(b), q, 1, gi, rng.seed, rng.band);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = 4 * b + u;
+                    if (j < js || j >= js + ncol) continue;
+                    const int t0 = vpos_t(2 * j, n, m), t1 = vpos_t(2 * j + 1, n, m);
+                    const float2 w1 = draw ? philox_normal_pair(rw, u) : make_float2(0.f, 0.f);
+                    const float d0 = __ldg(dq + t0), d1 = __ldg(dq + t1);
+                    const float s0v = __ldg(sq + t0), s1v = __ldg(sq + t1);
+                    const float r0 = flagged(fl, o + t0) ? 0.f : fmaf(d0 - g * s0v, inv_s2, w1.x * inv_s);
+                    const float r1 = flagged(fl, o + t1) ? 0.f : fmaf(d1 - g * s1v, inv_s2, w1.y * inv_s);
+                    cur[j1 * X.ncolmax + (j - js)] = make_float2(r0, r1);
                 }
-                v.x *= ba;
-                v.y *= bb;
-                cur[e] = v;
+            }
+            // padding columns of the last CTA stay zero
+            for (int e = threadIdx.x; e < X.m1 * X.ncolmax; e += DCT_T) {
+                const int j1 = fdiv(e, X.f_ncolmax);
+                if (e - j1 * X.ncolmax >= ncol) cur[e] = make_float2(0.f, 0.f);
             }
             __syncthreads();
         }
-        dct_inverse(sX, cur, oth, sm.tw1, sm.tw2, cl);      // cur = x0 (time layout)
+        dct_forward_pre(sX, cur, oth, cl);
+        // prior term sqrt(phi) w2 in the packed layout, into the free buffer
+        // oth, and the filter weights of this detscan (beta, gamma for both
+        // modes of each packed slot) into wt, once.
+        // Mode k takes normals 2k, 2k+1 (pair k mod 4 of block k/4); for a
+        // fixed k2 the own even slots hold k = p0 + pl + m1 k2 and the odd
+        // ones k = m1 - p0 - pl + m1 k2 (pl < npl), so one thread draws a
+        // block for up to four consecutive modes of one parity.
+        {
+            const int npl = X.npl, m1 = X.m1, m2 = X.m2, p0 = X.p0;
+            const int nbk = (npl + 3) / 4 + 1;                  // blocks touching a k range
+            const int items = 2 * nbk * m2;
+            for (int w = threadIdx.x; w < items; w += DCT_T) {
+                const int rest = fdiv(w, X.f_m2), k2 = w - rest * m2;
+                const int par = rest / nbk, bi = rest - par * nbk;
+                const int kbase = (par == 0 ? p0 : m1 - p0 - (npl - 1)) + m1 * k2;
+                const int b = (kbase >> 2) + bi;
+                if (npl <= 0 || 4 * b >= kbase + npl) continue;
+                u64x4 rw;
+                if (draw) rw = philox4x64(static_cast<uint64_t>(b), q, 2, gi, rng.seed, rng.band);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = 4 * b + u;
+                    if (k < kbase || k >= kbase + npl) continue;
+                    const int pl = par == 0 ? k - kbase : (npl - 1) - (k - kbase);
+                    const int p = p0 + pl;
+                    const int e = (2 * pl + par) * m2 + k2;
+                    if (par == 1 && (p == 0 || m1 - p == p)) {            // slot holds no modes
+                        wt[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        oth[e] = make_float2(0.f, 0.f);
+                        continue;
+                    }
+                    const int ka = k, kb = (k == 0) ? m : n - k;
+                    const float ra = (ka == 0) ? 0.f : fratio_pow(ka, fscale, -alpha);   // s2 phi
+                    const float rb = fratio_pow(kb, fscale, -alpha);
+                    const float ba = s2 / (1.0f + ra), bb = s2 / (1.0f + rb);
+                    wt[e] = make_float4(ba, bb, ra * ba, rb * bb);
+                    float2 nu = make_float2(0.f, 0.f);
+                    if (draw) {
+                        const float2 w2 = philox_normal_pair(rw, u);
+                        nu = make_float2(sqrtf(ra * inv_s2) * w2.x, sqrtf(rb * inv_s2) * w2.y);
+                    }
+                    oth[e] = nu;
+                }
+            }
+            __syncthreads();
+        }
+        // (C b + prior term) times beta, between the two halves of the split
+        split_roundtrip(X, cur, [&](int e, int, float2 Y) {
+            const float4 w = wt[e];
+            const float2 nu = oth[e];
+            return make_float2((Y.x + nu.x) * w.x, (Y.y + nu.y) * w.y);
+        });
+
+        dct_inverse_post(sX, cur, oth, cl);      // cur = x0 (time layout)
         // x0 -> x_out
         {
             const int tot = X.m1 * X.ncolmax;
@@ -897,6 +1003,9 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             if (base + 32 > n) bits &= (n - base >= 32) ? ~0u : ((1u << static_cast<int>(n - base)) - 1u);
             return bits;
         };
+        // per-word flagged counts, then their exclusive prefix, in the free
+        // transform buffer (oth: nothing reads it until the CG scatters)
+        int *wpre = reinterpret_cast<int *>(oth);
         int3 mine = make_int3(0, 0, 0);     // flagged samples, gap starts, gap ends
         for (int i = 0; i < per; ++i) {
             const int wi = threadIdx.x * per + i;
@@ -904,6 +1013,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             const uint32_t bits = word_bits(wi);
             const uint32_t prev = word_bits(wi - 1) >> 31;
             const uint32_t next = word_bits(wi + 1) & 1u;
+            wpre[wi] = __popc(bits);
             mine.x += __popc(bits);
             mine.y += __popc(bits & ~((bits << 1) | prev));
             mine.z += __popc(bits & ~((bits >> 1) | (next << 31)));
@@ -938,19 +1048,27 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                     if (epos < GAP_CAP) g_end[epos] = static_cast<int>(base + b + 1);
                     ++epos;
                 }
-                const int nb = __popc(bits);
-                if (cap_ovf || pos + nb <= k0 || pos >= k0 + kc) { pos += nb; continue; }
-                uint32_t bb = bits;
-                while (bb) {
-                    const int b = __popc((bb & (0u - bb)) - 1u);
-                    bb &= bb - 1;
-                    if (pos >= k0 && pos < k0 + kc) {
-                        int ow, loc;
-                        sample_loc(X, static_cast<int>(base + b), ow, loc);
-                        c_loc[pos - k0] = (ow << 20) | loc;
-                    }
-                    ++pos;
+                const int cnt = wpre[wi];
+                wpre[wi] = pos;
+                pos += cnt;
+            }
+        }
+        __syncthreads();
+        // own ranks [k0, k0 + kc): the word holding rank k is the last one whose
+        // prefix is <= k (a word without flags shares its prefix with the next)
+        if (!cap_ovf) {
+            for (int k = k0 + threadIdx.x; k < k0 + kc; k += DCT_T) {
+                int lo = 0, hi = nw - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (wpre[mid] <= k) lo = mid; else hi = mid - 1;
                 }
+                uint32_t bits = word_bits(lo);
+                for (int r = k - wpre[lo]; r > 0; --r) bits &= bits - 1;
+                const int b = __popc((bits & (0u - bits)) - 1u);
+                int ow, loc;
+                sample_loc(X, static_cast<int>(((wb0 + lo) << 5) - o + b), ow, loc);
+                c_loc[k - k0] = (ow << 20) | loc;
             }
         }
         __syncthreads();
@@ -961,21 +1079,30 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             // split gaps into blocks of at most lmax samples; block b goes to
             // CTA b mod C with the rank of its first sample
             const int lmax = max(1, min(TOEP_LMAX, a.lvalid[det]));
-            int nb = 0, ovf = 0, rank = 0;
+            int nb = 0, ovf = 0, rank = 0, rlen = 0, rq = 0, cb = 0;
             for (int g2 = 0; g2 < ngap; ++g2) {
                 for (int b0 = g_beg[g2]; b0 < g_end[g2]; b0 += lmax) {
                     const int len = min(lmax, g_end[g2] - b0);
-                    if ((nb % C) == c) {
+                    if (cb == c) {
                         if (s_nown < GAP_CAP) {
-                            o_len[s_nown] = len; o_rank[s_nown] = rank; ++s_nown;
+                            // own blocks are applied in rounds of at most GB_CAP
+                            // floats: 8 zeros, the block padded to a multiple of 4, 8 zeros
+                            const int reg = ((len + 3) & ~3) + 16;
+                            if (s_nown == 0 || rlen + reg > GB_CAP) { o_rnd[s_nrnd++] = s_nown; rlen = 0; rq = 0; }
+                            o_len[s_nown] = len; o_rank[s_nown] = rank; o_off[s_nown] = rlen; o_q[s_nown] = rq;
+                            ++s_nown;
+                            rlen += reg;
+                            rq += (len + 3) >> 2;
                         } else {
                             ovf = 1;
                         }
                     }
                     rank += len;
                     ++nb;
+                    if (++cb == C) cb = 0;
                 }
             }
+            o_rnd[s_nrnd] = s_nown;
             s_ovf = ovf;
         }
         if (!prec && threadIdx.x == 0) s_ovf = 1;
@@ -1011,36 +1138,87 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                     return;
                 }
                 cl.sync();     // every CTA's residual is complete before the gathers
-                for (int bi = 0; bi < s_nown; ++bi) {
-                    const int len = o_len[bi], r0 = o_rank[bi];
-                    const float *xv = xt_det + static_cast<int64_t>(len) * (len - 1) / 2;
-                    for (int u = threadIdx.x; u < len; u += DCT_T) {
-                        gb_r[u] = *rank_ref(c_r, r0 + u);
-                        gb_x[u] = xv[u];
-                    }
-                    __syncthreads();
-                    // u1 = L(x)^T r, u2 = L(w)^T r, w_0 = 0, w_j = x_{L-j}
-                    for (int i = threadIdx.x; i < len; i += DCT_T) {
-                        float s1 = 0.f, s2v = 0.f;
-                        for (int j = i; j < len; ++j) {
-                            const float rj = gb_r[j];
-                            s1 = fmaf(gb_x[j - i], rj, s1);
-                            if (j > i) s2v = fmaf(gb_x[len - (j - i)], rj, s2v);
+                for (int rd = 0; rd < s_nrnd; ++rd) {
+                    const int b0 = o_rnd[rd], b1 = o_rnd[rd + 1];
+                    const int Ll = o_len[b1 - 1];
+                    const int tot = o_off[b1 - 1] + ((Ll + 3) & ~3) + 16;
+                    const int totq = o_q[b1 - 1] + ((Ll + 3) >> 2);
+                    // gather r and each block's generator x (w_s = x_{L-s}, w_0 = 0)
+                    // into zero-padded regions; u1, u2 start at zero
+                    for (int f = threadIdx.x; f < tot; f += DCT_T) {
+                        int b = b0;
+                        while (b + 1 < b1 && o_off[b + 1] <= f) ++b;
+                        const int L = o_len[b], li = f - o_off[b] - 8;
+                        float rv = 0.f, xv = 0.f, wv = 0.f;
+                        if (li >= 0 && li < L) {
+                            const float *xt = xt_det + static_cast<int64_t>(L) * (L - 1) / 2;
+                            rv = *rank_ref(c_r, o_rank[b] + li);
+                            xv = xt[li];
+                            wv = li == 0 ? 0.f : xt[L - li];
                         }
-                        gb_u1[i] = s1;
-                        gb_u2[i] = s2v;
+                        gb_r[f] = rv; gb_x[f] = xv; gb_w[f] = wv; gb_u1[f] = 0.f; gb_u2[f] = 0.f;
                     }
                     __syncthreads();
-                    const float inv_x0 = 1.0f / gb_x[0];
-                    for (int i = threadIdx.x; i < len; i += DCT_T) {
-                        float z1 = 0.f, z2 = 0.f;
-                        for (int j = 0; j <= i; ++j) {
-                            z1 = fmaf(gb_x[i - j], gb_u1[j], z1);
-                            if (j < i) z2 = fmaf(gb_x[len - (i - j)], gb_u2[j], z2);
+                    // u1 = L(x)^T r, u2 = L(w)^T r: four outputs i0..i0+3 per
+                    // thread, float4 loads, the r window slid in registers
+                    for (int qi = threadIdx.x; qi < totq; qi += DCT_T) {
+                        int b = b0;
+                        while (b + 1 < b1 && o_q[b + 1] <= qi) ++b;
+                        const int L = o_len[b], i0 = 4 * (qi - o_q[b]), base = o_off[b] + 8;
+                        const float *xb = gb_x + base, *wb = gb_w + base, *rb = gb_r + base + i0;
+                        float4 a1 = make_float4(0.f, 0.f, 0.f, 0.f), a2 = a1;
+                        float4 rc = *reinterpret_cast<const float4 *>(rb);
+                        for (int k = 0; k < L - i0; k += 4) {
+                            const float4 xk = *reinterpret_cast<const float4 *>(xb + k);
+                            const float4 wk = *reinterpret_cast<const float4 *>(wb + k);
+                            const float4 rn = *reinterpret_cast<const float4 *>(rb + k + 4);
+                            a1.x = fmaf(xk.x, rc.x, fmaf(xk.y, rc.y, fmaf(xk.z, rc.z, fmaf(xk.w, rc.w, a1.x))));
+                            a1.y = fmaf(xk.x, rc.y, fmaf(xk.y, rc.z, fmaf(xk.z, rc.w, fmaf(xk.w, rn.x, a1.y))));
+                            a1.z = fmaf(xk.x, rc.z, fmaf(xk.y, rc.w, fmaf(xk.z, rn.x, fmaf(xk.w, rn.y, a1.z))));
+                            a1.w = fmaf(xk.x, rc.w, fmaf(xk.y, rn.x, fmaf(xk.z, rn.y, fmaf(xk.w, rn.z, a1.w))));
+                            a2.x = fmaf(wk.x, rc.x, fmaf(wk.y, rc.y, fmaf(wk.z, rc.z, fmaf(wk.w, rc.w, a2.x))));
+                            a2.y = fmaf(wk.x, rc.y, fmaf(wk.y, rc.z, fmaf(wk.z, rc.w, fmaf(wk.w, rn.x, a2.y))));
+                            a2.z = fmaf(wk.x, rc.z, fmaf(wk.y, rc.w, fmaf(wk.z, rn.x, fmaf(wk.w, rn.y, a2.z))));
+                            a2.w = fmaf(wk.x, rc.w, fmaf(wk.y, rn.x, fmaf(wk.z, rn.y, fmaf(wk.w, rn.z, a2.w))));
+                            rc = rn;
                         }
-                        *rank_ref(c_z, r0 + i) = (z1 - z2) * inv_x0;
+                        *reinterpret_cast<float4 *>(gb_u1 + base + i0) = a1;
+                        *reinterpret_cast<float4 *>(gb_u2 + base + i0) = a2;
                     }
                     __syncthreads();
+                    // z = (L(x) u1 - L(w) u2) / x_0, scattered to the owners
+                    for (int qi = threadIdx.x; qi < totq; qi += DCT_T) {
+                        int b = b0;
+                        while (b + 1 < b1 && o_q[b + 1] <= qi) ++b;
+                        const int L = o_len[b], i0 = 4 * (qi - o_q[b]), base = o_off[b] + 8;
+                        const float *xb = gb_x + base, *wb = gb_w + base;
+                        const float *u1b = gb_u1 + base + i0, *u2b = gb_u2 + base + i0;
+                        float4 z1 = make_float4(0.f, 0.f, 0.f, 0.f), z2 = z1;
+                        float4 ua = *reinterpret_cast<const float4 *>(u1b);      // u[i0 - s .. i0 - s + 3]
+                        float4 va = *reinterpret_cast<const float4 *>(u2b);
+                        for (int s0 = 0; s0 <= i0; s0 += 4) {
+                            const float4 xs = *reinterpret_cast<const float4 *>(xb + s0);
+                            const float4 ws = *reinterpret_cast<const float4 *>(wb + s0);
+                            const float4 ub = *reinterpret_cast<const float4 *>(u1b - s0 - 4);
+                            const float4 vb = *reinterpret_cast<const float4 *>(u2b - s0 - 4);
+                            z1.x = fmaf(xs.x, ua.x, fmaf(xs.y, ub.w, fmaf(xs.z, ub.z, fmaf(xs.w, ub.y, z1.x))));
+                            z1.y = fmaf(xs.x, ua.y, fmaf(xs.y, ua.x, fmaf(xs.z, ub.w, fmaf(xs.w, ub.z, z1.y))));
+                            z1.z = fmaf(xs.x, ua.z, fmaf(xs.y, ua.y, fmaf(xs.z, ua.x, fmaf(xs.w, ub.w, z1.z))));
+                            z1.w = fmaf(xs.x, ua.w, fmaf(xs.y, ua.z, fmaf(xs.z, ua.y, fmaf(xs.w, ua.x, z1.w))));
+                            z2.x = fmaf(ws.x, va.x, fmaf(ws.y, vb.w, fmaf(ws.z, vb.z, fmaf(ws.w, vb.y, z2.x))));
+                            z2.y = fmaf(ws.x, va.y, fmaf(ws.y, va.x, fmaf(ws.z, vb.w, fmaf(ws.w, vb.z, z2.y))));
+                            z2.z = fmaf(ws.x, va.z, fmaf(ws.y, va.y, fmaf(ws.z, va.x, fmaf(ws.w, vb.w, z2.z))));
+                            z2.w = fmaf(ws.x, va.w, fmaf(ws.y, va.z, fmaf(ws.z, va.y, fmaf(ws.w, va.x, z2.w))));
+                            ua = ub;
+                            va = vb;
+                        }
+                        const float inv = 1.0f / xb[0];
+                        const float zz[4] = {z1.x - z2.x, z1.y - z2.y, z1.z - z2.z, z1.w - z2.w};
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if (i0 + j < L) *rank_ref(c_z, o_rank[b] + i0 + j) = zz[j] * inv;
+                    }
+                    __syncthreads();     // the gb arrays are reused by the next round
                 }
                 cl.sync();     // every scatter into every CTA's c_z is done
             };
@@ -1070,9 +1248,12 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                 cl.sync();     // every buffer is zero before the scatters
                 for (int i = threadIdx.x; i < kc; i += DCT_T) *at(cur, i) = c_p[i];
                 cl.sync();     // every scatter has landed
-                dct_forward(sX, cur, oth, sm.tw1, sm.tw2, cl);
-                apply_filter(X, cur, fscale, alpha, s2, 1, wt);
-                dct_inverse(sX, cur, oth, sm.tw1, sm.tw2, cl);
+                dct_forward_pre(sX, cur, oth, cl);
+                split_roundtrip(X, cur, [&](int e, int, float2 Y) {
+                    const float4 w = wt[e];
+                    return make_float2(Y.x * w.z, Y.y * w.w);
+                });
+                dct_inverse_post(sX, cur, oth, cl);
                 cl.sync();     // every CTA's result is complete before the gathers
                 Acc2 pq_loc = {0.f, 0.f};
                 for (int i = threadIdx.x; i < kc; i += DCT_T) {
@@ -1108,9 +1289,12 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             cl.sync();
             for (int i = threadIdx.x; i < kc; i += DCT_T) *at(cur, i) = c_y[i];
             cl.sync();
-            dct_forward(sX, cur, oth, sm.tw1, sm.tw2, cl);
-            apply_filter(X, cur, fscale, alpha, s2, 0, wt);
-            dct_inverse(sX, cur, oth, sm.tw1, sm.tw2, cl);
+            dct_forward_pre(sX, cur, oth, cl);
+            split_roundtrip(X, cur, [&](int e, int, float2 Y) {
+                const float4 w = wt[e];
+                return make_float2(Y.x * w.x, Y.y * w.y);
+            });
+            dct_inverse_post(sX, cur, oth, cl);
             for (int e = threadIdx.x; e < tot; e += DCT_T) {
                 int t0, t1;
                 bool valid;
@@ -1256,7 +1440,7 @@ static size_t smem_bytes(const Plan &p, bool ncorr)
 {
     size_t b = sizeof(float2) * (2 * static_cast<size_t>(p.sz) + p.twsz);
     if (ncorr) b += static_cast<size_t>(CG_KCAP) * (sizeof(int) + 5 * sizeof(float)) +
-                    sizeof(float) * 4 * TOEP_LMAX;
+                    sizeof(float) * 5 * GB_CAP;
     return b;
 }
 
