@@ -212,15 +212,23 @@ int64_t fft_length_impl(int64_t n)
     return best;
 }
 
-std::vector<int8_t> radix_plan(int L)
+// Stockham radices of a sub-transform of length L: the largest register
+// DFT up to rmax (16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2) that divides what is
+// left.  Both column and row passes put consecutive threads on consecutive
+// vectors (the frequency layout's odd row stride keeps those rows in
+// distinct banks), so every pass may take the largest radix.
+std::vector<int8_t> radix_plan(int L, int rmax = 16)
 {
+    static const int kRadix[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
     std::vector<int8_t> r;
-    while (L % 8 == 0) { r.push_back(8); L /= 8; }
-    while (L % 4 == 0) { r.push_back(4); L /= 4; }
-    while (L % 2 == 0) { r.push_back(2); L /= 2; }
-    while (L % 3 == 0) { r.push_back(3); L /= 3; }
-    while (L % 5 == 0) { r.push_back(5); L /= 5; }
-    if (L != 1) r.clear();
+    while (L > 1) {
+        int pick = 0;
+        for (int R : kRadix)
+            if (R <= rmax && L % R == 0) { pick = R; break; }
+        if (!pick) { r.clear(); return r; }
+        r.push_back(static_cast<int8_t>(pick));
+        L /= pick;
+    }
     return r;
 }
 
@@ -250,7 +258,7 @@ bool choose_factor(int n, int C, DctPlan &out, int &sz)
         const int ncolmax = (m2 + C - 1) / C;
         const int P = m1 / 2 + 1;
         const int npmax = (P + C - 1) / C;
-        const int asz = m1 * ncolmax, bsz = 2 * npmax * m2;
+        const int asz = m1 * ncolmax, bsz = 2 * npmax * (m2 | 1);
         if (asz > DCT_SZ_MAX || bsz > DCT_SZ_MAX) continue;               // shared-memory budget
         // smallest shared-memory footprint (two buffers plus the length's
         // twiddle tables); within 5 % of it, the most balanced split
@@ -264,13 +272,14 @@ bool choose_factor(int n, int C, DctPlan &out, int &sz)
     }
     if (best >= 0) {   // best now holds the buffer size of the chosen split
         const int m2b = m / bestm1;
-        best = std::max(bestm1 * ((m2b + C - 1) / C), 2 * (((bestm1 / 2 + 1) + C - 1) / C) * m2b);
+        best = std::max(bestm1 * ((m2b + C - 1) / C), 2 * (((bestm1 / 2 + 1) + C - 1) / C) * (m2b | 1));
     }
     if (best < 0) return false;
     const int m1 = bestm1, m2 = m / m1;
     const auto r1 = radix_plan(m1), r2 = radix_plan(m2);
     std::memset(&out, 0, sizeof(out));
     out.n = n; out.m = m; out.m1 = m1; out.m2 = m2;
+    out.m2p = m2 | 1;      // odd row stride: rows in consecutive lanes hit distinct banks
     out.ncolmax = (m2 + C - 1) / C;
     out.P = m1 / 2 + 1;
     out.npmax = (out.P + C - 1) / C;

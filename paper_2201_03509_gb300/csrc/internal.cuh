@@ -54,6 +54,7 @@ struct DctStage {
 // FFT split as m1 x m2 across a cluster of C CTAs).
 struct DctPlan {
     int32_t n, m, m1, m2, ncolmax, npmax, P;
+    int32_t m2p;                     // row stride of the frequency layout: m2 made odd
     int32_t nr1, nr2;
     int32_t tw1, tw2;                // offsets of the W_{m1}^i and W_{m2}^i tables
     int32_t twb;                     // offset of this length's twiddle block (see k_dct.cu)

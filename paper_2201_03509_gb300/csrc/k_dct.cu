@@ -109,6 +109,94 @@ template <bool INV> struct Dft<5, INV> {
     }
 };
 
+// Composite radix R = A*B (Cooley-Tukey in registers): with n = B n1 + n2
+// and k = k1 + A k2,
+//   X[k1 + A k2] = sum_n2 W_B^{n2 k2} W_R^{n2 k1} sum_n1 x[B n1 + n2] W_A^{n1 k1}.
+// The inner twiddles W_R^{j} are compile-time constants from a Taylor series
+// (quarter-turn range reduction, |x| < pi/2, 14 terms: below 1e-17).
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+__host__ __device__ constexpr double cx_sin_q(double x) {
+    double term = x, sum = x;
+    for (int i = 1; i < 14; ++i) { term *= -x * x / ((2.0 * i) * (2.0 * i + 1.0)); sum += term; }
+    return sum;
+}
+__host__ __device__ constexpr double cx_cos_q(double x) {
+    double term = 1.0, sum = 1.0;
+    for (int i = 1; i < 14; ++i) { term *= -x * x / ((2.0 * i - 1.0) * (2.0 * i)); sum += term; }
+    return sum;
+}
+// cos and sin of 2 pi j / R
+__host__ __device__ constexpr double cx_cos_turn(int j, int R) {
+    const int jj = ((j % R) + R) % R;
+    const int q = (4 * jj) / R, rem = 4 * jj - q * R;
+    const double x = 0.25 * kTwoPi * rem / R;
+    return q == 0 ? cx_cos_q(x) : q == 1 ? -cx_sin_q(x) : q == 2 ? -cx_cos_q(x) : cx_sin_q(x);
+}
+__host__ __device__ constexpr double cx_sin_turn(int j, int R) {
+    const int jj = ((j % R) + R) % R;
+    const int q = (4 * jj) / R, rem = 4 * jj - q * R;
+    const double x = 0.25 * kTwoPi * rem / R;
+    return q == 0 ? cx_sin_q(x) : q == 1 ? cx_cos_q(x) : q == 2 ? -cx_sin_q(x) : -cx_cos_q(x);
+}
+// v * W_R^{j}, W = exp(-+2 pi i / R); exact for the quarter turns
+template <int R, int J, bool INV>
+__device__ __forceinline__ float2 twiddle_const(float2 v) {
+    constexpr int j = J % R;
+    if constexpr (j == 0) return v;
+    else if constexpr (2 * j == R) return make_float2(-v.x, -v.y);
+    else if constexpr (4 * j == R) return mul_i(v, INV);                 // -i forward
+    else if constexpr (4 * j == 3 * R) return mul_i(v, !INV);            // +i forward
+    else {
+        constexpr float c = static_cast<float>(cx_cos_turn(j, R));
+        constexpr float sn = static_cast<float>(INV ? cx_sin_turn(j, R) : -cx_sin_turn(j, R));
+        return make_float2(v.x * c - v.y * sn, v.x * sn + v.y * c);
+    }
+}
+__host__ __device__ constexpr int dft_first_factor(int R) {
+    return (R % 4 == 0) ? 4 : (R % 3 == 0) ? 3 : (R % 5 == 0) ? 5 : 2;
+}
+template <int A, int B, bool INV> struct DftAB {
+    template <int N2>
+    static __device__ __forceinline__ void inner(const float2 *v, float2 (&t)[B][A]) {
+        if constexpr (N2 < B) {
+            float2 u[A];
+#pragma unroll
+            for (int n1 = 0; n1 < A; ++n1) u[n1] = v[B * n1 + N2];
+            Dft<A, INV>::run(u);
+            twid<N2, 0>(u);
+#pragma unroll
+            for (int k1 = 0; k1 < A; ++k1) t[N2][k1] = u[k1];
+            inner<N2 + 1>(v, t);
+        }
+    }
+    template <int N2, int K1>
+    static __device__ __forceinline__ void twid(float2 *u) {
+        if constexpr (K1 < A) {
+            u[K1] = twiddle_const<A * B, N2 * K1, INV>(u[K1]);
+            twid<N2, K1 + 1>(u);
+        }
+    }
+    static __device__ __forceinline__ void run(float2 *v) {
+        float2 t[B][A];
+        inner<0>(v, t);
+#pragma unroll
+        for (int k1 = 0; k1 < A; ++k1) {
+            float2 w[B];
+#pragma unroll
+            for (int n2 = 0; n2 < B; ++n2) w[n2] = t[n2][k1];
+            Dft<B, INV>::run(w);
+#pragma unroll
+            for (int k2 = 0; k2 < B; ++k2) v[k1 + A * k2] = w[k2];
+        }
+    }
+};
+template <int R, bool INV> struct Dft {
+    static_assert(R % dft_first_factor(R) == 0 && R / dft_first_factor(R) > 1, "composite radix");
+    static __device__ __forceinline__ void run(float2 *v) {
+        DftAB<dft_first_factor(R), R / dft_first_factor(R), INV>::run(v);
+    }
+};
+
 // One Stockham radix-R pass (Govindaraju et al. 2008 formulation) over nvec
 // vectors of length L, out of place from src to dst in shared memory
 // (element stride es, vector stride vs).  Each thread loops over whole
@@ -135,11 +223,33 @@ __device__ __noinline__ void fft_pass(const float2 *__restrict__ src, float2 *__
         const int jq = fdiv(j, st.fNs);
         const int k = j - jq * Ns;
         if (Ns > 1) {
+            if constexpr (R <= 5) {
 #pragma unroll
-            for (int r = 1; r < R; ++r) {
-                float2 t = tw[r * k * tstep];
-                if (INV) t.y = -t.y;
-                v[r] = cmul(v[r], t);
+                for (int r = 1; r < R; ++r) {
+                    float2 t = tw[r * k * tstep];
+                    if (INV) t.y = -t.y;
+                    v[r] = cmul(v[r], t);
+                }
+            } else {
+                // W^r for r = 4q + j: W^{4q} from the table, times W^j (j < 4)
+                // from W^1 by at most two multiplies
+                const int ks = k * tstep;
+                float2 w1 = tw[ks];
+                if (INV) w1.y = -w1.y;
+                const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
+#pragma unroll
+                for (int q4 = 0; q4 < R; q4 += 4) {
+                    float2 wq = make_float2(1.f, 0.f);
+                    if (q4 > 0) { wq = tw[q4 * ks]; if (INV) wq.y = -wq.y; }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int r = q4 + j;
+                        if (r == 0 || r >= R) continue;
+                        const float2 wj = j == 0 ? make_float2(1.f, 0.f) : j == 1 ? w1 : j == 2 ? w2 : w3;
+                        const float2 t = q4 == 0 ? wj : (j == 0 ? wq : cmul(wq, wj));
+                        v[r] = cmul(v[r], t);
+                    }
+                }
             }
         }
         Dft<R, INV>::run(v);
@@ -158,11 +268,19 @@ __device__ void fft_seq(float2 *&cur, float2 *&oth, int L, const DctStage *stage
 {
     for (int s = 0; s < nr; ++s) {
         const DctStage st = stages[s];
-        if (st.R == 8) fft_pass<8, INV>(cur, oth, L, st, nvec, fnvec, es, vs, vfast, tw);
-        else if (st.R == 4) fft_pass<4, INV>(cur, oth, L, st, nvec, fnvec, es, vs, vfast, tw);
-        else if (st.R == 2) fft_pass<2, INV>(cur, oth, L, st, nvec, fnvec, es, vs, vfast, tw);
-        else if (st.R == 3) fft_pass<3, INV>(cur, oth, L, st, nvec, fnvec, es, vs, vfast, tw);
-        else fft_pass<5, INV>(cur, oth, L, st, nvec, fnvec, es, vs, vfast, tw);
+        switch (st.R) {
+        case 16: fft_pass<16, INV>(cur, oth, L, st, nvec, fnvec, es, vs, vfast, tw); break;
+        case 15: fft_pass<15, INV>(cur, oth, L, st, nvec, fnvec, es, vs, vfast, tw); break;
+        case 12: fft_pass<12, INV>(cur, oth, L, st, nvec, fnvec, es, vs, vfast, tw); break;
+        case 10: fft_pass<10, INV>(cur, oth, L, st, nvec, fnvec, es, vs, vfast, tw); break;
+        case 9: fft_pass<9, INV>(cur, oth, L, st, nvec, fnvec, es, vs, vfast, tw); break;
+        case 8: fft_pass<8, INV>(cur, oth, L, st, nvec, fnvec, es, vs, vfast, tw); break;
+        case 6: fft_pass<6, INV>(cur, oth, L, st, nvec, fnvec, es, vs, vfast, tw); break;
+        case 5: fft_pass<5, INV>(cur, oth, L, st, nvec, fnvec, es, vs, vfast, tw); break;
+        case 4: fft_pass<4, INV>(cur, oth, L, st, nvec, fnvec, es, vs, vfast, tw); break;
+        case 3: fft_pass<3, INV>(cur, oth, L, st, nvec, fnvec, es, vs, vfast, tw); break;
+        default: fft_pass<2, INV>(cur, oth, L, st, nvec, fnvec, es, vs, vfast, tw); break;
+        }
         float2 *t = cur; cur = oth; oth = t;
     }
 }
@@ -179,6 +297,8 @@ struct Geo {
     int p0, npl; // local row pairs
     FastDiv f_ncolmax, f_m2, f_npmax;
     float sq_fwd, s0_fwd, sq_inv, s0_inv;   // real-split scales
+    int m2p;                            // row stride of the frequency layout (odd)
+    FastDiv f_2npl;                     // division by the number of local rows
     // twiddles staged in shared memory (see load_plan)
     const float2 *tw1, *tw2;            // W_{m1}^i, W_{m2}^i
     const float2 *sa1, *sb1, *sa5, *sb5;// W_{4n}^{k1}, W_{4n}^{m1 k2}, W_{4n}^{5 k1}, W_{4n}^{5 m1 k2}
@@ -237,7 +357,7 @@ __device__ __forceinline__ float2 split_inv_one(const Geo &X, float2 yk, float2 
 template <bool INV>
 __device__ __noinline__ void split_pass(const Geo X, float2 *__restrict__ U)
 {
-    const int m2 = X.m2, m1 = X.m1, m = X.m, n = X.n, p0 = X.p0;
+    const int m2 = X.m2, m2p = X.m2p, m1 = X.m1, p0 = X.p0;
     const float sq = INV ? X.sq_inv : X.sq_fwd;
     const float s0 = INV ? X.s0_inv : X.s0_fwd;
     const int total = X.npl * m2;
@@ -249,9 +369,9 @@ __device__ __noinline__ void split_pass(const Geo X, float2 *__restrict__ U)
         if (k2 >= cnt) continue;
         // partner m - k: row (m1 - p) mod m1, column m2-1-k2 (p > 0) or (m2-k2) mod m2 (p = 0)
         int ib, q1, q2;
-        if (p == 0) { q1 = 0; q2 = (k2 == 0) ? 0 : m2 - k2; ib = 2 * pl * m2 + q2; }
-        else { q1 = m1 - p; q2 = m2 - 1 - k2; ib = ((q1 == p) ? 2 * pl : 2 * pl + 1) * m2 + q2; }
-        const int ia = 2 * pl * m2 + k2;
+        if (p == 0) { q1 = 0; q2 = (k2 == 0) ? 0 : m2 - k2; ib = 2 * pl * m2p + q2; }
+        else { q1 = m1 - p; q2 = m2 - 1 - k2; ib = ((q1 == p) ? 2 * pl : 2 * pl + 1) * m2p + q2; }
+        const int ia = 2 * pl * m2p + k2;
         const float2 Za = U[ia], Zb = U[ib];
         if (p == 0 && k2 == 0) {
             if (!INV) {
@@ -285,7 +405,7 @@ template <class F>
 __device__ __forceinline__ void split_roundtrip(const Geo &XS, float2 *__restrict__ U, F f)
 {
     const Geo X = XS;       // registers: the stores to U cannot alias it
-    const int m2 = X.m2, m1 = X.m1, p0 = X.p0;
+    const int m2 = X.m2, m2p = X.m2p, m1 = X.m1, p0 = X.p0;
     const float sqf = X.sq_fwd, s0f = X.s0_fwd, sqi = X.sq_inv, s0i = X.s0_inv;
     const int total = X.npl * m2;
     const FastDiv fm2 = X.f_m2;
@@ -295,9 +415,9 @@ __device__ __forceinline__ void split_roundtrip(const Geo &XS, float2 *__restric
         const int cnt = (p == 0) ? (m2 / 2 + 1) : ((2 * p == m1) ? (m2 + 1) / 2 : m2);
         if (k2 >= cnt) continue;
         int ib, q1, q2;
-        if (p == 0) { q1 = 0; q2 = (k2 == 0) ? 0 : m2 - k2; ib = 2 * pl * m2 + q2; }
-        else { q1 = m1 - p; q2 = m2 - 1 - k2; ib = ((q1 == p) ? 2 * pl : 2 * pl + 1) * m2 + q2; }
-        const int ia = 2 * pl * m2 + k2;
+        if (p == 0) { q1 = 0; q2 = (k2 == 0) ? 0 : m2 - k2; ib = 2 * pl * m2p + q2; }
+        else { q1 = m1 - p; q2 = m2 - 1 - k2; ib = ((q1 == p) ? 2 * pl : 2 * pl + 1) * m2p + q2; }
+        const int ia = 2 * pl * m2p + k2;
         const float2 Za = U[ia], Zb = U[ib];
         if (p == 0 && k2 == 0) {
             float2 Y = make_float2((Za.x + Za.y) * s0f, (Za.x - Za.y) * s0f);
@@ -354,7 +474,10 @@ __device__ __noinline__ void transpose(const Geo X, const float2 *src, float2 *_
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int e = e0 + u * DCT_T;
-                if (e < total) dst[e] = cmul(v[u], w[u]);
+                if (e < total) {
+                    const int slot = fdiv(e, fm2);
+                    dst[e + slot * (X.m2p - m2)] = cmul(v[u], w[u]);
+                }
             }
         }
     } else {
@@ -374,7 +497,7 @@ __device__ __noinline__ void transpose(const Geo X, const float2 *src, float2 *_
                         const int p = min(k1, m1 - k1);
                         const int o = fdiv(p, fnp);
                         const int slot = 2 * (p - o * npmax) + (k1 == p ? 0 : 1);
-                        v[u] = cl.map_shared_rank(src, o)[slot * m2 + j2];
+                        v[u] = cl.map_shared_rank(src, o)[slot * X.m2p + j2];
                         w[u] = tw4_lookup(X, j2 * k1);
                     }
                 }
@@ -389,6 +512,49 @@ __device__ __noinline__ void transpose(const Geo X, const float2 *src, float2 *_
     cl.sync();
 }
 
+// Transposes by remote stores ("push"): every CTA multiplies its own
+// elements by the four-step twiddle and stores them straight into the
+// owner's buffer, so no thread waits on a remote load.  The first cluster
+// barrier keeps every destination buffer free until its owner is done with
+// it; the second makes all stores visible.
+template <bool INV>
+__device__ __noinline__ void transpose_push(const Geo X, const float2 *__restrict__ src, float2 *dst,
+                                            cg::cluster_group &cl)
+{
+    const int m1 = X.m1, m2 = X.m2, ncolmax = X.ncolmax, npmax = X.npmax, c = X.c, ncol = X.ncol;
+    cl.sync();
+    if (!INV) {
+        const int total = m1 * ncolmax;
+        const FastDiv fnc = X.f_ncolmax, fnp = X.f_npmax;
+        for (int e = threadIdx.x; e < total; e += DCT_T) {
+            const int k1 = fdiv(e, fnc), lc = e - k1 * ncolmax;
+            if (lc >= ncol) continue;
+            const int j2 = c * ncolmax + lc;
+            const int p = min(k1, m1 - k1);
+            const int o = fdiv(p, fnp);
+            const int slot = 2 * (p - o * npmax) + (k1 == p ? 0 : 1);
+            *cl.map_shared_rank(dst + slot * X.m2p + j2, o) = cmul(src[e], tw4_lookup(X, j2 * k1));
+        }
+    } else {
+        const int total = 2 * X.npl * m2;
+        const FastDiv fm2 = X.f_m2, fnc = X.f_ncolmax;
+        for (int e = threadIdx.x; e < total; e += DCT_T) {
+            const int slot = fdiv(e, fm2), j2 = e - slot * m2;
+            const int k1 = slot_row(X, slot);
+            if (k1 < 0) continue;
+            const int o = fdiv(j2, fnc), lc = j2 - o * ncolmax;
+            *cl.map_shared_rank(dst + k1 * ncolmax + lc, o) = cmulc(src[slot * X.m2p + j2],
+                                                                   tw4_lookup(X, j2 * k1));
+        }
+        // padding columns of this CTA's own time layout stay zero
+        for (int e = threadIdx.x; e < m1 * ncolmax; e += DCT_T) {
+            const int k1 = fdiv(e, fnc);
+            if (e - k1 * ncolmax >= ncol) dst[e] = make_float2(0.f, 0.f);
+        }
+    }
+    cl.sync();
+}
+
 // Forward DCT: time layout in cur -> packed spectrum in cur (the two
 // buffers may swap roles).
 __device__ __noinline__ void dct_forward(const Ctx &XS, float2 *&cur, float2 *&oth, const float2 *,
@@ -397,9 +563,9 @@ __device__ __noinline__ void dct_forward(const Ctx &XS, float2 *&cur, float2 *&o
     const Geo X = XS;
     const float2 *tw1 = X.tw1, *tw2 = X.tw2;
     fft_seq<false>(cur, oth, X.m1, XS.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, tw1);
-    transpose<false>(X, cur, oth, cl);
+    transpose_push<false>(X, cur, oth, cl);
     { float2 *t = cur; cur = oth; oth = t; }
-    fft_seq<false>(cur, oth, X.m2, XS.s2, X.nr2, 2 * X.npl, X.f_m2, 1, X.m2, false, tw2);
+    fft_seq<false>(cur, oth, X.m2, XS.s2, X.nr2, 2 * X.npl, X.f_2npl, 1, X.m2p, true, tw2);
     split_pass<false>(X, cur);
 }
 // Inverse (transpose of the orthonormal DCT-II): packed spectrum in cur ->
@@ -410,8 +576,8 @@ __device__ __noinline__ void dct_inverse(const Ctx &XS, float2 *&cur, float2 *&o
     const Geo X = XS;
     const float2 *tw1 = X.tw1, *tw2 = X.tw2;
     split_pass<true>(X, cur);
-    fft_seq<true>(cur, oth, X.m2, XS.s2, X.nr2, 2 * X.npl, X.f_m2, 1, X.m2, false, tw2);
-    transpose<true>(X, cur, oth, cl);
+    fft_seq<true>(cur, oth, X.m2, XS.s2, X.nr2, 2 * X.npl, X.f_2npl, 1, X.m2p, true, tw2);
+    transpose_push<true>(X, cur, oth, cl);
     { float2 *t = cur; cur = oth; oth = t; }
     fft_seq<true>(cur, oth, X.m1, XS.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, tw1);
 }
@@ -422,15 +588,15 @@ __device__ __noinline__ void dct_forward_pre(const Ctx &XS, float2 *&cur, float2
 {
     const Geo X = XS;
     fft_seq<false>(cur, oth, X.m1, XS.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, X.tw1);
-    transpose<false>(X, cur, oth, cl);
+    transpose_push<false>(X, cur, oth, cl);
     { float2 *t = cur; cur = oth; oth = t; }
-    fft_seq<false>(cur, oth, X.m2, XS.s2, X.nr2, 2 * X.npl, X.f_m2, 1, X.m2, false, X.tw2);
+    fft_seq<false>(cur, oth, X.m2, XS.s2, X.nr2, 2 * X.npl, X.f_2npl, 1, X.m2p, true, X.tw2);
 }
 __device__ __noinline__ void dct_inverse_post(const Ctx &XS, float2 *&cur, float2 *&oth, cg::cluster_group &cl)
 {
     const Geo X = XS;
-    fft_seq<true>(cur, oth, X.m2, XS.s2, X.nr2, 2 * X.npl, X.f_m2, 1, X.m2, false, X.tw2);
-    transpose<true>(X, cur, oth, cl);
+    fft_seq<true>(cur, oth, X.m2, XS.s2, X.nr2, 2 * X.npl, X.f_2npl, 1, X.m2p, true, X.tw2);
+    transpose_push<true>(X, cur, oth, cl);
     { float2 *t = cur; cur = oth; oth = t; }
     fft_seq<true>(cur, oth, X.m1, XS.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, X.tw1);
 }
@@ -577,6 +743,8 @@ __device__ void load_plan(Ctx *sX, const DctPlan *plans, int pi, const float2 *t
         X.npl = max(0, min(P.npmax, P.P - X.p0));
         X.f_ncolmax = P.f_ncolmax; X.f_m2 = P.f_m2; X.f_npmax = P.f_npmax;
         X.sq_fwd = P.sq_fwd; X.s0_fwd = P.s0_fwd; X.sq_inv = P.sq_inv; X.s0_inv = P.s0_inv;
+        X.m2p = P.m2p;
+        X.f_2npl = make_fastdiv_dev(static_cast<uint32_t>(max(1, 2 * X.npl)));
         const float2 *b = sm.twb;
         X.tw1 = b; b += P.m1;
         X.tw2 = b; b += P.m2;
@@ -618,46 +786,6 @@ __device__ __forceinline__ void sample_loc(const Geo &X, int t, int &owner, int 
     loc = 2 * (j1 * X.ncolmax + lc) + (i & 1);
 }
 
-// Multiply the packed spectrum in U by a per-mode weight:
-//   kind 0: beta_kappa  = 1/(phi_kappa + 1/sigma0^2) = s2/(1 + r)
-//   kind 1: gamma_kappa = sigma0^2 - beta_kappa     = s2 r/(1 + r)
-//   kind 2: 1/P_kappa = 1/(s2 (1 + (f/f_knee)^alpha)),  0 at kappa = 0
-// with r = sigma0^2 phi = (f/f_knee)^-alpha (r = 0 at kappa = 0).  gamma is
-// evaluated directly, so the Schur operator sigma0^2 I - E^T B^{-1} E =
-// E^T C^T diag(gamma) C E carries no FP32 cancellation on its small modes.
-// Kinds 0 and 1 read (beta_a, beta_b, gamma_a, gamma_b) per packed element
-// from wt, filled once per detscan by fill_weights.
-__device__ __noinline__ void apply_filter(const Geo X, float2 *__restrict__ U, float fscale, float alpha, float s2,
-                                          int kind, const float4 *__restrict__ wt)
-{
-    const int total = 2 * X.npl * X.m2;
-    const FastDiv fm2 = X.f_m2;
-    if (kind != 2) {
-        for (int e = threadIdx.x; e < total; e += DCT_T) {
-            const float4 w = wt[e];
-            float2 v = U[e];
-            v.x *= kind ? w.z : w.x;
-            v.y *= kind ? w.w : w.y;
-            U[e] = v;
-        }
-        __syncthreads();
-        return;
-    }
-    for (int e = threadIdx.x; e < total; e += DCT_T) {
-        const int slot = fdiv(e, fm2), k2 = e - slot * X.m2;
-        const int k1 = slot_row(X, slot);
-        if (k1 < 0) continue;
-        const int k = k1 + X.m1 * k2;
-        const int ka = k, kb = (k == 0) ? X.m : X.n - k;
-        const float wa = (ka == 0) ? 0.f : 1.0f / (s2 * (1.0f + fratio_pow(ka, fscale, alpha)));
-        const float wb = 1.0f / (s2 * (1.0f + fratio_pow(kb, fscale, alpha)));
-        float2 v = U[e];
-        v.x *= wa;
-        v.y *= wb;
-        U[e] = v;
-    }
-    __syncthreads();
-}
 
 // ---------------------------------------------------------------------------
 // A4: gain.  a = sum_{k>=1} shat_k^2 / P_k from the forward transform of
@@ -943,7 +1071,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                     if (k < kbase || k >= kbase + npl) continue;
                     const int pl = par == 0 ? k - kbase : (npl - 1) - (k - kbase);
                     const int p = p0 + pl;
-                    const int e = (2 * pl + par) * m2 + k2;
+                    const int e = (2 * pl + par) * X.m2p + k2;
                     if (par == 1 && (p == 0 || m1 - p == p)) {            // slot holds no modes
                         wt[e] = make_float4(0.f, 0.f, 0.f, 0.f);
                         oth[e] = make_float2(0.f, 0.f);
@@ -1372,8 +1500,9 @@ __global__ void __launch_bounds__(DCT_T, 1) k_chi2(Chi2Args a)
         Acc2 aq = {0.f, 0.f}, al1 = {0.f, 0.f}, afk = {0.f, 0.f}, aal = {0.f, 0.f};
         {
             const int total = 2 * X.npl * X.m2;
-            for (int e = threadIdx.x; e < total; e += DCT_T) {
-                const int slot = fdiv(e, X.f_m2), k2 = e - slot * X.m2;
+            for (int e0 = threadIdx.x; e0 < total; e0 += DCT_T) {
+                const int slot = fdiv(e0, X.f_m2), k2 = e0 - slot * X.m2;
+                const int e = slot * X.m2p + k2;
                 const int k1 = slot_row(X, slot);
                 if (k1 < 0) continue;
                 const int k = k1 + X.m1 * k2;

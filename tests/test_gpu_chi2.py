@@ -70,8 +70,8 @@ def test_chi2_value_and_gradients_match_oracle(setup):
 def test_chi2_gain_gradient_matches_gpu_finite_difference(setup):
     """Central difference of the GPU forward itself.  The chi-squared is
     quadratic in each gain, so the central difference is exact for any step;
-    a 10 % step keeps the difference far above the FP32 rounding of the
-    transforms (FP64 sums of FP32 values)."""
+    a step of the gain's own size keeps the difference far above the FP32
+    rounding of the transforms (FP64 sums of FP32 values)."""
     S = setup
     torch = S["torch"]
     from paper_2201_03509_gb300.chi2 import tod_chi2
@@ -82,7 +82,7 @@ def test_chi2_gain_gradient_matches_gpu_finite_difference(setup):
     L = tod_chi2(tm, g, psd, S["plan"], S["d"], S["flags"], S["pix"], S["psi"])
     L.backward()
     q = 1
-    h = 0.1
+    h = 1.0
     gp, gmn = gains.clone(), gains.clone()
     gp[q] += h
     gmn[q] -= h
