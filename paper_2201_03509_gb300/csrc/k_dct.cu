@@ -355,8 +355,9 @@ __device__ __forceinline__ float2 split_inv_one(const Geo &X, float2 yk, float2 
 
 // Real split over this CTA's row pairs, in place (forward or inverse).
 template <bool INV>
-__device__ __noinline__ void split_pass(const Geo X, float2 *__restrict__ U)
+__device__ __noinline__ void split_pass(const Ctx &XS, float2 *__restrict__ U)
 {
+    const Geo X = XS;       // from shared memory into registers (no by-value copy on the stack)
     const int m2 = X.m2, m2p = X.m2p, m1 = X.m1, p0 = X.p0;
     const float sq = INV ? X.sq_inv : X.sq_fwd;
     const float s0 = INV ? X.s0_inv : X.s0_fwd;
@@ -445,9 +446,10 @@ __device__ __forceinline__ void split_roundtrip(const Geo &XS, float2 *__restric
 // first cluster barrier makes every CTA's src complete; the second keeps
 // src alive until every remote read of it has finished.
 template <bool INV>
-__device__ __noinline__ void transpose(const Geo X, const float2 *src, float2 *__restrict__ dst,
+__device__ __noinline__ void transpose(const Ctx &XS, const float2 *src, float2 *__restrict__ dst,
                                        cg::cluster_group &cl)
 {
+    const Geo X = XS;
     constexpr int U = 4;     // independent remote reads in flight per thread
     const int m = X.m, m1 = X.m1, m2 = X.m2, ncolmax = X.ncolmax, npmax = X.npmax;
     cl.sync();
@@ -518,9 +520,10 @@ __device__ __noinline__ void transpose(const Geo X, const float2 *src, float2 *_
 // barrier keeps every destination buffer free until its owner is done with
 // it; the second makes all stores visible.
 template <bool INV>
-__device__ __noinline__ void transpose_push(const Geo X, const float2 *__restrict__ src, float2 *dst,
+__device__ __noinline__ void transpose_push(const Ctx &XS, const float2 *__restrict__ src, float2 *dst,
                                             cg::cluster_group &cl)
 {
+    const Geo X = XS;
     const int m1 = X.m1, m2 = X.m2, ncolmax = X.ncolmax, npmax = X.npmax, c = X.c, ncol = X.ncol;
     cl.sync();
     if (!INV) {
@@ -563,10 +566,10 @@ __device__ __noinline__ void dct_forward(const Ctx &XS, float2 *&cur, float2 *&o
     const Geo X = XS;
     const float2 *tw1 = X.tw1, *tw2 = X.tw2;
     fft_seq<false>(cur, oth, X.m1, XS.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, tw1);
-    transpose_push<false>(X, cur, oth, cl);
+    transpose<false>(XS, cur, oth, cl);
     { float2 *t = cur; cur = oth; oth = t; }
     fft_seq<false>(cur, oth, X.m2, XS.s2, X.nr2, 2 * X.npl, X.f_2npl, 1, X.m2p, true, tw2);
-    split_pass<false>(X, cur);
+    split_pass<false>(XS, cur);
 }
 // Inverse (transpose of the orthonormal DCT-II): packed spectrum in cur ->
 // time layout in cur, scaled.
@@ -575,9 +578,9 @@ __device__ __noinline__ void dct_inverse(const Ctx &XS, float2 *&cur, float2 *&o
 {
     const Geo X = XS;
     const float2 *tw1 = X.tw1, *tw2 = X.tw2;
-    split_pass<true>(X, cur);
+    split_pass<true>(XS, cur);
     fft_seq<true>(cur, oth, X.m2, XS.s2, X.nr2, 2 * X.npl, X.f_2npl, 1, X.m2p, true, tw2);
-    transpose_push<true>(X, cur, oth, cl);
+    transpose<true>(XS, cur, oth, cl);
     { float2 *t = cur; cur = oth; oth = t; }
     fft_seq<true>(cur, oth, X.m1, XS.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, tw1);
 }
@@ -588,7 +591,7 @@ __device__ __noinline__ void dct_forward_pre(const Ctx &XS, float2 *&cur, float2
 {
     const Geo X = XS;
     fft_seq<false>(cur, oth, X.m1, XS.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, X.tw1);
-    transpose_push<false>(X, cur, oth, cl);
+    transpose<false>(XS, cur, oth, cl);
     { float2 *t = cur; cur = oth; oth = t; }
     fft_seq<false>(cur, oth, X.m2, XS.s2, X.nr2, 2 * X.npl, X.f_2npl, 1, X.m2p, true, X.tw2);
 }
@@ -596,7 +599,7 @@ __device__ __noinline__ void dct_inverse_post(const Ctx &XS, float2 *&cur, float
 {
     const Geo X = XS;
     fft_seq<true>(cur, oth, X.m2, XS.s2, X.nr2, 2 * X.npl, X.f_2npl, 1, X.m2p, true, X.tw2);
-    transpose_push<true>(X, cur, oth, cl);
+    transpose<true>(XS, cur, oth, cl);
     { float2 *t = cur; cur = oth; oth = t; }
     fft_seq<true>(cur, oth, X.m1, XS.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, X.tw1);
 }
