@@ -19,7 +19,7 @@ constexpr int DCT_MAXR = 20;          // maximum number of radix stages per sub-
 constexpr int CG_KCAP = 768;          // flagged samples per CTA held by the CG
 constexpr int TOEP_LMAX = 512;        // longest gap block of the Toeplitz preconditioner
 constexpr int GB_CAP = 1024;          // preconditioner elements applied per round in one CTA
-constexpr int BIN_TILE = 4096;        // sorted samples staged per binning tile
+constexpr int BIN_TILE = 2048;        // sorted samples staged per binning tile
 constexpr int GAP_CAP = 256;          // gap blocks per detscan handled by the preconditioner
 
 // Compressed stream kind, device copy + decode tables.

@@ -96,7 +96,7 @@ __device__ __forceinline__ uint16_t psi_flag(const BinArgs &a, int64_t tg) {
 __global__ void __launch_bounds__(BIN_T) k_bin(BinArgs a)
 {
     __shared__ float s_d[BIN_TILE], s_x[BIN_TILE];
-    __shared__ uint16_t s_pf[BIN_TILE];
+    __shared__ float2 s_cs[BIN_TILE];
     __shared__ Acc2 s_red[BIN_T / 32][11];
     __shared__ int s_hits[BIN_T / 32];
     const int tile = blockIdx.x;
@@ -156,37 +156,59 @@ __global__ void __launch_bounds__(BIN_T) k_bin(BinArgs a)
         return;
     }
 
-    // gather in sorted order: four independent loads in flight per thread
-    for (int i0 = threadIdx.x; i0 < cnt; i0 += 4 * BIN_T) {
-        int64_t tg[4];
+    // gather in sorted order: the tile's sorted positions first, then every
+    // value load of the thread in flight together; cos 2psi and sin 2psi are
+    // staged with the data, and a flagged sample is marked by cos = 2
+    constexpr int PER = BIN_TILE / BIN_T;
+    int idx[PER];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = i0 + u * BIN_T;
-            tg[u] = i < cnt ? o + __ldg(a.srt + s0 + i) : -1;
-        }
+    for (int u = 0; u < PER; ++u) {
+        const int i = threadIdx.x + u * BIN_T;
+        idx[u] = i < cnt ? static_cast<int>(__ldg(a.srt + s0 + i)) : -1;
+    }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = i0 + u * BIN_T;
-            if (tg[u] >= 0) {
-                s_d[i] = __ldg(a.d + tg[u]);
-                s_x[i] = __ldg(a.x + tg[u]);
-                s_pf[i] = psi_flag(a, tg[u]);
-            }
-        }
+    for (int u = 0; u < PER; ++u) {
+        const int i = threadIdx.x + u * BIN_T;
+        if (idx[u] < 0) continue;
+        const int64_t tg = o + idx[u];
+        const uint16_t pf = psi_flag(a, tg);
+        float2 cs = __ldg(a.trig + (pf & 0x0FFF));
+        if (pf >> 15) cs.x = 2.0f;
+        s_cs[i] = cs;
+        s_d[i] = __ldg(a.d + tg);
+        s_x[i] = __ldg(a.x + tg);
     }
     __syncthreads();
-    for (int r = threadIdx.x; r < nr; r += BIN_T) {
-        const int pr = r0 + r;
-        const int st = static_cast<int>(a.pair_start[pr] - s0);
-        const int len = a.pair_len[pr];
+    // four lanes per run: lane j of the quad takes samples j, j+4, ...; the
+    // quad's partial sums are merged in a fixed order (deterministic)
+    const int quad = threadIdx.x >> 2, ql = threadIdx.x & 3;
+    for (int rb = 0; rb < nr; rb += BIN_T / 4) {
+        const int r = rb + quad;
         RunSums rs;
         sums_zero(rs);
-        for (int i = st; i < st + len; ++i) {
-            const uint16_t pf = s_pf[i];
-            if (pf >> 15) continue;
-            sums_add(rs, __ldg(a.trig + (pf & 0x0FFF)), s_d[i], s_x[i]);
+        int pr = -1;
+        if (r < nr) {
+            pr = r0 + r;
+            const int st = static_cast<int>(a.pair_start[pr] - s0);
+            const int len = a.pair_len[pr];
+            for (int i = st + ql; i < st + len; i += 4) {
+                const float2 cs = s_cs[i];
+                if (cs.x > 1.5f) continue;
+                sums_add(rs, cs, s_d[i], s_x[i]);
+            }
         }
-        sums_store(rs, wA, wb, a.rec + static_cast<int64_t>(a.pair_slot[pr]) * 10);
+#pragma unroll
+        for (int ofs = 1; ofs <= 2; ofs <<= 1) {
+#pragma unroll
+            for (int k = 0; k < 11; ++k) {
+                Acc2 o2;
+                o2.s = __shfl_xor_sync(0xffffffffu, rs.a[k].s, ofs);
+                o2.c = __shfl_xor_sync(0xffffffffu, rs.a[k].c, ofs);
+                rs.a[k] = (ql & ofs) ? acc_merge(o2, rs.a[k]) : acc_merge(rs.a[k], o2);
+            }
+            rs.hits += __shfl_xor_sync(0xffffffffu, rs.hits, ofs);
+        }
+        if (pr >= 0 && ql == 0) sums_store(rs, wA, wb, a.rec + static_cast<int64_t>(a.pair_slot[pr]) * 10);
     }
 }
 

@@ -514,50 +514,6 @@ __device__ __noinline__ void transpose(const Ctx &XS, const float2 *src, float2 
     cl.sync();
 }
 
-// Transposes by remote stores ("push"): every CTA multiplies its own
-// elements by the four-step twiddle and stores them straight into the
-// owner's buffer, so no thread waits on a remote load.  The first cluster
-// barrier keeps every destination buffer free until its owner is done with
-// it; the second makes all stores visible.
-template <bool INV>
-__device__ __noinline__ void transpose_push(const Ctx &XS, const float2 *__restrict__ src, float2 *dst,
-                                            cg::cluster_group &cl)
-{
-    const Geo X = XS;
-    const int m1 = X.m1, m2 = X.m2, ncolmax = X.ncolmax, npmax = X.npmax, c = X.c, ncol = X.ncol;
-    cl.sync();
-    if (!INV) {
-        const int total = m1 * ncolmax;
-        const FastDiv fnc = X.f_ncolmax, fnp = X.f_npmax;
-        for (int e = threadIdx.x; e < total; e += DCT_T) {
-            const int k1 = fdiv(e, fnc), lc = e - k1 * ncolmax;
-            if (lc >= ncol) continue;
-            const int j2 = c * ncolmax + lc;
-            const int p = min(k1, m1 - k1);
-            const int o = fdiv(p, fnp);
-            const int slot = 2 * (p - o * npmax) + (k1 == p ? 0 : 1);
-            *cl.map_shared_rank(dst + slot * X.m2p + j2, o) = cmul(src[e], tw4_lookup(X, j2 * k1));
-        }
-    } else {
-        const int total = 2 * X.npl * m2;
-        const FastDiv fm2 = X.f_m2, fnc = X.f_ncolmax;
-        for (int e = threadIdx.x; e < total; e += DCT_T) {
-            const int slot = fdiv(e, fm2), j2 = e - slot * m2;
-            const int k1 = slot_row(X, slot);
-            if (k1 < 0) continue;
-            const int o = fdiv(j2, fnc), lc = j2 - o * ncolmax;
-            *cl.map_shared_rank(dst + k1 * ncolmax + lc, o) = cmulc(src[slot * X.m2p + j2],
-                                                                   tw4_lookup(X, j2 * k1));
-        }
-        // padding columns of this CTA's own time layout stay zero
-        for (int e = threadIdx.x; e < m1 * ncolmax; e += DCT_T) {
-            const int k1 = fdiv(e, fnc);
-            if (e - k1 * ncolmax >= ncol) dst[e] = make_float2(0.f, 0.f);
-        }
-    }
-    cl.sync();
-}
-
 // Forward DCT: time layout in cur -> packed spectrum in cur (the two
 // buffers may swap roles).
 __device__ __noinline__ void dct_forward(const Ctx &XS, float2 *&cur, float2 *&oth, const float2 *,
@@ -941,6 +897,216 @@ __device__ int3 block_exscan3(int3 v, int3 *s_w, int3 &total)
     return make_int3(b.x + inc.x - v.x, b.y + inc.y - v.y, b.z + inc.z - v.z);
 }
 
+// Own gap blocks of the preconditioner, applied in rounds of at most GB_CAP
+// padded elements (see the own-block set-up in k_ncorr).
+struct OwnBlocks {
+    int len[GAP_CAP], rank[GAP_CAP], off[GAP_CAP], q[GAP_CAP];
+    int rnd[GAP_CAP + 1];
+    int nrnd;
+};
+
+// CG vector element of global rank k: (CTA k / kper, index k mod kper)
+__device__ __forceinline__ float *rank_elem(cg::cluster_group &cl, float *vec, int kper, int k) {
+    const int ow = k / kper;
+    return cl.map_shared_rank(vec + (k - ow * kper), ow);
+}
+
+// Right-hand side of the n_corr system, time-domain part, M (r/s2 + w1/s)
+// with r = d - g s, into the time layout of U.  Element j takes normals 2j,
+// 2j+1 (pair j mod 4 of Philox block j/4 of stream 1): one thread draws a
+// block for four consecutive elements of a row.
+__device__ __noinline__ void ncorr_rhs(const Ctx &XS, float2 *__restrict__ U, const float *__restrict__ dq,
+                                       const float *__restrict__ sq, const uint32_t *__restrict__ fl, int64_t o,
+                                       float g, float inv_s2, float inv_s, bool draw, uint64_t q, uint64_t gi,
+                                       uint64_t seed, uint64_t band)
+{
+    const Geo X = XS;
+    const int n = X.n, m = X.m;
+    const int ncol = X.ncol, nbr = (ncol + 3) / 4 + 1;     // blocks touching a row
+    const int items = X.m1 * nbr;
+    for (int w = threadIdx.x; w < items; w += DCT_T) {
+        const int j1 = w / nbr, bi = w - j1 * nbr;
+        const int js = j1 * X.m2 + X.c * X.ncolmax;          // first element of the row
+        const int b = (js >> 2) + bi;
+        if (4 * b >= js + ncol) continue;
+        u64x4 rw;
+        if (draw) rw = philox4x64(static_cast<uint64_t>(b), q, 1, gi, seed, band);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = 4 * b + u;
+            if (j < js || j >= js + ncol) continue;
+            const int t0 = vpos_t(2 * j, n, m), t1 = vpos_t(2 * j + 1, n, m);
+            const float2 w1 = draw ? philox_normal_pair(rw, u) : make_float2(0.f, 0.f);
+            const float d0 = __ldg(dq + t0), d1 = __ldg(dq + t1);
+            const float s0v = __ldg(sq + t0), s1v = __ldg(sq + t1);
+            const float r0 = flagged(fl, o + t0) ? 0.f : fmaf(d0 - g * s0v, inv_s2, w1.x * inv_s);
+            const float r1 = flagged(fl, o + t1) ? 0.f : fmaf(d1 - g * s1v, inv_s2, w1.y * inv_s);
+            U[j1 * X.ncolmax + (j - js)] = make_float2(r0, r1);
+        }
+    }
+    // padding columns of the last CTA stay zero
+    for (int e = threadIdx.x; e < X.m1 * X.ncolmax; e += DCT_T) {
+        const int j1 = fdiv(e, X.f_ncolmax);
+        if (e - j1 * X.ncolmax >= ncol) U[e] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+}
+
+// Per packed slot of this CTA: the filter weights (beta_a, beta_b, gamma_a,
+// gamma_b) of its two modes into wt, and the prior term sqrt(phi) w2 into
+// nu (zero when not drawing).  Mode k takes normals 2k, 2k+1 (pair k mod 4
+// of block k/4 of stream 2); for a fixed k2 the own even slots hold
+// k = p0 + pl + m1 k2 and the odd ones k = m1 - p0 - pl + m1 k2 (pl < npl),
+// so one thread draws a block for up to four consecutive modes of a parity.
+__device__ __noinline__ void ncorr_weights(const Ctx &XS, float2 *__restrict__ nu_out, float4 *__restrict__ wt,
+                                           float fscale, float alpha, float s2, float inv_s2, bool draw,
+                                           uint64_t q, uint64_t gi, uint64_t seed, uint64_t band)
+{
+    const Geo X = XS;
+    const int n = X.n, m = X.m;
+    const int npl = X.npl, m1 = X.m1, m2 = X.m2, p0 = X.p0;
+    const int nbk = (npl + 3) / 4 + 1;                  // blocks touching a k range
+    const int items = 2 * nbk * m2;
+    for (int w = threadIdx.x; w < items; w += DCT_T) {
+        const int rest = fdiv(w, X.f_m2), k2 = w - rest * m2;
+        const int par = rest / nbk, bi = rest - par * nbk;
+        const int kbase = (par == 0 ? p0 : m1 - p0 - (npl - 1)) + m1 * k2;
+        const int b = (kbase >> 2) + bi;
+        if (npl <= 0 || 4 * b >= kbase + npl) continue;
+        u64x4 rw;
+        if (draw) rw = philox4x64(static_cast<uint64_t>(b), q, 2, gi, seed, band);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = 4 * b + u;
+            if (k < kbase || k >= kbase + npl) continue;
+            const int pl = par == 0 ? k - kbase : (npl - 1) - (k - kbase);
+            const int p = p0 + pl;
+            const int e = (2 * pl + par) * X.m2p + k2;
+            if (par == 1 && (p == 0 || m1 - p == p)) {            // slot holds no modes
+                wt[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+                nu_out[e] = make_float2(0.f, 0.f);
+                continue;
+            }
+            const int ka = k, kb = (k == 0) ? m : n - k;
+            const float ra = (ka == 0) ? 0.f : fratio_pow(ka, fscale, -alpha);   // s2 phi
+            const float rb = fratio_pow(kb, fscale, -alpha);
+            const float ba = s2 / (1.0f + ra), bb = s2 / (1.0f + rb);
+            wt[e] = make_float4(ba, bb, ra * ba, rb * bb);
+            float2 nu = make_float2(0.f, 0.f);
+            if (draw) {
+                const float2 w2 = philox_normal_pair(rw, u);
+                nu = make_float2(sqrtf(ra * inv_s2) * w2.x, sqrtf(rb * inv_s2) * w2.y);
+            }
+            nu_out[e] = nu;
+        }
+    }
+    __syncthreads();
+}
+
+// element i of this CTA's CG vectors: its sample's value in the transform
+// buffer U of CTA (c_loc[i] >> 20), element c_loc[i] & 0xFFFFF (as floats)
+__device__ __forceinline__ float *cg_elem(cg::cluster_group &cl, float2 *U, const int *c_loc, int i) {
+    const int cli = c_loc[i];
+    return cl.map_shared_rank(reinterpret_cast<float *>(U) + (cli & 0xFFFFF), cli >> 20);
+}
+
+// z = M^{-1} r with M the block-diagonal Toeplitz preconditioner: each own
+// block applies T_L^{-1} = (L(x) L(x)^T - L(w) L(w)^T) / x_0 (Gohberg-
+// Semencul; x = T_L^{-1} e_1 from the Durbin tables, w = (0, x_{L-1}, ..,
+// x_1)) to its slice of r, gathered from and scattered to the CTAs that
+// hold those ranks.  gb points at five GB_CAP float arrays.
+__device__ __noinline__ void apply_gap_precond(const OwnBlocks &ob, float *c_r, float *c_z, float *gb,
+                                               const float *__restrict__ xt_det, int kper,
+                                               cg::cluster_group &cl)
+{
+    float *gb_r = gb, *gb_x = gb + GB_CAP, *gb_w = gb + 2 * GB_CAP;
+    float *gb_u1 = gb + 3 * GB_CAP, *gb_u2 = gb + 4 * GB_CAP;
+    cl.sync();     // every CTA's residual is complete before the gathers
+    for (int rd = 0; rd < ob.nrnd; ++rd) {
+        const int b0 = ob.rnd[rd], b1 = ob.rnd[rd + 1];
+        const int Ll = ob.len[b1 - 1];
+        const int tot = ob.off[b1 - 1] + ((Ll + 3) & ~3) + 16;
+        const int totq = ob.q[b1 - 1] + ((Ll + 3) >> 2);
+        // gather r and each block's generator x (w_s = x_{L-s}, w_0 = 0)
+        // into zero-padded regions; u1, u2 start at zero
+        for (int f = threadIdx.x; f < tot; f += DCT_T) {
+            int b = b0;
+            while (b + 1 < b1 && ob.off[b + 1] <= f) ++b;
+            const int L = ob.len[b], li = f - ob.off[b] - 8;
+            float rv = 0.f, xv = 0.f, wv = 0.f;
+            if (li >= 0 && li < L) {
+                const float *xt = xt_det + static_cast<int64_t>(L) * (L - 1) / 2;
+                rv = *rank_elem(cl, c_r, kper, ob.rank[b] + li);
+                xv = xt[li];
+                wv = li == 0 ? 0.f : xt[L - li];
+            }
+            gb_r[f] = rv; gb_x[f] = xv; gb_w[f] = wv; gb_u1[f] = 0.f; gb_u2[f] = 0.f;
+        }
+        __syncthreads();
+        // u1 = L(x)^T r, u2 = L(w)^T r: four outputs i0..i0+3 per
+        // thread, float4 loads, the r window slid in registers
+        for (int qi = threadIdx.x; qi < totq; qi += DCT_T) {
+            int b = b0;
+            while (b + 1 < b1 && ob.q[b + 1] <= qi) ++b;
+            const int L = ob.len[b], i0 = 4 * (qi - ob.q[b]), base = ob.off[b] + 8;
+            const float *xb = gb_x + base, *wb = gb_w + base, *rb = gb_r + base + i0;
+            float4 a1 = make_float4(0.f, 0.f, 0.f, 0.f), a2 = a1;
+            float4 rc = *reinterpret_cast<const float4 *>(rb);
+            for (int k = 0; k < L - i0; k += 4) {
+                const float4 xk = *reinterpret_cast<const float4 *>(xb + k);
+                const float4 wk = *reinterpret_cast<const float4 *>(wb + k);
+                const float4 rn = *reinterpret_cast<const float4 *>(rb + k + 4);
+                a1.x = fmaf(xk.x, rc.x, fmaf(xk.y, rc.y, fmaf(xk.z, rc.z, fmaf(xk.w, rc.w, a1.x))));
+                a1.y = fmaf(xk.x, rc.y, fmaf(xk.y, rc.z, fmaf(xk.z, rc.w, fmaf(xk.w, rn.x, a1.y))));
+                a1.z = fmaf(xk.x, rc.z, fmaf(xk.y, rc.w, fmaf(xk.z, rn.x, fmaf(xk.w, rn.y, a1.z))));
+                a1.w = fmaf(xk.x, rc.w, fmaf(xk.y, rn.x, fmaf(xk.z, rn.y, fmaf(xk.w, rn.z, a1.w))));
+                a2.x = fmaf(wk.x, rc.x, fmaf(wk.y, rc.y, fmaf(wk.z, rc.z, fmaf(wk.w, rc.w, a2.x))));
+                a2.y = fmaf(wk.x, rc.y, fmaf(wk.y, rc.z, fmaf(wk.z, rc.w, fmaf(wk.w, rn.x, a2.y))));
+                a2.z = fmaf(wk.x, rc.z, fmaf(wk.y, rc.w, fmaf(wk.z, rn.x, fmaf(wk.w, rn.y, a2.z))));
+                a2.w = fmaf(wk.x, rc.w, fmaf(wk.y, rn.x, fmaf(wk.z, rn.y, fmaf(wk.w, rn.z, a2.w))));
+                rc = rn;
+            }
+            *reinterpret_cast<float4 *>(gb_u1 + base + i0) = a1;
+            *reinterpret_cast<float4 *>(gb_u2 + base + i0) = a2;
+        }
+        __syncthreads();
+        // z = (L(x) u1 - L(w) u2) / x_0, scattered to the owners
+        for (int qi = threadIdx.x; qi < totq; qi += DCT_T) {
+            int b = b0;
+            while (b + 1 < b1 && ob.q[b + 1] <= qi) ++b;
+            const int L = ob.len[b], i0 = 4 * (qi - ob.q[b]), base = ob.off[b] + 8;
+            const float *xb = gb_x + base, *wb = gb_w + base;
+            const float *u1b = gb_u1 + base + i0, *u2b = gb_u2 + base + i0;
+            float4 z1 = make_float4(0.f, 0.f, 0.f, 0.f), z2 = z1;
+            float4 ua = *reinterpret_cast<const float4 *>(u1b);      // u[i0 - s .. i0 - s + 3]
+            float4 va = *reinterpret_cast<const float4 *>(u2b);
+            for (int s0 = 0; s0 <= i0; s0 += 4) {
+                const float4 xs = *reinterpret_cast<const float4 *>(xb + s0);
+                const float4 ws = *reinterpret_cast<const float4 *>(wb + s0);
+                const float4 ub = *reinterpret_cast<const float4 *>(u1b - s0 - 4);
+                const float4 vb = *reinterpret_cast<const float4 *>(u2b - s0 - 4);
+                z1.x = fmaf(xs.x, ua.x, fmaf(xs.y, ub.w, fmaf(xs.z, ub.z, fmaf(xs.w, ub.y, z1.x))));
+                z1.y = fmaf(xs.x, ua.y, fmaf(xs.y, ua.x, fmaf(xs.z, ub.w, fmaf(xs.w, ub.z, z1.y))));
+                z1.z = fmaf(xs.x, ua.z, fmaf(xs.y, ua.y, fmaf(xs.z, ua.x, fmaf(xs.w, ub.w, z1.z))));
+                z1.w = fmaf(xs.x, ua.w, fmaf(xs.y, ua.z, fmaf(xs.z, ua.y, fmaf(xs.w, ua.x, z1.w))));
+                z2.x = fmaf(ws.x, va.x, fmaf(ws.y, vb.w, fmaf(ws.z, vb.z, fmaf(ws.w, vb.y, z2.x))));
+                z2.y = fmaf(ws.x, va.y, fmaf(ws.y, va.x, fmaf(ws.z, vb.w, fmaf(ws.w, vb.z, z2.y))));
+                z2.z = fmaf(ws.x, va.z, fmaf(ws.y, va.y, fmaf(ws.z, va.x, fmaf(ws.w, vb.w, z2.z))));
+                z2.w = fmaf(ws.x, va.w, fmaf(ws.y, va.z, fmaf(ws.z, va.y, fmaf(ws.w, va.x, z2.w))));
+                ua = ub;
+                va = vb;
+            }
+            const float inv = 1.0f / xb[0];
+            const float zz[4] = {z1.x - z2.x, z1.y - z2.y, z1.z - z2.z, z1.w - z2.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (i0 + j < L) *rank_elem(cl, c_z, kper, ob.rank[b] + i0 + j) = zz[j] * inv;
+        }
+        __syncthreads();     // the gb arrays are reused by the next round
+    }
+    cl.sync();     // every scatter into every CTA's c_z is done
+}
+
 struct NcorrArgs {
     const float *d, *s;
     const double *gain;
@@ -977,8 +1143,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
     __shared__ int3 s_wscan[DCT_T / 32 + 1];
     __shared__ int s_nown, s_ovf;
     __shared__ int g_beg[GAP_CAP], g_end[GAP_CAP];
-    __shared__ int o_len[GAP_CAP], o_rank[GAP_CAP], o_off[GAP_CAP], o_q[GAP_CAP];
-    __shared__ int o_rnd[GAP_CAP + 1], s_nrnd;    // rounds of own blocks, <= GB_CAP elements each
+    __shared__ OwnBlocks ob;
     cg::cluster_group cl = cg::this_cluster();
     const int C = static_cast<int>(cl.num_blocks()), c = static_cast<int>(cl.block_rank());
     const int cid = blockIdx.x / C, ncl = gridDim.x / C;
@@ -990,18 +1155,14 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
     float *c_p = c_r + CG_KCAP;
     float *c_q = c_p + CG_KCAP;
     float *c_z = c_q + CG_KCAP;
-    float *gb_r = c_z + CG_KCAP;
-    float *gb_x = gb_r + GB_CAP;
-    float *gb_w = gb_x + GB_CAP;
-    float *gb_u1 = gb_w + GB_CAP;
-    float *gb_u2 = gb_u1 + GB_CAP;
+    float *gb_r = c_z + CG_KCAP;        // five GB_CAP arrays of the preconditioner
     int parity = 0;
     for (int w = cid; w < a.work_count; w += ncl) {
         const int q = a.work[a.work_begin + w];
         const int det = q % a.ndet;
         const int64_t o = a.off[q];
         load_plan(&sX, a.plans, a.q_plan[q], a.tw, sm, c, C);
-        if (threadIdx.x == 0) { s_nown = 0; s_nrnd = 0; }
+        if (threadIdx.x == 0) { s_nown = 0; ob.nrnd = 0; }
         const Ctx &X = sX;     // read from shared memory: registers are scarce here
         const int n = X.n, m = X.m;
         const DetScal sc = det_scalars(&s_sc, a.psd, det, n, a.fsamp, a.gain, q);
@@ -1015,86 +1176,12 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
         float *xq = a.x_out + o;
         float4 *wt = a.wscratch + (static_cast<int64_t>(cid) * C + c) * a.sz;
         float2 *cur = sm.U0, *oth = sm.U1;
-        // right-hand side, time-domain part: M (r/s2 + w1/s).  Element j takes
-        // normals 2j, 2j+1, i.e. pair j mod 4 of Philox block j/4: one thread
-        // per block of four consecutive elements of a row draws it once.
-        {
-            const int ncol = X.ncol, nbr = (ncol + 3) / 4 + 1;     // blocks touching a row
-            const int items = X.m1 * nbr;
-            for (int w = threadIdx.x; w < items; w += DCT_T) {
-                const int j1 = w / nbr, bi = w - j1 * nbr;
-                const int js = j1 * X.m2 + X.c * X.ncolmax;          // first element of the row
-                const int b = (js >> 2) + bi;
-                if (4 * b >= js + ncol) continue;
-                u64x4 rw;
-                if (draw) rw = philox4x64(static_cast<uint64_t>(b), q, 1, gi, rng.seed, rng.band);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int j = 4 * b + u;
-                    if (j < js || j >= js + ncol) continue;
-                    const int t0 = vpos_t(2 * j, n, m), t1 = vpos_t(2 * j + 1, n, m);
-                    const float2 w1 = draw ? philox_normal_pair(rw, u) : make_float2(0.f, 0.f);
-                    const float d0 = __ldg(dq + t0), d1 = __ldg(dq + t1);
-                    const float s0v = __ldg(sq + t0), s1v = __ldg(sq + t1);
-                    const float r0 = flagged(fl, o + t0) ? 0.f : fmaf(d0 - g * s0v, inv_s2, w1.x * inv_s);
-                    const float r1 = flagged(fl, o + t1) ? 0.f : fmaf(d1 - g * s1v, inv_s2, w1.y * inv_s);
-                    cur[j1 * X.ncolmax + (j - js)] = make_float2(r0, r1);
-                }
-            }
-            // padding columns of the last CTA stay zero
-            for (int e = threadIdx.x; e < X.m1 * X.ncolmax; e += DCT_T) {
-                const int j1 = fdiv(e, X.f_ncolmax);
-                if (e - j1 * X.ncolmax >= ncol) cur[e] = make_float2(0.f, 0.f);
-            }
-            __syncthreads();
-        }
+        // right-hand side, time-domain part: M (r/s2 + w1/s)
+        ncorr_rhs(sX, cur, dq, sq, fl, o, g, inv_s2, inv_s, draw, q, gi, rng.seed, rng.band);
         dct_forward_pre(sX, cur, oth, cl);
-        // prior term sqrt(phi) w2 in the packed layout, into the free buffer
-        // oth, and the filter weights of this detscan (beta, gamma for both
-        // modes of each packed slot) into wt, once.
-        // Mode k takes normals 2k, 2k+1 (pair k mod 4 of block k/4); for a
-        // fixed k2 the own even slots hold k = p0 + pl + m1 k2 and the odd
-        // ones k = m1 - p0 - pl + m1 k2 (pl < npl), so one thread draws a
-        // block for up to four consecutive modes of one parity.
-        {
-            const int npl = X.npl, m1 = X.m1, m2 = X.m2, p0 = X.p0;
-            const int nbk = (npl + 3) / 4 + 1;                  // blocks touching a k range
-            const int items = 2 * nbk * m2;
-            for (int w = threadIdx.x; w < items; w += DCT_T) {
-                const int rest = fdiv(w, X.f_m2), k2 = w - rest * m2;
-                const int par = rest / nbk, bi = rest - par * nbk;
-                const int kbase = (par == 0 ? p0 : m1 - p0 - (npl - 1)) + m1 * k2;
-                const int b = (kbase >> 2) + bi;
-                if (npl <= 0 || 4 * b >= kbase + npl) continue;
-                u64x4 rw;
-                if (draw) rw = philox4x64(static_cast<uint64_t>(b), q, 2, gi, rng.seed, rng.band);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int k = 4 * b + u;
-                    if (k < kbase || k >= kbase + npl) continue;
-                    const int pl = par == 0 ? k - kbase : (npl - 1) - (k - kbase);
-                    const int p = p0 + pl;
-                    const int e = (2 * pl + par) * X.m2p + k2;
-                    if (par == 1 && (p == 0 || m1 - p == p)) {            // slot holds no modes
-                        wt[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        oth[e] = make_float2(0.f, 0.f);
-                        continue;
-                    }
-                    const int ka = k, kb = (k == 0) ? m : n - k;
-                    const float ra = (ka == 0) ? 0.f : fratio_pow(ka, fscale, -alpha);   // s2 phi
-                    const float rb = fratio_pow(kb, fscale, -alpha);
-                    const float ba = s2 / (1.0f + ra), bb = s2 / (1.0f + rb);
-                    wt[e] = make_float4(ba, bb, ra * ba, rb * bb);
-                    float2 nu = make_float2(0.f, 0.f);
-                    if (draw) {
-                        const float2 w2 = philox_normal_pair(rw, u);
-                        nu = make_float2(sqrtf(ra * inv_s2) * w2.x, sqrtf(rb * inv_s2) * w2.y);
-                    }
-                    oth[e] = nu;
-                }
-            }
-            __syncthreads();
-        }
+        // prior term sqrt(phi) w2 in the packed layout into the free buffer
+        // oth, filter weights of this detscan into wt
+        ncorr_weights(sX, oth, wt, fscale, alpha, s2, inv_s2, draw, q, gi, rng.seed, rng.band);
         // (C b + prior term) times beta, between the two halves of the split
         split_roundtrip(X, cur, [&](int e, int, float2 Y) {
             const float4 w = wt[e];
@@ -1219,8 +1306,8 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                             // own blocks are applied in rounds of at most GB_CAP
                             // floats: 8 zeros, the block padded to a multiple of 4, 8 zeros
                             const int reg = ((len + 3) & ~3) + 16;
-                            if (s_nown == 0 || rlen + reg > GB_CAP) { o_rnd[s_nrnd++] = s_nown; rlen = 0; rq = 0; }
-                            o_len[s_nown] = len; o_rank[s_nown] = rank; o_off[s_nown] = rlen; o_q[s_nown] = rq;
+                            if (s_nown == 0 || rlen + reg > GB_CAP) { ob.rnd[ob.nrnd++] = s_nown; rlen = 0; rq = 0; }
+                            ob.len[s_nown] = len; ob.rank[s_nown] = rank; ob.off[s_nown] = rlen; ob.q[s_nown] = rq;
                             ++s_nown;
                             rlen += reg;
                             rq += (len + 3) >> 2;
@@ -1233,7 +1320,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                     if (++cb == C) cb = 0;
                 }
             }
-            o_rnd[s_nrnd] = s_nown;
+            ob.rnd[ob.nrnd] = s_nown;
             s_ovf = ovf;
         }
         if (!prec && threadIdx.x == 0) s_ovf = 1;
@@ -1243,18 +1330,6 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
         const bool use_prec = ovf_all < 0.5;
         int it = 0;
         bool conv = true;
-        // element i of the CG vectors of this CTA: its sample's value in the
-        // transform buffer U of CTA (c_loc >> 20)
-        auto at = [&](float2 *U, int i) -> float * {
-            const int cl_i = c_loc[i];
-            float *uf = reinterpret_cast<float *>(U) + (cl_i & 0xFFFFF);
-            return cl.map_shared_rank(uf, cl_i >> 20);
-        };
-        // CG vector rank k: (CTA, index)
-        auto rank_ref = [&](float *vec, int k) -> float * {
-            const int ow = k / kper;
-            return cl.map_shared_rank(vec + (k - ow * kper), ow);
-        };
         if (kc_all > 0 && cap_ovf) {
             conv = false;      // too many flagged samples for the CG buffers: left as x0
             set_status(a.status, q, TOD_ERR_NOT_CONVERGED);
@@ -1268,96 +1343,13 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                     __syncthreads();
                     return;
                 }
-                cl.sync();     // every CTA's residual is complete before the gathers
-                for (int rd = 0; rd < s_nrnd; ++rd) {
-                    const int b0 = o_rnd[rd], b1 = o_rnd[rd + 1];
-                    const int Ll = o_len[b1 - 1];
-                    const int tot = o_off[b1 - 1] + ((Ll + 3) & ~3) + 16;
-                    const int totq = o_q[b1 - 1] + ((Ll + 3) >> 2);
-                    // gather r and each block's generator x (w_s = x_{L-s}, w_0 = 0)
-                    // into zero-padded regions; u1, u2 start at zero
-                    for (int f = threadIdx.x; f < tot; f += DCT_T) {
-                        int b = b0;
-                        while (b + 1 < b1 && o_off[b + 1] <= f) ++b;
-                        const int L = o_len[b], li = f - o_off[b] - 8;
-                        float rv = 0.f, xv = 0.f, wv = 0.f;
-                        if (li >= 0 && li < L) {
-                            const float *xt = xt_det + static_cast<int64_t>(L) * (L - 1) / 2;
-                            rv = *rank_ref(c_r, o_rank[b] + li);
-                            xv = xt[li];
-                            wv = li == 0 ? 0.f : xt[L - li];
-                        }
-                        gb_r[f] = rv; gb_x[f] = xv; gb_w[f] = wv; gb_u1[f] = 0.f; gb_u2[f] = 0.f;
-                    }
-                    __syncthreads();
-                    // u1 = L(x)^T r, u2 = L(w)^T r: four outputs i0..i0+3 per
-                    // thread, float4 loads, the r window slid in registers
-                    for (int qi = threadIdx.x; qi < totq; qi += DCT_T) {
-                        int b = b0;
-                        while (b + 1 < b1 && o_q[b + 1] <= qi) ++b;
-                        const int L = o_len[b], i0 = 4 * (qi - o_q[b]), base = o_off[b] + 8;
-                        const float *xb = gb_x + base, *wb = gb_w + base, *rb = gb_r + base + i0;
-                        float4 a1 = make_float4(0.f, 0.f, 0.f, 0.f), a2 = a1;
-                        float4 rc = *reinterpret_cast<const float4 *>(rb);
-                        for (int k = 0; k < L - i0; k += 4) {
-                            const float4 xk = *reinterpret_cast<const float4 *>(xb + k);
-                            const float4 wk = *reinterpret_cast<const float4 *>(wb + k);
-                            const float4 rn = *reinterpret_cast<const float4 *>(rb + k + 4);
-                            a1.x = fmaf(xk.x, rc.x, fmaf(xk.y, rc.y, fmaf(xk.z, rc.z, fmaf(xk.w, rc.w, a1.x))));
-                            a1.y = fmaf(xk.x, rc.y, fmaf(xk.y, rc.z, fmaf(xk.z, rc.w, fmaf(xk.w, rn.x, a1.y))));
-                            a1.z = fmaf(xk.x, rc.z, fmaf(xk.y, rc.w, fmaf(xk.z, rn.x, fmaf(xk.w, rn.y, a1.z))));
-                            a1.w = fmaf(xk.x, rc.w, fmaf(xk.y, rn.x, fmaf(xk.z, rn.y, fmaf(xk.w, rn.z, a1.w))));
-                            a2.x = fmaf(wk.x, rc.x, fmaf(wk.y, rc.y, fmaf(wk.z, rc.z, fmaf(wk.w, rc.w, a2.x))));
-                            a2.y = fmaf(wk.x, rc.y, fmaf(wk.y, rc.z, fmaf(wk.z, rc.w, fmaf(wk.w, rn.x, a2.y))));
-                            a2.z = fmaf(wk.x, rc.z, fmaf(wk.y, rc.w, fmaf(wk.z, rn.x, fmaf(wk.w, rn.y, a2.z))));
-                            a2.w = fmaf(wk.x, rc.w, fmaf(wk.y, rn.x, fmaf(wk.z, rn.y, fmaf(wk.w, rn.z, a2.w))));
-                            rc = rn;
-                        }
-                        *reinterpret_cast<float4 *>(gb_u1 + base + i0) = a1;
-                        *reinterpret_cast<float4 *>(gb_u2 + base + i0) = a2;
-                    }
-                    __syncthreads();
-                    // z = (L(x) u1 - L(w) u2) / x_0, scattered to the owners
-                    for (int qi = threadIdx.x; qi < totq; qi += DCT_T) {
-                        int b = b0;
-                        while (b + 1 < b1 && o_q[b + 1] <= qi) ++b;
-                        const int L = o_len[b], i0 = 4 * (qi - o_q[b]), base = o_off[b] + 8;
-                        const float *xb = gb_x + base, *wb = gb_w + base;
-                        const float *u1b = gb_u1 + base + i0, *u2b = gb_u2 + base + i0;
-                        float4 z1 = make_float4(0.f, 0.f, 0.f, 0.f), z2 = z1;
-                        float4 ua = *reinterpret_cast<const float4 *>(u1b);      // u[i0 - s .. i0 - s + 3]
-                        float4 va = *reinterpret_cast<const float4 *>(u2b);
-                        for (int s0 = 0; s0 <= i0; s0 += 4) {
-                            const float4 xs = *reinterpret_cast<const float4 *>(xb + s0);
-                            const float4 ws = *reinterpret_cast<const float4 *>(wb + s0);
-                            const float4 ub = *reinterpret_cast<const float4 *>(u1b - s0 - 4);
-                            const float4 vb = *reinterpret_cast<const float4 *>(u2b - s0 - 4);
-                            z1.x = fmaf(xs.x, ua.x, fmaf(xs.y, ub.w, fmaf(xs.z, ub.z, fmaf(xs.w, ub.y, z1.x))));
-                            z1.y = fmaf(xs.x, ua.y, fmaf(xs.y, ua.x, fmaf(xs.z, ub.w, fmaf(xs.w, ub.z, z1.y))));
-                            z1.z = fmaf(xs.x, ua.z, fmaf(xs.y, ua.y, fmaf(xs.z, ua.x, fmaf(xs.w, ub.w, z1.z))));
-                            z1.w = fmaf(xs.x, ua.w, fmaf(xs.y, ua.z, fmaf(xs.z, ua.y, fmaf(xs.w, ua.x, z1.w))));
-                            z2.x = fmaf(ws.x, va.x, fmaf(ws.y, vb.w, fmaf(ws.z, vb.z, fmaf(ws.w, vb.y, z2.x))));
-                            z2.y = fmaf(ws.x, va.y, fmaf(ws.y, va.x, fmaf(ws.z, vb.w, fmaf(ws.w, vb.z, z2.y))));
-                            z2.z = fmaf(ws.x, va.z, fmaf(ws.y, va.y, fmaf(ws.z, va.x, fmaf(ws.w, vb.w, z2.z))));
-                            z2.w = fmaf(ws.x, va.w, fmaf(ws.y, va.z, fmaf(ws.z, va.y, fmaf(ws.w, va.x, z2.w))));
-                            ua = ub;
-                            va = vb;
-                        }
-                        const float inv = 1.0f / xb[0];
-                        const float zz[4] = {z1.x - z2.x, z1.y - z2.y, z1.z - z2.z, z1.w - z2.w};
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            if (i0 + j < L) *rank_ref(c_z, o_rank[b] + i0 + j) = zz[j] * inv;
-                    }
-                    __syncthreads();     // the gb arrays are reused by the next round
-                }
-                cl.sync();     // every scatter into every CTA's c_z is done
+                apply_gap_precond(ob, c_r, c_z, gb_r, xt_det, kper, cl);
             };
             // rhs = E^T x0 ; y = 0 ; r = rhs ; z = M^{-1} r ; p = z
             cl.sync();         // x0 is complete in every CTA before the gathers
             Acc2 rr_loc = {0.f, 0.f};
             for (int i = threadIdx.x; i < kc; i += DCT_T) {
-                const float v = *at(cur, i);
+                const float v = *cg_elem(cl, cur, c_loc, i);
                 c_y[i] = 0.f; c_r[i] = v;
                 acc_add_prod(rr_loc, v, v);
             }
@@ -1377,7 +1369,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                 // cur <- C^T diag(gamma) C E p
                 for (int e = threadIdx.x; e < tot; e += DCT_T) cur[e] = make_float2(0.f, 0.f);
                 cl.sync();     // every buffer is zero before the scatters
-                for (int i = threadIdx.x; i < kc; i += DCT_T) *at(cur, i) = c_p[i];
+                for (int i = threadIdx.x; i < kc; i += DCT_T) *cg_elem(cl, cur, c_loc, i) = c_p[i];
                 cl.sync();     // every scatter has landed
                 dct_forward_pre(sX, cur, oth, cl);
                 split_roundtrip(X, cur, [&](int e, int, float2 Y) {
@@ -1388,7 +1380,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                 cl.sync();     // every CTA's result is complete before the gathers
                 Acc2 pq_loc = {0.f, 0.f};
                 for (int i = threadIdx.x; i < kc; i += DCT_T) {
-                    const float v = *at(cur, i);
+                    const float v = *cg_elem(cl, cur, c_loc, i);
                     c_q[i] = v;
                     acc_add_prod(pq_loc, c_p[i], v);
                 }
@@ -1418,7 +1410,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             // x = x0 + B^{-1} E y
             for (int e = threadIdx.x; e < tot; e += DCT_T) cur[e] = make_float2(0.f, 0.f);
             cl.sync();
-            for (int i = threadIdx.x; i < kc; i += DCT_T) *at(cur, i) = c_y[i];
+            for (int i = threadIdx.x; i < kc; i += DCT_T) *cg_elem(cl, cur, c_loc, i) = c_y[i];
             cl.sync();
             dct_forward_pre(sX, cur, oth, cl);
             split_roundtrip(X, cur, [&](int e, int, float2 Y) {

@@ -1,7 +1,8 @@
 """Parity at the full 30 GHz-like workload (4 detectors x 1000 scans of
 U[90k, 140k] samples at 32.5 Hz, Nside 512: 4.6e8 samples), in the launch
 configuration the benchmark times (default cluster size, persistent
-schedule, one Gibbs step through GibbsTODStep).
+schedule, one Gibbs step through GibbsTODStep), and on two scans of the
+70 GHz-like band (12 detectors, U[150k, 300k] samples at 78.8 Hz, Nside 1024).
 
 The oracle cannot redo the whole band in a test, so:
   * decode, gain and n_corr are checked on sampled detscans (the longest,
@@ -23,12 +24,20 @@ SEED, BAND, IT = 5, 0, 7
 CG_TOL = 1e-6          # the benchmark's setting
 
 
-@pytest.fixture(scope="module")
-def full():
+def _configs():
+    # the full 30 GHz band (the benchmark's workload) and two scans of the
+    # 70 GHz band (24 detscans of U[150k, 300k] samples, Nside 1024: the
+    # longest transforms, so the largest clusters)
+    return {"lfi30_full": synth.CONFIGS["lfi30"],
+            "lfi70_2scans": synth.scaled(synth.CONFIGS["lfi70"], nscan=2)}
+
+
+@pytest.fixture(scope="module", params=["lfi30_full", "lfi70_2scans"])
+def full(request):
     import torch
     import paper_2201_03509_gb300 as tg
     from paper_2201_03509_gb300.step import GibbsTODStep
-    cfg = synth.CONFIGS["lfi30"]
+    cfg = _configs()[request.param]
     band = synth.make_band(cfg)
     ing = tg.ingest(band)
     off = ing["offsets"]
@@ -44,7 +53,7 @@ def full():
     nq = len(off) - 1
     lens = np.diff(off)
     flagfrac = np.array([ing["flags"][off[q]:off[q + 1]].mean() for q in range(nq)])
-    qs = sorted({int(np.argmax(lens)), int(np.argmin(lens)), int(np.argmax(flagfrac)), 0, 1234, nq - 1})
+    qs = sorted({int(np.argmax(lens)), int(np.argmin(lens)), int(np.argmax(flagfrac)), 0, min(1234, nq - 2), nq - 1})
     return dict(cfg=cfg, band=band, ing=ing, off=off, plan=plan, step=step, map32=m4[:, :3].T.astype(np.float64),
                 qs=qs, torch=torch, tg=tg)
 
@@ -112,7 +121,7 @@ def test_full_hits_bin_and_solve_sampled(full):
     plan.bin(F["step"].psi, F["step"].d, t_x, t_g, F["step"].flags, F["step"].psd, A, b, hits)
     plan.status()
     hit_pix = np.nonzero(rh >= 3)[0]
-    sp = np.sort(np.random.default_rng(4).choice(hit_pix, 2000, replace=False))
+    sp = np.sort(np.random.default_rng(4).choice(hit_pix, min(2000, hit_pix.size), replace=False))
     sel = np.nonzero(np.isin(pix, sp))[0]
     psi = np.concatenate([band.psi[q][:off[q + 1] - off[q]] for q in range(nq)])[sel].astype(np.int64)
     qsel = np.searchsorted(off, sel, side="right") - 1
@@ -143,5 +152,8 @@ def test_full_hits_bin_and_solve_sampled(full):
     assert np.array_equal(gv[sp], rvalid)
     assert gv.sum() == rvalid.sum()          # nothing outside the sample is valid
     ok = rvalid > 0
-    for i in range(3):
-        assert np.abs(gm[i, ok] - rm[i, ok]).max() <= 1e-10 * np.abs(rm[i, ok]).max()
+    if F["cfg"].nscan >= 100:
+        assert ok.sum() > 100      # the full band solves most pixels
+    if ok.any():                   # a two-scan slice sees each pixel at one angle: none solvable
+        for i in range(3):
+            assert np.abs(gm[i, ok] - rm[i, ok]).max() <= 1e-10 * np.abs(rm[i, ok]).max()
