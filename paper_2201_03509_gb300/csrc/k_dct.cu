@@ -924,13 +924,25 @@ __device__ __noinline__ void ncorr_rhs(const Ctx &XS, float2 *__restrict__ U, co
     const int n = X.n, m = X.m;
     const int ncol = X.ncol, nbr = (ncol + 3) / 4 + 1;     // blocks touching a row
     const int items = X.m1 * nbr;
-    for (int w = threadIdx.x; w < items; w += DCT_T) {
-        const int j1 = w / nbr, bi = w - j1 * nbr;
-        const int js = j1 * X.m2 + X.c * X.ncolmax;          // first element of the row
-        const int b = (js >> 2) + bi;
-        if (4 * b >= js + ncol) continue;
-        u64x4 rw;
-        if (draw) rw = philox4x64(static_cast<uint64_t>(b), q, 1, gi, seed, band);
+    // two items per thread and step: their Philox chains are independent
+    for (int w0 = threadIdx.x; w0 < items; w0 += 2 * DCT_T) {
+        int js2[2], b2[2];
+        u64x4 rw2[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int w = w0 + h * DCT_T;
+            const int j1 = w / nbr, bi = w - j1 * nbr;
+            js2[h] = j1 * X.m2 + X.c * X.ncolmax;               // first element of the row
+            b2[h] = (w < items) ? (js2[h] >> 2) + bi : -1;
+            if (draw && b2[h] >= 0) rw2[h] = philox4x64(static_cast<uint64_t>(b2[h]), q, 1, gi, seed, band);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+        const int w = w0 + h * DCT_T;
+        const int j1 = w / nbr;
+        const int js = js2[h], b = b2[h];
+        if (b < 0 || 4 * b >= js + ncol) continue;
+        const u64x4 &rw = rw2[h];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int j = 4 * b + u;
@@ -942,6 +954,7 @@ __device__ __noinline__ void ncorr_rhs(const Ctx &XS, float2 *__restrict__ U, co
             const float r0 = flagged(fl, o + t0) ? 0.f : fmaf(d0 - g * s0v, inv_s2, w1.x * inv_s);
             const float r1 = flagged(fl, o + t1) ? 0.f : fmaf(d1 - g * s1v, inv_s2, w1.y * inv_s);
             U[j1 * X.ncolmax + (j - js)] = make_float2(r0, r1);
+        }
         }
     }
     // padding columns of the last CTA stay zero
@@ -967,14 +980,26 @@ __device__ __noinline__ void ncorr_weights(const Ctx &XS, float2 *__restrict__ n
     const int npl = X.npl, m1 = X.m1, m2 = X.m2, p0 = X.p0;
     const int nbk = (npl + 3) / 4 + 1;                  // blocks touching a k range
     const int items = 2 * nbk * m2;
-    for (int w = threadIdx.x; w < items; w += DCT_T) {
-        const int rest = fdiv(w, X.f_m2), k2 = w - rest * m2;
-        const int par = rest / nbk, bi = rest - par * nbk;
-        const int kbase = (par == 0 ? p0 : m1 - p0 - (npl - 1)) + m1 * k2;
-        const int b = (kbase >> 2) + bi;
-        if (npl <= 0 || 4 * b >= kbase + npl) continue;
-        u64x4 rw;
-        if (draw) rw = philox4x64(static_cast<uint64_t>(b), q, 2, gi, seed, band);
+    // two items per thread and step: their Philox chains are independent
+    for (int w0 = threadIdx.x; w0 < items; w0 += 2 * DCT_T) {
+        int kb2[2], b2[2], k22[2], par2[2];
+        u64x4 rw2[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int w = w0 + h * DCT_T;
+            const int rest = fdiv(w, X.f_m2), k2 = w - rest * m2;
+            const int par = rest / nbk, bi = rest - par * nbk;
+            kb2[h] = (par == 0 ? p0 : m1 - p0 - (npl - 1)) + m1 * k2;
+            b2[h] = (w < items && npl > 0) ? (kb2[h] >> 2) + bi : -1;
+            k22[h] = k2;
+            par2[h] = par;
+            if (draw && b2[h] >= 0) rw2[h] = philox4x64(static_cast<uint64_t>(b2[h]), q, 2, gi, seed, band);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+        const int kbase = kb2[h], b = b2[h], k2 = k22[h], par = par2[h];
+        if (b < 0 || 4 * b >= kbase + npl) continue;
+        const u64x4 &rw = rw2[h];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int k = 4 * b + u;
@@ -998,6 +1023,7 @@ __device__ __noinline__ void ncorr_weights(const Ctx &XS, float2 *__restrict__ n
                 nu = make_float2(sqrtf(ra * inv_s2) * w2.x, sqrtf(rb * inv_s2) * w2.y);
             }
             nu_out[e] = nu;
+        }
         }
     }
     __syncthreads();
@@ -1043,64 +1069,97 @@ __device__ __noinline__ void apply_gap_precond(const OwnBlocks &ob, float *c_r, 
             gb_r[f] = rv; gb_x[f] = xv; gb_w[f] = wv; gb_u1[f] = 0.f; gb_u2[f] = 0.f;
         }
         __syncthreads();
-        // u1 = L(x)^T r, u2 = L(w)^T r: four outputs i0..i0+3 per
-        // thread, float4 loads, the r window slid in registers
-        for (int qi = threadIdx.x; qi < totq; qi += DCT_T) {
-            int b = b0;
-            while (b + 1 < b1 && ob.q[b + 1] <= qi) ++b;
-            const int L = ob.len[b], i0 = 4 * (qi - ob.q[b]), base = ob.off[b] + 8;
-            const float *xb = gb_x + base, *wb = gb_w + base, *rb = gb_r + base + i0;
+        // u1 = L(x)^T r, u2 = L(w)^T r: four outputs i0..i0+3 per group of
+        // QT consecutive threads (QT = 4, 2 or 1 as the round's size allows),
+        // float4 loads; the group splits the sum and adds its partials in a
+        // fixed order
+        const int QT = (totq * 4 <= DCT_T) ? 4 : (totq * 2 <= DCT_T) ? 2 : 1;
+        const int qsh = QT == 4 ? 2 : QT == 2 ? 1 : 0;
+        const int totw = totq << qsh;
+        for (int t0 = 0; t0 < totw; t0 += DCT_T) {
+            const int t = t0 + threadIdx.x;
+            const bool act = t < totw;
+            const int qi = t >> qsh, part = t & (QT - 1);
             float4 a1 = make_float4(0.f, 0.f, 0.f, 0.f), a2 = a1;
-            float4 rc = *reinterpret_cast<const float4 *>(rb);
-            for (int k = 0; k < L - i0; k += 4) {
-                const float4 xk = *reinterpret_cast<const float4 *>(xb + k);
-                const float4 wk = *reinterpret_cast<const float4 *>(wb + k);
-                const float4 rn = *reinterpret_cast<const float4 *>(rb + k + 4);
-                a1.x = fmaf(xk.x, rc.x, fmaf(xk.y, rc.y, fmaf(xk.z, rc.z, fmaf(xk.w, rc.w, a1.x))));
-                a1.y = fmaf(xk.x, rc.y, fmaf(xk.y, rc.z, fmaf(xk.z, rc.w, fmaf(xk.w, rn.x, a1.y))));
-                a1.z = fmaf(xk.x, rc.z, fmaf(xk.y, rc.w, fmaf(xk.z, rn.x, fmaf(xk.w, rn.y, a1.z))));
-                a1.w = fmaf(xk.x, rc.w, fmaf(xk.y, rn.x, fmaf(xk.z, rn.y, fmaf(xk.w, rn.z, a1.w))));
-                a2.x = fmaf(wk.x, rc.x, fmaf(wk.y, rc.y, fmaf(wk.z, rc.z, fmaf(wk.w, rc.w, a2.x))));
-                a2.y = fmaf(wk.x, rc.y, fmaf(wk.y, rc.z, fmaf(wk.z, rc.w, fmaf(wk.w, rn.x, a2.y))));
-                a2.z = fmaf(wk.x, rc.z, fmaf(wk.y, rc.w, fmaf(wk.z, rn.x, fmaf(wk.w, rn.y, a2.z))));
-                a2.w = fmaf(wk.x, rc.w, fmaf(wk.y, rn.x, fmaf(wk.z, rn.y, fmaf(wk.w, rn.z, a2.w))));
-                rc = rn;
+            int base = 0, i0 = 0;
+            if (act) {
+                int b = b0;
+                while (b + 1 < b1 && ob.q[b + 1] <= qi) ++b;
+                const int L = ob.len[b];
+                i0 = 4 * (qi - ob.q[b]);
+                base = ob.off[b] + 8;
+                const float *xb = gb_x + base, *wb = gb_w + base, *rb = gb_r + base + i0;
+                for (int k = 4 * part; k < L - i0; k += 4 * QT) {
+                    const float4 xk = *reinterpret_cast<const float4 *>(xb + k);
+                    const float4 wk = *reinterpret_cast<const float4 *>(wb + k);
+                    const float4 rc = *reinterpret_cast<const float4 *>(rb + k);
+                    const float4 rn = *reinterpret_cast<const float4 *>(rb + k + 4);
+                    a1.x = fmaf(xk.x, rc.x, fmaf(xk.y, rc.y, fmaf(xk.z, rc.z, fmaf(xk.w, rc.w, a1.x))));
+                    a1.y = fmaf(xk.x, rc.y, fmaf(xk.y, rc.z, fmaf(xk.z, rc.w, fmaf(xk.w, rn.x, a1.y))));
+                    a1.z = fmaf(xk.x, rc.z, fmaf(xk.y, rc.w, fmaf(xk.z, rn.x, fmaf(xk.w, rn.y, a1.z))));
+                    a1.w = fmaf(xk.x, rc.w, fmaf(xk.y, rn.x, fmaf(xk.z, rn.y, fmaf(xk.w, rn.z, a1.w))));
+                    a2.x = fmaf(wk.x, rc.x, fmaf(wk.y, rc.y, fmaf(wk.z, rc.z, fmaf(wk.w, rc.w, a2.x))));
+                    a2.y = fmaf(wk.x, rc.y, fmaf(wk.y, rc.z, fmaf(wk.z, rc.w, fmaf(wk.w, rn.x, a2.y))));
+                    a2.z = fmaf(wk.x, rc.z, fmaf(wk.y, rc.w, fmaf(wk.z, rn.x, fmaf(wk.w, rn.y, a2.z))));
+                    a2.w = fmaf(wk.x, rc.w, fmaf(wk.y, rn.x, fmaf(wk.z, rn.y, fmaf(wk.w, rn.z, a2.w))));
+                }
             }
-            *reinterpret_cast<float4 *>(gb_u1 + base + i0) = a1;
-            *reinterpret_cast<float4 *>(gb_u2 + base + i0) = a2;
+            for (int ofs = 1; ofs < QT; ofs <<= 1) {       // every lane of the warp takes part
+                a1.x += __shfl_xor_sync(0xffffffffu, a1.x, ofs); a1.y += __shfl_xor_sync(0xffffffffu, a1.y, ofs);
+                a1.z += __shfl_xor_sync(0xffffffffu, a1.z, ofs); a1.w += __shfl_xor_sync(0xffffffffu, a1.w, ofs);
+                a2.x += __shfl_xor_sync(0xffffffffu, a2.x, ofs); a2.y += __shfl_xor_sync(0xffffffffu, a2.y, ofs);
+                a2.z += __shfl_xor_sync(0xffffffffu, a2.z, ofs); a2.w += __shfl_xor_sync(0xffffffffu, a2.w, ofs);
+            }
+            if (act && part == 0) {
+                *reinterpret_cast<float4 *>(gb_u1 + base + i0) = a1;
+                *reinterpret_cast<float4 *>(gb_u2 + base + i0) = a2;
+            }
         }
         __syncthreads();
-        // z = (L(x) u1 - L(w) u2) / x_0, scattered to the owners
-        for (int qi = threadIdx.x; qi < totq; qi += DCT_T) {
-            int b = b0;
-            while (b + 1 < b1 && ob.q[b + 1] <= qi) ++b;
-            const int L = ob.len[b], i0 = 4 * (qi - ob.q[b]), base = ob.off[b] + 8;
-            const float *xb = gb_x + base, *wb = gb_w + base;
-            const float *u1b = gb_u1 + base + i0, *u2b = gb_u2 + base + i0;
+        // z = (L(x) u1 - L(w) u2) / x_0, scattered to the owners; same split
+        for (int t0 = 0; t0 < totw; t0 += DCT_T) {
+            const int t = t0 + threadIdx.x;
+            const bool act = t < totw;
+            const int qi = t >> qsh, part = t & (QT - 1);
             float4 z1 = make_float4(0.f, 0.f, 0.f, 0.f), z2 = z1;
-            float4 ua = *reinterpret_cast<const float4 *>(u1b);      // u[i0 - s .. i0 - s + 3]
-            float4 va = *reinterpret_cast<const float4 *>(u2b);
-            for (int s0 = 0; s0 <= i0; s0 += 4) {
-                const float4 xs = *reinterpret_cast<const float4 *>(xb + s0);
-                const float4 ws = *reinterpret_cast<const float4 *>(wb + s0);
-                const float4 ub = *reinterpret_cast<const float4 *>(u1b - s0 - 4);
-                const float4 vb = *reinterpret_cast<const float4 *>(u2b - s0 - 4);
-                z1.x = fmaf(xs.x, ua.x, fmaf(xs.y, ub.w, fmaf(xs.z, ub.z, fmaf(xs.w, ub.y, z1.x))));
-                z1.y = fmaf(xs.x, ua.y, fmaf(xs.y, ua.x, fmaf(xs.z, ub.w, fmaf(xs.w, ub.z, z1.y))));
-                z1.z = fmaf(xs.x, ua.z, fmaf(xs.y, ua.y, fmaf(xs.z, ua.x, fmaf(xs.w, ub.w, z1.z))));
-                z1.w = fmaf(xs.x, ua.w, fmaf(xs.y, ua.z, fmaf(xs.z, ua.y, fmaf(xs.w, ua.x, z1.w))));
-                z2.x = fmaf(ws.x, va.x, fmaf(ws.y, vb.w, fmaf(ws.z, vb.z, fmaf(ws.w, vb.y, z2.x))));
-                z2.y = fmaf(ws.x, va.y, fmaf(ws.y, va.x, fmaf(ws.z, vb.w, fmaf(ws.w, vb.z, z2.y))));
-                z2.z = fmaf(ws.x, va.z, fmaf(ws.y, va.y, fmaf(ws.z, va.x, fmaf(ws.w, vb.w, z2.z))));
-                z2.w = fmaf(ws.x, va.w, fmaf(ws.y, va.z, fmaf(ws.z, va.y, fmaf(ws.w, va.x, z2.w))));
-                ua = ub;
-                va = vb;
+            int b = b0, i0 = 0, L = 0, base = 0;
+            if (act) {
+                while (b + 1 < b1 && ob.q[b + 1] <= qi) ++b;
+                L = ob.len[b];
+                i0 = 4 * (qi - ob.q[b]);
+                base = ob.off[b] + 8;
+                const float *xb = gb_x + base, *wb = gb_w + base;
+                const float *u1b = gb_u1 + base + i0, *u2b = gb_u2 + base + i0;
+                for (int s0 = 4 * part; s0 <= i0; s0 += 4 * QT) {
+                    const float4 xs = *reinterpret_cast<const float4 *>(xb + s0);
+                    const float4 ws = *reinterpret_cast<const float4 *>(wb + s0);
+                    const float4 ua = *reinterpret_cast<const float4 *>(u1b - s0);      // u[i0 - s0 ..]
+                    const float4 va = *reinterpret_cast<const float4 *>(u2b - s0);
+                    const float4 ub = *reinterpret_cast<const float4 *>(u1b - s0 - 4);
+                    const float4 vb = *reinterpret_cast<const float4 *>(u2b - s0 - 4);
+                    z1.x = fmaf(xs.x, ua.x, fmaf(xs.y, ub.w, fmaf(xs.z, ub.z, fmaf(xs.w, ub.y, z1.x))));
+                    z1.y = fmaf(xs.x, ua.y, fmaf(xs.y, ua.x, fmaf(xs.z, ub.w, fmaf(xs.w, ub.z, z1.y))));
+                    z1.z = fmaf(xs.x, ua.z, fmaf(xs.y, ua.y, fmaf(xs.z, ua.x, fmaf(xs.w, ub.w, z1.z))));
+                    z1.w = fmaf(xs.x, ua.w, fmaf(xs.y, ua.z, fmaf(xs.z, ua.y, fmaf(xs.w, ua.x, z1.w))));
+                    z2.x = fmaf(ws.x, va.x, fmaf(ws.y, vb.w, fmaf(ws.z, vb.z, fmaf(ws.w, vb.y, z2.x))));
+                    z2.y = fmaf(ws.x, va.y, fmaf(ws.y, va.x, fmaf(ws.z, vb.w, fmaf(ws.w, vb.z, z2.y))));
+                    z2.z = fmaf(ws.x, va.z, fmaf(ws.y, va.y, fmaf(ws.z, va.x, fmaf(ws.w, vb.w, z2.z))));
+                    z2.w = fmaf(ws.x, va.w, fmaf(ws.y, va.z, fmaf(ws.z, va.y, fmaf(ws.w, va.x, z2.w))));
+                }
             }
-            const float inv = 1.0f / xb[0];
-            const float zz[4] = {z1.x - z2.x, z1.y - z2.y, z1.z - z2.z, z1.w - z2.w};
+            for (int ofs = 1; ofs < QT; ofs <<= 1) {
+                z1.x += __shfl_xor_sync(0xffffffffu, z1.x, ofs); z1.y += __shfl_xor_sync(0xffffffffu, z1.y, ofs);
+                z1.z += __shfl_xor_sync(0xffffffffu, z1.z, ofs); z1.w += __shfl_xor_sync(0xffffffffu, z1.w, ofs);
+                z2.x += __shfl_xor_sync(0xffffffffu, z2.x, ofs); z2.y += __shfl_xor_sync(0xffffffffu, z2.y, ofs);
+                z2.z += __shfl_xor_sync(0xffffffffu, z2.z, ofs); z2.w += __shfl_xor_sync(0xffffffffu, z2.w, ofs);
+            }
+            if (act && part == 0) {
+                const float inv = 1.0f / gb_x[base];
+                const float zz[4] = {z1.x - z2.x, z1.y - z2.y, z1.z - z2.z, z1.w - z2.w};
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (i0 + j < L) *rank_elem(cl, c_z, kper, ob.rank[b] + i0 + j) = zz[j] * inv;
+                for (int j = 0; j < 4; ++j)
+                    if (i0 + j < L) *rank_elem(cl, c_z, kper, ob.rank[b] + i0 + j) = zz[j] * inv;
+            }
         }
         __syncthreads();     // the gb arrays are reused by the next round
     }
