@@ -924,25 +924,13 @@ __device__ __noinline__ void ncorr_rhs(const Ctx &XS, float2 *__restrict__ U, co
     const int n = X.n, m = X.m;
     const int ncol = X.ncol, nbr = (ncol + 3) / 4 + 1;     // blocks touching a row
     const int items = X.m1 * nbr;
-    // two items per thread and step: their Philox chains are independent
-    for (int w0 = threadIdx.x; w0 < items; w0 += 2 * DCT_T) {
-        int js2[2], b2[2];
-        u64x4 rw2[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int w = w0 + h * DCT_T;
-            const int j1 = w / nbr, bi = w - j1 * nbr;
-            js2[h] = j1 * X.m2 + X.c * X.ncolmax;               // first element of the row
-            b2[h] = (w < items) ? (js2[h] >> 2) + bi : -1;
-            if (draw && b2[h] >= 0) rw2[h] = philox4x64(static_cast<uint64_t>(b2[h]), q, 1, gi, seed, band);
-        }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-        const int w = w0 + h * DCT_T;
-        const int j1 = w / nbr;
-        const int js = js2[h], b = b2[h];
-        if (b < 0 || 4 * b >= js + ncol) continue;
-        const u64x4 &rw = rw2[h];
+    for (int w = threadIdx.x; w < items; w += DCT_T) {
+        const int j1 = w / nbr, bi = w - j1 * nbr;
+        const int js = j1 * X.m2 + X.c * X.ncolmax;          // first element of the row
+        const int b = (js >> 2) + bi;
+        if (4 * b >= js + ncol) continue;
+        u64x4 rw;
+        if (draw) rw = philox4x64(static_cast<uint64_t>(b), q, 1, gi, seed, band);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int j = 4 * b + u;
@@ -954,7 +942,6 @@ __device__ __noinline__ void ncorr_rhs(const Ctx &XS, float2 *__restrict__ U, co
             const float r0 = flagged(fl, o + t0) ? 0.f : fmaf(d0 - g * s0v, inv_s2, w1.x * inv_s);
             const float r1 = flagged(fl, o + t1) ? 0.f : fmaf(d1 - g * s1v, inv_s2, w1.y * inv_s);
             U[j1 * X.ncolmax + (j - js)] = make_float2(r0, r1);
-        }
         }
     }
     // padding columns of the last CTA stay zero
@@ -980,26 +967,14 @@ __device__ __noinline__ void ncorr_weights(const Ctx &XS, float2 *__restrict__ n
     const int npl = X.npl, m1 = X.m1, m2 = X.m2, p0 = X.p0;
     const int nbk = (npl + 3) / 4 + 1;                  // blocks touching a k range
     const int items = 2 * nbk * m2;
-    // two items per thread and step: their Philox chains are independent
-    for (int w0 = threadIdx.x; w0 < items; w0 += 2 * DCT_T) {
-        int kb2[2], b2[2], k22[2], par2[2];
-        u64x4 rw2[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int w = w0 + h * DCT_T;
-            const int rest = fdiv(w, X.f_m2), k2 = w - rest * m2;
-            const int par = rest / nbk, bi = rest - par * nbk;
-            kb2[h] = (par == 0 ? p0 : m1 - p0 - (npl - 1)) + m1 * k2;
-            b2[h] = (w < items && npl > 0) ? (kb2[h] >> 2) + bi : -1;
-            k22[h] = k2;
-            par2[h] = par;
-            if (draw && b2[h] >= 0) rw2[h] = philox4x64(static_cast<uint64_t>(b2[h]), q, 2, gi, seed, band);
-        }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-        const int kbase = kb2[h], b = b2[h], k2 = k22[h], par = par2[h];
-        if (b < 0 || 4 * b >= kbase + npl) continue;
-        const u64x4 &rw = rw2[h];
+    for (int w = threadIdx.x; w < items; w += DCT_T) {
+        const int rest = fdiv(w, X.f_m2), k2 = w - rest * m2;
+        const int par = rest / nbk, bi = rest - par * nbk;
+        const int kbase = (par == 0 ? p0 : m1 - p0 - (npl - 1)) + m1 * k2;
+        const int b = (kbase >> 2) + bi;
+        if (npl <= 0 || 4 * b >= kbase + npl) continue;
+        u64x4 rw;
+        if (draw) rw = philox4x64(static_cast<uint64_t>(b), q, 2, gi, seed, band);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int k = 4 * b + u;
@@ -1023,7 +998,6 @@ __device__ __noinline__ void ncorr_weights(const Ctx &XS, float2 *__restrict__ n
                 nu = make_float2(sqrtf(ra * inv_s2) * w2.x, sqrtf(rb * inv_s2) * w2.y);
             }
             nu_out[e] = nu;
-        }
         }
     }
     __syncthreads();
