@@ -142,14 +142,24 @@ def run_ours(args):
         dist.barrier()
     t_setup = time.time()
     cfg, band, ing = make_workload(args.nscan)
-    plan = tg.Plan(cfg.nside, cfg.ndet, cfg.nscan, cfg.fsamp, ing["offsets"], ing["pix_streams"],
-                   ing["psi_streams"], device=local)
-    info = plan.info()
-    step = GibbsTODStep(plan, band.psd, ing["flag_words"], cg_tol=args.cg_tol)
-    step.set_tod(ing["tod"])
     m4 = np.zeros((band.npix, 4), np.float32)
     m4[:, :3] = band.map_tqu.T
     map_in = torch.from_numpy(m4).cuda()
+    tuned = None
+    cs, rmax = 0, 0
+    if not args.no_autotune:
+        # measured launch shape (cluster size, largest radix) on the band's first scans
+        from paper_2201_03509_gb300.autotune import autotune
+        cs, rmax, tms = autotune(cfg.nside, cfg.ndet, cfg.nscan, cfg.fsamp, ing["offsets"], ing["pix_streams"],
+                                 ing["psi_streams"], ing["tod"], ing["flag_words"], band.psd, map_in,
+                                 device=local)
+        tuned = {"cluster_size": cs, "max_radix": rmax,
+                 "candidates_ms": {"C%d_R%d" % k: round(v, 3) for k, v in sorted(tms.items())}}
+    plan = tg.Plan(cfg.nside, cfg.ndet, cfg.nscan, cfg.fsamp, ing["offsets"], ing["pix_streams"],
+                   ing["psi_streams"], cluster_size=cs, device=local, max_radix=rmax)
+    info = plan.info()
+    step = GibbsTODStep(plan, band.psd, ing["flag_words"], cg_tol=args.cg_tol)
+    step.set_tod(ing["tod"])
     N, nq, npix = plan.N, plan.nq, plan.npix
     setup_s = time.time() - t_setup
     stream = torch.cuda.current_stream()
@@ -293,7 +303,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": cfg.name, "ndetscan": nq, "samples_per_step": N, "nside": cfg.nside,
-                   "flag_frac": cfg.flag_frac, "cluster_size": info["cluster_size"],
+                   "flag_frac": cfg.flag_frac, "cluster_size": info["cluster_size"], "autotune": tuned,
                    "l2": "inputs larger than L2 (%.2f GB per step)" % (4.0 * N / 1e9),
                    "parallelism": "replica x%d" % ws},
         "e2e": {"value": ws * N * args.steps / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": 4 * N,
@@ -405,6 +415,7 @@ def main():
     ap.add_argument("--ref-detscans-per-step", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the per-scan comparison step")
+    ap.add_argument("--no-autotune", action="store_true", help="use the plan's default launch shape")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

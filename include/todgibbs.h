@@ -138,6 +138,7 @@ typedef struct {
     tod_huff_streams psi;   /* HOST compressed psi-bin stream */
     int32_t cluster_size;   /* 0 = choose (most SMs busy); else 1..16 CTAs per detscan transform */
     int32_t device;         /* CUDA device ordinal the plan lives on */
+    int32_t max_radix;      /* largest Stockham radix of the transforms: 0 = 16; else 2..16 */
 } tod_band_desc;
 
 /* Counter-based random streams: Philox4x64-10 (Salmon et al. 2011) with key

@@ -52,7 +52,7 @@ class _HuffBuffers(ctypes.Structure):
 class _BandDesc(ctypes.Structure):
     _fields_ = [("nside", _i32), ("ndet", _i32), ("nscan", _i32), ("n_psi", _i32), ("fsamp", _f64),
                 ("offsets", _P), ("pix", _HuffStreams), ("psi", _HuffStreams),
-                ("cluster_size", _i32), ("device", _i32)]
+                ("cluster_size", _i32), ("device", _i32), ("max_radix", _i32)]
 
 
 class Rng(ctypes.Structure):
@@ -216,13 +216,14 @@ class Plan:
     """The band's TOD object on the GPU (todgibbs.h: tod_plan)."""
 
     def __init__(self, nside: int, ndet: int, nscan: int, fsamp: float, offsets: np.ndarray,
-                 pix_streams: dict, psi_streams: dict, cluster_size: int = 0, device: int = 0):
+                 pix_streams: dict, psi_streams: dict, cluster_size: int = 0, device: int = 0,
+                 max_radix: int = 0):
         keep = []
         off = _arr(offsets, np.int64)
         keep.append(off)
         desc = _BandDesc(nside, ndet, nscan, N_PSI, float(fsamp), off.ctypes.data,
                          _streams(pix_streams, keep), _streams(psi_streams, keep),
-                         int(cluster_size), int(device))
+                         int(cluster_size), int(device), int(max_radix))
         h = _P()
         _check(lib().tod_plan_create(ctypes.byref(h), ctypes.byref(desc)), "tod_plan_create")
         self._h = h

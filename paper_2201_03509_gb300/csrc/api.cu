@@ -217,7 +217,7 @@ int64_t fft_length_impl(int64_t n)
 // left.  Both column and row passes put consecutive threads on consecutive
 // vectors (the frequency layout's odd row stride keeps those rows in
 // distinct banks), so every pass may take the largest radix.
-std::vector<int8_t> radix_plan(int L, int rmax = 16)
+std::vector<int8_t> radix_plan(int L, int rmax)
 {
     static const int kRadix[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
     std::vector<int8_t> r;
@@ -245,7 +245,7 @@ void fill_stages(DctStage *st, const std::vector<int8_t> &r, int L)
 }
 
 // Choose m1 x m2 for one length with C CTAs; returns false if none fits.
-bool choose_factor(int n, int C, DctPlan &out, int &sz)
+bool choose_factor(int n, int C, int rmax, DctPlan &out, int &sz)
 {
     const int m = n / 2;
     int best = -1, bestm1 = 0;
@@ -253,7 +253,7 @@ bool choose_factor(int n, int C, DctPlan &out, int &sz)
         if (m % m1) continue;
         const int m2 = m / m1;
         if (m2 < 2) continue;
-        const auto r1 = radix_plan(m1), r2 = radix_plan(m2);
+        const auto r1 = radix_plan(m1, rmax), r2 = radix_plan(m2, rmax);
         if (r1.empty() || r2.empty() || r1.size() > DCT_MAXR || r2.size() > DCT_MAXR) continue;
         const int ncolmax = (m2 + C - 1) / C;
         const int P = m1 / 2 + 1;
@@ -276,7 +276,7 @@ bool choose_factor(int n, int C, DctPlan &out, int &sz)
     }
     if (best < 0) return false;
     const int m1 = bestm1, m2 = m / m1;
-    const auto r1 = radix_plan(m1), r2 = radix_plan(m2);
+    const auto r1 = radix_plan(m1, rmax), r2 = radix_plan(m2, rmax);
     std::memset(&out, 0, sizeof(out));
     out.n = n; out.m = m; out.m1 = m1; out.m2 = m2;
     out.m2p = m2 | 1;      // odd row stride: rows in consecutive lanes hit distinct banks
@@ -550,6 +550,8 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
         return TOD_ERR_ARG;
     const int cs = band->cluster_size;
     if (cs < 0 || cs > 16) return TOD_ERR_ARG;
+    const int rmax = band->max_radix > 0 ? band->max_radix : 16;
+    if (rmax < 2 || rmax > 16) return TOD_ERR_ARG;
     Plan *p = new (std::nothrow) Plan();
     if (!p) return TOD_ERR_OOM;
     p->device = band->device;
@@ -633,7 +635,7 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
             for (int n : uniq) {
                 DctPlan dp;
                 int s = 0;
-                if (!choose_factor(n, C, dp, s)) { ok = false; break; }
+                if (!choose_factor(n, C, rmax, dp, s)) { ok = false; break; }
                 cand.push_back(dp);
                 sz = std::max(sz, s);
                 m1max = std::max(m1max, dp.m1);

@@ -1,0 +1,93 @@
+"""Distribution of the GPU draws and CUDA-graph replay.
+
+* gain: over many Gibbs iterations, (g - mu) / sigma is N(0, 1)
+  (Kolmogorov-Smirnov);
+* n_corr on gap-free detscans: the draw minus the conditional mean, taken to
+  the DCT basis and scaled by sqrt(phi_k + 1/sigma0^2), is N(0, 1) in every
+  mode (the conditional covariance is C^T diag(1/(phi + 1/sigma0^2)) C);
+* a step captured as a CUDA graph and replayed at Gibbs iteration k gives
+  bit for bit what the eager step gives at k.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    from gpu_workload import Workload
+    cfg = synth.CONFIGS["tiny"]
+    assert cfg.flag_frac == 0.0
+    return Workload(cfg, cluster_size=0)
+
+
+@pytest.mark.gpu
+def test_gain_draws_are_standard_normal(tiny):
+    import torch
+    from scipy import stats
+    import paper_2201_03509_gb300 as tg
+    wl = tiny
+    g = torch.zeros(wl.nq, dtype=torch.float64, device=wl.dev)
+    mu = torch.zeros_like(g)
+    sg = torch.zeros_like(g)
+    zs = []
+    for it in range(300):
+        wl.plan.sample_gain(wl.t_d, wl.t_s, wl.t_flags, wl.t_psd, tg.Rng(7, 1, it), tg.MODE_DRAW, g, mu, sg)
+        zs.append(((g - mu) / sg).cpu().numpy())
+    wl.plan.status()
+    z = np.concatenate(zs)
+    assert z.size == 300 * wl.nq
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+    assert abs(z.mean()) < 4.0 / np.sqrt(z.size)
+
+
+@pytest.mark.gpu
+def test_ncorr_draws_have_the_conditional_covariance(tiny):
+    import torch
+    from scipy import fft, stats
+    import paper_2201_03509_gb300 as tg
+    wl = tiny
+    gains = torch.from_numpy(wl.band.gain.copy()).to(wl.dev)
+    xm = torch.zeros(wl.N, dtype=torch.float32, device=wl.dev)
+    x = torch.zeros_like(xm)
+    wl.plan.sample_ncorr(wl.t_d, wl.t_s, gains, wl.t_flags, wl.t_psd, tg.Rng(9, 2, 0), tg.MODE_MEAN, xm)
+    mean = xm.cpu().numpy().astype(np.float64)
+    ws = []
+    for it in range(4):
+        wl.plan.sample_ncorr(wl.t_d, wl.t_s, gains, wl.t_flags, wl.t_psd, tg.Rng(9, 2, it), tg.MODE_DRAW, x)
+        dx = x.cpu().numpy().astype(np.float64) - mean
+        for q in range(wl.nq):
+            sl = wl.sl(q)
+            n = sl.stop - sl.start
+            s0, fk, al = wl.band.psd[wl.det(q)]
+            phi = oracle.corr_inv_psd(n, wl.cfg.fsamp, s0, fk, al)
+            ws.append(fft.dct(dx[sl], type=2, norm="ortho") * np.sqrt(phi + 1.0 / s0 ** 2))
+    wl.plan.status()
+    w = np.concatenate(ws)
+    assert stats.kstest(w, "norm").pvalue > 1e-3
+    assert abs(w.std() - 1.0) < 0.02
+
+
+@pytest.mark.gpu
+def test_graph_replay_matches_eager_step(tiny):
+    import torch
+    import paper_2201_03509_gb300 as tg
+    from paper_2201_03509_gb300.step import GibbsTODStep
+    wl = tiny
+    step = GibbsTODStep(wl.plan, wl.band.psd, wl.ing["flag_words"])
+    step.set_tod(wl.d32)
+    step.run(wl.t_map, tg.Rng(3, 0, 5), tg.MODE_DRAW)
+    torch.cuda.synchronize()
+    ref = [t.clone() for t in (step.gain, step.ncorr, step.A, step.b, step.map)]
+    step.capture(wl.t_map, 3, 0, tg.MODE_DRAW)
+    step.replay(5)
+    torch.cuda.synchronize()
+    got = (step.gain, step.ncorr, step.A, step.b, step.map)
+    for a, b in zip(ref, got):
+        assert torch.equal(a, b)
+    step.replay(6)
+    torch.cuda.synchronize()
+    assert not torch.equal(ref[0], step.gain)      # a fresh iteration draws fresh numbers
+    wl.plan.status()

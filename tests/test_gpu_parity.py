@@ -18,7 +18,8 @@ def _cfgs():
     # a few LFI-30-like detscans, short enough for the oracle, with flags
     l30 = synth.scaled(synth.CONFIGS["lfi30"], nscan=3, len_lo=9000, len_hi=30000)
     return {"tiny_c1": (tiny, 1), "tiny_c4": (tiny, 4), "tiny_c3": (tiny, 3), "lfi30_small_c2": (l30, 2),
-            "lfi30_small_c8": (l30, 8), "lfi30_small_c9": (l30, 9), "lfi30_small_auto": (l30, 0)}
+            "lfi30_small_c8": (l30, 8), "lfi30_small_c9": (l30, 9), "lfi30_small_auto": (l30, 0),
+            "lfi30_small_c9_r8": (l30, 9, 8), "tiny_c2_r4": (tiny, 2, 4)}
 
 
 @pytest.fixture(scope="module", params=list(_cfgs().keys()))
@@ -27,8 +28,8 @@ def wl(request):
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     from gpu_workload import Workload
-    cfg, cs = _cfgs()[request.param]
-    return Workload(cfg, cluster_size=cs)
+    cfg, cs, *rmax = _cfgs()[request.param]
+    return Workload(cfg, cluster_size=cs, max_radix=rmax[0] if rmax else 0)
 
 
 def test_plan_info(wl):
