@@ -516,9 +516,10 @@ __device__ __noinline__ void transpose(const Ctx &XS, const float2 *src, float2 
 
 // Forward DCT: time layout in cur -> packed spectrum in cur (the two
 // buffers may swap roles).
-__device__ __noinline__ void dct_forward(const Ctx &XS, float2 *&cur, float2 *&oth, const float2 *,
+__device__ __noinline__ bool dct_forward(const Ctx &XS, float2 *cur, float2 *oth, const float2 *,
                                          const float2 *, cg::cluster_group &cl)
 {
+    float2 *const c0 = cur;
     const Geo X = XS;
     const float2 *tw1 = X.tw1, *tw2 = X.tw2;
     fft_seq<false>(cur, oth, X.m1, XS.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, tw1);
@@ -526,12 +527,14 @@ __device__ __noinline__ void dct_forward(const Ctx &XS, float2 *&cur, float2 *&o
     { float2 *t = cur; cur = oth; oth = t; }
     fft_seq<false>(cur, oth, X.m2, XS.s2, X.nr2, 2 * X.npl, X.f_2npl, 1, X.m2p, true, tw2);
     split_pass<false>(XS, cur);
+    return cur != c0;     // the result is in the caller's other buffer
 }
 // Inverse (transpose of the orthonormal DCT-II): packed spectrum in cur ->
 // time layout in cur, scaled.
-__device__ __noinline__ void dct_inverse(const Ctx &XS, float2 *&cur, float2 *&oth, const float2 *,
+__device__ __noinline__ bool dct_inverse(const Ctx &XS, float2 *cur, float2 *oth, const float2 *,
                                          const float2 *, cg::cluster_group &cl)
 {
+    float2 *const c0 = cur;
     const Geo X = XS;
     const float2 *tw1 = X.tw1, *tw2 = X.tw2;
     split_pass<true>(XS, cur);
@@ -539,25 +542,30 @@ __device__ __noinline__ void dct_inverse(const Ctx &XS, float2 *&cur, float2 *&o
     transpose<true>(XS, cur, oth, cl);
     { float2 *t = cur; cur = oth; oth = t; }
     fft_seq<true>(cur, oth, X.m1, XS.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, tw1);
+    return cur != c0;     // the result is in the caller's other buffer
 }
 
 // The two halves of a filter round trip: time layout -> row-FFT output
 // (split not applied), and back.
-__device__ __noinline__ void dct_forward_pre(const Ctx &XS, float2 *&cur, float2 *&oth, cg::cluster_group &cl)
+__device__ __noinline__ bool dct_forward_pre(const Ctx &XS, float2 *cur, float2 *oth, cg::cluster_group &cl)
 {
+    float2 *const c0 = cur;
     const Geo X = XS;
     fft_seq<false>(cur, oth, X.m1, XS.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, X.tw1);
     transpose<false>(XS, cur, oth, cl);
     { float2 *t = cur; cur = oth; oth = t; }
     fft_seq<false>(cur, oth, X.m2, XS.s2, X.nr2, 2 * X.npl, X.f_2npl, 1, X.m2p, true, X.tw2);
+    return cur != c0;     // the result is in the caller's other buffer
 }
-__device__ __noinline__ void dct_inverse_post(const Ctx &XS, float2 *&cur, float2 *&oth, cg::cluster_group &cl)
+__device__ __noinline__ bool dct_inverse_post(const Ctx &XS, float2 *cur, float2 *oth, cg::cluster_group &cl)
 {
+    float2 *const c0 = cur;
     const Geo X = XS;
     fft_seq<true>(cur, oth, X.m2, XS.s2, X.nr2, 2 * X.npl, X.f_2npl, 1, X.m2p, true, X.tw2);
     transpose<true>(XS, cur, oth, cl);
     { float2 *t = cur; cur = oth; oth = t; }
     fft_seq<true>(cur, oth, X.m1, XS.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, X.tw1);
+    return cur != c0;     // the result is in the caller's other buffer
 }
 
 // Fill U (time layout) with f(j) = (x_{t(2j)}, x_{t(2j+1)}) for own columns.
@@ -597,7 +605,7 @@ __device__ __forceinline__ Acc2 acc_merge2(const Acc2 &a, const Acc2 &b) {
     r.c = __fadd_rn(r.c, b.c);
     return r;
 }
-__device__ double2 cluster_sum_acc(Acc2 x, Acc2 y, double2 *s_red, double2 *s_part, int &parity,
+__device__ __forceinline__ double2 cluster_sum_acc(Acc2 x, Acc2 y, double2 *s_red, double2 *s_part, int &parity,
                                    cg::cluster_group &cl)
 {
 #pragma unroll
@@ -686,7 +694,7 @@ __device__ __forceinline__ Smem carve(void *raw, int sz, int twsz)
 
 // Stage plan pi in shared memory: scalars and stage tables into sX, the
 // length's twiddle block into sm.twb (all threads copy).
-__device__ void load_plan(Ctx *sX, const DctPlan *plans, int pi, const float2 *tw, Smem &sm, int c, int C)
+__device__ __forceinline__ void load_plan(Ctx *sX, const DctPlan *plans, int pi, const float2 *tw, Smem &sm, int c, int C)
 {
     __syncthreads();      // previous users of sX and the twiddle block are done
     const DctPlan &P = plans[pi];
@@ -787,7 +795,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_gain(GainArgs a)
         const int det = q % a.ndet;
         const int64_t o = a.off[q];
         load_plan(&sX, a.plans, a.q_plan[q], a.tw, sm, c, C);
-        const Geo X = sX;
+        const Ctx &X = sX;     // shared-memory copy (a register copy would live on the stack)
         const int n = X.n, m = X.m;
         const float *sq = a.s + o, *dq = a.d + o;
         const uint32_t *fl = a.flags;
@@ -801,7 +809,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_gain(GainArgs a)
             const float v0 = __ldg(sq + t0), v1 = __ldg(sq + t1);      // independent of the flags
             return make_float2(flagged(fl, o + t0) ? 0.f : v0, flagged(fl, o + t1) ? 0.f : v1);
         });
-        dct_forward_pre(sX, cur, oth, cl);
+        if (dct_forward_pre(sX, cur, oth, cl)) { float2 *t_ = cur; cur = oth; oth = t_; }
         Acc2 sa = {0.f, 0.f}, sb = {0.f, 0.f};
         split_roundtrip(X, cur, [&](int, int k, float2 S) {
             const int ka = k, kb = (k == 0) ? m : n - k;
@@ -812,7 +820,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_gain(GainArgs a)
             acc_add_prod(sa, S.y, W.y);
             return W;
         });
-        dct_inverse_post(sX, cur, oth, cl);
+        if (dct_inverse_post(sX, cur, oth, cl)) { float2 *t_ = cur; cur = oth; oth = t_; }
         {
             const int tot = X.m1 * X.ncolmax;
             for (int e = threadIdx.x; e < tot; e += DCT_T) {
@@ -1211,7 +1219,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
         float2 *cur = sm.U0, *oth = sm.U1;
         // right-hand side, time-domain part: M (r/s2 + w1/s)
         ncorr_rhs(sX, cur, dq, sq, fl, o, g, inv_s2, inv_s, draw, q, gi, rng.seed, rng.band);
-        dct_forward_pre(sX, cur, oth, cl);
+        if (dct_forward_pre(sX, cur, oth, cl)) { float2 *t_ = cur; cur = oth; oth = t_; }
         // prior term sqrt(phi) w2 in the packed layout into the free buffer
         // oth, filter weights of this detscan into wt
         ncorr_weights(sX, oth, wt, fscale, alpha, s2, inv_s2, draw, q, gi, rng.seed, rng.band);
@@ -1222,7 +1230,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             return make_float2((Y.x + nu.x) * w.x, (Y.y + nu.y) * w.y);
         });
 
-        dct_inverse_post(sX, cur, oth, cl);      // cur = x0 (time layout)
+        if (dct_inverse_post(sX, cur, oth, cl)) { float2 *t_ = cur; cur = oth; oth = t_; }      // cur = x0 (time layout)
         // x0 -> x_out
         {
             const int tot = X.m1 * X.ncolmax;
@@ -1404,12 +1412,12 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                 cl.sync();     // every buffer is zero before the scatters
                 for (int i = threadIdx.x; i < kc; i += DCT_T) *cg_elem(cl, cur, c_loc, i) = c_p[i];
                 cl.sync();     // every scatter has landed
-                dct_forward_pre(sX, cur, oth, cl);
+                if (dct_forward_pre(sX, cur, oth, cl)) { float2 *t_ = cur; cur = oth; oth = t_; }
                 split_roundtrip(X, cur, [&](int e, int, float2 Y) {
                     const float4 w = wt[e];
                     return make_float2(Y.x * w.z, Y.y * w.w);
                 });
-                dct_inverse_post(sX, cur, oth, cl);
+                if (dct_inverse_post(sX, cur, oth, cl)) { float2 *t_ = cur; cur = oth; oth = t_; }
                 cl.sync();     // every CTA's result is complete before the gathers
                 Acc2 pq_loc = {0.f, 0.f};
                 for (int i = threadIdx.x; i < kc; i += DCT_T) {
@@ -1445,12 +1453,12 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             cl.sync();
             for (int i = threadIdx.x; i < kc; i += DCT_T) *cg_elem(cl, cur, c_loc, i) = c_y[i];
             cl.sync();
-            dct_forward_pre(sX, cur, oth, cl);
+            if (dct_forward_pre(sX, cur, oth, cl)) { float2 *t_ = cur; cur = oth; oth = t_; }
             split_roundtrip(X, cur, [&](int e, int, float2 Y) {
                 const float4 w = wt[e];
                 return make_float2(Y.x * w.x, Y.y * w.y);
             });
-            dct_inverse_post(sX, cur, oth, cl);
+            if (dct_inverse_post(sX, cur, oth, cl)) { float2 *t_ = cur; cur = oth; oth = t_; }
             for (int e = threadIdx.x; e < tot; e += DCT_T) {
                 int t0, t1;
                 bool valid;
@@ -1511,7 +1519,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_chi2(Chi2Args a)
         const int det = q % a.ndet;
         const int64_t o = a.off[q];
         load_plan(&sX, a.plans, a.q_plan[q], a.tw, sm, c, C);
-        const Geo X = sX;
+        const Ctx &X = sX;     // shared-memory copy (a register copy would live on the stack)
         const int n = X.n, m = X.m;
         const float *sq = a.s + o, *dq = a.d + o;
         const uint32_t *fl = a.flags;
@@ -1523,7 +1531,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_chi2(Chi2Args a)
             const float d0 = __ldg(dq + t0), d1 = __ldg(dq + t1), s0v = __ldg(sq + t0), s1v = __ldg(sq + t1);
             return make_float2(flagged(fl, o + t0) ? 0.f : d0 - g * s0v, flagged(fl, o + t1) ? 0.f : d1 - g * s1v);
         });
-        dct_forward(sX, cur, oth, X.tw1, X.tw2, cl);
+        if (dct_forward(sX, cur, oth, X.tw1, X.tw2, cl)) { float2 *t_ = cur; cur = oth; oth = t_; }
         // per mode: rhat^2/P, ln(1+x), and the f_knee / alpha gradient terms
         Acc2 aq = {0.f, 0.f}, al1 = {0.f, 0.f}, afk = {0.f, 0.f}, aal = {0.f, 0.f};
         {
@@ -1557,7 +1565,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_chi2(Chi2Args a)
             }
             __syncthreads();
         }
-        dct_inverse(sX, cur, oth, X.tw1, X.tw2, cl);
+        if (dct_inverse(sX, cur, oth, X.tw1, X.tw2, cl)) { float2 *t_ = cur; cur = oth; oth = t_; }
         Acc2 ag = {0.f, 0.f};
         {
             const int tot = X.m1 * X.ncolmax;
