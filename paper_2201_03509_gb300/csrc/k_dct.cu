@@ -822,15 +822,33 @@ __global__ void __launch_bounds__(DCT_T, 1) k_gain(GainArgs a)
         });
         if (dct_inverse_post(sX, cur, oth, cl)) { float2 *t_ = cur; cur = oth; oth = t_; }
         {
+            // four elements per thread with every load in flight, summed in
+            // element order (a flagged sample adds an exact zero)
+            constexpr int UB = 4;
             const int tot = X.m1 * X.ncolmax;
-            for (int e = threadIdx.x; e < tot; e += DCT_T) {
-                int t0, t1;
-                bool valid;
-                elem_samples(X, e, t0, t1, valid);
-                if (!valid) continue;
-                const float2 v = cur[e];
-                if (!flagged(fl, o + t0)) acc_add_prod(sb, __ldg(dq + t0), v.x);
-                if (!flagged(fl, o + t1)) acc_add_prod(sb, __ldg(dq + t1), v.y);
+            for (int e0 = threadIdx.x; e0 < tot; e0 += UB * DCT_T) {
+                float2 v[UB], dv[UB];
+#pragma unroll
+                for (int u = 0; u < UB; ++u) {
+                    const int e = e0 + u * DCT_T;
+                    v[u] = make_float2(0.f, 0.f);
+                    dv[u] = make_float2(0.f, 0.f);
+                    if (e < tot) {
+                        int t0, t1;
+                        bool valid;
+                        elem_samples(X, e, t0, t1, valid);
+                        if (valid) {
+                            v[u] = cur[e];
+                            const float d0 = __ldg(dq + t0), d1 = __ldg(dq + t1);
+                            dv[u] = make_float2(flagged(fl, o + t0) ? 0.f : d0, flagged(fl, o + t1) ? 0.f : d1);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < UB; ++u) {
+                    acc_add_prod(sb, dv[u].x, v[u].x);
+                    acc_add_prod(sb, dv[u].y, v[u].y);
+                }
             }
         }
         const double2 ab = cluster_sum_acc(sa, sb, s_red, s_part,
