@@ -877,6 +877,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_gain(GainArgs a)
             }
         }
     }
+    cl.sync();     // no CTA leaves while a sibling may still read its cluster-sum slot
 }
 
 // ---------------------------------------------------------------------------
@@ -1414,6 +1415,12 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             }
             __syncthreads();
             precond();
+            if (!use_prec) cl.sync();     // (the preconditioner ends with one)
+            // every remote read of x0 ended before the preconditioner's closing
+            // cluster barrier: clear the buffer for the first scatter (the
+            // barrier of the sums below orders this before any scatter)
+            const int tot = X.m1 * X.ncolmax;
+            for (int e = threadIdx.x; e < tot; e += DCT_T) cur[e] = make_float2(0.f, 0.f);
             Acc2 rz_loc = {0.f, 0.f};
             for (int i = threadIdx.x; i < kc; i += DCT_T) {
                 c_p[i] = c_z[i];
@@ -1423,11 +1430,8 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             double rz = rr2.y;
             const double stop = static_cast<double>(a.tol) * a.tol * rr2.x;
             conv = rr2.x == 0.0;
-            const int tot = X.m1 * X.ncolmax;
             while (!conv && it < a.maxit) {
-                // cur <- C^T diag(gamma) C E p
-                for (int e = threadIdx.x; e < tot; e += DCT_T) cur[e] = make_float2(0.f, 0.f);
-                cl.sync();     // every buffer is zero before the scatters
+                // cur <- C^T diag(gamma) C E p (cur is zero in every CTA)
                 for (int i = threadIdx.x; i < kc; i += DCT_T) *cg_elem(cl, cur, c_loc, i) = c_p[i];
                 cl.sync();     // every scatter has landed
                 if (dct_forward_pre(sX, cur, oth, cl)) { float2 *t_ = cur; cur = oth; oth = t_; }
@@ -1444,6 +1448,9 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                     acc_add_prod(pq_loc, c_p[i], v);
                 }
                 const double pq = cluster_sum_acc(pq_loc, Acc2{0.f, 0.f}, s_red, s_part, parity, cl).x;
+                // the gathers ended before that cluster barrier: clear the buffer
+                // for the next scatter (ordered by the barriers below)
+                for (int e = threadIdx.x; e < tot; e += DCT_T) cur[e] = make_float2(0.f, 0.f);
                 // step lengths in FP32 (the vectors are FP32); FP64 division
                 // by every thread would cost more than the update itself
                 const float alp = static_cast<float>(rz) / static_cast<float>(pq);
@@ -1466,9 +1473,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                 __syncthreads();
                 rz = rn2.y;
             }
-            // x = x0 + B^{-1} E y
-            for (int e = threadIdx.x; e < tot; e += DCT_T) cur[e] = make_float2(0.f, 0.f);
-            cl.sync();
+            // x = x0 + B^{-1} E y (cur is zero in every CTA)
             for (int i = threadIdx.x; i < kc; i += DCT_T) *cg_elem(cl, cur, c_loc, i) = c_y[i];
             cl.sync();
             if (dct_forward_pre(sX, cur, oth, cl)) { float2 *t_ = cur; cur = oth; oth = t_; }
@@ -1489,10 +1494,11 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             if (!conv) set_status(a.status, q, TOD_ERR_NOT_CONVERGED);
         }
         if (a.iters && c == 0 && threadIdx.x == 0) a.iters[q] = it;
-        // the buffers of this CTA may still be read remotely by a sibling's
-        // last transpose: start the next detscan only after this barrier
-        cl.sync();
+        // No barrier here: every remote access of this detscan (transposes,
+        // CG gathers and scatters, preconditioner) is followed by a cluster
+        // barrier before it ends, and the cluster sums alternate their slot.
     }
+    cl.sync();     // no CTA leaves while a sibling may still read its shared memory
 }
 
 // ---------------------------------------------------------------------------
@@ -1614,6 +1620,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_chi2(Chi2Args a)
             a.dpsd[3 * q + 2] = r2.y;
         }
     }
+    cl.sync();     // no CTA leaves while a sibling may still read its cluster-sum slot
 }
 
 // ---------------------------------------------------------------------------
