@@ -212,11 +212,12 @@ int64_t fft_length_impl(int64_t n)
     return best;
 }
 
-// Stockham radices of a sub-transform of length L: the largest register
-// DFT up to rmax (16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2) that divides what is
-// left.  Both column and row passes put consecutive threads on consecutive
-// vectors (the frequency layout's odd row stride keeps those rows in
-// distinct banks), so every pass may take the largest radix.
+// Stockham radices of a sub-transform of length L: repeatedly the largest
+// register DFT up to rmax (16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2) that divides
+// what is left, applied in increasing order.  Column and row passes put
+// consecutive threads on consecutive vectors (the frequency layout's odd
+// row stride keeps those rows in distinct banks), so every pass may take
+// the largest radix.
 std::vector<int8_t> radix_plan(int L, int rmax)
 {
     static const int kRadix[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
@@ -229,6 +230,11 @@ std::vector<int8_t> radix_plan(int L, int rmax)
         r.push_back(static_cast<int8_t>(pick));
         L /= pick;
     }
+    // largest radix last: the last pass, which also writes the four-step
+    // transpose into the other CTAs, then has the fewest butterflies (one
+    // per thread where it can), so each thread's first butterfly is done
+    // while the cluster barrier before the remote writes completes
+    std::reverse(r.begin(), r.end());
     return r;
 }
 

@@ -13,12 +13,12 @@
 //                 [c*npmax, (c+1)*npmax), of Z[k1 + m1*k2], stored
 //                 [slot][k2] -- a row and its mirror share a CTA, so the real
 //                 split that combines Z_k with Z_{m-k} is local.
-// Column FFTs (length m1) and row FFTs (length m2) are mixed-radix (2,3,4,5)
-// Stockham passes in shared memory with butterflies in registers; the
-// transpose between them reads the other CTAs' shared memory (DSMEM) into
-// registers, applies the four-step twiddle, and writes back into the same
-// buffer after a cluster barrier, so one buffer of ~m/C complex values per
-// CTA holds a transform.  Nothing of a transform touches HBM.
+// Column FFTs (length m1) and row FFTs (length m2) are mixed-radix
+// Stockham passes (register DFTs of radix 2 to 16) ping-ponging between two
+// shared-memory buffers of ~m/C complex values per CTA; the last column
+// pass (forward) or row pass (inverse) writes its outputs, times the
+// four-step twiddle, straight into the other CTAs' buffers (DSMEM), which
+// is the transpose.  Nothing of a transform touches HBM.
 //
 // Spectra are kept packed: slot k (1 <= k < m) holds the orthonormal DCT
 // coefficients (X_k, X_{n-k}); slot 0 holds (X_0, X_m).
@@ -197,62 +197,76 @@ template <int R, bool INV> struct Dft {
     }
 };
 
-// One Stockham radix-R pass (Govindaraju et al. 2008 formulation) over nvec
-// vectors of length L, out of place from src to dst in shared memory
-// (element stride es, vector stride vs).  Each thread loops over whole
-// butterflies; one barrier per pass.  vfast: consecutive threads take
-// consecutive vectors (column FFTs) instead of consecutive elements (row
-// FFTs).  Index arithmetic uses precomputed multiply-shift divisions.
+// One butterfly w of a Stockham radix-R pass (Govindaraju et al. 2008
+// formulation) over nvec vectors of length L (element stride es, vector
+// stride vs): loads its R inputs from src, applies the pass twiddles and
+// the register DFT; v gets the outputs, which belong at elements
+// jq Ns R + k + r Ns of vector vec.  vfast: consecutive w take consecutive
+// vectors (column FFTs) instead of consecutive elements (row FFTs).  Index
+// arithmetic uses precomputed multiply-shift divisions.
+template <int R, bool INV>
+__device__ __forceinline__ void bfly(const float2 *__restrict__ src, int L, const DctStage &st, int nvec,
+                                     const FastDiv &fnvec, int es, int vs, bool vfast,
+                                     const float2 *__restrict__ tw, int w, float2 (&v)[R], int &vec, int &jq,
+                                     int &k)
+{
+    const int LR = L / R;
+    const int Ns = st.Ns;
+    const int tstep = L / (Ns * R);
+    int j;
+    if (vfast) { j = fdiv(w, fnvec); vec = w - j * nvec; }
+    else { vec = fdiv(w, st.fLR); j = w - vec * LR; }
+    const float2 *p = src + vec * vs + j * es;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = p[r * LR * es];
+    jq = fdiv(j, st.fNs);
+    k = j - jq * Ns;
+    if (Ns > 1) {
+        if constexpr (R <= 5) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                float2 t = tw[r * k * tstep];
+                if (INV) t.y = -t.y;
+                v[r] = cmul(v[r], t);
+            }
+        } else {
+            // W^r for r = 4q + j: W^{4q} from the table, times W^j (j < 4)
+            // from W^1 by at most two multiplies
+            const int ks = k * tstep;
+            float2 w1 = tw[ks];
+            if (INV) w1.y = -w1.y;
+            const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
+#pragma unroll
+            for (int q4 = 0; q4 < R; q4 += 4) {
+                float2 wq = make_float2(1.f, 0.f);
+                if (q4 > 0) { wq = tw[q4 * ks]; if (INV) wq.y = -wq.y; }
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const int r = q4 + jj;
+                    if (r == 0 || r >= R) continue;
+                    const float2 wj = jj == 0 ? make_float2(1.f, 0.f) : jj == 1 ? w1 : jj == 2 ? w2 : w3;
+                    const float2 t = q4 == 0 ? wj : (jj == 0 ? wq : cmul(wq, wj));
+                    v[r] = cmul(v[r], t);
+                }
+            }
+        }
+    }
+    Dft<R, INV>::run(v);
+}
+
+// One Stockham pass, out of place from src to dst in shared memory; each
+// thread loops over whole butterflies; one barrier per pass.
 template <int R, bool INV>
 __device__ __noinline__ void fft_pass(const float2 *__restrict__ src, float2 *__restrict__ dst, int L,
                                       const DctStage st, int nvec, const FastDiv fnvec, int es, int vs,
                                       bool vfast, const float2 *__restrict__ tw)
 {
-    const int LR = L / R;
+    const int total = nvec * (L / R);
     const int Ns = st.Ns;
-    const int total = nvec * LR;
-    const int tstep = L / (Ns * R);
     for (int w = threadIdx.x; w < total; w += DCT_T) {
-        int vec, j;
-        if (vfast) { j = fdiv(w, fnvec); vec = w - j * nvec; }
-        else { vec = fdiv(w, st.fLR); j = w - vec * LR; }
-        const float2 *p = src + vec * vs + j * es;
         float2 v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = p[r * LR * es];
-        const int jq = fdiv(j, st.fNs);
-        const int k = j - jq * Ns;
-        if (Ns > 1) {
-            if constexpr (R <= 5) {
-#pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    float2 t = tw[r * k * tstep];
-                    if (INV) t.y = -t.y;
-                    v[r] = cmul(v[r], t);
-                }
-            } else {
-                // W^r for r = 4q + j: W^{4q} from the table, times W^j (j < 4)
-                // from W^1 by at most two multiplies
-                const int ks = k * tstep;
-                float2 w1 = tw[ks];
-                if (INV) w1.y = -w1.y;
-                const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
-#pragma unroll
-                for (int q4 = 0; q4 < R; q4 += 4) {
-                    float2 wq = make_float2(1.f, 0.f);
-                    if (q4 > 0) { wq = tw[q4 * ks]; if (INV) wq.y = -wq.y; }
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int r = q4 + j;
-                        if (r == 0 || r >= R) continue;
-                        const float2 wj = j == 0 ? make_float2(1.f, 0.f) : j == 1 ? w1 : j == 2 ? w2 : w3;
-                        const float2 t = q4 == 0 ? wj : (j == 0 ? wq : cmul(wq, wj));
-                        v[r] = cmul(v[r], t);
-                    }
-                }
-            }
-        }
-        Dft<R, INV>::run(v);
+        int vec, jq, k;
+        bfly<R, INV>(src, L, st, nvec, fnvec, es, vs, vfast, tw, w, v, vec, jq, k);
         float2 *q = dst + vec * vs + (jq * Ns * R + k) * es;
 #pragma unroll
         for (int r = 0; r < R; ++r) q[r * Ns * es] = v[r];
@@ -441,77 +455,99 @@ __device__ __forceinline__ void split_roundtrip(const Geo &XS, float2 *__restric
     __syncthreads();
 }
 
-// Time layout (src, every CTA) -> freq layout (dst, local), or back.  The
-// four-step twiddle W_m^{-+ j2 k1} comes from the two-level table.  The
-// first cluster barrier makes every CTA's src complete; the second keeps
-// src alive until every remote read of it has finished.
-template <bool INV>
-__device__ __noinline__ void transpose(const Ctx &XS, const float2 *src, float2 *__restrict__ dst,
-                                       cg::cluster_group &cl)
+// The last Stockham pass of the column FFTs (forward) or of the row FFTs
+// (inverse) with the four-step transpose folded in: each output goes,
+// times the four-step twiddle W_m^{-+ j2 k1}, straight into the shared
+// memory of the CTA that owns it in the other layout, into that CTA's
+// buffer dst (the same offset in every CTA).  Forward: vector = local
+// column j2, output k1 -> frequency-layout slot of row k1 in the CTA that
+// holds the pair {k1, m1-k1}.  Inverse: vector = local row slot (row k1),
+// output j2 -> time-layout column j2 of its CTA.  The first butterfly of
+// each thread is computed between the two halves of the barrier that
+// frees every CTA's dst, hiding its latency; a full cluster barrier at the
+// end makes every remote write visible.  Slots and columns that hold no
+// data (the odd slot of a single-row pair, the padding columns of the last
+// CTA) are not written and are never read.
+template <int R, bool INV>
+__device__ __noinline__ void fft_push(const Ctx &XS, float2 *__restrict__ src, float2 *dst, int L,
+                                      const DctStage st, int nvec, const FastDiv fnvec, int es, int vs,
+                                      bool vfast, const float2 *__restrict__ tw, cg::cluster_group &cl)
 {
     const Geo X = XS;
-    constexpr int U = 4;     // independent remote reads in flight per thread
-    const int m = X.m, m1 = X.m1, m2 = X.m2, ncolmax = X.ncolmax, npmax = X.npmax;
-    cl.sync();
-    if (!INV) {
-        const int total = 2 * X.npl * m2;
-        const FastDiv fm2 = X.f_m2, fnc = X.f_ncolmax;
-        for (int e0 = threadIdx.x; e0 < total; e0 += U * DCT_T) {
-            float2 v[U], w[U];
+    const int total = nvec * (L / R);
+    const int Ns = st.Ns;
+    const int LR = L / R;
+    // The cluster barrier in two halves (every thread of every CTA takes
+    // both): arrive once this thread is done with dst and the earlier
+    // passes, wait until every thread of the cluster is.  In between, the
+    // thread's first butterfly is computed and put back in place (its R
+    // inputs are read by no other butterfly): registers live across the
+    // wait would go to local memory.
+    auto token = cl.barrier_arrive();
+    float2 v[R];
+    int vec = 0, jq = 0, k = 0;
+    if (threadIdx.x < total) {
+        bfly<R, INV>(src, L, st, nvec, fnvec, es, vs, vfast, tw, threadIdx.x, v, vec, jq, k);
+        float2 *pp = src + vec * vs + k * es;            // the last pass: jq = 0, j = k
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int e = e0 + u * DCT_T;
-                v[u] = make_float2(0.f, 0.f);
-                w[u] = make_float2(1.f, 0.f);
-                if (e < total) {
-                    const int slot = fdiv(e, fm2), j2 = e - slot * m2;
-                    const int k1 = slot_row(X, slot);
-                    if (k1 >= 0) {
-                        const int o = fdiv(j2, fnc), lc = j2 - o * ncolmax;
-                        v[u] = cl.map_shared_rank(src, o)[k1 * ncolmax + lc];
-                        w[u] = tw4_lookup(X, j2 * k1);
-                    }
-                }
-            }
+        for (int r = 0; r < R; ++r) pp[r * LR * es] = v[r];
+    }
+    cl.barrier_wait(std::move(token));      // every CTA's dst is free
+    for (int w = threadIdx.x; w < total; w += DCT_T) {
+        if (w != threadIdx.x) {
+            bfly<R, INV>(src, L, st, nvec, fnvec, es, vs, vfast, tw, w, v, vec, jq, k);
+        } else {
+            if (vfast) { k = fdiv(w, fnvec); vec = w - k * nvec; }
+            else { vec = fdiv(w, st.fLR); k = w - vec * LR; }
+            const float2 *pp = src + vec * vs + k * es;
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int e = e0 + u * DCT_T;
-                if (e < total) {
-                    const int slot = fdiv(e, fm2);
-                    dst[e + slot * (X.m2p - m2)] = cmul(v[u], w[u]);
-                }
-            }
+            for (int r = 0; r < R; ++r) v[r] = pp[r * LR * es];
         }
-    } else {
-        const int total = m1 * ncolmax;
-        const FastDiv fnc = X.f_ncolmax, fnp = X.f_npmax;
-        for (int e0 = threadIdx.x; e0 < total; e0 += U * DCT_T) {
-            float2 v[U], w[U];
+        if (!INV) {
+            if (vec >= X.ncol) continue;                     // padding column
+            const int j2 = X.c * X.ncolmax + vec;
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int e = e0 + u * DCT_T;
-                v[u] = make_float2(0.f, 0.f);
-                w[u] = make_float2(1.f, 0.f);
-                if (e < total) {
-                    const int k1 = fdiv(e, fnc), lc = e - k1 * ncolmax;
-                    if (lc < X.ncol) {
-                        const int j2 = X.c * ncolmax + lc;
-                        const int p = min(k1, m1 - k1);
-                        const int o = fdiv(p, fnp);
-                        const int slot = 2 * (p - o * npmax) + (k1 == p ? 0 : 1);
-                        v[u] = cl.map_shared_rank(src, o)[slot * X.m2p + j2];
-                        w[u] = tw4_lookup(X, j2 * k1);
-                    }
-                }
+            for (int r = 0; r < R; ++r) {
+                const int k1 = k + r * Ns;
+                const int p = min(k1, X.m1 - k1);
+                const int o = fdiv(p, X.f_npmax);
+                const int slot = 2 * (p - o * X.npmax) + (k1 == p ? 0 : 1);
+                cl.map_shared_rank(dst, o)[slot * X.m2p + j2] = cmul(v[r], tw4_lookup(X, j2 * k1));
             }
+        } else {
+            const int k1 = slot_row(X, vec);
+            if (k1 < 0) continue;                            // slot without a row
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int e = e0 + u * DCT_T;
-                if (e < total) dst[e] = cmulc(v[u], w[u]);
+            for (int r = 0; r < R; ++r) {
+                const int j2 = k + r * Ns;
+                const int o = fdiv(j2, X.f_ncolmax);
+                cl.map_shared_rank(dst, o)[k1 * X.ncolmax + (j2 - o * X.ncolmax)] =
+                    cmulc(v[r], tw4_lookup(X, j2 * k1));
             }
         }
     }
-    cl.sync();
+    cl.sync();                // every remote write has landed
+}
+
+// The last pass of a sub-transform as fft_push, by radix.
+template <bool INV>
+__device__ void fft_push_last(const Ctx &XS, float2 *src, float2 *dst, int L, const DctStage &st, int nvec,
+                              FastDiv fnvec, int es, int vs, bool vfast, const float2 *tw,
+                              cg::cluster_group &cl)
+{
+    switch (st.R) {
+    case 16: fft_push<16, INV>(XS, src, dst, L, st, nvec, fnvec, es, vs, vfast, tw, cl); break;
+    case 15: fft_push<15, INV>(XS, src, dst, L, st, nvec, fnvec, es, vs, vfast, tw, cl); break;
+    case 12: fft_push<12, INV>(XS, src, dst, L, st, nvec, fnvec, es, vs, vfast, tw, cl); break;
+    case 10: fft_push<10, INV>(XS, src, dst, L, st, nvec, fnvec, es, vs, vfast, tw, cl); break;
+    case 9: fft_push<9, INV>(XS, src, dst, L, st, nvec, fnvec, es, vs, vfast, tw, cl); break;
+    case 8: fft_push<8, INV>(XS, src, dst, L, st, nvec, fnvec, es, vs, vfast, tw, cl); break;
+    case 6: fft_push<6, INV>(XS, src, dst, L, st, nvec, fnvec, es, vs, vfast, tw, cl); break;
+    case 5: fft_push<5, INV>(XS, src, dst, L, st, nvec, fnvec, es, vs, vfast, tw, cl); break;
+    case 4: fft_push<4, INV>(XS, src, dst, L, st, nvec, fnvec, es, vs, vfast, tw, cl); break;
+    case 3: fft_push<3, INV>(XS, src, dst, L, st, nvec, fnvec, es, vs, vfast, tw, cl); break;
+    default: fft_push<2, INV>(XS, src, dst, L, st, nvec, fnvec, es, vs, vfast, tw, cl); break;
+    }
 }
 
 // Forward DCT: time layout in cur -> packed spectrum in cur (the two
@@ -522,8 +558,8 @@ __device__ __noinline__ bool dct_forward(const Ctx &XS, float2 *cur, float2 *oth
     float2 *const c0 = cur;
     const Geo X = XS;
     const float2 *tw1 = X.tw1, *tw2 = X.tw2;
-    fft_seq<false>(cur, oth, X.m1, XS.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, tw1);
-    transpose<false>(XS, cur, oth, cl);
+    fft_seq<false>(cur, oth, X.m1, XS.s1, X.nr1 - 1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, tw1);
+    fft_push_last<false>(XS, cur, oth, X.m1, XS.s1[X.nr1 - 1], X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, tw1, cl);
     { float2 *t = cur; cur = oth; oth = t; }
     fft_seq<false>(cur, oth, X.m2, XS.s2, X.nr2, 2 * X.npl, X.f_2npl, 1, X.m2p, true, tw2);
     split_pass<false>(XS, cur);
@@ -538,8 +574,8 @@ __device__ __noinline__ bool dct_inverse(const Ctx &XS, float2 *cur, float2 *oth
     const Geo X = XS;
     const float2 *tw1 = X.tw1, *tw2 = X.tw2;
     split_pass<true>(XS, cur);
-    fft_seq<true>(cur, oth, X.m2, XS.s2, X.nr2, 2 * X.npl, X.f_2npl, 1, X.m2p, true, tw2);
-    transpose<true>(XS, cur, oth, cl);
+    fft_seq<true>(cur, oth, X.m2, XS.s2, X.nr2 - 1, 2 * X.npl, X.f_2npl, 1, X.m2p, true, tw2);
+    fft_push_last<true>(XS, cur, oth, X.m2, XS.s2[X.nr2 - 1], 2 * X.npl, X.f_2npl, 1, X.m2p, false, tw2, cl);
     { float2 *t = cur; cur = oth; oth = t; }
     fft_seq<true>(cur, oth, X.m1, XS.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, tw1);
     return cur != c0;     // the result is in the caller's other buffer
@@ -551,8 +587,9 @@ __device__ __noinline__ bool dct_forward_pre(const Ctx &XS, float2 *cur, float2 
 {
     float2 *const c0 = cur;
     const Geo X = XS;
-    fft_seq<false>(cur, oth, X.m1, XS.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, X.tw1);
-    transpose<false>(XS, cur, oth, cl);
+    fft_seq<false>(cur, oth, X.m1, XS.s1, X.nr1 - 1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, X.tw1);
+    fft_push_last<false>(XS, cur, oth, X.m1, XS.s1[X.nr1 - 1], X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, X.tw1,
+                         cl);
     { float2 *t = cur; cur = oth; oth = t; }
     fft_seq<false>(cur, oth, X.m2, XS.s2, X.nr2, 2 * X.npl, X.f_2npl, 1, X.m2p, true, X.tw2);
     return cur != c0;     // the result is in the caller's other buffer
@@ -561,8 +598,8 @@ __device__ __noinline__ bool dct_inverse_post(const Ctx &XS, float2 *cur, float2
 {
     float2 *const c0 = cur;
     const Geo X = XS;
-    fft_seq<true>(cur, oth, X.m2, XS.s2, X.nr2, 2 * X.npl, X.f_2npl, 1, X.m2p, true, X.tw2);
-    transpose<true>(XS, cur, oth, cl);
+    fft_seq<true>(cur, oth, X.m2, XS.s2, X.nr2 - 1, 2 * X.npl, X.f_2npl, 1, X.m2p, true, X.tw2);
+    fft_push_last<true>(XS, cur, oth, X.m2, XS.s2[X.nr2 - 1], 2 * X.npl, X.f_2npl, 1, X.m2p, false, X.tw2, cl);
     { float2 *t = cur; cur = oth; oth = t; }
     fft_seq<true>(cur, oth, X.m1, XS.s1, X.nr1, X.ncolmax, X.f_ncolmax, X.ncolmax, 1, true, X.tw1);
     return cur != c0;     // the result is in the caller's other buffer
