@@ -642,8 +642,9 @@ __device__ __forceinline__ Acc2 acc_merge2(const Acc2 &a, const Acc2 &b) {
     r.c = __fadd_rn(r.c, b.c);
     return r;
 }
-__device__ __forceinline__ double2 cluster_sum_acc(Acc2 x, Acc2 y, double2 *s_red, double2 *s_part, int &parity,
-                                   cg::cluster_group &cl)
+// First half: this CTA's partial sums into its slot s_part[parity] (all
+// threads take part).  A cluster barrier must follow before the second.
+__device__ __forceinline__ void cluster_sum_publish(Acc2 x, Acc2 y, double2 *s_red, double2 *s_part, int parity)
 {
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
@@ -663,7 +664,13 @@ __device__ __forceinline__ double2 cluster_sum_acc(Acc2 x, Acc2 y, double2 *s_re
         for (int w = 0; w < DCT_T / 32; ++w) { t.x += s_red[w].x; t.y += s_red[w].y; }
         s_part[parity] = t;
     }
-    cl.sync();
+}
+// Second half, after the barrier: every CTA's slot added in rank order,
+// broadcast to the CTA; flips parity (consecutive sums use alternate slots,
+// so a slot is never rewritten while a sibling may still read it).
+__device__ __forceinline__ double2 cluster_sum_collect(double2 *s_red, double2 *s_part, int &parity,
+                                                       cg::cluster_group &cl)
+{
     if (threadIdx.x == 0) {
         double2 tot = make_double2(0.0, 0.0);
         for (int r = 0; r < static_cast<int>(cl.num_blocks()); ++r) {
@@ -677,6 +684,13 @@ __device__ __forceinline__ double2 cluster_sum_acc(Acc2 x, Acc2 y, double2 *s_re
     const double2 tot = s_red[DCT_T / 32];
     parity ^= 1;
     return tot;
+}
+__device__ __forceinline__ double2 cluster_sum_acc(Acc2 x, Acc2 y, double2 *s_red, double2 *s_part, int &parity,
+                                                   cg::cluster_group &cl)
+{
+    cluster_sum_publish(x, y, s_red, s_part, parity);
+    cl.sync();
+    return cluster_sum_collect(s_red, s_part, parity, cl);
 }
 
 // Per-detscan scalars: FP64 arithmetic (1/64 of the FP32 rate on this
@@ -1078,14 +1092,22 @@ __device__ __forceinline__ float *cg_elem(cg::cluster_group &cl, float2 *U, cons
 // block applies T_L^{-1} = (L(x) L(x)^T - L(w) L(w)^T) / x_0 (Gohberg-
 // Semencul; x = T_L^{-1} e_1 from the Durbin tables, w = (0, x_{L-1}, ..,
 // x_1)) to its slice of r, gathered from and scattered to the CTAs that
-// hold those ranks.  gb points at five GB_CAP float arrays.
+// hold those ranks.  gb points at five GB_CAP float arrays.  The CG sums
+// that need z ride on the closing cluster barrier: this CTA publishes
+// (rr_part, sum of r z over its own blocks) as its slot of a cluster sum,
+// which the caller collects.  With clear non-null, clear[0, nclear) is
+// zeroed once the opening barrier has ended every earlier remote read.
 __device__ __noinline__ void apply_gap_precond(const OwnBlocks &ob, float *c_r, float *c_z, float *gb,
                                                const float *__restrict__ xt_det, int kper,
-                                               cg::cluster_group &cl)
+                                               cg::cluster_group &cl, Acc2 rr_part, double2 *s_red,
+                                               double2 *s_part, int parity, float2 *clear, int nclear)
 {
     float *gb_r = gb, *gb_x = gb + GB_CAP, *gb_w = gb + 2 * GB_CAP;
     float *gb_u1 = gb + 3 * GB_CAP, *gb_u2 = gb + 4 * GB_CAP;
+    Acc2 rz = {0.f, 0.f};
     cl.sync();     // every CTA's residual is complete before the gathers
+    if (clear)
+        for (int e = threadIdx.x; e < nclear; e += DCT_T) clear[e] = make_float2(0.f, 0.f);
     for (int rd = 0; rd < ob.nrnd; ++rd) {
         const int b0 = ob.rnd[rd], b1 = ob.rnd[rd + 1];
         const int Ll = ob.len[b1 - 1];
@@ -1196,12 +1218,17 @@ __device__ __noinline__ void apply_gap_precond(const OwnBlocks &ob, float *c_r, 
                 const float zz[4] = {z1.x - z2.x, z1.y - z2.y, z1.z - z2.z, z1.w - z2.w};
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    if (i0 + j < L) *rank_elem(cl, c_z, kper, ob.rank[b] + i0 + j) = zz[j] * inv;
+                    if (i0 + j < L) {
+                        const float zj = zz[j] * inv;
+                        *rank_elem(cl, c_z, kper, ob.rank[b] + i0 + j) = zj;
+                        acc_add_prod(rz, gb_r[base + i0 + j], zj);
+                    }
             }
         }
         __syncthreads();     // the gb arrays are reused by the next round
     }
-    cl.sync();     // every scatter into every CTA's c_z is done
+    cluster_sum_publish(rr_part, rz, s_red, s_part, parity);
+    cl.sync();     // every scatter into every CTA's c_z is done, and every slot is published
 }
 
 struct NcorrArgs {
@@ -1394,12 +1421,12 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             // split gaps into blocks of at most lmax samples; block b goes to
             // CTA b mod C with the rank of its first sample
             const int lmax = max(1, min(TOEP_LMAX, a.lvalid[det]));
-            int nb = 0, ovf = 0, rank = 0, rlen = 0, rq = 0, cb = 0;
+            int nb = 0, rank = 0, rlen = 0, rq = 0, cb = 0;
             for (int g2 = 0; g2 < ngap; ++g2) {
                 for (int b0 = g_beg[g2]; b0 < g_end[g2]; b0 += lmax) {
                     const int len = min(lmax, g_end[g2] - b0);
                     if (cb == c) {
-                        if (s_nown < GAP_CAP) {
+                        if (s_nown < GAP_CAP) {     // else the whole cluster goes without (below)
                             // own blocks are applied in rounds of at most GB_CAP
                             // floats: 8 zeros, the block padded to a multiple of 4, 8 zeros
                             const int reg = ((len + 3) & ~3) + 16;
@@ -1408,8 +1435,6 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                             ++s_nown;
                             rlen += reg;
                             rq += (len + 3) >> 2;
-                        } else {
-                            ovf = 1;
                         }
                     }
                     rank += len;
@@ -1418,13 +1443,14 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                 }
             }
             ob.rnd[ob.nrnd] = s_nown;
-            s_ovf = ovf;
+            // every CTA counts the same nb blocks, and CTA 0 holds the most
+            // (ceil(nb / C)): the same decision in the whole cluster, with
+            // no exchange
+            s_ovf = (nb + C - 1) / C > GAP_CAP;
         }
         if (!prec && threadIdx.x == 0) s_ovf = 1;
         __syncthreads();
-        const double ovf_all = cluster_sum_acc(Acc2{threadIdx.x == 0 && s_ovf ? 1.0f : 0.0f, 0.0f},
-                                               Acc2{0.f, 0.f}, s_red, s_part, parity, cl).x;
-        const bool use_prec = ovf_all < 0.5;
+        const bool use_prec = s_ovf == 0;
         int it = 0;
         bool conv = true;
         if (kc_all > 0 && cap_ovf) {
@@ -1433,14 +1459,27 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
         } else if (kc_all > 0) {
             const float *xt_det = a.xtab ? a.xtab + static_cast<int64_t>(det) * (TOEP_LMAX * (TOEP_LMAX + 1) / 2)
                                          : nullptr;
-            // z = M^{-1} r: Gohberg-Semencul per own block, scattered to owners
-            auto precond = [&]() {
+            // z = M^{-1} r (Gohberg-Semencul per own block, scattered to
+            // owners) and the cluster sums (rr_part summed, r.z): returns
+            // (sum rr_part, sum r z) with z complete in every CTA
+            // With clear non-null, the transform buffer is zeroed after every
+            // earlier remote read of it and before the closing barrier.
+            const int tot = X.m1 * X.ncolmax;
+            auto precond = [&](Acc2 rr_part, float2 *clear) -> double2 {
                 if (!use_prec) {
-                    for (int i = threadIdx.x; i < kc; i += DCT_T) c_z[i] = c_r[i];
-                    __syncthreads();
-                    return;
+                    Acc2 rz_loc = {0.f, 0.f};
+                    for (int i = threadIdx.x; i < kc; i += DCT_T) {
+                        c_z[i] = c_r[i];
+                        acc_add_prod(rz_loc, c_r[i], c_r[i]);
+                    }
+                    if (clear) {
+                        cl.sync();
+                        for (int e = threadIdx.x; e < tot; e += DCT_T) clear[e] = make_float2(0.f, 0.f);
+                    }
+                    return cluster_sum_acc(rr_part, rz_loc, s_red, s_part, parity, cl);
                 }
-                apply_gap_precond(ob, c_r, c_z, gb_r, xt_det, kper, cl);
+                apply_gap_precond(ob, c_r, c_z, gb_r, xt_det, kper, cl, rr_part, s_red, s_part, parity, clear, tot);
+                return cluster_sum_collect(s_red, s_part, parity, cl);
             };
             // rhs = E^T x0 ; y = 0 ; r = rhs ; z = M^{-1} r ; p = z
             cl.sync();         // x0 is complete in every CTA before the gathers
@@ -1451,19 +1490,9 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                 acc_add_prod(rr_loc, v, v);
             }
             __syncthreads();
-            precond();
-            if (!use_prec) cl.sync();     // (the preconditioner ends with one)
-            // every remote read of x0 ended before the preconditioner's closing
-            // cluster barrier: clear the buffer for the first scatter (the
-            // barrier of the sums below orders this before any scatter)
-            const int tot = X.m1 * X.ncolmax;
-            for (int e = threadIdx.x; e < tot; e += DCT_T) cur[e] = make_float2(0.f, 0.f);
-            Acc2 rz_loc = {0.f, 0.f};
-            for (int i = threadIdx.x; i < kc; i += DCT_T) {
-                c_p[i] = c_z[i];
-                acc_add_prod(rz_loc, c_r[i], c_z[i]);
-            }
-            const double2 rr2 = cluster_sum_acc(rr_loc, rz_loc, s_red, s_part, parity, cl);
+            // z = M^{-1} r, (r.r, r.z); x0's buffer is cleared for the first scatter
+            const double2 rr2 = precond(rr_loc, cur);
+            for (int i = threadIdx.x; i < kc; i += DCT_T) c_p[i] = c_z[i];
             double rz = rr2.y;
             const double stop = static_cast<double>(a.tol) * a.tol * rr2.x;
             conv = rr2.x == 0.0;
@@ -1495,15 +1524,11 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                     c_y[i] = fmaf(alp, c_p[i], c_y[i]);
                     c_r[i] = fmaf(-alp, c_q[i], c_r[i]);
                 }
+                Acc2 rn_loc = {0.f, 0.f};
+                for (int i = threadIdx.x; i < kc; i += DCT_T) acc_add_prod(rn_loc, c_r[i], c_r[i]);
                 __syncthreads();
                 ++it;
-                precond();
-                Acc2 rn_loc = {0.f, 0.f}, rzn_loc = {0.f, 0.f};
-                for (int i = threadIdx.x; i < kc; i += DCT_T) {
-                    acc_add_prod(rn_loc, c_r[i], c_r[i]);
-                    acc_add_prod(rzn_loc, c_r[i], c_z[i]);
-                }
-                const double2 rn2 = cluster_sum_acc(rn_loc, rzn_loc, s_red, s_part, parity, cl);
+                const double2 rn2 = precond(rn_loc, nullptr);     // (r.r, r.z)
                 if (rn2.x <= stop) { conv = true; break; }
                 const float beta = static_cast<float>(rn2.y) / static_cast<float>(rz);
                 for (int i = threadIdx.x; i < kc; i += DCT_T) c_p[i] = fmaf(beta, c_p[i], c_z[i]);
