@@ -11,6 +11,7 @@ ranks is reported.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -96,6 +97,24 @@ def _peaks():
         return d, "measured"
     except (OSError, ValueError):
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# DRAM bytes of one n_corr call per TOD sample, from the ncu capture of
+# k_ncorr summarised in profiles/k_ncorr_lfi30_400detscans.md (400 detscans
+# of the 30 GHz band; scaled to a full launch by samples, since the kernel
+# moves each sample's d, s and n_corr once), valid only while the kernel's
+# sources hash to the digest taken with it.
+NCORR_TRAFFIC = {"bytes_per_sample": 12.94,
+                 "sources": ["csrc/k_dct.cu", "csrc/common.cuh", "csrc/internal.cuh", "csrc/api.cu"],
+                 "sha256": "3b979cb6b26802b27b8ff9c138577e1a8654c3ea9b0cbc999870451ce66030be"}
+
+
+def ncorr_sources_digest() -> str:
+    h = hashlib.sha256()
+    for rel in NCORR_TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, "paper_2201_03509_gb300", rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def make_workload(nscan: int | None):
@@ -287,8 +306,11 @@ def run_ours(args):
             flops = float(np.sum(per * (2 + np.where(iters > 0, 2 * (iters + 1), 0))))
         peak_tf = 152 * 128 * 2 * (peaks.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
         ach = flops / (stage_ms[dom] / 1e3) / 1e12
+        traffic = None
+        if dom == "ncorr" and ncorr_sources_digest() == NCORR_TRAFFIC["sha256"]:
+            traffic = NCORR_TRAFFIC["bytes_per_sample"] * N
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": ach / peak_tf, "traffic": None,
+                "frac": ach / peak_tf, "traffic": traffic, "traffic_unit": "bytes per launch",
                 "peak_source": "FP32 FMA issue: 152 SMs x 128 lanes x 2 flop x sm_max_mhz"}
     else:
         ach = byts.get(dom, 0.0) / (stage_ms[dom] / 1e3) / 1e9
@@ -411,7 +433,7 @@ def main():
     ap.add_argument("--seed", type=int, default=2022)
     ap.add_argument("--cg-tol", type=float, default=1e-6)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
-    ap.add_argument("--cpu-detscans", type=int, default=8)
+    ap.add_argument("--cpu-detscans", type=int, default=24)
     ap.add_argument("--ref-detscans-per-step", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the per-scan comparison step")
