@@ -741,17 +741,28 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
                 }
                 if (bad) continue;
                 std::sort(key.begin(), key.end());
-                for (int64_t i = 0; i < n; ++i) {
-                    // pixel-sorted position -> time index within the detscan
-                    srt[o + i] = static_cast<uint32_t>(key[i] & 0xFFFFFFFFu);
-                    const int32_t px = static_cast<int32_t>(key[i] >> 32);
-                    if (i == 0 || px != static_cast<int32_t>(key[i - 1] >> 32)) {
-                        rpix[q].push_back(px);
-                        rstart[q].push_back(o + i);
-                        rlen[q].push_back(1);
-                    } else {
-                        rlen[q].back()++;
-                    }
+                // runs (one per pixel, samples in time order), then ordered by
+                // their first sample: neighbouring runs are neighbours on the
+                // scan ring, so a tile's samples lie in a few stretches of
+                // consecutive time per revolution
+                std::vector<int64_t> rb;            // run starts in key
+                for (int64_t i = 0; i < n; ++i)
+                    if (i == 0 || (key[i] >> 32) != (key[i - 1] >> 32)) rb.push_back(i);
+                rb.push_back(n);
+                const size_t nrun = rb.size() - 1;
+                std::vector<int32_t> ord(nrun);
+                for (size_t r = 0; r < nrun; ++r) ord[r] = static_cast<int32_t>(r);
+                std::sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) {
+                    return (key[rb[x]] & 0xFFFFFFFFu) < (key[rb[y]] & 0xFFFFFFFFu);
+                });
+                int64_t pos = o;
+                for (size_t k = 0; k < nrun; ++k) {
+                    const int32_t r = ord[k];
+                    rpix[q].push_back(static_cast<int32_t>(key[rb[r]] >> 32));
+                    rstart[q].push_back(pos);
+                    rlen[q].push_back(static_cast<int32_t>(rb[r + 1] - rb[r]));
+                    for (int64_t i = rb[r]; i < rb[r + 1]; ++i)   // run-major position -> time index
+                        srt[pos++] = static_cast<uint32_t>(key[i] & 0xFFFFFFFFu);
                 }
             }
         });
@@ -790,7 +801,38 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
         }
         tr0.push_back(static_cast<int32_t>(p->npairs));
         p->nbin_tiles = static_cast<int32_t>(tq.size());
-        if ((e = dev_upload(*p, p->srt, srt.data(), srt.size()))) return fail(e);
+        // load order of each tile: the k-th sample of every run of the tile,
+        // k = 0, 1, ... (consecutive runs' k-th samples are close in time, so
+        // a warp's loads share sectors); ld_pos is the sample's run-major
+        // position in the tile, where the sums read it
+        std::vector<uint32_t> ld_t(p->N);
+        std::vector<uint16_t> ld_pos(p->N, 0);
+        parallel_for(p->nbin_tiles, [&](int64_t a, int64_t b) {
+            for (int64_t tl = a; tl < b; ++tl) {
+                const int64_t r0 = tr0[tl], r1 = tr0[tl + 1];
+                const int64_t s0 = pstart[r0];
+                int32_t lmax = 0;
+                for (int64_t r = r0; r < r1; ++r) lmax = std::max(lmax, plen[r]);
+                if (r1 - r0 == 1) {          // one run (possibly longer than a tile): its own order
+                    for (int32_t k = 0; k < plen[r0]; ++k) {
+                        ld_t[s0 + k] = srt[s0 + k];
+                        ld_pos[s0 + k] = static_cast<uint16_t>(std::min<int32_t>(k, 0xFFFF));
+                    }
+                    continue;
+                }
+                int64_t i = s0;
+                for (int32_t k = 0; k < lmax; ++k)
+                    for (int64_t r = r0; r < r1; ++r)
+                        if (k < plen[r]) {
+                            const int64_t pos = pstart[r] + k;
+                            ld_t[i] = srt[pos];
+                            ld_pos[i] = static_cast<uint16_t>(pos - s0);
+                            ++i;
+                        }
+            }
+        });
+        if ((e = dev_upload(*p, p->ld_t, ld_t.data(), ld_t.size()))) return fail(e);
+        if ((e = dev_upload(*p, p->ld_pos, ld_pos.data(), ld_pos.size()))) return fail(e);
         if ((e = dev_upload(*p, p->bin_tile_q, tq.data(), tq.size()))) return fail(e);
         if ((e = dev_upload(*p, p->bin_tile_r0, tr0.data(), tr0.size()))) return fail(e);
         if ((e = dev_upload(*p, p->pair_off, pair_off.data(), pair_off.size()))) return fail(e);

@@ -99,14 +99,18 @@ struct Plan {
     int32_t nbin_tiles = 0;          // binning tiles (whole runs of one detscan)
     size_t smem_gain = 0, smem_ncorr = 0;
     // binning
-    uint32_t *srt = nullptr;         // [N] pixel-sorted order of each detscan: time index within the detscan
+    // Runs: the samples of one (detscan, pixel), in time order; a detscan's
+    // runs ordered by their first sample, stored run-major.  A tile's samples
+    // are loaded k-major (the k-th sample of each of its runs, k = 0, 1, ..):
+    uint32_t *ld_t = nullptr;        // [N] time index within the detscan, in load order
+    uint16_t *ld_pos = nullptr;      // [N] run-major position within the tile, in load order
     int32_t *bin_tile_q = nullptr;   // [nbin_tiles] detscan of the tile
     int32_t *bin_tile_r0 = nullptr;  // [nbin_tiles + 1] first run (global run index); last entry = npairs
     int64_t npairs = 0;
     int64_t *pair_off = nullptr;     // [nq+1] runs of each detscan
-    int64_t *pair_start = nullptr;   // [npairs] first srt index (global) of the run
+    int64_t *pair_start = nullptr;   // [npairs] run-major position (global) of the run's first sample
     int32_t *pair_len = nullptr;     // [npairs]
-    int32_t *pair_slot = nullptr;    // [npairs] position in pixel-sorted run order
+    int32_t *pair_slot = nullptr;    // [npairs] the run's slot among its pixel's runs (detscan order)
     int64_t *pix_slot_off = nullptr; // [npix+1]
     double *rec = nullptr;           // [npairs][10] per-run partial sums (scratch)
     int64_t device_bytes = 0;

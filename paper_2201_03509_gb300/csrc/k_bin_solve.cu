@@ -34,7 +34,8 @@ struct BinArgs {
     const uint32_t *flags;
     const double *psd;
     const int64_t *off;
-    const uint32_t *srt;          // sorted position -> time index within the detscan
+    const uint32_t *ld_t;         // load order -> time index within the detscan
+    const uint16_t *ld_pos;       // load order -> run-major position within the tile
     const int64_t *pair_start;
     const int32_t *pair_len, *pair_slot;
     const int32_t *tile_q, *tile_r0;
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(BIN_T) k_bin(BinArgs a)
         RunSums r;
         sums_zero(r);
         for (int i = threadIdx.x; i < cnt; i += BIN_T) {
-            const int64_t tg = o + __ldg(a.srt + s0 + i);
+            const int64_t tg = o + __ldg(a.ld_t + s0 + i);     // a single run: run order
             const uint16_t pf = psi_flag(a, tg);
             if (pf >> 15) continue;
             sums_add(r, __ldg(a.trig + (pf & 0x0FFF)), __ldg(a.d + tg), __ldg(a.x + tg));
@@ -156,24 +157,31 @@ __global__ void __launch_bounds__(BIN_T) k_bin(BinArgs a)
         return;
     }
 
-    // gather in sorted order: the tile's sorted positions first, then every
-    // value load of the thread in flight together; cos 2psi and sin 2psi are
-    // staged with the data, and a flagged sample is marked by cos = 2
+    // gather in the tile's load order (the k-th sample of each run, k = 0,
+    // 1, ..: a warp's 32 samples are close in time, so they share sectors):
+    // the positions first, then every value load of the thread in flight
+    // together, each value into its run-major slot; cos 2psi and sin 2psi
+    // are staged with the data, and a flagged sample is marked by cos = 2
     constexpr int PER = BIN_TILE / BIN_T;
-    int idx[PER];
+    int idx[PER], pos[PER];
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int i = threadIdx.x + u * BIN_T;
-        idx[u] = i < cnt ? static_cast<int>(__ldg(a.srt + s0 + i)) : -1;
+        idx[u] = -1;
+        pos[u] = 0;
+        if (i < cnt) {
+            idx[u] = static_cast<int>(__ldg(a.ld_t + s0 + i));
+            pos[u] = __ldg(a.ld_pos + s0 + i);
+        }
     }
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
-        const int i = threadIdx.x + u * BIN_T;
         if (idx[u] < 0) continue;
         const int64_t tg = o + idx[u];
         const uint16_t pf = psi_flag(a, tg);
         float2 cs = __ldg(a.trig + (pf & 0x0FFF));
         if (pf >> 15) cs.x = 2.0f;
+        const int i = pos[u];
         s_cs[i] = cs;
         s_d[i] = __ldg(a.d + tg);
         s_x[i] = __ldg(a.x + tg);
@@ -285,7 +293,7 @@ cudaError_t launch_bin(const Plan &p, const uint16_t *psi, const float *d, const
     if (p.nq == 0) return cudaSuccess;
     BinArgs a;
     a.psi = psi; a.d = d; a.x = ncorr; a.gain = gain; a.flags = flags; a.psd = psd; a.off = p.off;
-    a.srt = p.srt; a.pair_start = p.pair_start; a.pair_len = p.pair_len; a.pair_slot = p.pair_slot;
+    a.ld_t = p.ld_t; a.ld_pos = p.ld_pos; a.pair_start = p.pair_start; a.pair_len = p.pair_len; a.pair_slot = p.pair_slot;
     a.tile_q = p.bin_tile_q; a.tile_r0 = p.bin_tile_r0; a.trig = p.trig; a.ndet = p.ndet; a.rec = p.rec;
     if (p.nbin_tiles > 0) k_bin<<<p.nbin_tiles, BIN_T, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
