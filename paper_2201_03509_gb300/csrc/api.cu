@@ -710,6 +710,8 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
             return fail(e);
         if ((e = dev_upload(*p, p->lvalid, static_cast<int32_t *>(nullptr), static_cast<size_t>(p->ndet))))
             return fail(e);
+        if ((e = dev_upload(*p, p->gain_ab, static_cast<double2 *>(nullptr), static_cast<size_t>(p->nq))))
+            return fail(e);
         // filter-weight scratch: one slot per CTA of every resident cluster
         p->wscratch_per_cluster = static_cast<int64_t>(p->C) * p->sz;
         if ((e = dev_upload(*p, p->wscratch, static_cast<float4 *>(nullptr),

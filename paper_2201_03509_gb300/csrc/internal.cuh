@@ -97,6 +97,7 @@ struct Plan {
     int64_t wscratch_per_cluster = 0;
     int32_t schedule = TOD_SCHED_PERSISTENT;
     int32_t nbin_tiles = 0;          // binning tiles (whole runs of one detscan)
+    double2 *gain_ab = nullptr;      // [nq] (a, b) of each detscan's gain conditional (scratch)
     size_t smem_gain = 0, smem_ncorr = 0;
     // binning
     // Runs: the samples of one (detscan, pixel), in time order; a detscan's

@@ -744,10 +744,15 @@ __device__ __forceinline__ Smem carve(void *raw, int sz, int twsz)
 }
 
 // Stage plan pi in shared memory: scalars and stage tables into sX, the
-// length's twiddle block into sm.twb (all threads copy).
-__device__ __forceinline__ void load_plan(Ctx *sX, const DctPlan *plans, int pi, const float2 *tw, Smem &sm, int c, int C)
+// length's twiddle block into sm.twb (all threads copy).  Nothing writes
+// either during a detscan, so when the previous detscan of this CTA had the
+// same plan (the work list is sorted by length) they are kept.
+__device__ __forceinline__ void load_plan(Ctx *sX, const DctPlan *plans, int pi, const float2 *tw, Smem &sm, int c,
+                                          int C, int &cur_pi)
 {
     __syncthreads();      // previous users of sX and the twiddle block are done
+    if (pi == cur_pi) return;
+    cur_pi = pi;
     const DctPlan &P = plans[pi];
     const int t = threadIdx.x;
     if (t >= 32 && t < 32 + DCT_MAXR) sX->s1[t - 32] = P.s1[t - 32];
@@ -824,8 +829,7 @@ struct GainArgs {
     double fsamp;
     tod_rng rng;
     int mode;
-    double *g_out, *mu_out, *sig_out;
-    int32_t *status;
+    double2 *ab_out;              // (a, b) of each detscan's conditional
     int sz, m1max, m2max, twsz;
 };
 
@@ -841,11 +845,12 @@ __global__ void __launch_bounds__(DCT_T, 1) k_gain(GainArgs a)
     const int cid = blockIdx.x / C, ncl = gridDim.x / C;
     Smem sm = carve(smem_raw, a.sz, a.twsz);
     int parity = 0;
+    int cur_pi = -1;      // plan staged in shared memory
     for (int w = cid; w < a.work_count; w += ncl) {
         const int q = a.work[a.work_begin + w];
         const int det = q % a.ndet;
         const int64_t o = a.off[q];
-        load_plan(&sX, a.plans, a.q_plan[q], a.tw, sm, c, C);
+        load_plan(&sX, a.plans, a.q_plan[q], a.tw, sm, c, C, cur_pi);
         const Ctx &X = sX;     // shared-memory copy (a register copy would live on the stack)
         const int n = X.n, m = X.m;
         const float *sq = a.s + o, *dq = a.d + o;
@@ -904,31 +909,43 @@ __global__ void __launch_bounds__(DCT_T, 1) k_gain(GainArgs a)
         }
         const double2 ab = cluster_sum_acc(sa, sb, s_red, s_part,
                                         parity, cl);
-        if (c == 0 && threadIdx.x == 0) {
-            const double A = ab.x, B = ab.y;
-            if (!(A > 0.0)) {
-                set_status(a.status, q, TOD_ERR_ARG);
-                a.g_out[q] = 0.0;
-                if (a.mu_out) a.mu_out[q] = 0.0;
-                if (a.sig_out) a.sig_out[q] = 0.0;
-            } else {
-                const double mu = B / A, sg = 1.0 / sqrt(A);
-                double z = 0.0;
-                if (a.mode == TOD_MODE_DRAW) {
-                    const uint64_t it = a.rng.gibbs_iter_dev ? *a.rng.gibbs_iter_dev : a.rng.gibbs_iter;
-                    const u64x4 wv = philox4x64(0, static_cast<uint64_t>(q), 0, it,
-                                                a.rng.seed, a.rng.band);
-                    const double u1 = (static_cast<double>(wv.x[0] >> 11) + 0.5) * 1.1102230246251565e-16;
-                    const double u2 = (static_cast<double>(wv.x[1] >> 11) + 0.5) * 1.1102230246251565e-16;
-                    z = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
-                }
-                a.g_out[q] = mu + z * sg;
-                if (a.mu_out) a.mu_out[q] = mu;
-                if (a.sig_out) a.sig_out[q] = sg;
-            }
-        }
+        // the FP64 draw (1/64 FP32 rate: long for one thread) runs afterwards
+        // in k_gain_draw, off this cluster's critical path
+        if (c == 0 && threadIdx.x == 0) a.ab_out[q] = ab;
     }
     cl.sync();     // no CTA leaves while a sibling may still read its cluster-sum slot
+}
+
+// The gain draws of the detscans k_gain just summed: g ~ N(b/a, 1/a)
+// (mean and rms also written when asked for); a <= 0 (no usable samples)
+// gives g = 0 and TOD_ERR_ARG for the detscan.  One thread per detscan.
+__global__ void __launch_bounds__(256) k_gain_draw(const double2 *__restrict__ ab, const int32_t *__restrict__ work,
+                                                   int work_begin, int work_count, tod_rng rng, int mode,
+                                                   double *g_out, double *mu_out, double *sig_out, int32_t *status)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= work_count) return;
+    const int q = work[work_begin + w];
+    const double A = ab[q].x, B = ab[q].y;
+    if (!(A > 0.0)) {
+        set_status(status, q, TOD_ERR_ARG);
+        g_out[q] = 0.0;
+        if (mu_out) mu_out[q] = 0.0;
+        if (sig_out) sig_out[q] = 0.0;
+        return;
+    }
+    const double mu = B / A, sg = 1.0 / sqrt(A);
+    double z = 0.0;
+    if (mode == TOD_MODE_DRAW) {
+        const uint64_t it = rng.gibbs_iter_dev ? *rng.gibbs_iter_dev : rng.gibbs_iter;
+        const u64x4 wv = philox4x64(0, static_cast<uint64_t>(q), 0, it, rng.seed, rng.band);
+        const double u1 = (static_cast<double>(wv.x[0] >> 11) + 0.5) * 1.1102230246251565e-16;
+        const double u2 = (static_cast<double>(wv.x[1] >> 11) + 0.5) * 1.1102230246251565e-16;
+        z = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+    }
+    g_out[q] = mu + z * sg;
+    if (mu_out) mu_out[q] = mu;
+    if (sig_out) sig_out[q] = sg;
 }
 
 // ---------------------------------------------------------------------------
@@ -1281,11 +1298,12 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
     float *c_z = c_q + CG_KCAP;
     float *gb_r = c_z + CG_KCAP;        // five GB_CAP arrays of the preconditioner
     int parity = 0;
+    int cur_pi = -1;      // plan staged in shared memory
     for (int w = cid; w < a.work_count; w += ncl) {
         const int q = a.work[a.work_begin + w];
         const int det = q % a.ndet;
         const int64_t o = a.off[q];
-        load_plan(&sX, a.plans, a.q_plan[q], a.tw, sm, c, C);
+        load_plan(&sX, a.plans, a.q_plan[q], a.tw, sm, c, C, cur_pi);
         if (threadIdx.x == 0) { s_nown = 0; ob.nrnd = 0; }
         const Ctx &X = sX;     // read from shared memory: registers are scarce here
         const int n = X.n, m = X.m;
@@ -1600,11 +1618,12 @@ __global__ void __launch_bounds__(DCT_T, 1) k_chi2(Chi2Args a)
     const int cid = blockIdx.x / C, ncl = gridDim.x / C;
     Smem sm = carve(smem_raw, a.sz, a.twsz);
     int parity = 0;
+    int cur_pi = -1;      // plan staged in shared memory
     for (int w = cid; w < a.work_count; w += ncl) {
         const int q = a.work[w];
         const int det = q % a.ndet;
         const int64_t o = a.off[q];
-        load_plan(&sX, a.plans, a.q_plan[q], a.tw, sm, c, C);
+        load_plan(&sX, a.plans, a.q_plan[q], a.tw, sm, c, C, cur_pi);
         const Ctx &X = sX;     // shared-memory copy (a register copy would live on the stack)
         const int n = X.n, m = X.m;
         const float *sq = a.s + o, *dq = a.d + o;
@@ -1799,19 +1818,23 @@ cudaError_t launch_gain(const Plan &p, const float *d, const float *s, const uin
     a.d = d; a.s = s; a.flags = flags; a.psd = psd; a.off = p.off; a.plans = p.plans;
     a.q_plan = p.q_plan; a.tw = p.tw; a.work = p.work; a.work_begin = work_begin;
     a.work_count = work_count; a.ndet = p.ndet; a.fsamp = p.fsamp; a.rng = rng; a.mode = mode;
-    a.g_out = g; a.mu_out = mu; a.sig_out = sig; a.status = p.status; a.sz = p.sz;
+    a.ab_out = p.gain_ab; a.sz = p.sz;
     a.m1max = p.m1max; a.m2max = p.m2max; a.twsz = p.twsz;
+    cudaError_t e = cudaSuccess;
     if (p.schedule == TOD_SCHED_PER_SCAN) {
-        for (int w = 0; w < work_count; ++w) {
+        for (int w = 0; w < work_count && e == cudaSuccess; ++w) {
             a.work_begin = work_begin + w;
             a.work_count = 1;
-            cudaError_t e = launch_cluster(reinterpret_cast<const void *>(k_gain), &a, p.C, 1, p.smem_gain, st);
-            if (e != cudaSuccess) return e;
+            e = launch_cluster(reinterpret_cast<const void *>(k_gain), &a, p.C, 1, p.smem_gain, st);
         }
-        return cudaSuccess;
+    } else {
+        const int ncl = std::min(work_count, p.nclusters_gain);
+        e = launch_cluster(reinterpret_cast<const void *>(k_gain), &a, p.C, ncl, p.smem_gain, st);
     }
-    const int ncl = std::min(work_count, p.nclusters_gain);
-    return launch_cluster(reinterpret_cast<const void *>(k_gain), &a, p.C, ncl, p.smem_gain, st);
+    if (e != cudaSuccess) return e;
+    k_gain_draw<<<(work_count + 255) / 256, 256, 0, st>>>(p.gain_ab, p.work, work_begin, work_count, rng, mode, g,
+                                                          mu, sig, p.status);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_ncorr(const Plan &p, const float *d, const float *s, const double *gain,

@@ -43,8 +43,59 @@ class GibbsTODStep:
             d = torch.from_numpy(np.ascontiguousarray(d, np.float32))
         self.d.copy_(d, non_blocking=True)
 
+    def prefetch_tod(self, d_host, stream=None):
+        """Start copying the next step's detector data (a pinned host float32
+        tensor of N samples) into a second device buffer on a copy stream, so
+        that the copy overlaps the step that is running.  The next run()
+        on `stream` waits for the copy and then uses that buffer; the copy
+        itself waits until the last step that read that buffer is done."""
+        import torch
+        if getattr(self, "_copy_stream", None) is None:
+            self._copy_stream = torch.cuda.Stream(device=self.d.device)
+            self._d_spare = torch.empty_like(self.d)
+            self._spare_free = None
+        cs = self._copy_stream
+        if self._spare_free is None:      # never read by a step: after what is already queued
+            self._spare_free = torch.cuda.Event()
+            self._spare_free.record(self._stream(stream))
+        cs.wait_event(self._spare_free)
+        with torch.cuda.stream(cs):
+            self._d_spare.copy_(d_host, non_blocking=True)
+        self._copied = torch.cuda.Event()
+        self._copied.record(cs)
+
+    def _stream(self, stream):
+        import torch
+        return stream if stream is not None else torch.cuda.current_stream(self.d.device)
+
+    def _take_prefetched(self, stream):
+        import torch
+        if getattr(self, "_copied", None) is None:
+            return
+        st = self._stream(stream)
+        st.wait_event(self._copied)
+        self._copied = None
+        # the buffer that becomes spare was last read by the step that
+        # recorded _d_done (or by none since it was last swapped in)
+        done = getattr(self, "_d_done", None)
+        if done is None:
+            done = torch.cuda.Event()
+            done.record(st)
+        self.d, self._d_spare = self._d_spare, self.d
+        self._spare_free = done
+        self._d_done = None
+
+    def _mark_d_done(self, stream):
+        import torch
+        if getattr(self, "_copy_stream", None) is None:
+            return
+        self._d_done = torch.cuda.Event()
+        self._d_done.record(self._stream(stream))     # self.d is read by nothing queued after this
+
     def run(self, map32_in, rng: Rng, mode: int = MODE_DRAW, stream=None):
-        """Enqueue one step; the new map lands in self.map / self.map32."""
+        """Enqueue one step; the new map lands in self.map / self.map32.
+        Uses the detector data of a pending prefetch_tod() if there is one."""
+        self._take_prefetched(stream)
         p = self.plan
         p.decode(self.pix, self.psi, stream)
         p.project(map32_in, self.pix, self.psi, None, self.s, stream)
@@ -56,8 +107,9 @@ class GibbsTODStep:
               stream)
         p.solve_maps(self.A, self.b, self.hits, self.rcond_min, self.map, self.map32, self.rcond,
                      self.valid, stream)
+        self._mark_d_done(stream)
 
-    LAUNCHES_PER_STEP = 10  # decode x2, project, gain, Toeplitz prep x2, ncorr, bin + reduce, solve
+    LAUNCHES_PER_STEP = 11  # decode x2, project, gain + draw, Toeplitz prep x2, ncorr, bin + reduce, solve
 
     def capture(self, map32_in, seed: int, band: int = 0, mode: int = MODE_DRAW):
         """Capture one step into a CUDA graph.  The Gibbs iteration is read by
