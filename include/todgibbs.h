@@ -221,6 +221,30 @@ tod_status tod_sample_ncorr(tod_plan *p, const float *d, const float *s,
                             float *ncorr_out, int32_t *cg_iters_out,
                             cudaStream_t stream);
 
+/* tod_ncorr_prepare / tod_sample_ncorr_prepared -- tod_sample_ncorr in two
+ * calls, so that the first can run on another stream while earlier stages
+ * of the step run.  The paper has no counterpart (its preconditioning is
+ * not described): a scheduling convenience.  tod_sample_ncorr is exactly
+ * tod_ncorr_prepare followed by tod_sample_ncorr_prepared on one stream.
+ *   tod_ncorr_prepare builds, from psd (double[ndet][3], device), the
+ *   per-detector gap preconditioner tables the plan holds (Toeplitz
+ *   autocovariance of the CG operator at a reference length and its Durbin
+ *   solutions), overwriting the previous ones.
+ *   tod_sample_ncorr_prepared is tod_sample_ncorr (same arguments, results
+ *   and errors) using those tables; psd must be the array they were built
+ *   from.
+ * Ordering is the caller's: the prepared draw must be queued after the
+ * preparation has completed (an event), and a new preparation only after
+ * every draw that reads the old tables has completed.  Two plans do not
+ * share tables. */
+tod_status tod_ncorr_prepare(tod_plan *p, const double *psd, cudaStream_t stream);
+tod_status tod_sample_ncorr_prepared(tod_plan *p, const float *d, const float *s,
+                                     const double *gain, const uint32_t *flags,
+                                     const double *psd, tod_rng rng, int32_t mode,
+                                     double cg_tol, int32_t cg_maxiter,
+                                     float *ncorr_out, int32_t *cg_iters_out,
+                                     cudaStream_t stream);
+
 /* tod_sample_ncorr_static -- tod_sample_ncorr with nothing allocated.
  * The paper has no counterpart: it is a library convenience.  Same
  * arguments, results and errors as tod_sample_ncorr, except that the

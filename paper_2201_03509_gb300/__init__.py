@@ -66,7 +66,8 @@ _lib = None
 SYMBOLS = ["tod_status_string", "tod_fft_length", "tod_huff_encode", "tod_huff_free",
            "tod_plan_create", "tod_plan_destroy", "tod_plan_info", "tod_plan_status",
            "tod_plan_set_schedule", "tod_chi2", "tod_decode", "tod_project", "tod_sample_gain", "tod_sample_ncorr", "tod_bin",
-           "tod_solve_maps", "tod_ncorr_static_setup", "tod_sample_ncorr_static"]
+           "tod_solve_maps", "tod_ncorr_static_setup", "tod_sample_ncorr_static", "tod_ncorr_prepare",
+           "tod_sample_ncorr_prepared"]
 
 
 def build(force: bool = False) -> str:
@@ -104,6 +105,8 @@ def lib():
         L.tod_chi2.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
         L.tod_ncorr_static_setup.argtypes = [_P, _P]
         L.tod_sample_ncorr_static.argtypes = [_P, _P, _P, _P, _P, _P, Rng, _i32, _f64, _i32, _P, _P, _P]
+        L.tod_ncorr_prepare.argtypes = [_P, _P, _P]
+        L.tod_sample_ncorr_prepared.argtypes = [_P, _P, _P, _P, _P, _P, Rng, _i32, _f64, _i32, _P, _P, _P]
         for name in SYMBOLS:
             if name not in ("tod_status_string", "tod_fft_length", "tod_huff_free"):
                 getattr(L, name).restype = _i32
@@ -284,6 +287,18 @@ class Plan:
         _check(lib().tod_sample_ncorr(self._h, _ptr(d), _ptr(s), _ptr(gain), _ptr(flags), _ptr(psd),
                                       rng, mode, float(cg_tol), int(cg_maxiter), _ptr(ncorr_out),
                                       _ptr(cg_iters_out), _stream(stream)), "tod_sample_ncorr")
+
+    def ncorr_prepare(self, psd, stream=None):
+        """First half of sample_ncorr: the per-detector gap preconditioner
+        tables from psd (may run on another stream; see the header)."""
+        _check(lib().tod_ncorr_prepare(self._h, _ptr(psd), _stream(stream)), "tod_ncorr_prepare")
+
+    def sample_ncorr_prepared(self, d, s, gain, flags, psd, rng: Rng, mode, ncorr_out, cg_iters_out=None,
+                              cg_tol: float = 0.0, cg_maxiter: int = 0, stream=None):
+        """Second half of sample_ncorr, with the tables of the last ncorr_prepare."""
+        _check(lib().tod_sample_ncorr_prepared(self._h, _ptr(d), _ptr(s), _ptr(gain), _ptr(flags), _ptr(psd),
+                                               rng, mode, float(cg_tol), int(cg_maxiter), _ptr(ncorr_out),
+                                               _ptr(cg_iters_out), _stream(stream)), "tod_sample_ncorr_prepared")
 
     def ncorr_static_setup(self) -> int:
         """Look up the fixed scratch array of sample_ncorr_static on this

@@ -941,6 +941,30 @@ tod_status tod_sample_ncorr(tod_plan *pl, const float *d, const float *s, const 
                                   cg_iters_out, stream, 0, p->nq));
 }
 
+tod_status tod_ncorr_prepare(tod_plan *pl, const double *psd, cudaStream_t stream)
+{
+    if (!pl || !psd) return TOD_ERR_ARG;
+    Plan *p = reinterpret_cast<Plan *>(pl);
+    DeviceGuard dg(p->device);
+    if (!p->use_prec) return TOD_OK;
+    return to_status(launch_toeplitz_prep(*p, psd, stream));
+}
+
+tod_status tod_sample_ncorr_prepared(tod_plan *pl, const float *d, const float *s, const double *gain,
+                                     const uint32_t *flags, const double *psd, tod_rng rng, int32_t mode,
+                                     double cg_tol, int32_t cg_maxiter, float *ncorr_out,
+                                     int32_t *cg_iters_out, cudaStream_t stream)
+{
+    if (!pl || !d || !s || !gain || !flags || !psd || !ncorr_out) return TOD_ERR_ARG;
+    if (mode != TOD_MODE_DRAW && mode != TOD_MODE_MEAN) return TOD_ERR_ARG;
+    Plan *p = reinterpret_cast<Plan *>(pl);
+    DeviceGuard dg(p->device);
+    const float tol = cg_tol > 0 ? static_cast<float>(cg_tol) : 1e-6f;
+    const int maxit = cg_maxiter > 0 ? cg_maxiter : 500;
+    return to_status(launch_ncorr(*p, d, s, gain, flags, psd, rng, mode, tol, maxit, ncorr_out,
+                                  cg_iters_out, stream, 0, p->nq, false));
+}
+
 tod_status tod_bin(tod_plan *pl, const uint16_t *psi, const float *d, const float *ncorr,
                    const double *gain, const uint32_t *flags, const double *psd, double *A_out,
                    double *b_out, int32_t *hits_out, cudaStream_t stream)

@@ -134,13 +134,14 @@ cudaError_t launch_gain(const Plan &p, const float *d, const float *s, const uin
 cudaError_t launch_ncorr(const Plan &p, const float *d, const float *s, const double *gain,
                          const uint32_t *flags, const double *psd, tod_rng rng, int mode,
                          float tol, int maxit, float *x, int32_t *iters, cudaStream_t st,
-                         int work_begin, int work_count);
+                         int work_begin, int work_count, bool prepare = true);
 // the same draw with caller-provided filter-weight scratch: at most
 // nclusters_max clusters, each using C x sz float4 of it
 cudaError_t launch_ncorr_scratch(const Plan &p, const float *d, const float *s, const double *gain,
                                  const uint32_t *flags, const double *psd, tod_rng rng, int mode,
                                  float tol, int maxit, float *x, int32_t *iters, cudaStream_t st,
-                                 int work_begin, int work_count, float4 *scratch, int nclusters_max);
+                                 int work_begin, int work_count, float4 *scratch, int nclusters_max,
+                                 bool prepare = true);
 cudaError_t launch_chi2(const Plan &p, const float *d, const float *s, const double *gain,
                         const uint32_t *flags, const double *psd, double *chi2, double *dgain,
                         double *dpsd, float *v, cudaStream_t st);

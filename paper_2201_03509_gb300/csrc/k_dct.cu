@@ -1840,16 +1840,17 @@ cudaError_t launch_gain(const Plan &p, const float *d, const float *s, const uin
 cudaError_t launch_ncorr(const Plan &p, const float *d, const float *s, const double *gain,
                          const uint32_t *flags, const double *psd, tod_rng rng, int mode,
                          float tol, int maxit, float *x, int32_t *iters, cudaStream_t st,
-                         int work_begin, int work_count)
+                         int work_begin, int work_count, bool prepare)
 {
     return launch_ncorr_scratch(p, d, s, gain, flags, psd, rng, mode, tol, maxit, x, iters, st,
-                                work_begin, work_count, p.wscratch, p.nclusters_ncorr);
+                                work_begin, work_count, p.wscratch, p.nclusters_ncorr, prepare);
 }
 
 cudaError_t launch_ncorr_scratch(const Plan &p, const float *d, const float *s, const double *gain,
                                  const uint32_t *flags, const double *psd, tod_rng rng, int mode,
                                  float tol, int maxit, float *x, int32_t *iters, cudaStream_t st,
-                                 int work_begin, int work_count, float4 *scratch, int nclusters_max)
+                                 int work_begin, int work_count, float4 *scratch, int nclusters_max,
+                                 bool prepare)
 {
     if (work_count <= 0) return cudaSuccess;
     if (nclusters_max < 1) return cudaErrorInvalidValue;
@@ -1861,7 +1862,7 @@ cudaError_t launch_ncorr_scratch(const Plan &p, const float *d, const float *s, 
     a.wscratch = scratch;
     a.xtab = p.use_prec ? p.xtab : nullptr;
     a.lvalid = p.lvalid;
-    if (p.use_prec) {
+    if (p.use_prec && prepare) {
         cudaError_t e = launch_toeplitz_prep(p, psd, st);
         if (e != cudaSuccess) return e;
     }

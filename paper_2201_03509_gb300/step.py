@@ -95,14 +95,28 @@ class GibbsTODStep:
     def run(self, map32_in, rng: Rng, mode: int = MODE_DRAW, stream=None):
         """Enqueue one step; the new map lands in self.map / self.map32.
         Uses the detector data of a pending prefetch_tod() if there is one."""
+        import torch
         self._take_prefetched(stream)
         p = self.plan
+        st = self._stream(stream)
+        # the n_corr gap preconditioner depends on the PSD alone: it is built
+        # on a side stream while decode, projection and the gain draw run
+        # (after everything already queued, so the previous step's draw has
+        # finished with the old tables)
+        if getattr(self, "_side", None) is None:
+            self._side = torch.cuda.Stream(device=self.d.device)
+        side = self._side
+        side.wait_stream(st)
+        p.ncorr_prepare(self.psd, side)
+        prepared = torch.cuda.Event()
+        prepared.record(side)
         p.decode(self.pix, self.psi, stream)
         p.project(map32_in, self.pix, self.psi, None, self.s, stream)
         p.sample_gain(self.d, self.s, self.flags, self.psd, rng, mode, self.gain, self.mu, self.sigma,
                       stream)
-        p.sample_ncorr(self.d, self.s, self.gain, self.flags, self.psd, rng, mode, self.ncorr,
-                       self.cg_iters, self.cg_tol, self.cg_maxiter, stream)
+        st.wait_event(prepared)
+        p.sample_ncorr_prepared(self.d, self.s, self.gain, self.flags, self.psd, rng, mode, self.ncorr,
+                                self.cg_iters, self.cg_tol, self.cg_maxiter, stream)
         p.bin(self.psi, self.d, self.ncorr, self.gain, self.flags, self.psd, self.A, self.b, self.hits,
               stream)
         p.solve_maps(self.A, self.b, self.hits, self.rcond_min, self.map, self.map32, self.rcond,

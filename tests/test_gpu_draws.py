@@ -8,7 +8,9 @@
 * a step captured as a CUDA graph and replayed at Gibbs iteration k gives
   bit for bit what the eager step gives at k;
 * steps whose detector data is prefetched into a second buffer on a copy
-  stream give bit for bit the steps of plain copies.
+  stream give bit for bit the steps of plain copies;
+* the n_corr draw split in preparation (on a side stream) and prepared draw
+  gives bit for bit the one-call draw.
 """
 import numpy as np
 import pytest
@@ -122,3 +124,39 @@ def test_prefetched_tod_matches_set_tod(tiny):
         for a, b in zip(refs[k], (step.gain, step.ncorr, step.map)):
             assert torch.equal(a, b), k
     wl.plan.status()
+
+
+@pytest.mark.gpu
+def test_prepared_ncorr_matches_sample_ncorr():
+    """tod_ncorr_prepare on a side stream + tod_sample_ncorr_prepared gives
+    bit for bit what tod_sample_ncorr gives (flagged detscans, so the gap
+    preconditioner is used)."""
+    import torch
+    import paper_2201_03509_gb300 as tg
+    from gpu_workload import Workload
+    cfg = synth.scaled(synth.CONFIGS["lfi30"], nscan=2, len_lo=9000, len_hi=30000)
+    assert cfg.flag_frac > 0
+    wl = Workload(cfg, cluster_size=0)
+    gains = torch.from_numpy(synth.gains(cfg)[:wl.nq].astype(np.float64)).to(wl.dev)
+    outs = []
+    for prepared in (False, True):
+        x = torch.full((wl.N,), float("nan"), dtype=torch.float32, device=wl.dev)
+        its = torch.zeros(wl.nq, dtype=torch.int32, device=wl.dev)
+        if prepared:
+            side = torch.cuda.Stream(device=wl.dev)
+            side.wait_stream(torch.cuda.current_stream())
+            wl.plan.ncorr_prepare(wl.t_psd, side)
+            ev = torch.cuda.Event()
+            ev.record(side)
+            torch.cuda.current_stream().wait_event(ev)
+            wl.plan.sample_ncorr_prepared(wl.t_d, wl.t_s, gains, wl.t_flags, wl.t_psd, tg.Rng(5, 1, 2),
+                                          tg.MODE_DRAW, x, its, cg_tol=1e-7)
+        else:
+            wl.plan.sample_ncorr(wl.t_d, wl.t_s, gains, wl.t_flags, wl.t_psd, tg.Rng(5, 1, 2), tg.MODE_DRAW, x,
+                                 its, cg_tol=1e-7)
+        torch.cuda.synchronize()
+        wl.plan.status()
+        outs.append((x.cpu().numpy(), its.cpu().numpy()))
+    assert outs[0][1].max() > 0                  # the CG (and its preconditioner) ran
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
