@@ -105,9 +105,18 @@ std::vector<uint32_t> canonical_codes(const std::vector<uint8_t> &len)
     return code;
 }
 
+// A first-level decode entry in 32 bits: value << 5 | code length, for
+// values that fit in 27 bits; 0 (length 0) sends the decoder to the
+// canonical limits instead.
+int32_t dec_lut_entry(int32_t value, int L)
+{
+    if (value < -(1 << 26) || value >= (1 << 26)) return 0;
+    return static_cast<int32_t>((static_cast<uint32_t>(value) << 5) | static_cast<uint32_t>(L));
+}
+
 // canonical decode tables of one code (symbols ascending with lengths)
 struct DecTab {
-    std::vector<int2> lut;                  // 1 << DEC_LUTB
+    std::vector<int32_t> lut;               // 1 << DEC_LUTB packed entries (see dec_lut_entry)
     unsigned long long lim[26];
     int32_t base[26];
     std::vector<int32_t> canon;
@@ -134,13 +143,13 @@ DecTab build_dectab(const int32_t *vals, const uint8_t *len, int64_t k)
         index += count[L];
     }
     t.lim[25] = ~0ull;
-    t.lut.assign(1 << DEC_LUTB, make_int2(0, 0));
+    t.lut.assign(1 << DEC_LUTB, 0);
     for (uint32_t v = 0; v < (1u << DEC_LUTB); ++v) {
         const uint64_t peek = static_cast<uint64_t>(v) << (32 - DEC_LUTB);
         for (int L = 1; L <= DEC_LUTB; ++L) {
             if (peek < t.lim[L]) {
                 const int64_t ci = t.base[L] + static_cast<int64_t>(peek >> (32 - L));
-                if (ci >= 0 && ci < k) t.lut[v] = make_int2(t.canon[ci], L);
+                if (ci >= 0 && ci < k) t.lut[v] = dec_lut_entry(t.canon[ci], L);
                 break;
             }
         }
@@ -357,7 +366,7 @@ cudaError_t build_huff(Plan &p, HuffDev &d, const tod_huff_streams &h)
         for (int64_t b = h.blk_off[q]; b < h.blk_off[q + 1]; ++b) blk_q[b] = static_cast<int32_t>(q);
     if ((e = dev_upload(p, d.blk_q, blk_q.data(), blk_q.size()))) return e;
     d.nblk = h.nblk;
-    std::vector<int2> lut(static_cast<size_t>(p.nscan) << DEC_LUTB);
+    std::vector<int32_t> lut(static_cast<size_t>(p.nscan) << DEC_LUTB);
     std::vector<unsigned long long> lim(static_cast<size_t>(p.nscan) * 26);
     std::vector<int32_t> base(static_cast<size_t>(p.nscan) * 26);
     std::vector<int32_t> canon_off(p.nscan + 1, 0), canon;

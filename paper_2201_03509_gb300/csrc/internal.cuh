@@ -8,7 +8,7 @@
 
 namespace tg {
 
-constexpr int DEC_LUTB = 12;          // first-level decode table: 2^12 entries
+constexpr int DEC_LUTB = 13;          // first-level decode table: 2^13 packed 32-bit entries
 constexpr int DEC_CANON_SMEM = 4096;  // symbols of one code staged in shared memory
 constexpr int DEC_T = 256;            // decode threads per CTA (one checkpoint block each)
 constexpr int DEC_ROUND = 16;         // symbols staged per thread before a coalesced write
@@ -31,7 +31,7 @@ struct HuffDev {
     uint32_t *ckpt_bit = nullptr;    // [nblk]
     int32_t *ckpt_val = nullptr;     // [nblk]
     int32_t *blk_q = nullptr;        // [nblk] detscan of each block
-    int2 *lut = nullptr;             // [nscan][1<<DEC_LUTB] (value, length) ; length 0 = long code
+    int32_t *lut = nullptr;          // [nscan][1<<DEC_LUTB] value << 5 | length; length 0 = long code
     unsigned long long *lim = nullptr;  // [nscan][26] left-justified limits, index = length
     int32_t *base = nullptr;         // [nscan][26]
     int32_t *canon_off = nullptr;    // [nscan+1]

@@ -18,14 +18,14 @@ __global__ void __launch_bounds__(DEC_T)
 k_decode(const uint32_t *__restrict__ words, const int64_t *__restrict__ word_off,
          const int64_t *__restrict__ nbits, const int64_t *__restrict__ blk_off,
          const uint32_t *__restrict__ ckpt_bit, const int32_t *__restrict__ ckpt_val,
-         const int32_t *__restrict__ blk_q, const int2 *__restrict__ lut,
+         const int32_t *__restrict__ blk_q, const int32_t *__restrict__ lut,
          const unsigned long long *__restrict__ lim_g, const int32_t *__restrict__ base_g,
          const int32_t *__restrict__ canon_off, const int32_t *__restrict__ canon_vals,
          const int32_t *__restrict__ cta_scan, const int64_t *__restrict__ cta_blk0,
          const int32_t *__restrict__ cta_nblk, const int64_t *__restrict__ off,
          OutT *__restrict__ out, int32_t *status)
 {
-    extern __shared__ int2 s_lut[];                        // [1 << DEC_LUTB] then canonical symbols
+    extern __shared__ int32_t s_lut[];                     // [1 << DEC_LUTB] then canonical symbols
     int32_t *s_canon = reinterpret_cast<int32_t *>(s_lut + (1 << DEC_LUTB));
     __shared__ unsigned long long s_lim[26];
     __shared__ int32_t s_base[26];
@@ -84,11 +84,11 @@ k_decode(const uint32_t *__restrict__ words, const int64_t *__restrict__ word_of
             const int idx = round * DEC_ROUND + i;
             if (active && ok && idx < cnt) {
                 const uint32_t peek = static_cast<uint32_t>(buf >> 32);
-                const int2 e = s_lut[peek >> (32 - DEC_LUTB)];
-                int len = e.y;
-                int32_t v = e.x;
+                const int32_t e = s_lut[peek >> (32 - DEC_LUTB)];
+                int len = e & 31;
+                int32_t v = e >> 5;
                 if (len == 0) {
-                    int L = DEC_LUTB + 1;
+                    int L = 1;            // a long code, or a value too wide for the packed entry
                     while (L <= TOD_HUFF_MAXLEN && static_cast<unsigned long long>(peek) >= s_lim[L]) ++L;
                     if (L > TOD_HUFF_MAXLEN) { ok = false; len = 1; v = 0; }
                     else {
@@ -125,7 +125,7 @@ k_decode(const uint32_t *__restrict__ words, const int64_t *__restrict__ word_of
 
 cudaError_t setup_decode_kernel()
 {
-    const int smem = static_cast<int>(sizeof(int2) * (1 << DEC_LUTB) + sizeof(int32_t) * DEC_CANON_SMEM);
+    const int smem = static_cast<int>(sizeof(int32_t) * (1 << DEC_LUTB) + sizeof(int32_t) * DEC_CANON_SMEM);
     cudaError_t e = cudaFuncSetAttribute(k_decode<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_decode<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -135,7 +135,7 @@ cudaError_t launch_decode(const Plan &p, const HuffDev &h, int32_t *pix_out, uin
                           cudaStream_t st)
 {
     if (h.ncta == 0) return cudaSuccess;
-    const size_t smem = sizeof(int2) * (1 << DEC_LUTB) + sizeof(int32_t) * DEC_CANON_SMEM;
+    const size_t smem = sizeof(int32_t) * (1 << DEC_LUTB) + sizeof(int32_t) * DEC_CANON_SMEM;
     if (pix_out) {
         k_decode<int32_t><<<h.ncta, DEC_T, smem, st>>>(
             h.words, h.word_off, h.nbits, h.blk_off, h.ckpt_bit, h.ckpt_val, h.blk_q, h.lut, h.lim,
