@@ -47,7 +47,7 @@ def autotune(nside: int, ndet: int, nscan: int, fsamp: float, offsets: np.ndarra
         auto = Plan(nside, ndet, nsub, fsamp, off, pix_s, psi_s, 0, device)
         c0 = auto.info()["cluster_size"]
         auto.close()
-        cs = sorted({c0, 8, 9, 10, 12, 16})
+        cs = sorted({c0, 6, 7, 8, 9, 10, 12, 16})
         candidates = [(c, r) for c in cs for r in (8, 16)]
     timings = {}
     for (c, r) in candidates:

@@ -9,8 +9,7 @@
 namespace tg {
 
 constexpr int DEC_LUTB = 13;          // first-level decode table: 2^13 packed 32-bit entries
-constexpr int DEC_CANON_SMEM = 4096;  // symbols of one code staged in shared memory
-constexpr int DEC_T = 256;            // decode threads per CTA (one checkpoint block each)
+constexpr int DEC_T = 512;            // decode threads per CTA (one checkpoint block each)
 constexpr int DEC_ROUND = 16;         // symbols staged per thread before a coalesced write
 constexpr int ELEM_TILE = 4096;       // samples per tile of the element-wise kernels
 constexpr int DCT_T = 512;            // threads per CTA of the cluster transform kernels

@@ -5,7 +5,10 @@
 // preceding it, so a band's ~10^6 blocks decode in parallel.  One CTA takes
 // up to DEC_T consecutive blocks of one scan and stages that scan's code
 // (a 2^DEC_LUTB-entry first-level table, per-length limits for the long
-// codes, symbols in canonical order) in shared memory.  Values are undone
+// codes) in shared memory; the rare long codes read their symbol through
+// the cache.  Each thread's decode is one long dependency chain, so the
+// CTA is large (the table is staged once for more threads) and three fit
+// on an SM.  Values are undone
 // from their differences on the fly and staged DEC_ROUND at a time per
 // thread in shared memory, then written with coalesced stores.
 #include "common.cuh"
@@ -25,8 +28,7 @@ k_decode(const uint32_t *__restrict__ words, const int64_t *__restrict__ word_of
          const int32_t *__restrict__ cta_nblk, const int64_t *__restrict__ off,
          OutT *__restrict__ out, int32_t *status)
 {
-    extern __shared__ int32_t s_lut[];                     // [1 << DEC_LUTB] then canonical symbols
-    int32_t *s_canon = reinterpret_cast<int32_t *>(s_lut + (1 << DEC_LUTB));
+    extern __shared__ int32_t s_lut[];                     // [1 << DEC_LUTB]
     __shared__ unsigned long long s_lim[26];
     __shared__ int32_t s_base[26];
     __shared__ OutT s_tile[DEC_T][DEC_ROUND + 1];
@@ -40,12 +42,8 @@ k_decode(const uint32_t *__restrict__ words, const int64_t *__restrict__ word_of
 
     for (int i = tid; i < (1 << DEC_LUTB); i += DEC_T) s_lut[i] = lut[(int64_t)scan * (1 << DEC_LUTB) + i];
     if (tid < 26) { s_lim[tid] = lim_g[scan * 26 + tid]; s_base[tid] = base_g[scan * 26 + tid]; }
-    // symbols of long codes (longer than DEC_LUTB bits) from shared memory
-    // when the code is small enough, else through the cache
+    // symbols of long codes (longer than DEC_LUTB bits: rare) through the cache
     const int c0 = canon_off[scan], nc = canon_off[scan + 1] - c0;
-    const bool canon_smem = nc <= DEC_CANON_SMEM;
-    if (canon_smem)
-        for (int i = tid; i < nc; i += DEC_T) s_canon[i] = canon_vals[c0 + i];
 
     // this thread's block
     const bool active = tid < nb;
@@ -94,7 +92,7 @@ k_decode(const uint32_t *__restrict__ words, const int64_t *__restrict__ word_of
                     else {
                         const int ci = s_base[L] + static_cast<int>(peek >> (32 - L));
                         if (ci < 0 || ci >= nc) { ok = false; v = 0; }
-                        else v = canon_smem ? s_canon[ci] : __ldg(canon_vals + c0 + ci);
+                        else v = __ldg(canon_vals + c0 + ci);
                         len = L;
                     }
                 }
@@ -125,7 +123,7 @@ k_decode(const uint32_t *__restrict__ words, const int64_t *__restrict__ word_of
 
 cudaError_t setup_decode_kernel()
 {
-    const int smem = static_cast<int>(sizeof(int32_t) * (1 << DEC_LUTB) + sizeof(int32_t) * DEC_CANON_SMEM);
+    const int smem = static_cast<int>(sizeof(int32_t) * (1 << DEC_LUTB));
     cudaError_t e = cudaFuncSetAttribute(k_decode<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_decode<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -135,7 +133,7 @@ cudaError_t launch_decode(const Plan &p, const HuffDev &h, int32_t *pix_out, uin
                           cudaStream_t st)
 {
     if (h.ncta == 0) return cudaSuccess;
-    const size_t smem = sizeof(int32_t) * (1 << DEC_LUTB) + sizeof(int32_t) * DEC_CANON_SMEM;
+    const size_t smem = sizeof(int32_t) * (1 << DEC_LUTB);
     if (pix_out) {
         k_decode<int32_t><<<h.ncta, DEC_T, smem, st>>>(
             h.words, h.word_off, h.nbits, h.blk_off, h.ckpt_bit, h.ckpt_val, h.blk_q, h.lut, h.lim,
