@@ -313,12 +313,12 @@ def run_ours(args):
     if dom in ("gain", "ncorr"):
         # FP32 FFT work: 5 (n/2) log2(n/2) flops per complex transform of a
         # length-n real DCT, plus the split (~10 n); transforms per detscan:
-        # gain 2, n_corr 2 + 2 (iterations + 1) when flagged.
+        # gain 2, n_corr 2 + 2 per CG iteration + 1 (the correction's inverse).
         per = 2.5 * lens * np.log2(lens / 2.0) + 10.0 * lens
         if dom == "gain":
             flops = float(np.sum(2 * per))
         else:
-            flops = float(np.sum(per * (2 + np.where(iters > 0, 2 * (iters + 1), 0))))
+            flops = float(np.sum(per * (2 + np.where(iters > 0, 2 * iters + 1, 0))))
         peak_tf = 152 * 128 * 2 * (peaks.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
         ach = flops / (stage_ms[dom] / 1e3) / 1e12
         traffic = None

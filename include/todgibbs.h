@@ -248,8 +248,9 @@ tod_status tod_sample_ncorr_prepared(tod_plan *p, const float *d, const float *s
 /* tod_sample_ncorr_static -- tod_sample_ncorr with nothing allocated.
  * The paper has no counterpart: it is a library convenience.  Same
  * arguments, results and errors as tod_sample_ncorr, except that the
- * per-cluster filter-weight scratch comes from one fixed device array
- * compiled into the library (TOD_NCORR_STATIC_SCRATCH_BYTES per device)
+ * per-cluster scratch (filter weights and CG spectra) comes from one fixed
+ * device array compiled into the library (TOD_NCORR_STATIC_SCRATCH_BYTES per
+ * device)
  * instead of the plan's buffer.  It is for callers that must not allocate
  * device memory once they run: a process whose free device memory is all
  * held by another allocator's pool (so a new allocation fails or forces that
@@ -259,19 +260,19 @@ tod_status tod_sample_ncorr_prepared(tod_plan *p, const float *d, const float *s
  *   the host before the first draw and before any stream capture; it looks
  *   up the array's device address (cudaGetSymbolAddress on the plan's
  *   device) and caches it.  A first draw without it does the lookup itself.
- *   Size: each cluster of the draw needs C x sz x 16 bytes (C the cluster
+ *   Size: each cluster of the draw needs C x sz x 32 bytes (C the cluster
  *   size, sz the plan's per-CTA transform buffer); the draw runs with as
  *   many clusters as fit (fewer than tod_sample_ncorr may use, so it can be
  *   slower) and returns TOD_ERR_SCRATCH, enqueuing nothing, when not even
  *   one cluster fits.  The setup call reports the cluster count that fits
  *   in *max_clusters_out (may be NULL) and returns TOD_ERR_SCRATCH likewise.
- *   Contents: every cluster writes its weights before it reads them, so no
+ *   Contents: every cluster writes its scratch before it reads it, so no
  *   part of the array must start at zero.
  *   Concurrency: all plans and streams on one device share the array; two
  *   calls that can overlap on the device (different streams, or host
  *   threads without ordering) race on it and give wrong results.  Serialise
  *   them on one stream. */
-#define TOD_NCORR_STATIC_SCRATCH_BYTES (32u << 20)
+#define TOD_NCORR_STATIC_SCRATCH_BYTES (64u << 20)
 tod_status tod_ncorr_static_setup(tod_plan *p, int32_t *max_clusters_out);
 tod_status tod_sample_ncorr_static(tod_plan *p, const float *d, const float *s,
                                    const double *gain, const uint32_t *flags,

@@ -722,7 +722,7 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
         if ((e = dev_upload(*p, p->gain_ab, static_cast<double2 *>(nullptr), static_cast<size_t>(p->nq))))
             return fail(e);
         // filter-weight scratch: one slot per CTA of every resident cluster
-        p->wscratch_per_cluster = static_cast<int64_t>(p->C) * p->sz;
+        p->wscratch_per_cluster = static_cast<int64_t>(p->C) * p->sz * NCORR_SCRATCH_F4;
         if ((e = dev_upload(*p, p->wscratch, static_cast<float4 *>(nullptr),
                             static_cast<size_t>(std::max(1, p->nclusters_ncorr)) * p->wscratch_per_cluster)))
             return fail(e);

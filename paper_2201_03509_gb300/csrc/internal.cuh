@@ -9,7 +9,8 @@
 namespace tg {
 
 constexpr int DEC_LUTB = 13;          // first-level decode table: 2^13 packed 32-bit entries
-constexpr int DEC_T = 512;            // decode threads per CTA (one checkpoint block each)
+constexpr int DEC_T = 512;
+constexpr int NCORR_SCRATCH_F4 = 2;   // float4 per packed slot of the n_corr scratch: filter weights, CG spectra            // decode threads per CTA (one checkpoint block each)
 constexpr int DEC_ROUND = 16;         // symbols staged per thread before a coalesced write
 constexpr int ELEM_TILE = 4096;       // samples per tile of the element-wise kernels
 constexpr int DCT_T = 512;            // threads per CTA of the cluster transform kernels
@@ -87,7 +88,7 @@ struct Plan {
     float2 *tw = nullptr;            // twiddle tables
     int32_t *work = nullptr;         // [nq] detscans sorted by decreasing length
     int32_t nclusters_gain = 1, nclusters_ncorr = 1;
-    float4 *wscratch = nullptr;      // per-cluster filter weights (beta, gamma) in packed layout
+    float4 *wscratch = nullptr;      // per-CTA filter weights (beta, gamma) and CG spectra, packed layout
     float *htab = nullptr;           // [ndet][TOEP_LMAX] gap-kernel h(d)
     float *xtab = nullptr;           // [ndet][TOEP_LMAX (TOEP_LMAX+1)/2] T_L^{-1} e_1 per order
     int32_t *lvalid = nullptr;       // [ndet]

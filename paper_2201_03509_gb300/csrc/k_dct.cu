@@ -455,6 +455,44 @@ __device__ __forceinline__ void split_roundtrip(const Geo &XS, float2 *__restric
     __syncthreads();
 }
 
+// The inverse split alone, from packed orthonormal coefficients given per
+// element: f(e) is the coefficient pair of element e (modes k and n - k, or
+// 0 and m); writes Z into this CTA's row pairs of U, as the second half of
+// split_roundtrip does.
+template <class F>
+__device__ __forceinline__ void split_inverse_from(const Geo &XS, float2 *__restrict__ U, F f)
+{
+    const Geo X = XS;
+    const int m2 = X.m2, m2p = X.m2p, m1 = X.m1, p0 = X.p0;
+    const float sqi = X.sq_inv, s0i = X.s0_inv;
+    const int total = X.npl * m2;
+    const FastDiv fm2 = X.f_m2;
+    for (int e = threadIdx.x; e < total; e += DCT_T) {
+        const int pl = fdiv(e, fm2), k2 = e - pl * m2;
+        const int p = p0 + pl;
+        const int cnt = (p == 0) ? (m2 / 2 + 1) : ((2 * p == m1) ? (m2 + 1) / 2 : m2);
+        if (k2 >= cnt) continue;
+        int ib, q1, q2;
+        if (p == 0) { q1 = 0; q2 = (k2 == 0) ? 0 : m2 - k2; ib = 2 * pl * m2p + q2; }
+        else { q1 = m1 - p; q2 = m2 - 1 - k2; ib = ((q1 == p) ? 2 * pl : 2 * pl + 1) * m2p + q2; }
+        const int ia = 2 * pl * m2p + k2;
+        const float2 Ya = f(ia);
+        if (p == 0 && k2 == 0) {
+            const float V0 = Ya.x * s0i, Vm = Ya.y * s0i;
+            U[ia] = make_float2(0.5f * (V0 + Vm), 0.5f * (V0 - Vm));
+            continue;
+        }
+        if (ib != ia) {
+            const float2 Yb = f(ib);
+            U[ib] = split_inv_one(X, Yb, Ya, q1, q2, p, k2, sqi);
+            U[ia] = split_inv_one(X, Ya, Yb, p, k2, q1, q2, sqi);
+        } else {
+            U[ia] = split_inv_one(X, Ya, Ya, p, k2, q1, q2, sqi);
+        }
+    }
+    __syncthreads();
+}
+
 // The last Stockham pass of the column FFTs (forward) or of the row FFTs
 // (inverse) with the four-step transpose folded in: each output goes,
 // times the four-step twiddle W_m^{-+ j2 k1}, straight into the shared
@@ -1316,7 +1354,9 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
         const tod_rng rng = a.rng;
         const uint64_t gi = rng.gibbs_iter_dev ? *rng.gibbs_iter_dev : rng.gibbs_iter;
         float *xq = a.x_out + o;
-        float4 *wt = a.wscratch + (static_cast<int64_t>(cid) * C + c) * a.sz;
+        // per-CTA scratch: filter weights, then the CG spectral accumulators
+        float4 *wt = a.wscratch + (static_cast<int64_t>(cid) * C + c) * (NCORR_SCRATCH_F4 * a.sz);
+        float4 *acc = wt + a.sz;
         float2 *cur = sm.U0, *oth = sm.U1;
         // right-hand side, time-domain part: M (r/s2 + w1/s)
         ncorr_rhs(sX, cur, dq, sq, fl, o, g, inv_s2, inv_s, draw, q, gi, rng.seed, rng.band);
@@ -1504,7 +1544,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             Acc2 rr_loc = {0.f, 0.f};
             for (int i = threadIdx.x; i < kc; i += DCT_T) {
                 const float v = *cg_elem(cl, cur, c_loc, i);
-                c_y[i] = 0.f; c_r[i] = v;
+                c_r[i] = v;
                 acc_add_prod(rr_loc, v, v);
             }
             __syncthreads();
@@ -1514,6 +1554,12 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             double rz = rr2.y;
             const double stop = static_cast<double>(a.tol) * a.tol * rr2.x;
             conv = rr2.x == 0.0;
+            // y = sum_i alpha_i p_i is never formed: the correction B^{-1} E y
+            // = C^T diag(beta) sum_i alpha_i (C E p_i) is built from the spectra
+            // C E p_i the iterations compute anyway, accumulated per packed
+            // slot in acc (x, y: sum so far; z, w: the latest spectrum, whose
+            // step length is known one iteration later)
+            float alp_prev = 0.f;
             while (!conv && it < a.maxit) {
                 // cur <- C^T diag(gamma) C E p (cur is zero in every CTA)
                 for (int i = threadIdx.x; i < kc; i += DCT_T) *cg_elem(cl, cur, c_loc, i) = c_p[i];
@@ -1521,6 +1567,12 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                 if (dct_forward_pre(sX, cur, oth, cl)) { float2 *t_ = cur; cur = oth; oth = t_; }
                 split_roundtrip(X, cur, [&](int e, int, float2 Y) {
                     const float4 w = wt[e];
+                    if (it == 0) {
+                        acc[e] = make_float4(0.f, 0.f, Y.x, Y.y);
+                    } else {
+                        const float4 A = acc[e];
+                        acc[e] = make_float4(fmaf(alp_prev, A.z, A.x), fmaf(alp_prev, A.w, A.y), Y.x, Y.y);
+                    }
                     return make_float2(Y.x * w.z, Y.y * w.w);
                 });
                 if (dct_inverse_post(sX, cur, oth, cl)) { float2 *t_ = cur; cur = oth; oth = t_; }
@@ -1538,10 +1590,8 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                 // step lengths in FP32 (the vectors are FP32); FP64 division
                 // by every thread would cost more than the update itself
                 const float alp = static_cast<float>(rz) / static_cast<float>(pq);
-                for (int i = threadIdx.x; i < kc; i += DCT_T) {
-                    c_y[i] = fmaf(alp, c_p[i], c_y[i]);
-                    c_r[i] = fmaf(-alp, c_q[i], c_r[i]);
-                }
+                alp_prev = alp;
+                for (int i = threadIdx.x; i < kc; i += DCT_T) c_r[i] = fmaf(-alp, c_q[i], c_r[i]);
                 Acc2 rn_loc = {0.f, 0.f};
                 for (int i = threadIdx.x; i < kc; i += DCT_T) acc_add_prod(rn_loc, c_r[i], c_r[i]);
                 __syncthreads();
@@ -1553,23 +1603,23 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                 __syncthreads();
                 rz = rn2.y;
             }
-            // x = x0 + B^{-1} E y (cur is zero in every CTA)
-            for (int i = threadIdx.x; i < kc; i += DCT_T) *cg_elem(cl, cur, c_loc, i) = c_y[i];
-            cl.sync();
-            if (dct_forward_pre(sX, cur, oth, cl)) { float2 *t_ = cur; cur = oth; oth = t_; }
-            split_roundtrip(X, cur, [&](int e, int, float2 Y) {
-                const float4 w = wt[e];
-                return make_float2(Y.x * w.x, Y.y * w.y);
-            });
-            if (dct_inverse_post(sX, cur, oth, cl)) { float2 *t_ = cur; cur = oth; oth = t_; }
-            for (int e = threadIdx.x; e < tot; e += DCT_T) {
-                int t0, t1;
-                bool valid;
-                elem_samples(X, e, t0, t1, valid);
-                if (!valid) continue;
-                const float2 v = cur[e];
-                xq[t0] += v.x;
-                xq[t1] += v.y;
+            // x = x0 + B^{-1} E y: the accumulated spectrum, filtered by beta,
+            // one inverse transform (none when y = 0)
+            if (it > 0) {
+                split_inverse_from(X, cur, [&](int e) {
+                    const float4 A = acc[e], w = wt[e];
+                    return make_float2(fmaf(alp_prev, A.z, A.x) * w.x, fmaf(alp_prev, A.w, A.y) * w.y);
+                });
+                if (dct_inverse_post(sX, cur, oth, cl)) { float2 *t_ = cur; cur = oth; oth = t_; }
+                for (int e = threadIdx.x; e < tot; e += DCT_T) {
+                    int t0, t1;
+                    bool valid;
+                    elem_samples(X, e, t0, t1, valid);
+                    if (!valid) continue;
+                    const float2 v = cur[e];
+                    xq[t0] += v.x;
+                    xq[t1] += v.y;
+                }
             }
             if (!conv) set_status(a.status, q, TOD_ERR_NOT_CONVERGED);
         }

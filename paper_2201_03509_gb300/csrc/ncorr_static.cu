@@ -1,11 +1,11 @@
 // tod_sample_ncorr_static: the correlated-noise draw of tod_sample_ncorr with
-// its per-cluster filter-weight scratch in a fixed device array compiled into
-// the library, so the call itself allocates nothing.
+// its per-cluster scratch (filter weights, CG spectra) in a fixed device
+// array compiled into the library, so the call itself allocates nothing.
 //
 // The scratch is one file-scope __device__ array per device of
 // TOD_NCORR_STATIC_SCRATCH_BYTES.  Its device address is looked up once per
 // device (with that device current) by cudaGetSymbolAddress and cached.  Each
-// cluster of the draw writes its filter weights before it reads them, so no
+// cluster of the draw writes its scratch before it reads it, so no
 // part of the array has to start at zero.  All calls on one device share the
 // array: two calls that may run at the same time (other streams, other
 // plans, other host threads) race on it.
@@ -55,7 +55,7 @@ tod_status tod_ncorr_static_setup(tod_plan *pl, int32_t *max_clusters_out)
     const cudaError_t e = static_scratch(p->device, &scratch);
     if (prev != p->device) cudaSetDevice(prev);
     if (e != cudaSuccess) return TOD_ERR_CUDA;
-    const int64_t per_cluster = static_cast<int64_t>(p->C) * p->sz;     // float4 per cluster
+    const int64_t per_cluster = static_cast<int64_t>(p->C) * p->sz * NCORR_SCRATCH_F4;     // float4 per cluster
     const int64_t fit = static_cast<int64_t>(kNcorrStaticFloat4) / std::max<int64_t>(1, per_cluster);
     if (max_clusters_out) max_clusters_out[0] = static_cast<int32_t>(std::min<int64_t>(fit, p->nclusters_ncorr));
     return fit < 1 ? TOD_ERR_SCRATCH : TOD_OK;
@@ -69,7 +69,7 @@ tod_status tod_sample_ncorr_static(tod_plan *pl, const float *d, const float *s,
     if (!pl || !d || !s || !gain || !flags || !psd || !ncorr_out) return TOD_ERR_ARG;
     if (mode != TOD_MODE_DRAW && mode != TOD_MODE_MEAN) return TOD_ERR_ARG;
     Plan *p = reinterpret_cast<Plan *>(pl);
-    const int64_t per_cluster = static_cast<int64_t>(p->C) * p->sz;
+    const int64_t per_cluster = static_cast<int64_t>(p->C) * p->sz * NCORR_SCRATCH_F4;
     const int64_t fit = static_cast<int64_t>(kNcorrStaticFloat4) / std::max<int64_t>(1, per_cluster);
     if (fit < 1) return TOD_ERR_SCRATCH;          // one cluster's weights exceed the array
     int prev = 0;
