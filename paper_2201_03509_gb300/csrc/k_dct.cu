@@ -988,7 +988,8 @@ __global__ void __launch_bounds__(256) k_gain_draw(const double2 *__restrict__ a
 
 // ---------------------------------------------------------------------------
 // A5: correlated noise.  x0 = B^{-1} b (B = C^T diag(phi + 1/sigma0^2) C)
-// is written to x_out; flagged detscans then solve the Schur complement
+// is the draw of a gap-free detscan; flagged detscans then solve the Schur
+// complement
 //   S y = E^T x0,  S = sigma0^2 I - E^T B^{-1} E = E^T C^T diag(gamma) C E
 // (E: flagged samples; C^T C = I) by CG and add B^{-1} E y (Woodbury):
 // x = A^{-1} b exactly, A = B - E E^T / sigma0^2.
@@ -1037,6 +1038,55 @@ struct OwnBlocks {
     int rnd[GAP_CAP + 1];
     int nrnd;
 };
+
+// Thread 0: split the detscan's gaps into blocks of at most lmax samples
+// (each with the rank of its first flagged sample); then each block, longest
+// first, goes to the CTA with the least work so far (a block's cost grows as
+// len^2: triangular Toeplitz products), the lowest rank on ties.  Every CTA
+// makes the same assignment, with no exchange.  Fills this CTA's own blocks
+// (applied in rounds of at most GB_CAP floats: 8 zeros, the block padded to
+// a multiple of 4, 8 zeros); returns the number of blocks (more than
+// GAP_CAP: nothing assigned).  Out of line: its registers stay out of the
+// kernel's.
+__device__ __noinline__ int assign_gap_blocks(OwnBlocks &ob, int &nown, const int *g_beg, const int *g_end, int ngap,
+                                              int lmax, int C, int c, int *blen, int *brank, int *bord)
+{
+    int nb = 0, rank = 0;
+    for (int g2 = 0; g2 < ngap; ++g2) {
+        for (int b0 = g_beg[g2]; b0 < g_end[g2]; b0 += lmax) {
+            const int len = min(lmax, g_end[g2] - b0);
+            if (nb < GAP_CAP) { blen[nb] = len; brank[nb] = rank; }
+            rank += len;
+            ++nb;
+        }
+    }
+    if (nb <= GAP_CAP) {
+        for (int i = 0; i < nb; ++i) {            // indices by decreasing length (stable)
+            int j = i;
+            while (j > 0 && blen[bord[j - 1]] < blen[i]) { bord[j] = bord[j - 1]; --j; }
+            bord[j] = i;
+        }
+        long long load[16];
+        for (int r = 0; r < C; ++r) load[r] = 0;
+        int rlen = 0, rq = 0;
+        for (int i = 0; i < nb; ++i) {
+            const int bi = bord[i], len = blen[bi];
+            int best = 0;
+            for (int r = 1; r < C; ++r)
+                if (load[r] < load[best]) best = r;
+            load[best] += static_cast<long long>(len) * len;
+            if (best != c) continue;
+            const int reg = ((len + 3) & ~3) + 16;
+            if (nown == 0 || rlen + reg > GB_CAP) { ob.rnd[ob.nrnd++] = nown; rlen = 0; rq = 0; }
+            ob.len[nown] = len; ob.rank[nown] = brank[bi]; ob.off[nown] = rlen; ob.q[nown] = rq;
+            ++nown;
+            rlen += reg;
+            rq += (len + 3) >> 2;
+        }
+    }
+    ob.rnd[ob.nrnd] = nown;
+    return nb;
+}
 
 // CG vector element of global rank k: (CTA k / kper, index k mod kper)
 __device__ __forceinline__ float *rank_elem(cg::cluster_group &cl, float *vec, int kper, int k) {
@@ -1322,6 +1372,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
     __shared__ int3 s_wscan[DCT_T / 32 + 1];
     __shared__ int s_nown, s_ovf;
     __shared__ int g_beg[GAP_CAP], g_end[GAP_CAP];
+    __shared__ int s_blen[GAP_CAP], s_brank[GAP_CAP], s_bord[GAP_CAP];   // gap blocks (thread 0)
     __shared__ OwnBlocks ob;
     cg::cluster_group cl = cg::this_cluster();
     const int C = static_cast<int>(cl.num_blocks()), c = static_cast<int>(cl.block_rank());
@@ -1368,24 +1419,12 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
         split_roundtrip(X, cur, [&](int e, int, float2 Y) {
             const float4 w = wt[e];
             const float2 nu = oth[e];
-            return make_float2((Y.x + nu.x) * w.x, (Y.y + nu.y) * w.y);
+            const float2 cb = make_float2(Y.x + nu.x, Y.y + nu.y);
+            acc[e] = make_float4(cb.x, cb.y, 0.f, 0.f);       // x0 = C^T diag(beta) cb
+            return make_float2(cb.x * w.x, cb.y * w.y);
         });
 
         if (dct_inverse_post(sX, cur, oth, cl)) { float2 *t_ = cur; cur = oth; oth = t_; }      // cur = x0 (time layout)
-        // x0 -> x_out
-        {
-            const int tot = X.m1 * X.ncolmax;
-            for (int e = threadIdx.x; e < tot; e += DCT_T) {
-                int t0, t1;
-                bool valid;
-                elem_samples(X, e, t0, t1, valid);
-                if (!valid) continue;
-                const float2 v = cur[e];
-                xq[t0] = v.x;
-                xq[t1] = v.y;
-            }
-        }
-
         // Flagged samples of the detscan, ranked in time order.  The CG
         // vectors are spread evenly over the cluster: CTA c holds ranks
         // [c kper, (c+1) kper), each entry with the (owner CTA, element) of
@@ -1425,6 +1464,19 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
         const int k0 = min(kc_all, c * kper);
         const int kc = min(kc_all, k0 + kper) - k0;     // entries held by this CTA
         const bool cap_ovf = kper > CG_KCAP;
+        if (kc_all == 0 || cap_ovf) {
+            // x = x0 (no flagged sample, or too many for the CG buffers)
+            const int tot = X.m1 * X.ncolmax;
+            for (int e = threadIdx.x; e < tot; e += DCT_T) {
+                int t0, t1;
+                bool valid;
+                elem_samples(X, e, t0, t1, valid);
+                if (!valid) continue;
+                const float2 v = cur[e];
+                xq[t0] = v.x;
+                xq[t1] = v.y;
+            }
+        }
         {
             int pos = ex.x, gpos = ex.y, epos = ex.z;
             for (int i = 0; i < per; ++i) {
@@ -1476,35 +1528,9 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
         // matched by index: starts and ends alternate in sample order
         const bool prec = a.xtab != nullptr && ngap <= GAP_CAP;
         if (prec && threadIdx.x == 0) {
-            // split gaps into blocks of at most lmax samples; block b goes to
-            // CTA b mod C with the rank of its first sample
             const int lmax = max(1, min(TOEP_LMAX, a.lvalid[det]));
-            int nb = 0, rank = 0, rlen = 0, rq = 0, cb = 0;
-            for (int g2 = 0; g2 < ngap; ++g2) {
-                for (int b0 = g_beg[g2]; b0 < g_end[g2]; b0 += lmax) {
-                    const int len = min(lmax, g_end[g2] - b0);
-                    if (cb == c) {
-                        if (s_nown < GAP_CAP) {     // else the whole cluster goes without (below)
-                            // own blocks are applied in rounds of at most GB_CAP
-                            // floats: 8 zeros, the block padded to a multiple of 4, 8 zeros
-                            const int reg = ((len + 3) & ~3) + 16;
-                            if (s_nown == 0 || rlen + reg > GB_CAP) { ob.rnd[ob.nrnd++] = s_nown; rlen = 0; rq = 0; }
-                            ob.len[s_nown] = len; ob.rank[s_nown] = rank; ob.off[s_nown] = rlen; ob.q[s_nown] = rq;
-                            ++s_nown;
-                            rlen += reg;
-                            rq += (len + 3) >> 2;
-                        }
-                    }
-                    rank += len;
-                    ++nb;
-                    if (++cb == C) cb = 0;
-                }
-            }
-            ob.rnd[ob.nrnd] = s_nown;
-            // every CTA counts the same nb blocks, and CTA 0 holds the most
-            // (ceil(nb / C)): the same decision in the whole cluster, with
-            // no exchange
-            s_ovf = (nb + C - 1) / C > GAP_CAP;
+            const int nb = assign_gap_blocks(ob, s_nown, g_beg, g_end, ngap, lmax, C, c, s_blen, s_brank, s_bord);
+            s_ovf = nb > GAP_CAP;      // the same in every CTA
         }
         if (!prec && threadIdx.x == 0) s_ovf = 1;
         __syncthreads();
@@ -1554,10 +1580,11 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             double rz = rr2.y;
             const double stop = static_cast<double>(a.tol) * a.tol * rr2.x;
             conv = rr2.x == 0.0;
-            // y = sum_i alpha_i p_i is never formed: the correction B^{-1} E y
-            // = C^T diag(beta) sum_i alpha_i (C E p_i) is built from the spectra
-            // C E p_i the iterations compute anyway, accumulated per packed
-            // slot in acc (x, y: sum so far; z, w: the latest spectrum, whose
+            // y = sum_i alpha_i p_i is never formed: x = x0 + B^{-1} E y
+            // = C^T diag(beta) (cb + sum_i alpha_i C E p_i), with cb the
+            // spectrum of x0 before the filter and C E p_i the spectra the
+            // iterations compute anyway, accumulated per packed slot in acc
+            // (x, y: cb plus the sum so far; z, w: the latest spectrum, whose
             // step length is known one iteration later)
             float alp_prev = 0.f;
             while (!conv && it < a.maxit) {
@@ -1567,12 +1594,8 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                 if (dct_forward_pre(sX, cur, oth, cl)) { float2 *t_ = cur; cur = oth; oth = t_; }
                 split_roundtrip(X, cur, [&](int e, int, float2 Y) {
                     const float4 w = wt[e];
-                    if (it == 0) {
-                        acc[e] = make_float4(0.f, 0.f, Y.x, Y.y);
-                    } else {
-                        const float4 A = acc[e];
-                        acc[e] = make_float4(fmaf(alp_prev, A.z, A.x), fmaf(alp_prev, A.w, A.y), Y.x, Y.y);
-                    }
+                    const float4 A = acc[e];          // (z, w) = 0 and alp_prev = 0 at the first
+                    acc[e] = make_float4(fmaf(alp_prev, A.z, A.x), fmaf(alp_prev, A.w, A.y), Y.x, Y.y);
                     return make_float2(Y.x * w.z, Y.y * w.w);
                 });
                 if (dct_inverse_post(sX, cur, oth, cl)) { float2 *t_ = cur; cur = oth; oth = t_; }
@@ -1603,23 +1626,21 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
                 __syncthreads();
                 rz = rn2.y;
             }
-            // x = x0 + B^{-1} E y: the accumulated spectrum, filtered by beta,
-            // one inverse transform (none when y = 0)
-            if (it > 0) {
-                split_inverse_from(X, cur, [&](int e) {
-                    const float4 A = acc[e], w = wt[e];
-                    return make_float2(fmaf(alp_prev, A.z, A.x) * w.x, fmaf(alp_prev, A.w, A.y) * w.y);
-                });
-                if (dct_inverse_post(sX, cur, oth, cl)) { float2 *t_ = cur; cur = oth; oth = t_; }
-                for (int e = threadIdx.x; e < tot; e += DCT_T) {
-                    int t0, t1;
-                    bool valid;
-                    elem_samples(X, e, t0, t1, valid);
-                    if (!valid) continue;
-                    const float2 v = cur[e];
-                    xq[t0] += v.x;
-                    xq[t1] += v.y;
-                }
+            // x from the accumulated spectrum, filtered by beta: one inverse
+            // transform, written once
+            split_inverse_from(X, cur, [&](int e) {
+                const float4 A = acc[e], w = wt[e];
+                return make_float2(fmaf(alp_prev, A.z, A.x) * w.x, fmaf(alp_prev, A.w, A.y) * w.y);
+            });
+            if (dct_inverse_post(sX, cur, oth, cl)) { float2 *t_ = cur; cur = oth; oth = t_; }
+            for (int e = threadIdx.x; e < tot; e += DCT_T) {
+                int t0, t1;
+                bool valid;
+                elem_samples(X, e, t0, t1, valid);
+                if (!valid) continue;
+                const float2 v = cur[e];
+                xq[t0] = v.x;
+                xq[t1] = v.y;
             }
             if (!conv) set_status(a.status, q, TOD_ERR_NOT_CONVERGED);
         }
