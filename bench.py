@@ -102,11 +102,11 @@ def _peaks():
 # DRAM bytes of one n_corr call per TOD sample, from the ncu capture of
 # k_ncorr summarised in profiles/k_ncorr_lfi30_400detscans.md (400 detscans
 # of the 30 GHz band; scaled to a full launch by samples, since the kernel
-# moves each sample's d, s and n_corr once), valid only while the kernel's
-# sources hash to the digest taken with it.
-NCORR_TRAFFIC = {"bytes_per_sample": 12.94,
+# moves each sample's d, s and n_corr once and its scratch in proportion),
+# valid only while the kernel's sources hash to the digest taken with it.
+NCORR_TRAFFIC = {"bytes_per_sample": 17.3,
                  "sources": ["csrc/k_dct.cu", "csrc/common.cuh", "csrc/internal.cuh", "csrc/api.cu"],
-                 "sha256": "3b979cb6b26802b27b8ff9c138577e1a8654c3ea9b0cbc999870451ce66030be"}
+                 "sha256": "a95d75fc8f6ab4b9c9d9f5769a4510f24ec889ea21fecd4f87c3062f56753de9"}
 
 
 def ncorr_sources_digest() -> str:
