@@ -35,6 +35,11 @@ class GibbsTODStep:
         self.map32 = torch.zeros((npix, 4), dtype=f32, device=dev)
         self.rcond = torch.zeros(npix, dtype=f64, device=dev)
         self.valid = torch.zeros(npix, dtype=torch.uint8, device=dev)
+        # each step decodes the next step's pointing under its n_corr draw
+        # (a spare pix/psi pair); the last step's lookahead is extra work
+        self.lookahead = True
+        self._pointing_ready = False
+        self._pix_next = self._psi_next = None
 
     def set_tod(self, d, stream=None):
         """Copy this band's detector data (host numpy float32 or a tensor)."""
@@ -63,6 +68,18 @@ class GibbsTODStep:
             self._d_spare.copy_(d_host, non_blocking=True)
         self._copied = torch.cuda.Event()
         self._copied.record(cs)
+
+    def _streams(self):
+        """(high-priority stream for the step, side stream for the n_corr
+        preparation, low-priority stream for the next step's decode)."""
+        import torch
+        if getattr(self, "_hp", None) is None:
+            lo_pri, hi_pri = torch.cuda.Stream.priority_range()
+            dev = self.d.device
+            self._hp = torch.cuda.Stream(device=dev, priority=hi_pri)
+            self._side = torch.cuda.Stream(device=dev, priority=hi_pri)
+            self._lo = torch.cuda.Stream(device=dev, priority=lo_pri)
+        return self._hp, self._side, self._lo
 
     def _stream(self, stream):
         import torch
@@ -99,28 +116,49 @@ class GibbsTODStep:
         self._take_prefetched(stream)
         p = self.plan
         st = self._stream(stream)
+        hp, side, lo = self._streams()
+        # the step's own work runs on a high-priority stream ordered after
+        # the caller's; the caller's stream waits for all of it at the end
+        hp.wait_stream(st)
         # the n_corr gap preconditioner depends on the PSD alone: it is built
         # on a side stream while decode, projection and the gain draw run
         # (after everything already queued, so the previous step's draw has
         # finished with the old tables)
-        if getattr(self, "_side", None) is None:
-            self._side = torch.cuda.Stream(device=self.d.device)
-        side = self._side
         side.wait_stream(st)
         p.ncorr_prepare(self.psd, side)
         prepared = torch.cuda.Event()
         prepared.record(side)
-        p.decode(self.pix, self.psi, stream)
-        p.project(map32_in, self.pix, self.psi, None, self.s, stream)
-        p.sample_gain(self.d, self.s, self.flags, self.psd, rng, mode, self.gain, self.mu, self.sigma,
-                      stream)
-        st.wait_event(prepared)
+        if self._pointing_ready:
+            # decoded by the previous step, under its n_corr draw
+            self.pix, self._pix_next = self._pix_next, self.pix
+            self.psi, self._psi_next = self._psi_next, self.psi
+            self._pointing_ready = False
+        else:
+            p.decode(self.pix, self.psi, hp)
+        p.project(map32_in, self.pix, self.psi, None, self.s, hp)
+        p.sample_gain(self.d, self.s, self.flags, self.psd, rng, mode, self.gain, self.mu, self.sigma, hp)
+        hp.wait_event(prepared)
+        lookahead = self.lookahead
+        if lookahead:
+            gained = torch.cuda.Event()
+            gained.record(hp)
         p.sample_ncorr_prepared(self.d, self.s, self.gain, self.flags, self.psd, rng, mode, self.ncorr,
-                                self.cg_iters, self.cg_tol, self.cg_maxiter, stream)
-        p.bin(self.psi, self.d, self.ncorr, self.gain, self.flags, self.psd, self.A, self.b, self.hits,
-              stream)
+                                self.cg_iters, self.cg_tol, self.cg_maxiter, hp)
+        if lookahead:
+            # the next step's pointing (the compressed streams do not change),
+            # decoded at low priority on the SMs the n_corr clusters leave idle
+            if self._pix_next is None:
+                self._pix_next = torch.empty_like(self.pix)
+                self._psi_next = torch.empty_like(self.psi)
+            lo.wait_event(gained)
+            p.decode(self._pix_next, self._psi_next, lo)
+            self._pointing_ready = True
+        p.bin(self.psi, self.d, self.ncorr, self.gain, self.flags, self.psd, self.A, self.b, self.hits, hp)
         p.solve_maps(self.A, self.b, self.hits, self.rcond_min, self.map, self.map32, self.rcond,
-                     self.valid, stream)
+                     self.valid, hp)
+        st.wait_stream(hp)
+        if lookahead:
+            st.wait_stream(lo)
         self._mark_d_done(stream)
 
     LAUNCHES_PER_STEP = 11  # decode x2, project, gain + draw, Toeplitz prep x2, ncorr, bin + reduce, solve
@@ -132,6 +170,9 @@ class GibbsTODStep:
         self.iter_dev = torch.zeros(1, dtype=torch.int64, device=self.d.device)
         self._rng_graph = Rng(seed, band, 0, self.iter_dev.data_ptr())
         self._map_graph = map32_in
+        # the captured step decodes its own pointing (no lookahead across replays)
+        saved_lookahead = self.lookahead
+        self.lookahead = False
         side = torch.cuda.Stream(device=self.d.device)
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):
@@ -140,6 +181,7 @@ class GibbsTODStep:
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.graph):
             self.run(map32_in, self._rng_graph, mode)
+        self.lookahead = saved_lookahead
         return self.graph
 
     def replay(self, it: int):

@@ -10,7 +10,9 @@
 * steps whose detector data is prefetched into a second buffer on a copy
   stream give bit for bit the steps of plain copies;
 * the n_corr draw split in preparation (on a side stream) and prepared draw
-  gives bit for bit the one-call draw.
+  gives bit for bit the one-call draw;
+* steps that decode the next step's pointing ahead give bit for bit the
+  steps that decode their own.
 """
 import numpy as np
 import pytest
@@ -160,3 +162,28 @@ def test_prepared_ncorr_matches_sample_ncorr():
     assert outs[0][1].max() > 0                  # the CG (and its preconditioner) ran
     assert np.array_equal(outs[0][0], outs[1][0])
     assert np.array_equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.gpu
+def test_pointing_lookahead_matches_in_step_decode(tiny):
+    """Steps that decode the next step's pointing under their n_corr draw
+    (GibbsTODStep.lookahead) give bit for bit the steps that decode in step."""
+    import torch
+    import paper_2201_03509_gb300 as tg
+    from paper_2201_03509_gb300.step import GibbsTODStep
+    wl = tiny
+    outs = []
+    for lookahead in (False, True):
+        step = GibbsTODStep(wl.plan, wl.band.psd, wl.ing["flag_words"])
+        step.lookahead = lookahead
+        step.set_tod(wl.d32)
+        got = []
+        for k in range(3):
+            step.run(wl.t_map, tg.Rng(6, 0, k), tg.MODE_DRAW)
+            torch.cuda.synchronize()
+            got.append([t.clone() for t in (step.pix, step.psi, step.gain, step.ncorr, step.map)])
+        outs.append(got)
+    for k in range(3):
+        for a, b in zip(outs[0][k], outs[1][k]):
+            assert torch.equal(a, b), k
+    wl.plan.status()
