@@ -5,8 +5,8 @@ Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on a
 bounded sample of the same workload instead.  Launched by torchrun for
 N > 1 GPUs: every rank runs an independent replica of the band (the step
 shards by detscan with no exchange but the final map reduction, which this
-single-band benchmark replicates), and the max time over
-ranks is reported.
+single-band benchmark replicates), and the max time over ranks is
+reported.
 """
 from __future__ import annotations
 
@@ -32,6 +32,18 @@ def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     return rank, ws
+
+
+def max_over_ranks(x: float, device="cuda") -> float:
+    """The largest x over the ranks of the default process group (x itself
+    when there is no group or one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 class ClockSampler:
@@ -129,7 +141,7 @@ def make_workload(nscan: int | None):
 
 
 # ---------------------------------------------------------------------------
-# per-stage algorithmic work ("roofline")
+# per-stage algorithmic work (compulsory bytes per stage)
 # ---------------------------------------------------------------------------
 def stage_bytes(N, nq, npix, npairs, comp_bytes):
     """Compulsory HBM bytes of each stage for one step."""
@@ -241,11 +253,7 @@ def run_ours(args):
     stage_ms = {nm: float(np.mean([evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps)]))
                 for i, nm in enumerate(names)}
     iters = step.cg_iters.cpu().numpy()
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed)
 
     # the same step captured in a CUDA graph (iteration read on the device)
     graph_ms = None
@@ -300,7 +308,7 @@ def run_ours(args):
         gain_host.copy_(step.gain, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_s = e0.elapsed_time(e1) / 1e3
+    e2e_s = max_over_ranks(e0.elapsed_time(e1) / 1e3)
 
     # roofline of the dominant stage
     peaks, peak_src = _peaks()

@@ -65,7 +65,8 @@ class BandConfig:
     seed: int = 20220110
 
 
-# Workloads of the benchmark suite (see the design doc for the recipe).
+# Workloads of the benchmark suite: the 30 GHz band is the benchmark's, the
+# others are parity-test cases.
 CONFIGS = {
     "tiny": BandConfig(name="tiny: 1 det x 16 scans x 4096 @32.5Hz, Nside 16",
                        nside=16, ndet=1, nscan=16, fsamp=32.5, len_lo=4096, len_hi=4096,

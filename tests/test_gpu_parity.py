@@ -1,6 +1,6 @@
 """GPU path vs the FP64 oracle, stage by stage, through the C ABI.
 
-Tolerances (derived in the design doc): integer work bit-exact; FP32 timelines
+Tolerances (derived from the FP32 arithmetic): integer work bit-exact; FP32 timelines
 1e-5 relative (l2 per detscan); FP64-accumulated maps 1e-10 relative."""
 import numpy as np
 import pytest
