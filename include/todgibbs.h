@@ -188,7 +188,7 @@ tod_status tod_project(tod_plan *p, const void *map_tqu, const int32_t *pix,
                        const uint16_t *psi, const double *gain, float *s_out,
                        cudaStream_t stream);
 
-/* A4 -- gain draw (Eq. `gibbsstart`, first line; n_corr marginalised, so
+/* A4 -- gain draw (the gain conditional of Eq. `gibbsstart`; n_corr marginalised, so
  * the full noise PSD weights the fit).  Per detscan, with shat = C(M s),
  * dhat = C(M d) the orthonormal DCT-II (the mirrored FFT of Sect. 4.2):
  *   a = sum_{k>=1} shat_k^2 / P_k,  b = sum_{k>=1} shat_k dhat_k / P_k,
@@ -201,7 +201,7 @@ tod_status tod_sample_gain(tod_plan *p, const float *d, const float *s,
                            double *sigma_out, cudaStream_t stream);
 
 /* A5 -- correlated-noise draw with flagged samples inpainted (Eq.
- * `gibbsstart`, second line; Sect. 5: CG gap filling).  Per detscan,
+ * `gibbsstart`, the n_corr conditional; Sect. 5: CG gap filling).  Per detscan,
  * r = d - g s and x solves
  *   (C^T diag(phi) C + M / sigma0^2) x = M r / sigma0^2 + M w1 / sigma0
  *                                        + C^T (sqrt(phi) w2),
@@ -308,8 +308,8 @@ tod_status tod_solve_maps(tod_plan *p, const double *A, const double *b,
                           cudaStream_t stream);
 
 /* A8 -- TOD chi^2 with the correlated noise marginalised, and its
- * gradients (the likelihood of the gain conditional, Eq. `gibbsstart`
- * first line, as a function of map, gains and noise parameters).  Per
+ * gradients (the likelihood of the gain conditional of Eq. `gibbsstart`,
+ * as a function of map, gains and noise parameters).  Per
  * detscan, with rhat = C(M(d - g s)) and P_k the noise PSD:
  *   chi2_out[q]  = 1/2 sum_{k>=1} [ rhat_k^2 / P_k + ln P_k ],
  *   dgain_out[q] = dL/dg_q = -<M s, v>,

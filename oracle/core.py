@@ -407,8 +407,8 @@ def sample_gain(s, d, mask, P, z: float, mode: int = MODE_DRAW) -> tuple:
 def ncorr_rhs(r, mask, sigma0, phi, w1, w2) -> np.ndarray:
     """b = M r / sigma0^2 + M w1 / sigma0 + C^T(sqrt(phi) w2): the standard
     constrained-realisation right-hand side (reading; the paper defers the
-    sampler to its noise companion paper, Eq. `gibbsstart` second line and
-    Sect. 5 on CG gap filling)."""
+    sampler to its noise companion paper: the n_corr conditional of Eq.
+    `gibbsstart` and Sect. 5 on CG gap filling)."""
     M = np.asarray(mask, dtype=np.float64)
     return M * r / sigma0 ** 2 + M * w1 / sigma0 + idct(np.sqrt(phi) * w2)
 
@@ -624,7 +624,7 @@ def chi2_detscan(d, s, gain, mask, sigma0, fknee, alpha, fsamp) -> dict:
     """L = 1/2 sum_{k>=1} [ rhat_k^2 / P_k + ln P_k ],  rhat = C(M (d - g s)),
     the negative log-likelihood of one detscan under the noise model
     P_k = sigma0^2 (1 + (f_k/fknee)^alpha) with n_corr marginalised (the
-    gain conditional's likelihood, paper Eq. `gibbsstart` first line, as a
+    likelihood of the gain conditional of paper Eq. `gibbsstart`, as a
     function of the map, the gain and xi_n).  Returns L and the gradients
     dL/dg, dL/d(sigma0, fknee, alpha), and the per-sample vector
     v = M C^T (rhat / P) with dL/ds = -g v (so dL/dm = -g P^T v)."""

@@ -1,6 +1,7 @@
 // A3 batched DCT-II (the mirrored FFT of paper Sect. 4.2), A4 gain draw and
-// A5 correlated-noise draw (Eq. `gibbsstart`, lines 1-2; Sect. 5 CG gap
-// filling), as persistent thread-block-cluster kernels.
+// A5 correlated-noise draw (the gain and n_corr conditionals of Eq.
+// `gibbsstart`; Sect. 5 CG gap filling), as persistent thread-block-cluster
+// kernels.
 //
 // One cluster of C CTAs owns one detscan at a time (work list sorted by
 // decreasing length; clusters stride through it).  A length-n real DCT-II

@@ -1,5 +1,6 @@
 """Pins of the oracle's gain and correlated-noise steps (readings of paper
-Eq. `gibbsstart` lines 1-2 and Sect. 5 CG gap filling)."""
+the gain and n_corr conditionals of Eq. `gibbsstart` and Sect. 5 CG gap
+filling)."""
 import math
 
 import numpy as np
