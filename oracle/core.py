@@ -31,6 +31,7 @@ CKPT_BLOCK = 512
 PURPOSE_GAIN = 0
 PURPOSE_NC_W1 = 1
 PURPOSE_NC_W2 = 2
+PURPOSE_PSD = 3
 
 MODE_DRAW = 0
 MODE_MEAN = 1
@@ -674,3 +675,79 @@ def chi2_band(map_tqu, pix, psi, d, gains, mask, psd, offsets, ndet, fsamp) -> d
                     np.bincount(pix, weights=gv * c[b_], minlength=npix),
                     np.bincount(pix, weights=gv * sn[b_], minlength=npix)])
     return dict(L=L, dm=dm, dg=dg, dpsd=dpsd)
+
+
+# ============================================================================
+# A10. noise PSD step: (f_knee, alpha) of each detector given n_corr
+# ============================================================================
+#
+# Reading (the paper defers the noise sampler to its noise companion paper;
+# Sect. 5 lists the noise PSD step among the TOD steps, and the Gibbs chain
+# of Eq. `gibbsstart` conditions xi_n on n_corr): with sigma0 held fixed,
+# each detector's (ln f_knee, alpha) is drawn from
+#   p(ln f_knee, alpha | n_corr) ~ L(f_knee, alpha) 1{(ln f_knee, alpha) in BOX},
+#   ln L = -1/2 sum_{q of the detector} sum_{k>=1} [ xhat_{q,k}^2 / Pc_{q,k}
+#                                                      + ln Pc_{q,k} ],
+#   Pc_{q,k} = sigma0^2 (f_{q,k} / f_knee)^alpha,  xhat_q = C n_corr_q,
+# i.e. the Gaussian density of n_corr under its 1/f prior, the offset mode
+# excluded as everywhere (reading 4).  Sampler: nsteps random-walk Metropolis
+# steps on (ln f_knee, alpha) per call.
+
+PSD_BOX = ((math.log(1e-4), math.log(10.0)), (-4.0, -0.25))
+
+
+def psd_loglike(spectra, lengths, fsamp: float, sigma0: float, fknee: float, alpha: float) -> float:
+    """ln L of one detector: spectra[j] = C n_corr of its j-th detscan (the
+    orthonormal DCT-II, length lengths[j]), modes k >= 1; the definition
+    above, term by term in FP64."""
+    tot = 0.0
+    for xh, n in zip(spectra, lengths):
+        f = dct_freqs(int(n), fsamp)[1:]
+        Pc = sigma0 ** 2 * (f / fknee) ** alpha
+        x = np.asarray(xh, np.float64)[1:int(n)]
+        tot += float(np.sum(x * x / Pc + np.log(Pc)))
+    return -0.5 * tot
+
+
+def psd_proposal(seed: int, band: int, det: int, step: int, it: int) -> tuple:
+    """The random numbers of Metropolis step `step` of detector det at Gibbs
+    iteration it: Philox block (step, det, PSD, it) with key (seed, band);
+    words 0 and 1 give 53-bit uniforms u1, u2 and the normal pair
+    (sqrt(-2 ln u1) cos 2 pi u2, sqrt(-2 ln u1) sin 2 pi u2); word 2 gives
+    the 53-bit acceptance uniform."""
+    w = philox4x64([step, det, PURPOSE_PSD, it], [seed, band])
+    u1 = (float(w[0] >> np.uint64(11)) + 0.5) * 2.0 ** -53
+    u2 = (float(w[1] >> np.uint64(11)) + 0.5) * 2.0 ** -53
+    ua = (float(w[2] >> np.uint64(11)) + 0.5) * 2.0 ** -53
+    r = math.sqrt(-2.0 * math.log(u1))
+    return r * math.cos(2.0 * math.pi * u2), r * math.sin(2.0 * math.pi * u2), ua
+
+
+def psd_in_box(lnfk: float, alpha: float) -> bool:
+    return PSD_BOX[0][0] <= lnfk <= PSD_BOX[0][1] and PSD_BOX[1][0] <= alpha <= PSD_BOX[1][1]
+
+
+def sample_noise_psd(spectra_by_det, lengths_by_det, fsamp: float, psd, seed: int, band: int, it: int,
+                     nsteps: int, step_lnfk: float, step_alpha: float) -> tuple:
+    """nsteps Metropolis steps on (ln f_knee, alpha) for every detector, from
+    psd[det] = (sigma0, f_knee, alpha).  Step s proposes (ln f_knee + step_lnfk
+    z1, alpha + step_alpha z2) with (z1, z2, u) = psd_proposal(..., s, it) and
+    accepts iff the proposal is in PSD_BOX and ln u < ln L(proposal) -
+    ln L(current).  Returns (psd_out (ndet, 3), accepted counts (ndet,))."""
+    psd = np.array(psd, dtype=np.float64, copy=True)
+    acc = np.zeros(len(psd), dtype=np.int64)
+    for det in range(len(psd)):
+        s0, fk, al = psd[det]
+        lnfk = math.log(fk)
+        cur = psd_loglike(spectra_by_det[det], lengths_by_det[det], fsamp, s0, fk, al)
+        for step in range(nsteps):
+            z1, z2, ua = psd_proposal(seed, band, det, step, it)
+            lp, ap = lnfk + step_lnfk * z1, al + step_alpha * z2
+            if not psd_in_box(lp, ap):
+                continue
+            new = psd_loglike(spectra_by_det[det], lengths_by_det[det], fsamp, s0, math.exp(lp), ap)
+            if math.log(ua) < new - cur:
+                lnfk, al, cur = lp, ap, new
+                acc[det] += 1
+        psd[det, 1], psd[det, 2] = math.exp(lnfk), al
+    return psd, acc
