@@ -310,6 +310,40 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(e0.elapsed_time(e1) / 1e3)
 
+    # row A10 (outside the step's value): the n_corr draw writing its
+    # spectra, then the noise-PSD Metropolis step on them
+    psd_info = None
+    if not args.no_psd:
+        spec = torch.empty(N, dtype=torch.float32, device=step.d.device)
+        psd_out = torch.empty_like(step.psd)
+        acc = torch.zeros(plan.ndet, dtype=torch.int32, device=step.d.device)
+        rng = tg.Rng(args.seed, 0, 60_000)
+        plan.set_ncorr_spectrum(spec)
+        plan.ncorr_prepare(step.psd)
+        ts = []
+        for k in range(2):
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            plan.sample_ncorr_prepared(step.d, step.s, step.gain, step.flags, step.psd, rng, tg.MODE_DRAW,
+                                       step.ncorr, step.cg_iters, step.cg_tol, step.cg_maxiter)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a0.elapsed_time(a1))
+        plan.set_ncorr_spectrum(None)
+        nst = 10
+        plan.sample_noise_psd(spec, step.psd, rng, nst, 2e-4, 2e-4, psd_out, acc)      # warm-up
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        plan.sample_noise_psd(spec, step.psd, rng, nst, 2e-4, 2e-4, psd_out, acc)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        plan.status()
+        psd_ms = b0.elapsed_time(b1)
+        per_eval = psd_ms / (nst + 1)
+        psd_info = {"ncorr_with_spectrum_ms": min(ts), "metropolis_steps": nst, "ms": psd_ms,
+                    "ms_per_evaluation": per_eval, "gbs_per_evaluation": 4.0 * N / (per_eval / 1e3) / 1e9,
+                    "accepted": acc.cpu().tolist()}
+
     # roofline of the dominant stage
     peaks, peak_src = _peaks()
     comp = int(ing["pix_streams"]["words"].nbytes + ing["psi_streams"]["words"].nbytes)
@@ -361,6 +395,7 @@ def run_ours(args):
         "plain_per_scan": ({"ms_per_step": plain_ms, "value": N / (plain_ms / 1e3),
                             "speedup_batched": plain_ms / (1e3 * elapsed / args.steps)}
                            if plain_ms else None),
+        "noise_psd": psd_info,
         "device_status_errors": int(np.count_nonzero(st)),
         "roofline": roof, "clocks": clocks, "setup_s": setup_s,
     }
@@ -461,6 +496,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the per-scan comparison step")
     ap.add_argument("--no-autotune", action="store_true", help="use the plan's default launch shape")
+    ap.add_argument("--no-psd", action="store_true", help="skip the noise-PSD step measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

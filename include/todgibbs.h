@@ -322,6 +322,45 @@ tod_status tod_chi2(tod_plan *p, const float *d, const float *s, const double *g
                     const uint32_t *flags, const double *psd, double *chi2_out,
                     double *dgain_out, double *dpsd_out, float *v_out, cudaStream_t stream);
 
+/* A10 -- noise PSD step (Sect. 5 lists it among the TOD steps; the paper
+ * defers the sampler to its noise companion paper, so this is a reading):
+ * with sigma0 held fixed, nsteps random-walk Metropolis steps on
+ * (ln f_knee, alpha) of every detector, targeting
+ *   ln L = -1/2 sum_{q of the detector} sum_{k>=1} [ xhat_{q,k}^2 / Pc_{q,k}
+ *                                                    + ln Pc_{q,k} ],
+ *   Pc_{q,k} = sigma0^2 (f_{q,k} / f_knee)^alpha,  f_{q,k} = k fsamp / (2 n_q),
+ * (the Gaussian density of the n_corr draw xhat = C n_corr under its 1/f
+ * prior, offset mode excluded) times a flat prior on the box
+ * [TOD_PSD_LNFK_MIN, TOD_PSD_LNFK_MAX] x [TOD_PSD_ALPHA_MIN, TOD_PSD_ALPHA_MAX].
+ * Step s proposes (ln f_knee + step_lnfknee z1, alpha + step_alpha z2) and
+ * accepts iff the proposal is in the box and ln u < ln L(proposal) - ln L(current);
+ * z1, z2, u come from Philox block (s, det, TOD_PURPOSE_PSD, iteration) with
+ * key (seed, band): 53-bit uniforms of words 0 and 1 give the Box-Muller
+ * pair (cos, sin), word 2 the uniform u.
+ *   spec: float32[N] (device), each detscan's orthonormal DCT-II coefficients
+ *   of its n_corr draw in mode order (spec[off_q + k] = xhat_{q,k}), as the
+ *   n_corr draws write them once tod_plan_set_ncorr_spectrum is set.
+ *   psd_in, psd_out: double[ndet][3] (sigma0, f_knee, alpha), device, distinct.
+ *   accepted_out: int32[ndet] or NULL; loglike_out: double[ndet] (ln L of the
+ *   final state) or NULL.  nsteps >= 0 (0: psd_out = psd_in).
+ * ln L from FP32 products summed as FP32 double-words and FP64 per tile;
+ * the decisions in FP64.  Deterministic.  The plan holds the chain's state:
+ * calls on one plan must not overlap. */
+#define TOD_PURPOSE_PSD 3
+#define TOD_PSD_LNFK_MIN (-9.2103403719761836)   /* ln 1e-4 (f_knee in Hz) */
+#define TOD_PSD_LNFK_MAX 2.3025850929940457      /* ln 10 */
+#define TOD_PSD_ALPHA_MIN (-4.0)
+#define TOD_PSD_ALPHA_MAX (-0.25)
+tod_status tod_sample_noise_psd(tod_plan *p, const float *spec, const double *psd_in, tod_rng rng,
+                                int32_t nsteps, double step_lnfknee, double step_alpha,
+                                double *psd_out, int32_t *accepted_out, double *loglike_out,
+                                cudaStream_t stream);
+/* The buffer (device float32[N], or NULL to stop) into which every
+ * following n_corr draw of this plan (tod_sample_ncorr and its variants)
+ * also writes the orthonormal DCT-II coefficients of its draw, in mode
+ * order per detscan; no counterpart in the paper (it feeds A10). */
+tod_status tod_plan_set_ncorr_spectrum(tod_plan *p, float *spec_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -67,7 +67,7 @@ SYMBOLS = ["tod_status_string", "tod_fft_length", "tod_huff_encode", "tod_huff_f
            "tod_plan_create", "tod_plan_destroy", "tod_plan_info", "tod_plan_status",
            "tod_plan_set_schedule", "tod_chi2", "tod_decode", "tod_project", "tod_sample_gain", "tod_sample_ncorr", "tod_bin",
            "tod_solve_maps", "tod_ncorr_static_setup", "tod_sample_ncorr_static", "tod_ncorr_prepare",
-           "tod_sample_ncorr_prepared"]
+           "tod_sample_ncorr_prepared", "tod_sample_noise_psd", "tod_plan_set_ncorr_spectrum"]
 
 
 def build(force: bool = False) -> str:
@@ -107,6 +107,8 @@ def lib():
         L.tod_sample_ncorr_static.argtypes = [_P, _P, _P, _P, _P, _P, Rng, _i32, _f64, _i32, _P, _P, _P]
         L.tod_ncorr_prepare.argtypes = [_P, _P, _P]
         L.tod_sample_ncorr_prepared.argtypes = [_P, _P, _P, _P, _P, _P, Rng, _i32, _f64, _i32, _P, _P, _P]
+        L.tod_sample_noise_psd.argtypes = [_P, _P, _P, Rng, _i32, _f64, _f64, _P, _P, _P, _P]
+        L.tod_plan_set_ncorr_spectrum.argtypes = [_P, _P]
         for name in SYMBOLS:
             if name not in ("tod_status_string", "tod_fft_length", "tod_huff_free"):
                 getattr(L, name).restype = _i32
@@ -299,6 +301,21 @@ class Plan:
         _check(lib().tod_sample_ncorr_prepared(self._h, _ptr(d), _ptr(s), _ptr(gain), _ptr(flags), _ptr(psd),
                                                rng, mode, float(cg_tol), int(cg_maxiter), _ptr(ncorr_out),
                                                _ptr(cg_iters_out), _stream(stream)), "tod_sample_ncorr_prepared")
+
+    def set_ncorr_spectrum(self, spec_out):
+        """Every following n_corr draw also writes its orthonormal DCT-II
+        coefficients into spec_out (float32[N], mode order per detscan);
+        None stops it.  The plan keeps a reference to the tensor."""
+        self._spec_ref = spec_out
+        _check(lib().tod_plan_set_ncorr_spectrum(self._h, _ptr(spec_out)), "tod_plan_set_ncorr_spectrum")
+
+    def sample_noise_psd(self, spec, psd_in, rng: Rng, nsteps: int, step_lnfknee: float, step_alpha: float,
+                         psd_out, accepted_out=None, loglike_out=None, stream=None):
+        """nsteps Metropolis steps on (ln f_knee, alpha) of every detector
+        from the n_corr spectra (row A10; see the header for the target)."""
+        _check(lib().tod_sample_noise_psd(self._h, _ptr(spec), _ptr(psd_in), rng, int(nsteps), float(step_lnfknee),
+                                          float(step_alpha), _ptr(psd_out), _ptr(accepted_out), _ptr(loglike_out),
+                                          _stream(stream)), "tod_sample_noise_psd")
 
     def ncorr_static_setup(self) -> int:
         """Look up the fixed scratch array of sample_ncorr_static on this

@@ -611,6 +611,34 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
         if ((e = dev_upload(*p, p->tile_q, tq.data(), tq.size()))) return fail(e);
         if ((e = dev_upload(*p, p->tile_t0, t0.data(), t0.size()))) return fail(e);
     }
+    // noise PSD step: ln k as FP32 pairs, ln(fsamp / (2 n_q)), and per
+    // detector the mode count and sum of ln f_k (k >= 1), all from FP64
+    {
+        int64_t kmax = 1;
+        for (int q = 0; q < p->nq; ++q) kmax = std::max<int64_t>(kmax, p->h_off[q + 1] - p->h_off[q]);
+        std::vector<float2> lnk(static_cast<size_t>(kmax));
+        for (int64_t k = 0; k < kmax; ++k) {
+            const double l = k > 0 ? std::log(static_cast<double>(k)) : 0.0;
+            const float hi = static_cast<float>(l);
+            lnk[k] = make_float2(hi, static_cast<float>(l - static_cast<double>(hi)));
+        }
+        std::vector<double> lnfs(p->nq), nmodes(p->ndet, 0.0), sumlnf(p->ndet, 0.0);
+        for (int q = 0; q < p->nq; ++q) {
+            const int64_t n = p->h_off[q + 1] - p->h_off[q];
+            lnfs[q] = n > 0 ? std::log(p->fsamp / (2.0 * static_cast<double>(n))) : 0.0;
+            if (n < 2) continue;
+            nmodes[q % p->ndet] += static_cast<double>(n - 1);
+            sumlnf[q % p->ndet] += std::lgamma(static_cast<double>(n)) + static_cast<double>(n - 1) * lnfs[q];
+        }
+        if ((e = dev_upload(*p, p->lnk, lnk.data(), lnk.size()))) return fail(e);
+        if ((e = dev_upload(*p, p->lnfs, lnfs.data(), lnfs.size()))) return fail(e);
+        if ((e = dev_upload(*p, p->psd_nmodes, nmodes.data(), nmodes.size()))) return fail(e);
+        if ((e = dev_upload(*p, p->psd_sumlnf, sumlnf.data(), sumlnf.size()))) return fail(e);
+        if ((e = dev_upload(*p, p->psd_part, static_cast<double *>(nullptr), static_cast<size_t>(p->ntile))))
+            return fail(e);
+        if ((e = dev_upload(*p, p->psd_state, static_cast<double *>(nullptr), static_cast<size_t>(p->ndet) * 8)))
+            return fail(e);
+    }
     // psi table: FP32 values of cos 2psi, sin 2psi at the bin centres
     {
         std::vector<float2> trig(TOD_N_PSI);
@@ -972,6 +1000,25 @@ tod_status tod_sample_ncorr_prepared(tod_plan *pl, const float *d, const float *
     const int maxit = cg_maxiter > 0 ? cg_maxiter : 500;
     return to_status(launch_ncorr(*p, d, s, gain, flags, psd, rng, mode, tol, maxit, ncorr_out,
                                   cg_iters_out, stream, 0, p->nq, false));
+}
+
+tod_status tod_plan_set_ncorr_spectrum(tod_plan *pl, float *spec_out)
+{
+    if (!pl) return TOD_ERR_ARG;
+    reinterpret_cast<Plan *>(pl)->spec_out = spec_out;
+    return TOD_OK;
+}
+
+tod_status tod_sample_noise_psd(tod_plan *pl, const float *spec, const double *psd_in, tod_rng rng,
+                                int32_t nsteps, double step_lnfknee, double step_alpha, double *psd_out,
+                                int32_t *accepted_out, double *loglike_out, cudaStream_t stream)
+{
+    if (!pl || !spec || !psd_in || !psd_out || psd_out == psd_in || nsteps < 0) return TOD_ERR_ARG;
+    if (!(step_lnfknee >= 0.0) || !(step_alpha >= 0.0)) return TOD_ERR_ARG;
+    Plan *p = reinterpret_cast<Plan *>(pl);
+    DeviceGuard dg(p->device);
+    return to_status(launch_noise_psd(*p, spec, psd_in, rng, nsteps, step_lnfknee, step_alpha, psd_out,
+                                      accepted_out, loglike_out, stream));
 }
 
 tod_status tod_bin(tod_plan *pl, const uint16_t *psi, const float *d, const float *ncorr,

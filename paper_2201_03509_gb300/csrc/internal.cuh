@@ -98,6 +98,14 @@ struct Plan {
     int32_t schedule = TOD_SCHED_PERSISTENT;
     int32_t nbin_tiles = 0;          // binning tiles (whole runs of one detscan)
     double2 *gain_ab = nullptr;      // [nq] (a, b) of each detscan's gain conditional (scratch)
+    // noise PSD step
+    float *spec_out = nullptr;       // caller's buffer for the n_corr spectra (NULL: not written)
+    float2 *lnk = nullptr;           // [longest detscan] ln k as an FP32 pair (hi, lo)
+    double *lnfs = nullptr;          // [nq] ln(fsamp / (2 n_q))
+    double *psd_nmodes = nullptr;    // [ndet] modes k >= 1 of the detector's detscans
+    double *psd_sumlnf = nullptr;    // [ndet] sum of ln f_k over them
+    double *psd_part = nullptr;      // [ntile] partial sums of one evaluation
+    double *psd_state = nullptr;     // [ndet][8] chain state
     size_t smem_gain = 0, smem_ncorr = 0;
     // binning
     // Runs: the samples of one (detscan, pixel), in time order; a detscan's
@@ -147,6 +155,9 @@ cudaError_t launch_chi2(const Plan &p, const float *d, const float *s, const dou
                         double *dpsd, float *v, cudaStream_t st);
 cudaError_t setup_bin_kernel(Plan &p);
 cudaError_t launch_toeplitz_prep(const Plan &p, const double *psd, cudaStream_t st);
+cudaError_t launch_noise_psd(const Plan &p, const float *spec, const double *psd_in, tod_rng rng, int nsteps,
+                             double step_lnfk, double step_al, double *psd_out, int32_t *acc_out,
+                             double *loglike_out, cudaStream_t st);
 cudaError_t launch_bin(const Plan &p, const uint16_t *psi, const float *d, const float *ncorr,
                        const double *gain, const uint32_t *flags, const double *psd, double *A,
                        double *b, int32_t *hits, cudaStream_t st);

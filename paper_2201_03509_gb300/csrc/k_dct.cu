@@ -457,9 +457,9 @@ __device__ __forceinline__ void split_roundtrip(const Geo &XS, float2 *__restric
 }
 
 // The inverse split alone, from packed orthonormal coefficients given per
-// element: f(e) is the coefficient pair of element e (modes k and n - k, or
-// 0 and m); writes Z into this CTA's row pairs of U, as the second half of
-// split_roundtrip does.
+// element: f(e, k) is the coefficient pair of element e (modes k and n - k,
+// or 0 and m when k = 0); writes Z into this CTA's row pairs of U, as the
+// second half of split_roundtrip does.
 template <class F>
 __device__ __forceinline__ void split_inverse_from(const Geo &XS, float2 *__restrict__ U, F f)
 {
@@ -477,14 +477,14 @@ __device__ __forceinline__ void split_inverse_from(const Geo &XS, float2 *__rest
         if (p == 0) { q1 = 0; q2 = (k2 == 0) ? 0 : m2 - k2; ib = 2 * pl * m2p + q2; }
         else { q1 = m1 - p; q2 = m2 - 1 - k2; ib = ((q1 == p) ? 2 * pl : 2 * pl + 1) * m2p + q2; }
         const int ia = 2 * pl * m2p + k2;
-        const float2 Ya = f(ia);
+        const float2 Ya = f(ia, p + m1 * k2);
         if (p == 0 && k2 == 0) {
             const float V0 = Ya.x * s0i, Vm = Ya.y * s0i;
             U[ia] = make_float2(0.5f * (V0 + Vm), 0.5f * (V0 - Vm));
             continue;
         }
         if (ib != ia) {
-            const float2 Yb = f(ib);
+            const float2 Yb = f(ib, q1 + m1 * q2);
             U[ib] = split_inv_one(X, Yb, Ya, q1, q2, p, k2, sqi);
             U[ia] = split_inv_one(X, Ya, Yb, p, k2, q1, q2, sqi);
         } else {
@@ -1337,6 +1337,38 @@ __device__ __noinline__ void apply_gap_precond(const OwnBlocks &ob, float *c_r, 
     cl.sync();     // every scatter into every CTA's c_z is done, and every slot is published
 }
 
+// The orthonormal DCT-II coefficients of this CTA's modes of the draw,
+// diag(beta) (acc.xy + alp acc.zw), into spec in mode order (spec[k], k of
+// the detscan); out of line, for callers that asked for the spectra.
+__device__ __noinline__ void write_spectrum(const Ctx &XS, float *__restrict__ spec, const float4 *acc,
+                                            const float4 *wt, float alp)
+{
+    const Geo X = XS;
+    const int n = X.n, m = X.m, m2 = X.m2, m2p = X.m2p, m1 = X.m1, p0 = X.p0;
+    const int total = X.npl * m2;
+    for (int e = threadIdx.x; e < total; e += DCT_T) {
+        const int pl = fdiv(e, X.f_m2), k2 = e - pl * m2;
+        const int p = p0 + pl;
+        const int cnt = (p == 0) ? (m2 / 2 + 1) : ((2 * p == m1) ? (m2 + 1) / 2 : m2);
+        if (k2 >= cnt) continue;
+        int ib, q1, q2;
+        if (p == 0) { q1 = 0; q2 = (k2 == 0) ? 0 : m2 - k2; ib = 2 * pl * m2p + q2; }
+        else { q1 = m1 - p; q2 = m2 - 1 - k2; ib = ((q1 == p) ? 2 * pl : 2 * pl + 1) * m2p + q2; }
+        const int ia = 2 * pl * m2p + k2;
+        const int ka = p + m1 * k2, kb = q1 + m1 * q2;
+        {
+            const float4 A = acc[ia], w = wt[ia];
+            spec[ka] = fmaf(alp, A.z, A.x) * w.x;
+            spec[ka == 0 ? m : n - ka] = fmaf(alp, A.w, A.y) * w.y;
+        }
+        if (ib != ia && !(p == 0 && k2 == 0)) {
+            const float4 A = acc[ib], w = wt[ib];
+            spec[kb] = fmaf(alp, A.z, A.x) * w.x;
+            spec[n - kb] = fmaf(alp, A.w, A.y) * w.y;
+        }
+    }
+}
+
 struct NcorrArgs {
     const float *d, *s;
     const double *gain;
@@ -1358,6 +1390,7 @@ struct NcorrArgs {
     int32_t *iters;
     int32_t *status;
     float4 *wscratch;
+    float *spec_out;          // spectra of the draws in mode order (NULL: not written)
     const float *xtab;       // Toeplitz inverses' first columns per detector (NULL: no preconditioner)
     const int32_t *lvalid;
     int sz, m1max, m2max, twsz;
@@ -1538,6 +1571,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
         const bool use_prec = s_ovf == 0;
         int it = 0;
         bool conv = true;
+        float alp_spec = 0.f;      // the draw's spectrum is diag(beta) (acc.xy + alp_spec acc.zw)
         if (kc_all > 0 && cap_ovf) {
             conv = false;      // too many flagged samples for the CG buffers: left as x0
             set_status(a.status, q, TOD_ERR_NOT_CONVERGED);
@@ -1629,10 +1663,11 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             }
             // x from the accumulated spectrum, filtered by beta: one inverse
             // transform, written once
-            split_inverse_from(X, cur, [&](int e) {
+            split_inverse_from(X, cur, [&](int e, int) {
                 const float4 A = acc[e], w = wt[e];
                 return make_float2(fmaf(alp_prev, A.z, A.x) * w.x, fmaf(alp_prev, A.w, A.y) * w.y);
             });
+            alp_spec = alp_prev;
             if (dct_inverse_post(sX, cur, oth, cl)) { float2 *t_ = cur; cur = oth; oth = t_; }
             for (int e = threadIdx.x; e < tot; e += DCT_T) {
                 int t0, t1;
@@ -1645,6 +1680,7 @@ __global__ void __launch_bounds__(DCT_T, 1) k_ncorr(NcorrArgs a)
             }
             if (!conv) set_status(a.status, q, TOD_ERR_NOT_CONVERGED);
         }
+        if (a.spec_out) write_spectrum(sX, a.spec_out + o, acc, wt, alp_spec);
         if (a.iters && c == 0 && threadIdx.x == 0) a.iters[q] = it;
         // No barrier here: every remote access of this detscan (transposes,
         // CG gathers and scatters, preconditioner) is followed by a cluster
@@ -1932,6 +1968,8 @@ cudaError_t launch_ncorr_scratch(const Plan &p, const float *d, const float *s, 
     a.work_count = work_count; a.ndet = p.ndet; a.fsamp = p.fsamp; a.rng = rng; a.mode = mode;
     a.tol = tol; a.maxit = maxit; a.x_out = x; a.iters = iters; a.status = p.status; a.sz = p.sz;
     a.wscratch = scratch;
+    a.spec_out = p.spec_out;
+    const void *kfn = reinterpret_cast<const void *>(k_ncorr);
     a.xtab = p.use_prec ? p.xtab : nullptr;
     a.lvalid = p.lvalid;
     if (p.use_prec && prepare) {
@@ -1943,13 +1981,13 @@ cudaError_t launch_ncorr_scratch(const Plan &p, const float *d, const float *s, 
         for (int w = 0; w < work_count; ++w) {
             a.work_begin = work_begin + w;
             a.work_count = 1;
-            cudaError_t e = launch_cluster(reinterpret_cast<const void *>(k_ncorr), &a, p.C, 1, p.smem_ncorr, st);
+            cudaError_t e = launch_cluster(kfn, &a, p.C, 1, p.smem_ncorr, st);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
     }
     const int ncl = std::min(work_count, std::min(p.nclusters_ncorr, nclusters_max));
-    return launch_cluster(reinterpret_cast<const void *>(k_ncorr), &a, p.C, ncl, p.smem_ncorr, st);
+    return launch_cluster(kfn, &a, p.C, ncl, p.smem_ncorr, st);
 }
 
 }  // namespace tg
