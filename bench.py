@@ -116,9 +116,9 @@ def _peaks():
 # of the 30 GHz band; scaled to a full launch by samples, since the kernel
 # moves each sample's d, s and n_corr once and its scratch in proportion),
 # valid only while the kernel's sources hash to the digest taken with it.
-NCORR_TRAFFIC = {"bytes_per_sample": 17.3,
+NCORR_TRAFFIC = {"bytes_per_sample": 15.82,
                  "sources": ["csrc/k_dct.cu", "csrc/common.cuh", "csrc/internal.cuh", "csrc/api.cu"],
-                 "sha256": "47167a89ac64cfe732fba94c3002aefbc244291548ec3d1934718a72b564cc5c"}
+                 "sha256": "7bf7c2192103d614209bf42e70955727bcb49d28fb38d3488403cd3fe0069254"}
 
 
 def ncorr_sources_digest() -> str:

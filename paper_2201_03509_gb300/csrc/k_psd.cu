@@ -86,28 +86,47 @@ __global__ void __launch_bounds__(PSD_T) k_psd_sums(const float *__restrict__ sp
     const float na_lo = static_cast<float>(-al - static_cast<double>(na));
     const int64_t o = off[q], t0 = tile_t0[blockIdx.x];
     const int64_t t1 = (t0 + ELEM_TILE < off[q + 1]) ? t0 + ELEM_TILE : off[q + 1];
-    Acc2 acc = {0.f, 0.f};
-    for (int64_t t = t0 + threadIdx.x; t < t1; t += PSD_T) {
-        const int k = static_cast<int>(t - o);
-        if (k == 0) continue;                          // the offset mode does not enter
-        const float x = __ldg(spec + t);
-        const float2 l = __ldg(lnk + k);               // ln k = l.x + l.y
-        // -alpha ln k as a double-float (p + e), then k^-alpha = e^p (1 + e)
-        const float p = na * l.x;
-        const float e = fmaf(na, l.x, -p) + fmaf(na, l.y, na_lo * l.x);
-        const float w = expf(p) * (1.0f + e);
-        acc_add_prod(acc, x * x, w);
+    // four modes per thread and round, every load in flight, four
+    // accumulators merged in a fixed order
+    constexpr int U = 4;
+    Acc2 acc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[u] = Acc2{0.f, 0.f};
+    for (int64_t tb = t0 + threadIdx.x; tb < t1; tb += U * PSD_T) {
+        float x[U];
+        float2 l[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t t = tb + u * PSD_T;
+            const int k = static_cast<int>(t - o);
+            x[u] = 0.f;                                // the offset mode (k = 0) does not enter
+            l[u] = make_float2(0.f, 0.f);
+            if (t < t1 && k > 0) { x[u] = __ldg(spec + t); l[u] = __ldg(lnk + k); }   // ln k = l.x + l.y
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            // -alpha ln k as a double-float (p + e), then k^-alpha = e^p (1 + e)
+            const float p = na * l[u].x;
+            const float e = fmaf(na, l[u].x, -p) + fmaf(na, l[u].y, na_lo * l[u].x);
+            const float w = expf(p) * (1.0f + e);
+            acc_add_prod(acc[u], x[u] * x[u], w);
+        }
+    }
+#pragma unroll
+    for (int u = 1; u < U; ++u) {
+        acc_add(acc[0], acc[u].s);
+        acc[0].c = __fadd_rn(acc[0].c, acc[u].c);
     }
     // fixed-order reduction: warp trees, then the warps in order (thread 0, FP64)
 #pragma unroll
     for (int ofs = 16; ofs; ofs >>= 1) {
         Acc2 o2;
-        o2.s = __shfl_xor_sync(0xffffffffu, acc.s, ofs);
-        o2.c = __shfl_xor_sync(0xffffffffu, acc.c, ofs);
-        acc_add(acc, o2.s);
-        acc.c = __fadd_rn(acc.c, o2.c);
+        o2.s = __shfl_xor_sync(0xffffffffu, acc[0].s, ofs);
+        o2.c = __shfl_xor_sync(0xffffffffu, acc[0].c, ofs);
+        acc_add(acc[0], o2.s);
+        acc[0].c = __fadd_rn(acc[0].c, o2.c);
     }
-    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc_value(acc);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc_value(acc[0]);
     __syncthreads();
     if (threadIdx.x == 0) {
         double sum = 0.0;
