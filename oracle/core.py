@@ -183,6 +183,25 @@ def decode_band(st: dict, offsets: np.ndarray, ndet: int) -> np.ndarray:
     return out
 
 
+def decode_tod(st: dict, offsets: np.ndarray, ndet: int, scale: np.ndarray) -> np.ndarray:
+    """The detector data from the compressed ADC counts (Sect. 4.1: the
+    TOD is held as differenced, Huffman-coded integers; Listing `tod`:
+    comm_detscan keeps tod as compressed bytes).  Reading (the paper does not
+    print the conversion): the counts c_t are ADC integers and d_t = scale_q
+    c_t, the product in FP64 rounded once to FP32, the precision the step
+    reads d in."""
+    c = decode_band(st, offsets, ndet).astype(np.float64)
+    return (c * per_sample(np.asarray(scale, np.float64), offsets)).astype(np.float32)
+
+
+def decode_flags(st: dict, offsets: np.ndarray, ndet: int, select: int) -> np.ndarray:
+    """The flag mask from the compressed flag words (Sect. 4.1; Listing
+    `tod`: flag kept as compressed bytes).  Reading: sample t is excluded
+    (M_t = 0) when its word has any of the bits in ``select``."""
+    w = decode_band(st, offsets, ndet)
+    return (w & int(select)) != 0
+
+
 # ============================================================================
 # RNG: Philox4x64-10 (Salmon, Moraes, Dror, Shaw 2011) + Box-Muller
 # ============================================================================
@@ -546,9 +565,10 @@ def solve_maps(A6: np.ndarray, b3: np.ndarray, hits: np.ndarray, rcond_min: floa
 # the whole step, A1..A7
 # ============================================================================
 
-def ingest(band, ndet=None) -> dict:
+def ingest(band, ndet=None, data_streams: bool = False) -> dict:
     """A0 on a synthetic band: truncate every scan to its FFT length and
-    compress its pixel and psi streams.  Returns the arrays the step uses."""
+    compress its pixel and psi streams (with ``data_streams``, its ADC
+    counts and flag words too).  Returns the arrays the step uses."""
     ndet = band.cfg.ndet
     nq = band.ndetscan
     nlen = np.array([fft_length(int(band.scan_len[q // ndet])) for q in range(nq)], dtype=np.int64)
@@ -556,13 +576,22 @@ def ingest(band, ndet=None) -> dict:
     off[1:] = np.cumsum(nlen)
     pix = [np.asarray(band.pix[q][:nlen[q]], np.int64) for q in range(nq)]
     psi = [np.asarray(band.psi[q][:nlen[q]], np.int64) for q in range(nq)]
-    return dict(
+    out = dict(
         offsets=off,
         pix_streams=encode_band_streams(pix, ndet),
         psi_streams=encode_band_streams(psi, ndet),
         tod=np.concatenate([band.tod[q][:nlen[q]] for q in range(nq)]).astype(np.float32),
         flags=np.concatenate([band.flags[q][:nlen[q]] for q in range(nq)]),
     )
+    if data_streams:
+        import synth
+        scale = synth.adc_quantum(band)
+        counts = [synth.adc_counts(band.tod[q][:nlen[q]], scale[q]) for q in range(nq)]
+        words = [synth.flag_words(band.cfg, q, band.flags[q][:nlen[q]]) for q in range(nq)]
+        out.update(tod_streams=encode_band_streams(counts, ndet), tod_scale=scale, tod_counts=counts,
+                   flag_streams=encode_band_streams(words, ndet), flag_words=words,
+                   flag_select=synth.FLAG_SELECT)
+    return out
 
 
 def gibbs_tod_step(ing: dict, band_cfg, npix: int, map_tqu: np.ndarray, psd: np.ndarray,

@@ -30,7 +30,7 @@ from .healpix import ang2pix_ring, pix2ang_ring, nside2npix  # noqa: F401
 N_PSI = 4096
 
 # purposes for the input-generation streams
-_P_MAP, _P_LEN, _P_GAIN, _P_NOISEPAR, _P_FLAGS, _P_WHITE, _P_CORR, _P_SCAN = range(8)
+_P_MAP, _P_LEN, _P_GAIN, _P_NOISEPAR, _P_FLAGS, _P_WHITE, _P_CORR, _P_SCAN, _P_FLAGINFO = range(9)
 
 
 def _gen(seed: int, purpose: int, sub: int = 0) -> np.random.Generator:
@@ -321,6 +321,48 @@ def make_band(cfg: BandConfig, with_noise: bool = True, threads: int | None = No
             pix[q], psi[q], fl[q], tod[q] = a, b, c, e
     return Band(cfg=cfg, npix=npix, map_tqu=m, scan_len=L, gain=gn, psd=psd,
                 pix=pix, psi=psi, flags=fl, tod=tod)
+
+
+# ----------------------------------------------------------------------------
+# integer data streams: ADC counts and quality-flag words (paper Sect. 4.1
+# stores the TOD and the flags as integers that are differenced and Huffman
+# coded like the pointing)
+# ----------------------------------------------------------------------------
+
+# ADC quantum = sigma0 / 100 of the detector: differenced white noise then
+# spans about 140 quanta rms, about 9.2 bits per sample after Huffman coding,
+# the TOD compression the paper's table reports for the 30 GHz channel
+# (361 MB of 8-byte samples to 52 MB).
+ADC_STEPS_PER_SIGMA0 = 100.0
+FLAG_EXCLUDE = 1 << 1       # set on the samples of the flagged gaps (flag_mask)
+FLAG_INFO = 1 << 4          # informational bit on runs of samples; not a reason to exclude
+FLAG_SELECT = 0xF           # the flag-word bits that exclude a sample
+
+
+def adc_quantum(band: "Band") -> np.ndarray:
+    """ADC quantum of every detscan, float64[ndetscan] (detector sigma0 / 100)."""
+    nd = band.cfg.ndet
+    return np.array([band.psd[q % nd, 0] / ADC_STEPS_PER_SIGMA0 for q in range(band.ndetscan)])
+
+
+def adc_counts(tod: np.ndarray, quantum: float) -> np.ndarray:
+    """Digitised timeline: the nearest integer count of tod / quantum, int32."""
+    c = np.rint(np.asarray(tod, dtype=np.float64) / quantum)
+    if np.any(np.abs(c) >= 2 ** 30):
+        raise ValueError("ADC counts out of range")
+    return c.astype(np.int32)
+
+
+def flag_words(cfg: BandConfig, q: int, flagged: np.ndarray) -> np.ndarray:
+    """Quality-flag words of one detscan, int32: FLAG_EXCLUDE on the flagged
+    samples, FLAG_INFO on seeded runs (about 5 % of the samples) anywhere."""
+    n = len(flagged)
+    w = np.where(np.asarray(flagged, dtype=bool), FLAG_EXCLUDE, 0).astype(np.int32)
+    g = _gen(cfg.seed, _P_FLAGINFO, q)
+    for _ in range(max(1, n // 40000)):
+        a = int(g.integers(0, max(1, n)))
+        w[a:a + int(g.integers(100, 4000))] |= FLAG_INFO
+    return w
 
 
 def uniform_draws(seed: int, shape, purpose: int = 99) -> np.ndarray:
