@@ -118,7 +118,7 @@ def _peaks():
 # valid only while the kernel's sources hash to the digest taken with it.
 NCORR_TRAFFIC = {"bytes_per_sample": 15.82,
                  "sources": ["csrc/k_dct.cu", "csrc/common.cuh", "csrc/internal.cuh", "csrc/api.cu"],
-                 "sha256": "7bf7c2192103d614209bf42e70955727bcb49d28fb38d3488403cd3fe0069254"}
+                 "sha256": "15e764c396324dfd1cee10ea09a8ed00a47444e339bc7f9fa6cb6e67208244c7"}
 
 
 def ncorr_sources_digest() -> str:
@@ -344,6 +344,47 @@ def run_ours(args):
                     "ms_per_evaluation": per_eval, "gbs_per_evaluation": 4.0 * N / (per_eval / 1e3) / 1e9,
                     "accepted": acc.cpu().tolist()}
 
+    # compressed TOD and flags (outside the step's value): the same step
+    # decoding d and the flag mask on the device every step
+    ds_info = None
+    if not args.no_data_streams:
+        t_enc = time.time()
+        ingd = tg.ingest_data(band, ing["offsets"])
+        plan.attach_data(ingd["tod_streams"], ingd["tod_scale"], ingd["flag_streams"], ingd["flag_select"])
+        enc_s = time.time() - t_enc
+        dstep = GibbsTODStep(plan, band.psd, None, cg_tol=args.cg_tol, data_streams=True)
+        for k in range(args.warmup):
+            dstep.run(map_in, tg.Rng(args.seed, 0, 70_000 + k), tg.MODE_DRAW)
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for k in range(args.steps):
+            dstep.run(map_in, tg.Rng(args.seed, 0, 70_100 + k), tg.MODE_DRAW)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        ds_ms = c0.elapsed_time(c1) / args.steps
+        dec = {}
+        for name, dd, ff in (("tod", dstep.d, None), ("flags", None, dstep.flags)):
+            tt = []
+            for _ in range(3):
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                plan.decode_data(dd, ff)
+                a1.record(stream)
+                torch.cuda.synchronize()
+                tt.append(a0.elapsed_time(a1))
+            dec[name] = min(tt)
+        plan.status()
+        tod_bytes = int(ingd["tod_streams"]["words"].nbytes)
+        flag_bytes = int(ingd["flag_streams"]["words"].nbytes)
+        ds_info = {"ms_per_step": ds_ms, "value": ws * N / (ds_ms / 1e3),
+                   "decode_tod_ms": dec["tod"], "decode_flags_ms": dec["flags"],
+                   "tod_bits_per_sample": 8.0 * tod_bytes / N, "flag_bits_per_sample": 8.0 * flag_bytes / N,
+                   "resident_bytes_per_sample": {"fp32_d_and_bitmask": 4.125,
+                                                 "compressed": (tod_bytes + flag_bytes) / N},
+                   "launches_per_step": dstep.launches_per_step, "ingest_s": enc_s}
+        del dstep
+
     # roofline of the dominant stage
     peaks, peak_src = _peaks()
     comp = int(ing["pix_streams"]["words"].nbytes + ing["psi_streams"]["words"].nbytes)
@@ -396,6 +437,7 @@ def run_ours(args):
                             "speedup_batched": plain_ms / (1e3 * elapsed / args.steps)}
                            if plain_ms else None),
         "noise_psd": psd_info,
+        "data_streams": ds_info,
         "device_status_errors": int(np.count_nonzero(st)),
         "roofline": roof, "clocks": clocks, "setup_s": setup_s,
     }
@@ -497,6 +539,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the per-scan comparison step")
     ap.add_argument("--no-autotune", action="store_true", help="use the plan's default launch shape")
     ap.add_argument("--no-psd", action="store_true", help="skip the noise-PSD step measurement")
+    ap.add_argument("--no-data-streams", action="store_true",
+                    help="skip the step with compressed TOD and flags")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -105,7 +105,9 @@ typedef struct {
 } tod_huff_buffers;
 
 /* Ingest (host, not on the per-step path): compress one stream kind of a
- * band.  values: HOST int32[offsets[ndetscan]] (pixel indices or psi bins);
+ * band.  values: HOST int32[offsets[ndetscan]] (pixel indices, psi bins,
+ * ADC counts or flag words); every difference of consecutive values of a
+ * detscan must fit in int32 (TOD_ERR_ARG otherwise).
  * offsets: HOST int64[ndet*nscan+1].  Fills *out with malloc'd arrays that
  * the caller releases with tod_huff_free.  Tie rules of the Huffman build:
  * leaves ordered by (count, value); two-queue merge taking the leaf on equal
@@ -178,6 +180,34 @@ tod_status tod_plan_set_schedule(tod_plan *p, int32_t schedule);
  * pix_out int32[N], psi_out uint16[N] (device).  Bit-exact; a stream that
  * does not decode marks its detscan TOD_ERR_CORRUPT_STREAM. */
 tod_status tod_decode(tod_plan *p, int32_t *pix_out, uint16_t *psi_out, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Compressed TOD and quality flags (Sect. 4.1: the ADC integers and the flag
+ * words are differenced and Huffman coded like the pointing; Listing `tod`:
+ * comm_detscan holds tod and flag as compressed bytes).  Both streams use
+ * the tod_huff_streams format above over the plan's offsets.
+ *   tod:   ADC counts c_t (int32); the detector data are
+ *          d_t = fl32(scale_q * c_t), the product in FP64, rounded once.
+ *   flag:  flag words w_t (int32, read as uint32); sample t is flagged
+ *          (M_t = 0) when (w_t & flag_select) != 0.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    tod_huff_streams tod;       /* HOST compressed ADC counts */
+    const double *tod_scale;    /* HOST [ndetscan] ADC quantum of each detscan (> 0, finite) */
+    tod_huff_streams flag;      /* HOST compressed flag words */
+    uint32_t flag_select;       /* flag-word bits that exclude a sample */
+} tod_data_desc;
+
+/* Ingest: copies both streams and their decode tables to the device (once
+ * per plan; TOD_ERR_ARG if already attached or a stream is malformed). */
+tod_status tod_plan_attach_data(tod_plan *p, const tod_data_desc *data);
+
+/* A1 for the data streams: d_out float32[N] (d_t above), flags_out
+ * uint32[(N+31)/32] (the flags layout of this header, fully rewritten:
+ * zeroed, then the flagged bits set).  Either may be NULL, not both.
+ * Bit-exact; TOD_ERR_ARG when nothing is attached; a stream that does not
+ * decode marks its detscan TOD_ERR_CORRUPT_STREAM. */
+tod_status tod_decode_data(tod_plan *p, float *d_out, uint32_t *flags_out, cudaStream_t stream);
 
 /* A2 -- projection (Eq. `todmodel`, the g P m term):
  * s_t = g_q (T_p + Q_p cos 2psi_t + U_p sin 2psi_t), p = pix_t,

@@ -15,7 +15,7 @@ import numpy as np
 
 from ._build import LIB as _LIB_PATH, build as _build_lib
 
-__all__ = ["build", "lib", "fft_length", "huff_encode", "ingest", "pack_flags", "Plan", "Rng",
+__all__ = ["build", "lib", "fft_length", "huff_encode", "ingest", "ingest_data", "pack_flags", "Plan", "Rng",
            "TodError", "MODE_DRAW", "MODE_MEAN", "N_PSI", "CKPT_BLOCK"]
 
 MODE_DRAW = 0
@@ -55,6 +55,10 @@ class _BandDesc(ctypes.Structure):
                 ("cluster_size", _i32), ("device", _i32), ("max_radix", _i32)]
 
 
+class _DataDesc(ctypes.Structure):
+    _fields_ = [("tod", _HuffStreams), ("tod_scale", _P), ("flag", _HuffStreams), ("flag_select", ctypes.c_uint32)]
+
+
 class Rng(ctypes.Structure):
     """Counter-based random streams: key (seed, band), counter carries the
     Gibbs iteration."""
@@ -67,7 +71,8 @@ SYMBOLS = ["tod_status_string", "tod_fft_length", "tod_huff_encode", "tod_huff_f
            "tod_plan_create", "tod_plan_destroy", "tod_plan_info", "tod_plan_status",
            "tod_plan_set_schedule", "tod_chi2", "tod_decode", "tod_project", "tod_sample_gain", "tod_sample_ncorr", "tod_bin",
            "tod_solve_maps", "tod_ncorr_static_setup", "tod_sample_ncorr_static", "tod_ncorr_prepare",
-           "tod_sample_ncorr_prepared", "tod_sample_noise_psd", "tod_plan_set_ncorr_spectrum"]
+           "tod_sample_ncorr_prepared", "tod_sample_noise_psd", "tod_plan_set_ncorr_spectrum",
+           "tod_plan_attach_data", "tod_decode_data"]
 
 
 def build(force: bool = False) -> str:
@@ -109,6 +114,8 @@ def lib():
         L.tod_sample_ncorr_prepared.argtypes = [_P, _P, _P, _P, _P, _P, Rng, _i32, _f64, _i32, _P, _P, _P]
         L.tod_sample_noise_psd.argtypes = [_P, _P, _P, Rng, _i32, _f64, _f64, _P, _P, _P, _P]
         L.tod_plan_set_ncorr_spectrum.argtypes = [_P, _P]
+        L.tod_plan_attach_data.argtypes = [_P, ctypes.POINTER(_DataDesc)]
+        L.tod_decode_data.argtypes = [_P, _P, _P, _P]
         for name in SYMBOLS:
             if name not in ("tod_status_string", "tod_fft_length", "tod_huff_free"):
                 getattr(L, name).restype = _i32
@@ -166,10 +173,13 @@ def pack_flags(flagged: np.ndarray) -> np.ndarray:
     return np.packbits(f, bitorder="little").view("<u4").copy()
 
 
-def ingest(band) -> dict:
+def ingest(band, data_streams: bool = False) -> dict:
     """Ingest of a synthetic band (not on the per-step path): truncate each
     scan to its FFT length (paper Sect. 4.2) and compress its pixel and psi
-    streams (Sect. 4.1)."""
+    streams (Sect. 4.1).  With ``data_streams`` the band's ADC counts and
+    flag words are compressed too (``tod_streams``, ``tod_scale``,
+    ``flag_streams``, ``flag_select``; the step then decodes d and the flags
+    on the device)."""
     ndet, nscan = band.cfg.ndet, band.cfg.nscan
     nq = ndet * nscan
     nlen = np.array([fft_length(int(band.scan_len[q // ndet])) for q in range(nq)], dtype=np.int64)
@@ -178,11 +188,29 @@ def ingest(band) -> dict:
     pix = np.concatenate([band.pix[q][:nlen[q]] for q in range(nq)]).astype(np.int32)
     psi = np.concatenate([band.psi[q][:nlen[q]] for q in range(nq)]).astype(np.int32)
     flags = np.concatenate([band.flags[q][:nlen[q]] for q in range(nq)])
-    return dict(offsets=off,
-                pix_streams=huff_encode(ndet, nscan, off, pix),
-                psi_streams=huff_encode(ndet, nscan, off, psi),
-                tod=np.concatenate([band.tod[q][:nlen[q]] for q in range(nq)]).astype(np.float32),
-                flags=flags, flag_words=pack_flags(flags))
+    out = dict(offsets=off,
+               pix_streams=huff_encode(ndet, nscan, off, pix),
+               psi_streams=huff_encode(ndet, nscan, off, psi),
+               tod=np.concatenate([band.tod[q][:nlen[q]] for q in range(nq)]).astype(np.float32),
+               flags=flags, flag_words=pack_flags(flags))
+    if data_streams:
+        out.update(ingest_data(band, off))
+    return out
+
+
+def ingest_data(band, offsets: np.ndarray) -> dict:
+    """The band's detector data as ADC counts and its flags as flag words
+    (from the synthetic generator), each compressed like the pointing
+    (Sect. 4.1), over the ingest's offsets."""
+    import synth
+    ndet, nscan = band.cfg.ndet, band.cfg.nscan
+    nlen = np.diff(offsets)
+    nq = len(nlen)
+    scale = synth.adc_quantum(band)
+    counts = np.concatenate([synth.adc_counts(band.tod[q][:nlen[q]], scale[q]) for q in range(nq)])
+    words = np.concatenate([synth.flag_words(band.cfg, q, band.flags[q][:nlen[q]]) for q in range(nq)])
+    return dict(tod_streams=huff_encode(ndet, nscan, offsets, counts), tod_scale=scale,
+                flag_streams=huff_encode(ndet, nscan, offsets, words), flag_select=synth.FLAG_SELECT)
 
 
 def _streams(d: dict, keep: list) -> _HuffStreams:
@@ -273,6 +301,20 @@ class Plan:
     # --- A1..A7 -------------------------------------------------------------
     def decode(self, pix_out, psi_out, stream=None):
         _check(lib().tod_decode(self._h, _ptr(pix_out), _ptr(psi_out), _stream(stream)), "tod_decode")
+
+    def attach_data(self, tod_streams: dict, tod_scale, flag_streams: dict, flag_select: int):
+        """Compressed ADC counts (with each detscan's quantum) and flag
+        words of the band, copied to the device once."""
+        keep = []
+        scale = _arr(tod_scale, np.float64)
+        keep.append(scale)
+        desc = _DataDesc(_streams(tod_streams, keep), scale.ctypes.data, _streams(flag_streams, keep),
+                         int(flag_select) & 0xFFFFFFFF)
+        _check(lib().tod_plan_attach_data(self._h, ctypes.byref(desc)), "tod_plan_attach_data")
+
+    def decode_data(self, d_out, flags_out, stream=None):
+        _check(lib().tod_decode_data(self._h, _ptr(d_out), _ptr(flags_out), _stream(stream)),
+               "tod_decode_data")
 
     def project(self, map_tqu4, pix, psi, gain, s_out, stream=None):
         _check(lib().tod_project(self._h, _ptr(map_tqu4), _ptr(pix), _ptr(psi), _ptr(gain),

@@ -444,6 +444,14 @@ tod_status tod_huff_encode(int32_t ndet, int32_t nscan, const int64_t *offsets, 
     for (int64_t q = 0; q < nq; ++q)
         if (offsets[q + 1] < offsets[q]) return TOD_ERR_ARG;
     if (offsets[0] != 0 || (offsets[nq] > 0 && !values)) return TOD_ERR_ARG;
+    for (int64_t q = 0; q < nq; ++q) {          // every difference must be an int32 symbol
+        int64_t prev = 0;
+        for (int64_t t = offsets[q]; t < offsets[q + 1]; ++t) {
+            const int64_t dv = static_cast<int64_t>(values[t]) - prev;
+            if (dv < INT32_MIN || dv > INT32_MAX) return TOD_ERR_ARG;
+            prev = values[t];
+        }
+    }
     try {
         // per scan: code over the deltas of all its detectors
         std::vector<std::vector<int32_t>> svals(nscan);
@@ -940,6 +948,39 @@ tod_status tod_decode(tod_plan *pl, int32_t *pix_out, uint16_t *psi_out, cudaStr
     cudaError_t e = cudaSuccess;
     if (pix_out) e = launch_decode(*p, p->hpix, pix_out, nullptr, stream);
     if (e == cudaSuccess && psi_out) e = launch_decode(*p, p->hpsi, nullptr, psi_out, stream);
+    return to_status(e);
+}
+
+tod_status tod_plan_attach_data(tod_plan *pl, const tod_data_desc *data)
+{
+    if (!pl || !data) return TOD_ERR_ARG;
+    Plan *p = reinterpret_cast<Plan *>(pl);
+    if (p->has_tod || p->has_flag || !data->tod_scale) return TOD_ERR_ARG;
+    if (!valid_streams(data->tod, p->nq, p->nscan, p->h_off) ||
+        !valid_streams(data->flag, p->nq, p->nscan, p->h_off))
+        return TOD_ERR_ARG;
+    for (int q = 0; q < p->nq; ++q)
+        if (!(data->tod_scale[q] > 0.0) || !std::isfinite(data->tod_scale[q])) return TOD_ERR_ARG;
+    DeviceGuard dg(p->device);
+    cudaError_t e;
+    if ((e = build_huff(*p, p->htod, data->tod))) return to_status(e);
+    if ((e = dev_upload(*p, p->tod_scale, data->tod_scale, p->nq))) return to_status(e);
+    p->has_tod = true;
+    if ((e = build_huff(*p, p->hflag, data->flag))) return to_status(e);
+    p->flag_select = data->flag_select;
+    p->has_flag = true;
+    return TOD_OK;
+}
+
+tod_status tod_decode_data(tod_plan *pl, float *d_out, uint32_t *flags_out, cudaStream_t stream)
+{
+    if (!pl || (!d_out && !flags_out)) return TOD_ERR_ARG;
+    Plan *p = reinterpret_cast<Plan *>(pl);
+    if (!p->has_tod || !p->has_flag) return TOD_ERR_ARG;
+    DeviceGuard dg(p->device);
+    cudaError_t e = cudaSuccess;
+    if (d_out) e = launch_decode_tod(*p, d_out, stream);
+    if (e == cudaSuccess && flags_out) e = launch_decode_flags(*p, flags_out, stream);
     return to_status(e);
 }
 

@@ -12,6 +12,8 @@ constexpr int DEC_LUTB = 13;          // first-level decode table: 2^13 packed 3
 constexpr int DEC_T = 512;
 constexpr int NCORR_SCRATCH_F4 = 2;   // float4 per packed slot of the n_corr scratch: filter weights, CG spectra            // decode threads per CTA (one checkpoint block each)
 constexpr int DEC_ROUND = 16;         // symbols staged per thread before a coalesced write
+// what a decoded value becomes: itself (pointing), the FP32 TOD, a flag bit
+enum : int { DEC_VALUE = 0, DEC_TOD = 1, DEC_FLAG = 2 };
 constexpr int ELEM_TILE = 4096;       // samples per tile of the element-wise kernels
 constexpr int DCT_T = 512;            // threads per CTA of the cluster transform kernels
 constexpr int DCT_SZ_MAX = 11776;     // complex values per CTA buffer (two buffers + CG fit in 227 KB)
@@ -72,6 +74,11 @@ struct Plan {
     int64_t *off = nullptr;          // [nq+1] device
     int32_t *status = nullptr;       // [nq] device
     HuffDev hpix, hpsi;
+    // compressed TOD (ADC counts) and flag words, when attached
+    HuffDev htod, hflag;
+    bool has_tod = false, has_flag = false;
+    double *tod_scale = nullptr;     // [nq] ADC quantum per detscan
+    uint32_t flag_select = 0;        // flag-word bits that exclude a sample
     // element-wise tiles
     int32_t ntile = 0;
     int32_t *tile_q = nullptr;
@@ -130,6 +137,8 @@ struct Plan {
 cudaError_t setup_decode_kernel();
 cudaError_t launch_decode(const Plan &p, const HuffDev &h, int32_t *pix_out, uint16_t *psi_out,
                           cudaStream_t st);
+cudaError_t launch_decode_tod(const Plan &p, float *d_out, cudaStream_t st);
+cudaError_t launch_decode_flags(const Plan &p, uint32_t *flags_out, cudaStream_t st);
 cudaError_t launch_project(const Plan &p, const float4 *map, const int32_t *pix, const uint16_t *psi,
                            const double *gain, float *s_out, cudaStream_t st);
 cudaError_t setup_dct_kernels(Plan &p);

@@ -11,12 +11,24 @@
 // on an SM.  Values are undone
 // from their differences on the fly and staged DEC_ROUND at a time per
 // thread in shared memory, then written with coalesced stores.
+//
+// The same decoder serves the TOD and quality-flag streams (Sect. 4.1:
+// the ADC integers and flag words are differenced and coded like the
+// pointing; Listing `tod`: tod and flag held as compressed bytes).  What a
+// decoded value becomes is the kernel's KIND: the value itself (pointing),
+// the FP32 TOD d = fl32(scale_q * count) (one FP64 product, one rounding),
+// or the flag bit (word & select) != 0, packed into the sample bitmask with
+// one warp vote and at most two atomic ORs per DEC_ROUND samples.
+#include <type_traits>
+
 #include "common.cuh"
 #include "internal.cuh"
 
 namespace tg {
 
-template <typename OutT>
+static_assert(DEC_ROUND == 16, "the flag packing takes two runs of 16 samples per warp");
+
+template <typename OutT, int KIND>
 __global__ void __launch_bounds__(DEC_T)
 k_decode(const uint32_t *__restrict__ words, const int64_t *__restrict__ word_off,
          const int64_t *__restrict__ nbits, const int64_t *__restrict__ blk_off,
@@ -26,12 +38,13 @@ k_decode(const uint32_t *__restrict__ words, const int64_t *__restrict__ word_of
          const int32_t *__restrict__ canon_off, const int32_t *__restrict__ canon_vals,
          const int32_t *__restrict__ cta_scan, const int64_t *__restrict__ cta_blk0,
          const int32_t *__restrict__ cta_nblk, const int64_t *__restrict__ off,
-         OutT *__restrict__ out, int32_t *status)
+         const double *__restrict__ scale, uint32_t select, OutT *__restrict__ out, int32_t *status)
 {
+    using StageT = typename std::conditional<KIND == DEC_FLAG, uint8_t, OutT>::type;
     extern __shared__ int32_t s_lut[];                     // [1 << DEC_LUTB]
     __shared__ unsigned long long s_lim[26];
     __shared__ int32_t s_base[26];
-    __shared__ OutT s_tile[DEC_T][DEC_ROUND + 1];
+    __shared__ StageT s_tile[DEC_T][DEC_ROUND + 1];
     __shared__ int64_t s_out0[DEC_T];
     __shared__ int32_t s_cnt[DEC_T];
 
@@ -50,6 +63,7 @@ k_decode(const uint32_t *__restrict__ words, const int64_t *__restrict__ word_of
     int q = 0, cnt = 0;
     int64_t pos = 0, end = 0, wptr = 0;
     int32_t x = 0;
+    double sc = 0.0;                    // DEC_TOD: the detscan's ADC quantum
     unsigned long long buf = 0;
     int have = 0;                       // valid bits in buf (left-aligned)
     bool ok = true;
@@ -65,6 +79,7 @@ k_decode(const uint32_t *__restrict__ words, const int64_t *__restrict__ word_of
         pos = w0 * 32 + ckpt_bit[b];
         end = w0 * 32 + nbits[q];
         x = ckpt_val[b];
+        if constexpr (KIND == DEC_TOD) sc = scale[q];
         wptr = pos >> 5;
         const int sh = static_cast<int>(pos & 31);
         buf = ((static_cast<unsigned long long>(words[wptr]) << 32) | words[wptr + 1]) << sh;
@@ -106,7 +121,12 @@ k_decode(const uint32_t *__restrict__ words, const int64_t *__restrict__ word_of
                     ++wptr;
                     have += 32;
                 }
-                s_tile[tid][i] = static_cast<OutT>(x);
+                if constexpr (KIND == DEC_TOD)
+                    s_tile[tid][i] = __double2float_rn(static_cast<double>(x) * sc);
+                else if constexpr (KIND == DEC_FLAG)
+                    s_tile[tid][i] = (static_cast<uint32_t>(x) & select) != 0u;
+                else
+                    s_tile[tid][i] = static_cast<OutT>(x);
             }
         }
         __syncthreads();
@@ -114,7 +134,22 @@ k_decode(const uint32_t *__restrict__ words, const int64_t *__restrict__ word_of
         for (int e = tid; e < DEC_T * DEC_ROUND; e += DEC_T) {
             const int bl = e / DEC_ROUND, i = e % DEC_ROUND;
             const int idx = round * DEC_ROUND + i;
-            if (idx < s_cnt[bl]) out[s_out0[bl] + idx] = s_tile[bl][i];
+            if constexpr (KIND == DEC_FLAG) {
+                // lanes 0-15 and 16-31 each hold DEC_ROUND consecutive samples
+                // of one block; their flagged bits are ORed into the bitmask
+                // (bit t & 31 of word t >> 5; the words start zeroed)
+                const uint32_t vote =
+                    __ballot_sync(0xffffffffu, idx < s_cnt[bl] && s_tile[bl][i] != 0);
+                const uint32_t mine = (vote >> (tid & 31 & ~(DEC_ROUND - 1))) & 0xffffu;
+                if (i == 0 && mine) {
+                    const int64_t g0 = s_out0[bl] + round * DEC_ROUND;
+                    const unsigned long long v = static_cast<unsigned long long>(mine) << (g0 & 31);
+                    atomicOr(out + (g0 >> 5), static_cast<uint32_t>(v));
+                    if (v >> 32) atomicOr(out + (g0 >> 5) + 1, static_cast<uint32_t>(v >> 32));
+                }
+            } else {
+                if (idx < s_cnt[bl]) out[s_out0[bl] + idx] = s_tile[bl][i];
+            }
         }
         __syncthreads();
     }
@@ -124,28 +159,50 @@ k_decode(const uint32_t *__restrict__ words, const int64_t *__restrict__ word_of
 cudaError_t setup_decode_kernel()
 {
     const int smem = static_cast<int>(sizeof(int32_t) * (1 << DEC_LUTB));
-    cudaError_t e = cudaFuncSetAttribute(k_decode<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_decode<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(k_decode<int32_t, DEC_VALUE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_decode<uint16_t, DEC_VALUE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_decode<float, DEC_TOD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_decode<uint32_t, DEC_FLAG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
 }
+
+namespace {
+
+template <typename OutT, int KIND>
+cudaError_t decode_into(const Plan &p, const HuffDev &h, const double *scale, uint32_t select, OutT *out,
+                        cudaStream_t st)
+{
+    if (h.ncta == 0) return cudaSuccess;
+    const size_t smem = sizeof(int32_t) * (1 << DEC_LUTB);
+    k_decode<OutT, KIND><<<h.ncta, DEC_T, smem, st>>>(
+        h.words, h.word_off, h.nbits, h.blk_off, h.ckpt_bit, h.ckpt_val, h.blk_q, h.lut, h.lim, h.base,
+        h.canon_off, h.canon_vals, h.cta_scan, h.cta_blk0, h.cta_nblk, p.off, scale, select, out, p.status);
+    return cudaGetLastError();
+}
+
+}  // namespace
 
 cudaError_t launch_decode(const Plan &p, const HuffDev &h, int32_t *pix_out, uint16_t *psi_out,
                           cudaStream_t st)
 {
-    if (h.ncta == 0) return cudaSuccess;
-    const size_t smem = sizeof(int32_t) * (1 << DEC_LUTB);
-    if (pix_out) {
-        k_decode<int32_t><<<h.ncta, DEC_T, smem, st>>>(
-            h.words, h.word_off, h.nbits, h.blk_off, h.ckpt_bit, h.ckpt_val, h.blk_q, h.lut, h.lim,
-            h.base, h.canon_off, h.canon_vals, h.cta_scan, h.cta_blk0, h.cta_nblk, p.off, pix_out,
-            p.status);
-    } else {
-        k_decode<uint16_t><<<h.ncta, DEC_T, smem, st>>>(
-            h.words, h.word_off, h.nbits, h.blk_off, h.ckpt_bit, h.ckpt_val, h.blk_q, h.lut, h.lim,
-            h.base, h.canon_off, h.canon_vals, h.cta_scan, h.cta_blk0, h.cta_nblk, p.off, psi_out,
-            p.status);
-    }
-    return cudaGetLastError();
+    if (pix_out) return decode_into<int32_t, DEC_VALUE>(p, h, nullptr, 0u, pix_out, st);
+    return decode_into<uint16_t, DEC_VALUE>(p, h, nullptr, 0u, psi_out, st);
+}
+
+cudaError_t launch_decode_tod(const Plan &p, float *d_out, cudaStream_t st)
+{
+    return decode_into<float, DEC_TOD>(p, p.htod, p.tod_scale, 0u, d_out, st);
+}
+
+cudaError_t launch_decode_flags(const Plan &p, uint32_t *flags_out, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(flags_out, 0, sizeof(uint32_t) * ((p.N + 31) / 32), st);
+    if (e != cudaSuccess) return e;
+    return decode_into<uint32_t, DEC_FLAG>(p, p.hflag, nullptr, p.flag_select, flags_out, st);
 }
 
 // ---------------------------------------------------------------------------

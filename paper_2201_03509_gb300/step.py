@@ -1,6 +1,10 @@
 """One Gibbs TOD step on the GPU (paper Listing `code:gibbs`, step 1):
 decode -> project -> sample gain -> sample n_corr -> bin -> solve, as a
-sequence of the C-ABI calls on one stream.  Holds the device buffers."""
+sequence of the C-ABI calls on one stream.  Holds the device buffers.
+
+With ``data_streams`` the detector data and flags stay compressed on the
+device too (Sect. 4.1; the plan must have them attached) and every step
+decodes them along with the pointing."""
 from __future__ import annotations
 
 import numpy as np
@@ -9,8 +13,8 @@ from . import MODE_DRAW, Plan, Rng
 
 
 class GibbsTODStep:
-    def __init__(self, plan: Plan, psd: np.ndarray, flag_words: np.ndarray, rcond_min: float = 1e-6,
-                 cg_tol: float = 1e-6, cg_maxiter: int = 500):
+    def __init__(self, plan: Plan, psd: np.ndarray, flag_words: np.ndarray | None, rcond_min: float = 1e-6,
+                 cg_tol: float = 1e-6, cg_maxiter: int = 500, data_streams: bool = False):
         import torch
         dev = torch.device("cuda", plan.device)
         N, nq, npix = plan.N, plan.nq, plan.npix
@@ -18,7 +22,11 @@ class GibbsTODStep:
         self.rcond_min, self.cg_tol, self.cg_maxiter = rcond_min, cg_tol, cg_maxiter
         f32, f64, i32 = torch.float32, torch.float64, torch.int32
         self.psd = torch.from_numpy(np.ascontiguousarray(psd, np.float64)).to(dev)
-        self.flags = torch.from_numpy(np.ascontiguousarray(flag_words, np.uint32).view(np.int32)).to(dev)
+        self.data_streams = data_streams
+        if data_streams:
+            self.flags = torch.zeros((N + 31) // 32, dtype=i32, device=dev)   # decoded every step
+        else:
+            self.flags = torch.from_numpy(np.ascontiguousarray(flag_words, np.uint32).view(np.int32)).to(dev)
         self.d = torch.empty(N, dtype=f32, device=dev)
         self.pix = torch.empty(N, dtype=i32, device=dev)
         self.psi = torch.empty(N, dtype=torch.int16, device=dev)
@@ -40,6 +48,7 @@ class GibbsTODStep:
         self.lookahead = True
         self._pointing_ready = False
         self._pix_next = self._psi_next = None
+        self._d_next = self._flags_next = None
 
     def set_tod(self, d, stream=None):
         """Copy this band's detector data (host numpy float32 or a tensor)."""
@@ -55,6 +64,8 @@ class GibbsTODStep:
         on `stream` waits for the copy and then uses that buffer; the copy
         itself waits until the last step that read that buffer is done."""
         import torch
+        if self.data_streams:
+            raise ValueError("the detector data are decoded on the device: nothing to prefetch")
         if getattr(self, "_copy_stream", None) is None:
             self._copy_stream = torch.cuda.Stream(device=self.d.device)
             self._d_spare = torch.empty_like(self.d)
@@ -132,9 +143,14 @@ class GibbsTODStep:
             # decoded by the previous step, under its n_corr draw
             self.pix, self._pix_next = self._pix_next, self.pix
             self.psi, self._psi_next = self._psi_next, self.psi
+            if self.data_streams:
+                self.d, self._d_next = self._d_next, self.d
+                self.flags, self._flags_next = self._flags_next, self.flags
             self._pointing_ready = False
         else:
             p.decode(self.pix, self.psi, hp)
+            if self.data_streams:
+                p.decode_data(self.d, self.flags, hp)
         p.project(map32_in, self.pix, self.psi, None, self.s, hp)
         p.sample_gain(self.d, self.s, self.flags, self.psd, rng, mode, self.gain, self.mu, self.sigma, hp)
         hp.wait_event(prepared)
@@ -150,8 +166,13 @@ class GibbsTODStep:
             if self._pix_next is None:
                 self._pix_next = torch.empty_like(self.pix)
                 self._psi_next = torch.empty_like(self.psi)
+            if self.data_streams and self._d_next is None:
+                self._d_next = torch.empty_like(self.d)
+                self._flags_next = torch.empty_like(self.flags)
             lo.wait_event(gained)
             p.decode(self._pix_next, self._psi_next, lo)
+            if self.data_streams:
+                p.decode_data(self._d_next, self._flags_next, lo)
             self._pointing_ready = True
         p.bin(self.psi, self.d, self.ncorr, self.gain, self.flags, self.psd, self.A, self.b, self.hits, hp)
         p.solve_maps(self.A, self.b, self.hits, self.rcond_min, self.map, self.map32, self.rcond,
@@ -162,6 +183,11 @@ class GibbsTODStep:
         self._mark_d_done(stream)
 
     LAUNCHES_PER_STEP = 11  # decode x2, project, gain + draw, Toeplitz prep x2, ncorr, bin + reduce, solve
+    DATA_LAUNCHES = 2       # with data_streams: decode of the TOD and of the flags
+
+    @property
+    def launches_per_step(self) -> int:
+        return self.LAUNCHES_PER_STEP + (self.DATA_LAUNCHES if self.data_streams else 0)
 
     def capture(self, map32_in, seed: int, band: int = 0, mode: int = MODE_DRAW):
         """Capture one step into a CUDA graph.  The Gibbs iteration is read by

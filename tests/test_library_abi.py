@@ -57,6 +57,23 @@ def test_encoder_adversarial_matches_oracle(tgmod):
         assert np.array_equal(np.asarray(v), np.asarray(a[k])), k
 
 
+def test_data_stream_encoder_matches_oracle(tgmod):
+    cfg = synth.scaled(synth.CONFIGS["lfi30"], nscan=2, len_lo=5000, len_hi=20000)
+    band = synth.make_band(cfg)
+    a = tgmod.ingest(band, data_streams=True)
+    b = oracle.ingest(band, data_streams=True)
+    assert np.array_equal(a["tod_scale"], b["tod_scale"]) and a["flag_select"] == b["flag_select"]
+    for kind in ("tod_streams", "flag_streams"):
+        for k, v in b[kind].items():
+            assert np.array_equal(np.asarray(v), np.asarray(a[kind][k])), (kind, k)
+
+
+def test_encoder_rejects_a_difference_outside_int32(tgmod):
+    vals = np.array([2 ** 31 - 1, -2 ** 31, 0, 1], np.int32)
+    with pytest.raises(tgmod.TodError):
+        tgmod.huff_encode(1, 1, np.array([0, 4]), vals)
+
+
 def test_encoder_rejects_bad_offsets(tgmod):
     with pytest.raises(tgmod.TodError):
         tgmod.huff_encode(1, 2, np.array([0, 10, 5]), np.zeros(10, np.int32))
