@@ -32,6 +32,7 @@ PURPOSE_GAIN = 0
 PURPOSE_NC_W1 = 1
 PURPOSE_NC_W2 = 2
 PURPOSE_PSD = 3
+PURPOSE_GAIN_SMOOTH = 4
 
 MODE_DRAW = 0
 MODE_MEAN = 1
@@ -418,6 +419,54 @@ def sample_gain(s, d, mask, P, z: float, mode: int = MODE_DRAW) -> tuple:
     mu = b / a
     sig = 1.0 / math.sqrt(a)
     return (mu + (z * sig if mode == MODE_DRAW else 0.0)), mu, sig
+
+
+# ============================================================================
+# A12. gains of all scans of a detector under a smooth prior
+# ============================================================================
+
+def gain_smooth_normals(seed: int, band: int, det: int, it: int, nscan: int) -> tuple:
+    """The two standard normals of scan s in the smooth gain draw of detector
+    det: Philox block (s, det, GAIN_SMOOTH, it); 53-bit uniforms from words
+    0, 1 (w1_s) and 2, 3 (w2_s), Box-Muller cosine branch, FP64."""
+    w1 = np.empty(nscan)
+    w2 = np.empty(nscan)
+    for sc in range(nscan):
+        w = philox4x64([sc, det, PURPOSE_GAIN_SMOOTH, it], [seed, band])
+        u = [(float(w[j] >> np.uint64(11)) + 0.5) * 2.0 ** -53 for j in range(4)]
+        w1[sc] = math.sqrt(-2.0 * math.log(u[0])) * math.cos(2.0 * math.pi * u[1])
+        w2[sc] = math.sqrt(-2.0 * math.log(u[2])) * math.cos(2.0 * math.pi * u[3])
+    return w1, w2
+
+
+def gain_prior_precision(nscan: int, sigma_g: float, alpha_g: float) -> np.ndarray:
+    """Prior precision of a detector's scan gains in the orthonormal DCT-II
+    basis of the scan index: lambda_0 = 0 (the mean gain is free),
+    lambda_k = 1 / (sigma_g^2 k^alpha_g) for k >= 1 (reading: the paper
+    defers the gain model to its calibration companion paper)."""
+    lam = np.zeros(nscan)
+    k = np.arange(1, nscan, dtype=np.float64)
+    lam[1:] = 1.0 / (sigma_g ** 2 * k ** alpha_g)
+    return lam
+
+
+def sample_gain_smooth(mu, sigma, sigma_g: float, alpha_g: float, w1, w2, mode: int = MODE_DRAW) -> np.ndarray:
+    """Joint draw of one detector's scan gains: each scan's gain conditional
+    N(mu_s, sigma_s^2) (the per-detscan draw, n_corr marginalised) times the
+    smooth prior of ``gain_prior_precision``.  Posterior precision
+    A = diag(1/sigma^2) + C^T diag(lambda) C, with C the orthonormal DCT-II
+    matrix; g = A^-1 (mu/sigma^2 + w1/sigma + C^T (sqrt(lambda) w2)), the
+    noise terms dropped in MODE_MEAN.  Dense FP64 solve."""
+    mu = np.asarray(mu, np.float64)
+    sigma = np.asarray(sigma, np.float64)
+    S = len(mu)
+    C = sfft.dct(np.eye(S), type=2, norm="ortho", axis=0)     # column q = C e_q
+    lam = gain_prior_precision(S, sigma_g, alpha_g)
+    A = np.diag(1.0 / sigma ** 2) + C.T @ np.diag(lam) @ C
+    rhs = mu / sigma ** 2
+    if mode == MODE_DRAW:
+        rhs = rhs + np.asarray(w1, np.float64) / sigma + C.T @ (np.sqrt(lam) * np.asarray(w2, np.float64))
+    return np.linalg.solve(A, rhs)
 
 
 # ============================================================================
