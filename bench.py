@@ -118,7 +118,7 @@ def _peaks():
 # valid only while the kernel's sources hash to the digest taken with it.
 NCORR_TRAFFIC = {"bytes_per_sample": 15.82,
                  "sources": ["csrc/k_dct.cu", "csrc/common.cuh", "csrc/internal.cuh", "csrc/api.cu"],
-                 "sha256": "15e764c396324dfd1cee10ea09a8ed00a47444e339bc7f9fa6cb6e67208244c7"}
+                 "sha256": "a01eb296836fd5ea94b8c3d7cc90763b7bf552c1645ee3220d546fcab52d24f1"}
 
 
 def ncorr_sources_digest() -> str:
@@ -385,6 +385,26 @@ def run_ours(args):
                    "launches_per_step": dstep.launches_per_step, "ingest_s": enc_s}
         del dstep
 
+    # joint gain draw under the smooth prior across scans (outside the step's
+    # value), from the last step's per-detscan conditionals
+    gs_info = None
+    if not args.no_gain_smooth:
+        prior = torch.tensor([[1e-3, -2.0]] * plan.ndet, dtype=torch.float64, device=step.d.device)
+        gsm = torch.empty_like(step.gain)
+        gits = torch.zeros(plan.ndet, dtype=torch.int32, device=step.d.device)
+        ts = []
+        for k in range(4):
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            plan.sample_gain_smooth(step.mu, step.sigma, prior, tg.Rng(args.seed, 0, 80_000 + k), tg.MODE_DRAW,
+                                    gsm, gits, cg_tol=1e-6)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a0.elapsed_time(a1))
+        plan.status()
+        gs_info = {"ms": min(ts[1:]), "cg_iters": gits.cpu().tolist(), "nscan": plan.nscan, "ndet": plan.ndet,
+                   "prior": {"sigma_g": 1e-3, "alpha_g": -2.0}, "cg_tol": 1e-6}
+
     # roofline of the dominant stage
     peaks, peak_src = _peaks()
     comp = int(ing["pix_streams"]["words"].nbytes + ing["psi_streams"]["words"].nbytes)
@@ -438,6 +458,7 @@ def run_ours(args):
                            if plain_ms else None),
         "noise_psd": psd_info,
         "data_streams": ds_info,
+        "gain_smooth": gs_info,
         "device_status_errors": int(np.count_nonzero(st)),
         "roofline": roof, "clocks": clocks, "setup_s": setup_s,
     }
@@ -541,6 +562,8 @@ def main():
     ap.add_argument("--no-psd", action="store_true", help="skip the noise-PSD step measurement")
     ap.add_argument("--no-data-streams", action="store_true",
                     help="skip the step with compressed TOD and flags")
+    ap.add_argument("--no-gain-smooth", action="store_true",
+                    help="skip the joint gain draw under the smooth prior")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

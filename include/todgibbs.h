@@ -182,6 +182,35 @@ tod_status tod_plan_set_schedule(tod_plan *p, int32_t schedule);
 tod_status tod_decode(tod_plan *p, int32_t *pix_out, uint16_t *psi_out, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Joint gain draw of every detector's scans under a smooth prior across
+ * scans (the gain conditional of Eq. `gibbsstart` per detscan as the
+ * likelihood; the paper defers the gain model to its calibration companion
+ * paper, so the prior is this library's reading).  Per detector, with S
+ * scans, a_s = 1/sigma_s^2 and b_s = mu_s/sigma_s^2 from the per-detscan
+ * conditionals N(mu_s, sigma_s^2) (tod_sample_gain's mu_out, sigma_out):
+ *   prior precision C^T diag(lambda) C, C the orthonormal DCT-II over the
+ *   scan index, lambda_0 = 0 (mean gain free),
+ *   lambda_k = 1 / (sigma_g^2 k^alpha_g) for k >= 1;
+ *   A g = b + a^(1/2) w1 + C^T (lambda^(1/2) w2),
+ *   A = diag(a) + C^T diag(lambda) C (noise terms dropped in TOD_MODE_MEAN).
+ * w1_s, w2_s: Philox block (s, det, TOD_PURPOSE_GAIN_SMOOTH, iteration),
+ * 53-bit uniforms from words 0, 1 (w1) and 2, 3 (w2), Box-Muller cosine
+ * branch in FP64.  Preconditioned CG in FP32 (double-word transform sums,
+ * FP64 dot products) to relative residual cg_tol, at most cg_maxiter
+ * iterations; a detector that does not converge marks detscan det
+ * TOD_ERR_NOT_CONVERGED, a sigma_s <= 0 or non-finite input marks its
+ * detscan TOD_ERR_ARG.
+ *   mu, sigma: DEVICE double[ndetscan]; prior: DEVICE double[ndet][2]
+ *   (sigma_g > 0, alpha_g); gain_out: DEVICE double[ndetscan];
+ *   cg_iters_out: DEVICE int32[ndet] or NULL.
+ * TOD_ERR_ARG (host) when nscan > TOD_GAIN_SMOOTH_MAX_SCANS.
+ * ------------------------------------------------------------------------- */
+#define TOD_GAIN_SMOOTH_MAX_SCANS 4096
+tod_status tod_sample_gain_smooth(tod_plan *p, const double *mu, const double *sigma, const double *prior,
+                                  tod_rng rng, int32_t mode, double cg_tol, int32_t cg_maxiter,
+                                  double *gain_out, int32_t *cg_iters_out, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Compressed TOD and quality flags (Sect. 4.1: the ADC integers and the flag
  * words are differenced and Huffman coded like the pointing; Listing `tod`:
  * comm_detscan holds tod and flag as compressed bytes).  Both streams use
@@ -377,6 +406,7 @@ tod_status tod_chi2(tod_plan *p, const float *d, const float *s, const double *g
  * the decisions in FP64.  Deterministic.  The plan holds the chain's state:
  * calls on one plan must not overlap. */
 #define TOD_PURPOSE_PSD 3
+#define TOD_PURPOSE_GAIN_SMOOTH 4
 #define TOD_PSD_LNFK_MIN (-9.2103403719761836)   /* ln 1e-4 (f_knee in Hz) */
 #define TOD_PSD_LNFK_MAX 2.3025850929940457      /* ln 10 */
 #define TOD_PSD_ALPHA_MIN (-4.0)

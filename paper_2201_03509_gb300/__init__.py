@@ -72,7 +72,7 @@ SYMBOLS = ["tod_status_string", "tod_fft_length", "tod_huff_encode", "tod_huff_f
            "tod_plan_set_schedule", "tod_chi2", "tod_decode", "tod_project", "tod_sample_gain", "tod_sample_ncorr", "tod_bin",
            "tod_solve_maps", "tod_ncorr_static_setup", "tod_sample_ncorr_static", "tod_ncorr_prepare",
            "tod_sample_ncorr_prepared", "tod_sample_noise_psd", "tod_plan_set_ncorr_spectrum",
-           "tod_plan_attach_data", "tod_decode_data"]
+           "tod_plan_attach_data", "tod_decode_data", "tod_sample_gain_smooth"]
 
 
 def build(force: bool = False) -> str:
@@ -116,6 +116,7 @@ def lib():
         L.tod_plan_set_ncorr_spectrum.argtypes = [_P, _P]
         L.tod_plan_attach_data.argtypes = [_P, ctypes.POINTER(_DataDesc)]
         L.tod_decode_data.argtypes = [_P, _P, _P, _P]
+        L.tod_sample_gain_smooth.argtypes = [_P, _P, _P, _P, Rng, _i32, _f64, _i32, _P, _P, _P]
         for name in SYMBOLS:
             if name not in ("tod_status_string", "tod_fft_length", "tod_huff_free"):
                 getattr(L, name).restype = _i32
@@ -311,6 +312,14 @@ class Plan:
         desc = _DataDesc(_streams(tod_streams, keep), scale.ctypes.data, _streams(flag_streams, keep),
                          int(flag_select) & 0xFFFFFFFF)
         _check(lib().tod_plan_attach_data(self._h, ctypes.byref(desc)), "tod_plan_attach_data")
+
+    def sample_gain_smooth(self, mu, sigma, prior, rng: Rng, mode, gain_out, cg_iters_out=None,
+                           cg_tol: float = 1e-6, cg_maxiter: int = 200, stream=None):
+        """Joint draw of each detector's scan gains under the smooth prior
+        (prior: device float64[ndet, 2] = sigma_g, alpha_g)."""
+        _check(lib().tod_sample_gain_smooth(self._h, _ptr(mu), _ptr(sigma), _ptr(prior), rng, int(mode),
+                                            float(cg_tol), int(cg_maxiter), _ptr(gain_out), _ptr(cg_iters_out),
+                                            _stream(stream)), "tod_sample_gain_smooth")
 
     def decode_data(self, d_out, flags_out, stream=None):
         _check(lib().tod_decode_data(self._h, _ptr(d_out), _ptr(flags_out), _stream(stream)),

@@ -972,6 +972,31 @@ tod_status tod_plan_attach_data(tod_plan *pl, const tod_data_desc *data)
     return TOD_OK;
 }
 
+tod_status tod_sample_gain_smooth(tod_plan *pl, const double *mu, const double *sigma, const double *prior,
+                                  tod_rng rng, int32_t mode, double cg_tol, int32_t cg_maxiter,
+                                  double *gain_out, int32_t *cg_iters_out, cudaStream_t stream)
+{
+    if (!pl || !mu || !sigma || !prior || !gain_out) return TOD_ERR_ARG;
+    if ((mode != TOD_MODE_DRAW && mode != TOD_MODE_MEAN) || !(cg_tol > 0.0) || cg_maxiter < 0) return TOD_ERR_ARG;
+    Plan *p = reinterpret_cast<Plan *>(pl);
+    if (p->nscan > TOD_GAIN_SMOOTH_MAX_SCANS) return TOD_ERR_ARG;
+    DeviceGuard dg(p->device);
+    GainSmoothArgs a{};
+    a.mu = mu;
+    a.sigma = sigma;
+    a.prior = prior;
+    a.nscan = p->nscan;
+    a.ndet = p->ndet;
+    a.rng = rng;
+    a.mode = mode;
+    a.tol = static_cast<float>(cg_tol);
+    a.maxiter = cg_maxiter;
+    a.gain_out = gain_out;
+    a.iters_out = cg_iters_out;
+    a.status = p->status;
+    return to_status(launch_gain_smooth(a, stream));
+}
+
 tod_status tod_decode_data(tod_plan *pl, float *d_out, uint32_t *flags_out, cudaStream_t stream)
 {
     if (!pl || (!d_out && !flags_out)) return TOD_ERR_ARG;

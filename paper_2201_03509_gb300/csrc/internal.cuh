@@ -138,6 +138,22 @@ cudaError_t setup_decode_kernel();
 cudaError_t launch_decode(const Plan &p, const HuffDev &h, int32_t *pix_out, uint16_t *psi_out,
                           cudaStream_t st);
 cudaError_t launch_decode_tod(const Plan &p, float *d_out, cudaStream_t st);
+
+// joint gain draw under the smooth prior across scans (one CTA per detector)
+struct GainSmoothArgs {
+    const double *mu, *sigma;    // [nq] per-detscan gain conditionals, q = scan * ndet + det
+    const double *prior;         // [ndet][2] sigma_g, alpha_g
+    int32_t nscan, ndet;
+    tod_rng rng;
+    int32_t mode;
+    float tol;
+    int32_t maxiter;
+    double *gain_out;            // [nq]
+    int32_t *iters_out;          // [ndet] or null
+    int32_t *status;
+};
+size_t gain_smooth_smem(int nscan);
+cudaError_t launch_gain_smooth(const GainSmoothArgs &a, cudaStream_t st);
 cudaError_t launch_decode_flags(const Plan &p, uint32_t *flags_out, cudaStream_t st);
 cudaError_t launch_project(const Plan &p, const float4 *map, const int32_t *pix, const uint16_t *psi,
                            const double *gain, float *s_out, cudaStream_t st);

@@ -1,0 +1,243 @@
+// A12 joint gain draw of all scans of one detector under a smooth prior
+// (the per-detscan gain conditional of Eq. `gibbsstart` as likelihood; the
+// paper defers the gain model to its calibration companion paper, so the
+// prior is a reading): precision diagonal in the orthonormal DCT-II basis
+// of the scan index, lambda_0 = 0 (mean gain free), lambda_k = 1 /
+// (sigma_g^2 k^alpha_g).  With a_s = 1/sigma_s^2, b_s = mu_s/sigma_s^2:
+//   A g = b + a^(1/2) w1 + C^T (lambda^(1/2) w2),  A = diag(a) + C^T diag(lambda) C.
+// One CTA per detector solves it by preconditioned CG for the fluctuation
+// x = g - g_ref about the weighted mean g_ref = sum b / sum a (A g_ref =
+// a g_ref: the prior does not see a constant), scaled by the mean of a.
+// The preconditioner C^T diag(1 / (1 + lambda/abar)) C is A^-1 exactly when
+// every scan has the same a.  Transforms are direct sums over a shared
+// quarter-wave cosine table (a detector has at most a few thousand scans),
+// FP32 products in double-word sums, dot products in FP64, every sum in a
+// fixed order: deterministic.  The table is padded by one word every 32
+// (entry m at m + m/32) so that the inverse transform's even lane strides
+// do not all fall in one shared-memory bank.
+#include "common.cuh"
+#include "internal.cuh"
+
+namespace tg {
+
+namespace {
+
+constexpr int GS_T = 1024;
+constexpr int GS_CHUNK = 16;          // terms summed in FP32 before entering the double-word sum
+
+__host__ __device__ __forceinline__ int cpad(int m) { return m + (m >> 5); }
+
+// FP64 block sum of two per-thread values, fixed order (warp trees, then
+// the warps in order); every thread gets both sums.
+__device__ double2 block_sum2(double u, double v, double2 *s_red)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        u += __shfl_xor_sync(0xffffffffu, u, o);
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    }
+    const int w = threadIdx.x >> 5;
+    __syncthreads();                            // s_red free from the previous use
+    if ((threadIdx.x & 31) == 0) s_red[w] = make_double2(u, v);
+    __syncthreads();
+    double su = 0.0, sv = 0.0;
+    for (int i = 0; i < GS_T / 32; ++i) { su += s_red[i].x; sv += s_red[i].y; }
+    return make_double2(su, sv);
+}
+
+// y_k = c_k sum_q x_q cos(pi k (2q+1) / (2S)), c_0 = sqrt(1/S), c_k = sqrt(2/S)
+__device__ void dct_fwd(const float *x, float *y, const float *cosT, int S)
+{
+    const int S4 = 4 * S;
+    const double c0 = sqrt(1.0 / S), c1 = sqrt(2.0 / S);
+    for (int k = threadIdx.x; k < S; k += GS_T) {
+        Acc2 acc{0.f, 0.f};
+        int m = k;
+        const int step = 2 * k;
+        for (int q0 = 0; q0 < S; q0 += GS_CHUNK) {
+            const int q1 = min(q0 + GS_CHUNK, S);
+            float part = 0.f;
+            for (int q = q0; q < q1; ++q) {
+                part = fmaf(x[q], cosT[cpad(m)], part);
+                m += step;
+                if (m >= S4) m -= S4;
+            }
+            acc_add(acc, part);
+        }
+        y[k] = static_cast<float>(acc_value(acc) * (k ? c1 : c0));
+    }
+}
+
+// x_q = sum_k c_k y_k cos(pi k (2q+1) / (2S)); ys holds c_k y_k
+__device__ void dct_inv(const float *ys, float *x, const float *cosT, int S)
+{
+    const int S4 = 4 * S;
+    for (int q = threadIdx.x; q < S; q += GS_T) {
+        Acc2 acc{0.f, 0.f};
+        int m = 0;
+        const int step = 2 * q + 1;
+        for (int k0 = 0; k0 < S; k0 += GS_CHUNK) {
+            const int k1 = min(k0 + GS_CHUNK, S);
+            float part = 0.f;
+            for (int k = k0; k < k1; ++k) {
+                part = fmaf(ys[k], cosT[cpad(m)], part);
+                m += step;
+                if (m >= S4) m -= S4;
+            }
+            acc_add(acc, part);
+        }
+        x[q] = static_cast<float>(acc_value(acc));
+    }
+}
+
+// out = C^T diag(w) C in, through t (DCT domain); in and out may not alias t
+__device__ void filter(const float *in, float *out, const float *w, float *t, const float *cosT, int S)
+{
+    const double c0 = sqrt(1.0 / S), c1 = sqrt(2.0 / S);
+    dct_fwd(in, t, cosT, S);
+    __syncthreads();
+    for (int k = threadIdx.x; k < S; k += GS_T)
+        t[k] = static_cast<float>(static_cast<double>(t[k]) * w[k] * (k ? c1 : c0));
+    __syncthreads();
+    dct_inv(t, out, cosT, S);
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(GS_T) k_gain_smooth(GainSmoothArgs g)
+{
+    extern __shared__ float sm[];
+    __shared__ double2 s_red[GS_T / 32];
+    const int S = g.nscan, det = blockIdx.x;
+    float *cosT = sm;                  // [cpad(4S)] cos(pi m / (2S)) at cpad(m)
+    float *ah = cosT + cpad(4 * S);    // a / abar
+    float *lh = ah + S;                // lambda / abar
+    float *ph = lh + S;                // 1 / (1 + lambda / abar)
+    float *x = ph + S, *r = x + S, *z = r + S, *p = z + S, *q = p + S, *t = q + S;
+    const int tid = threadIdx.x;
+
+    for (int m = tid; m < 4 * S; m += GS_T)
+        cosT[cpad(m)] = static_cast<float>(cospi(static_cast<double>(m) / (2.0 * S)));
+    // sums of a and b (FP64), bad inputs flagged
+    double sa = 0.0, sb = 0.0;
+    for (int s = tid; s < S; s += GS_T) {
+        const double sg = g.sigma[static_cast<int64_t>(s) * g.ndet + det];
+        const double mu = g.mu[static_cast<int64_t>(s) * g.ndet + det];
+        if (!(sg > 0.0) || !isfinite(sg) || !isfinite(mu)) {
+            set_status(g.status, s * g.ndet + det, TOD_ERR_ARG);
+            continue;
+        }
+        const double a = 1.0 / (sg * sg);
+        sa += a;
+        sb += a * mu;
+    }
+    const double2 ssum = block_sum2(sa, sb, s_red);
+    if (!(ssum.x > 0.0)) return;                                  // uniform: nothing to solve
+    const double gref = ssum.y / ssum.x, abar = ssum.x / S;
+    const double sgp = g.prior[2 * det], alp = g.prior[2 * det + 1];
+    const uint64_t it = g.rng.gibbs_iter_dev ? *g.rng.gibbs_iter_dev : g.rng.gibbs_iter;
+    // scaled right-hand side (b - a g_ref + a^(1/2) w1) / abar, prior term after
+    double rr0 = 0.0;
+    for (int s = tid; s < S; s += GS_T) {
+        const double sg = g.sigma[static_cast<int64_t>(s) * g.ndet + det];
+        const double mu = g.mu[static_cast<int64_t>(s) * g.ndet + det];
+        const double a = (sg > 0.0 && isfinite(sg) && isfinite(mu)) ? 1.0 / (sg * sg) : 0.0;
+        double rhs = a * (mu - gref);
+        const double lam = s ? 1.0 / (sgp * sgp * pow(static_cast<double>(s), alp)) : 0.0;
+        ah[s] = static_cast<float>(a / abar);
+        lh[s] = static_cast<float>(lam / abar);
+        ph[s] = static_cast<float>(1.0 / (1.0 + lam / abar));
+        t[s] = 0.0f;
+        if (g.mode == TOD_MODE_DRAW) {
+            const u64x4 w = philox4x64(static_cast<uint64_t>(s), static_cast<uint64_t>(det),
+                                       TOD_PURPOSE_GAIN_SMOOTH, it, g.rng.seed, g.rng.band);
+            double u[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) u[j] = (static_cast<double>(w.x[j] >> 11) + 0.5) * 1.1102230246251565e-16;
+            const double w1 = sqrt(-2.0 * log(u[0])) * cospi(2.0 * u[1]);
+            const double w2 = sqrt(-2.0 * log(u[2])) * cospi(2.0 * u[3]);
+            rhs += sqrt(a) * w1;
+            // c_k sqrt(lambda_k) w2_k / abar: the inverse transform's input
+            t[s] = static_cast<float>(sqrt(lam) * w2 / abar * (s ? sqrt(2.0 / S) : sqrt(1.0 / S)));
+        }
+        r[s] = static_cast<float>(rhs / abar);
+        x[s] = 0.0f;
+    }
+    __syncthreads();
+    if (g.mode == TOD_MODE_DRAW) {
+        dct_inv(t, z, cosT, S);
+        __syncthreads();
+        for (int s = tid; s < S; s += GS_T) r[s] += z[s];
+    }
+    __syncthreads();
+    for (int s = tid; s < S; s += GS_T) rr0 += static_cast<double>(r[s]) * r[s];
+    const double nrm0 = block_sum2(rr0, 0.0, s_red).x;
+    const double tol2 = static_cast<double>(g.tol) * g.tol * nrm0;
+
+    // z = M^-1 r, p = z
+    filter(r, z, ph, t, cosT, S);
+    double rz = 0.0, rr = 0.0;
+    for (int s = tid; s < S; s += GS_T) {
+        p[s] = z[s];
+        rz += static_cast<double>(r[s]) * z[s];
+        rr += static_cast<double>(r[s]) * r[s];
+    }
+    double2 d2 = block_sum2(rz, rr, s_red);
+    rz = d2.x;
+    rr = d2.y;
+    int iter = 0;
+    while (rr > tol2 && iter < g.maxiter) {
+        // q = A p / abar
+        filter(p, q, lh, t, cosT, S);
+        double pq = 0.0;
+        for (int s = tid; s < S; s += GS_T) {
+            q[s] = fmaf(ah[s], p[s], q[s]);
+            pq += static_cast<double>(p[s]) * q[s];
+        }
+        pq = block_sum2(pq, 0.0, s_red).x;
+        if (!(pq > 0.0)) break;
+        const double al = rz / pq;
+        for (int s = tid; s < S; s += GS_T) {
+            x[s] = static_cast<float>(x[s] + al * p[s]);
+            r[s] = static_cast<float>(r[s] - al * q[s]);
+        }
+        __syncthreads();
+        filter(r, z, ph, t, cosT, S);
+        double rz1 = 0.0, rr1 = 0.0;
+        for (int s = tid; s < S; s += GS_T) {
+            rz1 += static_cast<double>(r[s]) * z[s];
+            rr1 += static_cast<double>(r[s]) * r[s];
+        }
+        d2 = block_sum2(rz1, rr1, s_red);
+        const double be = d2.x / rz;
+        rz = d2.x;
+        rr = d2.y;
+        for (int s = tid; s < S; s += GS_T) p[s] = static_cast<float>(z[s] + be * p[s]);
+        __syncthreads();
+        ++iter;
+    }
+    for (int s = tid; s < S; s += GS_T)
+        g.gain_out[static_cast<int64_t>(s) * g.ndet + det] = gref + static_cast<double>(x[s]);
+    if (tid == 0) {
+        if (g.iters_out) g.iters_out[det] = iter;
+        if (rr > tol2) set_status(g.status, det, TOD_ERR_NOT_CONVERGED);
+    }
+}
+
+}  // namespace
+
+size_t gain_smooth_smem(int nscan)
+{
+    return sizeof(float) * (static_cast<size_t>(cpad(4 * nscan)) + 9u * static_cast<size_t>(nscan));
+}
+
+cudaError_t launch_gain_smooth(const GainSmoothArgs &a, cudaStream_t st)
+{
+    const size_t smem = gain_smooth_smem(a.nscan);
+    cudaError_t e = cudaFuncSetAttribute(k_gain_smooth, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    k_gain_smooth<<<a.ndet, GS_T, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace tg

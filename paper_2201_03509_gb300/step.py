@@ -4,7 +4,9 @@ sequence of the C-ABI calls on one stream.  Holds the device buffers.
 
 With ``data_streams`` the detector data and flags stay compressed on the
 device too (Sect. 4.1; the plan must have them attached) and every step
-decodes them along with the pointing."""
+decodes them along with the pointing.  With ``gain_prior`` each step draws
+every detector's scan gains jointly under the smooth prior across scans
+(tod_sample_gain_smooth) in place of the independent per-scan draws."""
 from __future__ import annotations
 
 import numpy as np
@@ -14,7 +16,8 @@ from . import MODE_DRAW, Plan, Rng
 
 class GibbsTODStep:
     def __init__(self, plan: Plan, psd: np.ndarray, flag_words: np.ndarray | None, rcond_min: float = 1e-6,
-                 cg_tol: float = 1e-6, cg_maxiter: int = 500, data_streams: bool = False):
+                 cg_tol: float = 1e-6, cg_maxiter: int = 500, data_streams: bool = False,
+                 gain_prior: np.ndarray | None = None):
         import torch
         dev = torch.device("cuda", plan.device)
         N, nq, npix = plan.N, plan.nq, plan.npix
@@ -23,6 +26,10 @@ class GibbsTODStep:
         f32, f64, i32 = torch.float32, torch.float64, torch.int32
         self.psd = torch.from_numpy(np.ascontiguousarray(psd, np.float64)).to(dev)
         self.data_streams = data_streams
+        # optional smooth prior across scans: float64[ndet, 2] (sigma_g, alpha_g)
+        self.gain_prior = (None if gain_prior is None else
+                           torch.from_numpy(np.ascontiguousarray(gain_prior, np.float64).reshape(plan.ndet, 2)).to(dev))
+        self.gain_iters = torch.zeros(plan.ndet, dtype=torch.int32, device=dev)
         if data_streams:
             self.flags = torch.zeros((N + 31) // 32, dtype=i32, device=dev)   # decoded every step
         else:
@@ -153,6 +160,10 @@ class GibbsTODStep:
                 p.decode_data(self.d, self.flags, hp)
         p.project(map32_in, self.pix, self.psi, None, self.s, hp)
         p.sample_gain(self.d, self.s, self.flags, self.psd, rng, mode, self.gain, self.mu, self.sigma, hp)
+        if self.gain_prior is not None:
+            # every detector's scans drawn jointly from their conditionals and the prior
+            p.sample_gain_smooth(self.mu, self.sigma, self.gain_prior, rng, mode, self.gain, self.gain_iters,
+                                 stream=hp)
         hp.wait_event(prepared)
         lookahead = self.lookahead
         if lookahead:
@@ -187,7 +198,8 @@ class GibbsTODStep:
 
     @property
     def launches_per_step(self) -> int:
-        return self.LAUNCHES_PER_STEP + (self.DATA_LAUNCHES if self.data_streams else 0)
+        return (self.LAUNCHES_PER_STEP + (self.DATA_LAUNCHES if self.data_streams else 0)
+                + (1 if self.gain_prior is not None else 0))
 
     def capture(self, map32_in, seed: int, band: int = 0, mode: int = MODE_DRAW):
         """Capture one step into a CUDA graph.  The Gibbs iteration is read by
