@@ -105,12 +105,13 @@ std::vector<uint32_t> canonical_codes(const std::vector<uint8_t> &len)
     return code;
 }
 
-// A first-level decode entry in 32 bits: value << 5 | code length, for
-// values that fit in 27 bits; 0 (length 0) sends the decoder to the
-// canonical limits instead.
+// A first-level decode entry in 32 bits: value << 5 | code length.  A value
+// outside (DEC_WIDE, 2^26) is stored as DEC_WIDE with its length (the decoder
+// reads the symbol from the canonical list); an entry 0 (length 0) means a
+// code longer than DEC_LUTB bits, found from the canonical limits.
 int32_t dec_lut_entry(int32_t value, int L)
 {
-    if (value < -(1 << 26) || value >= (1 << 26)) return 0;
+    if (value <= DEC_WIDE || value >= (1 << 26)) value = DEC_WIDE;     // symbol read canonically, length known
     return static_cast<int32_t>((static_cast<uint32_t>(value) << 5) | static_cast<uint32_t>(L));
 }
 
@@ -606,6 +607,7 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
     if ((e = dev_upload(*p, p->off, p->h_off.data(), p->h_off.size()))) return fail(e);
     if ((e = dev_upload(*p, p->status, static_cast<int32_t *>(nullptr), p->nq))) return fail(e);
     if ((e = setup_decode_kernel())) return fail(e);
+    if ((e = setup_gain_smooth_kernel())) return fail(e);
     if ((e = build_huff(*p, p->hpix, band->pix))) return fail(e);
     if ((e = build_huff(*p, p->hpsi, band->psi))) return fail(e);
 

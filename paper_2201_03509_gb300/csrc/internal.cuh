@@ -9,6 +9,7 @@
 namespace tg {
 
 constexpr int DEC_LUTB = 13;          // first-level decode table: 2^13 packed 32-bit entries
+constexpr int32_t DEC_WIDE = -(1 << 26);   // table value: symbol too wide for the entry, read canonically
 constexpr int DEC_T = 512;
 constexpr int NCORR_SCRATCH_F4 = 2;   // float4 per packed slot of the n_corr scratch: filter weights, CG spectra            // decode threads per CTA (one checkpoint block each)
 constexpr int DEC_ROUND = 16;         // symbols staged per thread before a coalesced write
@@ -153,6 +154,7 @@ struct GainSmoothArgs {
     int32_t *status;
 };
 size_t gain_smooth_smem(int nscan);
+cudaError_t setup_gain_smooth_kernel();
 cudaError_t launch_gain_smooth(const GainSmoothArgs &a, cudaStream_t st);
 cudaError_t launch_decode_flags(const Plan &p, uint32_t *flags_out, cudaStream_t st);
 cudaError_t launch_project(const Plan &p, const float4 *map, const int32_t *pix, const uint16_t *psi,

@@ -100,9 +100,15 @@ k_decode(const uint32_t *__restrict__ words, const int64_t *__restrict__ word_of
                 const int32_t e = s_lut[peek >> (32 - DEC_LUTB)];
                 int len = e & 31;
                 int32_t v = e >> 5;
-                if (len == 0) {
-                    int L = 1;            // a long code, or a value too wide for the packed entry
-                    while (L <= TOD_HUFF_MAXLEN && static_cast<unsigned long long>(peek) >= s_lim[L]) ++L;
+                if (len == 0 || v == DEC_WIDE) {
+                    // a code longer than the table (its length found from the
+                    // canonical limits above DEC_LUTB), or a value too wide for
+                    // the packed entry (length known)
+                    int L = len;
+                    if (len == 0) {
+                        L = DEC_LUTB + 1;
+                        while (L <= TOD_HUFF_MAXLEN && static_cast<unsigned long long>(peek) >= s_lim[L]) ++L;
+                    }
                     if (L > TOD_HUFF_MAXLEN) { ok = false; len = 1; v = 0; }
                     else {
                         const int ci = s_base[L] + static_cast<int>(peek >> (32 - L));

@@ -45,49 +45,58 @@ __device__ double2 block_sum2(double u, double v, double2 *s_red)
     return make_double2(su, sv);
 }
 
+// sum_j v_j cos(pi m_j / (2S)) over j = 0..S-1 with m_j = (m0 + j step) mod 4S:
+// four interleaved chains (j = 4i + c), each summing GS_CHUNK terms in FP32
+// before its double-word sum; the chains are merged in a fixed order
+__device__ __forceinline__ double cos_sum(const float *v, int m0, int step, const float *cosT, int S)
+{
+    const int S4 = 4 * S;
+    const int step4 = static_cast<int>((4ll * step) % S4);
+    int m[4];
+    Acc2 acc[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        m[c] = static_cast<int>((static_cast<long long>(m0) + static_cast<long long>(c) * step) % S4);
+        acc[c] = Acc2{0.f, 0.f};
+    }
+    const int S4q = S & ~3;
+    for (int j0 = 0; j0 < S4q; j0 += 4 * GS_CHUNK) {
+        const int j1 = min(j0 + 4 * GS_CHUNK, S4q);
+        float part[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int j = j0; j < j1; j += 4) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                part[c] = fmaf(v[j + c], cosT[cpad(m[c])], part[c]);
+                m[c] += step4;
+                if (m[c] >= S4) m[c] -= S4;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc_add(acc[c], part[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)                                   // the last S mod 4 terms
+        if (S4q + c < S) acc_add(acc[c], v[S4q + c] * cosT[cpad(m[c])]);
+#pragma unroll
+    for (int c = 1; c < 4; ++c) {
+        acc_add(acc[0], acc[c].s);
+        acc[0].c = __fadd_rn(acc[0].c, acc[c].c);
+    }
+    return acc_value(acc[0]);
+}
+
 // y_k = c_k sum_q x_q cos(pi k (2q+1) / (2S)), c_0 = sqrt(1/S), c_k = sqrt(2/S)
 __device__ void dct_fwd(const float *x, float *y, const float *cosT, int S)
 {
-    const int S4 = 4 * S;
     const double c0 = sqrt(1.0 / S), c1 = sqrt(2.0 / S);
-    for (int k = threadIdx.x; k < S; k += GS_T) {
-        Acc2 acc{0.f, 0.f};
-        int m = k;
-        const int step = 2 * k;
-        for (int q0 = 0; q0 < S; q0 += GS_CHUNK) {
-            const int q1 = min(q0 + GS_CHUNK, S);
-            float part = 0.f;
-            for (int q = q0; q < q1; ++q) {
-                part = fmaf(x[q], cosT[cpad(m)], part);
-                m += step;
-                if (m >= S4) m -= S4;
-            }
-            acc_add(acc, part);
-        }
-        y[k] = static_cast<float>(acc_value(acc) * (k ? c1 : c0));
-    }
+    for (int k = threadIdx.x; k < S; k += GS_T)
+        y[k] = static_cast<float>(cos_sum(x, k, 2 * k, cosT, S) * (k ? c1 : c0));
 }
 
 // x_q = sum_k c_k y_k cos(pi k (2q+1) / (2S)); ys holds c_k y_k
 __device__ void dct_inv(const float *ys, float *x, const float *cosT, int S)
 {
-    const int S4 = 4 * S;
-    for (int q = threadIdx.x; q < S; q += GS_T) {
-        Acc2 acc{0.f, 0.f};
-        int m = 0;
-        const int step = 2 * q + 1;
-        for (int k0 = 0; k0 < S; k0 += GS_CHUNK) {
-            const int k1 = min(k0 + GS_CHUNK, S);
-            float part = 0.f;
-            for (int k = k0; k < k1; ++k) {
-                part = fmaf(ys[k], cosT[cpad(m)], part);
-                m += step;
-                if (m >= S4) m -= S4;
-            }
-            acc_add(acc, part);
-        }
-        x[q] = static_cast<float>(acc_value(acc));
-    }
+    for (int q = threadIdx.x; q < S; q += GS_T) x[q] = static_cast<float>(cos_sum(ys, 0, 2 * q + 1, cosT, S));
 }
 
 // out = C^T diag(w) C in, through t (DCT domain); in and out may not alias t
@@ -230,13 +239,16 @@ size_t gain_smooth_smem(int nscan)
     return sizeof(float) * (static_cast<size_t>(cpad(4 * nscan)) + 9u * static_cast<size_t>(nscan));
 }
 
+// once per plan (outside any stream capture): room for the largest scan count
+cudaError_t setup_gain_smooth_kernel()
+{
+    return cudaFuncSetAttribute(k_gain_smooth, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(gain_smooth_smem(TOD_GAIN_SMOOTH_MAX_SCANS)));
+}
+
 cudaError_t launch_gain_smooth(const GainSmoothArgs &a, cudaStream_t st)
 {
-    const size_t smem = gain_smooth_smem(a.nscan);
-    cudaError_t e = cudaFuncSetAttribute(k_gain_smooth, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    k_gain_smooth<<<a.ndet, GS_T, smem, st>>>(a);
+    k_gain_smooth<<<a.ndet, GS_T, gain_smooth_smem(a.nscan), st>>>(a);
     return cudaGetLastError();
 }
 

@@ -106,3 +106,66 @@ def test_step_with_data_streams_equals_step_fed_decoded_data(dw, lookahead):
             assert torch.equal(getattr(a, name), getattr(b, name)), (it, name)
         assert torch.equal(a.d, b.d) and torch.equal(a.flags, b.flags)
     assert a.launches_per_step == b.launches_per_step + 2
+
+
+def test_graph_replay_with_data_streams_and_gain_prior(dw):
+    """A captured step that decodes its own data and draws the gains under
+    the smooth prior replays bit for bit like the eager step."""
+    import torch
+    import paper_2201_03509_gb300 as tg
+    from paper_2201_03509_gb300.step import GibbsTODStep
+    band, plan = dw["band"], dw["plan"]
+    m4 = np.zeros((band.npix, 4), np.float32)
+    m4[:, :3] = band.map_tqu.T
+    t_map = torch.from_numpy(m4).to("cuda:0")
+    prior = np.array([[2e-3, -2.0]] * dw["cfg"].ndet)
+    step = GibbsTODStep(plan, band.psd, None, data_streams=True, gain_prior=prior)
+    step.lookahead = False
+    step.run(t_map, tg.Rng(3, 0, 5), tg.MODE_DRAW)
+    torch.cuda.synchronize()
+    plan.status()
+    ref = [t.clone() for t in (step.gain, step.ncorr, step.map, step.d, step.flags)]
+    step.capture(t_map, 3, 0, tg.MODE_DRAW)
+    step.replay(5)
+    torch.cuda.synchronize()
+    plan.status()
+    for a, b in zip(ref, (step.gain, step.ncorr, step.map, step.d, step.flags)):
+        assert torch.equal(a, b)
+    assert step.gain_iters.min().item() >= 1
+
+
+def test_decode_wide_values_and_long_codes(dw):
+    """ADC counts whose differences include values too wide for the packed
+    table entry (|delta| >= 2^26) and many rare symbols (codes longer than
+    the 13-bit table) decode bit for bit."""
+    import torch
+    import paper_2201_03509_gb300 as tg
+    cfg, off, ing = dw["cfg"], dw["off"], dw["ing"]
+    rng = np.random.default_rng(11)
+    N = int(off[-1])
+    counts = np.empty(N, np.int64)
+    for q in range(len(off) - 1):
+        n = int(off[q + 1] - off[q])
+        dl = rng.integers(-3, 4, n)
+        rare = rng.random(n) < 0.05
+        dl[rare] = rng.integers(-5000, 5000, rare.sum())             # many distinct, long codes
+        wide = np.flatnonzero(rng.random(n) < 0.002)
+        # jumps of 2^26 .. 2^27 with alternating signs: the walk stays bounded
+        dl[wide] = np.where(np.arange(len(wide)) % 2 == 0, 1, -1) * rng.integers(1 << 26, 1 << 27, len(wide))
+        c = np.cumsum(dl)
+        c -= (c.max() + c.min()) // 2                              # centred: |c| well inside int32
+        assert np.abs(c).max() < 2 ** 30
+        counts[off[q]:off[q + 1]] = c
+    st = tg.huff_encode(cfg.ndet, cfg.nscan, off, counts.astype(np.int32))
+    if dw["ragged"]:                                               # 4 detscans per code: rare symbols get long codes
+        assert st["sym_len"].max() > 13
+    scale = np.full(len(off) - 1, 2.0 ** -10)
+    plan = tg.Plan(cfg.nside, cfg.ndet, cfg.nscan, cfg.fsamp, off, ing["pix_streams"], ing["psi_streams"])
+    plan.attach_data(st, scale, ing["flag_streams"], ing["flag_select"])
+    d = torch.empty(N, dtype=torch.float32, device="cuda:0")
+    plan.decode_data(d, None)
+    plan.status()
+    want = oracle.decode_tod(st, off, cfg.ndet, scale)
+    assert np.array_equal(d.cpu().numpy().view(np.uint32), want.view(np.uint32))
+    assert np.array_equal(oracle.decode_band(st, off, cfg.ndet), counts)
+    plan.close()
