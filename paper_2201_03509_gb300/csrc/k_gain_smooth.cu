@@ -27,8 +27,10 @@ constexpr int GS_CHUNK = 16;          // terms summed in FP32 before entering th
 
 __host__ __device__ __forceinline__ int cpad(int m) { return m + (m >> 5); }
 
-// FP64 block sum of two per-thread values, fixed order (warp trees, then
-// the warps in order); every thread gets both sums.
+// FP64 block sum of two per-thread values, fixed order (warp trees, then a
+// tree over the warps in warp 0); every thread gets both sums.  s_red holds
+// GS_T / 32 + 1 entries.  (GB300 issues FP64 at a low rate: the sum over the
+// warps is done once, not by every thread.)
 __device__ double2 block_sum2(double u, double v, double2 *s_red)
 {
 #pragma unroll
@@ -36,13 +38,22 @@ __device__ double2 block_sum2(double u, double v, double2 *s_red)
         u += __shfl_xor_sync(0xffffffffu, u, o);
         v += __shfl_xor_sync(0xffffffffu, v, o);
     }
-    const int w = threadIdx.x >> 5;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __syncthreads();                            // s_red free from the previous use
-    if ((threadIdx.x & 31) == 0) s_red[w] = make_double2(u, v);
+    if (lane == 0) s_red[w] = make_double2(u, v);
     __syncthreads();
-    double su = 0.0, sv = 0.0;
-    for (int i = 0; i < GS_T / 32; ++i) { su += s_red[i].x; sv += s_red[i].y; }
-    return make_double2(su, sv);
+    if (w == 0) {
+        static_assert(GS_T / 32 == 32, "one partial per lane of warp 0");
+        double su = s_red[lane].x, sv = s_red[lane].y;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            su += __shfl_xor_sync(0xffffffffu, su, o);
+            sv += __shfl_xor_sync(0xffffffffu, sv, o);
+        }
+        if (lane == 0) s_red[GS_T / 32] = make_double2(su, sv);
+    }
+    __syncthreads();
+    return s_red[GS_T / 32];
 }
 
 // sum_j v_j cos(pi m_j / (2S)) over j = 0..S-1 with m_j = (m0 + j step) mod 4S:
@@ -86,11 +97,11 @@ __device__ __forceinline__ double cos_sum(const float *v, int m0, int step, cons
 }
 
 // y_k = c_k sum_q x_q cos(pi k (2q+1) / (2S)), c_0 = sqrt(1/S), c_k = sqrt(2/S)
-__device__ void dct_fwd(const float *x, float *y, const float *cosT, int S)
+// (c = (c_0, c_k), computed once per CTA)
+__device__ void dct_fwd(const float *x, float *y, const float *cosT, int S, double2 c)
 {
-    const double c0 = sqrt(1.0 / S), c1 = sqrt(2.0 / S);
     for (int k = threadIdx.x; k < S; k += GS_T)
-        y[k] = static_cast<float>(cos_sum(x, k, 2 * k, cosT, S) * (k ? c1 : c0));
+        y[k] = static_cast<float>(cos_sum(x, k, 2 * k, cosT, S) * (k ? c.y : c.x));
 }
 
 // x_q = sum_k c_k y_k cos(pi k (2q+1) / (2S)); ys holds c_k y_k
@@ -100,13 +111,13 @@ __device__ void dct_inv(const float *ys, float *x, const float *cosT, int S)
 }
 
 // out = C^T diag(w) C in, through t (DCT domain); in and out may not alias t
-__device__ void filter(const float *in, float *out, const float *w, float *t, const float *cosT, int S)
+__device__ void filter(const float *in, float *out, const float *w, float *t, const float *cosT, int S,
+                       double2 c)
 {
-    const double c0 = sqrt(1.0 / S), c1 = sqrt(2.0 / S);
-    dct_fwd(in, t, cosT, S);
+    dct_fwd(in, t, cosT, S, c);
     __syncthreads();
     for (int k = threadIdx.x; k < S; k += GS_T)
-        t[k] = static_cast<float>(static_cast<double>(t[k]) * w[k] * (k ? c1 : c0));
+        t[k] = static_cast<float>(static_cast<double>(t[k]) * w[k] * (k ? c.y : c.x));
     __syncthreads();
     dct_inv(t, out, cosT, S);
     __syncthreads();
@@ -115,7 +126,8 @@ __device__ void filter(const float *in, float *out, const float *w, float *t, co
 __global__ void __launch_bounds__(GS_T) k_gain_smooth(GainSmoothArgs g)
 {
     extern __shared__ float sm[];
-    __shared__ double2 s_red[GS_T / 32];
+    __shared__ double2 s_red[GS_T / 32 + 1];
+    __shared__ double2 s_c;
     const int S = g.nscan, det = blockIdx.x;
     float *cosT = sm;                  // [cpad(4S)] cos(pi m / (2S)) at cpad(m)
     float *ah = cosT + cpad(4 * S);    // a / abar
@@ -124,8 +136,19 @@ __global__ void __launch_bounds__(GS_T) k_gain_smooth(GainSmoothArgs g)
     float *x = ph + S, *r = x + S, *z = r + S, *p = z + S, *q = p + S, *t = q + S;
     const int tid = threadIdx.x;
 
-    for (int m = tid; m < 4 * S; m += GS_T)
+    // quarter wave in FP64 (m <= S), the rest by symmetry; the normalisation once
+    for (int m = tid; m <= S; m += GS_T)
         cosT[cpad(m)] = static_cast<float>(cospi(static_cast<double>(m) / (2.0 * S)));
+    if (tid == 0) s_c = make_double2(sqrt(1.0 / S), sqrt(2.0 / S));
+    __syncthreads();
+    for (int m = S + 1 + tid; m < 4 * S; m += GS_T) {
+        float v;
+        if (m <= 2 * S) v = -cosT[cpad(2 * S - m)];
+        else if (m <= 3 * S) v = -cosT[cpad(m - 2 * S)];
+        else v = cosT[cpad(4 * S - m)];
+        cosT[cpad(m)] = v;
+    }
+    const double2 cn = s_c;
     // sums of a and b (FP64), bad inputs flagged
     double sa = 0.0, sb = 0.0;
     for (int s = tid; s < S; s += GS_T) {
@@ -142,7 +165,8 @@ __global__ void __launch_bounds__(GS_T) k_gain_smooth(GainSmoothArgs g)
     const double2 ssum = block_sum2(sa, sb, s_red);
     if (!(ssum.x > 0.0)) return;                                  // uniform: nothing to solve
     const double gref = ssum.y / ssum.x, abar = ssum.x / S;
-    const double sgp = g.prior[2 * det], alp = g.prior[2 * det + 1];
+    const float sgpf = static_cast<float>(g.prior[2 * det]), alpf = static_cast<float>(g.prior[2 * det + 1]);
+    const float sg2f = sgpf * sgpf, abarf = static_cast<float>(abar);
     const uint64_t it = g.rng.gibbs_iter_dev ? *g.rng.gibbs_iter_dev : g.rng.gibbs_iter;
     // scaled right-hand side (b - a g_ref + a^(1/2) w1) / abar, prior term after
     double rr0 = 0.0;
@@ -151,10 +175,12 @@ __global__ void __launch_bounds__(GS_T) k_gain_smooth(GainSmoothArgs g)
         const double mu = g.mu[static_cast<int64_t>(s) * g.ndet + det];
         const double a = (sg > 0.0 && isfinite(sg) && isfinite(mu)) ? 1.0 / (sg * sg) : 0.0;
         double rhs = a * (mu - gref);
-        const double lam = s ? 1.0 / (sgp * sgp * pow(static_cast<double>(s), alp)) : 0.0;
+        // lambda_k / abar in FP32 (it is stored in FP32)
+        const float lam = s ? exp2f(-alpf * log2f(static_cast<float>(s))) / sg2f : 0.0f;
+        const float lamh = lam / abarf;
         ah[s] = static_cast<float>(a / abar);
-        lh[s] = static_cast<float>(lam / abar);
-        ph[s] = static_cast<float>(1.0 / (1.0 + lam / abar));
+        lh[s] = lamh;
+        ph[s] = 1.0f / (1.0f + lamh);
         t[s] = 0.0f;
         if (g.mode == TOD_MODE_DRAW) {
             const u64x4 w = philox4x64(static_cast<uint64_t>(s), static_cast<uint64_t>(det),
@@ -166,7 +192,7 @@ __global__ void __launch_bounds__(GS_T) k_gain_smooth(GainSmoothArgs g)
             const double w2 = sqrt(-2.0 * log(u[2])) * cospi(2.0 * u[3]);
             rhs += sqrt(a) * w1;
             // c_k sqrt(lambda_k) w2_k / abar: the inverse transform's input
-            t[s] = static_cast<float>(sqrt(lam) * w2 / abar * (s ? sqrt(2.0 / S) : sqrt(1.0 / S)));
+            t[s] = sqrtf(lam) / abarf * static_cast<float>(w2 * (s ? cn.y : cn.x));
         }
         r[s] = static_cast<float>(rhs / abar);
         x[s] = 0.0f;
@@ -183,7 +209,7 @@ __global__ void __launch_bounds__(GS_T) k_gain_smooth(GainSmoothArgs g)
     const double tol2 = static_cast<double>(g.tol) * g.tol * nrm0;
 
     // z = M^-1 r, p = z
-    filter(r, z, ph, t, cosT, S);
+    filter(r, z, ph, t, cosT, S, cn);
     double rz = 0.0, rr = 0.0;
     for (int s = tid; s < S; s += GS_T) {
         p[s] = z[s];
@@ -196,7 +222,7 @@ __global__ void __launch_bounds__(GS_T) k_gain_smooth(GainSmoothArgs g)
     int iter = 0;
     while (rr > tol2 && iter < g.maxiter) {
         // q = A p / abar
-        filter(p, q, lh, t, cosT, S);
+        filter(p, q, lh, t, cosT, S, cn);
         double pq = 0.0;
         for (int s = tid; s < S; s += GS_T) {
             q[s] = fmaf(ah[s], p[s], q[s]);
@@ -210,7 +236,7 @@ __global__ void __launch_bounds__(GS_T) k_gain_smooth(GainSmoothArgs g)
             r[s] = static_cast<float>(r[s] - al * q[s]);
         }
         __syncthreads();
-        filter(r, z, ph, t, cosT, S);
+        filter(r, z, ph, t, cosT, S, cn);
         double rz1 = 0.0, rr1 = 0.0;
         for (int s = tid; s < S; s += GS_T) {
             rz1 += static_cast<double>(r[s]) * z[s];
