@@ -7,9 +7,9 @@
 //   A g = b + a^(1/2) w1 + C^T (lambda^(1/2) w2),  A = diag(a) + C^T diag(lambda) C.
 // One CTA per detector solves it by preconditioned CG for the fluctuation
 // x = g - g_ref about the weighted mean g_ref = sum b / sum a (A g_ref =
-// a g_ref: the prior does not see a constant), scaled by the mean of a.
-// The preconditioner C^T diag(1 / (1 + lambda/abar)) C is A^-1 exactly when
-// every scan has the same a.  Transforms are direct sums over a shared
+// a g_ref: the prior does not see a constant), scaled by the mean of a, in
+// the DCT domain, where the preconditioner diag(1 / (1 + lambda/abar)) is
+// (C A C^T)^-1 exactly when every scan has the same a.  Transforms are direct sums over a shared
 // quarter-wave cosine table (a detector has at most a few thousand scans),
 // FP32 products in double-word sums, dot products in FP64, every sum in a
 // fixed order: deterministic.  The table is padded by one word every 32
@@ -110,19 +110,6 @@ __device__ void dct_inv(const float *ys, float *x, const float *cosT, int S)
     for (int q = threadIdx.x; q < S; q += GS_T) x[q] = static_cast<float>(cos_sum(ys, 0, 2 * q + 1, cosT, S));
 }
 
-// out = C^T diag(w) C in, through t (DCT domain); in and out may not alias t
-__device__ void filter(const float *in, float *out, const float *w, float *t, const float *cosT, int S,
-                       double2 c)
-{
-    dct_fwd(in, t, cosT, S, c);
-    __syncthreads();
-    for (int k = threadIdx.x; k < S; k += GS_T)
-        t[k] = static_cast<float>(static_cast<double>(t[k]) * w[k] * (k ? c.y : c.x));
-    __syncthreads();
-    dct_inv(t, out, cosT, S);
-    __syncthreads();
-}
-
 __global__ void __launch_bounds__(GS_T) k_gain_smooth(GainSmoothArgs g)
 {
     extern __shared__ float sm[];
@@ -168,8 +155,10 @@ __global__ void __launch_bounds__(GS_T) k_gain_smooth(GainSmoothArgs g)
     const float sgpf = static_cast<float>(g.prior[2 * det]), alpf = static_cast<float>(g.prior[2 * det + 1]);
     const float sg2f = sgpf * sgpf, abarf = static_cast<float>(abar);
     const uint64_t it = g.rng.gibbs_iter_dev ? *g.rng.gibbs_iter_dev : g.rng.gibbs_iter;
-    // scaled right-hand side (b - a g_ref + a^(1/2) w1) / abar, prior term after
-    double rr0 = 0.0;
+    // The solve runs in the DCT domain (hats: C v): there the prior and the
+    // preconditioner are diagonal, C A C^T v^ = C (a o C^T v^) + lambda o v^,
+    // so an iteration takes two transforms.  Scaled by 1/abar throughout.
+    // Right-hand side: C ((b - a g_ref + a^(1/2) w1) / abar) + lambda^(1/2) w2 / abar.
     for (int s = tid; s < S; s += GS_T) {
         const double sg = g.sigma[static_cast<int64_t>(s) * g.ndet + det];
         const double mu = g.mu[static_cast<int64_t>(s) * g.ndet + det];
@@ -191,67 +180,74 @@ __global__ void __launch_bounds__(GS_T) k_gain_smooth(GainSmoothArgs g)
             const double w1 = sqrt(-2.0 * log(u[0])) * cospi(2.0 * u[1]);
             const double w2 = sqrt(-2.0 * log(u[2])) * cospi(2.0 * u[3]);
             rhs += sqrt(a) * w1;
-            // c_k sqrt(lambda_k) w2_k / abar: the inverse transform's input
-            t[s] = sqrtf(lam) / abarf * static_cast<float>(w2 * (s ? cn.y : cn.x));
+            t[s] = sqrtf(lam) / abarf * static_cast<float>(w2);      // prior term, mode s of the DCT
         }
-        r[s] = static_cast<float>(rhs / abar);
+        z[s] = static_cast<float>(rhs / abar);
         x[s] = 0.0f;
     }
     __syncthreads();
-    if (g.mode == TOD_MODE_DRAW) {
-        dct_inv(t, z, cosT, S);
-        __syncthreads();
-        for (int s = tid; s < S; s += GS_T) r[s] += z[s];
-    }
+    dct_fwd(z, r, cosT, S, cn);
     __syncthreads();
-    for (int s = tid; s < S; s += GS_T) rr0 += static_cast<double>(r[s]) * r[s];
-    const double nrm0 = block_sum2(rr0, 0.0, s_red).x;
-    const double tol2 = static_cast<double>(g.tol) * g.tol * nrm0;
-
-    // z = M^-1 r, p = z
-    filter(r, z, ph, t, cosT, S, cn);
+    // r^ (with the prior term), z^ = M^-1 r^ = ph o r^, p^ = z^
     double rz = 0.0, rr = 0.0;
-    for (int s = tid; s < S; s += GS_T) {
-        p[s] = z[s];
-        rz += static_cast<double>(r[s]) * z[s];
-        rr += static_cast<double>(r[s]) * r[s];
+    for (int k = tid; k < S; k += GS_T) {
+        const float rk = r[k] + t[k];
+        const float zk = ph[k] * rk;
+        r[k] = rk;
+        z[k] = zk;
+        p[k] = zk;
+        rz += static_cast<double>(rk) * zk;
+        rr += static_cast<double>(rk) * rk;
     }
     double2 d2 = block_sum2(rz, rr, s_red);
     rz = d2.x;
     rr = d2.y;
+    const double tol2 = static_cast<double>(g.tol) * g.tol * rr;
     int iter = 0;
     while (rr > tol2 && iter < g.maxiter) {
-        // q = A p / abar
-        filter(p, q, lh, t, cosT, S, cn);
+        // q^ = C (ah o C^T p^) + lh o p^   (z is free here: it is rebuilt below)
+        for (int k = tid; k < S; k += GS_T)
+            t[k] = static_cast<float>(static_cast<double>(p[k]) * (k ? cn.y : cn.x));
+        __syncthreads();
+        dct_inv(t, z, cosT, S);
+        __syncthreads();
+        for (int s = tid; s < S; s += GS_T) z[s] *= ah[s];
+        __syncthreads();
+        dct_fwd(z, q, cosT, S, cn);
+        __syncthreads();
         double pq = 0.0;
-        for (int s = tid; s < S; s += GS_T) {
-            q[s] = fmaf(ah[s], p[s], q[s]);
-            pq += static_cast<double>(p[s]) * q[s];
+        for (int k = tid; k < S; k += GS_T) {
+            q[k] = fmaf(lh[k], p[k], q[k]);
+            pq += static_cast<double>(p[k]) * q[k];
         }
         pq = block_sum2(pq, 0.0, s_red).x;
         if (!(pq > 0.0)) break;
         const double al = rz / pq;
-        for (int s = tid; s < S; s += GS_T) {
-            x[s] = static_cast<float>(x[s] + al * p[s]);
-            r[s] = static_cast<float>(r[s] - al * q[s]);
-        }
-        __syncthreads();
-        filter(r, z, ph, t, cosT, S, cn);
         double rz1 = 0.0, rr1 = 0.0;
-        for (int s = tid; s < S; s += GS_T) {
-            rz1 += static_cast<double>(r[s]) * z[s];
-            rr1 += static_cast<double>(r[s]) * r[s];
+        for (int k = tid; k < S; k += GS_T) {
+            x[k] = static_cast<float>(x[k] + al * p[k]);
+            const float rk = static_cast<float>(r[k] - al * q[k]);
+            const float zk = ph[k] * rk;
+            r[k] = rk;
+            z[k] = zk;
+            rz1 += static_cast<double>(rk) * zk;
+            rr1 += static_cast<double>(rk) * rk;
         }
         d2 = block_sum2(rz1, rr1, s_red);
         const double be = d2.x / rz;
         rz = d2.x;
         rr = d2.y;
-        for (int s = tid; s < S; s += GS_T) p[s] = static_cast<float>(z[s] + be * p[s]);
+        for (int k = tid; k < S; k += GS_T) p[k] = static_cast<float>(z[k] + be * p[k]);
         __syncthreads();
         ++iter;
     }
+    // back to the scan domain: x = C^T x^
+    for (int k = tid; k < S; k += GS_T) t[k] = static_cast<float>(static_cast<double>(x[k]) * (k ? cn.y : cn.x));
+    __syncthreads();
+    dct_inv(t, z, cosT, S);
+    __syncthreads();
     for (int s = tid; s < S; s += GS_T)
-        g.gain_out[static_cast<int64_t>(s) * g.ndet + det] = gref + static_cast<double>(x[s]);
+        g.gain_out[static_cast<int64_t>(s) * g.ndet + det] = gref + static_cast<double>(z[s]);
     if (tid == 0) {
         if (g.iters_out) g.iters_out[det] = iter;
         if (rr > tol2) set_status(g.status, det, TOD_ERR_NOT_CONVERGED);
