@@ -73,3 +73,22 @@ def test_tod_compression_matches_the_paper_table(band_ing):
     assert 8.6 < bits < 9.8, bits
     fbits = ing["flag_streams"]["nbits"].sum() / ing["offsets"][-1]
     assert 1.0 <= fbits < 1.2, fbits          # one bit per sample is a symbol code's floor
+
+
+def test_round_trip_wide_differences_and_long_codes():
+    """Counts whose differences reach +-2^27 and a heavy tail of rare
+    symbols (codes longer than 13 bits) round-trip exactly."""
+    rng = np.random.default_rng(12)
+    vals = []
+    for n in (20000, 20000, 15001, 15001):
+        dl = rng.integers(-3, 4, n)
+        rare = rng.random(n) < 0.05
+        dl[rare] = rng.integers(-5000, 5000, rare.sum())
+        wide = np.flatnonzero(rng.random(n) < 0.003)
+        dl[wide] = np.where(np.arange(len(wide)) % 2 == 0, 1, -1) * rng.integers(1 << 26, 1 << 27, len(wide))
+        vals.append(np.cumsum(dl))
+    st = oracle.encode_band_streams(vals, 2)
+    assert st["sym_len"].max() > 13
+    assert np.abs(st["sym_vals"]).max() >= 2 ** 26
+    off = np.concatenate([[0], np.cumsum([len(v) for v in vals])]).astype(np.int64)
+    assert np.array_equal(oracle.decode_band(st, off, 2), np.concatenate(vals))
