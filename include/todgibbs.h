@@ -19,10 +19,13 @@
  *    pointers owned by the caller; the library never frees them.  Calls are
  *    asynchronous on the given stream (0 = legacy default stream), return
  *    after enqueueing, and only argument errors are reported immediately.
- *    Faults found on the device (corrupt stream, CG not converged, bounded
- *    wait timed out) are recorded per detscan and read with
- *    tod_plan_status() after the stream is synchronised.  No call traps the
- *    GPU.
+ *    Faults found on the device (a data stream that does not decode, CG not
+ *    converged, a detscan without usable samples or with non-finite sums)
+ *    are recorded per detscan and read with tod_plan_status() after the
+ *    stream is synchronised.  No call traps the GPU.  Non-finite detector
+ *    data are not checked sample by sample: they surface as TOD_ERR_ARG
+ *    from the gain draw (non-finite sums) and TOD_ERR_NOT_CONVERGED from
+ *    the gap filling of flagged detscans.
  *  - flags: bit (t & 31) of word (t >> 5) is 1 when sample t (global index)
  *    is flagged (excluded: M_t = 0).
  *  - psd: double[ndet][3] = (sigma0 [data units], f_knee [Hz], alpha < 0).
@@ -47,7 +50,7 @@ typedef int32_t tod_status;
 #define TOD_ERR_ARG           -1   /* bad argument; nothing was enqueued */
 #define TOD_ERR_CORRUPT_STREAM -2  /* a Huffman stream did not decode */
 #define TOD_ERR_NOT_CONVERGED -3   /* CG gap filling hit its iteration cap */
-#define TOD_ERR_TIMEOUT       -4   /* a bounded device-side wait gave up */
+#define TOD_ERR_TIMEOUT       -4   /* reserved: no call of this library waits on the device */
 #define TOD_ERR_CUDA          -5   /* a CUDA runtime call failed */
 #define TOD_ERR_OOM           -6   /* device or host allocation failed */
 #define TOD_ERR_UNIMPLEMENTED -7
@@ -138,7 +141,8 @@ typedef struct {
     const int64_t *offsets; /* HOST [ndet*nscan+1]; every length an FFT length */
     tod_huff_streams pix;   /* HOST compressed pixel stream */
     tod_huff_streams psi;   /* HOST compressed psi-bin stream */
-    int32_t cluster_size;   /* 0 = choose (most SMs busy); else 1..16 CTAs per detscan transform */
+    int32_t tile_pairs;     /* column pairs per tile of the transforms' column passes: 0 = choose
+                               (up to 16), else a cap 1..2048 */
     int32_t device;         /* CUDA device ordinal the plan lives on */
     int32_t max_radix;      /* largest Stockham radix of the transforms: 0 = 16; else 2..16 */
 } tod_band_desc;
@@ -161,24 +165,27 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band);
 tod_status tod_plan_destroy(tod_plan *p);
 /* Sizes of the plan (host scalars; any pointer may be NULL). */
 tod_status tod_plan_info(const tod_plan *p, int64_t *nsamples, int32_t *ndetscan,
-                         int32_t *npix, int32_t *cluster_size, int64_t *device_bytes);
+                         int32_t *npix, int32_t *tile_pairs, int64_t *device_bytes);
 /* Synchronises the device, copies the per-detscan status words
  * (TOD_OK or an error code) into HOST int32[ndetscan] (may be NULL), clears
  * them, and returns the first error found (TOD_OK if none). */
 tod_status tod_plan_status(tod_plan *p, int32_t *detscan_status);
 
 /* Launch schedule of the transform stages (gain, n_corr):
- * TOD_SCHED_PERSISTENT (default): one persistent cluster launch per stage
- * over the work list sorted by decreasing length;
- * TOD_SCHED_PER_SCAN: one launch of one cluster per detscan (the plain
- * per-scan path, kept for comparison).  Results are identical. */
+ * TOD_SCHED_PERSISTENT (default): every pass of a stage is one launch over
+ * the tiles of all detscans (the n_corr draw is one cooperative launch);
+ * TOD_SCHED_PER_SCAN: the same kernels launched once per detscan (the
+ * plain per-scan path, kept for comparison).  Results are identical: each
+ * detscan's arithmetic does not depend on the others or on the launch. */
 #define TOD_SCHED_PERSISTENT 0
 #define TOD_SCHED_PER_SCAN   1
 tod_status tod_plan_set_schedule(tod_plan *p, int32_t schedule);
 
 /* A1 -- Huffman decode + undo differencing (Sect. 4.1).
- * pix_out int32[N], psi_out uint16[N] (device).  Bit-exact; a stream that
- * does not decode marks its detscan TOD_ERR_CORRUPT_STREAM. */
+ * pix_out int32[N], psi_out uint16[N] (device).  Bit-exact.  The pointing
+ * streams are decoded once on the host by tod_plan_create (to build the
+ * binning order), which rejects a stream that does not decode, so the
+ * device-side check (TOD_ERR_CORRUPT_STREAM) cannot fire here. */
 tod_status tod_decode(tod_plan *p, int32_t *pix_out, uint16_t *psi_out, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------------
@@ -246,6 +253,11 @@ tod_status tod_decode_data(tod_plan *p, float *d_out, uint32_t *flags_out, cudaS
 tod_status tod_project(tod_plan *p, const void *map_tqu, const int32_t *pix,
                        const uint16_t *psi, const double *gain, float *s_out,
                        cudaStream_t stream);
+/* tod_project in FP64: map double[3][npix] (rows T, Q, U, the layout of
+ * tod_solve_maps), the same tabulated cos 2psi, sin 2psi values, s_out
+ * double[N]; for the FP64 chi^2 and its finite-difference checks. */
+tod_status tod_project_f64(tod_plan *p, const double *map, const int32_t *pix, const uint16_t *psi,
+                           const double *gain, double *s_out, cudaStream_t stream);
 
 /* A4 -- gain draw (the gain conditional of Eq. `gibbsstart`; n_corr marginalised, so
  * the full noise PSD weights the fit).  Per detscan, with shat = C(M s),
@@ -306,33 +318,40 @@ tod_status tod_sample_ncorr_prepared(tod_plan *p, const float *d, const float *s
 
 /* tod_sample_ncorr_static -- tod_sample_ncorr with nothing allocated.
  * The paper has no counterpart: it is a library convenience.  Same
- * arguments, results and errors as tod_sample_ncorr, except that the
- * per-cluster scratch (filter weights and CG spectra) comes from one fixed
- * device array compiled into the library (TOD_NCORR_STATIC_SCRATCH_BYTES per
- * device)
- * instead of the plan's buffer.  It is for callers that must not allocate
- * device memory once they run: a process whose free device memory is all
- * held by another allocator's pool (so a new allocation fails or forces that
- * pool to release), or a pipeline whose policy forbids allocation after
- * start-up.  The call never calls an allocating routine.
- *   Set-up: call tod_ncorr_static_setup once per device, with the plan, on
- *   the host before the first draw and before any stream capture; it looks
- *   up the array's device address (cudaGetSymbolAddress on the plan's
- *   device) and caches it.  A first draw without it does the lookup itself.
- *   Size: each cluster of the draw needs C x sz x 32 bytes (C the cluster
- *   size, sz the plan's per-CTA transform buffer); the draw runs with as
- *   many clusters as fit (fewer than tod_sample_ncorr may use, so it can be
- *   slower) and returns TOD_ERR_SCRATCH, enqueuing nothing, when not even
- *   one cluster fits.  The setup call reports the cluster count that fits
- *   in *max_clusters_out (may be NULL) and returns TOD_ERR_SCRATCH likewise.
- *   Contents: every cluster writes its scratch before it reads it, so no
- *   part of the array must start at zero.
+ * arguments, results and errors as tod_sample_ncorr, except that the draw's
+ * working memory (the transforms' complex intermediate, the flag-word
+ * prefix and the CG vectors) comes from one fixed device array compiled into
+ * the library (TOD_NCORR_STATIC_SCRATCH_BYTES per device) instead of the
+ * plan's buffers.  It is for callers that must not allocate device memory
+ * once they run: a process whose free device memory is all held by another
+ * allocator's pool (so a new allocation fails or forces that pool to
+ * release), or a pipeline whose policy forbids allocation after start-up.
+ *   Set-up: call tod_ncorr_static_setup once per device, with a plan of that
+ *   device, on the host before the first draw and before any stream
+ *   capture.  It looks up the array's device address (cudaGetSymbolAddress
+ *   with the plan's device current) and caches it; that lookup is what
+ *   loads the array's module and so backs the array with device memory
+ *   (with CUDA_MODULE_LOADING=EAGER every process that loads the library
+ *   backs it at context creation, used or not).  A draw on a device where
+ *   set-up has not run returns TOD_ERR_ARG and enqueues nothing; the draw
+ *   itself calls no allocating routine.  After a device reset (a new primary
+ *   context) call set-up again: it always refreshes the cached address.
+ *   Size: the draw takes the band in waves of consecutive detscans of at
+ *   most *max_wave_samples_out samples (about 7.2 million: the intermediate
+ *   takes 4 bytes per sample, the CG vectors 20 bytes per flagged sample
+ *   for up to a quarter of the wave's samples), one cooperative launch per
+ *   wave, so it is slower than tod_sample_ncorr.  Set-up and draw return
+ *   TOD_ERR_SCRATCH (the draw enqueuing nothing) when a single detscan is
+ *   longer than a wave; detscans of a wave whose flagged samples exceed the
+ *   quarter are left at the gap-free solution with TOD_ERR_NOT_CONVERGED.
+ *   Contents: every wave writes the parts of the array it reads, so no part
+ *   has to start at zero.
  *   Concurrency: all plans and streams on one device share the array; two
  *   calls that can overlap on the device (different streams, or host
  *   threads without ordering) race on it and give wrong results.  Serialise
  *   them on one stream. */
 #define TOD_NCORR_STATIC_SCRATCH_BYTES (64u << 20)
-tod_status tod_ncorr_static_setup(tod_plan *p, int32_t *max_clusters_out);
+tod_status tod_ncorr_static_setup(tod_plan *p, int64_t *max_wave_samples_out);
 tod_status tod_sample_ncorr_static(tod_plan *p, const float *d, const float *s,
                                    const double *gain, const uint32_t *flags,
                                    const double *psd, tod_rng rng, int32_t mode,
@@ -354,6 +373,25 @@ tod_status tod_bin(tod_plan *p, const uint16_t *psi, const float *d,
                    const double *psd, double *A_out, double *b_out,
                    int32_t *hits_out, cudaStream_t stream);
 
+/* A6 for a band split over several processes (Sect. 2.3-2.4: the TOD is
+ * distributed in chunks, coadded locally, and the maps synchronised once
+ * per sweep).  tod_bin_partial is tod_bin (same arguments) writing, per
+ * pixel, the ten sums (A 6, b 3, hits) unrounded as double-double pairs
+ * (hi, lo): part_out double[npix][20] (value i at [2i], [2i+1]).  tod_bin
+ * itself adds a pixel's runs the same way and rounds once.
+ * tod_combine_partials adds nparts such arrays of npix_range pixels
+ * ([nparts][npix_range][20], DEVICE, consecutive by rank) in rank order, as
+ * double-doubles, and rounds once into A_out [npix_range][6],
+ * b_out [npix_range][3], hits_out [npix_range]: the normal equations of
+ * contiguous scan ranges combined this way equal tod_bin of the whole band
+ * bit for bit (but for sums within ~2^-104 of a rounding tie).  No
+ * counterpart in the paper's arithmetic (its coaddition order is MPI's). */
+tod_status tod_bin_partial(tod_plan *p, const uint16_t *psi, const float *d, const float *ncorr,
+                           const double *gain, const uint32_t *flags, const double *psd, double *part_out,
+                           cudaStream_t stream);
+tod_status tod_combine_partials(const double *parts, int32_t nparts, int64_t npix_range, double *A_out,
+                                double *b_out, int32_t *hits_out, cudaStream_t stream);
+
 /* A7 -- per-pixel solve (Sect. 5 table, "Map solution (Ax=b for each
  * pixel)"): m_p = A_p^{-1} b_p by FP64 3x3 Cholesky.  A pixel is valid iff
  * hits_p >= 3 and its Hadamard ratio det(A_p)/(A_TT A_QQ A_UU) >= rcond_min;
@@ -368,18 +406,34 @@ tod_status tod_solve_maps(tod_plan *p, const double *A, const double *b,
 
 /* A8 -- TOD chi^2 with the correlated noise marginalised, and its
  * gradients (the likelihood of the gain conditional of Eq. `gibbsstart`,
- * as a function of map, gains and noise parameters).  Per
- * detscan, with rhat = C(M(d - g s)) and P_k the noise PSD:
+ * as a function of map, gains and noise parameters).  Per detscan, with
+ * rhat = C(M(d - g s)) and P_k the noise PSD:
  *   chi2_out[q]  = 1/2 sum_{k>=1} [ rhat_k^2 / P_k + ln P_k ],
  *   dgain_out[q] = dL/dg_q = -<M s, v>,
- *   dpsd_out[q][3] = dL/d(sigma0, f_knee, alpha) of this detscan's terms,
- *   v_out[t] = M_t (C^T(rhat/P))_t (NULL to skip), so dL/ds = -g v and the
- *   map gradient is -P^T(g v): tod_bin of d = v, n_corr = 0 with every
- *   sigma0 = 1 returns it in b_out (negated).
- * s is the unit-gain projection.  Transforms in FP32, sums in FP64. */
-tod_status tod_chi2(tod_plan *p, const float *d, const float *s, const double *gain,
-                    const uint32_t *flags, const double *psd, double *chi2_out,
-                    double *dgain_out, double *dpsd_out, float *v_out, cudaStream_t stream);
+ *   v[t] = M_t (C^T(rhat/P))_t, so dL/ds = -g v and dL/dm = -P^T(g v)
+ *          (tod_project_adjoint of v),
+ * and for the band total_out[0] = sum_q chi2_out[q] and
+ * dpsd_out[det][3] = dL/d(sigma0, f_knee, alpha) of the detector, summed
+ * over its detscans in detscan order.  s is the unit-gain projection, float[N]
+ * (tod_project) with TOD_PREC_F32, double[N] (tod_project_f64) with
+ * TOD_PREC_F64.  precision: TOD_PREC_F32 (FP32 transforms) or TOD_PREC_F64
+ * (FP64 transforms and per-mode terms); sums in FP64 either way.  v_out: float[N]
+ * (F32) or double[N] (F64), or NULL.  Outputs device memory; chi2_out,
+ * dgain_out double[ndetscan], total_out double[1], dpsd_out double[ndet][3]. */
+#define TOD_PREC_F32 0
+#define TOD_PREC_F64 1
+tod_status tod_chi2(tod_plan *p, const float *d, const void *s, const double *gain,
+                    const uint32_t *flags, const double *psd, int32_t precision,
+                    double *chi2_out, double *dgain_out, double *total_out, double *dpsd_out,
+                    void *v_out, cudaStream_t stream);
+
+/* Adjoint of tod_project (the transpose of the g P m term of Eq. `todmodel`):
+ *   out_p = sum over samples t of pixel p of g_q y_t (1, cos 2psi_t, sin 2psi_t),
+ * out double[npix][3] (T, Q, U), overwritten.  y: float[N] (TOD_PREC_F32) or
+ * double[N] (TOD_PREC_F64, summed to FP64 accuracy); every sample counts
+ * (mask y first).  Deterministic, in the binning order of tod_bin. */
+tod_status tod_project_adjoint(tod_plan *p, const uint16_t *psi, const void *y, int32_t precision,
+                               const double *gain, double *out, cudaStream_t stream);
 
 /* A10 -- noise PSD step (Sect. 5 lists it among the TOD steps; the paper
  * defers the sampler to its noise companion paper, so this is a reading):

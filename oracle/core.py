@@ -522,6 +522,17 @@ def ncorr_solve_pcg(b, mask, sigma0, phi, tol=1e-12, maxiter=5000) -> tuple:
     return x, -1
 
 
+def ncorr_solve_allflagged(b, phi) -> np.ndarray:
+    """Every sample flagged: A = C^T diag(phi) C, singular in the offset mode
+    (phi_0 = 0) which no data constrain.  Reading: the draw is the
+    minimum-norm solution x = C^T[(C b) / phi] with mode 0 set to zero
+    (the right-hand side has no offset component then: b = C^T(sqrt(phi) w2))."""
+    X = dct(b)
+    inv = np.zeros_like(phi)
+    inv[1:] = 1.0 / phi[1:]
+    return idct(X * inv)
+
+
 def ncorr_dense_A(n, mask, sigma0, phi) -> np.ndarray:
     """The explicit n x n matrix A (brute force, small n only)."""
     C = np.stack([dct(e) for e in np.eye(n)], axis=1)     # column j = C e_j
@@ -546,6 +557,8 @@ def sample_ncorr(d, s, gain, mask, sigma0, fknee, alpha, fsamp, w1, w2, tol=1e-1
     b = ncorr_rhs(r, mask, sigma0, phi, w1, w2)
     if np.all(np.asarray(mask) != 0):
         return ncorr_solve_gapfree(b, sigma0, phi), 0
+    if not np.any(np.asarray(mask) != 0):
+        return ncorr_solve_allflagged(b, phi), 0
     return ncorr_solve_pcg(b, mask, sigma0, phi, tol=tol)
 
 

@@ -52,7 +52,7 @@ class _HuffBuffers(ctypes.Structure):
 class _BandDesc(ctypes.Structure):
     _fields_ = [("nside", _i32), ("ndet", _i32), ("nscan", _i32), ("n_psi", _i32), ("fsamp", _f64),
                 ("offsets", _P), ("pix", _HuffStreams), ("psi", _HuffStreams),
-                ("cluster_size", _i32), ("device", _i32), ("max_radix", _i32)]
+                ("tile_pairs", _i32), ("device", _i32), ("max_radix", _i32)]
 
 
 class _DataDesc(ctypes.Structure):
@@ -69,7 +69,7 @@ _lib = None
 
 SYMBOLS = ["tod_status_string", "tod_fft_length", "tod_huff_encode", "tod_huff_free",
            "tod_plan_create", "tod_plan_destroy", "tod_plan_info", "tod_plan_status",
-           "tod_plan_set_schedule", "tod_chi2", "tod_decode", "tod_project", "tod_sample_gain", "tod_sample_ncorr", "tod_bin",
+           "tod_plan_set_schedule", "tod_chi2", "tod_project_adjoint", "tod_project_f64", "tod_decode", "tod_project", "tod_sample_gain", "tod_sample_ncorr", "tod_bin",
            "tod_solve_maps", "tod_ncorr_static_setup", "tod_sample_ncorr_static", "tod_ncorr_prepare",
            "tod_sample_ncorr_prepared", "tod_sample_noise_psd", "tod_plan_set_ncorr_spectrum",
            "tod_plan_attach_data", "tod_decode_data", "tod_sample_gain_smooth"]
@@ -107,7 +107,9 @@ def lib():
         L.tod_sample_ncorr.argtypes = [_P, _P, _P, _P, _P, _P, Rng, _i32, _f64, _i32, _P, _P, _P]
         L.tod_bin.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
         L.tod_solve_maps.argtypes = [_P, _P, _P, _P, _f64, _P, _P, _P, _P, _P]
-        L.tod_chi2.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
+        L.tod_chi2.argtypes = [_P, _P, _P, _P, _P, _P, _i32, _P, _P, _P, _P, _P, _P]
+        L.tod_project_adjoint.argtypes = [_P, _P, _P, _i32, _P, _P, _P]
+        L.tod_project_f64.argtypes = [_P, _P, _P, _P, _P, _P, _P]
         L.tod_ncorr_static_setup.argtypes = [_P, _P]
         L.tod_sample_ncorr_static.argtypes = [_P, _P, _P, _P, _P, _P, Rng, _i32, _f64, _i32, _P, _P, _P]
         L.tod_ncorr_prepare.argtypes = [_P, _P, _P]
@@ -199,6 +201,30 @@ def ingest(band, data_streams: bool = False) -> dict:
     return out
 
 
+def kept_lengths(cfg) -> np.ndarray:
+    """FFT length (tod_fft_length) of every scan of a synthetic band."""
+    import synth
+    return np.array([fft_length(int(n)) for n in synth.raw_lengths(cfg)], dtype=np.int64)
+
+
+def ingest_arrays(arr) -> dict:
+    """ingest() for a band generated straight into concatenated arrays
+    (synth.make_band_arrays with kept_lengths): compress its pixel and psi
+    streams; the arrays are used in place (psi is widened to int32 for the
+    coder)."""
+    cfg = arr.cfg
+    ndet, nscan = cfg.ndet, cfg.nscan
+    off = arr.offsets
+    psi32 = np.empty(len(arr.psi), np.int32)
+    np.copyto(psi32, arr.psi, casting="unsafe")
+    out = dict(offsets=off,
+               pix_streams=huff_encode(ndet, nscan, off, arr.pix),
+               psi_streams=huff_encode(ndet, nscan, off, psi32),
+               tod=arr.tod, flags=arr.flags, flag_words=pack_flags(arr.flags))
+    del psi32
+    return out
+
+
 def ingest_data(band, offsets: np.ndarray) -> dict:
     """The band's detector data as ADC counts and its flags as flag words
     (from the synthetic generator), each compressed like the pointing
@@ -250,14 +276,14 @@ class Plan:
     """The band's TOD object on the GPU (todgibbs.h: tod_plan)."""
 
     def __init__(self, nside: int, ndet: int, nscan: int, fsamp: float, offsets: np.ndarray,
-                 pix_streams: dict, psi_streams: dict, cluster_size: int = 0, device: int = 0,
+                 pix_streams: dict, psi_streams: dict, tile_pairs: int = 0, device: int = 0,
                  max_radix: int = 0):
         keep = []
         off = _arr(offsets, np.int64)
         keep.append(off)
         desc = _BandDesc(nside, ndet, nscan, N_PSI, float(fsamp), off.ctypes.data,
                          _streams(pix_streams, keep), _streams(psi_streams, keep),
-                         int(cluster_size), int(device), int(max_radix))
+                         int(tile_pairs), int(device), int(max_radix))
         h = _P()
         _check(lib().tod_plan_create(ctypes.byref(h), ctypes.byref(desc)), "tod_plan_create")
         self._h = h
@@ -283,7 +309,7 @@ class Plan:
         ns, nq, npix, cs, nb = _i64(), _i32(), _i32(), _i32(), _i64()
         _check(lib().tod_plan_info(self._h, ctypes.byref(ns), ctypes.byref(nq), ctypes.byref(npix),
                                    ctypes.byref(cs), ctypes.byref(nb)), "tod_plan_info")
-        return dict(nsamples=ns.value, ndetscan=nq.value, npix=npix.value, cluster_size=cs.value,
+        return dict(nsamples=ns.value, ndetscan=nq.value, npix=npix.value, tile_pairs=cs.value,
                     device_bytes=nb.value)
 
     SCHED_PERSISTENT = 0
@@ -370,8 +396,8 @@ class Plan:
 
     def ncorr_static_setup(self) -> int:
         """Look up the fixed scratch array of sample_ncorr_static on this
-        plan's device; returns how many clusters fit in it."""
-        n = _i32()
+        plan's device; returns the most samples one wave of the draw takes."""
+        n = _i64()
         _check(lib().tod_ncorr_static_setup(self._h, ctypes.byref(n)), "tod_ncorr_static_setup")
         return n.value
 
@@ -388,10 +414,38 @@ class Plan:
                              _ptr(psd), _ptr(A_out), _ptr(b_out), _ptr(hits_out), _stream(stream)),
                "tod_bin")
 
-    def chi2(self, d, s, gain, flags, psd, chi2_out, dgain_out, dpsd_out, v_out=None, stream=None):
-        _check(lib().tod_chi2(self._h, _ptr(d), _ptr(s), _ptr(gain), _ptr(flags), _ptr(psd),
-                              _ptr(chi2_out), _ptr(dgain_out), _ptr(dpsd_out), _ptr(v_out),
+    PREC_F32 = 0
+    PREC_F64 = 1
+
+    def chi2(self, d, s, gain, flags, psd, chi2_out, dgain_out, total_out, dpsd_out, v_out=None,
+             precision: int = 0, stream=None):
+        """Per-detscan chi^2 and gain gradient, band total and per-detector
+        PSD gradient (todgibbs.h: tod_chi2); v_out float32 or float64 [N]."""
+        _check(lib().tod_chi2(self._h, _ptr(d), _ptr(s), _ptr(gain), _ptr(flags), _ptr(psd), int(precision),
+                              _ptr(chi2_out), _ptr(dgain_out), _ptr(total_out), _ptr(dpsd_out), _ptr(v_out),
                               _stream(stream)), "tod_chi2")
+
+    def project_f64(self, map3, pix, psi, gain, s_out, stream=None):
+        """FP64 projection: map3 float64 [3, npix] -> s_out float64 [N]."""
+        _check(lib().tod_project_f64(self._h, _ptr(map3), _ptr(pix), _ptr(psi), _ptr(gain), _ptr(s_out),
+                                     _stream(stream)), "tod_project_f64")
+
+    def pointing(self):
+        """The plan's decoded pointing (pix int32[N], psi int16[N] device
+        tensors), decoded once and kept."""
+        import torch
+        if getattr(self, "_pointing", None) is None:
+            dev = torch.device("cuda", self.device)
+            pix = torch.empty(self.N, dtype=torch.int32, device=dev)
+            psi = torch.empty(self.N, dtype=torch.int16, device=dev)
+            self.decode(pix, psi)
+            self._pointing = (pix, psi)
+        return self._pointing
+
+    def project_adjoint(self, psi, y, gain, out, precision: int = 0, stream=None):
+        """out[npix, 3] = P^T (g y) (todgibbs.h: tod_project_adjoint)."""
+        _check(lib().tod_project_adjoint(self._h, _ptr(psi), _ptr(y), int(precision), _ptr(gain), _ptr(out),
+                                         _stream(stream)), "tod_project_adjoint")
 
     def solve_maps(self, A, b, hits, rcond_min, map_out, map_f32_out=None, rcond_out=None,
                    valid_out=None, stream=None):

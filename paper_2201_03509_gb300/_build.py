@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtodgibbs.so")
-SOURCES = ["api.cu", "k_decode_project.cu", "k_dct.cu", "k_bin_solve.cu", "k_toeplitz.cu",
+SOURCES = ["api.cu", "k_decode_project.cu", "k_tx.cu", "k_bin_solve.cu", "k_toeplitz.cu",
            "ncorr_static.cu", "k_psd.cu", "k_gain_smooth.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -1,9 +1,9 @@
-"""Measured choice of the transform launch shape: the cluster size (CTAs per
-detscan transform) and the largest Stockham radix, timed on a slice of the
-band's own detscans (the first scans of the band, every detector) through
-the same gain and n_corr calls the Gibbs step makes.  The plan's own choice
-(the cluster size that keeps the most SMs busy) is always a candidate, so
-the result is never slower on the slice than the default."""
+"""Measured choice of the transform tile shape: the column pairs per tile of
+the column passes (tile_pairs) and the largest Stockham radix, timed on a
+slice of the band's own detscans (the first scans of the band, every
+detector) through the same gain and n_corr calls the Gibbs step makes.  The
+plan's own choice (tile_pairs = 0) is always a candidate, so the result is
+never slower on the slice than the default."""
 from __future__ import annotations
 
 import numpy as np
@@ -24,8 +24,8 @@ def _slice_streams(st: dict, ndet: int, nscan_sub: int) -> dict:
 def autotune(nside: int, ndet: int, nscan: int, fsamp: float, offsets: np.ndarray, pix_streams: dict,
              psi_streams: dict, tod: np.ndarray, flag_words: np.ndarray, psd: np.ndarray, map32,
              candidates=None, nscan_sample: int = 48, reps: int = 3, device: int = 0):
-    """Time (cluster size, max radix) candidates; returns (cluster_size,
-    max_radix, {(C, R): ms per gain + n_corr pass over the slice})."""
+    """Time (tile_pairs, max radix) candidates; returns (tile_pairs,
+    max_radix, {(T, R): ms per gain + n_corr pass over the slice})."""
     import torch
     nsub = max(1, min(nscan, nscan_sample))
     nq = ndet * nsub
@@ -44,17 +44,13 @@ def autotune(nside: int, ndet: int, nscan: int, fsamp: float, offsets: np.ndarra
     g = torch.zeros(nq, dtype=torch.float64, device=dev)
     its = torch.zeros(nq, dtype=torch.int32, device=dev)
     if candidates is None:
-        auto = Plan(nside, ndet, nsub, fsamp, off, pix_s, psi_s, 0, device)
-        c0 = auto.info()["cluster_size"]
-        auto.close()
-        cs = sorted({c0, 6, 7, 8, 9, 10, 12, 16})
-        candidates = [(c, r) for c in cs for r in (8, 16)]
+        candidates = [(t, r) for t in (0, 4, 8) for r in (8, 16)]
     timings = {}
     for (c, r) in candidates:
         try:
-            plan = Plan(nside, ndet, nsub, fsamp, off, pix_s, psi_s, cluster_size=c, device=device, max_radix=r)
+            plan = Plan(nside, ndet, nsub, fsamp, off, pix_s, psi_s, tile_pairs=c, device=device, max_radix=r)
         except Exception:
-            continue                        # this cluster size does not fit the lengths
+            continue                        # no split of these lengths for this radix
         try:
             plan.decode(pix, psi)
             plan.project(map32, pix, psi, None, s)
@@ -77,6 +73,6 @@ def autotune(nside: int, ndet: int, nscan: int, fsamp: float, offsets: np.ndarra
         finally:
             plan.close()
     if not timings:
-        raise RuntimeError("no transform launch shape fits this band")
+        raise RuntimeError("no transform tile shape fits this band")
     best = min(timings, key=timings.get)
     return best[0], best[1], timings

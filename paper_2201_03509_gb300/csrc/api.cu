@@ -224,10 +224,7 @@ int64_t fft_length_impl(int64_t n)
 
 // Stockham radices of a sub-transform of length L: repeatedly the largest
 // register DFT up to rmax (16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2) that divides
-// what is left, applied in increasing order.  Column and row passes put
-// consecutive threads on consecutive vectors (the frequency layout's odd
-// row stride keeps those rows in distinct banks), so every pass may take
-// the largest radix.
+// what is left (empty for L = 1).
 std::vector<int8_t> radix_plan(int L, int rmax)
 {
     static const int kRadix[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
@@ -240,10 +237,6 @@ std::vector<int8_t> radix_plan(int L, int rmax)
         r.push_back(static_cast<int8_t>(pick));
         L /= pick;
     }
-    // largest radix last: the last pass, which also writes the four-step
-    // transpose into the other CTAs, then has the fewest butterflies (one
-    // per thread where it can), so each thread's first butterfly is done
-    // while the cluster barrier before the remote writes completes
     std::reverse(r.begin(), r.end());
     return r;
 }
@@ -260,57 +253,53 @@ void fill_stages(DctStage *st, const std::vector<int8_t> &r, int L)
     }
 }
 
-// Choose m1 x m2 for one length with C CTAs; returns false if none fits.
-bool choose_factor(int n, int C, int rmax, DctPlan &out, int &sz)
+// Split m = n/2 = m1 x m2 for the multi-pass transform.  A column tile holds
+// m1 rows of 2 TP columns and a row tile 2 TR rows of m2 (made odd), each at
+// most TX_TILE values.  Wide column tiles (TP up to 16: sample runs of 64
+// floats) and several row pairs (TR up to 4: fewer Philox blocks per mode)
+// score highest, then m2 / m1 nearest 2.5.  tile_pairs > 0 caps TP.
+bool choose_tx_split(int n, int rmax, int tile_pairs, TxLen &out)
 {
     const int m = n / 2;
-    int best = -1, bestm1 = 0;
-    for (int m1 = 2; m1 <= m; ++m1) {
+    double best = -1.0;
+    int bm1 = 0;
+    for (int m1 = 1; m1 <= m; ++m1) {
         if (m % m1) continue;
         const int m2 = m / m1;
-        if (m2 < 2) continue;
         const auto r1 = radix_plan(m1, rmax), r2 = radix_plan(m2, rmax);
-        if (r1.empty() || r2.empty() || r1.size() > DCT_MAXR || r2.size() > DCT_MAXR) continue;
-        const int ncolmax = (m2 + C - 1) / C;
-        const int P = m1 / 2 + 1;
-        const int npmax = (P + C - 1) / C;
-        const int asz = m1 * ncolmax, bsz = 2 * npmax * (m2 | 1);
-        if (asz > DCT_SZ_MAX || bsz > DCT_SZ_MAX) continue;               // shared-memory budget
-        // smallest shared-memory footprint (two buffers plus the length's
-        // twiddle tables); within 5 % of it, the most balanced split
-        const int s = 2 * std::max(asz, bsz) + 3 * (m1 + m2);
-        const bool better = best < 0 || s * 20 < best * 19 ||
-                            (s * 20 <= best * 21 && std::max(m1, m2) < std::max(bestm1, m / bestm1));
-        if (better) {
-            best = s;
-            bestm1 = m1;
-        }
+        if ((m1 > 1 && r1.empty()) || (m2 > 1 && r2.empty())) continue;
+        if (r1.size() > TX_MAXR || r2.size() > TX_MAXR) continue;
+        const int m2p = m2 | 1;
+        if (2 * m1 > TX_TILE || 2 * m2p > TX_TILE) continue;
+        const int P1 = m1 / 2 + 1, P2 = (m2 + 1) / 2;
+        int TP = std::min(P2, TX_TILE / (2 * m1));
+        if (tile_pairs > 0) TP = std::min(TP, tile_pairs);
+        const int TR = std::min(P1, TX_TILE / (2 * m2p));
+        const double score = std::min(TP, 16) / 16.0 + std::min(TR, 4) / 4.0 -
+                             1e-3 * std::fabs(std::log(static_cast<double>(m2) / m1 / 2.5));
+        if (score > best) { best = score; bm1 = m1; }
     }
-    if (best >= 0) {   // best now holds the buffer size of the chosen split
-        const int m2b = m / bestm1;
-        best = std::max(bestm1 * ((m2b + C - 1) / C), 2 * (((bestm1 / 2 + 1) + C - 1) / C) * (m2b | 1));
-    }
-    if (best < 0) return false;
-    const int m1 = bestm1, m2 = m / m1;
+    if (bm1 == 0) return false;
+    const int m1 = bm1, m2 = m / m1;
     const auto r1 = radix_plan(m1, rmax), r2 = radix_plan(m2, rmax);
     std::memset(&out, 0, sizeof(out));
-    out.n = n; out.m = m; out.m1 = m1; out.m2 = m2;
-    out.m2p = m2 | 1;      // odd row stride: rows in consecutive lanes hit distinct banks
-    out.ncolmax = (m2 + C - 1) / C;
-    out.P = m1 / 2 + 1;
-    out.npmax = (out.P + C - 1) / C;
+    out.n = n; out.m = m; out.m1 = m1; out.m2 = m2; out.m2p = m2 | 1;
+    out.P1 = m1 / 2 + 1;
+    out.P2 = (m2 + 1) / 2;
+    out.TP = std::min(out.P2, TX_TILE / (2 * m1));
+    if (tile_pairs > 0) out.TP = std::min(out.TP, tile_pairs);
+    out.TR = std::min(out.P1, TX_TILE / (2 * out.m2p));
     out.nr1 = static_cast<int32_t>(r1.size());
     out.nr2 = static_cast<int32_t>(r2.size());
     fill_stages(out.s1, r1, m1);
     fill_stages(out.s2, r2, m2);
-    out.f_ncolmax = make_fastdiv(static_cast<uint32_t>(out.ncolmax));
     out.f_m2 = make_fastdiv(static_cast<uint32_t>(m2));
-    out.f_npmax = make_fastdiv(static_cast<uint32_t>(out.npmax));
-    out.sq_fwd = static_cast<float>(std::sqrt(2.0 / n));
-    out.s0_fwd = static_cast<float>(1.0 / std::sqrt(static_cast<double>(n)));
-    out.sq_inv = static_cast<float>(std::sqrt(0.5 * n) / m);
-    out.s0_inv = static_cast<float>(std::sqrt(static_cast<double>(n)) / m);
-    sz = best;
+    out.f_W = make_fastdiv(static_cast<uint32_t>(2 * out.TP));
+    out.f_2TR = make_fastdiv(static_cast<uint32_t>(2 * out.TR));
+    out.sq_fwd = std::sqrt(2.0 / n);
+    out.s0_fwd = 1.0 / std::sqrt(static_cast<double>(n));
+    out.sq_inv = std::sqrt(0.5 * n) / m;
+    out.s0_inv = std::sqrt(static_cast<double>(n)) / m;
     return true;
 }
 
@@ -400,6 +389,25 @@ cudaError_t build_huff(Plan &p, HuffDev &d, const tod_huff_streams &h)
     if ((e = dev_upload(p, d.cta_nblk, cta_nblk.data(), cta_nblk.size()))) return e;
     d.ncta = static_cast<int32_t>(cta_scan.size());
     return cudaSuccess;
+}
+
+// The n_corr draw over the whole band (one cooperative launch) or, with the
+// per-scan schedule, one launch per detscan.
+cudaError_t ncorr_draw(const Plan &p, const float *d, const float *s, const double *gain, const uint32_t *flags,
+                       const double *psd, tod_rng rng, int mode, float tol, int maxit, float *x, int32_t *iters,
+                       cudaStream_t st)
+{
+    const TxNcorrScratch sc = {p.ybuf, p.wpre, p.cgv, p.cgcap};
+    if (p.schedule != TOD_SCHED_PER_SCAN)
+        return launch_tx_ncorr(p, d, s, gain, flags, psd, rng, mode, tol, maxit, x, iters, st, 0, p.nq, sc,
+                               p.coop_grid);
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < p.nq && e == cudaSuccess; ++q) {
+        const int items = std::max(p.h_col_off[q + 1] - p.h_col_off[q], p.h_row_off[q + 1] - p.h_row_off[q]);
+        e = launch_tx_ncorr(p, d, s, gain, flags, psd, rng, mode, tol, maxit, x, iters, st, q, q + 1, sc,
+                            std::min(p.coop_grid, std::max(1, items)));
+    }
+    return e;
 }
 
 }  // namespace
@@ -572,8 +580,8 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
     if (band->nside <= 0 || band->nside > 8192 || band->ndet <= 0 || band->nscan <= 0 ||
         band->n_psi != TOD_N_PSI || !(band->fsamp > 0) || !band->offsets)
         return TOD_ERR_ARG;
-    const int cs = band->cluster_size;
-    if (cs < 0 || cs > 16) return TOD_ERR_ARG;
+    const int tile_pairs = band->tile_pairs;
+    if (tile_pairs < 0 || tile_pairs > TX_TILE / 2) return TOD_ERR_ARG;
     const int rmax = band->max_radix > 0 ? band->max_radix : 16;
     if (rmax < 2 || rmax > 16) return TOD_ERR_ARG;
     Plan *p = new (std::nothrow) Plan();
@@ -586,6 +594,7 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
     p->nscan = band->nscan;
     p->nq = band->ndet * band->nscan;
     p->fsamp = band->fsamp;
+    p->tile_pairs = tile_pairs;
     p->h_off.assign(band->offsets, band->offsets + p->nq + 1);
     if (p->h_off[0] != 0) { delete p; return TOD_ERR_ARG; }
     for (int q = 0; q < p->nq; ++q) {
@@ -594,7 +603,7 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
         if (q % p->ndet && n != p->h_off[q] - p->h_off[q - 1]) { delete p; return TOD_ERR_ARG; }
     }
     p->N = p->h_off[p->nq];
-    if (p->N >= (int64_t(1) << 32)) { delete p; return TOD_ERR_ARG; }
+    if (p->N >= (int64_t(1) << 40)) { delete p; return TOD_ERR_ARG; }
     if (!valid_streams(band->pix, p->nq, p->nscan, p->h_off) ||
         !valid_streams(band->psi, p->nq, p->nscan, p->h_off)) {
         delete p;
@@ -658,111 +667,100 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
         }
         if ((e = dev_upload(*p, p->trig, trig.data(), trig.size()))) return fail(e);
     }
-    // work list: decreasing length
+    // transform plans of the multi-pass DCT (k_tx.cu): one per distinct length
     {
-        std::vector<int32_t> w(p->nq);
-        std::iota(w.begin(), w.end(), 0);
-        std::stable_sort(w.begin(), w.end(), [&](int a, int b) {
-            return p->h_off[a + 1] - p->h_off[a] > p->h_off[b + 1] - p->h_off[b];
-        });
-        if ((e = dev_upload(*p, p->work, w.data(), w.size()))) return fail(e);
-    }
-    // transform plans
-    {
-        std::vector<int> lens;
-        for (int q = 0; q < p->nq; ++q) lens.push_back(static_cast<int>(p->h_off[q + 1] - p->h_off[q]));
+        std::vector<int> lens(p->nq);
+        int maxlen = 0;
+        for (int q = 0; q < p->nq; ++q) {
+            lens[q] = static_cast<int>(p->h_off[q + 1] - p->h_off[q]);
+            maxlen = std::max(maxlen, lens[q]);
+        }
         std::vector<int> uniq(lens);
         std::sort(uniq.begin(), uniq.end());
         uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
-        // Cluster size: every C in 1..16 whose per-CTA buffers, twiddle block
-        // and CG areas fit in shared memory is scored by the SMs it keeps
-        // busy (C x co-resident clusters, which depends on how clusters pack
-        // into the GPCs); the best score wins, ties to the smaller C.
-        std::vector<DctPlan> plans;
-        int chosenC = 0, best_sms = 0;
-        for (int C = 1; C <= 16; ++C) {
-            if (cs && C != cs) continue;
-            std::vector<DctPlan> cand;
-            int sz = 0, m1max = 0, m2max = 0;
-            bool ok = true;
-            for (int n : uniq) {
-                DctPlan dp;
-                int s = 0;
-                if (!choose_factor(n, C, rmax, dp, s)) { ok = false; break; }
-                cand.push_back(dp);
-                sz = std::max(sz, s);
-                m1max = std::max(m1max, dp.m1);
-                m2max = std::max(m2max, dp.m2);
-            }
-            if (!ok) continue;
-            // twiddle block: 3 (m1 + m2) + m/64 + 65 complex values
-            int twmax = 0;
-            for (auto &dp : cand) twmax = std::max(twmax, 3 * (dp.m1 + dp.m2) + dp.m / 64 + 65);
-            twmax = (twmax + 1) & ~1;
-            const size_t smem_dyn = sizeof(float2) * (2 * static_cast<size_t>(sz) + twmax) +
-                                    static_cast<size_t>(CG_KCAP) * 24 + sizeof(float) * 5 * GB_CAP;
-            if (smem_dyn + 12288 > 227 * 1024) continue;
-            int ncl = 0;
-            if ((e = transform_cluster_occupancy(C, smem_dyn, &ncl))) return fail(e);
-            if (ncl < 1) continue;
-            if (C * ncl > best_sms) {
-                best_sms = C * ncl;
-                chosenC = C;
-                plans.swap(cand);
-                p->sz = sz; p->m1max = m1max; p->m2max = m2max;
-            }
+        std::vector<TxLen> tl;
+        for (int n : uniq) {
+            TxLen L;
+            if (!choose_tx_split(n, rmax, tile_pairs, L)) { free_plan(p); return TOD_ERR_ARG; }
+            tl.push_back(L);
         }
-        if (!chosenC) { free_plan(p); return TOD_ERR_ARG; }
-        p->C = chosenC;
-        // twiddle block per length, FP64-generated: W_{m1}^i (m1), W_{m2}^i (m2),
-        // real-split factors W_{4n}^{k1}, W_{4n}^{m1 k2}, W_{4n}^{5 k1},
-        // W_{4n}^{5 m1 k2} (m1, m2, m1, m2), four-step factors W_m^{64 i}
-        // (m/64 + 1) and W_m^i (64); staged in shared memory per detscan
-        std::vector<float2> tw;
-        const auto push_w = [&](int64_t L, int64_t i) {
-            const double ang = -2.0 * kPi * static_cast<double>(i % L) / static_cast<double>(L);
-            tw.push_back(make_float2(static_cast<float>(std::cos(ang)), static_cast<float>(std::sin(ang))));
+        // twiddle block per length, FP64-generated: W_m1^i (m1), W_m2^i (m2),
+        // W_4n^{k1} (m1), W_4n^{m1 k2} (m2), W_4n^{5 k1} (m1),
+        // W_4n^{5 m1 k2} (m2), W_m^{64 i} (m/64 + 1), W_m^i (64)
+        std::vector<double2> tw;
+        const auto push_w = [&](int64_t Lp, int64_t i) {
+            const double ang = -2.0 * kPi * static_cast<double>(i % Lp) / static_cast<double>(Lp);
+            tw.push_back(make_double2(std::cos(ang), std::sin(ang)));
         };
-        int twsz = 0;
-        for (auto &dp : plans) {
-            dp.twb = static_cast<int32_t>(tw.size());
-            const int64_t n4 = 4 * static_cast<int64_t>(dp.n);
-            for (int i = 0; i < dp.m1; ++i) push_w(dp.m1, i);
-            for (int i = 0; i < dp.m2; ++i) push_w(dp.m2, i);
-            for (int i = 0; i < dp.m1; ++i) push_w(n4, i);
-            for (int i = 0; i < dp.m2; ++i) push_w(n4, static_cast<int64_t>(dp.m1) * i);
-            for (int i = 0; i < dp.m1; ++i) push_w(n4, 5 * static_cast<int64_t>(i));
-            for (int i = 0; i < dp.m2; ++i) push_w(n4, 5 * static_cast<int64_t>(dp.m1) * i);
-            for (int i = 0; i <= dp.m / 64; ++i) push_w(dp.m, 64 * static_cast<int64_t>(i));
-            for (int i = 0; i < 64; ++i) push_w(dp.m, i);
-            twsz = std::max(twsz, static_cast<int>(tw.size()) - dp.twb);
+        for (auto &L : tl) {
+            L.twb = static_cast<int64_t>(tw.size());
+            const int64_t n4 = 4 * static_cast<int64_t>(L.n);
+            for (int i = 0; i < L.m1; ++i) push_w(L.m1, i);
+            for (int i = 0; i < L.m2; ++i) push_w(L.m2, i);
+            for (int i = 0; i < L.m1; ++i) push_w(n4, i);
+            for (int i = 0; i < L.m2; ++i) push_w(n4, static_cast<int64_t>(L.m1) * i);
+            for (int i = 0; i < L.m1; ++i) push_w(n4, 5 * static_cast<int64_t>(i));
+            for (int i = 0; i < L.m2; ++i) push_w(n4, 5 * static_cast<int64_t>(L.m1) * i);
+            for (int i = 0; i <= L.m / 64; ++i) push_w(L.m, 64 * static_cast<int64_t>(i));
+            for (int i = 0; i < 64; ++i) push_w(L.m, i);
         }
-        p->twsz = (twsz + 1) & ~1;      // keeps the areas after the block 16-byte aligned
-        std::vector<int32_t> qp(p->nq);
-        for (int q = 0; q < p->nq; ++q)
-            qp[q] = static_cast<int32_t>(std::lower_bound(uniq.begin(), uniq.end(), lens[q]) - uniq.begin());
-        p->nplans = static_cast<int32_t>(plans.size());
-        if ((e = dev_upload(*p, p->plans, plans.data(), plans.size()))) return fail(e);
-        if ((e = dev_upload(*p, p->q_plan, qp.data(), qp.size()))) return fail(e);
-        if ((e = dev_upload(*p, p->tw, tw.data(), tw.size()))) return fail(e);
-        if ((e = setup_dct_kernels(*p))) return fail(e);
+        std::vector<float2> tw32(tw.size());
+        for (size_t i = 0; i < tw.size(); ++i)
+            tw32[i] = make_float2(static_cast<float>(tw[i].x), static_cast<float>(tw[i].y));
+        // work items, detscan-major
+        std::vector<int32_t> qtx(p->nq);
+        std::vector<int2> ci, ri;
+        p->h_col_off.assign(p->nq + 1, 0);
+        p->h_row_off.assign(p->nq + 1, 0);
+        for (int q = 0; q < p->nq; ++q) {
+            qtx[q] = static_cast<int32_t>(std::lower_bound(uniq.begin(), uniq.end(), lens[q]) - uniq.begin());
+            const TxLen &L = tl[qtx[q]];
+            for (int b = 0; b * L.TP < L.P2; ++b) ci.push_back(make_int2(q, b));
+            for (int b = 0; b * L.TR < L.P1; ++b) ri.push_back(make_int2(q, b));
+            p->h_col_off[q + 1] = static_cast<int32_t>(ci.size());
+            p->h_row_off[q + 1] = static_cast<int32_t>(ri.size());
+        }
+        p->ntx = static_cast<int32_t>(tl.size());
+        p->h_txl = tl;
+        p->h_q_tx = qtx;
+        if ((e = dev_upload(*p, p->txl, tl.data(), tl.size()))) return fail(e);
+        if ((e = dev_upload(*p, p->q_tx, qtx.data(), qtx.size()))) return fail(e);
+        if ((e = dev_upload(*p, p->txtw, tw32.data(), tw32.size()))) return fail(e);
+        if ((e = dev_upload(*p, p->txtw64, tw.data(), tw.size()))) return fail(e);
+        if ((e = dev_upload(*p, p->colitems, ci.data(), ci.size()))) return fail(e);
+        if ((e = dev_upload(*p, p->rowitems, ri.data(), ri.size()))) return fail(e);
+        if ((e = dev_upload(*p, p->col_off, p->h_col_off.data(), p->h_col_off.size()))) return fail(e);
+        if ((e = dev_upload(*p, p->row_off, p->h_row_off.data(), p->h_row_off.size()))) return fail(e);
+        if ((e = setup_tx_kernels(*p))) return fail(e);
+        // scratch: the complex intermediate (room for one whole detscan in FP64
+        // too), per-item partial sums, the flag prefix, CG state and vectors
+        p->ybuf_floats = std::max<int64_t>(p->N, 2 * static_cast<int64_t>(maxlen));
+        if ((e = dev_upload(*p, p->ybuf, static_cast<float2 *>(nullptr), static_cast<size_t>(p->ybuf_floats / 2))))
+            return fail(e);
+        if ((e = dev_upload(*p, p->part, static_cast<double *>(nullptr), 4 * (ci.size() + ri.size()))))
+            return fail(e);
+        if ((e = dev_upload(*p, p->wpre, static_cast<int64_t *>(nullptr), static_cast<size_t>(p->N / 32 + 3))))
+            return fail(e);
+        if ((e = dev_upload(*p, p->chunk, static_cast<int64_t *>(nullptr), static_cast<size_t>(p->coop_grid + 1))))
+            return fail(e);
+        if ((e = dev_upload(*p, p->cgs, static_cast<CgState *>(nullptr), static_cast<size_t>(p->nq)))) return fail(e);
+        if ((e = dev_upload(*p, p->gblk, static_cast<int2 *>(nullptr), static_cast<size_t>(p->nq) * TX_GBMAX)))
+            return fail(e);
+        if ((e = dev_upload(*p, p->gnb, static_cast<int32_t *>(nullptr), static_cast<size_t>(p->nq)))) return fail(e);
+        p->cgcap = std::max<int64_t>(p->N / 16, 2 * static_cast<int64_t>(maxlen));
+        if ((e = dev_upload(*p, p->cgv, static_cast<float *>(nullptr), static_cast<size_t>(5 * p->cgcap))))
+            return fail(e);
+        if ((e = dev_upload(*p, p->cg_count, static_cast<int32_t *>(nullptr), 2))) return fail(e);
+        if ((e = dev_upload(*p, p->chi2_dpsd, static_cast<double *>(nullptr), 3 * static_cast<size_t>(p->nq))))
+            return fail(e);
         // Toeplitz preconditioner tables (per detector)
-        p->toep_nref = 0;
-        for (int q = 0; q < p->nq; ++q)
-            p->toep_nref = std::max<int32_t>(p->toep_nref, static_cast<int32_t>(p->h_off[q + 1] - p->h_off[q]));
+        p->toep_nref = maxlen;
         if ((e = dev_upload(*p, p->htab, static_cast<float *>(nullptr), static_cast<size_t>(p->ndet) * TOEP_LMAX)))
             return fail(e);
         if ((e = dev_upload(*p, p->xtab, static_cast<float *>(nullptr),
                             static_cast<size_t>(p->ndet) * (TOEP_LMAX * (TOEP_LMAX + 1) / 2))))
             return fail(e);
         if ((e = dev_upload(*p, p->lvalid, static_cast<int32_t *>(nullptr), static_cast<size_t>(p->ndet))))
-            return fail(e);
-        if ((e = dev_upload(*p, p->gain_ab, static_cast<double2 *>(nullptr), static_cast<size_t>(p->nq))))
-            return fail(e);
-        // filter-weight scratch: one slot per CTA of every resident cluster
-        p->wscratch_per_cluster = static_cast<int64_t>(p->C) * p->sz * NCORR_SCRATCH_F4;
-        if ((e = dev_upload(*p, p->wscratch, static_cast<float4 *>(nullptr),
-                            static_cast<size_t>(std::max(1, p->nclusters_ncorr)) * p->wscratch_per_cluster)))
             return fail(e);
     }
     // binning structure from the pointing (fixed during the run)
@@ -905,14 +903,14 @@ tod_status tod_plan_destroy(tod_plan *pl)
 }
 
 tod_status tod_plan_info(const tod_plan *pl, int64_t *nsamples, int32_t *ndetscan, int32_t *npix,
-                         int32_t *cluster_size, int64_t *device_bytes)
+                         int32_t *tile_pairs, int64_t *device_bytes)
 {
     if (!pl) return TOD_ERR_ARG;
     const Plan *p = reinterpret_cast<const Plan *>(pl);
     if (nsamples) *nsamples = p->N;
     if (ndetscan) *ndetscan = p->nq;
     if (npix) *npix = p->npix;
-    if (cluster_size) *cluster_size = p->C;
+    if (tile_pairs) *tile_pairs = p->tile_pairs;
     if (device_bytes) *device_bytes = p->device_bytes;
     return TOD_OK;
 }
@@ -1020,6 +1018,15 @@ tod_status tod_project(tod_plan *pl, const void *map_tqu, const int32_t *pix, co
     return to_status(launch_project(*p, static_cast<const float4 *>(map_tqu), pix, psi, gain, s_out, stream));
 }
 
+tod_status tod_project_f64(tod_plan *pl, const double *map, const int32_t *pix, const uint16_t *psi,
+                           const double *gain, double *s_out, cudaStream_t stream)
+{
+    if (!pl || !map || !pix || !psi || !s_out) return TOD_ERR_ARG;
+    Plan *p = reinterpret_cast<Plan *>(pl);
+    DeviceGuard dg(p->device);
+    return to_status(launch_project64(*p, map, pix, psi, gain, s_out, stream));
+}
+
 tod_status tod_sample_gain(tod_plan *pl, const float *d, const float *s, const uint32_t *flags,
                            const double *psd, tod_rng rng, int32_t mode, double *gain_out,
                            double *mu_out, double *sigma_out, cudaStream_t stream)
@@ -1028,7 +1035,14 @@ tod_status tod_sample_gain(tod_plan *pl, const float *d, const float *s, const u
     if (mode != TOD_MODE_DRAW && mode != TOD_MODE_MEAN) return TOD_ERR_ARG;
     Plan *p = reinterpret_cast<Plan *>(pl);
     DeviceGuard dg(p->device);
-    return to_status(launch_gain(*p, d, s, flags, psd, rng, mode, gain_out, mu_out, sigma_out, stream, 0, p->nq));
+    cudaError_t e = cudaSuccess;
+    if (p->schedule == TOD_SCHED_PER_SCAN) {
+        for (int q = 0; q < p->nq && e == cudaSuccess; ++q)
+            e = launch_tx_gain(*p, d, s, flags, psd, rng, mode, gain_out, mu_out, sigma_out, stream, q, q + 1);
+    } else {
+        e = launch_tx_gain(*p, d, s, flags, psd, rng, mode, gain_out, mu_out, sigma_out, stream, 0, p->nq);
+    }
+    return to_status(e);
 }
 
 tod_status tod_sample_ncorr(tod_plan *pl, const float *d, const float *s, const double *gain,
@@ -1042,8 +1056,9 @@ tod_status tod_sample_ncorr(tod_plan *pl, const float *d, const float *s, const 
     DeviceGuard dg(p->device);
     const float tol = cg_tol > 0 ? static_cast<float>(cg_tol) : 1e-6f;
     const int maxit = cg_maxiter > 0 ? cg_maxiter : 500;
-    return to_status(launch_ncorr(*p, d, s, gain, flags, psd, rng, mode, tol, maxit, ncorr_out,
-                                  cg_iters_out, stream, 0, p->nq));
+    cudaError_t e = p->use_prec ? launch_toeplitz_prep(*p, psd, stream) : cudaSuccess;
+    if (e == cudaSuccess) e = ncorr_draw(*p, d, s, gain, flags, psd, rng, mode, tol, maxit, ncorr_out, cg_iters_out, stream);
+    return to_status(e);
 }
 
 tod_status tod_ncorr_prepare(tod_plan *pl, const double *psd, cudaStream_t stream)
@@ -1066,8 +1081,8 @@ tod_status tod_sample_ncorr_prepared(tod_plan *pl, const float *d, const float *
     DeviceGuard dg(p->device);
     const float tol = cg_tol > 0 ? static_cast<float>(cg_tol) : 1e-6f;
     const int maxit = cg_maxiter > 0 ? cg_maxiter : 500;
-    return to_status(launch_ncorr(*p, d, s, gain, flags, psd, rng, mode, tol, maxit, ncorr_out,
-                                  cg_iters_out, stream, 0, p->nq, false));
+    return to_status(ncorr_draw(*p, d, s, gain, flags, psd, rng, mode, tol, maxit, ncorr_out, cg_iters_out,
+                                stream));
 }
 
 tod_status tod_plan_set_ncorr_spectrum(tod_plan *pl, float *spec_out)
@@ -1097,18 +1112,47 @@ tod_status tod_bin(tod_plan *pl, const uint16_t *psi, const float *d, const floa
         return TOD_ERR_ARG;
     Plan *p = reinterpret_cast<Plan *>(pl);
     DeviceGuard dg(p->device);
-    return to_status(launch_bin(*p, psi, d, ncorr, gain, flags, psd, A_out, b_out, hits_out, stream));
+    return to_status(launch_bin(*p, psi, d, ncorr, gain, flags, psd, A_out, b_out, hits_out, nullptr, stream));
 }
 
-tod_status tod_chi2(tod_plan *pl, const float *d, const float *s, const double *gain,
-                    const uint32_t *flags, const double *psd, double *chi2_out, double *dgain_out,
-                    double *dpsd_out, float *v_out, cudaStream_t stream)
+tod_status tod_bin_partial(tod_plan *pl, const uint16_t *psi, const float *d, const float *ncorr,
+                           const double *gain, const uint32_t *flags, const double *psd, double *part_out,
+                           cudaStream_t stream)
 {
-    if (!pl || !d || !s || !gain || !flags || !psd || !chi2_out || !dgain_out || !dpsd_out)
-        return TOD_ERR_ARG;
+    if (!pl || !psi || !d || !ncorr || !gain || !flags || !psd || !part_out) return TOD_ERR_ARG;
     Plan *p = reinterpret_cast<Plan *>(pl);
     DeviceGuard dg(p->device);
-    return to_status(launch_chi2(*p, d, s, gain, flags, psd, chi2_out, dgain_out, dpsd_out, v_out, stream));
+    return to_status(launch_bin(*p, psi, d, ncorr, gain, flags, psd, nullptr, nullptr, nullptr, part_out, stream));
+}
+
+tod_status tod_combine_partials(const double *parts, int32_t nparts, int64_t npix_range, double *A_out,
+                                double *b_out, int32_t *hits_out, cudaStream_t stream)
+{
+    if (!parts || nparts < 1 || npix_range < 0 || !A_out || !b_out || !hits_out) return TOD_ERR_ARG;
+    return to_status(launch_combine(parts, nparts, npix_range, A_out, b_out, hits_out, stream));
+}
+
+tod_status tod_chi2(tod_plan *pl, const float *d, const void *s, const double *gain, const uint32_t *flags,
+                    const double *psd, int32_t precision, double *chi2_out, double *dgain_out, double *total_out,
+                    double *dpsd_out, void *v_out, cudaStream_t stream)
+{
+    if (!pl || !d || !s || !gain || !flags || !psd || !chi2_out || !dgain_out || !total_out || !dpsd_out)
+        return TOD_ERR_ARG;
+    if (precision != TOD_PREC_F32 && precision != TOD_PREC_F64) return TOD_ERR_ARG;
+    Plan *p = reinterpret_cast<Plan *>(pl);
+    DeviceGuard dg(p->device);
+    return to_status(launch_tx_chi2(*p, precision == TOD_PREC_F64, d, s, gain, flags, psd, chi2_out, dgain_out,
+                                    p->chi2_dpsd, total_out, dpsd_out, v_out, stream));
+}
+
+tod_status tod_project_adjoint(tod_plan *pl, const uint16_t *psi, const void *y, int32_t precision,
+                               const double *gain, double *out, cudaStream_t stream)
+{
+    if (!pl || !psi || !y || !gain || !out) return TOD_ERR_ARG;
+    if (precision != TOD_PREC_F32 && precision != TOD_PREC_F64) return TOD_ERR_ARG;
+    Plan *p = reinterpret_cast<Plan *>(pl);
+    DeviceGuard dg(p->device);
+    return to_status(launch_project_adjoint(*p, psi, y, precision == TOD_PREC_F64, gain, out, stream));
 }
 
 tod_status tod_solve_maps(tod_plan *pl, const double *A, const double *b, const int32_t *hits,

@@ -10,20 +10,13 @@ namespace tg {
 
 constexpr int DEC_LUTB = 13;          // first-level decode table: 2^13 packed 32-bit entries
 constexpr int32_t DEC_WIDE = -(1 << 26);   // table value: symbol too wide for the entry, read canonically
-constexpr int DEC_T = 512;
-constexpr int NCORR_SCRATCH_F4 = 2;   // float4 per packed slot of the n_corr scratch: filter weights, CG spectra            // decode threads per CTA (one checkpoint block each)
+constexpr int DEC_T = 512;            // decode threads per CTA (one checkpoint block each)
 constexpr int DEC_ROUND = 16;         // symbols staged per thread before a coalesced write
 // what a decoded value becomes: itself (pointing), the FP32 TOD, a flag bit
 enum : int { DEC_VALUE = 0, DEC_TOD = 1, DEC_FLAG = 2 };
 constexpr int ELEM_TILE = 4096;       // samples per tile of the element-wise kernels
-constexpr int DCT_T = 512;            // threads per CTA of the cluster transform kernels
-constexpr int DCT_SZ_MAX = 11776;     // complex values per CTA buffer (two buffers + CG fit in 227 KB)
-constexpr int DCT_MAXR = 20;          // maximum number of radix stages per sub-transform
-constexpr int CG_KCAP = 768;          // flagged samples per CTA held by the CG
 constexpr int TOEP_LMAX = 512;        // longest gap block of the Toeplitz preconditioner
-constexpr int GB_CAP = 1024;          // preconditioner elements applied per round in one CTA
 constexpr int BIN_TILE = 2048;        // sorted samples staged per binning tile
-constexpr int GAP_CAP = 256;          // gap blocks per detscan handled by the preconditioner
 
 // Compressed stream kind, device copy + decode tables.
 struct HuffDev {
@@ -53,18 +46,43 @@ struct DctStage {
     FastDiv fLR, fNs;                // divisions by L/R and Ns
 };
 
-// Per-length transform plan (real DCT-II of length n via an m = n/2 complex
-// FFT split as m1 x m2 across a cluster of C CTAs).
-struct DctPlan {
-    int32_t n, m, m1, m2, ncolmax, npmax, P;
-    int32_t m2p;                     // row stride of the frequency layout: m2 made odd
-    int32_t nr1, nr2;
-    int32_t tw1, tw2;                // offsets of the W_{m1}^i and W_{m2}^i tables
-    int32_t twb;                     // offset of this length's twiddle block (see k_dct.cu)
-    FastDiv f_ncolmax, f_m2, f_npmax;
-    float sq_fwd, s0_fwd, sq_inv, s0_inv;   // real-split scales (FP64-computed on the host)
-    DctStage s1[DCT_MAXR], s2[DCT_MAXR];
+// ---------------------------------------------------------------------------
+// Multi-pass batched DCT-II (k_tx.cu).  A length-n transform is an m = n/2
+// complex FFT split m = m1 x m2: a column pass (FFTs of length m1 over
+// tiles of column pairs {c, m2-1-c}, four-step twiddle, written row-major
+// to an intermediate in memory), a row pass (FFTs of length m2 over tiles of
+// row pairs {k1, m1-k1}, where the real split and any per-mode filter run,
+// then the inverse row FFTs), and an inverse column pass.
+// ---------------------------------------------------------------------------
+constexpr int TX_T = 256;             // threads per CTA of the pass kernels
+constexpr int TX_TILE = 4096;         // complex values per tile buffer (two buffers per CTA)
+constexpr int TX_MAXR = 20;           // radix stages per sub-transform
+constexpr int TX_GBMAX = 256;         // preconditioner gap blocks per detscan
+constexpr int TX_GBCAP = 2048;        // padded preconditioner elements staged per round
+
+struct alignas(16) TxLen {
+    int32_t n, m, m1, m2, m2p;        // m2p: row stride of a row tile (m2 made odd)
+    int32_t P1, P2;                   // row pairs m1/2 + 1, column pairs (m2 + 1)/2
+    int32_t TP, TR;                   // column pairs per column tile, row pairs per row tile
+    int32_t nr1, nr2;                 // radix stages of the column and row FFTs
+    int32_t pad0;
+    int64_t twb;                      // offset of this length's twiddle block
+    FastDiv f_m2, f_W, f_2TR;         // divisions by m2, 2 TP, 2 TR
+    int32_t pad1;
+    double sq_fwd, s0_fwd, sq_inv, s0_inv;   // real-split scales
+    DctStage s1[TX_MAXR], s2[TX_MAXR];
 };
+
+// Per-detscan state of the CG gap filling (device).
+struct CgState {
+    double rz, stop;                  // r.z, stopping threshold tol^2 |r0|^2
+    int64_t koff;                     // first flagged rank of the detscan in the launch range
+    int32_t K;                        // flagged samples
+    int32_t it;                       // iterations done
+    int32_t mode;                     // CG_* below
+    int32_t pad;
+};
+enum : int32_t { CG_NONE = 0, CG_ACTIVE = 1, CG_DONE = 2, CG_ALLFLAG = 3, CG_OVER = 4 };
 
 struct Plan {
     int device = 0;
@@ -85,27 +103,14 @@ struct Plan {
     int32_t *tile_q = nullptr;
     int64_t *tile_t0 = nullptr;
     float2 *trig = nullptr;          // [TOD_N_PSI] (cos 2psi, sin 2psi) at bin centres, FP32
-    // transforms
-    int32_t C = 1;                   // CTAs per cluster
-    int32_t sz = 0;                  // complex values per CTA buffer (max over plans)
-    int32_t twsz = 0;                // complex values of the largest twiddle block
-    int32_t m1max = 0, m2max = 0;
-    int32_t nplans = 0;
-    DctPlan *plans = nullptr;        // device
-    int32_t *q_plan = nullptr;       // [nq] plan index of each detscan
-    float2 *tw = nullptr;            // twiddle tables
-    int32_t *work = nullptr;         // [nq] detscans sorted by decreasing length
-    int32_t nclusters_gain = 1, nclusters_ncorr = 1;
-    float4 *wscratch = nullptr;      // per-CTA filter weights (beta, gamma) and CG spectra, packed layout
+    // correlated-noise preconditioner (k_toeplitz.cu)
     float *htab = nullptr;           // [ndet][TOEP_LMAX] gap-kernel h(d)
     float *xtab = nullptr;           // [ndet][TOEP_LMAX (TOEP_LMAX+1)/2] T_L^{-1} e_1 per order
     int32_t *lvalid = nullptr;       // [ndet]
     int32_t toep_nref = 0;
     bool use_prec = true;
-    int64_t wscratch_per_cluster = 0;
     int32_t schedule = TOD_SCHED_PERSISTENT;
     int32_t nbin_tiles = 0;          // binning tiles (whole runs of one detscan)
-    double2 *gain_ab = nullptr;      // [nq] (a, b) of each detscan's gain conditional (scratch)
     // noise PSD step
     float *spec_out = nullptr;       // caller's buffer for the n_corr spectra (NULL: not written)
     float2 *lnk = nullptr;           // [longest detscan] ln k as an FP32 pair (hi, lo)
@@ -114,7 +119,6 @@ struct Plan {
     double *psd_sumlnf = nullptr;    // [ndet] sum of ln f_k over them
     double *psd_part = nullptr;      // [ntile] partial sums of one evaluation
     double *psd_state = nullptr;     // [ndet][8] chain state
-    size_t smem_gain = 0, smem_ncorr = 0;
     // binning
     // Runs: the samples of one (detscan, pixel), in time order; a detscan's
     // runs ordered by their first sample, stored run-major.  A tile's samples
@@ -130,6 +134,32 @@ struct Plan {
     int32_t *pair_slot = nullptr;    // [npairs] the run's slot among its pixel's runs (detscan order)
     int64_t *pix_slot_off = nullptr; // [npix+1]
     double *rec = nullptr;           // [npairs][10] per-run partial sums (scratch)
+    // multi-pass transforms (k_tx.cu)
+    int32_t ntx = 0;                 // distinct lengths
+    TxLen *txl = nullptr;            // [ntx] device
+    std::vector<TxLen> h_txl;
+    int32_t *q_tx = nullptr;         // [nq] length index of each detscan
+    std::vector<int32_t> h_q_tx;
+    float2 *txtw = nullptr;          // twiddle blocks, FP32
+    double2 *txtw64 = nullptr;       // the same, FP64
+    int2 *colitems = nullptr, *rowitems = nullptr;   // (detscan, tile) work items, detscan-major
+    int32_t *col_off = nullptr, *row_off = nullptr;  // [nq+1] first item of each detscan
+    std::vector<int32_t> h_col_off, h_row_off;
+    float2 *ybuf = nullptr;          // complex intermediate (FP64 calls use it as double2)
+    int64_t ybuf_floats = 0;         // its size in floats: max(N, 2 x longest detscan)
+    double *part = nullptr;          // [max items][4] per-item partial sums
+    int64_t *wpre = nullptr;         // [N/32 + 3] flagged samples before each flag word (range-relative)
+    int64_t *chunk = nullptr;        // [grid + 1] word-chunk counts of the flag scan
+    CgState *cgs = nullptr;          // [nq]
+    int2 *gblk = nullptr;            // [nq][TX_GBMAX] preconditioner blocks (rank in detscan, length)
+    int32_t *gnb = nullptr;          // [nq] blocks (-1: too many, no preconditioner)
+    float *cgv = nullptr;            // [5][cgcap] CG vectors y, r, p, q, z by flagged rank
+    int64_t cgcap = 0;
+    int32_t *cg_count = nullptr;     // [2] active detscans (alternating)
+    double *chi2_dpsd = nullptr;     // [nq][3] per-detscan PSD terms of the chi^2 gradient
+    int32_t coop_grid = 0;           // co-resident CTAs of the cooperative n_corr kernel
+    int32_t pass_grid = 0;           // persistent grid of the other pass kernels
+    int32_t tile_pairs = 0;          // requested column pairs per tile (0 = choose)
     int64_t device_bytes = 0;
     std::vector<void *> allocs;
 };
@@ -159,35 +189,41 @@ cudaError_t launch_gain_smooth(const GainSmoothArgs &a, cudaStream_t st);
 cudaError_t launch_decode_flags(const Plan &p, uint32_t *flags_out, cudaStream_t st);
 cudaError_t launch_project(const Plan &p, const float4 *map, const int32_t *pix, const uint16_t *psi,
                            const double *gain, float *s_out, cudaStream_t st);
-cudaError_t setup_dct_kernels(Plan &p);
-// co-resident clusters of C CTAs of the n_corr kernel with smem_dyn bytes of
-// dynamic shared memory each (0 if none fits)
-cudaError_t transform_cluster_occupancy(int C, size_t smem_dyn, int *nclusters);
-cudaError_t launch_gain(const Plan &p, const float *d, const float *s, const uint32_t *flags,
-                        const double *psd, tod_rng rng, int mode, double *g, double *mu,
-                        double *sig, cudaStream_t st, int work_begin, int work_count);
-cudaError_t launch_ncorr(const Plan &p, const float *d, const float *s, const double *gain,
-                         const uint32_t *flags, const double *psd, tod_rng rng, int mode,
-                         float tol, int maxit, float *x, int32_t *iters, cudaStream_t st,
-                         int work_begin, int work_count, bool prepare = true);
-// the same draw with caller-provided filter-weight scratch: at most
-// nclusters_max clusters, each using C x sz float4 of it
-cudaError_t launch_ncorr_scratch(const Plan &p, const float *d, const float *s, const double *gain,
-                                 const uint32_t *flags, const double *psd, tod_rng rng, int mode,
-                                 float tol, int maxit, float *x, int32_t *iters, cudaStream_t st,
-                                 int work_begin, int work_count, float4 *scratch, int nclusters_max,
-                                 bool prepare = true);
-cudaError_t launch_chi2(const Plan &p, const float *d, const float *s, const double *gain,
-                        const uint32_t *flags, const double *psd, double *chi2, double *dgain,
-                        double *dpsd, float *v, cudaStream_t st);
+cudaError_t launch_project64(const Plan &p, const double *map, const int32_t *pix, const uint16_t *psi,
+                             const double *gain, double *s_out, cudaStream_t st);
+// multi-pass transform stages (k_tx.cu)
+struct TxNcorrScratch {
+    float2 *Y;          // complex intermediate of the launch's detscans
+    int64_t *wpre;      // flag-word prefix: (launch samples)/32 + 3 entries
+    float *cgv;         // CG vectors, 5 x cgcap
+    int64_t cgcap;      // flagged samples the vectors hold
+};
+cudaError_t setup_tx_kernels(Plan &p);
+cudaError_t launch_tx_gain(const Plan &p, const float *d, const float *s, const uint32_t *flags, const double *psd,
+                           tod_rng rng, int mode, double *g, double *mu, double *sig, cudaStream_t st, int q0, int q1);
+// one cooperative launch over detscans [q0, q1) with `grid` CTAs (at most p.coop_grid)
+cudaError_t launch_tx_ncorr(const Plan &p, const float *d, const float *s, const double *gain,
+                            const uint32_t *flags, const double *psd, tod_rng rng, int mode, float tol, int maxit,
+                            float *x, int32_t *iters, cudaStream_t st, int q0, int q1, const TxNcorrScratch &sc,
+                            int grid);
+cudaError_t launch_tx_chi2(const Plan &p, bool fp64, const float *d, const void *s, const double *gain,
+                           const uint32_t *flags, const double *psd, double *chi2_q, double *dgain, double *dpsd_q,
+                           double *total, double *dpsd_det, void *v_out, cudaStream_t st);
 cudaError_t setup_bin_kernel(Plan &p);
 cudaError_t launch_toeplitz_prep(const Plan &p, const double *psd, cudaStream_t st);
 cudaError_t launch_noise_psd(const Plan &p, const float *spec, const double *psd_in, tod_rng rng, int nsteps,
                              double step_lnfk, double step_al, double *psd_out, int32_t *acc_out,
                              double *loglike_out, cudaStream_t st);
+// with part non-null the per-pixel double-double pairs go there ([npix][20])
+// instead of A, b, hits
 cudaError_t launch_bin(const Plan &p, const uint16_t *psi, const float *d, const float *ncorr,
                        const double *gain, const uint32_t *flags, const double *psd, double *A,
-                       double *b, int32_t *hits, cudaStream_t st);
+                       double *b, int32_t *hits, double *part, cudaStream_t st);
+cudaError_t launch_combine(const double *parts, int nparts, int64_t np, double *A, double *b, int32_t *hits,
+                           cudaStream_t st);
+// P^T (g y): out_p = sum over the samples of pixel p of g_q y_t (1, cos 2psi, sin 2psi)
+cudaError_t launch_project_adjoint(const Plan &p, const uint16_t *psi, const void *y, bool fp64, const double *gain,
+                                   double *out, cudaStream_t st);
 cudaError_t launch_solve(const Plan &p, const double *A, const double *b, const int32_t *hits,
                          double rcond_min, double *map, float4 *map32, double *rcond,
                          uint8_t *valid, cudaStream_t st);

@@ -42,6 +42,10 @@ struct BinArgs {
     const float2 *trig;
     int ndet;
     double *rec;
+    // adjoint of the projection: no mask (flags null), weights 0 and g, and,
+    // when y64 is set, the FP64 input y = hi + lo read as d = hi, x = -lo
+    bool adjoint;
+    const double *y64;
 };
 
 // sum of two double-words (two-sum on the heads, tails added)
@@ -90,8 +94,22 @@ __device__ __forceinline__ void sums_store(const RunSums &r, double wA, double w
 }
 
 __device__ __forceinline__ uint16_t psi_flag(const BinArgs &a, int64_t tg) {
-    const uint32_t fb = (__ldg(a.flags + (tg >> 5)) >> (tg & 31)) & 1u;
+    const uint32_t fb = a.flags ? (__ldg(a.flags + (tg >> 5)) >> (tg & 31)) & 1u : 0u;
     return static_cast<uint16_t>((__ldg(a.psi + tg) & 0x0FFF) | (fb << 15));
+}
+
+// data and residual of sample tg (the adjoint's input: y, or the head and
+// negated tail of the FP64 y, whose difference is y to FP64 accuracy)
+__device__ __forceinline__ void load_dx(const BinArgs &a, int64_t tg, float &dv, float &xv) {
+    if (a.y64) {
+        const double y = __ldg(a.y64 + tg);
+        const float hi = static_cast<float>(y);
+        dv = hi;
+        xv = -static_cast<float>(y - static_cast<double>(hi));
+    } else {
+        dv = __ldg(a.d + tg);
+        xv = a.x ? __ldg(a.x + tg) : 0.f;
+    }
 }
 
 __global__ void __launch_bounds__(BIN_T) k_bin(BinArgs a)
@@ -110,10 +128,15 @@ __global__ void __launch_bounds__(BIN_T) k_bin(BinArgs a)
     // by thread 0 (FP64 issues at 1/64 of the FP32 rate on this part)
     __shared__ double s_w[2];
     if (threadIdx.x == 0) {
-        const double sig0 = a.psd[3 * (q % a.ndet)];
         const double gq = a.gain[q];
-        s_w[0] = gq * gq / (sig0 * sig0);
-        s_w[1] = gq / (sig0 * sig0);
+        if (a.adjoint) {
+            s_w[0] = 0.0;
+            s_w[1] = gq;
+        } else {
+            const double sig0 = a.psd[3 * (q % a.ndet)];
+            s_w[0] = gq * gq / (sig0 * sig0);
+            s_w[1] = gq / (sig0 * sig0);
+        }
     }
     __syncthreads();
     const double wA = s_w[0], wb = s_w[1];
@@ -126,7 +149,9 @@ __global__ void __launch_bounds__(BIN_T) k_bin(BinArgs a)
             const int64_t tg = o + __ldg(a.ld_t + s0 + i);     // a single run: run order
             const uint16_t pf = psi_flag(a, tg);
             if (pf >> 15) continue;
-            sums_add(r, __ldg(a.trig + (pf & 0x0FFF)), __ldg(a.d + tg), __ldg(a.x + tg));
+            float dv, xv;
+            load_dx(a, tg, dv, xv);
+            sums_add(r, __ldg(a.trig + (pf & 0x0FFF)), dv, xv);
         }
 #pragma unroll
         for (int ofs = 16; ofs; ofs >>= 1) {
@@ -183,8 +208,7 @@ __global__ void __launch_bounds__(BIN_T) k_bin(BinArgs a)
         if (pf >> 15) cs.x = 2.0f;
         const int i = pos[u];
         s_cs[i] = cs;
-        s_d[i] = __ldg(a.d + tg);
-        s_x[i] = __ldg(a.x + tg);
+        load_dx(a, tg, s_d[i], s_x[i]);
     }
     __syncthreads();
     // four lanes per run: lane j of the quad takes samples j, j+4, ...; the
@@ -220,25 +244,75 @@ __global__ void __launch_bounds__(BIN_T) k_bin(BinArgs a)
     }
 }
 
+// Per pixel, its runs added in ascending detscan order as a double-double
+// (Knuth two-sum: hi + lo carries the sum to about 2^-104 of its size), then
+// rounded once.  The rounded total is the sum of the runs correctly rounded
+// but for sums within ~2^-104 of a rounding tie, whatever the grouping: the
+// normal equations of a band split into scan ranges and combined with
+// tod_combine_partials equal those of the whole band.
+struct DD { double hi, lo; };
+__device__ __forceinline__ void dd_add(DD &a, double x) {
+    const double s = a.hi + x;
+    const double bb = s - a.hi;
+    const double e = (a.hi - (s - bb)) + (x - bb);
+    a.hi = s;
+    a.lo += e;
+}
+__device__ __forceinline__ void dd_add_dd(DD &a, const DD &b) {
+    dd_add(a, b.hi);
+    a.lo += b.lo;
+}
+
 __global__ void __launch_bounds__(256)
 k_reduce(const double *__restrict__ rec, const int64_t *__restrict__ pix_slot_off, int npix,
-         double *__restrict__ A, double *__restrict__ b, int32_t *__restrict__ hits)
+         double *__restrict__ A, double *__restrict__ b, int32_t *__restrict__ hits, double *__restrict__ part)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npix) return;
-    double s[10];
+    DD s[10];
 #pragma unroll
-    for (int i = 0; i < 10; ++i) s[i] = 0.0;
+    for (int i = 0; i < 10; ++i) s[i] = DD{0.0, 0.0};
     for (int64_t k = pix_slot_off[p]; k < pix_slot_off[p + 1]; ++k) {
         const double *r = rec + k * 10;
 #pragma unroll
-        for (int i = 0; i < 10; ++i) s[i] += r[i];
+        for (int i = 0; i < 10; ++i) dd_add(s[i], r[i]);
+    }
+    if (part) {          // the unrounded pairs (hi, lo) of the ten sums
+        double *o = part + static_cast<int64_t>(p) * 20;
+#pragma unroll
+        for (int i = 0; i < 10; ++i) { o[2 * i] = s[i].hi; o[2 * i + 1] = s[i].lo; }
+        return;
+    }
+    if (A) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) A[static_cast<int64_t>(p) * 6 + i] = s[i].hi + s[i].lo;
     }
 #pragma unroll
-    for (int i = 0; i < 6; ++i) A[static_cast<int64_t>(p) * 6 + i] = s[i];
+    for (int i = 0; i < 3; ++i) b[static_cast<int64_t>(p) * 3 + i] = s[6 + i].hi + s[6 + i].lo;
+    if (hits) hits[p] = static_cast<int32_t>(s[9].hi + s[9].lo);
+}
+
+// Shards' pairs of pixels [0, np) added in rank order as double-doubles,
+// rounded once: parts [nparts][np][20] -> A [np][6], b [np][3], hits [np].
+__global__ void __launch_bounds__(256)
+k_combine(const double *__restrict__ parts, int nparts, int64_t np, double *__restrict__ A, double *__restrict__ b,
+          int32_t *__restrict__ hits)
+{
+    const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    DD s[10];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) b[static_cast<int64_t>(p) * 3 + i] = s[6 + i];
-    hits[p] = static_cast<int32_t>(s[9]);
+    for (int i = 0; i < 10; ++i) s[i] = DD{0.0, 0.0};
+    for (int r = 0; r < nparts; ++r) {
+        const double *o = parts + (static_cast<int64_t>(r) * np + p) * 20;
+#pragma unroll
+        for (int i = 0; i < 10; ++i) dd_add_dd(s[i], DD{o[2 * i], o[2 * i + 1]});
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) A[p * 6 + i] = s[i].hi + s[i].lo;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) b[p * 3 + i] = s[6 + i].hi + s[6 + i].lo;
+    hits[p] = static_cast<int32_t>(s[9].hi + s[9].lo);
 }
 
 // ---------------------------------------------------------------------------
@@ -288,18 +362,45 @@ cudaError_t setup_bin_kernel(Plan &)
 
 cudaError_t launch_bin(const Plan &p, const uint16_t *psi, const float *d, const float *ncorr,
                        const double *gain, const uint32_t *flags, const double *psd, double *A,
-                       double *b, int32_t *hits, cudaStream_t st)
+                       double *b, int32_t *hits, double *part, cudaStream_t st)
 {
     if (p.nq == 0) return cudaSuccess;
     BinArgs a;
     a.psi = psi; a.d = d; a.x = ncorr; a.gain = gain; a.flags = flags; a.psd = psd; a.off = p.off;
     a.ld_t = p.ld_t; a.ld_pos = p.ld_pos; a.pair_start = p.pair_start; a.pair_len = p.pair_len; a.pair_slot = p.pair_slot;
     a.tile_q = p.bin_tile_q; a.tile_r0 = p.bin_tile_r0; a.trig = p.trig; a.ndet = p.ndet; a.rec = p.rec;
+    a.adjoint = false; a.y64 = nullptr;
     if (p.nbin_tiles > 0) k_bin<<<p.nbin_tiles, BIN_T, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int nb = (p.npix + 255) / 256;
-    k_reduce<<<nb, 256, 0, st>>>(p.rec, p.pix_slot_off, p.npix, A, b, hits);
+    k_reduce<<<nb, 256, 0, st>>>(p.rec, p.pix_slot_off, p.npix, A, b, hits, part);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine(const double *parts, int nparts, int64_t np, double *A, double *b, int32_t *hits,
+                           cudaStream_t st)
+{
+    if (np <= 0) return cudaSuccess;
+    k_combine<<<static_cast<unsigned>((np + 255) / 256), 256, 0, st>>>(parts, nparts, np, A, b, hits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project_adjoint(const Plan &p, const uint16_t *psi, const void *y, bool fp64, const double *gain,
+                                   double *out, cudaStream_t st)
+{
+    if (p.nq == 0) return cudaSuccess;
+    BinArgs a;
+    a.psi = psi; a.d = fp64 ? nullptr : static_cast<const float *>(y); a.x = nullptr; a.gain = gain;
+    a.flags = nullptr; a.psd = nullptr; a.off = p.off;
+    a.ld_t = p.ld_t; a.ld_pos = p.ld_pos; a.pair_start = p.pair_start; a.pair_len = p.pair_len; a.pair_slot = p.pair_slot;
+    a.tile_q = p.bin_tile_q; a.tile_r0 = p.bin_tile_r0; a.trig = p.trig; a.ndet = p.ndet; a.rec = p.rec;
+    a.adjoint = true; a.y64 = fp64 ? static_cast<const double *>(y) : nullptr;
+    if (p.nbin_tiles > 0) k_bin<<<p.nbin_tiles, BIN_T, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int nb = (p.npix + 255) / 256;
+    k_reduce<<<nb, 256, 0, st>>>(p.rec, p.pix_slot_off, p.npix, nullptr, out, nullptr, nullptr);
     return cudaGetLastError();
 }
 

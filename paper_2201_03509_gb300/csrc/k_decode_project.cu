@@ -241,6 +241,42 @@ k_project(const float4 *__restrict__ map, const int32_t *__restrict__ pix,
     }
 }
 
+// The same in FP64: map double[3][npix] (rows T, Q, U), the FP32 table
+// values read as FP64, s in FP64.
+__global__ void __launch_bounds__(256)
+k_project64(const double *__restrict__ map, const int32_t *__restrict__ pix,
+            const uint16_t *__restrict__ psi, const double *__restrict__ gain,
+            const float2 *__restrict__ trig, const int32_t *__restrict__ tile_q,
+            const int64_t *__restrict__ tile_t0, const int64_t *__restrict__ off,
+            int32_t npix, double *__restrict__ s_out, int32_t *status)
+{
+    const int q = tile_q[blockIdx.x];
+    const int64_t t0 = tile_t0[blockIdx.x];
+    const int64_t t1 = (t0 + ELEM_TILE < off[q + 1]) ? t0 + ELEM_TILE : off[q + 1];
+    const double g = gain ? gain[q] : 1.0;
+    for (int64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+        const int32_t pp = pix[t];
+        const uint32_t b = psi[t];
+        if (static_cast<uint32_t>(pp) >= static_cast<uint32_t>(npix) || b >= TOD_N_PSI) {
+            set_status(status, q, TOD_ERR_ARG);
+            s_out[t] = 0.0;
+            continue;
+        }
+        const float2 cs = __ldg(trig + b);
+        const double T = __ldg(map + pp), Q = __ldg(map + npix + pp), U = __ldg(map + 2 * static_cast<int64_t>(npix) + pp);
+        s_out[t] = g * (T + Q * static_cast<double>(cs.x) + U * static_cast<double>(cs.y));
+    }
+}
+
+cudaError_t launch_project64(const Plan &p, const double *map, const int32_t *pix, const uint16_t *psi,
+                             const double *gain, double *s_out, cudaStream_t st)
+{
+    if (p.ntile == 0) return cudaSuccess;
+    k_project64<<<p.ntile, 256, 0, st>>>(map, pix, psi, gain, p.trig, p.tile_q, p.tile_t0, p.off, p.npix,
+                                         s_out, p.status);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_project(const Plan &p, const float4 *map, const int32_t *pix, const uint16_t *psi,
                            const double *gain, float *s_out, cudaStream_t st)
 {

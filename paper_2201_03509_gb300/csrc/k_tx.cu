@@ -1,0 +1,1668 @@
+// A3 batched DCT-II (the mirrored FFT of Sect. 4.2) as passes through
+// memory, and on it A4 (gain draw), A5 (correlated-noise draw with CG gap
+// filling; Eq. `gibbsstart`, Sect. 5) and A8 (TOD chi^2 and gradients).
+//
+// A length-n real DCT-II is an m = n/2 complex FFT of the even/odd-packed,
+// reversed-odd sequence z_j = (v_{2j}, v_{2j+1}), v_i = x_{2i} (i < m),
+// x_{2n-1-2i} (i >= m) (Makhoul 1980), plus a real split.  The FFT is
+// four-step, m = m1 x m2, with j = j1 m2 + j2 and k = k1 + m1 k2:
+//   column pass: for a tile of column pairs {c, m2-1-c}: FFTs of length m1
+//     along j1, times W_m^{c k1}, written row-major to the intermediate Y;
+//     z_j and z_{m-1-j} together are the four samples x_{4j..4j+3}, so the
+//     tile reads and writes whole runs of samples;
+//   row pass: for a tile of row pairs {k1, m1-k1}: FFTs of length m2 along
+//     k2, the real split (Z_k with Z_{m-k}) into packed orthonormal
+//     coefficients (X_k, X_{n-k}) (slot 0: (X_0, X_m)), a per-mode filter,
+//     the inverse split and inverse FFTs, written back to Y;
+//   inverse column pass: times W_m^{-c k1}, inverse FFTs, samples out.
+// Every tile is independent: a CTA holds one tile in shared memory, passes
+// are separate grid-wide phases, and the intermediate goes through L2/HBM.
+#include <cooperative_groups.h>
+#include "fft_reg.cuh"
+
+namespace cgrp = cooperative_groups;
+
+namespace tg {
+
+// ---------------------------------------------------------------------------
+// per-item context
+// ---------------------------------------------------------------------------
+struct TxCtx {
+    TxLen L;
+    float s2, inv_s2, inv_s, fscale, alpha, g;   // detector noise, detscan gain
+    int q, blk, det;
+    int mode;                                    // CgState mode of the detscan (n_corr)
+    int64_t o;                                   // first sample of the detscan
+    int64_t yb;                                  // first complex value of its Y block
+    int64_t koff;                                // first flagged rank (n_corr)
+};
+
+// Copy the length plan of item (q, blk) into shared memory (skipped when the
+// previous item had the same length) and set the detscan scalars.  All
+// threads call it; it ends with a barrier.
+__device__ __forceinline__ void tx_begin(TxCtx &X, const TxLen *__restrict__ txl, const int32_t *__restrict__ q_tx,
+                                         const int64_t *__restrict__ off, int q, int blk, int64_t obase, int ndet,
+                                         double fsamp, const double *psd, const double *gain, int &cur)
+{
+    __syncthreads();                 // earlier readers of X are done
+    const int li = q_tx[q];
+    if (li != cur) {
+        const int4 *src = reinterpret_cast<const int4 *>(txl + li);
+        int4 *dst = reinterpret_cast<int4 *>(&X.L);
+        for (int i = threadIdx.x; i < static_cast<int>(sizeof(TxLen) / 16); i += blockDim.x) dst[i] = src[i];
+    }
+    if (threadIdx.x == 0) {
+        X.q = q;
+        X.blk = blk;
+        X.det = q % ndet;
+        X.o = off[q];
+        X.yb = (off[q] - obase) >> 1;
+        if (psd) {
+            const double sig0 = psd[3 * X.det], fk = psd[3 * X.det + 1], al = psd[3 * X.det + 2];
+            const int n = static_cast<int>(off[q + 1] - off[q]);
+            X.s2 = static_cast<float>(sig0 * sig0);
+            X.inv_s2 = static_cast<float>(1.0 / (sig0 * sig0));
+            X.inv_s = static_cast<float>(1.0 / sig0);
+            X.fscale = static_cast<float>(fsamp / (2.0 * n * fk));
+            X.alpha = static_cast<float>(al);
+        }
+        X.g = gain ? static_cast<float>(gain[q]) : 1.0f;
+    }
+    cur = li;
+    __syncthreads();
+}
+
+// (f_k / f_knee)^alpha at DCT mode k, FP32
+__device__ __forceinline__ float tx_fpow(int k, float fscale, float alpha) {
+    return exp2f(alpha * log2f(static_cast<float>(k) * fscale));
+}
+
+// twiddle block of a length: W_m1^i, W_m2^i, W_4n^{k1}, W_4n^{m1 k2},
+// W_4n^{5 k1}, W_4n^{5 m1 k2}, W_m^{64 i}, W_m^i (i < 64)
+template <class V> struct TwB {
+    const V *tw1, *tw2, *sa1, *sb1, *sa5, *sb5, *t4hi, *t4lo;
+    __device__ __forceinline__ TwB(const V *base, const TxLen &L) {
+        tw1 = base;
+        tw2 = tw1 + L.m1;
+        sa1 = tw2 + L.m2;
+        sb1 = sa1 + L.m1;
+        sa5 = sb1 + L.m2;
+        sb5 = sa5 + L.m1;
+        t4hi = sb5 + L.m2;
+        t4lo = t4hi + L.m / 64 + 1;
+    }
+    __device__ __forceinline__ V w4(int r) const { return vmul(vld(t4hi + (r >> 6)), vld(t4lo + (r & 63))); }
+};
+
+// ---------------------------------------------------------------------------
+// column tiles: pairs p in [p0, p0 + np), tile column lc = side * TP + i
+// (side 0: column p0 + i; side 1: column m2-1-p0-i, absent when it is the
+// middle column already held by side 0); element (j1, lc) at j1 * W + lc.
+// ---------------------------------------------------------------------------
+struct ColGeo {
+    int n, m, m1, m2, P2, TP, W, p0, np, m1h;
+    __device__ __forceinline__ ColGeo(const TxLen &L, int blk) {
+        n = L.n; m = L.m; m1 = L.m1; m2 = L.m2; P2 = L.P2; TP = L.TP; W = 2 * L.TP;
+        p0 = blk * TP;
+        np = min(TP, P2 - p0);
+        m1h = (m1 + 1) >> 1;
+    }
+    __device__ __forceinline__ int col(int lc) const {     // -1: no column
+        const int side = lc >= TP, i = lc - side * TP;
+        if (i >= np) return -1;
+        const int p = p0 + i;
+        if (!side) return p;
+        const int c = m2 - 1 - p;
+        return c == p ? -1 : c;
+    }
+    __device__ __forceinline__ int lcol(int c) const { return c < P2 ? c - p0 : TP + (m2 - 1 - c - p0); }
+};
+
+// flagged-sample mask (bit u: sample t + u) of samples t..t+cnt-1, cnt <= 4
+__device__ __forceinline__ uint32_t flag_bits(const uint32_t *__restrict__ fl, int64_t t, int cnt) {
+    const int64_t w = t >> 5;
+    const int b = static_cast<int>(t & 31);
+    uint32_t v = __ldg(fl + w) >> b;
+    if (b + cnt > 32) v |= __ldg(fl + w + 1) << (32 - b);
+    return v & ((1u << cnt) - 1u);
+}
+
+// The four samples of unit j (x_{4j..4j+3}; two at the centre j = m-1-j):
+// load them as z_j = (x0, x2), z_{m-1-j} = (x3, x1).
+__device__ __forceinline__ float4 ld4(const float *__restrict__ x, int64_t t, bool centre) {
+    const float2 a = __ldg(reinterpret_cast<const float2 *>(x + t));
+    if (centre) return make_float4(a.x, a.y, 0.f, 0.f);
+    const float2 b = __ldg(reinterpret_cast<const float2 *>(x + t + 2));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Forward column pass: fill the tile through fill(j1, lc, c, j, jm, centre,
+// tile) -- called for every unit j <= m-1-j of the tile, it writes z_j at
+// (j1, lc) and z_{m-1-j} at (m1-1-j1, lcol(m2-1-c)) --, FFT the columns,
+// twiddle, store Y.  pre(tile) runs before fill (after the invalid columns
+// are zeroed) with a barrier in between.
+template <class V, class Pre, class Fill>
+__device__ __forceinline__ void col_forward(const TxCtx &X, V *b0, V *b1, V *__restrict__ Y, const V *__restrict__ twb,
+                                            Pre pre, Fill fill)
+{
+    const ColGeo G(X.L, X.blk);
+    const int W = G.W, m1 = G.m1, m2 = G.m2;
+    // invalid columns are zero
+    for (int e = threadIdx.x; e < m1 * W; e += TX_T) {
+        const int j1 = fdiv(e, X.L.f_W), lc = e - j1 * W;
+        if (G.col(lc) < 0) b0[e] = vzero<V>();
+    }
+    pre(b0);
+    __syncthreads();
+    for (int u = threadIdx.x; u < G.m1h * W; u += TX_T) {
+        const int j1 = fdiv(u, X.L.f_W), lc = u - j1 * W;
+        const int c = G.col(lc);
+        if (c < 0) continue;
+        const int j = j1 * m2 + c, jm = G.m - 1 - j;
+        if (j > jm) continue;
+        fill(j1, lc, c, j, jm, b0);
+    }
+    __syncthreads();
+    const TwB<V> T(twb, X.L);
+    V *R = sp_transform<false, TX_T>(b0, b1, m1, X.L.s1, X.L.nr1, W, X.L.f_W, W, 1, true, T.tw1);
+    V *Yq = Y + X.yb;
+    for (int e = threadIdx.x; e < m1 * W; e += TX_T) {
+        const int k1 = fdiv(e, X.L.f_W), lc = e - k1 * W;
+        const int c = G.col(lc);
+        if (c < 0) continue;
+        Yq[static_cast<int64_t>(k1) * m2 + c] = vmul(R[e], T.w4(c * k1));
+    }
+}
+
+// Inverse column pass: load Y, twiddle, inverse FFT the columns, then
+// out(j1, lc, c, j, jm, centre, tile) for every unit j <= m-1-j.
+template <class V, class Out>
+__device__ __forceinline__ void col_inverse(const TxCtx &X, V *b0, V *b1, const V *__restrict__ Y,
+                                            const V *__restrict__ twb, Out out)
+{
+    const ColGeo G(X.L, X.blk);
+    const int W = G.W, m1 = G.m1, m2 = G.m2;
+    const TwB<V> T(twb, X.L);
+    const V *Yq = Y + X.yb;
+    for (int e = threadIdx.x; e < m1 * W; e += TX_T) {
+        const int k1 = fdiv(e, X.L.f_W), lc = e - k1 * W;
+        const int c = G.col(lc);
+        b0[e] = c < 0 ? vzero<V>() : vmulc(Yq[static_cast<int64_t>(k1) * m2 + c], T.w4(c * k1));
+    }
+    __syncthreads();
+    V *R = sp_transform<true, TX_T>(b0, b1, m1, X.L.s1, X.L.nr1, W, X.L.f_W, W, 1, true, T.tw1);
+    for (int u = threadIdx.x; u < G.m1h * W; u += TX_T) {
+        const int j1 = fdiv(u, X.L.f_W), lc = u - j1 * W;
+        const int c = G.col(lc);
+        if (c < 0) continue;
+        const int j = j1 * m2 + c, jm = G.m - 1 - j;
+        if (j > jm) continue;
+        out(j1, lc, c, j, jm, R);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// row tiles: row pairs p in [r0, r0 + nr); slot 2i is row r0 + i, slot
+// 2i+1 row m1 - r0 - i (unused when that row is the same, or r0 + i = 0);
+// element (slot, k2) at slot * m2p + k2.
+// ---------------------------------------------------------------------------
+struct RowGeo {
+    int n, m, m1, m2, m2p, r0, nr, TR;
+    __device__ __forceinline__ RowGeo(const TxLen &L, int blk) {
+        n = L.n; m = L.m; m1 = L.m1; m2 = L.m2; m2p = L.m2p; TR = L.TR;
+        r0 = blk * TR;
+        nr = min(TR, L.P1 - r0);
+    }
+    __device__ __forceinline__ int row(int slot) const {   // -1: unused
+        const int i = slot >> 1;
+        if (i >= nr) return -1;
+        const int p = r0 + i;
+        if (!(slot & 1)) return p;
+        const int r = m1 - p;
+        return (p == 0 || r == p) ? -1 : r;
+    }
+};
+
+// Packed orthonormal coefficients of slot k from Z_k, Z_{m-k} (forward
+// half-split): W = e^{-i pi k/2n} A + e^{-i 5 pi k/2n} B, k = k1 + m1 k2.
+template <class V>
+__device__ __forceinline__ V split_f(const TwB<V> &T, V a, V b, int k1, int k2, typename VecT<V>::S sq) {
+    typedef typename VecT<V>::S S;
+    const V cb = vconj(b);
+    const V A = vscale(vadd(a, cb), static_cast<S>(0.5));
+    const V d = vsub(a, cb);
+    const V Bv = vmake<V>(static_cast<S>(0.5) * d.y, static_cast<S>(-0.5) * d.x);
+    const V e1 = vmul(vld(T.sa1 + k1), vld(T.sb1 + k2)), e5 = vmul(vld(T.sa5 + k1), vld(T.sb5 + k2));
+    const V Wv = vadd(vmul(e1, A), vmul(e5, Bv));
+    return vmake<V>(sq * Wv.x, -sq * Wv.y);
+}
+// Z_k from the packed slots k and m-k (inverse half-split; sq includes 1/m).
+template <class V>
+__device__ __forceinline__ V split_i(const TwB<V> &T, V yk, V yp, int k1, int k2, int q1, int q2,
+                                     typename VecT<V>::S sq) {
+    typedef typename VecT<V>::S S;
+    const V ek = vmul(vld(T.sa1 + k1), vld(T.sb1 + k2)), ep = vmul(vld(T.sa1 + q1), vld(T.sb1 + q2));
+    const V Vk = vscale(vmulc(vconj(yk), ek), sq);
+    const V Vp = vscale(vmulc(vconj(yp), ep), sq);
+    const V cVp = vconj(Vp);
+    const V A = vscale(vadd(Vk, cVp), static_cast<S>(0.5));
+    const V e4 = vmulc(vmul(vld(T.sa5 + k1), vld(T.sb5 + k2)), ek);
+    const V Bv = vscale(vmulc(vsub(Vk, cVp), e4), static_cast<S>(0.5));
+    return vmake<V>(A.x - Bv.y, A.y + Bv.x);
+}
+
+// Row pass.  Loads the tile's rows from Y, forward row FFTs, then
+// pre(free_buffer) (a barrier follows), then for every packed slot:
+// Y' = f(e, k, Y) (e: tile element, k: slot, Y = (X_k, X_{n-k}) or (X_0, X_m));
+// with INV_BACK the inverse split and inverse row FFTs follow and the rows go
+// back to Y.
+template <class V, bool INV_BACK, class Pre, class F>
+__device__ __forceinline__ void row_pass(const TxCtx &X, V *b0, V *b1, V *__restrict__ Y, const V *__restrict__ twb,
+                                         Pre pre, F f)
+{
+    typedef typename VecT<V>::S S;
+    const RowGeo G(X.L, X.blk);
+    const int m1 = G.m1, m2 = G.m2, m2p = G.m2p;
+    const int nslot = 2 * G.TR;
+    V *Yq = Y + X.yb;
+    for (int e = threadIdx.x; e < nslot * m2; e += TX_T) {
+        const int s = fdiv(e, X.L.f_m2), k2 = e - s * m2;
+        const int r = G.row(s);
+        b0[s * m2p + k2] = r < 0 ? vzero<V>() : Yq[static_cast<int64_t>(r) * m2 + k2];
+    }
+    __syncthreads();
+    const TwB<V> T(twb, X.L);
+    V *R = sp_transform<false, TX_T>(b0, b1, m2, X.L.s2, X.L.nr2, nslot, X.L.f_2TR, 1, m2p, true, T.tw2);
+    V *Fr = R == b0 ? b1 : b0;
+    pre(Fr);
+    __syncthreads();
+    const S sqf = static_cast<S>(X.L.sq_fwd), s0f = static_cast<S>(X.L.s0_fwd);
+    const S sqi = static_cast<S>(X.L.sq_inv), s0i = static_cast<S>(X.L.s0_inv);
+    for (int e = threadIdx.x; e < G.nr * m2; e += TX_T) {
+        const int pl = fdiv(e, X.L.f_m2), k2 = e - pl * m2;
+        const int p = G.r0 + pl;
+        const int cnt = (p == 0) ? (m2 / 2 + 1) : ((2 * p == m1) ? (m2 + 1) / 2 : m2);
+        if (k2 >= cnt) continue;
+        int ib, q1, q2;
+        if (p == 0) { q1 = 0; q2 = (k2 == 0) ? 0 : m2 - k2; ib = 2 * pl * m2p + q2; }
+        else { q1 = m1 - p; q2 = m2 - 1 - k2; ib = ((q1 == p) ? 2 * pl : 2 * pl + 1) * m2p + q2; }
+        const int ia = 2 * pl * m2p + k2;
+        const V Za = R[ia], Zb = R[ib];
+        if (p == 0 && k2 == 0) {
+            V Yv = vmake<V>((Za.x + Za.y) * s0f, (Za.x - Za.y) * s0f);
+            Yv = f(ia, 0, Yv);
+            if (INV_BACK) {
+                const S V0 = Yv.x * s0i, Vm = Yv.y * s0i;
+                R[ia] = vmake<V>(static_cast<S>(0.5) * (V0 + Vm), static_cast<S>(0.5) * (V0 - Vm));
+            }
+            continue;
+        }
+        V Ya = split_f(T, Za, Zb, p, k2, sqf);
+        Ya = f(ia, p + m1 * k2, Ya);
+        if (ib != ia) {
+            V Yb = split_f(T, Zb, Za, q1, q2, sqf);
+            Yb = f(ib, q1 + m1 * q2, Yb);
+            if (INV_BACK) {
+                R[ib] = split_i(T, Yb, Ya, q1, q2, p, k2, sqi);
+                R[ia] = split_i(T, Ya, Yb, p, k2, q1, q2, sqi);
+            }
+        } else if (INV_BACK) {
+            R[ia] = split_i(T, Ya, Ya, p, k2, q1, q2, sqi);
+        }
+    }
+    if (!INV_BACK) return;
+    __syncthreads();
+    V *Ri = sp_transform<true, TX_T>(R, Fr, m2, X.L.s2, X.L.nr2, nslot, X.L.f_2TR, 1, m2p, true, T.tw2);
+    for (int e = threadIdx.x; e < nslot * m2; e += TX_T) {
+        const int s = fdiv(e, X.L.f_m2), k2 = e - s * m2;
+        const int r = G.row(s);
+        if (r >= 0) Yq[static_cast<int64_t>(r) * m2 + k2] = Ri[s * m2p + k2];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CTA reductions: FP32 double-word partials, warps merged by shuffles, the
+// warp results added in FP64 in a fixed order by thread 0.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ Acc2 acc_merge_tx(const Acc2 &a, const Acc2 &b) {
+    Acc2 r = a;
+    acc_add(r, b.s);
+    r.c = __fadd_rn(r.c, b.c);
+    return r;
+}
+__device__ __forceinline__ Acc2 warp_acc(Acc2 x) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        Acc2 y;
+        y.s = __shfl_xor_sync(0xffffffffu, x.s, o);
+        y.c = __shfl_xor_sync(0xffffffffu, x.c, o);
+        x = acc_merge_tx(x, y);
+    }
+    return x;
+}
+// NV values per thread summed over the CTA; the totals land in out[0..NV)
+// (shared) for every thread after the call.  s_red holds NV * TX_T/32.
+template <int NV>
+__device__ __forceinline__ void block_sums(const Acc2 (&a)[NV], double *s_red, double *out) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const Acc2 w = warp_acc(a[v]);
+        if (lane == 0) s_red[v * (TX_T / 32) + warp] = acc_value(w);
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double t = 0.0;
+        for (int w = 0; w < TX_T / 32; ++w) t += s_red[threadIdx.x * (TX_T / 32) + w];
+        out[threadIdx.x] = t;
+    }
+    __syncthreads();
+}
+template <int NV>
+__device__ __forceinline__ void block_sums_d(const double (&a)[NV], double *s_red, double *out) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        double x = a[v];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) s_red[v * (TX_T / 32) + warp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double t = 0.0;
+        for (int w = 0; w < TX_T / 32; ++w) t += s_red[threadIdx.x * (TX_T / 32) + w];
+        out[threadIdx.x] = t;
+    }
+    __syncthreads();
+}
+
+// ===========================================================================
+// A4: gain.  a = sum_{k>=1} shat_k^2 / P_k (row pass), u = C^T(shat / P) and
+// b = sum_t M_t d_t u_t (inverse column pass): b = sum_k shat_k dhat_k / P_k.
+// ===========================================================================
+struct GainTx {
+    const float *d, *s;
+    const uint32_t *flags;
+    const double *psd;
+    const int64_t *off;
+    const TxLen *txl;
+    const int32_t *q_tx;
+    const float2 *tw;
+    const int2 *items;
+    int item0, nitems;
+    int ndet;
+    double fsamp;
+    int64_t obase;
+    float2 *Y;
+    double *part;                 // [item][4]
+};
+
+__global__ void __launch_bounds__(TX_T, 3) k_gain_cols(GainTx a)
+{
+    extern __shared__ __align__(16) float2 tx_smem[];
+    __shared__ TxCtx X;
+    float2 *b0 = tx_smem, *b1 = tx_smem + TX_TILE;
+    int cur = -1;
+    for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
+        const int2 w = a.items[a.item0 + it];
+        tx_begin(X, a.txl, a.q_tx, a.off, w.x, w.y, a.obase, a.ndet, a.fsamp, nullptr, nullptr, cur);
+        const float *sq = a.s + X.o;
+        const int64_t o = X.o;
+        col_forward(X, b0, b1, a.Y, a.tw + X.L.twb, [](float2 *) {},
+                    [&](int j1, int lc, int c, int j, int jm, float2 *U) {
+                        const ColGeo G(X.L, X.blk);
+                        const bool ctr = j == jm;
+                        const float4 v = ld4(sq, 4 * static_cast<int64_t>(j), ctr);
+                        const uint32_t fb = flag_bits(a.flags, o + 4 * static_cast<int64_t>(j), ctr ? 2 : 4);
+                        const float x0 = (fb & 1) ? 0.f : v.x, x1 = (fb & 2) ? 0.f : v.y;
+                        const float x2 = (fb & 4) ? 0.f : v.z, x3 = (fb & 8) ? 0.f : v.w;
+                        if (ctr) { U[j1 * G.W + lc] = make_float2(x0, x1); return; }
+                        U[j1 * G.W + lc] = make_float2(x0, x2);
+                        U[(G.m1 - 1 - j1) * G.W + G.lcol(G.m2 - 1 - c)] = make_float2(x3, x1);
+                    });
+    }
+}
+
+__global__ void __launch_bounds__(TX_T, 3) k_gain_rows(GainTx a)
+{
+    extern __shared__ __align__(16) float2 tx_smem[];
+    __shared__ TxCtx X;
+    __shared__ double s_red[TX_T / 32], s_out[1];
+    float2 *b0 = tx_smem, *b1 = tx_smem + TX_TILE;
+    int cur = -1;
+    for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
+        const int2 w = a.items[a.item0 + it];
+        tx_begin(X, a.txl, a.q_tx, a.off, w.x, w.y, a.obase, a.ndet, a.fsamp, a.psd, nullptr, cur);
+        const float fscale = X.fscale, alpha = X.alpha, s2 = X.s2;
+        const int n = X.L.n, m = X.L.m;
+        Acc2 sa[1] = {{0.f, 0.f}};
+        row_pass<float2, true>(X, b0, b1, a.Y, a.tw + X.L.twb, [](float2 *) {}, [&](int, int k, float2 S) {
+            const int ka = k, kb = (k == 0) ? m : n - k;
+            const float wa = ka == 0 ? 0.f : 1.0f / (s2 * (1.0f + tx_fpow(ka, fscale, alpha)));
+            const float wb = 1.0f / (s2 * (1.0f + tx_fpow(kb, fscale, alpha)));
+            const float2 Wv = make_float2(S.x * wa, S.y * wb);
+            acc_add_prod(sa[0], S.x, Wv.x);
+            acc_add_prod(sa[0], S.y, Wv.y);
+            return Wv;
+        });
+        block_sums<1>(sa, s_red, s_out);
+        if (threadIdx.x == 0) a.part[4 * static_cast<int64_t>(a.item0 + it)] = s_out[0];
+    }
+}
+
+__global__ void __launch_bounds__(TX_T, 3) k_gain_colsinv(GainTx a)
+{
+    extern __shared__ __align__(16) float2 tx_smem[];
+    __shared__ TxCtx X;
+    __shared__ double s_red[TX_T / 32], s_out[1];
+    float2 *b0 = tx_smem, *b1 = tx_smem + TX_TILE;
+    int cur = -1;
+    for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
+        const int2 w = a.items[a.item0 + it];
+        tx_begin(X, a.txl, a.q_tx, a.off, w.x, w.y, a.obase, a.ndet, a.fsamp, nullptr, nullptr, cur);
+        const float *dq = a.d + X.o;
+        const int64_t o = X.o;
+        Acc2 sb[1] = {{0.f, 0.f}};
+        col_inverse(X, b0, b1, a.Y, a.tw + X.L.twb, [&](int j1, int lc, int c, int j, int jm, const float2 *U) {
+            const ColGeo G(X.L, X.blk);
+            const bool ctr = j == jm;
+            const float4 dv = ld4(dq, 4 * static_cast<int64_t>(j), ctr);
+            const uint32_t fb = flag_bits(a.flags, o + 4 * static_cast<int64_t>(j), ctr ? 2 : 4);
+            const float2 za = U[j1 * G.W + lc];
+            if (ctr) {
+                acc_add_prod(sb[0], (fb & 1) ? 0.f : dv.x, za.x);
+                acc_add_prod(sb[0], (fb & 2) ? 0.f : dv.y, za.y);
+                return;
+            }
+            const float2 zb = U[(G.m1 - 1 - j1) * G.W + G.lcol(G.m2 - 1 - c)];
+            acc_add_prod(sb[0], (fb & 1) ? 0.f : dv.x, za.x);
+            acc_add_prod(sb[0], (fb & 2) ? 0.f : dv.y, zb.y);
+            acc_add_prod(sb[0], (fb & 4) ? 0.f : dv.z, za.y);
+            acc_add_prod(sb[0], (fb & 8) ? 0.f : dv.w, zb.x);
+        });
+        block_sums<1>(sb, s_red, s_out);
+        if (threadIdx.x == 0) a.part[4 * static_cast<int64_t>(a.item0 + it) + 1] = s_out[0];
+    }
+}
+
+// Per detscan: a and b summed over its row and column items in item order,
+// then the draw g ~ N(b/a, 1/a); a <= 0 (no usable sample) or a non-finite
+// sum gives g = 0 and TOD_ERR_ARG.  One thread per detscan.
+__global__ void __launch_bounds__(256) k_gain_fin(const double *__restrict__ rpart, const double *__restrict__ cpart,
+                                                  const int32_t *__restrict__ row_off,
+                                                  const int32_t *__restrict__ col_off, int q0, int q1,
+                                                  int rbase, int cbase, tod_rng rng, int mode, double *g_out,
+                                                  double *mu_out, double *sig_out, int32_t *status)
+{
+    const int q = q0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= q1) return;
+    double A = 0.0, B = 0.0;
+    for (int i = row_off[q]; i < row_off[q + 1]; ++i) A += rpart[4 * static_cast<int64_t>(i - rbase)];
+    for (int i = col_off[q]; i < col_off[q + 1]; ++i) B += cpart[4 * static_cast<int64_t>(i - cbase) + 1];
+    if (!(A > 0.0) || !isfinite(A) || !isfinite(B)) {
+        set_status(status, q, TOD_ERR_ARG);
+        g_out[q] = 0.0;
+        if (mu_out) mu_out[q] = 0.0;
+        if (sig_out) sig_out[q] = 0.0;
+        return;
+    }
+    const double mu = B / A, sg = 1.0 / sqrt(A);
+    double z = 0.0;
+    if (mode == TOD_MODE_DRAW) {
+        const uint64_t it = rng.gibbs_iter_dev ? *rng.gibbs_iter_dev : rng.gibbs_iter;
+        const u64x4 wv = philox4x64(0, static_cast<uint64_t>(q), 0, it, rng.seed, rng.band);
+        const double u1 = (static_cast<double>(wv.x[0] >> 11) + 0.5) * 1.1102230246251565e-16;
+        const double u2 = (static_cast<double>(wv.x[1] >> 11) + 0.5) * 1.1102230246251565e-16;
+        z = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+    }
+    g_out[q] = mu + z * sg;
+    if (mu_out) mu_out[q] = mu;
+    if (sig_out) sig_out[q] = sg;
+}
+
+// ===========================================================================
+// A8: chi^2 with n_corr marginalised and its gradients, FP32 or FP64
+// transforms.  rhat = C(M(d - g s)); L = 1/2 sum_{k>=1} [rhat^2/P + ln P];
+// dL/dtheta = 1/2 sum_k (1/P - rhat^2/P^2) dP/dtheta (row pass);
+// v = M C^T(rhat / P), dL/dg = -<M s, v> (inverse column pass).
+// ===========================================================================
+// the samples of unit j of s in the pass's precision (float or double s)
+template <class S>
+__device__ __forceinline__ void ld4s(const void *x, int64_t t, bool centre, S (&v)[4]) {
+    if constexpr (sizeof(S) == sizeof(float)) {
+        const float4 a = ld4(static_cast<const float *>(x), t, centre);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    } else {
+        const double *p = static_cast<const double *>(x) + t;     // t even: 16-byte aligned
+        const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+        v[0] = a.x; v[1] = a.y; v[2] = 0.0; v[3] = 0.0;
+        if (!centre) {
+            const double2 b = __ldg(reinterpret_cast<const double2 *>(p + 2));
+            v[2] = b.x; v[3] = b.y;
+        }
+    }
+}
+
+template <class V> struct Chi2Tx {
+    const float *d;
+    const void *s;                // float or double [N] as V
+    const double *gain;
+    const uint32_t *flags;
+    const double *psd;
+    const int64_t *off;
+    const TxLen *txl;
+    const int32_t *q_tx;
+    const V *tw;
+    const int2 *items;
+    int item0, nitems;
+    int ndet;
+    double fsamp;
+    int64_t obase;
+    V *Y;
+    double *part;                 // [item][4]
+    void *v_out;                  // float or double [N] (global sample index), or null
+};
+
+template <class V>
+__global__ void __launch_bounds__(TX_T) k_chi2_cols(Chi2Tx<V> a)
+{
+    typedef typename VecT<V>::S S;
+    extern __shared__ __align__(16) double2 tx_smem64[];
+    __shared__ TxCtx X;
+    V *b0 = reinterpret_cast<V *>(tx_smem64), *b1 = b0 + TX_TILE;
+    int cur = -1;
+    for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
+        const int2 w = a.items[a.item0 + it];
+        tx_begin(X, a.txl, a.q_tx, a.off, w.x, w.y, a.obase, a.ndet, a.fsamp, nullptr, nullptr, cur);
+        const double gq = a.gain[X.q];
+        const float *dq = a.d + X.o;
+        const int64_t o = X.o;
+        col_forward(X, b0, b1, a.Y, a.tw + X.L.twb, [](V *) {},
+                    [&](int j1, int lc, int c, int j, int jm, V *U) {
+                        const ColGeo G(X.L, X.blk);
+                        const bool ctr = j == jm;
+                        const float4 dv = ld4(dq, 4 * static_cast<int64_t>(j), ctr);
+                        S sx[4];
+                        ld4s<S>(a.s, o + 4 * static_cast<int64_t>(j), ctr, sx);
+                        const struct { S x, y, z, w; } sv = {sx[0], sx[1], sx[2], sx[3]};
+                        const uint32_t fb = flag_bits(a.flags, o + 4 * static_cast<int64_t>(j), ctr ? 2 : 4);
+                        const S g = static_cast<S>(gq);
+                        const S r0 = (fb & 1) ? S(0) : static_cast<S>(dv.x) - g * static_cast<S>(sv.x);
+                        const S r1 = (fb & 2) ? S(0) : static_cast<S>(dv.y) - g * static_cast<S>(sv.y);
+                        const S r2 = (fb & 4) ? S(0) : static_cast<S>(dv.z) - g * static_cast<S>(sv.z);
+                        const S r3 = (fb & 8) ? S(0) : static_cast<S>(dv.w) - g * static_cast<S>(sv.w);
+                        if (ctr) { U[j1 * G.W + lc] = vmake<V>(r0, r1); return; }
+                        U[j1 * G.W + lc] = vmake<V>(r0, r2);
+                        U[(G.m1 - 1 - j1) * G.W + G.lcol(G.m2 - 1 - c)] = vmake<V>(r3, r1);
+                    });
+    }
+}
+
+// FP64 per-mode quantities of the chi^2 row pass: the weights and the
+// gradient factors are formed in the pass's precision from the FP64 PSD.
+template <class V>
+__global__ void __launch_bounds__(TX_T) k_chi2_rows(Chi2Tx<V> a)
+{
+    typedef typename VecT<V>::S S;
+    extern __shared__ __align__(16) double2 tx_smem64[];
+    __shared__ TxCtx X;
+    __shared__ double s_red[4 * (TX_T / 32)], s_out[4];
+    __shared__ double s_par[4];       // sigma0^2, ln(fsamp/(2 n f_knee)), alpha, f_knee
+    V *b0 = reinterpret_cast<V *>(tx_smem64), *b1 = b0 + TX_TILE;
+    int cur = -1;
+    for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
+        const int2 w = a.items[a.item0 + it];
+        tx_begin(X, a.txl, a.q_tx, a.off, w.x, w.y, a.obase, a.ndet, a.fsamp, a.psd, nullptr, cur);
+        if (threadIdx.x == 0) {
+            const double sig0 = a.psd[3 * X.det], fk = a.psd[3 * X.det + 1], al = a.psd[3 * X.det + 2];
+            s_par[0] = sig0;
+            s_par[1] = log(a.fsamp / (2.0 * X.L.n * fk));
+            s_par[2] = al;
+            s_par[3] = fk;
+        }
+        __syncthreads();
+        const S sig0 = static_cast<S>(s_par[0]), lfs = static_cast<S>(s_par[1]), al = static_cast<S>(s_par[2]);
+        const S fk = static_cast<S>(s_par[3]);
+        const S s2 = sig0 * sig0;
+        const int n = X.L.n, m = X.L.m;
+        // sums: L, dL/dsigma0, dL/dfknee, dL/dalpha (FP64 per thread, as the
+        // FP64 path needs; the FP32 path adds FP32 terms into FP64)
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        auto mode_terms = [&](int k, S r) -> S {
+            // ln(f/fk) = ln k + ln(fsamp/(2 n fk)); P = s2 (1 + e^{alpha ln(f/fk)})
+            const S lr = log(static_cast<S>(k)) + lfs;
+            const S pw = exp(al * lr);
+            const S P = s2 * (S(1) + pw);
+            const S iP = S(1) / P;
+            const S r2P = r * r * iP;
+            acc[0] += 0.5 * (static_cast<double>(r2P) + static_cast<double>(log(P)));
+            const S h = S(0.5) * (iP - r2P * iP);             // 1/2 (1/P - r^2/P^2)
+            acc[1] += static_cast<double>(h * S(2) * P / sig0);
+            acc[2] += static_cast<double>(h * (-s2 * al * pw / fk));
+            acc[3] += static_cast<double>(h * s2 * pw * lr);
+            return r * iP;
+        };
+        row_pass<V, true>(X, b0, b1, a.Y, a.tw + X.L.twb, [](V *) {}, [&](int, int k, V Rv) {
+            const int ka = k, kb = (k == 0) ? m : n - k;
+            const S wa = ka == 0 ? S(0) : mode_terms(ka, Rv.x);
+            const S wb = mode_terms(kb, Rv.y);
+            return vmake<V>(ka == 0 ? S(0) : wa, wb);
+        });
+        block_sums_d<4>(acc, s_red, s_out);
+        if (threadIdx.x < 4) a.part[4 * static_cast<int64_t>(a.item0 + it) + threadIdx.x] = s_out[threadIdx.x];
+    }
+}
+
+template <class V>
+__global__ void __launch_bounds__(TX_T) k_chi2_colsinv(Chi2Tx<V> a)
+{
+    typedef typename VecT<V>::S S;
+    extern __shared__ __align__(16) double2 tx_smem64[];
+    __shared__ TxCtx X;
+    __shared__ double s_red[TX_T / 32], s_out[1];
+    V *b0 = reinterpret_cast<V *>(tx_smem64), *b1 = b0 + TX_TILE;
+    int cur = -1;
+    for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
+        const int2 w = a.items[a.item0 + it];
+        tx_begin(X, a.txl, a.q_tx, a.off, w.x, w.y, a.obase, a.ndet, a.fsamp, nullptr, nullptr, cur);
+        const int64_t o = X.o;
+        double acc[1] = {0.0};
+        col_inverse(X, b0, b1, a.Y, a.tw + X.L.twb, [&](int j1, int lc, int c, int j, int jm, const V *U) {
+            const ColGeo G(X.L, X.blk);
+            const bool ctr = j == jm;
+            const int64_t t = 4 * static_cast<int64_t>(j);
+            S sx[4];
+            ld4s<S>(a.s, o + t, ctr, sx);
+            const uint32_t fb = flag_bits(a.flags, o + t, ctr ? 2 : 4);
+            const V za = U[j1 * G.W + lc];
+            const V zb = ctr ? za : U[(G.m1 - 1 - j1) * G.W + G.lcol(G.m2 - 1 - c)];
+            S v[4] = {(fb & 1) ? S(0) : za.x, (fb & 2) ? S(0) : (ctr ? za.y : zb.y),
+                      (fb & 4) ? S(0) : za.y, (fb & 8) ? S(0) : zb.x};
+            const int cnt = ctr ? 2 : 4;
+            for (int u = 0; u < cnt; ++u) acc[0] -= static_cast<double>(sx[u] * v[u]);
+            if (a.v_out) {
+                S *vo = static_cast<S *>(a.v_out) + o + t;
+                for (int u = 0; u < cnt; ++u) vo[u] = v[u];
+            }
+        });
+        block_sums_d<1>(acc, s_red, s_out);
+        if (threadIdx.x == 0) a.part[4 * static_cast<int64_t>(a.item0 + it) + 1] = s_out[0];
+    }
+}
+
+// Per detscan: chi^2 and its PSD-parameter terms from the row items, the
+// gain derivative from the column items (item order).
+__global__ void __launch_bounds__(256) k_chi2_fin(const double *__restrict__ rpart, const double *__restrict__ cpart,
+                                                  const int32_t *__restrict__ row_off,
+                                                  const int32_t *__restrict__ col_off, int q0, int q1, int rbase,
+                                                  int cbase, double *chi2_q, double *dgain, double *dpsd_q)
+{
+    const int q = q0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= q1) return;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = row_off[q]; i < row_off[q + 1]; ++i)
+        for (int k = 0; k < 4; ++k) s[k] += rpart[4 * static_cast<int64_t>(i - rbase) + k];
+    double g = 0.0;
+    for (int i = col_off[q]; i < col_off[q + 1]; ++i) g += cpart[4 * static_cast<int64_t>(i - cbase) + 1];
+    chi2_q[q] = s[0];
+    dgain[q] = g;
+    for (int k = 0; k < 3; ++k) dpsd_q[3 * static_cast<int64_t>(q) + k] = s[k + 1];
+}
+
+// Band totals in detscan order (one thread): chi^2 and the PSD gradient of
+// every detector.
+__global__ void k_chi2_total(const double *__restrict__ chi2_q, const double *__restrict__ dpsd_q, int nq, int ndet,
+                             double *total, double *dpsd_det)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double t = 0.0;
+    for (int q = 0; q < nq; ++q) t += chi2_q[q];
+    total[0] = t;
+    for (int det = 0; det < ndet; ++det)
+        for (int k = 0; k < 3; ++k) {
+            double s = 0.0;
+            for (int q = det; q < nq; q += ndet) s += dpsd_q[3 * static_cast<int64_t>(q) + k];
+            dpsd_det[3 * det + k] = s;
+        }
+}
+
+// ===========================================================================
+// A5: correlated noise.  x0 = B^{-1} b with B = C^T diag(phi + 1/sigma0^2) C
+// is the draw of a gap-free detscan; flagged detscans then solve the Schur
+// complement S y = E^T x0, S = sigma0^2 I - E^T B^{-1} E
+// = E^T C^T diag(gamma) C E (E: flagged samples), by CG preconditioned with
+// the exact inverse of each gap's Toeplitz block, and x = x0 + B^{-1} E y
+// (Woodbury): x = A^{-1} b, A = B - E E^T / sigma0^2.  A detscan with every
+// sample flagged has A = C^T diag(phi) C: x is its exact spectral solution
+// (the offset mode, unconstrained, set to zero).
+//
+// One cooperative launch: phases separated by grid barriers.
+// ===========================================================================
+struct NcorrTx {
+    const float *d, *s;
+    const double *gain;
+    const uint32_t *flags;
+    const double *psd;
+    const int64_t *off;
+    const TxLen *txl;
+    const int32_t *q_tx;
+    const float2 *tw;
+    const int2 *colitems, *rowitems;
+    const int32_t *col_off, *row_off;
+    int q0, q1;                   // detscan range of this launch
+    int ndet;
+    double fsamp;
+    tod_rng rng;
+    int mode;
+    float tol;
+    int maxit;
+    float *x_out;
+    int32_t *iters;
+    int32_t *status;
+    float *spec_out;
+    const float *xtab;            // Toeplitz inverses' first columns per detector (null: no preconditioner)
+    const int32_t *lvalid;
+    // scratch
+    float2 *Y;                    // launch-range intermediate
+    int64_t *wpre;                // [range words + 1]
+    int64_t *chunk;               // [gridDim + 1]
+    CgState *cgs;                 // [nq]
+    int2 *gblk;                   // [nq][TX_GBMAX]
+    int32_t *gnb;                 // [nq]
+    float *cgv;                   // [5][cgcap]
+    int64_t cgcap;
+    int32_t *count;               // [2]
+};
+
+struct CgVec { float *y, *r, *p, *q, *z; };
+__device__ __forceinline__ CgVec cg_vecs(const NcorrTx &a) {
+    CgVec v;
+    v.y = a.cgv; v.r = v.y + a.cgcap; v.p = v.r + a.cgcap; v.q = v.p + a.cgcap; v.z = v.q + a.cgcap;
+    return v;
+}
+
+// flagged samples of the launch range before sample t (global index)
+__device__ __forceinline__ int64_t flag_rank(const uint32_t *__restrict__ fl, const int64_t *__restrict__ wpre,
+                                             int64_t w_lo, int64_t obase, int64_t t) {
+    const int64_t w = t >> 5;
+    uint32_t bits = __ldg(fl + w) & ((1u << (t & 31)) - 1u);
+    if (w == w_lo) bits &= ~((1u << (obase & 31)) - 1u);
+    return wpre[w - w_lo] + __popc(bits);
+}
+
+// Shared memory of the n_corr kernel besides the tiles.
+struct NcShared {
+    TxCtx X;
+    double red[4 * (TX_T / 32)];
+    double out[4];
+    int3 scan[TX_T / 32 + 1];
+    int gbeg[TX_GBMAX], gend[TX_GBMAX];
+    int blen[TX_GBMAX], brank[TX_GBMAX], boff[TX_GBMAX], bq[TX_GBMAX];
+    int rnd[TX_GBMAX + 1];
+    int nrnd, nb;
+    int64_t i64[2];
+    double d64[4];
+    int flag;
+};
+
+// Exclusive scan of one int3 per thread over the CTA; total gets the sum.
+__device__ int3 cta_exscan3(int3 v, int3 *s_w, int3 &total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int3 inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int x = __shfl_up_sync(0xffffffffu, inc.x, d);
+        const int y = __shfl_up_sync(0xffffffffu, inc.y, d);
+        const int z = __shfl_up_sync(0xffffffffu, inc.z, d);
+        if (lane >= d) { inc.x += x; inc.y += y; inc.z += z; }
+    }
+    if (lane == 31) s_w[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        constexpr int NW = TX_T / 32;
+        const int3 w = lane < NW ? s_w[lane] : make_int3(0, 0, 0);
+        int3 wi = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, wi.x, d);
+            const int y = __shfl_up_sync(0xffffffffu, wi.y, d);
+            const int z = __shfl_up_sync(0xffffffffu, wi.z, d);
+            if (lane >= d) { wi.x += x; wi.y += y; wi.z += z; }
+        }
+        __syncwarp();
+        if (lane < NW) s_w[lane] = make_int3(wi.x - w.x, wi.y - w.y, wi.z - w.z);
+        if (lane == NW - 1) s_w[NW] = wi;
+    }
+    __syncthreads();
+    const int3 b = s_w[warp];
+    total = s_w[TX_T / 32];
+    __syncthreads();
+    return make_int3(b.x + inc.x - v.x, b.y + inc.y - v.y, b.z + inc.z - v.z);
+}
+
+// Phase 1: flagged-sample prefix over the range's flag words, in chunks of
+// words per CTA, with grid barriers between count, chunk scan and write.
+__device__ void nc_flag_prefix(const NcorrTx &a, NcShared &S, cgrp::grid_group &grid)
+{
+    const int64_t obase = a.off[a.q0], oend = a.off[a.q1];
+    const int64_t w_lo = obase >> 5, w_hi = (oend + 31) >> 5;
+    const int64_t nw = w_hi - w_lo;
+    const int G = gridDim.x;
+    const int64_t cw = (nw + G - 1) / G;
+    const int64_t c0 = min(nw, blockIdx.x * cw), c1 = min(nw, c0 + cw);
+    const int64_t per = (c1 - c0 + TX_T - 1) / TX_T;
+    auto word = [&](int64_t i) -> uint32_t {     // word w_lo + i restricted to the range
+        const int64_t w = w_lo + i;
+        uint32_t b = __ldg(a.flags + w);
+        const int64_t base = w << 5;
+        if (base < obase) b &= ~0u << static_cast<int>(obase - base);
+        if (base + 32 > oend) b &= (oend - base >= 32) ? ~0u : ((1u << static_cast<int>(oend - base)) - 1u);
+        return b;
+    };
+    int mine = 0;
+    const int64_t t0 = c0 + threadIdx.x * per;
+    for (int64_t i = t0; i < min(c1, t0 + per); ++i) mine += __popc(word(i));
+    int3 tot3;
+    const int3 ex = cta_exscan3(make_int3(mine, 0, 0), S.scan, tot3);
+    if (threadIdx.x == 0) a.chunk[blockIdx.x] = tot3.x;
+    grid.sync();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int64_t acc = 0;
+        for (int c = 0; c < G; ++c) { const int64_t v = a.chunk[c]; a.chunk[c] = acc; acc += v; }
+        a.chunk[G] = acc;
+    }
+    grid.sync();
+    int64_t run = a.chunk[blockIdx.x] + ex.x;
+    for (int64_t i = t0; i < min(c1, t0 + per); ++i) {
+        a.wpre[i] = run;
+        run += __popc(word(i));
+    }
+    if (blockIdx.x == G - 1 && threadIdx.x == 0) a.wpre[nw] = a.chunk[G];
+}
+
+// Phase 2 (per detscan): flagged count and rank offset, CG mode, and the
+// gap blocks of the preconditioner (gaps split into blocks of at most lmax).
+__device__ void nc_detscan_index(const NcorrTx &a, NcShared &S, int q)
+{
+    const int64_t obase = a.off[a.q0];
+    const int64_t w_lo = obase >> 5;
+    const int64_t o = a.off[q], n = a.off[q + 1] - o;
+    const int det = q % a.ndet;
+    if (threadIdx.x == 0) {
+        const int64_t k0 = flag_rank(a.flags, a.wpre, w_lo, obase, o);
+        const int64_t k1 = (a.off[q + 1] == a.off[a.q1] && ((a.off[q + 1] & 31) == 0))
+                               ? a.wpre[((a.off[q + 1]) >> 5) - w_lo]
+                               : flag_rank(a.flags, a.wpre, w_lo, obase, a.off[q + 1]);
+        S.i64[0] = k0;
+        S.i64[1] = k1 - k0;
+    }
+    __syncthreads();
+    const int64_t koff = S.i64[0];
+    const int K = static_cast<int>(S.i64[1]);
+    // gaps: runs of flagged samples
+    const int64_t wb0 = o >> 5, wb1 = (o + n - 1) >> 5;
+    const int nw = static_cast<int>(wb1 - wb0 + 1);
+    const int per = (nw + TX_T - 1) / TX_T;
+    auto wbits = [&](int wi) -> uint32_t {
+        if (wi < 0 || wi >= nw) return 0u;
+        uint32_t bits = __ldg(a.flags + wb0 + wi);
+        const int64_t base = ((wb0 + wi) << 5) - o;
+        if (base < 0) bits &= ~0u << static_cast<int>(-base);
+        if (base + 32 > n) bits &= (n - base >= 32) ? ~0u : ((1u << static_cast<int>(n - base)) - 1u);
+        return bits;
+    };
+    int3 mine = make_int3(0, 0, 0);
+    for (int i = 0; i < per; ++i) {
+        const int wi = threadIdx.x * per + i;
+        if (wi >= nw) break;
+        const uint32_t bits = wbits(wi), prev = wbits(wi - 1) >> 31, next = wbits(wi + 1) & 1u;
+        mine.y += __popc(bits & ~((bits << 1) | prev));
+        mine.z += __popc(bits & ~((bits >> 1) | (next << 31)));
+    }
+    int3 tot3;
+    const int3 ex = cta_exscan3(mine, S.scan, tot3);
+    const int ngap = tot3.y;
+    if (ngap <= TX_GBMAX) {
+        int gpos = ex.y, epos = ex.z;
+        for (int i = 0; i < per; ++i) {
+            const int wi = threadIdx.x * per + i;
+            if (wi >= nw) break;
+            const uint32_t bits = wbits(wi), prev = wbits(wi - 1) >> 31, next = wbits(wi + 1) & 1u;
+            uint32_t st = bits & ~((bits << 1) | prev), en = bits & ~((bits >> 1) | (next << 31));
+            const int base = static_cast<int>(((wb0 + wi) << 5) - o);
+            while (st) { S.gbeg[gpos++] = base + __ffs(st) - 1; st &= st - 1; }
+            while (en) { S.gend[epos++] = base + __ffs(en); en &= en - 1; }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        CgState cs;
+        cs.rz = 0.0; cs.stop = 0.0; cs.koff = koff; cs.K = K; cs.it = 0; cs.pad = 0;
+        if (K == 0) cs.mode = CG_NONE;
+        else if (K == n) cs.mode = CG_ALLFLAG;
+        else if (koff + K > a.cgcap) cs.mode = CG_OVER;
+        else cs.mode = CG_ACTIVE;
+        a.cgs[q] = cs;
+        // preconditioner blocks (rank within the detscan, length)
+        int nb = 0;
+        const int lmax = (a.xtab && a.lvalid) ? min(TOEP_LMAX, a.lvalid[det]) : 0;
+        if (cs.mode == CG_ACTIVE && ngap <= TX_GBMAX && lmax >= 1) {
+            int rank = 0;
+            for (int g = 0; g < ngap && nb >= 0; ++g)
+                for (int b0 = S.gbeg[g]; b0 < S.gend[g]; b0 += lmax) {
+                    const int len = min(lmax, S.gend[g] - b0);
+                    if (nb >= TX_GBMAX) { nb = -1; break; }
+                    a.gblk[static_cast<int64_t>(q) * TX_GBMAX + nb] = make_int2(rank, len);
+                    ++nb;
+                    rank += len;
+                }
+        } else {
+            nb = -1;
+        }
+        a.gnb[q] = nb;
+    }
+}
+
+// Phase 3, column pass of the right-hand side: M (r/sigma0^2 + w1/sigma0),
+// r = d - g s; w1 of z_j is normal pair j of the NC_W1 stream (pair j mod 4
+// of Philox block j/4).
+__device__ void nc_rhs_cols(const NcorrTx &a, NcShared &S, float2 *b0, float2 *b1, uint64_t gi)
+{
+    const TxCtx &X = S.X;
+    const bool draw = a.mode == TOD_MODE_DRAW;
+    const float *dq = a.d + X.o, *sq = a.s + X.o;
+    const int64_t o = X.o;
+    const float g = X.g, inv_s2 = X.inv_s2, inv_s = X.inv_s;
+    const uint64_t q = static_cast<uint64_t>(X.q);
+    col_forward(X, b0, b1, a.Y, a.tw + X.L.twb,
+                [&](float2 *U) {
+                    // the tile's normals: one Philox block per thread, its four
+                    // pairs to the tile elements whose index j falls in it
+                    const ColGeo G(X.L, X.blk);
+                    if (!draw) {
+                        for (int e = threadIdx.x; e < G.m1 * G.W; e += TX_T) U[e] = make_float2(0.f, 0.f);
+                        return;
+                    }
+                    const int nbk = (G.np + 3) / 4 + 1;          // blocks touching a side's j range of a row
+                    const int total = G.m1 * 2 * nbk;
+                    for (int w = threadIdx.x; w < total; w += TX_T) {
+                        const int j1 = w / (2 * nbk), rest = w - j1 * 2 * nbk;
+                        const int side = rest / nbk, bi = rest - side * nbk;
+                        // j range of this row and side: [ja, jb)
+                        int ja, jb;
+                        if (side == 0) { ja = j1 * G.m2 + G.p0; jb = ja + G.np; }
+                        else { jb = j1 * G.m2 + G.m2 - G.p0; ja = jb - G.np; }
+                        const int bk = (ja >> 2) + bi;
+                        if (4 * bk >= jb) continue;
+                        const u64x4 rw = philox4x64(static_cast<uint64_t>(bk), q, 1, gi, a.rng.seed, a.rng.band);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int j = 4 * bk + u;
+                            if (j < ja || j >= jb) continue;
+                            const int c = j - j1 * G.m2;
+                            const int lc = side == 0 ? c - G.p0 : G.TP + (G.m2 - 1 - c - G.p0);
+                            if (G.col(lc) < 0) continue;      // the middle column's duplicate
+                            U[j1 * G.W + lc] = philox_normal_pair(rw, u);
+                        }
+                    }
+                },
+                [&](int j1, int lc, int c, int j, int jm, float2 *U) {
+                    const ColGeo G(X.L, X.blk);
+                    const bool ctr = j == jm;
+                    const int64_t t = 4 * static_cast<int64_t>(j);
+                    const float4 dv = ld4(dq, t, ctr), sv = ld4(sq, t, ctr);
+                    const uint32_t fb = flag_bits(a.flags, o + t, ctr ? 2 : 4);
+                    const int ea = j1 * G.W + lc;
+                    const float2 wa = U[ea];
+                    if (ctr) {
+                        U[ea] = make_float2((fb & 1) ? 0.f : fmaf(dv.x - g * sv.x, inv_s2, wa.x * inv_s),
+                                            (fb & 2) ? 0.f : fmaf(dv.y - g * sv.y, inv_s2, wa.y * inv_s));
+                        return;
+                    }
+                    const int eb = (G.m1 - 1 - j1) * G.W + G.lcol(G.m2 - 1 - c);
+                    const float2 wb = U[eb];
+                    // samples 4j, 4j+2 -> z_j = (v_{2j}, v_{2j+1}); 4j+3, 4j+1 -> z_{m-1-j}
+                    U[ea] = make_float2((fb & 1) ? 0.f : fmaf(dv.x - g * sv.x, inv_s2, wa.x * inv_s),
+                                        (fb & 4) ? 0.f : fmaf(dv.z - g * sv.z, inv_s2, wa.y * inv_s));
+                    U[eb] = make_float2((fb & 8) ? 0.f : fmaf(dv.w - g * sv.w, inv_s2, wb.x * inv_s),
+                                        (fb & 2) ? 0.f : fmaf(dv.y - g * sv.y, inv_s2, wb.y * inv_s));
+                });
+}
+
+// Filter weights of the packed slot pair: beta = 1/(phi + 1/sigma0^2) =
+// sigma0^2/(1 + r), gamma = sigma0^2 r/(1 + r) with r = sigma0^2 phi =
+// (f/f_knee)^-alpha (r = 0 at mode 0).  With every sample flagged beta is
+// 1/phi = sigma0^2 / r (0 at mode 0).
+__device__ __forceinline__ float nc_r(int k, const TxCtx &X) {
+    return k == 0 ? 0.f : tx_fpow(k, X.fscale, -X.alpha);
+}
+
+// Phase 3, row pass of the right-hand side: + sqrt(phi) w2 (mode pair k of
+// the NC_W2 stream), times beta; the spectrum beta (C b + prior term) is
+// written when asked for.
+__device__ void nc_rhs_rows(const NcorrTx &a, NcShared &S, float2 *b0, float2 *b1, uint64_t gi)
+{
+    const TxCtx &X = S.X;
+    const bool draw = a.mode == TOD_MODE_DRAW;
+    const bool allf = X.mode == CG_ALLFLAG;
+    const uint64_t q = static_cast<uint64_t>(X.q);
+    const float s2 = X.s2, inv_s2 = X.inv_s2;
+    const int n = X.L.n, m = X.L.m;
+    float *spec = a.spec_out ? a.spec_out + X.o : nullptr;
+    float2 *nu = nullptr;
+    row_pass<float2, true>(X, b0, b1, a.Y, a.tw + X.L.twb,
+        [&](float2 *Fr) {
+            nu = Fr;
+            const RowGeo G(X.L, X.blk);
+            const int npl = G.nr, m1 = G.m1, m2 = G.m2, p0 = G.r0;
+            if (!draw) {
+                for (int e = threadIdx.x; e < 2 * G.TR * G.m2p; e += TX_T) Fr[e] = make_float2(0.f, 0.f);
+                return;
+            }
+            // for a fixed k2 the even slots hold k = p0 + pl + m1 k2 and the
+            // odd ones k = m1 - p0 - pl + m1 k2: one Philox block per thread
+            // for up to four consecutive modes of a parity
+            const int nbk = (npl + 3) / 4 + 1;
+            const int items = 2 * nbk * m2;
+            for (int w = threadIdx.x; w < items; w += TX_T) {
+                const int rest = fdiv(w, X.L.f_m2), k2 = w - rest * m2;
+                const int par = rest / nbk, bi = rest - par * nbk;
+                const int kbase = (par == 0 ? p0 : m1 - p0 - (npl - 1)) + m1 * k2;
+                const int bk = (kbase >> 2) + bi;
+                if (npl <= 0 || 4 * bk >= kbase + npl) continue;
+                const u64x4 rw = philox4x64(static_cast<uint64_t>(bk), q, 2, gi, a.rng.seed, a.rng.band);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = 4 * bk + u;
+                    if (k < kbase || k >= kbase + npl) continue;
+                    const int pl = par == 0 ? k - kbase : (npl - 1) - (k - kbase);
+                    const int p = p0 + pl;
+                    const int e = (2 * pl + par) * G.m2p + k2;
+                    if (par == 1 && (p == 0 || m1 - p == p)) { Fr[e] = make_float2(0.f, 0.f); continue; }
+                    const int ka = k, kb = (k == 0) ? m : n - k;
+                    const float ra = nc_r(ka, X), rb = nc_r(kb, X);
+                    const float2 w2 = philox_normal_pair(rw, u);
+                    Fr[e] = make_float2(sqrtf(ra * inv_s2) * w2.x, sqrtf(rb * inv_s2) * w2.y);
+                }
+            }
+        },
+        [&](int e, int k, float2 Yv) {
+            const int ka = k, kb = (k == 0) ? m : n - k;
+            const float ra = nc_r(ka, X), rb = nc_r(kb, X);
+            float ba, bb;
+            if (allf) { ba = ka == 0 ? 0.f : s2 / ra; bb = s2 / rb; }
+            else { ba = s2 / (1.0f + ra); bb = s2 / (1.0f + rb); }
+            const float2 cb = make_float2(Yv.x + nu[e].x, Yv.y + nu[e].y);
+            const float2 xs = make_float2(cb.x * ba, cb.y * bb);
+            if (spec) { spec[ka] = xs.x; spec[kb] = xs.y; }
+            return xs;
+        });
+}
+
+// Phase 3, inverse column pass: x0 out; its flagged samples are the CG
+// right-hand side E^T x0.
+__device__ void nc_x0_cols(const NcorrTx &a, NcShared &S, float2 *b0, float2 *b1)
+{
+    const TxCtx &X = S.X;
+    const bool cg = X.mode == CG_ACTIVE;
+    float *xq = a.x_out + X.o;
+    const int64_t o = X.o, obase = a.off[a.q0], w_lo = obase >> 5;
+    float *r = a.cgv + a.cgcap;
+    col_inverse(X, b0, b1, a.Y, a.tw + X.L.twb, [&](int j1, int lc, int c, int j, int jm, const float2 *U) {
+        const ColGeo G(X.L, X.blk);
+        const bool ctr = j == jm;
+        const int64_t t = 4 * static_cast<int64_t>(j);
+        const float2 za = U[j1 * G.W + lc];
+        float v[4];
+        if (ctr) { v[0] = za.x; v[1] = za.y; }
+        else {
+            const float2 zb = U[(G.m1 - 1 - j1) * G.W + G.lcol(G.m2 - 1 - c)];
+            v[0] = za.x; v[1] = zb.y; v[2] = za.y; v[3] = zb.x;
+        }
+        const int cnt = ctr ? 2 : 4;
+        reinterpret_cast<float2 *>(xq + t)[0] = make_float2(v[0], v[1]);
+        if (!ctr) reinterpret_cast<float2 *>(xq + t + 2)[0] = make_float2(v[2], v[3]);
+        if (cg) {
+            uint32_t fb = flag_bits(a.flags, o + t, cnt);
+            while (fb) {
+                const int u = __ffs(fb) - 1;
+                fb &= fb - 1;
+                r[flag_rank(a.flags, a.wpre, w_lo, obase, o + t + u)] = v[u];
+            }
+        }
+    });
+}
+
+// CG column pass: z = E vec (the flagged samples' entries of vec, zero
+// elsewhere), forward columns.
+__device__ void nc_scatter_cols(const NcorrTx &a, NcShared &S, float2 *b0, float2 *b1, const float *vec)
+{
+    const TxCtx &X = S.X;
+    const int64_t o = X.o, obase = a.off[a.q0], w_lo = obase >> 5;
+    col_forward(X, b0, b1, a.Y, a.tw + X.L.twb, [](float2 *) {},
+                [&](int j1, int lc, int c, int j, int jm, float2 *U) {
+                    const ColGeo G(X.L, X.blk);
+                    const bool ctr = j == jm;
+                    const int64_t t = 4 * static_cast<int64_t>(j);
+                    const int cnt = ctr ? 2 : 4;
+                    uint32_t fb = flag_bits(a.flags, o + t, cnt);
+                    float v[4] = {0.f, 0.f, 0.f, 0.f};
+                    while (fb) {
+                        const int u = __ffs(fb) - 1;
+                        fb &= fb - 1;
+                        v[u] = vec[flag_rank(a.flags, a.wpre, w_lo, obase, o + t + u)];
+                    }
+                    if (ctr) { U[j1 * G.W + lc] = make_float2(v[0], v[1]); return; }
+                    U[j1 * G.W + lc] = make_float2(v[0], v[2]);
+                    U[(G.m1 - 1 - j1) * G.W + G.lcol(G.m2 - 1 - c)] = make_float2(v[3], v[1]);
+                });
+}
+
+// CG row pass: times gamma (apply S), or times beta (the final B^{-1} E y,
+// whose spectrum is added to the one written at the right-hand side).
+template <bool BETA>
+__device__ void nc_filter_rows(const NcorrTx &a, NcShared &S, float2 *b0, float2 *b1)
+{
+    const TxCtx &X = S.X;
+    const float s2 = X.s2;
+    const int n = X.L.n, m = X.L.m;
+    float *spec = (BETA && a.spec_out) ? a.spec_out + X.o : nullptr;
+    row_pass<float2, true>(X, b0, b1, a.Y, a.tw + X.L.twb, [](float2 *) {}, [&](int, int k, float2 Yv) {
+        const int ka = k, kb = (k == 0) ? m : n - k;
+        const float ra = nc_r(ka, X), rb = nc_r(kb, X);
+        float2 r;
+        if (BETA) {
+            r = make_float2(Yv.x * (s2 / (1.0f + ra)), Yv.y * (s2 / (1.0f + rb)));
+            if (spec) { spec[ka] += r.x; spec[kb] += r.y; }
+        } else {
+            r = make_float2(Yv.x * (s2 * ra / (1.0f + ra)), Yv.y * (s2 * rb / (1.0f + rb)));
+        }
+        return r;
+    });
+}
+
+// CG inverse column pass: q = E^T (...) (gather), or x += (...) (final).
+template <bool ADD>
+__device__ void nc_gather_cols(const NcorrTx &a, NcShared &S, float2 *b0, float2 *b1, float *qv)
+{
+    const TxCtx &X = S.X;
+    const int64_t o = X.o, obase = a.off[a.q0], w_lo = obase >> 5;
+    float *xq = a.x_out + X.o;
+    col_inverse(X, b0, b1, a.Y, a.tw + X.L.twb, [&](int j1, int lc, int c, int j, int jm, const float2 *U) {
+        const ColGeo G(X.L, X.blk);
+        const bool ctr = j == jm;
+        const int64_t t = 4 * static_cast<int64_t>(j);
+        const int cnt = ctr ? 2 : 4;
+        const float2 za = U[j1 * G.W + lc];
+        float v[4];
+        if (ctr) { v[0] = za.x; v[1] = za.y; }
+        else {
+            const float2 zb = U[(G.m1 - 1 - j1) * G.W + G.lcol(G.m2 - 1 - c)];
+            v[0] = za.x; v[1] = zb.y; v[2] = za.y; v[3] = zb.x;
+        }
+        if (ADD) {
+            float2 *p = reinterpret_cast<float2 *>(xq + t);
+            const float2 x01 = p[0];
+            p[0] = make_float2(x01.x + v[0], x01.y + v[1]);
+            if (!ctr) {
+                const float2 x23 = p[1];
+                p[1] = make_float2(x23.x + v[2], x23.y + v[3]);
+            }
+        } else {
+            uint32_t fb = flag_bits(a.flags, o + t, cnt);
+            while (fb) {
+                const int u = __ffs(fb) - 1;
+                fb &= fb - 1;
+                qv[flag_rank(a.flags, a.wpre, w_lo, obase, o + t + u)] = v[u];
+            }
+        }
+    });
+}
+
+// z = M^{-1} r over the detscan's gap blocks: T_L^{-1} = (L(x) L(x)^T -
+// L(w) L(w)^T) / x_0 (Gohberg-Semencul; x = T_L^{-1} e_1 from the Durbin
+// tables, w = (0, x_{L-1}, .., x_1)), blocks staged in rounds of at most
+// TX_GBCAP padded floats.  Returns r.z (CTA total, every thread).  gb: five
+// TX_GBCAP float arrays.
+__device__ double nc_precond(const NcorrTx &a, NcShared &S, int q, const float *r, float *z, float *gb)
+{
+    const int nb = a.gnb[q];
+    const CgState &cs = a.cgs[q];
+    const int K = cs.K;
+    Acc2 rz[1] = {{0.f, 0.f}};
+    if (nb < 0) {             // no preconditioner: z = r
+        for (int i = threadIdx.x; i < K; i += TX_T) {
+            const float v = r[i];
+            z[i] = v;
+            acc_add_prod(rz[0], v, v);
+        }
+        block_sums<1>(rz, S.red, S.out);
+        return S.out[0];
+    }
+    const int det = q % a.ndet;
+    const float *xt_det = a.xtab + static_cast<int64_t>(det) * (TOEP_LMAX * (TOEP_LMAX + 1) / 2);
+    if (threadIdx.x == 0) {
+        int nrnd = 0, len = 0, rq = 0;
+        for (int b = 0; b < nb; ++b) {
+            const int2 bl = a.gblk[static_cast<int64_t>(q) * TX_GBMAX + b];
+            const int reg = ((bl.y + 3) & ~3) + 16;
+            if (b == 0 || len + reg > TX_GBCAP) { S.rnd[nrnd++] = b; len = 0; rq = 0; }
+            S.brank[b] = bl.x; S.blen[b] = bl.y; S.boff[b] = len; S.bq[b] = rq;
+            len += reg;
+            rq += (bl.y + 3) >> 2;
+        }
+        S.rnd[nrnd] = nb;
+        S.nrnd = nrnd;
+    }
+    __syncthreads();
+    float *gb_r = gb, *gb_x = gb + TX_GBCAP, *gb_w = gb + 2 * TX_GBCAP;
+    float *gb_u1 = gb + 3 * TX_GBCAP, *gb_u2 = gb + 4 * TX_GBCAP;
+    for (int rd = 0; rd < S.nrnd; ++rd) {
+        const int b0 = S.rnd[rd], b1 = S.rnd[rd + 1];
+        const int Ll = S.blen[b1 - 1];
+        const int tot = S.boff[b1 - 1] + ((Ll + 3) & ~3) + 16;
+        const int totq = S.bq[b1 - 1] + ((Ll + 3) >> 2);
+        for (int f = threadIdx.x; f < tot; f += TX_T) {
+            int b = b0;
+            while (b + 1 < b1 && S.boff[b + 1] <= f) ++b;
+            const int L = S.blen[b], li = f - S.boff[b] - 8;
+            float rv = 0.f, xv = 0.f, wv = 0.f;
+            if (li >= 0 && li < L) {
+                const float *xt = xt_det + static_cast<int64_t>(L) * (L - 1) / 2;
+                rv = r[S.brank[b] + li];
+                xv = xt[li];
+                wv = li == 0 ? 0.f : xt[L - li];
+            }
+            gb_r[f] = rv; gb_x[f] = xv; gb_w[f] = wv; gb_u1[f] = 0.f; gb_u2[f] = 0.f;
+        }
+        __syncthreads();
+        // u1 = L(x)^T r, u2 = L(w)^T r: four outputs per group of QT threads
+        const int QT = (totq * 4 <= TX_T) ? 4 : (totq * 2 <= TX_T) ? 2 : 1;
+        const int qsh = QT == 4 ? 2 : QT == 2 ? 1 : 0;
+        const int totw = totq << qsh;
+        for (int t0 = 0; t0 < totw; t0 += TX_T) {
+            const int t = t0 + threadIdx.x;
+            const bool act = t < totw;
+            const int qi = t >> qsh, part = t & (QT - 1);
+            float4 a1 = make_float4(0.f, 0.f, 0.f, 0.f), a2 = a1;
+            int base = 0, i0 = 0;
+            if (act) {
+                int b = b0;
+                while (b + 1 < b1 && S.bq[b + 1] <= qi) ++b;
+                const int L = S.blen[b];
+                i0 = 4 * (qi - S.bq[b]);
+                base = S.boff[b] + 8;
+                const float *xb = gb_x + base, *wb = gb_w + base, *rb = gb_r + base + i0;
+                for (int k = 4 * part; k < L - i0; k += 4 * QT) {
+                    const float4 xk = *reinterpret_cast<const float4 *>(xb + k);
+                    const float4 wk = *reinterpret_cast<const float4 *>(wb + k);
+                    const float4 rc = *reinterpret_cast<const float4 *>(rb + k);
+                    const float4 rn = *reinterpret_cast<const float4 *>(rb + k + 4);
+                    a1.x = fmaf(xk.x, rc.x, fmaf(xk.y, rc.y, fmaf(xk.z, rc.z, fmaf(xk.w, rc.w, a1.x))));
+                    a1.y = fmaf(xk.x, rc.y, fmaf(xk.y, rc.z, fmaf(xk.z, rc.w, fmaf(xk.w, rn.x, a1.y))));
+                    a1.z = fmaf(xk.x, rc.z, fmaf(xk.y, rc.w, fmaf(xk.z, rn.x, fmaf(xk.w, rn.y, a1.z))));
+                    a1.w = fmaf(xk.x, rc.w, fmaf(xk.y, rn.x, fmaf(xk.z, rn.y, fmaf(xk.w, rn.z, a1.w))));
+                    a2.x = fmaf(wk.x, rc.x, fmaf(wk.y, rc.y, fmaf(wk.z, rc.z, fmaf(wk.w, rc.w, a2.x))));
+                    a2.y = fmaf(wk.x, rc.y, fmaf(wk.y, rc.z, fmaf(wk.z, rc.w, fmaf(wk.w, rn.x, a2.y))));
+                    a2.z = fmaf(wk.x, rc.z, fmaf(wk.y, rc.w, fmaf(wk.z, rn.x, fmaf(wk.w, rn.y, a2.z))));
+                    a2.w = fmaf(wk.x, rc.w, fmaf(wk.y, rn.x, fmaf(wk.z, rn.y, fmaf(wk.w, rn.z, a2.w))));
+                }
+            }
+            for (int ofs = 1; ofs < QT; ofs <<= 1) {
+                a1.x += __shfl_xor_sync(0xffffffffu, a1.x, ofs); a1.y += __shfl_xor_sync(0xffffffffu, a1.y, ofs);
+                a1.z += __shfl_xor_sync(0xffffffffu, a1.z, ofs); a1.w += __shfl_xor_sync(0xffffffffu, a1.w, ofs);
+                a2.x += __shfl_xor_sync(0xffffffffu, a2.x, ofs); a2.y += __shfl_xor_sync(0xffffffffu, a2.y, ofs);
+                a2.z += __shfl_xor_sync(0xffffffffu, a2.z, ofs); a2.w += __shfl_xor_sync(0xffffffffu, a2.w, ofs);
+            }
+            if (act && part == 0) {
+                *reinterpret_cast<float4 *>(gb_u1 + base + i0) = a1;
+                *reinterpret_cast<float4 *>(gb_u2 + base + i0) = a2;
+            }
+        }
+        __syncthreads();
+        // z = (L(x) u1 - L(w) u2) / x_0
+        for (int t0 = 0; t0 < totw; t0 += TX_T) {
+            const int t = t0 + threadIdx.x;
+            const bool act = t < totw;
+            const int qi = t >> qsh, part = t & (QT - 1);
+            float4 z1 = make_float4(0.f, 0.f, 0.f, 0.f), z2 = z1;
+            int b = b0, i0 = 0, L = 0, base = 0;
+            if (act) {
+                while (b + 1 < b1 && S.bq[b + 1] <= qi) ++b;
+                L = S.blen[b];
+                i0 = 4 * (qi - S.bq[b]);
+                base = S.boff[b] + 8;
+                const float *xb = gb_x + base, *wb = gb_w + base;
+                const float *u1b = gb_u1 + base + i0, *u2b = gb_u2 + base + i0;
+                for (int s0 = 4 * part; s0 <= i0; s0 += 4 * QT) {
+                    const float4 xs = *reinterpret_cast<const float4 *>(xb + s0);
+                    const float4 ws = *reinterpret_cast<const float4 *>(wb + s0);
+                    const float4 ua = *reinterpret_cast<const float4 *>(u1b - s0);
+                    const float4 va = *reinterpret_cast<const float4 *>(u2b - s0);
+                    const float4 ub = *reinterpret_cast<const float4 *>(u1b - s0 - 4);
+                    const float4 vb = *reinterpret_cast<const float4 *>(u2b - s0 - 4);
+                    z1.x = fmaf(xs.x, ua.x, fmaf(xs.y, ub.w, fmaf(xs.z, ub.z, fmaf(xs.w, ub.y, z1.x))));
+                    z1.y = fmaf(xs.x, ua.y, fmaf(xs.y, ua.x, fmaf(xs.z, ub.w, fmaf(xs.w, ub.z, z1.y))));
+                    z1.z = fmaf(xs.x, ua.z, fmaf(xs.y, ua.y, fmaf(xs.z, ua.x, fmaf(xs.w, ub.w, z1.z))));
+                    z1.w = fmaf(xs.x, ua.w, fmaf(xs.y, ua.z, fmaf(xs.z, ua.y, fmaf(xs.w, ua.x, z1.w))));
+                    z2.x = fmaf(ws.x, va.x, fmaf(ws.y, vb.w, fmaf(ws.z, vb.z, fmaf(ws.w, vb.y, z2.x))));
+                    z2.y = fmaf(ws.x, va.y, fmaf(ws.y, va.x, fmaf(ws.z, vb.w, fmaf(ws.w, vb.z, z2.y))));
+                    z2.z = fmaf(ws.x, va.z, fmaf(ws.y, va.y, fmaf(ws.z, va.x, fmaf(ws.w, vb.w, z2.z))));
+                    z2.w = fmaf(ws.x, va.w, fmaf(ws.y, va.z, fmaf(ws.z, va.y, fmaf(ws.w, va.x, z2.w))));
+                }
+            }
+            for (int ofs = 1; ofs < QT; ofs <<= 1) {
+                z1.x += __shfl_xor_sync(0xffffffffu, z1.x, ofs); z1.y += __shfl_xor_sync(0xffffffffu, z1.y, ofs);
+                z1.z += __shfl_xor_sync(0xffffffffu, z1.z, ofs); z1.w += __shfl_xor_sync(0xffffffffu, z1.w, ofs);
+                z2.x += __shfl_xor_sync(0xffffffffu, z2.x, ofs); z2.y += __shfl_xor_sync(0xffffffffu, z2.y, ofs);
+                z2.z += __shfl_xor_sync(0xffffffffu, z2.z, ofs); z2.w += __shfl_xor_sync(0xffffffffu, z2.w, ofs);
+            }
+            if (act && part == 0) {
+                const float inv = 1.0f / gb_x[base];
+                const float zz[4] = {z1.x - z2.x, z1.y - z2.y, z1.z - z2.z, z1.w - z2.w};
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj)
+                    if (i0 + jj < L) {
+                        const float zj = zz[jj] * inv;
+                        z[S.brank[b] + i0 + jj] = zj;
+                        acc_add_prod(rz[0], gb_r[base + i0 + jj], zj);
+                    }
+            }
+        }
+        __syncthreads();
+    }
+    block_sums<1>(rz, S.red, S.out);
+    return S.out[0];
+}
+
+// CG start of detscan q: r = E^T x0 (already gathered), y = 0, z = M^{-1} r,
+// p = z, (r.r, r.z); nothing to do when r = 0.
+__device__ void nc_cg_init(const NcorrTx &a, NcShared &S, int q, float *gb)
+{
+    CgState cs = a.cgs[q];
+    if (cs.mode != CG_ACTIVE) return;
+    const CgVec V = cg_vecs(a);
+    const int64_t k0 = cs.koff;
+    const int K = cs.K;
+    Acc2 rr[1] = {{0.f, 0.f}};
+    for (int i = threadIdx.x; i < K; i += TX_T) {
+        const float v = V.r[k0 + i];
+        V.y[k0 + i] = 0.f;
+        acc_add_prod(rr[0], v, v);
+    }
+    block_sums<1>(rr, S.red, S.out);
+    const double rr0 = S.out[0];
+    const double rz = nc_precond(a, S, q, V.r + k0, V.z + k0, gb);
+    for (int i = threadIdx.x; i < K; i += TX_T) V.p[k0 + i] = V.z[k0 + i];
+    if (threadIdx.x == 0) {
+        cs.rz = rz;
+        cs.stop = static_cast<double>(a.tol) * a.tol * rr0;
+        cs.it = 0;
+        if (rr0 == 0.0) cs.mode = CG_DONE;
+        a.cgs[q] = cs;
+        if (cs.mode == CG_ACTIVE) atomicAdd(a.count, 1);
+    }
+}
+
+// One CG iteration of detscan q after q = S p is gathered.
+__device__ void nc_cg_update(const NcorrTx &a, NcShared &S, int q, float *gb, int32_t *count_next)
+{
+    CgState cs = a.cgs[q];
+    if (cs.mode != CG_ACTIVE) return;
+    const CgVec V = cg_vecs(a);
+    const int64_t k0 = cs.koff;
+    const int K = cs.K;
+    Acc2 pq[1] = {{0.f, 0.f}};
+    for (int i = threadIdx.x; i < K; i += TX_T) acc_add_prod(pq[0], V.p[k0 + i], V.q[k0 + i]);
+    block_sums<1>(pq, S.red, S.out);
+    const float alp = static_cast<float>(cs.rz / S.out[0]);
+    Acc2 rr[1] = {{0.f, 0.f}};
+    for (int i = threadIdx.x; i < K; i += TX_T) {
+        V.y[k0 + i] = fmaf(alp, V.p[k0 + i], V.y[k0 + i]);
+        const float rn = fmaf(-alp, V.q[k0 + i], V.r[k0 + i]);
+        V.r[k0 + i] = rn;
+        acc_add_prod(rr[0], rn, rn);
+    }
+    block_sums<1>(rr, S.red, S.out);
+    const double rrn = S.out[0];
+    ++cs.it;
+    bool cont = true;
+    if (rrn <= cs.stop) { cs.mode = CG_DONE; cont = false; }
+    else if (cs.it >= a.maxit || !(rrn == rrn)) {
+        cs.mode = CG_DONE;
+        cont = false;
+        if (threadIdx.x == 0) set_status(a.status, q, TOD_ERR_NOT_CONVERGED);
+    }
+    if (cont) {
+        const double rzn = nc_precond(a, S, q, V.r + k0, V.z + k0, gb);
+        const float beta = static_cast<float>(rzn / cs.rz);
+        for (int i = threadIdx.x; i < K; i += TX_T) V.p[k0 + i] = fmaf(beta, V.p[k0 + i], V.z[k0 + i]);
+        cs.rz = rzn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a.cgs[q] = cs;
+        if (cs.mode == CG_ACTIVE) atomicAdd(count_next, 1);
+    }
+}
+
+// Loop over the launch's column or row items, skipping detscans that fn
+// should not visit (keep(mode)).
+template <class Keep, class Fn>
+__device__ __forceinline__ void nc_items(const NcorrTx &a, NcShared &S, bool rows, uint64_t, int &cur, Keep keep,
+                                         Fn fn)
+{
+    const int2 *items = rows ? a.rowitems : a.colitems;
+    const int i0 = rows ? a.row_off[a.q0] : a.col_off[a.q0];
+    const int i1 = rows ? a.row_off[a.q1] : a.col_off[a.q1];
+    for (int it = i0 + blockIdx.x; it < i1; it += gridDim.x) {
+        const int2 w = items[it];
+        const int md = a.cgs[w.x].mode;
+        if (!keep(md)) continue;
+        tx_begin(S.X, a.txl, a.q_tx, a.off, w.x, w.y, a.off[a.q0], a.ndet, a.fsamp, a.psd, a.gain, cur);
+        if (threadIdx.x == 0) { S.X.mode = md; S.X.koff = a.cgs[w.x].koff; }
+        __syncthreads();
+        fn();
+    }
+}
+
+__global__ void __launch_bounds__(TX_T, 2) k_ncorr_tx(NcorrTx a)
+{
+    extern __shared__ __align__(16) float2 tx_smem[];
+    __shared__ NcShared S;
+    cgrp::grid_group grid = cgrp::this_grid();
+    float2 *b0 = tx_smem, *b1 = tx_smem + TX_TILE;
+    float *gb = reinterpret_cast<float *>(tx_smem);
+    const uint64_t gi = a.rng.gibbs_iter_dev ? *a.rng.gibbs_iter_dev : a.rng.gibbs_iter;
+    int cur = -1;
+    // 1. flag index
+    nc_flag_prefix(a, S, grid);
+    if (blockIdx.x == 0 && threadIdx.x == 0) { a.count[0] = 0; a.count[1] = 0; }
+    grid.sync();
+    for (int q = a.q0 + blockIdx.x; q < a.q1; q += gridDim.x) {
+        nc_detscan_index(a, S, q);
+        __syncthreads();
+    }
+    grid.sync();
+    // 2. x0 = B^{-1} b
+    auto all = [](int) { return true; };
+    nc_items(a, S, false, gi, cur, all, [&] { nc_rhs_cols(a, S, b0, b1, gi); });
+    grid.sync();
+    nc_items(a, S, true, gi, cur, all, [&] { nc_rhs_rows(a, S, b0, b1, gi); });
+    grid.sync();
+    nc_items(a, S, false, gi, cur, all, [&] { nc_x0_cols(a, S, b0, b1); });
+    grid.sync();
+    // 3. CG on the Schur complement
+    for (int q = a.q0 + blockIdx.x; q < a.q1; q += gridDim.x) {
+        __syncthreads();
+        nc_cg_init(a, S, q, gb);
+    }
+    grid.sync();
+    const CgVec V = cg_vecs(a);
+    auto active = [](int md) { return md == CG_ACTIVE; };
+    int par = 0;
+    for (;;) {
+        if (*reinterpret_cast<volatile int32_t *>(a.count + par) == 0) break;
+        nc_items(a, S, false, gi, cur, active, [&] { nc_scatter_cols(a, S, b0, b1, V.p); });
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.count[par ^ 1] = 0;
+        grid.sync();
+        nc_items(a, S, true, gi, cur, active, [&] { nc_filter_rows<false>(a, S, b0, b1); });
+        grid.sync();
+        nc_items(a, S, false, gi, cur, active, [&] { nc_gather_cols<false>(a, S, b0, b1, V.q); });
+        grid.sync();
+        for (int q = a.q0 + blockIdx.x; q < a.q1; q += gridDim.x) {
+            __syncthreads();
+            nc_cg_update(a, S, q, gb, a.count + (par ^ 1));
+        }
+        grid.sync();
+        par ^= 1;
+    }
+    // 4. x = x0 + B^{-1} E y for every detscan that ran the CG
+    auto ran = [](int md) { return md == CG_DONE; };
+    nc_items(a, S, false, gi, cur, ran, [&] { nc_scatter_cols(a, S, b0, b1, V.y); });
+    grid.sync();
+    nc_items(a, S, true, gi, cur, ran, [&] { nc_filter_rows<true>(a, S, b0, b1); });
+    grid.sync();
+    nc_items(a, S, false, gi, cur, ran, [&] { nc_gather_cols<true>(a, S, b0, b1, nullptr); });
+    // iteration counts and the detscans left at x0
+    for (int q = a.q0 + blockIdx.x * TX_T + threadIdx.x; q < a.q1; q += gridDim.x * TX_T) {
+        const CgState cs = a.cgs[q];
+        if (a.iters) a.iters[q] = cs.it;
+        if (cs.mode == CG_OVER) set_status(a.status, q, TOD_ERR_NOT_CONVERGED);
+    }
+}
+
+// ===========================================================================
+// launchers
+// ===========================================================================
+static size_t tx_smem_bytes(bool fp64) { return (fp64 ? sizeof(double2) : sizeof(float2)) * 2 * TX_TILE; }
+
+cudaError_t setup_tx_kernels(Plan &p)
+{
+    cudaError_t e;
+    const size_t s32 = tx_smem_bytes(false), s64 = tx_smem_bytes(true);
+    if ((e = cudaFuncSetAttribute(k_gain_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32))) return e;
+    if ((e = cudaFuncSetAttribute(k_gain_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32))) return e;
+    if ((e = cudaFuncSetAttribute(k_gain_colsinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32))) return e;
+    if ((e = cudaFuncSetAttribute(k_ncorr_tx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32))) return e;
+    if ((e = cudaFuncSetAttribute(k_chi2_cols<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_chi2_rows<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_chi2_colsinv<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_chi2_cols<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_chi2_rows<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_chi2_colsinv<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64)))
+        return e;
+    int dev = 0, nsm = 0, per = 0;
+    if ((e = cudaGetDevice(&dev))) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev))) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ncorr_tx, TX_T, s32))) return e;
+    p.coop_grid = std::max(1, per) * nsm;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gain_rows, TX_T, s32))) return e;
+    p.pass_grid = std::max(1, per) * nsm;
+    return cudaSuccess;
+}
+
+static int grid_for(const Plan &p, int nitems) { return std::max(1, std::min(nitems, p.pass_grid)); }
+
+cudaError_t launch_tx_gain(const Plan &p, const float *d, const float *s, const uint32_t *flags, const double *psd,
+                           tod_rng rng, int mode, double *g, double *mu, double *sig, cudaStream_t st, int q0, int q1)
+{
+    if (q1 <= q0) return cudaSuccess;
+    GainTx a = {};
+    a.d = d; a.s = s; a.flags = flags; a.psd = psd; a.off = p.off; a.txl = p.txl; a.q_tx = p.q_tx; a.tw = p.txtw;
+    a.ndet = p.ndet; a.fsamp = p.fsamp; a.obase = p.h_off[q0]; a.Y = p.ybuf; a.part = p.part;
+    const int c0 = p.h_col_off[q0], c1 = p.h_col_off[q1], r0 = p.h_row_off[q0], r1 = p.h_row_off[q1];
+    const size_t sm = tx_smem_bytes(false);
+    // column items' partials at part[c], row items' at part[ncol + r]
+    a.items = p.colitems; a.item0 = c0; a.nitems = c1 - c0;
+    k_gain_cols<<<grid_for(p, a.nitems), TX_T, sm, st>>>(a);
+    a.items = p.rowitems; a.item0 = r0; a.nitems = r1 - r0;
+    double *cpart = p.part;
+    double *rpart = p.part + 4 * static_cast<int64_t>(p.h_col_off[p.nq] - 0);
+    a.part = rpart - 4 * static_cast<int64_t>(0);
+    k_gain_rows<<<grid_for(p, a.nitems), TX_T, sm, st>>>(a);
+    a.items = p.colitems; a.item0 = c0; a.nitems = c1 - c0; a.part = cpart;
+    k_gain_colsinv<<<grid_for(p, a.nitems), TX_T, sm, st>>>(a);
+    const int nq = q1 - q0;
+    k_gain_fin<<<(nq + 255) / 256, 256, 0, st>>>(rpart, cpart, p.row_off, p.col_off, q0, q1, 0, 0, rng, mode, g, mu,
+                                                  sig, p.status);
+    return cudaGetLastError();
+}
+
+template <class V>
+static cudaError_t chi2_range(const Plan &p, const float *d, const void *s, const double *gain,
+                              const uint32_t *flags, const double *psd, double *chi2_q, double *dgain, double *dpsd_q,
+                              void *v_out, cudaStream_t st, int q0, int q1)
+{
+    Chi2Tx<V> a = {};
+    a.d = d; a.s = s; a.gain = gain; a.flags = flags; a.psd = psd; a.off = p.off; a.txl = p.txl; a.q_tx = p.q_tx;
+    a.tw = reinterpret_cast<const V *>(sizeof(V) == sizeof(float2) ? static_cast<const void *>(p.txtw)
+                                                                     : static_cast<const void *>(p.txtw64));
+    a.ndet = p.ndet; a.fsamp = p.fsamp; a.obase = p.h_off[q0];
+    a.Y = reinterpret_cast<V *>(p.ybuf);
+    a.v_out = v_out;
+    const size_t sm = tx_smem_bytes(sizeof(V) != sizeof(float2));
+    const int c0 = p.h_col_off[q0], c1 = p.h_col_off[q1], r0 = p.h_row_off[q0], r1 = p.h_row_off[q1];
+    double *cpart = p.part;
+    double *rpart = p.part + 4 * static_cast<int64_t>(p.h_col_off[p.nq]);
+    a.items = p.colitems; a.item0 = c0; a.nitems = c1 - c0; a.part = cpart;
+    k_chi2_cols<V><<<grid_for(p, a.nitems), TX_T, sm, st>>>(a);
+    a.items = p.rowitems; a.item0 = r0; a.nitems = r1 - r0; a.part = rpart;
+    k_chi2_rows<V><<<grid_for(p, a.nitems), TX_T, sm, st>>>(a);
+    a.items = p.colitems; a.item0 = c0; a.nitems = c1 - c0; a.part = cpart;
+    k_chi2_colsinv<V><<<grid_for(p, a.nitems), TX_T, sm, st>>>(a);
+    k_chi2_fin<<<(q1 - q0 + 255) / 256, 256, 0, st>>>(rpart, cpart, p.row_off, p.col_off, q0, q1, 0, 0, chi2_q, dgain,
+                                                       dpsd_q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tx_chi2(const Plan &p, bool fp64, const float *d, const void *s, const double *gain,
+                           const uint32_t *flags, const double *psd, double *chi2_q, double *dgain, double *dpsd_q,
+                           double *total, double *dpsd_det, void *v_out, cudaStream_t st)
+{
+    cudaError_t e = cudaSuccess;
+    if (!fp64) {
+        e = chi2_range<float2>(p, d, s, gain, flags, psd, chi2_q, dgain, dpsd_q, v_out, st, 0, p.nq);
+    } else {
+        // the intermediate holds ybuf_floats / 4 double2: waves of detscans of
+        // at most ybuf_floats / 2 samples (a whole detscan always fits)
+        int q = 0;
+        while (q < p.nq && e == cudaSuccess) {
+            int q1 = q + 1;
+            while (q1 < p.nq && p.h_off[q1 + 1] - p.h_off[q] <= p.ybuf_floats / 2) ++q1;
+            e = chi2_range<double2>(p, d, s, gain, flags, psd, chi2_q, dgain, dpsd_q, v_out, st, q, q1);
+            q = q1;
+        }
+    }
+    if (e != cudaSuccess) return e;
+    k_chi2_total<<<1, 1, 0, st>>>(chi2_q, dpsd_q, p.nq, p.ndet, total, dpsd_det);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tx_ncorr(const Plan &p, const float *d, const float *s, const double *gain,
+                            const uint32_t *flags, const double *psd, tod_rng rng, int mode, float tol, int maxit,
+                            float *x, int32_t *iters, cudaStream_t st, int q0, int q1, const TxNcorrScratch &sc,
+                            int grid)
+{
+    if (q1 <= q0) return cudaSuccess;
+    NcorrTx a = {};
+    a.d = d; a.s = s; a.gain = gain; a.flags = flags; a.psd = psd; a.off = p.off; a.txl = p.txl; a.q_tx = p.q_tx;
+    a.tw = p.txtw; a.colitems = p.colitems; a.rowitems = p.rowitems; a.col_off = p.col_off; a.row_off = p.row_off;
+    a.q0 = q0; a.q1 = q1; a.ndet = p.ndet; a.fsamp = p.fsamp; a.rng = rng; a.mode = mode; a.tol = tol;
+    a.maxit = maxit; a.x_out = x; a.iters = iters; a.status = p.status; a.spec_out = p.spec_out;
+    a.xtab = p.use_prec ? p.xtab : nullptr; a.lvalid = p.lvalid;
+    a.Y = sc.Y; a.wpre = sc.wpre; a.chunk = p.chunk; a.cgs = p.cgs; a.gblk = p.gblk; a.gnb = p.gnb;
+    a.cgv = sc.cgv; a.cgcap = sc.cgcap; a.count = p.cg_count;
+    void *args[] = {&a};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_ncorr_tx), dim3(grid), dim3(TX_T), args,
+                                       tx_smem_bytes(false), st);
+}
+
+}  // namespace tg

@@ -323,6 +323,69 @@ def make_band(cfg: BandConfig, with_noise: bool = True, threads: int | None = No
                 pix=pix, psi=psi, flags=fl, tod=tod)
 
 
+@dataclasses.dataclass
+class BandArrays:
+    """A band generated straight into concatenated arrays: detscan q owns
+    samples [offsets[q], offsets[q+1]), the first kept[q] samples of its raw
+    timeline (the caller chooses kept; the values are those of make_band)."""
+    cfg: BandConfig
+    npix: int
+    map_tqu: np.ndarray          # float64 (3, npix)
+    scan_len: np.ndarray         # raw samples per scan
+    gain: np.ndarray             # float64[ndetscan]
+    psd: np.ndarray              # float64[ndet, 3]
+    offsets: np.ndarray          # int64[ndetscan + 1]
+    pix: np.ndarray              # int32[N]
+    psi: np.ndarray              # uint16[N]
+    flags: np.ndarray            # bool[N] (True = flagged)
+    tod: np.ndarray              # float32[N]
+
+
+def make_band_arrays(cfg: BandConfig, kept_per_scan, with_noise: bool = True,
+                     threads: int | None = None, scans=None) -> BandArrays:
+    """Generate every input of one band (or of the listed scans only), each
+    detscan at its raw length as make_band does and truncated to
+    kept_per_scan[scan] samples, written into concatenated arrays: the
+    whole band never exists as per-detscan lists, so bands of billions of
+    samples fit in host memory."""
+    npix = nside2npix(cfg.nside)
+    m = sky_map(cfg)
+    L = raw_lengths(cfg)
+    gn = gains(cfg)
+    psd = noise_params(cfg)
+    scans = list(range(cfg.nscan)) if scans is None else list(scans)
+    kept = np.asarray(kept_per_scan, dtype=np.int64)
+    qs = [(sc, d) for sc in scans for d in range(cfg.ndet)]
+    nlen = np.array([kept[sc] for sc, _ in qs], dtype=np.int64)
+    off = np.zeros(len(qs) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(nlen)
+    N = int(off[-1])
+    pix = np.empty(N, np.int32)
+    psi = np.empty(N, np.uint16)
+    fl = np.empty(N, bool)
+    tod = np.empty(N, np.float32)
+    threads = threads or min(32, os.cpu_count() or 1)
+
+    def work(i):
+        sc, d = qs[i]
+        _, a, b, c, e = _make_detscan(cfg, m, gn, psd, sc, d, int(L[sc]), with_noise)
+        k = int(nlen[i])
+        o = int(off[i])
+        pix[o:o + k] = a[:k]
+        psi[o:o + k] = b[:k]
+        fl[o:o + k] = c[:k]
+        tod[o:o + k] = e[:k]
+
+    if threads > 1 and len(qs) > 1:
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(work, range(len(qs))))
+    else:
+        for i in range(len(qs)):
+            work(i)
+    return BandArrays(cfg=cfg, npix=npix, map_tqu=m, scan_len=L, gain=gn, psd=psd, offsets=off,
+                      pix=pix, psi=psi, flags=fl, tod=tod)
+
+
 # ----------------------------------------------------------------------------
 # integer data streams: ADC counts and quality-flag words (paper Sect. 4.1
 # stores the TOD and the flags as integers that are differenced and Huffman

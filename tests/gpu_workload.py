@@ -9,7 +9,7 @@ import synth
 
 
 class Workload:
-    def __init__(self, cfg, cluster_size=0, with_noise=True, max_radix=0):
+    def __init__(self, cfg, tile_pairs=0, with_noise=True, max_radix=0):
         import torch
         self.cfg = cfg
         self.band = synth.make_band(cfg, with_noise=with_noise)
@@ -18,7 +18,7 @@ class Workload:
         self.nq = len(self.off) - 1
         self.N = int(self.off[-1])
         self.plan = tg.Plan(cfg.nside, cfg.ndet, cfg.nscan, cfg.fsamp, self.off,
-                            self.ing["pix_streams"], self.ing["psi_streams"], cluster_size=cluster_size,
+                            self.ing["pix_streams"], self.ing["psi_streams"], tile_pairs=tile_pairs,
                             max_radix=max_radix)
         dev = torch.device("cuda:0")
         self.dev = dev

@@ -17,13 +17,13 @@ def test_autotune_picks_a_measured_candidate():
     m4 = np.zeros((band.npix, 4), np.float32)
     m4[:, :3] = band.map_tqu.T
     map_in = torch.from_numpy(m4).cuda()
-    cands = [(4, 16), (8, 8), (8, 16), (9, 16)]
+    cands = [(0, 16), (4, 8), (8, 16), (3, 16)]
     c, r, t = autotune(cfg.nside, cfg.ndet, cfg.nscan, cfg.fsamp, ing["offsets"], ing["pix_streams"],
                        ing["psi_streams"], ing["tod"], ing["flag_words"], band.psd, map_in,
                        candidates=cands, nscan_sample=4, reps=2)
     assert (c, r) in t and set(t) <= set(cands) and len(t) >= 3
     assert t[(c, r)] == min(t.values())
     plan = tg.Plan(cfg.nside, cfg.ndet, cfg.nscan, cfg.fsamp, ing["offsets"], ing["pix_streams"],
-                   ing["psi_streams"], cluster_size=c, max_radix=r)
-    assert plan.info()["cluster_size"] == c
+                   ing["psi_streams"], tile_pairs=c, max_radix=r)
+    assert plan.info()["tile_pairs"] == c
     plan.close()

@@ -26,7 +26,7 @@ def tiny():
     from gpu_workload import Workload
     cfg = synth.CONFIGS["tiny"]
     assert cfg.flag_frac == 0.0
-    return Workload(cfg, cluster_size=0)
+    return Workload(cfg, tile_pairs=0)
 
 
 @pytest.mark.gpu
@@ -138,7 +138,7 @@ def test_prepared_ncorr_matches_sample_ncorr():
     from gpu_workload import Workload
     cfg = synth.scaled(synth.CONFIGS["lfi30"], nscan=2, len_lo=9000, len_hi=30000)
     assert cfg.flag_frac > 0
-    wl = Workload(cfg, cluster_size=0)
+    wl = Workload(cfg, tile_pairs=0)
     gains = torch.from_numpy(synth.gains(cfg)[:wl.nq].astype(np.float64)).to(wl.dev)
     outs = []
     for prepared in (False, True):

@@ -149,7 +149,7 @@ def test_step_with_the_smooth_prior():
     import paper_2201_03509_gb300 as tg
     from paper_2201_03509_gb300.step import GibbsTODStep
     from gpu_workload import Workload
-    wl = Workload(synth.CONFIGS["tiny"], cluster_size=2)
+    wl = Workload(synth.CONFIGS["tiny"], tile_pairs=2)
     prior = np.array([[2e-3, -2.0]])
     st = GibbsTODStep(wl.plan, wl.band.psd, wl.ing["flag_words"], gain_prior=prior)
     st.set_tod(wl.d32)

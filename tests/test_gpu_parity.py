@@ -14,12 +14,15 @@ SEED, BAND, IT = 777, 3, 5
 
 
 def _cfgs():
+    """(band, column pairs per tile (0: the plan's choice), largest radix,
+    per-scan schedule): several tiles per detscan and ragged last tiles."""
     tiny = synth.CONFIGS["tiny"]
     # a few LFI-30-like detscans, short enough for the oracle, with flags
     l30 = synth.scaled(synth.CONFIGS["lfi30"], nscan=3, len_lo=9000, len_hi=30000)
-    return {"tiny_c1": (tiny, 1), "tiny_c4": (tiny, 4), "tiny_c3": (tiny, 3), "lfi30_small_c2": (l30, 2),
-            "lfi30_small_c8": (l30, 8), "lfi30_small_c9": (l30, 9), "lfi30_small_auto": (l30, 0),
-            "lfi30_small_c9_r8": (l30, 9, 8), "tiny_c2_r4": (tiny, 2, 4)}
+    return {"tiny_t1": (tiny, 1), "tiny_t4": (tiny, 4), "tiny_t3": (tiny, 3), "lfi30_small_t2": (l30, 2),
+            "lfi30_small_t5": (l30, 5), "lfi30_small_t9": (l30, 9), "lfi30_small_auto": (l30, 0),
+            "lfi30_small_t9_r8": (l30, 9, 8), "tiny_t2_r4": (tiny, 2, 4),
+            "lfi30_small_perscan": (l30, 0, 0, True), "tiny_perscan_t3": (tiny, 3, 0, True)}
 
 
 @pytest.fixture(scope="module", params=list(_cfgs().keys()))
@@ -28,8 +31,12 @@ def wl(request):
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     from gpu_workload import Workload
-    cfg, cs, *rmax = _cfgs()[request.param]
-    return Workload(cfg, cluster_size=cs, max_radix=rmax[0] if rmax else 0)
+    cfg, tp, *rest = _cfgs()[request.param]
+    rmax = rest[0] if rest else 0
+    w = Workload(cfg, tile_pairs=tp, max_radix=rmax)
+    if len(rest) > 1 and rest[1]:
+        w.plan.set_schedule(w.plan.SCHED_PER_SCAN)
+    return w
 
 
 def test_plan_info(wl):

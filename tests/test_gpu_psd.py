@@ -18,7 +18,7 @@ def wl():
     from gpu_workload import Workload
     cfg = synth.scaled(synth.CONFIGS["lfi30"], nscan=3, len_lo=9000, len_hi=30000)
     assert cfg.flag_frac > 0
-    return Workload(cfg, cluster_size=0)
+    return Workload(cfg, tile_pairs=0)
 
 
 @pytest.mark.gpu

@@ -80,6 +80,25 @@ def test_ncorr_pcg_matches_dense_bruteforce(flags):
         assert np.allclose(xg, xd, rtol=0, atol=1e-10 * np.abs(xd).max())
 
 
+def test_ncorr_all_flagged_is_minimum_norm_dense_solution():
+    """Every sample flagged: A = C^T diag(phi) C is singular (phi_0 = 0, the
+    offset).  The draw equals the minimum-norm solution of the explicit
+    dense system (pseudo-inverse), and has no offset component."""
+    n = 60
+    rng = np.random.default_rng(8)
+    phi = oracle.corr_inv_psd(n, FS, 1e-3, 0.12, -1.4)
+    w2 = rng.standard_normal(n)
+    r = rng.standard_normal(n) * 1e-3
+    mask = np.zeros(n)
+    b = oracle.ncorr_rhs(r, mask, 1e-3, phi, rng.standard_normal(n), w2)
+    A = oracle.ncorr_dense_A(n, mask, 1e-3, phi)
+    xref = np.linalg.pinv(A, rcond=1e-12) @ b
+    x, it = oracle.sample_ncorr(r, np.zeros(n), 1.0, mask, 1e-3, 0.12, -1.4, FS, rng.standard_normal(n), w2)
+    assert it == 0
+    assert np.allclose(x, xref, rtol=0, atol=1e-9 * np.abs(xref).max())
+    assert abs(x.sum()) <= 1e-9 * np.abs(x).sum()
+
+
 def test_ncorr_mean_is_wiener_interpolation():
     """MODE_MEAN: A^{-1} M r / sigma^2 equals the textbook Gaussian
     conditional mean F_{.o} (F_oo + sigma^2 I)^{-1} r_o of the correlated
