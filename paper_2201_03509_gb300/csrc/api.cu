@@ -753,6 +753,8 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
         if ((e = dev_upload(*p, p->cg_count, static_cast<int32_t *>(nullptr), 2))) return fail(e);
         if ((e = dev_upload(*p, p->chi2_dpsd, static_cast<double *>(nullptr), 3 * static_cast<size_t>(p->nq))))
             return fail(e);
+        if ((e = dev_upload(*p, p->qsc, static_cast<float4 *>(nullptr), 2 * static_cast<size_t>(p->nq))))
+            return fail(e);
         // Toeplitz preconditioner tables (per detector)
         p->toep_nref = maxlen;
         if ((e = dev_upload(*p, p->htab, static_cast<float *>(nullptr), static_cast<size_t>(p->ndet) * TOEP_LMAX)))

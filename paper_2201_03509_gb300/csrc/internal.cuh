@@ -157,6 +157,7 @@ struct Plan {
     int64_t cgcap = 0;
     int32_t *cg_count = nullptr;     // [2] active detscans (alternating)
     double *chi2_dpsd = nullptr;     // [nq][3] per-detscan PSD terms of the chi^2 gradient
+    float4 *qsc = nullptr;           // [nq][2] per-detscan FP32 noise scalars of the current call
     int32_t coop_grid = 0;           // co-resident CTAs of the cooperative n_corr kernel
     int32_t pass_grid = 0;           // persistent grid of the other pass kernels
     int32_t tile_pairs = 0;          // requested column pairs per tile (0 = choose)

@@ -42,7 +42,8 @@ struct TxCtx {
 // threads call it; it ends with a barrier.
 __device__ __forceinline__ void tx_begin(TxCtx &X, const TxLen *__restrict__ txl, const int32_t *__restrict__ q_tx,
                                          const int64_t *__restrict__ off, int q, int blk, int64_t obase, int ndet,
-                                         double fsamp, const double *psd, const double *gain, int &cur)
+                                         double fsamp, const double *psd, const double *gain, int &cur,
+                                         const float4 *__restrict__ qsc = nullptr)
 {
     __syncthreads();                 // earlier readers of X are done
     const int li = q_tx[q];
@@ -57,7 +58,12 @@ __device__ __forceinline__ void tx_begin(TxCtx &X, const TxLen *__restrict__ txl
         X.det = q % ndet;
         X.o = off[q];
         X.yb = (off[q] - obase) >> 1;
-        if (psd) {
+        if (qsc) {          // precomputed for this call: (s2, 1/s2, 1/s, fscale), (alpha, g, -, -)
+            const float4 a0 = qsc[2 * q], a1 = qsc[2 * q + 1];
+            X.s2 = a0.x; X.inv_s2 = a0.y; X.inv_s = a0.z; X.fscale = a0.w;
+            X.alpha = a1.x;
+            X.g = a1.y;
+        } else if (psd) {
             const double sig0 = psd[3 * X.det], fk = psd[3 * X.det + 1], al = psd[3 * X.det + 2];
             const int n = static_cast<int>(off[q + 1] - off[q]);
             X.s2 = static_cast<float>(sig0 * sig0);
@@ -66,10 +72,40 @@ __device__ __forceinline__ void tx_begin(TxCtx &X, const TxLen *__restrict__ txl
             X.fscale = static_cast<float>(fsamp / (2.0 * n * fk));
             X.alpha = static_cast<float>(al);
         }
-        X.g = gain ? static_cast<float>(gain[q]) : 1.0f;
+        if (!qsc) X.g = gain ? static_cast<float>(gain[q]) : 1.0f;
     }
     cur = li;
     __syncthreads();
+}
+
+// The FP32 scalars of every detscan of a call, from the FP64 noise
+// parameters (and gains): (sigma0^2, 1/sigma0^2, 1/sigma0, fsamp/(2 n f_knee)),
+// (alpha, g, 0, 0).  Computed once per call instead of in every tile.
+__device__ __forceinline__ void det_scalars_q(const double *psd, const double *gain, const int64_t *off, int ndet,
+                                              double fsamp, int q, float4 *qsc)
+{
+    const int det = q % ndet;
+    const double sig0 = psd[3 * det], fk = psd[3 * det + 1], al = psd[3 * det + 2];
+    const double n = static_cast<double>(off[q + 1] - off[q]);
+    qsc[2 * q] = make_float4(static_cast<float>(sig0 * sig0), static_cast<float>(1.0 / (sig0 * sig0)),
+                             static_cast<float>(1.0 / sig0), static_cast<float>(fsamp / (2.0 * n * fk)));
+    qsc[2 * q + 1] = make_float4(static_cast<float>(al), gain ? static_cast<float>(gain[q]) : 1.0f, 0.f, 0.f);
+}
+__global__ void k_det_scalars(const double *__restrict__ psd, const double *__restrict__ gain,
+                              const int64_t *__restrict__ off, int ndet, double fsamp, int q0, int q1,
+                              float4 *__restrict__ qsc)
+{
+    const int q = q0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < q1) det_scalars_q(psd, gain, off, ndet, fsamp, q, qsc);
+}
+
+// This CTA's contiguous share [i0, i1) of nitems work items: consecutive
+// items of a CTA are mostly tiles of one detscan (same length: the plan
+// copy and the twiddles stay hot).
+__device__ __forceinline__ void cta_share(int nitems, int &i0, int &i1) {
+    const int per = (nitems + gridDim.x - 1) / gridDim.x;
+    i0 = min(nitems, static_cast<int>(blockIdx.x) * per);
+    i1 = min(nitems, i0 + per);
 }
 
 // (f_k / f_knee)^alpha at DCT mode k, FP32
@@ -136,49 +172,96 @@ __device__ __forceinline__ float4 ld4(const float *__restrict__ x, int64_t t, bo
     return make_float4(a.x, a.y, b.x, b.y);
 }
 
-// Forward column pass: fill the tile through fill(j1, lc, c, j, jm, centre,
-// tile) -- called for every unit j <= m-1-j of the tile, it writes z_j at
-// (j1, lc) and z_{m-1-j} at (m1-1-j1, lcol(m2-1-c)) --, FFT the columns,
-// twiddle, store Y.  pre(tile) runs before fill (after the invalid columns
-// are zeroed) with a barrier in between.
-template <class V, class Pre, class Fill>
+// Asynchronous global -> shared copies (cp.async, Ampere and later): every
+// copy of a tile is in flight at once; cp_wait ends them (a barrier must
+// follow before other threads read the tile).
+__device__ __forceinline__ void cp_async(float2 *dst, const float2 *src) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async(double2 *dst, const double2 *src) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+constexpr int TX_UNR = 4;     // units per thread whose loads are issued together
+
+// Forward column pass.  For every unit j <= m-1-j of the tile (the four
+// samples x_{4j..4j+3}, two at the centre j = m-1-j): D = ld(j, centre)
+// issues the unit's loads (TX_UNR units per thread at a time), then
+// put(D, j1, lc, c, j, jm, tile) writes z_j at (j1, lc) and z_{m-1-j} at
+// (m1-1-j1, lcol(m2-1-c)).  pre(tile) runs first (after the invalid columns
+// are zeroed), with a barrier before the units.  Then the column FFTs, the
+// twiddle, and the tile out to Y.
+template <class V, class Pre, class Ld, class Put>
 __device__ __forceinline__ void col_forward(const TxCtx &X, V *b0, V *b1, V *__restrict__ Y, const V *__restrict__ twb,
-                                            Pre pre, Fill fill)
+                                            Pre pre, Ld ld, Put put)
 {
     const ColGeo G(X.L, X.blk);
     const int W = G.W, m1 = G.m1, m2 = G.m2;
-    // invalid columns are zero
     for (int e = threadIdx.x; e < m1 * W; e += TX_T) {
         const int j1 = fdiv(e, X.L.f_W), lc = e - j1 * W;
         if (G.col(lc) < 0) b0[e] = vzero<V>();
     }
     pre(b0);
     __syncthreads();
-    for (int u = threadIdx.x; u < G.m1h * W; u += TX_T) {
-        const int j1 = fdiv(u, X.L.f_W), lc = u - j1 * W;
-        const int c = G.col(lc);
-        if (c < 0) continue;
-        const int j = j1 * m2 + c, jm = G.m - 1 - j;
-        if (j > jm) continue;
-        fill(j1, lc, c, j, jm, b0);
+    const int nu = G.m1h * W;
+    for (int u0 = threadIdx.x; u0 < nu; u0 += TX_UNR * TX_T) {
+        decltype(ld(0, false)) D[TX_UNR];
+        int jj[TX_UNR], cc[TX_UNR];
+#pragma unroll
+        for (int k = 0; k < TX_UNR; ++k) {
+            const int u = u0 + k * TX_T;
+            jj[k] = -1;
+            if (u < nu) {
+                const int j1 = fdiv(u, X.L.f_W), lc = u - j1 * W;
+                const int c = G.col(lc);
+                if (c >= 0) {
+                    const int j = j1 * m2 + c;
+                    if (j <= G.m - 1 - j) { jj[k] = j; cc[k] = c; D[k] = ld(j, j == G.m - 1 - j); }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < TX_UNR; ++k) {
+            if (jj[k] < 0) continue;
+            const int u = u0 + k * TX_T;
+            const int j1 = fdiv(u, X.L.f_W), lc = u - j1 * W;
+            put(D[k], j1, lc, cc[k], jj[k], G.m - 1 - jj[k], b0);
+        }
     }
     __syncthreads();
     const TwB<V> T(twb, X.L);
     V *R = sp_transform<false, TX_T>(b0, b1, m1, X.L.s1, X.L.nr1, W, X.L.f_W, W, 1, true, T.tw1);
     V *Yq = Y + X.yb;
-    for (int e = threadIdx.x; e < m1 * W; e += TX_T) {
-        const int k1 = fdiv(e, X.L.f_W), lc = e - k1 * W;
-        const int c = G.col(lc);
-        if (c < 0) continue;
-        Yq[static_cast<int64_t>(k1) * m2 + c] = vmul(R[e], T.w4(c * k1));
+    for (int e0 = threadIdx.x; e0 < m1 * W; e0 += TX_UNR * TX_T) {
+        V w[TX_UNR];
+        int k1v[TX_UNR], cv[TX_UNR];
+#pragma unroll
+        for (int k = 0; k < TX_UNR; ++k) {
+            const int e = e0 + k * TX_T;
+            cv[k] = -1;
+            if (e < m1 * W) {
+                const int k1 = fdiv(e, X.L.f_W), lc = e - k1 * W;
+                cv[k] = G.col(lc);
+                k1v[k] = k1;
+                if (cv[k] >= 0) w[k] = T.w4(cv[k] * k1);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < TX_UNR; ++k)
+            if (cv[k] >= 0) Yq[static_cast<int64_t>(k1v[k]) * m2 + cv[k]] = vmul(R[e0 + k * TX_T], w[k]);
     }
 }
 
-// Inverse column pass: load Y, twiddle, inverse FFT the columns, then
-// out(j1, lc, c, j, jm, centre, tile) for every unit j <= m-1-j.
-template <class V, class Out>
+// Inverse column pass: the tile's Y values copied in asynchronously,
+// twiddled in place, inverse FFT of the columns; then for every unit
+// j <= m-1-j: D = ld(j, centre) (issued TX_UNR units at a time) and
+// out(D, j1, lc, c, j, jm, tile).
+template <class V, class Ld, class Out>
 __device__ __forceinline__ void col_inverse(const TxCtx &X, V *b0, V *b1, const V *__restrict__ Y,
-                                            const V *__restrict__ twb, Out out)
+                                            const V *__restrict__ twb, Ld ld, Out out)
 {
     const ColGeo G(X.L, X.blk);
     const int W = G.W, m1 = G.m1, m2 = G.m2;
@@ -187,17 +270,54 @@ __device__ __forceinline__ void col_inverse(const TxCtx &X, V *b0, V *b1, const 
     for (int e = threadIdx.x; e < m1 * W; e += TX_T) {
         const int k1 = fdiv(e, X.L.f_W), lc = e - k1 * W;
         const int c = G.col(lc);
-        b0[e] = c < 0 ? vzero<V>() : vmulc(Yq[static_cast<int64_t>(k1) * m2 + c], T.w4(c * k1));
+        if (c < 0) b0[e] = vzero<V>();
+        else cp_async(b0 + e, Yq + static_cast<int64_t>(k1) * m2 + c);
+    }
+    cp_wait();
+    __syncthreads();
+    for (int e0 = threadIdx.x; e0 < m1 * W; e0 += TX_UNR * TX_T) {
+        V w[TX_UNR];
+        bool ok[TX_UNR];
+#pragma unroll
+        for (int k = 0; k < TX_UNR; ++k) {
+            const int e = e0 + k * TX_T;
+            ok[k] = false;
+            if (e < m1 * W) {
+                const int k1 = fdiv(e, X.L.f_W), lc = e - k1 * W;
+                const int c = G.col(lc);
+                if (c >= 0) { ok[k] = true; w[k] = T.w4(c * k1); }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < TX_UNR; ++k)
+            if (ok[k]) b0[e0 + k * TX_T] = vmulc(b0[e0 + k * TX_T], w[k]);
     }
     __syncthreads();
     V *R = sp_transform<true, TX_T>(b0, b1, m1, X.L.s1, X.L.nr1, W, X.L.f_W, W, 1, true, T.tw1);
-    for (int u = threadIdx.x; u < G.m1h * W; u += TX_T) {
-        const int j1 = fdiv(u, X.L.f_W), lc = u - j1 * W;
-        const int c = G.col(lc);
-        if (c < 0) continue;
-        const int j = j1 * m2 + c, jm = G.m - 1 - j;
-        if (j > jm) continue;
-        out(j1, lc, c, j, jm, R);
+    const int nu = G.m1h * W;
+    for (int u0 = threadIdx.x; u0 < nu; u0 += TX_UNR * TX_T) {
+        decltype(ld(0, false)) D[TX_UNR];
+        int jj[TX_UNR], cc[TX_UNR];
+#pragma unroll
+        for (int k = 0; k < TX_UNR; ++k) {
+            const int u = u0 + k * TX_T;
+            jj[k] = -1;
+            if (u < nu) {
+                const int j1 = fdiv(u, X.L.f_W), lc = u - j1 * W;
+                const int c = G.col(lc);
+                if (c >= 0) {
+                    const int j = j1 * m2 + c;
+                    if (j <= G.m - 1 - j) { jj[k] = j; cc[k] = c; D[k] = ld(j, j == G.m - 1 - j); }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < TX_UNR; ++k) {
+            if (jj[k] < 0) continue;
+            const int u = u0 + k * TX_T;
+            const int j1 = fdiv(u, X.L.f_W), lc = u - j1 * W;
+            out(D[k], j1, lc, cc[k], jj[k], G.m - 1 - jj[k], R);
+        }
     }
 }
 
@@ -268,8 +388,10 @@ __device__ __forceinline__ void row_pass(const TxCtx &X, V *b0, V *b1, V *__rest
     for (int e = threadIdx.x; e < nslot * m2; e += TX_T) {
         const int s = fdiv(e, X.L.f_m2), k2 = e - s * m2;
         const int r = G.row(s);
-        b0[s * m2p + k2] = r < 0 ? vzero<V>() : Yq[static_cast<int64_t>(r) * m2 + k2];
+        if (r < 0) b0[s * m2p + k2] = vzero<V>();
+        else cp_async(b0 + s * m2p + k2, Yq + static_cast<int64_t>(r) * m2 + k2);
     }
+    cp_wait();
     __syncthreads();
     const TwB<V> T(twb, X.L);
     V *R = sp_transform<false, TX_T>(b0, b1, m2, X.L.s2, X.L.nr2, nslot, X.L.f_2TR, 1, m2p, true, T.tw2);
@@ -396,28 +518,34 @@ struct GainTx {
     int64_t obase;
     float2 *Y;
     double *part;                 // [item][4]
+    const float4 *qsc;            // per-detscan FP32 scalars of the call
 };
 
-__global__ void __launch_bounds__(TX_T, 3) k_gain_cols(GainTx a)
+__global__ void __launch_bounds__(TX_T, 2) k_gain_cols(GainTx a)
 {
     extern __shared__ __align__(16) float2 tx_smem[];
     __shared__ TxCtx X;
     float2 *b0 = tx_smem, *b1 = tx_smem + TX_TILE;
     int cur = -1;
-    for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
+    int i0, i1;
+    cta_share(a.nitems, i0, i1);
+    for (int it = i0; it < i1; ++it) {
         const int2 w = a.items[a.item0 + it];
         tx_begin(X, a.txl, a.q_tx, a.off, w.x, w.y, a.obase, a.ndet, a.fsamp, nullptr, nullptr, cur);
         const float *sq = a.s + X.o;
         const int64_t o = X.o;
+        const ColGeo G(X.L, X.blk);
+        struct U4 { float4 v; uint32_t fb; };
         col_forward(X, b0, b1, a.Y, a.tw + X.L.twb, [](float2 *) {},
-                    [&](int j1, int lc, int c, int j, int jm, float2 *U) {
-                        const ColGeo G(X.L, X.blk);
-                        const bool ctr = j == jm;
-                        const float4 v = ld4(sq, 4 * static_cast<int64_t>(j), ctr);
-                        const uint32_t fb = flag_bits(a.flags, o + 4 * static_cast<int64_t>(j), ctr ? 2 : 4);
-                        const float x0 = (fb & 1) ? 0.f : v.x, x1 = (fb & 2) ? 0.f : v.y;
-                        const float x2 = (fb & 4) ? 0.f : v.z, x3 = (fb & 8) ? 0.f : v.w;
-                        if (ctr) { U[j1 * G.W + lc] = make_float2(x0, x1); return; }
+                    [&](int j, bool ctr) {
+                        const int64_t t = 4 * static_cast<int64_t>(j);
+                        return U4{ld4(sq, t, ctr), flag_bits(a.flags, o + t, ctr ? 2 : 4)};
+                    },
+                    [&](const U4 &D, int j1, int lc, int c, int j, int jm, float2 *U) {
+                        const uint32_t fb = D.fb;
+                        const float x0 = (fb & 1) ? 0.f : D.v.x, x1 = (fb & 2) ? 0.f : D.v.y;
+                        const float x2 = (fb & 4) ? 0.f : D.v.z, x3 = (fb & 8) ? 0.f : D.v.w;
+                        if (j == jm) { U[j1 * G.W + lc] = make_float2(x0, x1); return; }
                         U[j1 * G.W + lc] = make_float2(x0, x2);
                         U[(G.m1 - 1 - j1) * G.W + G.lcol(G.m2 - 1 - c)] = make_float2(x3, x1);
                     });
@@ -431,9 +559,11 @@ __global__ void __launch_bounds__(TX_T, 3) k_gain_rows(GainTx a)
     __shared__ double s_red[TX_T / 32], s_out[1];
     float2 *b0 = tx_smem, *b1 = tx_smem + TX_TILE;
     int cur = -1;
-    for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
+    int i0, i1;
+    cta_share(a.nitems, i0, i1);
+    for (int it = i0; it < i1; ++it) {
         const int2 w = a.items[a.item0 + it];
-        tx_begin(X, a.txl, a.q_tx, a.off, w.x, w.y, a.obase, a.ndet, a.fsamp, a.psd, nullptr, cur);
+        tx_begin(X, a.txl, a.q_tx, a.off, w.x, w.y, a.obase, a.ndet, a.fsamp, a.psd, nullptr, cur, a.qsc);
         const float fscale = X.fscale, alpha = X.alpha, s2 = X.s2;
         const int n = X.L.n, m = X.L.m;
         Acc2 sa[1] = {{0.f, 0.f}};
@@ -451,24 +581,30 @@ __global__ void __launch_bounds__(TX_T, 3) k_gain_rows(GainTx a)
     }
 }
 
-__global__ void __launch_bounds__(TX_T, 3) k_gain_colsinv(GainTx a)
+__global__ void __launch_bounds__(TX_T, 2) k_gain_colsinv(GainTx a)
 {
     extern __shared__ __align__(16) float2 tx_smem[];
     __shared__ TxCtx X;
     __shared__ double s_red[TX_T / 32], s_out[1];
     float2 *b0 = tx_smem, *b1 = tx_smem + TX_TILE;
     int cur = -1;
-    for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
+    int i0, i1;
+    cta_share(a.nitems, i0, i1);
+    for (int it = i0; it < i1; ++it) {
         const int2 w = a.items[a.item0 + it];
         tx_begin(X, a.txl, a.q_tx, a.off, w.x, w.y, a.obase, a.ndet, a.fsamp, nullptr, nullptr, cur);
         const float *dq = a.d + X.o;
         const int64_t o = X.o;
         Acc2 sb[1] = {{0.f, 0.f}};
-        col_inverse(X, b0, b1, a.Y, a.tw + X.L.twb, [&](int j1, int lc, int c, int j, int jm, const float2 *U) {
-            const ColGeo G(X.L, X.blk);
+        const ColGeo G(X.L, X.blk);
+        struct U4 { float4 v; uint32_t fb; };
+        col_inverse(X, b0, b1, a.Y, a.tw + X.L.twb, [&](int j, bool ctr) {
+            const int64_t t = 4 * static_cast<int64_t>(j);
+            return U4{ld4(dq, t, ctr), flag_bits(a.flags, o + t, ctr ? 2 : 4)};
+        }, [&](const U4 &D, int j1, int lc, int c, int j, int jm, const float2 *U) {
             const bool ctr = j == jm;
-            const float4 dv = ld4(dq, 4 * static_cast<int64_t>(j), ctr);
-            const uint32_t fb = flag_bits(a.flags, o + 4 * static_cast<int64_t>(j), ctr ? 2 : 4);
+            const float4 dv = D.v;
+            const uint32_t fb = D.fb;
             const float2 za = U[j1 * G.W + lc];
             if (ctr) {
                 acc_add_prod(sb[0], (fb & 1) ? 0.f : dv.x, za.x);
@@ -572,21 +708,30 @@ __global__ void __launch_bounds__(TX_T) k_chi2_cols(Chi2Tx<V> a)
     __shared__ TxCtx X;
     V *b0 = reinterpret_cast<V *>(tx_smem64), *b1 = b0 + TX_TILE;
     int cur = -1;
-    for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
+    int i0, i1;
+    cta_share(a.nitems, i0, i1);
+    for (int it = i0; it < i1; ++it) {
         const int2 w = a.items[a.item0 + it];
         tx_begin(X, a.txl, a.q_tx, a.off, w.x, w.y, a.obase, a.ndet, a.fsamp, nullptr, nullptr, cur);
         const double gq = a.gain[X.q];
         const float *dq = a.d + X.o;
         const int64_t o = X.o;
+        const ColGeo G(X.L, X.blk);
+        struct U4 { float4 dv; S sx[4]; uint32_t fb; };
         col_forward(X, b0, b1, a.Y, a.tw + X.L.twb, [](V *) {},
-                    [&](int j1, int lc, int c, int j, int jm, V *U) {
-                        const ColGeo G(X.L, X.blk);
+                    [&](int j, bool ctr) {
+                        const int64_t t = 4 * static_cast<int64_t>(j);
+                        U4 D;
+                        D.dv = ld4(dq, t, ctr);
+                        ld4s<S>(a.s, o + t, ctr, D.sx);
+                        D.fb = flag_bits(a.flags, o + t, ctr ? 2 : 4);
+                        return D;
+                    },
+                    [&](const U4 &D, int j1, int lc, int c, int j, int jm, V *U) {
                         const bool ctr = j == jm;
-                        const float4 dv = ld4(dq, 4 * static_cast<int64_t>(j), ctr);
-                        S sx[4];
-                        ld4s<S>(a.s, o + 4 * static_cast<int64_t>(j), ctr, sx);
-                        const struct { S x, y, z, w; } sv = {sx[0], sx[1], sx[2], sx[3]};
-                        const uint32_t fb = flag_bits(a.flags, o + 4 * static_cast<int64_t>(j), ctr ? 2 : 4);
+                        const float4 dv = D.dv;
+                        const struct { S x, y, z, w; } sv = {D.sx[0], D.sx[1], D.sx[2], D.sx[3]};
+                        const uint32_t fb = D.fb;
                         const S g = static_cast<S>(gq);
                         const S r0 = (fb & 1) ? S(0) : static_cast<S>(dv.x) - g * static_cast<S>(sv.x);
                         const S r1 = (fb & 2) ? S(0) : static_cast<S>(dv.y) - g * static_cast<S>(sv.y);
@@ -611,7 +756,9 @@ __global__ void __launch_bounds__(TX_T) k_chi2_rows(Chi2Tx<V> a)
     __shared__ double s_par[4];       // sigma0^2, ln(fsamp/(2 n f_knee)), alpha, f_knee
     V *b0 = reinterpret_cast<V *>(tx_smem64), *b1 = b0 + TX_TILE;
     int cur = -1;
-    for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
+    int i0, i1;
+    cta_share(a.nitems, i0, i1);
+    for (int it = i0; it < i1; ++it) {
         const int2 w = a.items[a.item0 + it];
         tx_begin(X, a.txl, a.q_tx, a.off, w.x, w.y, a.obase, a.ndet, a.fsamp, a.psd, nullptr, cur);
         if (threadIdx.x == 0) {
@@ -663,18 +810,26 @@ __global__ void __launch_bounds__(TX_T) k_chi2_colsinv(Chi2Tx<V> a)
     __shared__ double s_red[TX_T / 32], s_out[1];
     V *b0 = reinterpret_cast<V *>(tx_smem64), *b1 = b0 + TX_TILE;
     int cur = -1;
-    for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
+    int i0, i1;
+    cta_share(a.nitems, i0, i1);
+    for (int it = i0; it < i1; ++it) {
         const int2 w = a.items[a.item0 + it];
         tx_begin(X, a.txl, a.q_tx, a.off, w.x, w.y, a.obase, a.ndet, a.fsamp, nullptr, nullptr, cur);
         const int64_t o = X.o;
         double acc[1] = {0.0};
-        col_inverse(X, b0, b1, a.Y, a.tw + X.L.twb, [&](int j1, int lc, int c, int j, int jm, const V *U) {
-            const ColGeo G(X.L, X.blk);
+        const ColGeo G(X.L, X.blk);
+        struct U4 { S sx[4]; uint32_t fb; };
+        col_inverse(X, b0, b1, a.Y, a.tw + X.L.twb, [&](int j, bool ctr) {
+            const int64_t t = 4 * static_cast<int64_t>(j);
+            U4 D;
+            ld4s<S>(a.s, o + t, ctr, D.sx);
+            D.fb = flag_bits(a.flags, o + t, ctr ? 2 : 4);
+            return D;
+        }, [&](const U4 &D, int j1, int lc, int c, int j, int jm, const V *U) {
             const bool ctr = j == jm;
             const int64_t t = 4 * static_cast<int64_t>(j);
-            S sx[4];
-            ld4s<S>(a.s, o + t, ctr, sx);
-            const uint32_t fb = flag_bits(a.flags, o + t, ctr ? 2 : 4);
+            const S *sx = D.sx;
+            const uint32_t fb = D.fb;
             const V za = U[j1 * G.W + lc];
             const V zb = ctr ? za : U[(G.m1 - 1 - j1) * G.W + G.lcol(G.m2 - 1 - c)];
             S v[4] = {(fb & 1) ? S(0) : za.x, (fb & 2) ? S(0) : (ctr ? za.y : zb.y),
@@ -773,6 +928,7 @@ struct NcorrTx {
     float *cgv;                   // [5][cgcap]
     int64_t cgcap;
     int32_t *count;               // [2]
+    float4 *qsc;                  // [nq][2] per-detscan FP32 scalars, written in the index phase
 };
 
 struct CgVec { float *y, *r, *p, *q, *z; };
@@ -938,6 +1094,7 @@ __device__ void nc_detscan_index(const NcorrTx &a, NcShared &S, int q)
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        det_scalars_q(a.psd, a.gain, a.off, a.ndet, a.fsamp, q, a.qsc);
         CgState cs;
         cs.rz = 0.0; cs.stop = 0.0; cs.koff = koff; cs.K = K; cs.it = 0; cs.pad = 0;
         if (K == 0) cs.mode = CG_NONE;
@@ -976,6 +1133,8 @@ __device__ void nc_rhs_cols(const NcorrTx &a, NcShared &S, float2 *b0, float2 *b
     const int64_t o = X.o;
     const float g = X.g, inv_s2 = X.inv_s2, inv_s = X.inv_s;
     const uint64_t q = static_cast<uint64_t>(X.q);
+    const ColGeo G(X.L, X.blk);
+    struct U8 { float4 dv, sv; uint32_t fb; };
     col_forward(X, b0, b1, a.Y, a.tw + X.L.twb,
                 [&](float2 *U) {
                     // the tile's normals: one Philox block per thread, its four
@@ -1008,12 +1167,14 @@ __device__ void nc_rhs_cols(const NcorrTx &a, NcShared &S, float2 *b0, float2 *b
                         }
                     }
                 },
-                [&](int j1, int lc, int c, int j, int jm, float2 *U) {
-                    const ColGeo G(X.L, X.blk);
-                    const bool ctr = j == jm;
+                [&](int j, bool ctr) {
                     const int64_t t = 4 * static_cast<int64_t>(j);
-                    const float4 dv = ld4(dq, t, ctr), sv = ld4(sq, t, ctr);
-                    const uint32_t fb = flag_bits(a.flags, o + t, ctr ? 2 : 4);
+                    return U8{ld4(dq, t, ctr), ld4(sq, t, ctr), flag_bits(a.flags, o + t, ctr ? 2 : 4)};
+                },
+                [&](const U8 &D, int j1, int lc, int c, int j, int jm, float2 *U) {
+                    const bool ctr = j == jm;
+                    const float4 dv = D.dv, sv = D.sv;
+                    const uint32_t fb = D.fb;
                     const int ea = j1 * G.W + lc;
                     const float2 wa = U[ea];
                     if (ctr) {
@@ -1110,8 +1271,10 @@ __device__ void nc_x0_cols(const NcorrTx &a, NcShared &S, float2 *b0, float2 *b1
     float *xq = a.x_out + X.o;
     const int64_t o = X.o, obase = a.off[a.q0], w_lo = obase >> 5;
     float *r = a.cgv + a.cgcap;
-    col_inverse(X, b0, b1, a.Y, a.tw + X.L.twb, [&](int j1, int lc, int c, int j, int jm, const float2 *U) {
-        const ColGeo G(X.L, X.blk);
+    const ColGeo G(X.L, X.blk);
+    col_inverse(X, b0, b1, a.Y, a.tw + X.L.twb, [&](int j, bool ctr) {
+        return cg ? flag_bits(a.flags, o + 4 * static_cast<int64_t>(j), ctr ? 2 : 4) : 0u;
+    }, [&](uint32_t fbits, int j1, int lc, int c, int j, int jm, const float2 *U) {
         const bool ctr = j == jm;
         const int64_t t = 4 * static_cast<int64_t>(j);
         const float2 za = U[j1 * G.W + lc];
@@ -1121,11 +1284,10 @@ __device__ void nc_x0_cols(const NcorrTx &a, NcShared &S, float2 *b0, float2 *b1
             const float2 zb = U[(G.m1 - 1 - j1) * G.W + G.lcol(G.m2 - 1 - c)];
             v[0] = za.x; v[1] = zb.y; v[2] = za.y; v[3] = zb.x;
         }
-        const int cnt = ctr ? 2 : 4;
         reinterpret_cast<float2 *>(xq + t)[0] = make_float2(v[0], v[1]);
         if (!ctr) reinterpret_cast<float2 *>(xq + t + 2)[0] = make_float2(v[2], v[3]);
         if (cg) {
-            uint32_t fb = flag_bits(a.flags, o + t, cnt);
+            uint32_t fb = fbits;
             while (fb) {
                 const int u = __ffs(fb) - 1;
                 fb &= fb - 1;
@@ -1141,20 +1303,24 @@ __device__ void nc_scatter_cols(const NcorrTx &a, NcShared &S, float2 *b0, float
 {
     const TxCtx &X = S.X;
     const int64_t o = X.o, obase = a.off[a.q0], w_lo = obase >> 5;
+    const ColGeo G(X.L, X.blk);
     col_forward(X, b0, b1, a.Y, a.tw + X.L.twb, [](float2 *) {},
-                [&](int j1, int lc, int c, int j, int jm, float2 *U) {
-                    const ColGeo G(X.L, X.blk);
-                    const bool ctr = j == jm;
+                [&](int j, bool ctr) {
+                    // the unit's flagged entries of vec (a rank lookup only where flagged)
                     const int64_t t = 4 * static_cast<int64_t>(j);
-                    const int cnt = ctr ? 2 : 4;
-                    uint32_t fb = flag_bits(a.flags, o + t, cnt);
-                    float v[4] = {0.f, 0.f, 0.f, 0.f};
+                    uint32_t fb = flag_bits(a.flags, o + t, ctr ? 2 : 4);
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
                     while (fb) {
                         const int u = __ffs(fb) - 1;
                         fb &= fb - 1;
-                        v[u] = vec[flag_rank(a.flags, a.wpre, w_lo, obase, o + t + u)];
+                        const float val = vec[flag_rank(a.flags, a.wpre, w_lo, obase, o + t + u)];
+                        if (u == 0) v.x = val; else if (u == 1) v.y = val; else if (u == 2) v.z = val; else v.w = val;
                     }
-                    if (ctr) { U[j1 * G.W + lc] = make_float2(v[0], v[1]); return; }
+                    return v;
+                },
+                [&](const float4 &D, int j1, int lc, int c, int j, int jm, float2 *U) {
+                    const float v[4] = {D.x, D.y, D.z, D.w};
+                    if (j == jm) { U[j1 * G.W + lc] = make_float2(v[0], v[1]); return; }
                     U[j1 * G.W + lc] = make_float2(v[0], v[2]);
                     U[(G.m1 - 1 - j1) * G.W + G.lcol(G.m2 - 1 - c)] = make_float2(v[3], v[1]);
                 });
@@ -1190,11 +1356,23 @@ __device__ void nc_gather_cols(const NcorrTx &a, NcShared &S, float2 *b0, float2
     const TxCtx &X = S.X;
     const int64_t o = X.o, obase = a.off[a.q0], w_lo = obase >> 5;
     float *xq = a.x_out + X.o;
-    col_inverse(X, b0, b1, a.Y, a.tw + X.L.twb, [&](int j1, int lc, int c, int j, int jm, const float2 *U) {
-        const ColGeo G(X.L, X.blk);
+    const ColGeo G(X.L, X.blk);
+    struct U4 { float4 x; uint32_t fb; };
+    col_inverse(X, b0, b1, a.Y, a.tw + X.L.twb, [&](int j, bool ctr) {
+        // ADD: the unit's x0; gather: its flag bits
+        const int64_t t = 4 * static_cast<int64_t>(j);
+        U4 D;
+        if (ADD) {      // x0 was written earlier in this launch: coherent loads, not the read-only path
+            const float2 a01 = reinterpret_cast<const float2 *>(xq + t)[0];
+            const float2 a23 = ctr ? make_float2(0.f, 0.f) : reinterpret_cast<const float2 *>(xq + t + 2)[0];
+            D.x = make_float4(a01.x, a01.y, a23.x, a23.y);
+            D.fb = 0u;
+        }
+        else { D.x = make_float4(0.f, 0.f, 0.f, 0.f); D.fb = flag_bits(a.flags, o + t, ctr ? 2 : 4); }
+        return D;
+    }, [&](const U4 &D, int j1, int lc, int c, int j, int jm, const float2 *U) {
         const bool ctr = j == jm;
         const int64_t t = 4 * static_cast<int64_t>(j);
-        const int cnt = ctr ? 2 : 4;
         const float2 za = U[j1 * G.W + lc];
         float v[4];
         if (ctr) { v[0] = za.x; v[1] = za.y; }
@@ -1204,14 +1382,10 @@ __device__ void nc_gather_cols(const NcorrTx &a, NcShared &S, float2 *b0, float2
         }
         if (ADD) {
             float2 *p = reinterpret_cast<float2 *>(xq + t);
-            const float2 x01 = p[0];
-            p[0] = make_float2(x01.x + v[0], x01.y + v[1]);
-            if (!ctr) {
-                const float2 x23 = p[1];
-                p[1] = make_float2(x23.x + v[2], x23.y + v[3]);
-            }
+            p[0] = make_float2(D.x.x + v[0], D.x.y + v[1]);
+            if (!ctr) p[1] = make_float2(D.x.z + v[2], D.x.w + v[3]);
         } else {
-            uint32_t fb = flag_bits(a.flags, o + t, cnt);
+            uint32_t fb = D.fb;
             while (fb) {
                 const int u = __ffs(fb) - 1;
                 fb &= fb - 1;
@@ -1455,13 +1629,15 @@ __device__ __forceinline__ void nc_items(const NcorrTx &a, NcShared &S, bool row
                                          Fn fn)
 {
     const int2 *items = rows ? a.rowitems : a.colitems;
-    const int i0 = rows ? a.row_off[a.q0] : a.col_off[a.q0];
-    const int i1 = rows ? a.row_off[a.q1] : a.col_off[a.q1];
-    for (int it = i0 + blockIdx.x; it < i1; it += gridDim.x) {
+    const int j0 = rows ? a.row_off[a.q0] : a.col_off[a.q0];
+    const int j1 = rows ? a.row_off[a.q1] : a.col_off[a.q1];
+    int i0, i1;
+    cta_share(j1 - j0, i0, i1);
+    for (int it = j0 + i0; it < j0 + i1; ++it) {
         const int2 w = items[it];
         const int md = a.cgs[w.x].mode;
         if (!keep(md)) continue;
-        tx_begin(S.X, a.txl, a.q_tx, a.off, w.x, w.y, a.off[a.q0], a.ndet, a.fsamp, a.psd, a.gain, cur);
+        tx_begin(S.X, a.txl, a.q_tx, a.off, w.x, w.y, a.off[a.q0], a.ndet, a.fsamp, a.psd, a.gain, cur, a.qsc);
         if (threadIdx.x == 0) { S.X.mode = md; S.X.koff = a.cgs[w.x].koff; }
         __syncthreads();
         fn();
@@ -1577,9 +1753,10 @@ cudaError_t launch_tx_gain(const Plan &p, const float *d, const float *s, const 
     if (q1 <= q0) return cudaSuccess;
     GainTx a = {};
     a.d = d; a.s = s; a.flags = flags; a.psd = psd; a.off = p.off; a.txl = p.txl; a.q_tx = p.q_tx; a.tw = p.txtw;
-    a.ndet = p.ndet; a.fsamp = p.fsamp; a.obase = p.h_off[q0]; a.Y = p.ybuf; a.part = p.part;
+    a.ndet = p.ndet; a.fsamp = p.fsamp; a.obase = p.h_off[q0]; a.Y = p.ybuf; a.part = p.part; a.qsc = p.qsc;
     const int c0 = p.h_col_off[q0], c1 = p.h_col_off[q1], r0 = p.h_row_off[q0], r1 = p.h_row_off[q1];
     const size_t sm = tx_smem_bytes(false);
+    k_det_scalars<<<(q1 - q0 + 127) / 128, 128, 0, st>>>(psd, nullptr, p.off, p.ndet, p.fsamp, q0, q1, p.qsc);
     // column items' partials at part[c], row items' at part[ncol + r]
     a.items = p.colitems; a.item0 = c0; a.nitems = c1 - c0;
     k_gain_cols<<<grid_for(p, a.nitems), TX_T, sm, st>>>(a);
@@ -1659,7 +1836,7 @@ cudaError_t launch_tx_ncorr(const Plan &p, const float *d, const float *s, const
     a.maxit = maxit; a.x_out = x; a.iters = iters; a.status = p.status; a.spec_out = p.spec_out;
     a.xtab = p.use_prec ? p.xtab : nullptr; a.lvalid = p.lvalid;
     a.Y = sc.Y; a.wpre = sc.wpre; a.chunk = p.chunk; a.cgs = p.cgs; a.gblk = p.gblk; a.gnb = p.gnb;
-    a.cgv = sc.cgv; a.cgcap = sc.cgcap; a.count = p.cg_count;
+    a.cgv = sc.cgv; a.cgcap = sc.cgcap; a.count = p.cg_count; a.qsc = p.qsc;
     void *args[] = {&a};
     return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_ncorr_tx), dim3(grid), dim3(TX_T), args,
                                        tx_smem_bytes(false), st);
