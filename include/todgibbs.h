@@ -141,8 +141,9 @@ typedef struct {
     const int64_t *offsets; /* HOST [ndet*nscan+1]; every length an FFT length */
     tod_huff_streams pix;   /* HOST compressed pixel stream */
     tod_huff_streams psi;   /* HOST compressed psi-bin stream */
-    int32_t tile_pairs;     /* column pairs per tile of the transforms' column passes: 0 = choose
-                               (up to 16), else a cap 1..2048 */
+    int32_t tile_pairs;     /* column pairs per tile of the transforms' column passes: 0 = the
+                               widest tile that fits, else a cap 1..64 (the tile takes the
+                               largest power of two not above it) */
     int32_t device;         /* CUDA device ordinal the plan lives on */
     int32_t max_radix;      /* largest Stockham radix of the transforms: 0 = 16; else 2..16 */
 } tod_band_desc;

@@ -223,11 +223,12 @@ int64_t fft_length_impl(int64_t n)
 }
 
 // Stockham radices of a sub-transform of length L: repeatedly the largest
-// register DFT up to rmax (16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2) that divides
-// what is left (empty for L = 1).
+// register DFT up to rmax (16, 10, 9, 8, 6, 5, 4, 3, 2) that divides what is
+// left (empty for L = 1).  A thread of the in-place passes holds the inputs
+// of ceil(16/R) butterflies: at most 20 values with these radices.
 std::vector<int8_t> radix_plan(int L, int rmax)
 {
-    static const int kRadix[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
+    static const int kRadix[] = {16, 10, 9, 8, 6, 5, 4, 3, 2};
     std::vector<int8_t> r;
     while (L > 1) {
         int pick = 0;
@@ -253,6 +254,18 @@ void fill_stages(DctStage *st, const std::vector<int8_t> &r, int L)
     }
 }
 
+// Column pairs per column tile: the largest power of two (at most 64, so
+// that the 2 TP columns divide the CTA's threads) with 2 TP m1 <= TX_TILE,
+// capped by tile_pairs when given.
+int tile_width(int P2, int m1, int tile_pairs)
+{
+    int cap = std::min(64, TX_TILE / (2 * m1));
+    if (tile_pairs > 0) cap = std::min(cap, tile_pairs);
+    int tp = 1;
+    while (2 * tp <= cap && tp < P2) tp *= 2;
+    return tp;
+}
+
 // Split m = n/2 = m1 x m2 for the multi-pass transform.  A column tile holds
 // m1 rows of 2 TP columns and a row tile 2 TR rows of m2 (made odd), each at
 // most TX_TILE values.  Wide column tiles (TP up to 16: sample runs of 64
@@ -272,8 +285,7 @@ bool choose_tx_split(int n, int rmax, int tile_pairs, TxLen &out)
         const int m2p = m2 | 1;
         if (2 * m1 > TX_TILE || 2 * m2p > TX_TILE) continue;
         const int P1 = m1 / 2 + 1, P2 = (m2 + 1) / 2;
-        int TP = std::min(P2, TX_TILE / (2 * m1));
-        if (tile_pairs > 0) TP = std::min(TP, tile_pairs);
+        const int TP = tile_width(P2, m1, tile_pairs);
         const int TR = std::min(P1, TX_TILE / (2 * m2p));
         const double score = std::min(TP, 16) / 16.0 + std::min(TR, 4) / 4.0 -
                              1e-3 * std::fabs(std::log(static_cast<double>(m2) / m1 / 2.5));
@@ -286,8 +298,7 @@ bool choose_tx_split(int n, int rmax, int tile_pairs, TxLen &out)
     out.n = n; out.m = m; out.m1 = m1; out.m2 = m2; out.m2p = m2 | 1;
     out.P1 = m1 / 2 + 1;
     out.P2 = (m2 + 1) / 2;
-    out.TP = std::min(out.P2, TX_TILE / (2 * m1));
-    if (tile_pairs > 0) out.TP = std::min(out.TP, tile_pairs);
+    out.TP = tile_width(out.P2, m1, tile_pairs);
     out.TR = std::min(out.P1, TX_TILE / (2 * out.m2p));
     out.nr1 = static_cast<int32_t>(r1.size());
     out.nr2 = static_cast<int32_t>(r2.size());
@@ -581,7 +592,7 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
         band->n_psi != TOD_N_PSI || !(band->fsamp > 0) || !band->offsets)
         return TOD_ERR_ARG;
     const int tile_pairs = band->tile_pairs;
-    if (tile_pairs < 0 || tile_pairs > TX_TILE / 2) return TOD_ERR_ARG;
+    if (tile_pairs < 0 || tile_pairs > 64) return TOD_ERR_ARG;
     const int rmax = band->max_radix > 0 ? band->max_radix : 16;
     if (rmax < 2 || rmax > 16) return TOD_ERR_ARG;
     Plan *p = new (std::nothrow) Plan();

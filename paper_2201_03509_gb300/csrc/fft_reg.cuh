@@ -190,6 +190,7 @@ template <int R, bool INV, class V> struct RDft {
 // src[c * vs + e * es].  Butterfly w: vector-fast (w -> vector w mod nvec)
 // when vfast, else element-fast.  Pass twiddles W_L^{r k Lr/(Ns R)}... read
 // from tw (W_L^i, i < L, global).  NT threads; the caller synchronises.
+// Radices 16, 10, 9, 8, 6, 5, 4, 3, 2.
 // ---------------------------------------------------------------------------
 template <int R, bool INV, int NT, class V>
 __device__ __forceinline__ void sp_pass(const V *__restrict__ src, V *__restrict__ dst, int L, const DctStage &st,
@@ -236,8 +237,6 @@ __device__ V *sp_transform(V *a, V *b, int L, const DctStage *stages, int nr, in
         const DctStage st = stages[s];
         switch (st.R) {
         case 16: sp_pass<16, INV, NT>(a, b, L, st, nvec, fnvec, es, vs, vfast, tw); break;
-        case 15: sp_pass<15, INV, NT>(a, b, L, st, nvec, fnvec, es, vs, vfast, tw); break;
-        case 12: sp_pass<12, INV, NT>(a, b, L, st, nvec, fnvec, es, vs, vfast, tw); break;
         case 10: sp_pass<10, INV, NT>(a, b, L, st, nvec, fnvec, es, vs, vfast, tw); break;
         case 9: sp_pass<9, INV, NT>(a, b, L, st, nvec, fnvec, es, vs, vfast, tw); break;
         case 8: sp_pass<8, INV, NT>(a, b, L, st, nvec, fnvec, es, vs, vfast, tw); break;

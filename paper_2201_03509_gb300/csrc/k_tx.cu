@@ -187,71 +187,76 @@ __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_all;\n" 
 
 constexpr int TX_UNR = 4;     // units per thread whose loads are issued together
 
+// Column tiles have 2 TP = W columns with W a power of two dividing TX_T:
+// thread t keeps column lc = t mod W and takes rows t / W, t / W + TX_T / W,
+// ..., so a column's index arithmetic is done once per thread.
+struct ColThread {
+    int lc, c, r0, rstep, cpart, lpart;   // own column, its index, first row, row step; partner column and slot
+    __device__ __forceinline__ ColThread(const ColGeo &G) {
+        lc = threadIdx.x & (G.W - 1);
+        r0 = threadIdx.x / G.W;
+        rstep = TX_T / G.W;
+        c = G.col(lc);
+        cpart = c < 0 ? -1 : G.m2 - 1 - c;
+        lpart = c < 0 ? -1 : G.lcol(cpart);
+    }
+};
+
 // Forward column pass.  For every unit j <= m-1-j of the tile (the four
 // samples x_{4j..4j+3}, two at the centre j = m-1-j): D = ld(j, centre)
 // issues the unit's loads (TX_UNR units per thread at a time), then
 // put(D, j1, lc, c, j, jm, tile) writes z_j at (j1, lc) and z_{m-1-j} at
-// (m1-1-j1, lcol(m2-1-c)).  pre(tile) runs first (after the invalid columns
-// are zeroed), with a barrier before the units.  Then the column FFTs, the
-// twiddle, and the tile out to Y.
+// (m1-1-j1, lcol(m2-1-c)).  pre(tile) runs first (after the columns a
+// ragged tile lacks are zeroed), with a barrier before the units.  Then
+// the column FFTs, the twiddle, and the tile out to Y.
 template <class V, class Pre, class Ld, class Put>
 __device__ __forceinline__ void col_forward(const TxCtx &X, V *b0, V *b1, V *__restrict__ Y, const V *__restrict__ twb,
                                             Pre pre, Ld ld, Put put)
 {
     const ColGeo G(X.L, X.blk);
+    const ColThread C(G);
     const int W = G.W, m1 = G.m1, m2 = G.m2;
-    for (int e = threadIdx.x; e < m1 * W; e += TX_T) {
-        const int j1 = fdiv(e, X.L.f_W), lc = e - j1 * W;
-        if (G.col(lc) < 0) b0[e] = vzero<V>();
-    }
+    if (C.c < 0)
+        for (int j1 = C.r0; j1 < m1; j1 += C.rstep) b0[j1 * W + C.lc] = vzero<V>();
     pre(b0);
     __syncthreads();
-    const int nu = G.m1h * W;
-    for (int u0 = threadIdx.x; u0 < nu; u0 += TX_UNR * TX_T) {
-        decltype(ld(0, false)) D[TX_UNR];
-        int jj[TX_UNR], cc[TX_UNR];
+    if (C.c >= 0) {
+        for (int j10 = C.r0; j10 < G.m1h; j10 += TX_UNR * C.rstep) {
+            decltype(ld(0, false)) D[TX_UNR];
+            bool ok[TX_UNR];
 #pragma unroll
-        for (int k = 0; k < TX_UNR; ++k) {
-            const int u = u0 + k * TX_T;
-            jj[k] = -1;
-            if (u < nu) {
-                const int j1 = fdiv(u, X.L.f_W), lc = u - j1 * W;
-                const int c = G.col(lc);
-                if (c >= 0) {
-                    const int j = j1 * m2 + c;
-                    if (j <= G.m - 1 - j) { jj[k] = j; cc[k] = c; D[k] = ld(j, j == G.m - 1 - j); }
-                }
+            for (int k = 0; k < TX_UNR; ++k) {
+                const int j1 = j10 + k * C.rstep;
+                const int j = j1 * m2 + C.c;
+                ok[k] = j1 < G.m1h && j <= G.m - 1 - j;
+                if (ok[k]) D[k] = ld(j, j == G.m - 1 - j);
             }
-        }
 #pragma unroll
-        for (int k = 0; k < TX_UNR; ++k) {
-            if (jj[k] < 0) continue;
-            const int u = u0 + k * TX_T;
-            const int j1 = fdiv(u, X.L.f_W), lc = u - j1 * W;
-            put(D[k], j1, lc, cc[k], jj[k], G.m - 1 - jj[k], b0);
+            for (int k = 0; k < TX_UNR; ++k) {
+                if (!ok[k]) continue;
+                const int j1 = j10 + k * C.rstep;
+                const int j = j1 * m2 + C.c;
+                put(D[k], j1, C.lc, C.c, j, G.m - 1 - j, b0);
+            }
         }
     }
     __syncthreads();
     const TwB<V> T(twb, X.L);
     V *R = sp_transform<false, TX_T>(b0, b1, m1, X.L.s1, X.L.nr1, W, X.L.f_W, W, 1, true, T.tw1);
-    V *Yq = Y + X.yb;
-    for (int e0 = threadIdx.x; e0 < m1 * W; e0 += TX_UNR * TX_T) {
+    if (C.c < 0) return;
+    V *Yq = Y + X.yb + C.c;
+    for (int k10 = C.r0; k10 < m1; k10 += TX_UNR * C.rstep) {
         V w[TX_UNR];
-        int k1v[TX_UNR], cv[TX_UNR];
 #pragma unroll
         for (int k = 0; k < TX_UNR; ++k) {
-            const int e = e0 + k * TX_T;
-            cv[k] = -1;
-            if (e < m1 * W) {
-                const int k1 = fdiv(e, X.L.f_W), lc = e - k1 * W;
-                cv[k] = G.col(lc);
-                k1v[k] = k1;
-                if (cv[k] >= 0) w[k] = T.w4(cv[k] * k1);
-            }
+            const int k1 = k10 + k * C.rstep;
+            if (k1 < m1) w[k] = T.w4(C.c * k1);
         }
 #pragma unroll
-        for (int k = 0; k < TX_UNR; ++k)
-            if (cv[k] >= 0) Yq[static_cast<int64_t>(k1v[k]) * m2 + cv[k]] = vmul(R[e0 + k * TX_T], w[k]);
+        for (int k = 0; k < TX_UNR; ++k) {
+            const int k1 = k10 + k * C.rstep;
+            if (k1 < m1) Yq[static_cast<int64_t>(k1) * m2] = vmul(R[k1 * W + C.lc], w[k]);
+        }
     }
 }
 
@@ -264,59 +269,48 @@ __device__ __forceinline__ void col_inverse(const TxCtx &X, V *b0, V *b1, const 
                                             const V *__restrict__ twb, Ld ld, Out out)
 {
     const ColGeo G(X.L, X.blk);
+    const ColThread C(G);
     const int W = G.W, m1 = G.m1, m2 = G.m2;
     const TwB<V> T(twb, X.L);
-    const V *Yq = Y + X.yb;
-    for (int e = threadIdx.x; e < m1 * W; e += TX_T) {
-        const int k1 = fdiv(e, X.L.f_W), lc = e - k1 * W;
-        const int c = G.col(lc);
-        if (c < 0) b0[e] = vzero<V>();
-        else cp_async(b0 + e, Yq + static_cast<int64_t>(k1) * m2 + c);
-    }
-    cp_wait();
-    __syncthreads();
-    for (int e0 = threadIdx.x; e0 < m1 * W; e0 += TX_UNR * TX_T) {
-        V w[TX_UNR];
-        bool ok[TX_UNR];
+    if (C.c < 0) {
+        for (int k1 = C.r0; k1 < m1; k1 += C.rstep) b0[k1 * W + C.lc] = vzero<V>();
+    } else {
+        const V *Yq = Y + X.yb + C.c;
+        for (int k1 = C.r0; k1 < m1; k1 += C.rstep) cp_async(b0 + k1 * W + C.lc, Yq + static_cast<int64_t>(k1) * m2);
+        cp_wait();
+        for (int k10 = C.r0; k10 < m1; k10 += TX_UNR * C.rstep) {
+            V w[TX_UNR];
 #pragma unroll
-        for (int k = 0; k < TX_UNR; ++k) {
-            const int e = e0 + k * TX_T;
-            ok[k] = false;
-            if (e < m1 * W) {
-                const int k1 = fdiv(e, X.L.f_W), lc = e - k1 * W;
-                const int c = G.col(lc);
-                if (c >= 0) { ok[k] = true; w[k] = T.w4(c * k1); }
+            for (int k = 0; k < TX_UNR; ++k) {
+                const int k1 = k10 + k * C.rstep;
+                if (k1 < m1) w[k] = T.w4(C.c * k1);
+            }
+#pragma unroll
+            for (int k = 0; k < TX_UNR; ++k) {
+                const int k1 = k10 + k * C.rstep;
+                if (k1 < m1) b0[k1 * W + C.lc] = vmulc(b0[k1 * W + C.lc], w[k]);
             }
         }
-#pragma unroll
-        for (int k = 0; k < TX_UNR; ++k)
-            if (ok[k]) b0[e0 + k * TX_T] = vmulc(b0[e0 + k * TX_T], w[k]);
     }
     __syncthreads();
     V *R = sp_transform<true, TX_T>(b0, b1, m1, X.L.s1, X.L.nr1, W, X.L.f_W, W, 1, true, T.tw1);
-    const int nu = G.m1h * W;
-    for (int u0 = threadIdx.x; u0 < nu; u0 += TX_UNR * TX_T) {
+    if (C.c < 0) return;
+    for (int j10 = C.r0; j10 < G.m1h; j10 += TX_UNR * C.rstep) {
         decltype(ld(0, false)) D[TX_UNR];
-        int jj[TX_UNR], cc[TX_UNR];
+        bool ok[TX_UNR];
 #pragma unroll
         for (int k = 0; k < TX_UNR; ++k) {
-            const int u = u0 + k * TX_T;
-            jj[k] = -1;
-            if (u < nu) {
-                const int j1 = fdiv(u, X.L.f_W), lc = u - j1 * W;
-                const int c = G.col(lc);
-                if (c >= 0) {
-                    const int j = j1 * m2 + c;
-                    if (j <= G.m - 1 - j) { jj[k] = j; cc[k] = c; D[k] = ld(j, j == G.m - 1 - j); }
-                }
-            }
+            const int j1 = j10 + k * C.rstep;
+            const int j = j1 * m2 + C.c;
+            ok[k] = j1 < G.m1h && j <= G.m - 1 - j;
+            if (ok[k]) D[k] = ld(j, j == G.m - 1 - j);
         }
 #pragma unroll
         for (int k = 0; k < TX_UNR; ++k) {
-            if (jj[k] < 0) continue;
-            const int u = u0 + k * TX_T;
-            const int j1 = fdiv(u, X.L.f_W), lc = u - j1 * W;
-            out(D[k], j1, lc, cc[k], jj[k], G.m - 1 - jj[k], R);
+            if (!ok[k]) continue;
+            const int j1 = j10 + k * C.rstep;
+            const int j = j1 * m2 + C.c;
+            out(D[k], j1, C.lc, C.c, j, G.m - 1 - j, R);
         }
     }
 }
@@ -372,7 +366,8 @@ __device__ __forceinline__ V split_i(const TwB<V> &T, V yk, V yp, int k1, int k2
 }
 
 // Row pass.  Loads the tile's rows from Y, forward row FFTs, then
-// pre(free_buffer) (a barrier follows), then for every packed slot:
+// pre(nubuf) (a second tile-sized buffer, or null when pre needs none; a
+// barrier follows), then for every packed slot:
 // Y' = f(e, k, Y) (e: tile element, k: slot, Y = (X_k, X_{n-k}) or (X_0, X_m));
 // with INV_BACK the inverse split and inverse row FFTs follow and the rows go
 // back to Y.
@@ -385,11 +380,17 @@ __device__ __forceinline__ void row_pass(const TxCtx &X, V *b0, V *b1, V *__rest
     const int m1 = G.m1, m2 = G.m2, m2p = G.m2p;
     const int nslot = 2 * G.TR;
     V *Yq = Y + X.yb;
-    for (int e = threadIdx.x; e < nslot * m2; e += TX_T) {
-        const int s = fdiv(e, X.L.f_m2), k2 = e - s * m2;
-        const int r = G.row(s);
-        if (r < 0) b0[s * m2p + k2] = vzero<V>();
-        else cp_async(b0 + s * m2p + k2, Yq + static_cast<int64_t>(r) * m2 + k2);
+    {
+        // element e = s m2 + k2, stepped by TX_T without divisions
+        int s = 0, k2 = threadIdx.x;
+        while (k2 >= m2) { k2 -= m2; ++s; }
+        for (; s < nslot;) {
+            const int r = G.row(s);
+            if (r < 0) b0[s * m2p + k2] = vzero<V>();
+            else cp_async(b0 + s * m2p + k2, Yq + static_cast<int64_t>(r) * m2 + k2);
+            k2 += TX_T;
+            while (k2 >= m2) { k2 -= m2; ++s; }
+        }
     }
     cp_wait();
     __syncthreads();
@@ -400,45 +401,56 @@ __device__ __forceinline__ void row_pass(const TxCtx &X, V *b0, V *b1, V *__rest
     __syncthreads();
     const S sqf = static_cast<S>(X.L.sq_fwd), s0f = static_cast<S>(X.L.s0_fwd);
     const S sqi = static_cast<S>(X.L.sq_inv), s0i = static_cast<S>(X.L.s0_inv);
-    for (int e = threadIdx.x; e < G.nr * m2; e += TX_T) {
-        const int pl = fdiv(e, X.L.f_m2), k2 = e - pl * m2;
-        const int p = G.r0 + pl;
-        const int cnt = (p == 0) ? (m2 / 2 + 1) : ((2 * p == m1) ? (m2 + 1) / 2 : m2);
-        if (k2 >= cnt) continue;
-        int ib, q1, q2;
-        if (p == 0) { q1 = 0; q2 = (k2 == 0) ? 0 : m2 - k2; ib = 2 * pl * m2p + q2; }
-        else { q1 = m1 - p; q2 = m2 - 1 - k2; ib = ((q1 == p) ? 2 * pl : 2 * pl + 1) * m2p + q2; }
-        const int ia = 2 * pl * m2p + k2;
-        const V Za = R[ia], Zb = R[ib];
-        if (p == 0 && k2 == 0) {
-            V Yv = vmake<V>((Za.x + Za.y) * s0f, (Za.x - Za.y) * s0f);
-            Yv = f(ia, 0, Yv);
-            if (INV_BACK) {
-                const S V0 = Yv.x * s0i, Vm = Yv.y * s0i;
-                R[ia] = vmake<V>(static_cast<S>(0.5) * (V0 + Vm), static_cast<S>(0.5) * (V0 - Vm));
+    {
+        int pl = 0, k2 = threadIdx.x;
+        while (k2 >= m2) { k2 -= m2; ++pl; }
+        for (; pl < G.nr;) {
+            const int p = G.r0 + pl;
+            const int cnt = (p == 0) ? (m2 / 2 + 1) : ((2 * p == m1) ? (m2 + 1) / 2 : m2);
+            if (k2 < cnt) {
+                int ib, q1, q2;
+                if (p == 0) { q1 = 0; q2 = (k2 == 0) ? 0 : m2 - k2; ib = 2 * pl * m2p + q2; }
+                else { q1 = m1 - p; q2 = m2 - 1 - k2; ib = ((q1 == p) ? 2 * pl : 2 * pl + 1) * m2p + q2; }
+                const int ia = 2 * pl * m2p + k2;
+                const V Za = R[ia], Zb = R[ib];
+                if (p == 0 && k2 == 0) {
+                    V Yv = vmake<V>((Za.x + Za.y) * s0f, (Za.x - Za.y) * s0f);
+                    Yv = f(ia, 0, Yv);
+                    if (INV_BACK) {
+                        const S V0 = Yv.x * s0i, Vm = Yv.y * s0i;
+                        R[ia] = vmake<V>(static_cast<S>(0.5) * (V0 + Vm), static_cast<S>(0.5) * (V0 - Vm));
+                    }
+                } else {
+                    V Ya = split_f(T, Za, Zb, p, k2, sqf);
+                    Ya = f(ia, p + m1 * k2, Ya);
+                    if (ib != ia) {
+                        V Yb = split_f(T, Zb, Za, q1, q2, sqf);
+                        Yb = f(ib, q1 + m1 * q2, Yb);
+                        if (INV_BACK) {
+                            R[ib] = split_i(T, Yb, Ya, q1, q2, p, k2, sqi);
+                            R[ia] = split_i(T, Ya, Yb, p, k2, q1, q2, sqi);
+                        }
+                    } else if (INV_BACK) {
+                        R[ia] = split_i(T, Ya, Ya, p, k2, q1, q2, sqi);
+                    }
+                }
             }
-            continue;
-        }
-        V Ya = split_f(T, Za, Zb, p, k2, sqf);
-        Ya = f(ia, p + m1 * k2, Ya);
-        if (ib != ia) {
-            V Yb = split_f(T, Zb, Za, q1, q2, sqf);
-            Yb = f(ib, q1 + m1 * q2, Yb);
-            if (INV_BACK) {
-                R[ib] = split_i(T, Yb, Ya, q1, q2, p, k2, sqi);
-                R[ia] = split_i(T, Ya, Yb, p, k2, q1, q2, sqi);
-            }
-        } else if (INV_BACK) {
-            R[ia] = split_i(T, Ya, Ya, p, k2, q1, q2, sqi);
+            k2 += TX_T;
+            while (k2 >= m2) { k2 -= m2; ++pl; }
         }
     }
     if (!INV_BACK) return;
     __syncthreads();
     V *Ri = sp_transform<true, TX_T>(R, Fr, m2, X.L.s2, X.L.nr2, nslot, X.L.f_2TR, 1, m2p, true, T.tw2);
-    for (int e = threadIdx.x; e < nslot * m2; e += TX_T) {
-        const int s = fdiv(e, X.L.f_m2), k2 = e - s * m2;
-        const int r = G.row(s);
-        if (r >= 0) Yq[static_cast<int64_t>(r) * m2 + k2] = Ri[s * m2p + k2];
+    {
+        int s = 0, k2 = threadIdx.x;
+        while (k2 >= m2) { k2 -= m2; ++s; }
+        for (; s < nslot;) {
+            const int r = G.row(s);
+            if (r >= 0) Yq[static_cast<int64_t>(r) * m2 + k2] = Ri[s * m2p + k2];
+            k2 += TX_T;
+            while (k2 >= m2) { k2 -= m2; ++s; }
+        }
     }
 }
 
@@ -521,7 +533,7 @@ struct GainTx {
     const float4 *qsc;            // per-detscan FP32 scalars of the call
 };
 
-__global__ void __launch_bounds__(TX_T, 2) k_gain_cols(GainTx a)
+__global__ void __launch_bounds__(TX_T, 3) k_gain_cols(GainTx a)
 {
     extern __shared__ __align__(16) float2 tx_smem[];
     __shared__ TxCtx X;
@@ -581,7 +593,7 @@ __global__ void __launch_bounds__(TX_T, 3) k_gain_rows(GainTx a)
     }
 }
 
-__global__ void __launch_bounds__(TX_T, 2) k_gain_colsinv(GainTx a)
+__global__ void __launch_bounds__(TX_T, 3) k_gain_colsinv(GainTx a)
 {
     extern __shared__ __align__(16) float2 tx_smem[];
     __shared__ TxCtx X;
@@ -998,44 +1010,55 @@ __device__ int3 cta_exscan3(int3 v, int3 *s_w, int3 &total)
     return make_int3(b.x + inc.x - v.x, b.y + inc.y - v.y, b.z + inc.z - v.z);
 }
 
-// Phase 1: flagged-sample prefix over the range's flag words, in chunks of
-// words per CTA, with grid barriers between count, chunk scan and write.
-__device__ void nc_flag_prefix(const NcorrTx &a, NcShared &S, cgrp::grid_group &grid)
+// Flagged-sample prefix over the range's flag words, in chunks of words per
+// CTA: count (chunk totals), scan (one thread), write (per-word prefix).
+struct FlagChunk {
+    int64_t w_lo, nw, c0, c1, t0, per, obase, oend;
+};
+__device__ __forceinline__ FlagChunk flag_chunk(const NcorrTx &a) {
+    FlagChunk f;
+    f.obase = a.off[a.q0];
+    f.oend = a.off[a.q1];
+    f.w_lo = f.obase >> 5;
+    f.nw = ((f.oend + 31) >> 5) - f.w_lo;
+    const int64_t cw = (f.nw + gridDim.x - 1) / gridDim.x;
+    f.c0 = min(f.nw, static_cast<int64_t>(blockIdx.x) * cw);
+    f.c1 = min(f.nw, f.c0 + cw);
+    f.per = (f.c1 - f.c0 + TX_T - 1) / TX_T;
+    f.t0 = f.c0 + threadIdx.x * f.per;
+    return f;
+}
+// word w_lo + i restricted to the range
+__device__ __forceinline__ uint32_t flag_word(const NcorrTx &a, const FlagChunk &f, int64_t i) {
+    const int64_t w = f.w_lo + i;
+    uint32_t b = __ldg(a.flags + w);
+    const int64_t base = w << 5;
+    if (base < f.obase) b &= ~0u << static_cast<int>(f.obase - base);
+    if (base + 32 > f.oend) b &= (f.oend - base >= 32) ? ~0u : ((1u << static_cast<int>(f.oend - base)) - 1u);
+    return b;
+}
+__device__ void nc_flag_count(const NcorrTx &a, NcShared &S)
 {
-    const int64_t obase = a.off[a.q0], oend = a.off[a.q1];
-    const int64_t w_lo = obase >> 5, w_hi = (oend + 31) >> 5;
-    const int64_t nw = w_hi - w_lo;
-    const int G = gridDim.x;
-    const int64_t cw = (nw + G - 1) / G;
-    const int64_t c0 = min(nw, blockIdx.x * cw), c1 = min(nw, c0 + cw);
-    const int64_t per = (c1 - c0 + TX_T - 1) / TX_T;
-    auto word = [&](int64_t i) -> uint32_t {     // word w_lo + i restricted to the range
-        const int64_t w = w_lo + i;
-        uint32_t b = __ldg(a.flags + w);
-        const int64_t base = w << 5;
-        if (base < obase) b &= ~0u << static_cast<int>(obase - base);
-        if (base + 32 > oend) b &= (oend - base >= 32) ? ~0u : ((1u << static_cast<int>(oend - base)) - 1u);
-        return b;
-    };
+    const FlagChunk f = flag_chunk(a);
     int mine = 0;
-    const int64_t t0 = c0 + threadIdx.x * per;
-    for (int64_t i = t0; i < min(c1, t0 + per); ++i) mine += __popc(word(i));
+    for (int64_t i = f.t0; i < min(f.c1, f.t0 + f.per); ++i) mine += __popc(flag_word(a, f, i));
+    int3 tot3;
+    cta_exscan3(make_int3(mine, 0, 0), S.scan, tot3);
+    if (threadIdx.x == 0) a.chunk[blockIdx.x] = tot3.x;
+}
+__device__ void nc_flag_write(const NcorrTx &a, NcShared &S)
+{
+    const FlagChunk f = flag_chunk(a);
+    int mine = 0;
+    for (int64_t i = f.t0; i < min(f.c1, f.t0 + f.per); ++i) mine += __popc(flag_word(a, f, i));
     int3 tot3;
     const int3 ex = cta_exscan3(make_int3(mine, 0, 0), S.scan, tot3);
-    if (threadIdx.x == 0) a.chunk[blockIdx.x] = tot3.x;
-    grid.sync();
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        int64_t acc = 0;
-        for (int c = 0; c < G; ++c) { const int64_t v = a.chunk[c]; a.chunk[c] = acc; acc += v; }
-        a.chunk[G] = acc;
-    }
-    grid.sync();
     int64_t run = a.chunk[blockIdx.x] + ex.x;
-    for (int64_t i = t0; i < min(c1, t0 + per); ++i) {
+    for (int64_t i = f.t0; i < min(f.c1, f.t0 + f.per); ++i) {
         a.wpre[i] = run;
-        run += __popc(word(i));
+        run += __popc(flag_word(a, f, i));
     }
-    if (blockIdx.x == G - 1 && threadIdx.x == 0) a.wpre[nw] = a.chunk[G];
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) a.wpre[f.nw] = a.chunk[gridDim.x];
 }
 
 // Phase 2 (per detscan): flagged count and rank offset, CG mode, and the
@@ -1125,9 +1148,8 @@ __device__ void nc_detscan_index(const NcorrTx &a, NcShared &S, int q)
 // Phase 3, column pass of the right-hand side: M (r/sigma0^2 + w1/sigma0),
 // r = d - g s; w1 of z_j is normal pair j of the NC_W1 stream (pair j mod 4
 // of Philox block j/4).
-__device__ void nc_rhs_cols(const NcorrTx &a, NcShared &S, float2 *b0, float2 *b1, uint64_t gi)
+__device__ void nc_rhs_cols(const NcorrTx &a, const TxCtx &X, float2 *b0, float2 *b1, uint64_t gi)
 {
-    const TxCtx &X = S.X;
     const bool draw = a.mode == TOD_MODE_DRAW;
     const float *dq = a.d + X.o, *sq = a.s + X.o;
     const int64_t o = X.o;
@@ -1203,9 +1225,8 @@ __device__ __forceinline__ float nc_r(int k, const TxCtx &X) {
 // Phase 3, row pass of the right-hand side: + sqrt(phi) w2 (mode pair k of
 // the NC_W2 stream), times beta; the spectrum beta (C b + prior term) is
 // written when asked for.
-__device__ void nc_rhs_rows(const NcorrTx &a, NcShared &S, float2 *b0, float2 *b1, uint64_t gi)
+__device__ void nc_rhs_rows(const NcorrTx &a, const TxCtx &X, float2 *b0, float2 *b1, uint64_t gi)
 {
-    const TxCtx &X = S.X;
     const bool draw = a.mode == TOD_MODE_DRAW;
     const bool allf = X.mode == CG_ALLFLAG;
     const uint64_t q = static_cast<uint64_t>(X.q);
@@ -1264,9 +1285,8 @@ __device__ void nc_rhs_rows(const NcorrTx &a, NcShared &S, float2 *b0, float2 *b
 
 // Phase 3, inverse column pass: x0 out; its flagged samples are the CG
 // right-hand side E^T x0.
-__device__ void nc_x0_cols(const NcorrTx &a, NcShared &S, float2 *b0, float2 *b1)
+__device__ void nc_x0_cols(const NcorrTx &a, const TxCtx &X, float2 *b0, float2 *b1)
 {
-    const TxCtx &X = S.X;
     const bool cg = X.mode == CG_ACTIVE;
     float *xq = a.x_out + X.o;
     const int64_t o = X.o, obase = a.off[a.q0], w_lo = obase >> 5;
@@ -1299,9 +1319,8 @@ __device__ void nc_x0_cols(const NcorrTx &a, NcShared &S, float2 *b0, float2 *b1
 
 // CG column pass: z = E vec (the flagged samples' entries of vec, zero
 // elsewhere), forward columns.
-__device__ void nc_scatter_cols(const NcorrTx &a, NcShared &S, float2 *b0, float2 *b1, const float *vec)
+__device__ void nc_scatter_cols(const NcorrTx &a, const TxCtx &X, float2 *b0, float2 *b1, const float *vec)
 {
-    const TxCtx &X = S.X;
     const int64_t o = X.o, obase = a.off[a.q0], w_lo = obase >> 5;
     const ColGeo G(X.L, X.blk);
     col_forward(X, b0, b1, a.Y, a.tw + X.L.twb, [](float2 *) {},
@@ -1329,9 +1348,8 @@ __device__ void nc_scatter_cols(const NcorrTx &a, NcShared &S, float2 *b0, float
 // CG row pass: times gamma (apply S), or times beta (the final B^{-1} E y,
 // whose spectrum is added to the one written at the right-hand side).
 template <bool BETA>
-__device__ void nc_filter_rows(const NcorrTx &a, NcShared &S, float2 *b0, float2 *b1)
+__device__ void nc_filter_rows(const NcorrTx &a, const TxCtx &X, float2 *b0, float2 *b1)
 {
-    const TxCtx &X = S.X;
     const float s2 = X.s2;
     const int n = X.L.n, m = X.L.m;
     float *spec = (BETA && a.spec_out) ? a.spec_out + X.o : nullptr;
@@ -1351,9 +1369,8 @@ __device__ void nc_filter_rows(const NcorrTx &a, NcShared &S, float2 *b0, float2
 
 // CG inverse column pass: q = E^T (...) (gather), or x += (...) (final).
 template <bool ADD>
-__device__ void nc_gather_cols(const NcorrTx &a, NcShared &S, float2 *b0, float2 *b1, float *qv)
+__device__ void nc_gather_cols(const NcorrTx &a, const TxCtx &X, float2 *b0, float2 *b1, float *qv)
 {
-    const TxCtx &X = S.X;
     const int64_t o = X.o, obase = a.off[a.q0], w_lo = obase >> 5;
     float *xq = a.x_out + X.o;
     const ColGeo G(X.L, X.blk);
@@ -1622,11 +1639,15 @@ __device__ void nc_cg_update(const NcorrTx &a, NcShared &S, int q, float *gb, in
     }
 }
 
-// Loop over the launch's column or row items, skipping detscans that fn
-// should not visit (keep(mode)).
+// ---------------------------------------------------------------------------
+// The n_corr kernels.  Each pass is its own launch over the tiles of the
+// launch range (skipping detscans that the pass does not concern); the CG
+// runs a fixed number of iterations as launches of their own, and a
+// cooperative tail kernel finishes any detscan still iterating (grid
+// barriers between its passes; it returns at once when none is).
+// ---------------------------------------------------------------------------
 template <class Keep, class Fn>
-__device__ __forceinline__ void nc_items(const NcorrTx &a, NcShared &S, bool rows, uint64_t, int &cur, Keep keep,
-                                         Fn fn)
+__device__ __forceinline__ void nc_items(const NcorrTx &a, TxCtx &X, bool rows, int &cur, Keep keep, Fn fn)
 {
     const int2 *items = rows ? a.rowitems : a.colitems;
     const int j0 = rows ? a.row_off[a.q0] : a.col_off[a.q0];
@@ -1637,108 +1658,192 @@ __device__ __forceinline__ void nc_items(const NcorrTx &a, NcShared &S, bool row
         const int2 w = items[it];
         const int md = a.cgs[w.x].mode;
         if (!keep(md)) continue;
-        tx_begin(S.X, a.txl, a.q_tx, a.off, w.x, w.y, a.off[a.q0], a.ndet, a.fsamp, a.psd, a.gain, cur, a.qsc);
-        if (threadIdx.x == 0) { S.X.mode = md; S.X.koff = a.cgs[w.x].koff; }
+        tx_begin(X, a.txl, a.q_tx, a.off, w.x, w.y, a.off[a.q0], a.ndet, a.fsamp, a.psd, a.gain, cur, a.qsc);
+        if (threadIdx.x == 0) { X.mode = md; X.koff = a.cgs[w.x].koff; }
         __syncthreads();
         fn();
     }
 }
+__device__ __forceinline__ bool nc_all(int) { return true; }
+__device__ __forceinline__ bool nc_active(int md) { return md == CG_ACTIVE; }
+__device__ __forceinline__ bool nc_ran(int md) { return md == CG_DONE; }
 
-__global__ void __launch_bounds__(TX_T, 2) k_ncorr_tx(NcorrTx a)
+__global__ void __launch_bounds__(TX_T) k_nc_flag_count(NcorrTx a)
 {
-    extern __shared__ __align__(16) float2 tx_smem[];
     __shared__ NcShared S;
-    cgrp::grid_group grid = cgrp::this_grid();
-    float2 *b0 = tx_smem, *b1 = tx_smem + TX_TILE;
-    float *gb = reinterpret_cast<float *>(tx_smem);
-    const uint64_t gi = a.rng.gibbs_iter_dev ? *a.rng.gibbs_iter_dev : a.rng.gibbs_iter;
-    int cur = -1;
-    // 1. flag index
-    nc_flag_prefix(a, S, grid);
+    nc_flag_count(a, S);
+}
+__global__ void k_nc_flag_scan(NcorrTx a, int G)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    int64_t acc = 0;
+    for (int c = 0; c < G; ++c) { const int64_t v = a.chunk[c]; a.chunk[c] = acc; acc += v; }
+    a.chunk[G] = acc;
+}
+__global__ void __launch_bounds__(TX_T) k_nc_flag_write(NcorrTx a)
+{
+    __shared__ NcShared S;
+    nc_flag_write(a, S);
+}
+__global__ void __launch_bounds__(TX_T) k_nc_index(NcorrTx a)
+{
+    __shared__ NcShared S;
     if (blockIdx.x == 0 && threadIdx.x == 0) { a.count[0] = 0; a.count[1] = 0; }
-    grid.sync();
     for (int q = a.q0 + blockIdx.x; q < a.q1; q += gridDim.x) {
         nc_detscan_index(a, S, q);
         __syncthreads();
     }
-    grid.sync();
-    // 2. x0 = B^{-1} b
-    auto all = [](int) { return true; };
-    nc_items(a, S, false, gi, cur, all, [&] { nc_rhs_cols(a, S, b0, b1, gi); });
-    grid.sync();
-    nc_items(a, S, true, gi, cur, all, [&] { nc_rhs_rows(a, S, b0, b1, gi); });
-    grid.sync();
-    nc_items(a, S, false, gi, cur, all, [&] { nc_x0_cols(a, S, b0, b1); });
-    grid.sync();
-    // 3. CG on the Schur complement
+}
+__global__ void __launch_bounds__(TX_T, 3) k_nc_rhs_cols(NcorrTx a)
+{
+    extern __shared__ __align__(16) float2 tx_smem[];
+    __shared__ TxCtx X;
+    const uint64_t gi = a.rng.gibbs_iter_dev ? *a.rng.gibbs_iter_dev : a.rng.gibbs_iter;
+    int cur = -1;
+    nc_items(a, X, false, cur, nc_all, [&] { nc_rhs_cols(a, X, tx_smem, tx_smem + TX_TILE, gi); });
+}
+__global__ void __launch_bounds__(TX_T, 3) k_nc_rhs_rows(NcorrTx a)
+{
+    extern __shared__ __align__(16) float2 tx_smem[];
+    __shared__ TxCtx X;
+    const uint64_t gi = a.rng.gibbs_iter_dev ? *a.rng.gibbs_iter_dev : a.rng.gibbs_iter;
+    int cur = -1;
+    nc_items(a, X, true, cur, nc_all, [&] { nc_rhs_rows(a, X, tx_smem, tx_smem + TX_TILE, gi); });
+}
+__global__ void __launch_bounds__(TX_T, 3) k_nc_x0_cols(NcorrTx a)
+{
+    extern __shared__ __align__(16) float2 tx_smem[];
+    __shared__ TxCtx X;
+    int cur = -1;
+    nc_items(a, X, false, cur, nc_all, [&] { nc_x0_cols(a, X, tx_smem, tx_smem + TX_TILE); });
+}
+__global__ void __launch_bounds__(TX_T, 3) k_nc_cg_init(NcorrTx a)
+{
+    extern __shared__ __align__(16) float2 tx_smem[];
+    __shared__ NcShared S;
     for (int q = a.q0 + blockIdx.x; q < a.q1; q += gridDim.x) {
         __syncthreads();
-        nc_cg_init(a, S, q, gb);
+        nc_cg_init(a, S, q, reinterpret_cast<float *>(tx_smem));
     }
-    grid.sync();
-    const CgVec V = cg_vecs(a);
-    auto active = [](int md) { return md == CG_ACTIVE; };
-    int par = 0;
-    for (;;) {
-        if (*reinterpret_cast<volatile int32_t *>(a.count + par) == 0) break;
-        nc_items(a, S, false, gi, cur, active, [&] { nc_scatter_cols(a, S, b0, b1, V.p); });
+}
+// One CG iteration (parity par: count[par] active detscans going in, the
+// update counts into count[par ^ 1]), or with FINAL the correction B^{-1} E y.
+template <bool FINAL>
+__global__ void __launch_bounds__(TX_T, 3) k_nc_scatter(NcorrTx a, int par)
+{
+    extern __shared__ __align__(16) float2 tx_smem[];
+    __shared__ TxCtx X;
+    if (!FINAL) {
         if (blockIdx.x == 0 && threadIdx.x == 0) a.count[par ^ 1] = 0;
+        if (*reinterpret_cast<volatile const int32_t *>(a.count + par) == 0) return;
+    }
+    const CgVec V = cg_vecs(a);
+    int cur = -1;
+    if (FINAL) nc_items(a, X, false, cur, nc_ran, [&] { nc_scatter_cols(a, X, tx_smem, tx_smem + TX_TILE, V.y); });
+    else nc_items(a, X, false, cur, nc_active, [&] { nc_scatter_cols(a, X, tx_smem, tx_smem + TX_TILE, V.p); });
+}
+template <bool FINAL>
+__global__ void __launch_bounds__(TX_T, 3) k_nc_filter(NcorrTx a, int par)
+{
+    extern __shared__ __align__(16) float2 tx_smem[];
+    __shared__ TxCtx X;
+    if (!FINAL && *reinterpret_cast<volatile const int32_t *>(a.count + par) == 0) return;
+    int cur = -1;
+    if (FINAL) nc_items(a, X, true, cur, nc_ran, [&] { nc_filter_rows<true>(a, X, tx_smem, tx_smem + TX_TILE); });
+    else nc_items(a, X, true, cur, nc_active, [&] { nc_filter_rows<false>(a, X, tx_smem, tx_smem + TX_TILE); });
+}
+template <bool FINAL>
+__global__ void __launch_bounds__(TX_T, 3) k_nc_gather(NcorrTx a, int par)
+{
+    extern __shared__ __align__(16) float2 tx_smem[];
+    __shared__ TxCtx X;
+    if (!FINAL && *reinterpret_cast<volatile const int32_t *>(a.count + par) == 0) return;
+    const CgVec V = cg_vecs(a);
+    int cur = -1;
+    if (FINAL) nc_items(a, X, false, cur, nc_ran, [&] { nc_gather_cols<true>(a, X, tx_smem, tx_smem + TX_TILE, nullptr); });
+    else nc_items(a, X, false, cur, nc_active, [&] { nc_gather_cols<false>(a, X, tx_smem, tx_smem + TX_TILE, V.q); });
+}
+__global__ void __launch_bounds__(TX_T, 3) k_nc_update(NcorrTx a, int par)
+{
+    extern __shared__ __align__(16) float2 tx_smem[];
+    __shared__ NcShared S;
+    if (*reinterpret_cast<volatile const int32_t *>(a.count + par) == 0) return;
+    for (int q = a.q0 + blockIdx.x; q < a.q1; q += gridDim.x) {
+        __syncthreads();
+        nc_cg_update(a, S, q, reinterpret_cast<float *>(tx_smem), a.count + (par ^ 1));
+    }
+}
+// The iterations left after the launched ones, in one cooperative launch.
+__global__ void __launch_bounds__(TX_T, 2) k_nc_tail(NcorrTx a, int par)
+{
+    extern __shared__ __align__(16) float2 tx_smem[];
+    __shared__ NcShared S;
+    cgrp::grid_group grid = cgrp::this_grid();
+    const CgVec V = cg_vecs(a);
+    int cur = -1;
+    for (;;) {
+        if (*reinterpret_cast<volatile const int32_t *>(a.count + par) == 0) break;
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.count[par ^ 1] = 0;
+        nc_items(a, S.X, false, cur, nc_active, [&] { nc_scatter_cols(a, S.X, tx_smem, tx_smem + TX_TILE, V.p); });
         grid.sync();
-        nc_items(a, S, true, gi, cur, active, [&] { nc_filter_rows<false>(a, S, b0, b1); });
+        nc_items(a, S.X, true, cur, nc_active, [&] { nc_filter_rows<false>(a, S.X, tx_smem, tx_smem + TX_TILE); });
         grid.sync();
-        nc_items(a, S, false, gi, cur, active, [&] { nc_gather_cols<false>(a, S, b0, b1, V.q); });
+        nc_items(a, S.X, false, cur, nc_active, [&] { nc_gather_cols<false>(a, S.X, tx_smem, tx_smem + TX_TILE, V.q); });
         grid.sync();
         for (int q = a.q0 + blockIdx.x; q < a.q1; q += gridDim.x) {
             __syncthreads();
-            nc_cg_update(a, S, q, gb, a.count + (par ^ 1));
+            nc_cg_update(a, S, q, reinterpret_cast<float *>(tx_smem), a.count + (par ^ 1));
         }
         grid.sync();
         par ^= 1;
     }
-    // 4. x = x0 + B^{-1} E y for every detscan that ran the CG
-    auto ran = [](int md) { return md == CG_DONE; };
-    nc_items(a, S, false, gi, cur, ran, [&] { nc_scatter_cols(a, S, b0, b1, V.y); });
-    grid.sync();
-    nc_items(a, S, true, gi, cur, ran, [&] { nc_filter_rows<true>(a, S, b0, b1); });
-    grid.sync();
-    nc_items(a, S, false, gi, cur, ran, [&] { nc_gather_cols<true>(a, S, b0, b1, nullptr); });
-    // iteration counts and the detscans left at x0
-    for (int q = a.q0 + blockIdx.x * TX_T + threadIdx.x; q < a.q1; q += gridDim.x * TX_T) {
-        const CgState cs = a.cgs[q];
-        if (a.iters) a.iters[q] = cs.it;
-        if (cs.mode == CG_OVER) set_status(a.status, q, TOD_ERR_NOT_CONVERGED);
-    }
+}
+// Iteration counts; detscans left at x0 for want of CG room are reported.
+__global__ void k_nc_finish(NcorrTx a)
+{
+    const int q = a.q0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= a.q1) return;
+    const CgState cs = a.cgs[q];
+    if (a.iters) a.iters[q] = cs.it;
+    if (cs.mode == CG_OVER) set_status(a.status, q, TOD_ERR_NOT_CONVERGED);
 }
 
 // ===========================================================================
 // launchers
 // ===========================================================================
 static size_t tx_smem_bytes(bool fp64) { return (fp64 ? sizeof(double2) : sizeof(float2)) * 2 * TX_TILE; }
+constexpr size_t kGbBytes = 5 * TX_GBCAP * sizeof(float);           // preconditioner staging
+constexpr int NC_LAUNCHED_ITERS = 3;                                // CG iterations as separate launches
+
+template <class K>
+static cudaError_t smem_attr(K k, size_t bytes) {
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+}
 
 cudaError_t setup_tx_kernels(Plan &p)
 {
     cudaError_t e;
     const size_t s32 = tx_smem_bytes(false), s64 = tx_smem_bytes(true);
-    if ((e = cudaFuncSetAttribute(k_gain_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32))) return e;
-    if ((e = cudaFuncSetAttribute(k_gain_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32))) return e;
-    if ((e = cudaFuncSetAttribute(k_gain_colsinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32))) return e;
-    if ((e = cudaFuncSetAttribute(k_ncorr_tx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32))) return e;
-    if ((e = cudaFuncSetAttribute(k_chi2_cols<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32)))
+    const size_t sgb = std::max(s32, kGbBytes);
+    if ((e = smem_attr(k_gain_cols, s32)) || (e = smem_attr(k_gain_rows, s32)) || (e = smem_attr(k_gain_colsinv, s32)))
         return e;
-    if ((e = cudaFuncSetAttribute(k_chi2_rows<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32)))
+    if ((e = smem_attr(k_chi2_cols<float2>, s32)) || (e = smem_attr(k_chi2_rows<float2>, s32)) ||
+        (e = smem_attr(k_chi2_colsinv<float2>, s32)))
         return e;
-    if ((e = cudaFuncSetAttribute(k_chi2_colsinv<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32)))
+    if ((e = smem_attr(k_chi2_cols<double2>, s64)) || (e = smem_attr(k_chi2_rows<double2>, s64)) ||
+        (e = smem_attr(k_chi2_colsinv<double2>, s64)))
         return e;
-    if ((e = cudaFuncSetAttribute(k_chi2_cols<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64)))
-        return e;
-    if ((e = cudaFuncSetAttribute(k_chi2_rows<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64)))
-        return e;
-    if ((e = cudaFuncSetAttribute(k_chi2_colsinv<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64)))
+    if ((e = smem_attr(k_nc_rhs_cols, s32)) || (e = smem_attr(k_nc_rhs_rows, s32)) ||
+        (e = smem_attr(k_nc_x0_cols, s32)) || (e = smem_attr(k_nc_cg_init, sgb)) ||
+        (e = smem_attr(k_nc_scatter<false>, s32)) || (e = smem_attr(k_nc_scatter<true>, s32)) ||
+        (e = smem_attr(k_nc_filter<false>, s32)) || (e = smem_attr(k_nc_filter<true>, s32)) ||
+        (e = smem_attr(k_nc_gather<false>, s32)) || (e = smem_attr(k_nc_gather<true>, s32)) ||
+        (e = smem_attr(k_nc_update, sgb)) || (e = smem_attr(k_nc_tail, sgb)))
         return e;
     int dev = 0, nsm = 0, per = 0;
     if ((e = cudaGetDevice(&dev))) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev))) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ncorr_tx, TX_T, s32))) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_nc_tail, TX_T, sgb))) return e;
     p.coop_grid = std::max(1, per) * nsm;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gain_rows, TX_T, s32))) return e;
     p.pass_grid = std::max(1, per) * nsm;
@@ -1757,19 +1862,17 @@ cudaError_t launch_tx_gain(const Plan &p, const float *d, const float *s, const 
     const int c0 = p.h_col_off[q0], c1 = p.h_col_off[q1], r0 = p.h_row_off[q0], r1 = p.h_row_off[q1];
     const size_t sm = tx_smem_bytes(false);
     k_det_scalars<<<(q1 - q0 + 127) / 128, 128, 0, st>>>(psd, nullptr, p.off, p.ndet, p.fsamp, q0, q1, p.qsc);
-    // column items' partials at part[c], row items' at part[ncol + r]
-    a.items = p.colitems; a.item0 = c0; a.nitems = c1 - c0;
-    k_gain_cols<<<grid_for(p, a.nitems), TX_T, sm, st>>>(a);
-    a.items = p.rowitems; a.item0 = r0; a.nitems = r1 - r0;
+    // column items' partials at part[4 c], row items' at part[4 (ncol + r)]
     double *cpart = p.part;
-    double *rpart = p.part + 4 * static_cast<int64_t>(p.h_col_off[p.nq] - 0);
-    a.part = rpart - 4 * static_cast<int64_t>(0);
+    double *rpart = p.part + 4 * static_cast<int64_t>(p.h_col_off[p.nq]);
+    a.items = p.colitems; a.item0 = c0; a.nitems = c1 - c0; a.part = cpart;
+    k_gain_cols<<<grid_for(p, a.nitems), TX_T, sm, st>>>(a);
+    a.items = p.rowitems; a.item0 = r0; a.nitems = r1 - r0; a.part = rpart;
     k_gain_rows<<<grid_for(p, a.nitems), TX_T, sm, st>>>(a);
     a.items = p.colitems; a.item0 = c0; a.nitems = c1 - c0; a.part = cpart;
     k_gain_colsinv<<<grid_for(p, a.nitems), TX_T, sm, st>>>(a);
-    const int nq = q1 - q0;
-    k_gain_fin<<<(nq + 255) / 256, 256, 0, st>>>(rpart, cpart, p.row_off, p.col_off, q0, q1, 0, 0, rng, mode, g, mu,
-                                                  sig, p.status);
+    k_gain_fin<<<(q1 - q0 + 255) / 256, 256, 0, st>>>(rpart, cpart, p.row_off, p.col_off, q0, q1, 0, 0, rng, mode,
+                                                      g, mu, sig, p.status);
     return cudaGetLastError();
 }
 
@@ -1837,9 +1940,43 @@ cudaError_t launch_tx_ncorr(const Plan &p, const float *d, const float *s, const
     a.xtab = p.use_prec ? p.xtab : nullptr; a.lvalid = p.lvalid;
     a.Y = sc.Y; a.wpre = sc.wpre; a.chunk = p.chunk; a.cgs = p.cgs; a.gblk = p.gblk; a.gnb = p.gnb;
     a.cgv = sc.cgv; a.cgcap = sc.cgcap; a.count = p.cg_count; a.qsc = p.qsc;
-    void *args[] = {&a};
-    return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_ncorr_tx), dim3(grid), dim3(TX_T), args,
-                                       tx_smem_bytes(false), st);
+    const size_t s32 = tx_smem_bytes(false), sgb = std::max(s32, kGbBytes);
+    const int nq = q1 - q0;
+    const int ncol = p.h_col_off[q1] - p.h_col_off[q0], nrow = p.h_row_off[q1] - p.h_row_off[q0];
+    const int gc = std::min(grid_for(p, ncol), grid), gr = std::min(grid_for(p, nrow), grid);
+    const int gq = std::min(nq, std::max(1, grid));
+    // flag index (the chunked scan uses the same grid for count and write)
+    const int gf = std::max(1, std::min(p.pass_grid, grid));
+    k_nc_flag_count<<<gf, TX_T, 0, st>>>(a);
+    k_nc_flag_scan<<<1, 1, 0, st>>>(a, gf);
+    k_nc_flag_write<<<gf, TX_T, 0, st>>>(a);
+    k_nc_index<<<gq, TX_T, 0, st>>>(a);
+    // x0 = B^{-1} b
+    k_nc_rhs_cols<<<gc, TX_T, s32, st>>>(a);
+    k_nc_rhs_rows<<<gr, TX_T, s32, st>>>(a);
+    k_nc_x0_cols<<<gc, TX_T, s32, st>>>(a);
+    // CG on the Schur complement
+    k_nc_cg_init<<<gq, TX_T, sgb, st>>>(a);
+    int par = 0;
+    for (int it = 0; it < NC_LAUNCHED_ITERS; ++it, par ^= 1) {
+        k_nc_scatter<false><<<gc, TX_T, s32, st>>>(a, par);
+        k_nc_filter<false><<<gr, TX_T, s32, st>>>(a, par);
+        k_nc_gather<false><<<gc, TX_T, s32, st>>>(a, par);
+        k_nc_update<<<gq, TX_T, sgb, st>>>(a, par);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int tail_par = par;
+    void *args[] = {&a, &tail_par};
+    e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_nc_tail), dim3(std::max(1, std::min(grid, p.coop_grid))),
+                                    dim3(TX_T), args, sgb, st);
+    if (e != cudaSuccess) return e;
+    // x = x0 + B^{-1} E y for every detscan that ran the CG
+    k_nc_scatter<true><<<gc, TX_T, s32, st>>>(a, 0);
+    k_nc_filter<true><<<gr, TX_T, s32, st>>>(a, 0);
+    k_nc_gather<true><<<gc, TX_T, s32, st>>>(a, 0);
+    k_nc_finish<<<(nq + 255) / 256, 256, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace tg
