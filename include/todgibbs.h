@@ -392,6 +392,14 @@ tod_status tod_bin_partial(tod_plan *p, const uint16_t *psi, const float *d, con
                            cudaStream_t stream);
 tod_status tod_combine_partials(const double *parts, int32_t nparts, int64_t npix_range, double *A_out,
                                 double *b_out, int32_t *hits_out, cudaStream_t stream);
+/* A7 on a range of npix_range pixels held by this process (the solve after
+ * the reduction above): the arithmetic and validity rule of tod_solve_maps,
+ * with every array of the range alone: A [npix_range][6], b [npix_range][3],
+ * hits [npix_range] in; map_out double[3][npix_range], map_f32_out
+ * float4[npix_range] or NULL, rcond_out, valid_out [npix_range] or NULL. */
+tod_status tod_solve_range(int64_t npix_range, const double *A, const double *b, const int32_t *hits, double rcond_min,
+                           double *map_out, void *map_f32_out, double *rcond_out, uint8_t *valid_out,
+                           cudaStream_t stream);
 
 /* A7 -- per-pixel solve (Sect. 5 table, "Map solution (Ax=b for each
  * pixel)"): m_p = A_p^{-1} b_p by FP64 3x3 Cholesky.  A pixel is valid iff

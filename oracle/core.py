@@ -590,6 +590,50 @@ def bin_maps(npix, pix, psi, resid, weight) -> tuple:
     return A, b
 
 
+def bin_partials(npix, pix, psi, resid, weight) -> tuple:
+    """The ten per-pixel sums of bin_maps (A 6, b 3, hits) as exact partial
+    sums: each the correctly rounded sum of its terms (math.fsum) and the
+    correctly rounded remainder, hi + lo, so that partial sums of separate
+    sample sets add without a rounding of their own (the reduction of a
+    band split over processes).  Returns (hi, lo), each float64[npix, 10]."""
+    c, sn = psi_trig_table()
+    pix = np.asarray(pix, np.int64)
+    b = np.asarray(psi, np.int64)
+    w, v = weight
+    cc, ss = c[b], sn[b]
+    terms = np.stack([w, w * cc, w * ss, w * cc * cc, w * cc * ss, w * ss * ss,
+                      v * resid, v * cc * resid, v * ss * resid, (np.asarray(w) > 0).astype(np.float64)], axis=1)
+    order = np.argsort(pix, kind="stable")
+    ps = pix[order]
+    edges = np.searchsorted(ps, np.arange(npix + 1))
+    hi = np.zeros((npix, 10))
+    lo = np.zeros((npix, 10))
+    for p in range(npix):
+        sel = order[edges[p]:edges[p + 1]]
+        if len(sel) == 0:
+            continue
+        for k in range(10):
+            col = terms[sel, k].tolist()
+            h = math.fsum(col)
+            hi[p, k] = h
+            lo[p, k] = math.fsum(col + [-h])
+    return hi, lo
+
+
+def combine_partials(partials) -> tuple:
+    """Partial sums (hi, lo) of several sample sets, in order, to the
+    correctly rounded totals: A float64[npix, 6], b float64[npix, 3],
+    hits int64[npix]."""
+    his = [h for h, _ in partials]
+    los = [l for _, l in partials]
+    npix = his[0].shape[0]
+    tot = np.zeros((npix, 10))
+    for p in range(npix):
+        for k in range(10):
+            tot[p, k] = math.fsum([x[p, k] for x in his] + [x[p, k] for x in los])
+    return tot[:, :6], tot[:, 6:9], np.rint(tot[:, 9]).astype(np.int64)
+
+
 def solve_maps(A6: np.ndarray, b3: np.ndarray, hits: np.ndarray, rcond_min: float = 1e-6) -> tuple:
     """m_p = A_p^{-1} b_p by an explicit 3x3 Cholesky factorisation.
     Reading of validity (the paper is silent): a pixel is solved iff it has

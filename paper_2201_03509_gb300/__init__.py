@@ -69,7 +69,8 @@ _lib = None
 
 SYMBOLS = ["tod_status_string", "tod_fft_length", "tod_huff_encode", "tod_huff_free",
            "tod_plan_create", "tod_plan_destroy", "tod_plan_info", "tod_plan_status",
-           "tod_plan_set_schedule", "tod_chi2", "tod_project_adjoint", "tod_project_f64", "tod_decode", "tod_project", "tod_sample_gain", "tod_sample_ncorr", "tod_bin",
+           "tod_plan_set_schedule", "tod_chi2", "tod_project_adjoint", "tod_project_f64", "tod_bin_partial",
+           "tod_combine_partials", "tod_solve_range", "tod_decode", "tod_project", "tod_sample_gain", "tod_sample_ncorr", "tod_bin",
            "tod_solve_maps", "tod_ncorr_static_setup", "tod_sample_ncorr_static", "tod_ncorr_prepare",
            "tod_sample_ncorr_prepared", "tod_sample_noise_psd", "tod_plan_set_ncorr_spectrum",
            "tod_plan_attach_data", "tod_decode_data", "tod_sample_gain_smooth"]
@@ -110,6 +111,9 @@ def lib():
         L.tod_chi2.argtypes = [_P, _P, _P, _P, _P, _P, _i32, _P, _P, _P, _P, _P, _P]
         L.tod_project_adjoint.argtypes = [_P, _P, _P, _i32, _P, _P, _P]
         L.tod_project_f64.argtypes = [_P, _P, _P, _P, _P, _P, _P]
+        L.tod_bin_partial.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P]
+        L.tod_combine_partials.argtypes = [_P, _i32, _i64, _P, _P, _P, _P]
+        L.tod_solve_range.argtypes = [_i64, _P, _P, _P, _f64, _P, _P, _P, _P, _P]
         L.tod_ncorr_static_setup.argtypes = [_P, _P]
         L.tod_sample_ncorr_static.argtypes = [_P, _P, _P, _P, _P, _P, Rng, _i32, _f64, _i32, _P, _P, _P]
         L.tod_ncorr_prepare.argtypes = [_P, _P, _P]
@@ -165,6 +169,21 @@ def huff_encode(ndet: int, nscan: int, offsets: np.ndarray, values: np.ndarray) 
     finally:
         lib().tod_huff_free(ctypes.byref(buf))
     return out
+
+
+def combine_partials(parts, A_out, b_out, hits_out, stream=None):
+    """Rank-order double-double sum of parts [nparts, np, 20] into A [np, 6],
+    b [np, 3], hits [np] (todgibbs.h: tod_combine_partials)."""
+    _check(lib().tod_combine_partials(_ptr(parts), int(parts.shape[0]), int(parts.shape[1]), _ptr(A_out),
+                                      _ptr(b_out), _ptr(hits_out), _stream(stream)), "tod_combine_partials")
+
+
+def solve_range(A, b, hits, rcond_min, map_out, map_f32_out=None, rcond_out=None, valid_out=None, stream=None):
+    """The per-pixel solve of a pixel range (todgibbs.h: tod_solve_range);
+    map_out float64 [3, np]."""
+    _check(lib().tod_solve_range(int(A.shape[0]), _ptr(A), _ptr(b), _ptr(hits), float(rcond_min), _ptr(map_out),
+                                 _ptr(map_f32_out), _ptr(rcond_out), _ptr(valid_out), _stream(stream)),
+           "tod_solve_range")
 
 
 def pack_flags(flagged: np.ndarray) -> np.ndarray:
@@ -416,6 +435,12 @@ class Plan:
 
     PREC_F32 = 0
     PREC_F64 = 1
+
+    def bin_partial(self, psi, d, ncorr, gain, flags, psd, part_out, stream=None):
+        """tod_bin with the per-pixel sums left as double-double pairs,
+        part_out float64 [npix, 20] (todgibbs.h: tod_bin_partial)."""
+        _check(lib().tod_bin_partial(self._h, _ptr(psi), _ptr(d), _ptr(ncorr), _ptr(gain), _ptr(flags), _ptr(psd),
+                                     _ptr(part_out), _stream(stream)), "tod_bin_partial")
 
     def chi2(self, d, s, gain, flags, psd, chi2_out, dgain_out, total_out, dpsd_out, v_out=None,
              precision: int = 0, stream=None):

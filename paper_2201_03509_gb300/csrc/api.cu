@@ -1145,6 +1145,15 @@ tod_status tod_combine_partials(const double *parts, int32_t nparts, int64_t npi
     return to_status(launch_combine(parts, nparts, npix_range, A_out, b_out, hits_out, stream));
 }
 
+tod_status tod_solve_range(int64_t npix_range, const double *A, const double *b, const int32_t *hits, double rcond_min,
+                           double *map_out, void *map_f32_out, double *rcond_out, uint8_t *valid_out,
+                           cudaStream_t stream)
+{
+    if (npix_range < 0 || npix_range >= (int64_t(1) << 31) || !A || !b || !hits || !map_out) return TOD_ERR_ARG;
+    return to_status(launch_solve_n(npix_range, A, b, hits, rcond_min, map_out, static_cast<float4 *>(map_f32_out),
+                                    rcond_out, valid_out, stream));
+}
+
 tod_status tod_chi2(tod_plan *pl, const float *d, const void *s, const double *gain, const uint32_t *flags,
                     const double *psd, int32_t precision, double *chi2_out, double *dgain_out, double *total_out,
                     double *dpsd_out, void *v_out, cudaStream_t stream)

@@ -225,6 +225,9 @@ cudaError_t launch_combine(const double *parts, int nparts, int64_t np, double *
 // P^T (g y): out_p = sum over the samples of pixel p of g_q y_t (1, cos 2psi, sin 2psi)
 cudaError_t launch_project_adjoint(const Plan &p, const uint16_t *psi, const void *y, bool fp64, const double *gain,
                                    double *out, cudaStream_t st);
+// the solve of npix pixels (map as [3][npix], outputs indexed like the inputs)
+cudaError_t launch_solve_n(int64_t npix, const double *A, const double *b, const int32_t *hits, double rcond_min,
+                           double *map, float4 *map32, double *rcond, uint8_t *valid, cudaStream_t st);
 cudaError_t launch_solve(const Plan &p, const double *A, const double *b, const int32_t *hits,
                          double rcond_min, double *map, float4 *map32, double *rcond,
                          uint8_t *valid, cudaStream_t st);

@@ -318,6 +318,8 @@ k_combine(const double *__restrict__ parts, int nparts, int64_t np, double *__re
 // ---------------------------------------------------------------------------
 // A7: FP64 3x3 Cholesky per pixel, validity by hits and Hadamard ratio.
 // ---------------------------------------------------------------------------
+// Pixels [0, npix) of A, b, hits (a whole map, or one range of it: the
+// outputs are indexed like the inputs).
 __global__ void __launch_bounds__(256)
 k_solve(const double *__restrict__ A, const double *__restrict__ b, const int32_t *__restrict__ hits,
         int npix, double rcond_min, double *__restrict__ map, float4 *__restrict__ map32,
@@ -408,8 +410,15 @@ cudaError_t launch_solve(const Plan &p, const double *A, const double *b, const 
                          double rcond_min, double *map, float4 *map32, double *rcond,
                          uint8_t *valid, cudaStream_t st)
 {
-    const int nb = (p.npix + 255) / 256;
-    k_solve<<<nb, 256, 0, st>>>(A, b, hits, p.npix, rcond_min, map, map32, rcond, valid);
+    return launch_solve_n(p.npix, A, b, hits, rcond_min, map, map32, rcond, valid, st);
+}
+
+cudaError_t launch_solve_n(int64_t npix, const double *A, const double *b, const int32_t *hits, double rcond_min,
+                           double *map, float4 *map32, double *rcond, uint8_t *valid, cudaStream_t st)
+{
+    if (npix <= 0) return cudaSuccess;
+    const int nb = static_cast<int>((npix + 255) / 256);
+    k_solve<<<nb, 256, 0, st>>>(A, b, hits, static_cast<int>(npix), rcond_min, map, map32, rcond, valid);
     return cudaGetLastError();
 }
 
