@@ -1,12 +1,19 @@
 """Throughput of the Gibbs TOD step (decode -> project -> gain -> n_corr ->
-bin -> solve) on synthetic LFI-30-GHz-shaped data.
+bin -> solve) on synthetic Planck-LFI-shaped data.
+
+The headline workload is the batched 70 GHz-like band: 12 detectors x 2000
+scans of U[150k, 300k] samples at 78.8 Hz, Nside 1024 (5.3e9 samples per
+step).  The same step on the 30 GHz-like band and the added rows (noise
+PSD step, compressed TOD and flags, smooth gain prior) are measured in a
+secondary section.
 
 Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on a
 bounded sample of the same workload instead.  Launched by torchrun for
-N > 1 GPUs: every rank runs an independent replica of the band (the step
-shards by detscan with no exchange but the final map reduction, which this
-single-band benchmark replicates), and the max time over ranks is
-reported.
+N > 1 GPUs, the band is split into contiguous scan ranges of nearly equal
+sample counts, one per rank; every rank runs its scans' step and the
+per-pixel normal equations are reduced over the ranks by pixel range (the
+one exchange of the step), solved per range and gathered; the max time
+over ranks is reported.
 """
 from __future__ import annotations
 
@@ -25,7 +32,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "TOD samples/s per Gibbs TOD step"
-CONFIG_NAME = "lfi30"
+WORKLOAD = "lfi70"
+SECONDARY = "lfi30"
 
 
 def _dist():
@@ -111,14 +119,16 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# DRAM bytes of one n_corr call per TOD sample, from the ncu capture of
-# k_ncorr summarised in profiles/k_ncorr_lfi30_400detscans.md (400 detscans
-# of the 30 GHz band; scaled to a full launch by samples, since the kernel
-# moves each sample's d, s and n_corr once and its scratch in proportion),
-# valid only while the kernel's sources hash to the digest taken with it.
-NCORR_TRAFFIC = {"bytes_per_sample": 15.82,
-                 "sources": ["csrc/k_dct.cu", "csrc/common.cuh", "csrc/internal.cuh", "csrc/api.cu"],
-                 "sha256": "a01eb296836fd5ea94b8c3d7cc90763b7bf552c1645ee3220d546fcab52d24f1"}
+# DRAM bytes (read + write) per TOD sample of the n_corr draw's kernels from
+# an ncu capture of the same draw on a slice of the 70 GHz band (the
+# summary under profiles/ names the command), at the capture's mean CG
+# iteration count; scaled to a full draw by samples (every pass moves each
+# sample's values once) with the CG passes' share adjusted to the draw's
+# own mean count.  Valid only while the kernels' sources hash to the digest
+# taken with it; otherwise the traffic is reported as null.
+NCORR_TRAFFIC = {"bytes_per_sample": None, "cg_iters_mean": None,
+                 "sources": ["csrc/k_tx.cu", "csrc/fft_reg.cuh", "csrc/common.cuh", "csrc/internal.cuh"],
+                 "sha256": None}
 
 
 def ncorr_sources_digest() -> str | None:
@@ -132,78 +142,119 @@ def ncorr_sources_digest() -> str | None:
     return h.hexdigest()
 
 
-def make_workload(nscan: int | None):
+def build_band(cfg, scans=None):
+    """The band (or the listed scans of it) generated straight into
+    concatenated arrays and ingested by the library; the uncompressed
+    pointing is dropped once it is encoded."""
     import synth
     import paper_2201_03509_gb300 as tg
-    cfg = synth.CONFIGS[CONFIG_NAME]
-    if nscan:
-        cfg = synth.scaled(cfg, nscan=nscan)
-    band = synth.make_band(cfg)
-    ing = tg.ingest(band)
-    return cfg, band, ing
+    arr = synth.make_band_arrays(cfg, tg.kept_lengths(cfg), scans=scans)
+    ing = tg.ingest_arrays(arr)
+    arr.pix = arr.psi = None
+    return arr, ing
 
 
 # ---------------------------------------------------------------------------
-# per-stage algorithmic work (compulsory bytes per stage)
+# algorithmic work per stage (compulsory HBM bytes of this design)
 # ---------------------------------------------------------------------------
-def stage_bytes(N, nq, npix, npairs, comp_bytes):
-    """Compulsory HBM bytes of each stage for one step."""
+def stage_bytes(N, npix, npairs, comp_bytes, ncorr_bytes):
+    """Compulsory HBM bytes of each stage for one step.  The gain and n_corr
+    transforms go through one complex intermediate of 4 bytes per sample
+    between their column and row passes (the two-pass transform of the
+    measurement plan)."""
     return {
         "decode": comp_bytes + 6.0 * N,                 # streams in, pix int32 + psi uint16 out
         "project": 6.0 * N + 4.0 * N,                   # pix, psi in, s out (map gathers hit L2)
-        "gain": 8.0 * N + N / 8.0,                      # s, d, flags
-        "ncorr": 12.0 * N + N / 8.0,                    # s, d in, n_corr out, flags
+        # columns: s, flags in, Y out; rows: Y in and out; inverse columns: Y, d, flags in
+        "gain": ((4.0 + 0.125 + 4.0) + 8.0 + (4.0 + 4.0 + 0.125)) * N,
+        "ncorr": ncorr_bytes,
         "bin": 10.0 * N + N / 8.0 + 6.0 * N + 80.0 * npairs,   # d, n_corr, psi, flags, load order + slot, runs out
-        "reduce": 80.0 * npairs + 76.0 * npix,
         "solve": 76.0 * npix + 61.0 * npix,
     }
 
 
-def run_ours(args):
+def ncorr_algorithmic_bytes(lens, iters, flagged):
+    """HBM bytes of one n_corr draw: right-hand side (columns: d, s, flags
+    in, Y out; rows: Y in and out; inverse columns: Y, flags in, x0 out),
+    then per CG iteration of a flagged detscan (scatter: Y out; rows: Y in
+    and out; gather: Y in, flags) and its correction (scatter; rows;
+    inverse columns: Y, x0 in, x out)."""
+    lens = np.asarray(lens, np.float64)
+    b = lens * ((8.0 + 0.125 + 4.0) + 8.0 + (4.0 + 0.125 + 4.0))
+    b += np.where(flagged, lens * ((4.0 + 8.0 + 4.0 + 0.125) * np.asarray(iters) + (4.0 + 8.0 + 12.0)), 0.0)
+    return float(b.sum())
+
+
+def _event():
+    import torch
+    return torch.cuda.Event(enable_timing=True)
+
+
+def measure_step(args, cfg, arr, ing, local, rank, ws, label="main"):
+    """Build the plan and step of one band (this rank's scan range under
+    torchrun) and time it."""
     import torch
     import paper_2201_03509_gb300 as tg
     from paper_2201_03509_gb300.step import GibbsTODStep
-
-    rank, ws = _dist()
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
+    nscan_local = (len(ing["offsets"]) - 1) // cfg.ndet
+    m4 = np.zeros((arr.npix, 4), np.float32)
+    m4[:, :3] = arr.map_tqu.T
+    map_in = torch.from_numpy(m4).cuda()
+    tuned = None
+    tp, rmax = 0, 0
+    if not args.no_autotune and label == "main":
+        # measured tile shape (column pairs, largest radix) on the band's first scans
+        from paper_2201_03509_gb300.autotune import autotune
+        tp, rmax, tms = autotune(cfg.nside, cfg.ndet, nscan_local, cfg.fsamp, ing["offsets"], ing["pix_streams"],
+                                 ing["psi_streams"], ing["tod"], ing["flag_words"], arr.psd, map_in,
+                                 nscan_sample=args.tune_scans, device=local)
+        tuned = {"tile_pairs": tp, "max_radix": rmax,
+                 "candidates_ms": {"T%d_R%d" % k: round(v, 3) for k, v in sorted(tms.items())}}
+    plan = tg.Plan(cfg.nside, cfg.ndet, nscan_local, cfg.fsamp, ing["offsets"], ing["pix_streams"],
+                   ing["psi_streams"], tile_pairs=tp, device=local, max_radix=rmax)
+    shard = None
     if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    tg.build() if rank == 0 or ws == 1 else None
+        from paper_2201_03509_gb300.shard import ShardedMaps
+        shard = ShardedMaps(plan, ws, rank)
+    step = GibbsTODStep(plan, arr.psd, ing["flag_words"], cg_tol=args.cg_tol, shard=shard)
+    step.set_tod(ing["tod"])
+    N, nq, npix = plan.N, plan.nq, plan.npix
+    stream = torch.cuda.current_stream()
+
+    def one(it):
+        step.run(map_in, tg.Rng(args.seed, 0, it), tg.MODE_DRAW)
+
+    for w in range(args.warmup):
+        one(10_000 + w)
+    torch.cuda.synchronize()
+    plan.status()
+    sampler = ClockSampler(local)
+    sampler.start()
     if ws > 1:
         import torch.distributed as dist
         dist.barrier()
-    t_setup = time.time()
-    cfg, band, ing = make_workload(args.nscan)
-    m4 = np.zeros((band.npix, 4), np.float32)
-    m4[:, :3] = band.map_tqu.T
-    map_in = torch.from_numpy(m4).cuda()
-    tuned = None
-    cs, rmax = 0, 0
-    if not args.no_autotune:
-        # measured launch shape (cluster size, largest radix) on the band's first scans
-        from paper_2201_03509_gb300.autotune import autotune
-        cs, rmax, tms = autotune(cfg.nside, cfg.ndet, cfg.nscan, cfg.fsamp, ing["offsets"], ing["pix_streams"],
-                                 ing["psi_streams"], ing["tod"], ing["flag_words"], band.psd, map_in,
-                                 device=local)
-        tuned = {"tile_pairs": cs, "max_radix": rmax,
-                 "candidates_ms": {"C%d_R%d" % k: round(v, 3) for k, v in sorted(tms.items())}}
-    plan = tg.Plan(cfg.nside, cfg.ndet, cfg.nscan, cfg.fsamp, ing["offsets"], ing["pix_streams"],
-                   ing["psi_streams"], tile_pairs=cs, device=local, max_radix=rmax)
-    info = plan.info()
-    step = GibbsTODStep(plan, band.psd, ing["flag_words"], cg_tol=args.cg_tol)
-    step.set_tod(ing["tod"])
-    N, nq, npix = plan.N, plan.nq, plan.npix
-    setup_s = time.time() - t_setup
-    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    t0, t1 = _event(), _event()
+    t0.record(stream)
+    for k in range(args.steps):
+        one(k)                     # the step as a user runs it (GibbsTODStep.run)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clocks = sampler.stop()
+    elapsed = max_over_ranks(t0.elapsed_time(t1) / 1e3)
+    iters = step.cg_iters.cpu().numpy()
 
-    def one(it, timed_events=None):
-        rng = tg.Rng(args.seed, 0, it)
-        if timed_events is None:
-            step.run(map_in, rng, tg.MODE_DRAW)
-            return
-        ev = timed_events
+    # per-stage times: the step's calls one by one on one stream with events
+    # between them (the n_corr preparation, which the step overlaps with
+    # decode, projection and gain, as its own stage), after the timed region
+    names = ["decode", "project", "gain", "ncorr_prepare", "ncorr", "bin", "solve"]
+    evs = [[_event() for _ in range(8)] for _ in range(args.steps)]
+    for k in range(args.steps):
+        rng = tg.Rng(args.seed, 0, 20_000 + k)
+        ev = evs[k]
         p = step.plan
         ev[0].record(stream)
         p.decode(step.pix, step.psi)
@@ -221,67 +272,36 @@ def run_ours(args):
         ev[6].record(stream)
         p.solve_maps(step.A, step.b, step.hits, step.rcond_min, step.map, step.map32, step.rcond, step.valid)
         ev[7].record(stream)
-
-    for w in range(args.warmup):
-        one(10_000 + w)
-    torch.cuda.synchronize()
-    plan.status()
-    sampler = ClockSampler(local)
-    sampler.start()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    torch.cuda.synchronize()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for k in range(args.steps):
-        one(k)                     # the step as a user runs it (GibbsTODStep.run)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    clocks = sampler.stop()
-    elapsed = t0.elapsed_time(t1) / 1e3
-    # per-stage times: the same calls in sequence on one stream with events
-    # between them (the n_corr preparation, which the step overlaps with
-    # decode, projection and gain, as its own stage), after the timed region
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(args.steps)]
-    for k in range(args.steps):
-        one(args.steps + k, evs[k])
     torch.cuda.synchronize()
     st = plan.status(raise_on_error=False)
-    names = ["decode", "project", "gain", "ncorr_prepare", "ncorr", "bin", "solve"]
     stage_ms = {nm: float(np.mean([evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps)]))
                 for i, nm in enumerate(names)}
-    iters = step.cg_iters.cpu().numpy()
-    elapsed = max_over_ranks(elapsed)
+    iters_stage = step.cg_iters.cpu().numpy()
 
     # the same step captured in a CUDA graph (iteration read on the device)
     graph_ms = None
-    try:
-        step.capture(map_in, args.seed, 0, tg.MODE_DRAW)
-        for k in range(2):
-            step.replay(30_000 + k)
-        torch.cuda.synchronize()
-        g0 = torch.cuda.Event(enable_timing=True)
-        g1 = torch.cuda.Event(enable_timing=True)
-        g0.record(stream)
-        for k in range(args.steps):
-            step.replay(40_000 + k)
-        g1.record(stream)
-        torch.cuda.synchronize()
-        graph_ms = g0.elapsed_time(g1) / args.steps
-    except Exception as ex:          # report, do not hide
-        graph_ms = "capture failed: %s" % ex
-    # the plain per-scan path: one cluster launch per detscan per stage
+    if not args.no_graph and ws == 1:
+        try:
+            step.capture(map_in, args.seed, 0, tg.MODE_DRAW)
+            for k in range(2):
+                step.replay(30_000 + k)
+            torch.cuda.synchronize()
+            g0, g1 = _event(), _event()
+            g0.record(stream)
+            for k in range(args.steps):
+                step.replay(40_000 + k)
+            g1.record(stream)
+            torch.cuda.synchronize()
+            graph_ms = g0.elapsed_time(g1) / args.steps
+            step.graph = None
+        except Exception as ex:          # report, do not hide
+            graph_ms = "capture failed: %s" % ex
+    # the plain per-scan path: every pass launched once per detscan
     plain_ms = None
-    if not args.no_plain:
+    if not args.no_plain and label == "main":
         plan.set_schedule(plan.SCHED_PER_SCAN)
         torch.cuda.synchronize()
-        p0 = torch.cuda.Event(enable_timing=True)
-        p1 = torch.cuda.Event(enable_timing=True)
+        p0, p1 = _event(), _event()
         p0.record(stream)
         step.run(map_in, tg.Rng(args.seed, 0, 50_000), tg.MODE_DRAW)
         p1.record(stream)
@@ -289,18 +309,24 @@ def run_ours(args):
         plain_ms = p0.elapsed_time(p1)
         plan.set_schedule(plan.SCHED_PERSISTENT)
 
-    # end to end through the public API with host buffers
-    d_host = torch.from_numpy(ing["tod"]).pin_memory()
+    # end to end through the public API with host buffers: every step's d
+    # copied in from page-locked host memory (double-buffered, the copy for
+    # step k+1 under step k) and the map and gains copied out
+    d_host = torch.from_numpy(ing["tod"])
+    registered = False
+    try:
+        rc = torch.cuda.cudart().cudaHostRegister(d_host.data_ptr(), d_host.numel() * 4, 0)
+        registered = int(rc) == 0
+    except Exception:
+        registered = False
+    if not registered:
+        d_host = d_host.pin_memory()
     map_host = torch.empty((3, npix), dtype=torch.float64).pin_memory()
     gain_host = torch.empty(nq, dtype=torch.float64).pin_memory()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    # every step's d is copied from pinned host memory; the copy for step k+1
-    # runs on a second stream while step k computes (double-buffered d); one
-    # untimed step first sets up the second buffer and the copy stream
     step.prefetch_tod(d_host)
     step.run(map_in, tg.Rng(args.seed, 0, 19_999), tg.MODE_DRAW)
     torch.cuda.synchronize()
+    e0, e1 = _event(), _event()
     e0.record(stream)
     step.prefetch_tod(d_host)
     for k in range(args.steps):
@@ -312,10 +338,161 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    if registered:
+        torch.cuda.cudart().cudaHostUnregister(d_host.data_ptr())
 
-    # row A10 (outside the step's value): the n_corr draw writing its
-    # spectra, then the noise-PSD Metropolis step on them
-    psd_info = None
+    off = ing["offsets"]
+    lens = np.diff(off)
+    fl = ing["flags"]
+    flagged = np.array([bool(fl[int(off[q]):int(off[q + 1])].any()) for q in range(nq)])
+    return dict(plan=plan, step=step, map_in=map_in, N=N, nq=nq, npix=npix, elapsed=elapsed, e2e_s=e2e_s,
+                stage_ms=stage_ms, iters=iters, iters_stage=iters_stage, clocks=clocks, graph_ms=graph_ms,
+                plain_ms=plain_ms, tuned=tuned, status_errors=int(np.count_nonzero(st)), lens=lens,
+                flagged=flagged,
+                comp_bytes=int(ing["pix_streams"]["words"].nbytes + ing["psi_streams"]["words"].nbytes),
+                npairs=int(getattr(plan, "npairs", 0) or 0))
+
+
+def roofline_and_stages(res, peaks, peak_src):
+    N, npix = res["N"], res["npix"]
+    ncorr_b = ncorr_algorithmic_bytes(res["lens"], res["iters_stage"], res["flagged"])
+    byts = stage_bytes(N, npix, res["npairs"], res["comp_bytes"], ncorr_b)
+    stage_ms = res["stage_ms"]
+    stage_gbs = {k: (byts[k] / (stage_ms[k] / 1e3) / 1e9 if k in byts else None) for k in stage_ms}
+    dom = max(("gain", "ncorr", "bin", "decode", "project"), key=lambda k: stage_ms[k])
+    pk = float(peaks["hbm_gbs"])
+    ach = byts[dom] / (stage_ms[dom] / 1e3) / 1e9
+    traffic = None
+    if dom == "ncorr" and NCORR_TRAFFIC["sha256"] and ncorr_sources_digest() == NCORR_TRAFFIC["sha256"]:
+        adj = 16.25 * (float(np.mean(res["iters_stage"])) - NCORR_TRAFFIC["cg_iters_mean"])
+        traffic = (NCORR_TRAFFIC["bytes_per_sample"] + adj) * N
+    roof = {"kernel": "%s stage (its pass kernels)" % dom, "bound": "hbm", "achieved": ach, "peak": pk,
+            "unit": "GB/s", "frac": ach / pk, "traffic": traffic, "traffic_unit": "bytes per call",
+            "algorithmic_bytes": byts[dom], "peak_source": "%s hbm_gbs (MEASURED_PEAKS.json)" % peak_src}
+    return roof, stage_gbs
+
+
+def oracle_errors(args, cfg, arr, ing, res, nsample=3):
+    """Error of each output against the FP64 oracle on sampled detscans of
+    the band (the first, the longest, the most flagged), from the inputs of
+    the last per-stage step: decoded pointing (mismatching values),
+    projection, gain mean and draw, n_corr (relative l2)."""
+    import oracle
+    step = res["step"]
+    off = ing["offsets"]
+    nq = len(off) - 1
+    lens = np.diff(off)
+    nfl = np.array([int(ing["flags"][int(off[q]):int(off[q + 1])].sum()) for q in range(nq)])
+    qs = sorted({0, int(np.argmax(lens)), int(np.argmax(nfl))})[:nsample]
+    it = 20_000 + args.steps - 1
+    pix = step.pix.cpu().numpy()
+    psi = step.psi.cpu().numpy().view(np.uint16)
+    s32 = step.s.cpu().numpy()
+    gains = step.gain.cpu().numpy()
+    mus = step.mu.cpu().numpy()
+    ncorr = step.ncorr.cpu().numpy()
+    m_in = res["map_in"].cpu().numpy()[:, :3].T.astype(np.float64)
+    errs = {"decode_mismatches": 0, "project": 0.0, "gain_mean": 0.0, "gain": 0.0, "ncorr": 0.0}
+    for q in qs:
+        a, b = int(off[q]), int(off[q + 1])
+        n = b - a
+        det = q % cfg.ndet
+        pr = oracle.decode_detscan(ing["pix_streams"], q, n, cfg.ndet)
+        qr = oracle.decode_detscan(ing["psi_streams"], q, n, cfg.ndet)
+        errs["decode_mismatches"] += int(np.count_nonzero(pr != pix[a:b]) + np.count_nonzero(qr != psi[a:b]))
+        sref = oracle.project(m_in, pr, qr)
+        errs["project"] = max(errs["project"], float(np.abs(s32[a:b] - sref).max() / np.abs(sref).max()))
+        s0, fk, al = arr.psd[det]
+        d = ing["tod"][a:b].astype(np.float64)
+        M = (~ing["flags"][a:b]).astype(np.float64)
+        P = oracle.noise_psd(n, cfg.fsamp, s0, fk, al)
+        g, mu, _ = oracle.sample_gain(s32[a:b].astype(np.float64), d, M, P,
+                                      oracle.gain_normal(args.seed, 0, q, it))
+        errs["gain_mean"] = max(errs["gain_mean"], abs(mus[q] - mu) / abs(mu))
+        errs["gain"] = max(errs["gain"], abs(gains[q] - g) / abs(g))
+        w1 = oracle.omega1(args.seed, 0, q, it, n)
+        w2 = oracle.omega2(args.seed, 0, q, it, n)
+        x, _ = oracle.sample_ncorr(d, s32[a:b].astype(np.float64), gains[q], M, s0, fk, al, cfg.fsamp, w1, w2)
+        errs["ncorr"] = max(errs["ncorr"], float(np.linalg.norm(ncorr[a:b] - x) / np.linalg.norm(x)))
+    errs["detscans"] = [int(q) for q in qs]
+    errs["norms"] = ("max over the detscans; decode: mismatching values; project: max |err| / max |ref|; "
+                     "gain: relative; ncorr: relative l2")
+    return errs
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores
+# ---------------------------------------------------------------------------
+_W = {}
+
+
+def _worker_init(cfg_dict, nscan, seed):
+    import synth
+    import oracle
+    from oracle import _huff
+    _huff.build()
+    cfg = synth.scaled(synth.BandConfig(**cfg_dict), nscan=nscan)
+    band = synth.make_band(cfg, threads=1)
+    _W.update(cfg=cfg, band=band, ing=oracle.ingest(band), seed=seed)
+
+
+def _worker_detscan(q):
+    import oracle
+    cfg, band, ing = _W["cfg"], _W["band"], _W["ing"]
+    oracle.gibbs_tod_step(ing, cfg, band.npix, band.map_tqu, band.psd, _W["seed"], 0, 0, detscans=[q])
+    return int(ing["offsets"][q + 1] - ing["offsets"][q])
+
+
+def cpu_baseline(args, cfg, budget_s=20.0):
+    """The FP64 oracle, as it stands, on the first detscans of the workload,
+    one detscan per task over a process pool of every host core."""
+    import dataclasses
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    cores = os.cpu_count() or 1
+    nq = min(args.cpu_detscans, cfg.ndet * cfg.nscan)
+    nscan = -(-nq // cfg.ndet)
+    ctx = mp.get_context("spawn")
+    with ProcessPoolExecutor(cores, mp_context=ctx, initializer=_worker_init,
+                             initargs=(dataclasses.asdict(cfg), nscan, args.seed)) as ex:
+        # one untimed task per worker: the workers build the sample first
+        list(ex.map(_worker_detscan, [0] * cores))
+        t = time.time()
+        done = samples = 0
+        q = 0
+        while q < nq and time.time() - t < budget_s:
+            batch = list(range(q, min(nq, q + cores)))
+            samples += sum(ex.map(_worker_detscan, batch))
+            done += len(batch)
+            q += len(batch)
+        el = time.time() - t
+    return {"value": samples / el, "unit": "samples/s", "cores": cores, "kind": "oracle",
+            "sample": "%d of %d detscans (%d samples) of the %s workload, one detscan per task on %d "
+                      "processes; FP64 numpy/scipy + C Huffman" % (done, cfg.ndet * cfg.nscan, samples,
+                                                                  cfg.name, cores),
+            "seconds": el, "nproc": cores}
+
+
+def secondary_section(args, local):
+    """The 30 GHz band's step and the added rows measured on it."""
+    import torch
+    import synth
+    import paper_2201_03509_gb300 as tg
+    from paper_2201_03509_gb300.step import GibbsTODStep
+    cfg = synth.CONFIGS[SECONDARY]
+    t_set = time.time()
+    arr, ing = build_band(cfg)
+    res = measure_step(args, cfg, arr, ing, local, 0, 1, label="secondary")
+    plan, step, map_in = res["plan"], res["step"], res["map_in"]
+    N, stream = res["N"], torch.cuda.current_stream()
+    peaks, peak_src = _peaks()
+    roof, stage_gbs = roofline_and_stages(res, peaks, peak_src)
+    out = {"workload": cfg.name, "samples_per_step": N, "ms_per_step": 1e3 * res["elapsed"] / args.steps,
+           "value": N * args.steps / res["elapsed"], "e2e_value": N * args.steps / res["e2e_s"],
+           "stage_ms": res["stage_ms"], "stage_gbs": stage_gbs, "roofline": roof,
+           "cg_iters_mean": float(res["iters"].mean()), "graph_ms_per_step": res["graph_ms"],
+           "setup_s": time.time() - t_set}
+    # row A10: the n_corr draw writing its spectra, then Metropolis steps
     if not args.no_psd:
         spec = torch.empty(N, dtype=torch.float32, device=step.d.device)
         psd_out = torch.empty_like(step.psd)
@@ -325,7 +502,7 @@ def run_ours(args):
         plan.ncorr_prepare(step.psd)
         ts = []
         for k in range(2):
-            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0, a1 = _event(), _event()
             a0.record(stream)
             plan.sample_ncorr_prepared(step.d, step.s, step.gain, step.flags, step.psd, rng, tg.MODE_DRAW,
                                        step.ncorr, step.cg_iters, step.cg_tol, step.cg_maxiter)
@@ -335,31 +512,30 @@ def run_ours(args):
         plan.set_ncorr_spectrum(None)
         nst = 10
         plan.sample_noise_psd(spec, step.psd, rng, nst, 2e-4, 2e-4, psd_out, acc)      # warm-up
-        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0, b1 = _event(), _event()
         b0.record(stream)
         plan.sample_noise_psd(spec, step.psd, rng, nst, 2e-4, 2e-4, psd_out, acc)
         b1.record(stream)
         torch.cuda.synchronize()
         plan.status()
-        psd_ms = b0.elapsed_time(b1)
-        per_eval = psd_ms / (nst + 1)
-        psd_info = {"ncorr_with_spectrum_ms": min(ts), "metropolis_steps": nst, "ms": psd_ms,
-                    "ms_per_evaluation": per_eval, "gbs_per_evaluation": 4.0 * N / (per_eval / 1e3) / 1e9,
-                    "accepted": acc.cpu().tolist()}
-
-    # compressed TOD and flags (outside the step's value): the same step
-    # decoding d and the flag mask on the device every step
-    ds_info = None
+        per_eval = b0.elapsed_time(b1) / (nst + 1)
+        out["noise_psd"] = {"ncorr_with_spectrum_ms": min(ts), "metropolis_steps": nst,
+                            "ms": b0.elapsed_time(b1), "ms_per_evaluation": per_eval,
+                            "gbs_per_evaluation": 4.0 * N / (per_eval / 1e3) / 1e9,
+                            "accepted": acc.cpu().tolist()}
+    # row A11: the step decoding d and the flag mask every step
     if not args.no_data_streams:
+        band = synth.make_band(cfg)
         t_enc = time.time()
         ingd = tg.ingest_data(band, ing["offsets"])
+        del band
         plan.attach_data(ingd["tod_streams"], ingd["tod_scale"], ingd["flag_streams"], ingd["flag_select"])
         enc_s = time.time() - t_enc
-        dstep = GibbsTODStep(plan, band.psd, None, cg_tol=args.cg_tol, data_streams=True)
+        dstep = GibbsTODStep(plan, arr.psd, None, cg_tol=args.cg_tol, data_streams=True)
         for k in range(args.warmup):
             dstep.run(map_in, tg.Rng(args.seed, 0, 70_000 + k), tg.MODE_DRAW)
         torch.cuda.synchronize()
-        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0, c1 = _event(), _event()
         c0.record(stream)
         for k in range(args.steps):
             dstep.run(map_in, tg.Rng(args.seed, 0, 70_100 + k), tg.MODE_DRAW)
@@ -370,7 +546,7 @@ def run_ours(args):
         for name, dd, ff in (("tod", dstep.d, None), ("flags", None, dstep.flags)):
             tt = []
             for _ in range(3):
-                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0, a1 = _event(), _event()
                 a0.record(stream)
                 plan.decode_data(dd, ff)
                 a1.record(stream)
@@ -380,24 +556,21 @@ def run_ours(args):
         plan.status()
         tod_bytes = int(ingd["tod_streams"]["words"].nbytes)
         flag_bytes = int(ingd["flag_streams"]["words"].nbytes)
-        ds_info = {"ms_per_step": ds_ms, "value": ws * N / (ds_ms / 1e3),
-                   "decode_tod_ms": dec["tod"], "decode_flags_ms": dec["flags"],
-                   "tod_bits_per_sample": 8.0 * tod_bytes / N, "flag_bits_per_sample": 8.0 * flag_bytes / N,
-                   "resident_bytes_per_sample": {"fp32_d_and_bitmask": 4.125,
-                                                 "compressed": (tod_bytes + flag_bytes) / N},
-                   "launches_per_step": dstep.launches_per_step, "ingest_s": enc_s}
+        out["data_streams"] = {"ms_per_step": ds_ms, "value": N / (ds_ms / 1e3), "decode_tod_ms": dec["tod"],
+                               "decode_flags_ms": dec["flags"], "tod_bits_per_sample": 8.0 * tod_bytes / N,
+                               "flag_bits_per_sample": 8.0 * flag_bytes / N,
+                               "resident_bytes_per_sample": {"fp32_d_and_bitmask": 4.125,
+                                                             "compressed": (tod_bytes + flag_bytes) / N},
+                               "launches_per_step": dstep.launches_per_step, "ingest_s": enc_s}
         del dstep
-
-    # joint gain draw under the smooth prior across scans (outside the step's
-    # value), from the last step's per-detscan conditionals
-    gs_info = None
+    # row A12: the joint gain draw under the smooth prior across scans
     if not args.no_gain_smooth:
         prior = torch.tensor([[1e-3, -2.0]] * plan.ndet, dtype=torch.float64, device=step.d.device)
         gsm = torch.empty_like(step.gain)
         gits = torch.zeros(plan.ndet, dtype=torch.int32, device=step.d.device)
         ts = []
         for k in range(4):
-            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0, a1 = _event(), _event()
             a0.record(stream)
             plan.sample_gain_smooth(step.mu, step.sigma, prior, tg.Rng(args.seed, 0, 80_000 + k), tg.MODE_DRAW,
                                     gsm, gits, cg_tol=1e-6)
@@ -405,106 +578,92 @@ def run_ours(args):
             torch.cuda.synchronize()
             ts.append(a0.elapsed_time(a1))
         plan.status()
-        gs_info = {"ms": min(ts[1:]), "cg_iters": gits.cpu().tolist(), "nscan": plan.nscan, "ndet": plan.ndet,
-                   "prior": {"sigma_g": 1e-3, "alpha_g": -2.0}, "cg_tol": 1e-6}
+        out["gain_smooth"] = {"ms": min(ts[1:]), "cg_iters": gits.cpu().tolist(), "nscan": plan.nscan,
+                              "ndet": plan.ndet, "prior": {"sigma_g": 1e-3, "alpha_g": -2.0}, "cg_tol": 1e-6}
+    plan.close()
+    return out
 
-    # roofline of the dominant stage
+
+def run_ours(args):
+    import torch
+    import synth
+    import paper_2201_03509_gb300 as tg
+
+    rank, ws = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    tg.build() if rank == 0 or ws == 1 else None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    t_setup = time.time()
+    cfg = synth.CONFIGS[args.workload]
+    if args.nscan:
+        cfg = synth.scaled(cfg, nscan=args.nscan)
+    scans = None
+    if ws > 1:
+        # contiguous scan ranges of nearly equal sample counts
+        from paper_2201_03509_gb300.shard import partition_scans
+        kept = tg.kept_lengths(cfg)
+        bounds = partition_scans(kept * cfg.ndet, ws)
+        scans = range(int(bounds[rank]), int(bounds[rank + 1]))
+    arr, ing = build_band(cfg, scans)
+    setup_s = time.time() - t_setup
+    res = measure_step(args, cfg, arr, ing, local, rank, ws)
     peaks, peak_src = _peaks()
-    comp = int(ing["pix_streams"]["words"].nbytes + ing["psi_streams"]["words"].nbytes)
-    npairs = int(getattr(plan, "npairs", 0) or 0)
-    byts = stage_bytes(N, nq, npix, npairs, comp)
-    dom = max(stage_ms, key=stage_ms.get)
-    lens = np.diff(ing["offsets"])
-    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    if dom in ("gain", "ncorr"):
-        # FP32 FFT work: 5 (n/2) log2(n/2) flops per complex transform of a
-        # length-n real DCT, plus the split (~10 n); transforms per detscan:
-        # gain 2, n_corr 2 + 2 per CG iteration + 1 (the correction's inverse).
-        per = 2.5 * lens * np.log2(lens / 2.0) + 10.0 * lens
-        if dom == "gain":
-            flops = float(np.sum(2 * per))
-        else:
-            flops = float(np.sum(per * (2 + np.where(iters > 0, 2 * iters + 1, 0))))
-        peak_tf = 152 * 128 * 2 * (peaks.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
-        ach = flops / (stage_ms[dom] / 1e3) / 1e12
-        traffic = None
-        if dom == "ncorr" and ncorr_sources_digest() == NCORR_TRAFFIC["sha256"]:
-            traffic = NCORR_TRAFFIC["bytes_per_sample"] * N
-        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": ach / peak_tf, "traffic": traffic, "traffic_unit": "bytes per launch",
-                "peak_source": "FP32 FMA issue: 152 SMs x 128 lanes x 2 flop x sm_max_mhz"}
-    else:
-        ach = byts.get(dom, 0.0) / (stage_ms[dom] / 1e3) / 1e9
-        pk = float(peaks["hbm_gbs"])
-        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s",
-                "frac": ach / pk, "traffic": None, "peak_source": peak_src}
-    stage_gbs = {k: (byts[k] / (stage_ms[k] / 1e3) / 1e9 if k in byts else None) for k in stage_ms}
-
-    value = ws * N * args.steps / elapsed
+    roof, stage_gbs = roofline_and_stages(res, peaks, peak_src)
+    N, nq, npix = res["N"], res["nq"], res["npix"]
+    Ntot = N
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([float(N)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t)
+        Ntot = int(t.item())
+    elapsed = res["elapsed"]
+    graph_ms, plain_ms = res["graph_ms"], res["plain_ms"]
     out = {
-        "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": cfg.name, "ndetscan": nq, "samples_per_step": N, "nside": cfg.nside,
-                   "flag_frac": cfg.flag_frac, "tile_pairs": info["tile_pairs"], "autotune": tuned,
-                   "l2": "inputs larger than L2 (%.2f GB per step)" % (4.0 * N / 1e9),
-                   "parallelism": "replica x%d" % ws},
-        "e2e": {"value": ws * N * args.steps / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": 4 * N,
+        "metric": METRIC, "value": Ntot * args.steps / elapsed, "unit": "samples/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+        "higher_is_better": True, "scaling": "strong" if ws > 1 else "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": cfg.name, "ndetscan": cfg.ndet * cfg.nscan, "samples_per_step": Ntot,
+                   "nside": cfg.nside, "flag_frac": cfg.flag_frac,
+                   "tile_pairs": res["plan"].info()["tile_pairs"], "autotune": res["tuned"],
+                   "l2": "inputs larger than L2 (%.1f GB of d per step)" % (4.0 * Ntot / 1e9),
+                   "parallelism": "single GPU" if ws == 1 else
+                   "%d scan ranges (one per rank), normal equations reduced by pixel range" % ws},
+        "e2e": {"value": Ntot * args.steps / res["e2e_s"], "unit": "samples/s", "h2d_bytes_per_step": 4 * N,
                 "d2h_bytes_per_step": 8 * (3 * npix + nq)},
-        "gpu_launches": GibbsTODStep.LAUNCHES_PER_STEP * args.steps,
-        "stage_ms": stage_ms, "stage_gbs": stage_gbs,
-        "cg_iters": {"mean": float(iters.mean()), "max": int(iters.max()), "min": int(iters.min())},
-        "graph": ({"ms_per_step": graph_ms, "value": ws * N / (graph_ms / 1e3)}
+        "gpu_launches": res["step"].launches_per_step * args.steps,
+        "stage_ms": res["stage_ms"], "stage_gbs": stage_gbs,
+        "cg_iters": {"mean": float(res["iters"].mean()), "max": int(res["iters"].max()),
+                     "min": int(res["iters"].min())},
+        "graph": ({"ms_per_step": graph_ms, "value": Ntot / (graph_ms / 1e3)}
                   if isinstance(graph_ms, float) else graph_ms),
         "plain_per_scan": ({"ms_per_step": plain_ms, "value": N / (plain_ms / 1e3),
                             "speedup_batched": plain_ms / (1e3 * elapsed / args.steps)}
                            if plain_ms else None),
-        "noise_psd": psd_info,
-        "data_streams": ds_info,
-        "gain_smooth": gs_info,
-        "device_status_errors": int(np.count_nonzero(st)),
-        "roofline": roof, "clocks": clocks, "setup_s": setup_s,
+        "device_status_errors": res["status_errors"],
+        "roofline": roof, "clocks": res["clocks"], "setup_s": setup_s,
     }
+    if rank == 0 and ws == 1 and not args.no_oracle_error:
+        out["oracle_error"] = oracle_errors(args, cfg, arr, ing, res)
+    res["plan"].close()
+    del res
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    if rank == 0 and ws == 1 and not args.no_secondary and args.workload != SECONDARY:
+        out["secondary"] = secondary_section(args, local)
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args, cfg, band, budget_s=args.cpu_seconds)
-    plan.close()
+        out["cpu_baseline"] = cpu_baseline(args, cfg, budget_s=args.cpu_seconds)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
-
-
-def cpu_baseline(args, cfg, band, budget_s=20.0, steps=1):
-    """The FP64 oracle, as it stands, on the first detscans of the workload."""
-    import oracle
-    ing = oracle_ingest_subset(band, cfg, max_detscans=args.cpu_detscans)
-    off = ing["offsets"]
-    nq = len(off) - 1
-    t = time.time()
-    done = 0
-    samples = 0
-    while done < nq and time.time() - t < budget_s:
-        oracle.gibbs_tod_step(ing, cfg, band.npix, band.map_tqu, band.psd, args.seed, 0, 0,
-                              detscans=[done])
-        samples += int(off[done + 1] - off[done])
-        done += 1
-    el = time.time() - t
-    return {"value": samples / el, "unit": "samples/s", "cores": 1, "kind": "oracle",
-            "sample": "%d of %d detscans (%d samples), FP64 numpy/scipy + C Huffman, one thread"
-                      % (done, cfg.ndet * cfg.nscan, samples), "seconds": el}
-
-
-def oracle_ingest_subset(band, cfg, max_detscans):
-    """The oracle's own ingest of the first scans (enough for the sample)."""
-    import oracle
-    import synth
-    nscan = max(1, -(-max_detscans // cfg.ndet))
-    sub = synth.Band(cfg=synth.scaled(cfg, nscan=nscan), npix=band.npix, map_tqu=band.map_tqu,
-                     scan_len=band.scan_len[:nscan], gain=band.gain[:nscan * cfg.ndet], psd=band.psd,
-                     pix=band.pix[:nscan * cfg.ndet], psi=band.psi[:nscan * cfg.ndet],
-                     flags=band.flags[:nscan * cfg.ndet], tod=band.tod[:nscan * cfg.ndet])
-    return oracle.ingest(sub)
 
 
 def run_reference(args):
@@ -515,7 +674,7 @@ def run_reference(args):
     from oracle import _huff
     _huff.build()
     import synth
-    cfg = synth.CONFIGS[CONFIG_NAME]
+    cfg = synth.CONFIGS[args.workload]
     # only the scans the timed sample touches are generated
     nsc = max(1, -(-args.cpu_detscans // cfg.ndet))
     sub_cfg = synth.scaled(cfg, nscan=nsc)
@@ -541,7 +700,7 @@ def run_reference(args):
            "impl": "reference",
            "config": {"workload": cfg.name, "sample": "%d detscans per step" % per_step},
            "cpu_baseline": {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle",
-                            "sample": "%d detscans (%d samples) per step of the %s workload"
+                            "sample": "%d detscans (%d samples) per step of the %s workload, one process"
                                       % (per_step, samples // max(1, args.steps), cfg.name)},
            "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -553,15 +712,20 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=["lfi70", "lfi30"])
     ap.add_argument("--nscan", type=int, default=0, help="fewer scans (testing only)")
     ap.add_argument("--seed", type=int, default=2022)
     ap.add_argument("--cg-tol", type=float, default=1e-6)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
-    ap.add_argument("--cpu-detscans", type=int, default=24)
-    ap.add_argument("--ref-detscans-per-step", type=int, default=2)
+    ap.add_argument("--cpu-detscans", type=int, default=64)
+    ap.add_argument("--ref-detscans-per-step", type=int, default=1)
+    ap.add_argument("--tune-scans", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the per-scan comparison step")
-    ap.add_argument("--no-autotune", action="store_true", help="use the plan's default launch shape")
+    ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay")
+    ap.add_argument("--no-autotune", action="store_true", help="use the plan's default tile shape")
+    ap.add_argument("--no-oracle-error", action="store_true", help="skip the oracle comparison")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the 30 GHz section and the added rows")
     ap.add_argument("--no-psd", action="store_true", help="skip the noise-PSD step measurement")
     ap.add_argument("--no-data-streams", action="store_true",
                     help="skip the step with compressed TOD and flags")

@@ -232,8 +232,9 @@ def ingest_arrays(arr) -> dict:
     streams; the arrays are used in place (psi is widened to int32 for the
     coder)."""
     cfg = arr.cfg
-    ndet, nscan = cfg.ndet, cfg.nscan
     off = arr.offsets
+    ndet = cfg.ndet
+    nscan = (len(off) - 1) // ndet        # the generated scans (all, or a scan range)
     psi32 = np.empty(len(arr.psi), np.int32)
     np.copyto(psi32, arr.psi, casting="unsafe")
     out = dict(offsets=off,

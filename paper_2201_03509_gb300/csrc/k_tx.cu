@@ -337,30 +337,37 @@ struct RowGeo {
     }
 };
 
-// Packed orthonormal coefficients of slot k from Z_k, Z_{m-k} (forward
-// half-split): W = e^{-i pi k/2n} A + e^{-i 5 pi k/2n} B, k = k1 + m1 k2.
+// The split's twiddles of slot k = k1 + m1 k2: e1 = W_4n^k, e5 = W_4n^{5k}.
+template <class V> struct SplitTw { V e1, e5; };
 template <class V>
-__device__ __forceinline__ V split_f(const TwB<V> &T, V a, V b, int k1, int k2, typename VecT<V>::S sq) {
+__device__ __forceinline__ SplitTw<V> split_tw(const TwB<V> &T, int k1, int k2) {
+    SplitTw<V> t;
+    t.e1 = vmul(vld(T.sa1 + k1), vld(T.sb1 + k2));
+    t.e5 = vmul(vld(T.sa5 + k1), vld(T.sb5 + k2));
+    return t;
+}
+// Packed orthonormal coefficients of slot k from Z_k, Z_{m-k} (forward
+// half-split): W = e^{-i pi k/2n} A + e^{-i 5 pi k/2n} B.
+template <class V>
+__device__ __forceinline__ V split_f(const SplitTw<V> &w, V a, V b, typename VecT<V>::S sq) {
     typedef typename VecT<V>::S S;
     const V cb = vconj(b);
     const V A = vscale(vadd(a, cb), static_cast<S>(0.5));
     const V d = vsub(a, cb);
     const V Bv = vmake<V>(static_cast<S>(0.5) * d.y, static_cast<S>(-0.5) * d.x);
-    const V e1 = vmul(vld(T.sa1 + k1), vld(T.sb1 + k2)), e5 = vmul(vld(T.sa5 + k1), vld(T.sb5 + k2));
-    const V Wv = vadd(vmul(e1, A), vmul(e5, Bv));
+    const V Wv = vadd(vmul(w.e1, A), vmul(w.e5, Bv));
     return vmake<V>(sq * Wv.x, -sq * Wv.y);
 }
 // Z_k from the packed slots k and m-k (inverse half-split; sq includes 1/m).
 template <class V>
-__device__ __forceinline__ V split_i(const TwB<V> &T, V yk, V yp, int k1, int k2, int q1, int q2,
+__device__ __forceinline__ V split_i(const SplitTw<V> &wk, const SplitTw<V> &wp, V yk, V yp,
                                      typename VecT<V>::S sq) {
     typedef typename VecT<V>::S S;
-    const V ek = vmul(vld(T.sa1 + k1), vld(T.sb1 + k2)), ep = vmul(vld(T.sa1 + q1), vld(T.sb1 + q2));
-    const V Vk = vscale(vmulc(vconj(yk), ek), sq);
-    const V Vp = vscale(vmulc(vconj(yp), ep), sq);
+    const V Vk = vscale(vmulc(vconj(yk), wk.e1), sq);
+    const V Vp = vscale(vmulc(vconj(yp), wp.e1), sq);
     const V cVp = vconj(Vp);
     const V A = vscale(vadd(Vk, cVp), static_cast<S>(0.5));
-    const V e4 = vmulc(vmul(vld(T.sa5 + k1), vld(T.sb5 + k2)), ek);
+    const V e4 = vmulc(wk.e5, wk.e1);                                   // W_4n^{4k} = e^{-2 pi i k/n}
     const V Bv = vscale(vmulc(vsub(Vk, cVp), e4), static_cast<S>(0.5));
     return vmake<V>(A.x - Bv.y, A.y + Bv.x);
 }
@@ -421,17 +428,19 @@ __device__ __forceinline__ void row_pass(const TxCtx &X, V *b0, V *b1, V *__rest
                         R[ia] = vmake<V>(static_cast<S>(0.5) * (V0 + Vm), static_cast<S>(0.5) * (V0 - Vm));
                     }
                 } else {
-                    V Ya = split_f(T, Za, Zb, p, k2, sqf);
+                    const SplitTw<V> wa = split_tw(T, p, k2);
+                    V Ya = split_f(wa, Za, Zb, sqf);
                     Ya = f(ia, p + m1 * k2, Ya);
                     if (ib != ia) {
-                        V Yb = split_f(T, Zb, Za, q1, q2, sqf);
+                        const SplitTw<V> wb = split_tw(T, q1, q2);
+                        V Yb = split_f(wb, Zb, Za, sqf);
                         Yb = f(ib, q1 + m1 * q2, Yb);
                         if (INV_BACK) {
-                            R[ib] = split_i(T, Yb, Ya, q1, q2, p, k2, sqi);
-                            R[ia] = split_i(T, Ya, Yb, p, k2, q1, q2, sqi);
+                            R[ib] = split_i(wb, wa, Yb, Ya, sqi);
+                            R[ia] = split_i(wa, wb, Ya, Yb, sqi);
                         }
                     } else if (INV_BACK) {
-                        R[ia] = split_i(T, Ya, Ya, p, k2, q1, q2, sqi);
+                        R[ia] = split_i(wa, wa, Ya, Ya, sqi);
                     }
                 }
             }
@@ -1646,15 +1655,20 @@ __device__ void nc_cg_update(const NcorrTx &a, NcShared &S, int q, float *gb, in
 // cooperative tail kernel finishes any detscan still iterating (grid
 // barriers between its passes; it returns at once when none is).
 // ---------------------------------------------------------------------------
+// Work items of the launch range: a contiguous share per CTA when every
+// detscan takes part (tiles of one length together), grid-stride when only
+// the detscans still iterating do (their tiles spread over every CTA).
 template <class Keep, class Fn>
-__device__ __forceinline__ void nc_items(const NcorrTx &a, TxCtx &X, bool rows, int &cur, Keep keep, Fn fn)
+__device__ __forceinline__ void nc_items(const NcorrTx &a, TxCtx &X, bool rows, int &cur, Keep keep, Fn fn,
+                                         bool stride = false)
 {
     const int2 *items = rows ? a.rowitems : a.colitems;
     const int j0 = rows ? a.row_off[a.q0] : a.col_off[a.q0];
     const int j1 = rows ? a.row_off[a.q1] : a.col_off[a.q1];
-    int i0, i1;
+    int i0, i1, step = 1;
     cta_share(j1 - j0, i0, i1);
-    for (int it = j0 + i0; it < j0 + i1; ++it) {
+    if (stride) { i0 = blockIdx.x; i1 = j1 - j0; step = gridDim.x; }
+    for (int it = j0 + i0; it < j0 + i1; it += step) {
         const int2 w = items[it];
         const int md = a.cgs[w.x].mode;
         if (!keep(md)) continue;
@@ -1739,8 +1753,8 @@ __global__ void __launch_bounds__(TX_T, 3) k_nc_scatter(NcorrTx a, int par)
     }
     const CgVec V = cg_vecs(a);
     int cur = -1;
-    if (FINAL) nc_items(a, X, false, cur, nc_ran, [&] { nc_scatter_cols(a, X, tx_smem, tx_smem + TX_TILE, V.y); });
-    else nc_items(a, X, false, cur, nc_active, [&] { nc_scatter_cols(a, X, tx_smem, tx_smem + TX_TILE, V.p); });
+    if (FINAL) nc_items(a, X, false, cur, nc_ran, [&] { nc_scatter_cols(a, X, tx_smem, tx_smem + TX_TILE, V.y); }, true);
+    else nc_items(a, X, false, cur, nc_active, [&] { nc_scatter_cols(a, X, tx_smem, tx_smem + TX_TILE, V.p); }, true);
 }
 template <bool FINAL>
 __global__ void __launch_bounds__(TX_T, 3) k_nc_filter(NcorrTx a, int par)
@@ -1749,8 +1763,8 @@ __global__ void __launch_bounds__(TX_T, 3) k_nc_filter(NcorrTx a, int par)
     __shared__ TxCtx X;
     if (!FINAL && *reinterpret_cast<volatile const int32_t *>(a.count + par) == 0) return;
     int cur = -1;
-    if (FINAL) nc_items(a, X, true, cur, nc_ran, [&] { nc_filter_rows<true>(a, X, tx_smem, tx_smem + TX_TILE); });
-    else nc_items(a, X, true, cur, nc_active, [&] { nc_filter_rows<false>(a, X, tx_smem, tx_smem + TX_TILE); });
+    if (FINAL) nc_items(a, X, true, cur, nc_ran, [&] { nc_filter_rows<true>(a, X, tx_smem, tx_smem + TX_TILE); }, true);
+    else nc_items(a, X, true, cur, nc_active, [&] { nc_filter_rows<false>(a, X, tx_smem, tx_smem + TX_TILE); }, true);
 }
 template <bool FINAL>
 __global__ void __launch_bounds__(TX_T, 3) k_nc_gather(NcorrTx a, int par)
@@ -1760,8 +1774,8 @@ __global__ void __launch_bounds__(TX_T, 3) k_nc_gather(NcorrTx a, int par)
     if (!FINAL && *reinterpret_cast<volatile const int32_t *>(a.count + par) == 0) return;
     const CgVec V = cg_vecs(a);
     int cur = -1;
-    if (FINAL) nc_items(a, X, false, cur, nc_ran, [&] { nc_gather_cols<true>(a, X, tx_smem, tx_smem + TX_TILE, nullptr); });
-    else nc_items(a, X, false, cur, nc_active, [&] { nc_gather_cols<false>(a, X, tx_smem, tx_smem + TX_TILE, V.q); });
+    if (FINAL) nc_items(a, X, false, cur, nc_ran, [&] { nc_gather_cols<true>(a, X, tx_smem, tx_smem + TX_TILE, nullptr); }, true);
+    else nc_items(a, X, false, cur, nc_active, [&] { nc_gather_cols<false>(a, X, tx_smem, tx_smem + TX_TILE, V.q); }, true);
 }
 __global__ void __launch_bounds__(TX_T, 3) k_nc_update(NcorrTx a, int par)
 {
@@ -1784,11 +1798,11 @@ __global__ void __launch_bounds__(TX_T, 2) k_nc_tail(NcorrTx a, int par)
     for (;;) {
         if (*reinterpret_cast<volatile const int32_t *>(a.count + par) == 0) break;
         if (blockIdx.x == 0 && threadIdx.x == 0) a.count[par ^ 1] = 0;
-        nc_items(a, S.X, false, cur, nc_active, [&] { nc_scatter_cols(a, S.X, tx_smem, tx_smem + TX_TILE, V.p); });
+        nc_items(a, S.X, false, cur, nc_active, [&] { nc_scatter_cols(a, S.X, tx_smem, tx_smem + TX_TILE, V.p); }, true);
         grid.sync();
-        nc_items(a, S.X, true, cur, nc_active, [&] { nc_filter_rows<false>(a, S.X, tx_smem, tx_smem + TX_TILE); });
+        nc_items(a, S.X, true, cur, nc_active, [&] { nc_filter_rows<false>(a, S.X, tx_smem, tx_smem + TX_TILE); }, true);
         grid.sync();
-        nc_items(a, S.X, false, cur, nc_active, [&] { nc_gather_cols<false>(a, S.X, tx_smem, tx_smem + TX_TILE, V.q); });
+        nc_items(a, S.X, false, cur, nc_active, [&] { nc_gather_cols<false>(a, S.X, tx_smem, tx_smem + TX_TILE, V.q); }, true);
         grid.sync();
         for (int q = a.q0 + blockIdx.x; q < a.q1; q += gridDim.x) {
             __syncthreads();

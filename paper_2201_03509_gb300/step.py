@@ -6,7 +6,9 @@ With ``data_streams`` the detector data and flags stay compressed on the
 device too (Sect. 4.1; the plan must have them attached) and every step
 decodes them along with the pointing.  With ``gain_prior`` each step draws
 every detector's scan gains jointly under the smooth prior across scans
-(tod_sample_gain_smooth) in place of the independent per-scan draws."""
+(tod_sample_gain_smooth) in place of the independent per-scan draws.  With
+``shard`` (a shard.ShardedMaps) the plan holds one process's scan range and
+the binning + solve become the reduction over processes (Sect. 2.3-2.4)."""
 from __future__ import annotations
 
 import numpy as np
@@ -17,7 +19,7 @@ from . import MODE_DRAW, Plan, Rng
 class GibbsTODStep:
     def __init__(self, plan: Plan, psd: np.ndarray, flag_words: np.ndarray | None, rcond_min: float = 1e-6,
                  cg_tol: float = 1e-6, cg_maxiter: int = 500, data_streams: bool = False,
-                 gain_prior: np.ndarray | None = None):
+                 gain_prior: np.ndarray | None = None, shard=None):
         import torch
         dev = torch.device("cuda", plan.device)
         N, nq, npix = plan.N, plan.nq, plan.npix
@@ -53,6 +55,7 @@ class GibbsTODStep:
         # each step decodes the next step's pointing under its n_corr draw
         # (a spare pix/psi pair); the last step's lookahead is extra work
         self.lookahead = True
+        self.shard = shard
         self._pointing_ready = False
         self._pix_next = self._psi_next = None
         self._d_next = self._flags_next = None
@@ -185,15 +188,27 @@ class GibbsTODStep:
             if self.data_streams:
                 p.decode_data(self._d_next, self._flags_next, lo)
             self._pointing_ready = True
-        p.bin(self.psi, self.d, self.ncorr, self.gain, self.flags, self.psd, self.A, self.b, self.hits, hp)
-        p.solve_maps(self.A, self.b, self.hits, self.rcond_min, self.map, self.map32, self.rcond,
-                     self.valid, hp)
+        if self.shard is None:
+            p.bin(self.psi, self.d, self.ncorr, self.gain, self.flags, self.psd, self.A, self.b, self.hits, hp)
+            p.solve_maps(self.A, self.b, self.hits, self.rcond_min, self.map, self.map32, self.rcond,
+                         self.valid, hp)
+        else:
+            # this process's partials, reduced over processes by pixel range, solved and gathered
+            with torch.cuda.stream(hp):
+                m, m32, va = self.shard.reduce_and_solve(self.psi, self.d, self.ncorr, self.gain, self.flags,
+                                                         self.psd, self.rcond_min)
+                self.map.copy_(m)
+                self.map32.copy_(m32)
+                self.valid.copy_(va)
         st.wait_stream(hp)
         if lookahead:
             st.wait_stream(lo)
         self._mark_d_done(stream)
 
-    LAUNCHES_PER_STEP = 11  # decode x2, project, gain + draw, Toeplitz prep x2, ncorr, bin + reduce, solve
+    # decode x2, project, gain (scalars, three passes, draw), Toeplitz prep x2,
+    # n_corr (flag index 4, right-hand side 3, CG start, 3 launched CG
+    # iterations x 4, cooperative tail, correction 3, finish), bin + reduce, solve
+    LAUNCHES_PER_STEP = 2 + 1 + 5 + 2 + 25 + 2 + 1
     DATA_LAUNCHES = 2       # with data_streams: decode of the TOD and of the flags
 
     @property
