@@ -119,21 +119,20 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# DRAM bytes (read + write) per TOD sample of the n_corr draw's kernels from
-# an ncu capture of the same draw on a slice of the 70 GHz band (the
-# summary under profiles/ names the command), at the capture's mean CG
-# iteration count; scaled to a full draw by samples (every pass moves each
-# sample's values once) with the CG passes' share adjusted to the draw's
-# own mean count.  Valid only while the kernels' sources hash to the digest
-# taken with it; otherwise the traffic is reported as null.
-NCORR_TRAFFIC = {"bytes_per_sample": None, "cg_iters_mean": None,
-                 "sources": ["csrc/k_tx.cu", "csrc/fft_reg.cuh", "csrc/common.cuh", "csrc/internal.cuh"],
-                 "sha256": None}
+# DRAM bytes (read + write) of a kernel per byte of its algorithmic traffic,
+# from an ncu capture of that kernel on a smaller case of the same band (the
+# summary under profiles/ gives the command and the figures); a full launch's
+# traffic is that ratio times its algorithmic bytes (every pass moves each
+# sample's values in proportion).  Valid only while the kernels' sources
+# hash to the digest taken with it; otherwise the traffic is reported as null.
+KERNEL_TRAFFIC = {}
+TRAFFIC_SOURCES = ["csrc/k_tx.cu", "csrc/fft_reg.cuh", "csrc/common.cuh", "csrc/internal.cuh",
+                   "csrc/k_bin_solve.cu", "csrc/k_decode_project.cu"]
 
 
-def ncorr_sources_digest() -> str | None:
+def kernel_sources_digest() -> str | None:
     h = hashlib.sha256()
-    for rel in NCORR_TRAFFIC["sources"]:
+    for rel in TRAFFIC_SOURCES:
         try:
             with open(os.path.join(ROOT, "paper_2201_03509_gb300", rel), "rb") as f:
                 h.update(f.read())
@@ -185,6 +184,36 @@ def ncorr_algorithmic_bytes(lens, iters, flagged):
     return float(b.sum())
 
 
+def kernel_bytes(N, npix, npairs, comp_bytes, lens, iters, flagged):
+    """Algorithmic HBM bytes of one step per kernel class (the names of
+    tod_kernel_name).  Transforms: the column pass moves its inputs and the
+    complex intermediate Y (4 B per sample), the row pass reads and writes
+    Y, the inverse column pass reads Y and moves its outputs.  A CG pass
+    touches only the detscans still iterating: iteration i of detscan q
+    runs when q took more than i iterations; the cooperative tail runs the
+    iterations past the third; the correction passes run over every detscan
+    that ran the CG.  Small per-detscan kernels are left out."""
+    lens = np.asarray(lens, np.float64)
+    it = np.asarray(iters, np.float64)
+    fl = np.asarray(flagged, bool)
+    act = [float(lens[fl & (it > i)].sum()) for i in range(3)]
+    tail = float((lens * np.maximum(it - 3, 0) * fl).sum())
+    ran = float(lens[fl & (it > 0)].sum())
+    return {
+        "k_decode": comp_bytes + 6.0 * N,
+        "k_project": 10.0 * N,
+        "k_gain_cols": 8.125 * N, "k_gain_rows": 8.0 * N, "k_gain_colsinv": 8.125 * N,
+        "k_nc_flag_count": N / 8.0, "k_nc_flag_write": N / 8.0 + N / 4.0,
+        "k_nc_rhs_cols": 12.125 * N, "k_nc_rhs_rows": 8.0 * N, "k_nc_x0_cols": 8.125 * N,
+        "k_nc_scatter": 4.0 * sum(act), "k_nc_filter": 8.0 * sum(act), "k_nc_gather": 4.125 * sum(act),
+        "k_nc_tail": 16.125 * tail,
+        "k_nc_scatter_final": 4.0 * ran, "k_nc_filter_final": 8.0 * ran, "k_nc_gather_final": 12.125 * ran,
+        "k_bin": 16.125 * N + 80.0 * npairs,
+        "k_reduce": 80.0 * npairs + 84.0 * npix,
+        "k_solve": 137.0 * npix,
+    }
+
+
 def _event():
     import torch
     return torch.cuda.Event(enable_timing=True)
@@ -202,7 +231,7 @@ def measure_step(args, cfg, arr, ing, local, rank, ws, label="main"):
     map_in = torch.from_numpy(m4).cuda()
     tuned = None
     tp, rmax = 0, 0
-    if not args.no_autotune and label == "main":
+    if args.autotune and label == "main":
         # measured tile shape (column pairs, largest radix) on the band's first scans
         from paper_2201_03509_gb300.autotune import autotune
         tp, rmax, tms = autotune(cfg.nside, cfg.ndet, nscan_local, cfg.fsamp, ing["offsets"], ing["pix_streams"],
@@ -251,32 +280,48 @@ def measure_step(args, cfg, arr, ing, local, rank, ws, label="main"):
     # between them (the n_corr preparation, which the step overlaps with
     # decode, projection and gain, as its own stage), after the timed region
     names = ["decode", "project", "gain", "ncorr_prepare", "ncorr", "bin", "solve"]
-    evs = [[_event() for _ in range(8)] for _ in range(args.steps)]
-    for k in range(args.steps):
-        rng = tg.Rng(args.seed, 0, 20_000 + k)
-        ev = evs[k]
+
+    def calls(rng, ev=None):
         p = step.plan
-        ev[0].record(stream)
+        mark = (lambda i: ev[i].record(stream)) if ev else (lambda i: None)
+        mark(0)
         p.decode(step.pix, step.psi)
-        ev[1].record(stream)
+        mark(1)
         p.project(map_in, step.pix, step.psi, None, step.s)
-        ev[2].record(stream)
+        mark(2)
         p.sample_gain(step.d, step.s, step.flags, step.psd, rng, tg.MODE_DRAW, step.gain, step.mu, step.sigma)
-        ev[3].record(stream)
+        mark(3)
         p.ncorr_prepare(step.psd)
-        ev[4].record(stream)
+        mark(4)
         p.sample_ncorr_prepared(step.d, step.s, step.gain, step.flags, step.psd, rng, tg.MODE_DRAW, step.ncorr,
                                 step.cg_iters, step.cg_tol, step.cg_maxiter)
-        ev[5].record(stream)
+        mark(5)
         p.bin(step.psi, step.d, step.ncorr, step.gain, step.flags, step.psd, step.A, step.b, step.hits)
-        ev[6].record(stream)
+        mark(6)
         p.solve_maps(step.A, step.b, step.hits, step.rcond_min, step.map, step.map32, step.rcond, step.valid)
-        ev[7].record(stream)
+        mark(7)
+
+    evs = [[_event() for _ in range(8)] for _ in range(args.steps)]
+    for k in range(args.steps):
+        calls(tg.Rng(args.seed, 0, 20_000 + k), evs[k])
     torch.cuda.synchronize()
     st = plan.status(raise_on_error=False)
     stage_ms = {nm: float(np.mean([evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps)]))
                 for i, nm in enumerate(names)}
     iters_stage = step.cg_iters.cpu().numpy()
+    # per-kernel times: the same calls with the library's kernel timing on
+    # (two events around every launch, on the launching stream)
+    kt_steps = 2
+    plan.set_kernel_timing(True)
+    its_kt = []
+    for k in range(kt_steps):
+        calls(tg.Rng(args.seed, 0, 25_000 + k))
+        its_kt.append(step.cg_iters.clone())
+    plan.set_kernel_timing(False)
+    kt = plan.kernel_times()
+    kernel_ms = {nm: (ms / kt_steps, n / kt_steps) for nm, (ms, n) in kt.items()}
+    iters_kt = [t.cpu().numpy() for t in its_kt]
+    plan.status(raise_on_error=False)
 
     # the same step captured in a CUDA graph (iteration read on the device)
     graph_ms = None
@@ -347,6 +392,7 @@ def measure_step(args, cfg, arr, ing, local, rank, ws, label="main"):
     flagged = np.array([bool(fl[int(off[q]):int(off[q + 1])].any()) for q in range(nq)])
     return dict(plan=plan, step=step, map_in=map_in, N=N, nq=nq, npix=npix, elapsed=elapsed, e2e_s=e2e_s,
                 stage_ms=stage_ms, iters=iters, iters_stage=iters_stage, clocks=clocks, graph_ms=graph_ms,
+                kernel_ms=kernel_ms, iters_kt=iters_kt,
                 plain_ms=plain_ms, tuned=tuned, status_errors=int(np.count_nonzero(st)), lens=lens,
                 flagged=flagged,
                 comp_bytes=int(ing["pix_streams"]["words"].nbytes + ing["psi_streams"]["words"].nbytes),
@@ -354,22 +400,46 @@ def measure_step(args, cfg, arr, ing, local, rank, ws, label="main"):
 
 
 def roofline_and_stages(res, peaks, peak_src):
+    """Per-stage GB/s over the stages' algorithmic bytes, the per-kernel
+    table (CUDA-event time per step, launches, share of the step's kernel
+    time, algorithmic bytes and GB/s), and the roofline of the dominant
+    kernel: its algorithmic bytes per launch over its mean launch time."""
     N, npix = res["N"], res["npix"]
     ncorr_b = ncorr_algorithmic_bytes(res["lens"], res["iters_stage"], res["flagged"])
     byts = stage_bytes(N, npix, res["npairs"], res["comp_bytes"], ncorr_b)
     stage_ms = res["stage_ms"]
     stage_gbs = {k: (byts[k] / (stage_ms[k] / 1e3) / 1e9 if k in byts else None) for k in stage_ms}
-    dom = max(("gain", "ncorr", "bin", "decode", "project"), key=lambda k: stage_ms[k])
+    # kernel bytes averaged over the timed calls' own CG iteration counts
+    kb = {}
+    for it in res["iters_kt"]:
+        for nm, v in kernel_bytes(N, npix, res["npairs"], res["comp_bytes"], res["lens"], it,
+                                  res["flagged"]).items():
+            kb[nm] = kb.get(nm, 0.0) + v / len(res["iters_kt"])
+    kms = res["kernel_ms"]
+    total = sum(ms for ms, _ in kms.values())
+    table = {}
+    for nm, (ms, n) in sorted(kms.items(), key=lambda x: -x[1][0]):
+        b = kb.get(nm)
+        table[nm] = {"ms_per_step": ms, "launches_per_step": n, "share": ms / total if total else None,
+                     "algorithmic_bytes": b, "gbs": (b / (ms / 1e3) / 1e9) if (b and ms > 0) else None}
+    dom = max((nm for nm in kms if nm in kb), key=lambda nm: kms[nm][0])
+    ms, n = kms[dom]
     pk = float(peaks["hbm_gbs"])
-    ach = byts[dom] / (stage_ms[dom] / 1e3) / 1e9
+    per_launch = kb[dom] / n
+    ms_launch = ms / n
+    ach = per_launch / (ms_launch / 1e3) / 1e9
     traffic = None
-    if dom == "ncorr" and NCORR_TRAFFIC["sha256"] and ncorr_sources_digest() == NCORR_TRAFFIC["sha256"]:
-        adj = 16.25 * (float(np.mean(res["iters_stage"])) - NCORR_TRAFFIC["cg_iters_mean"])
-        traffic = (NCORR_TRAFFIC["bytes_per_sample"] + adj) * N
-    roof = {"kernel": "%s stage (its pass kernels)" % dom, "bound": "hbm", "achieved": ach, "peak": pk,
-            "unit": "GB/s", "frac": ach / pk, "traffic": traffic, "traffic_unit": "bytes per call",
-            "algorithmic_bytes": byts[dom], "peak_source": "%s hbm_gbs (MEASURED_PEAKS.json)" % peak_src}
-    return roof, stage_gbs
+    tr = KERNEL_TRAFFIC.get(dom)
+    if tr and tr.get("sha256") and kernel_sources_digest() == tr["sha256"]:
+        traffic = tr["dram_per_algorithmic_byte"] * per_launch
+    roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,
+            "traffic": traffic, "traffic_unit": "bytes per launch", "launches_per_step": n,
+            "ms_per_launch": ms_launch, "algorithmic_bytes_per_launch": per_launch,
+            "share_of_kernel_time": ms / total if total else None,
+            "timing": "CUDA events around each launch on its stream (library kernel timing), after the "
+                      "timed region",
+            "peak_source": "%s hbm_gbs (MEASURED_PEAKS.json)" % peak_src}
+    return roof, stage_gbs, table
 
 
 def oracle_errors(args, cfg, arr, ing, res, nsample=3):
@@ -486,10 +556,10 @@ def secondary_section(args, local):
     plan, step, map_in = res["plan"], res["step"], res["map_in"]
     N, stream = res["N"], torch.cuda.current_stream()
     peaks, peak_src = _peaks()
-    roof, stage_gbs = roofline_and_stages(res, peaks, peak_src)
+    roof, stage_gbs, ktab = roofline_and_stages(res, peaks, peak_src)
     out = {"workload": cfg.name, "samples_per_step": N, "ms_per_step": 1e3 * res["elapsed"] / args.steps,
            "value": N * args.steps / res["elapsed"], "e2e_value": N * args.steps / res["e2e_s"],
-           "stage_ms": res["stage_ms"], "stage_gbs": stage_gbs, "roofline": roof,
+           "stage_ms": res["stage_ms"], "stage_gbs": stage_gbs, "kernels": ktab, "roofline": roof,
            "cg_iters_mean": float(res["iters"].mean()), "graph_ms_per_step": res["graph_ms"],
            "setup_s": time.time() - t_set}
     # row A10: the n_corr draw writing its spectra, then Metropolis steps
@@ -614,7 +684,7 @@ def run_ours(args):
     setup_s = time.time() - t_setup
     res = measure_step(args, cfg, arr, ing, local, rank, ws)
     peaks, peak_src = _peaks()
-    roof, stage_gbs = roofline_and_stages(res, peaks, peak_src)
+    roof, stage_gbs, ktab = roofline_and_stages(res, peaks, peak_src)
     N, nq, npix = res["N"], res["nq"], res["npix"]
     Ntot = N
     if ws > 1:
@@ -638,7 +708,7 @@ def run_ours(args):
         "e2e": {"value": Ntot * args.steps / res["e2e_s"], "unit": "samples/s", "h2d_bytes_per_step": 4 * N,
                 "d2h_bytes_per_step": 8 * (3 * npix + nq)},
         "gpu_launches": res["step"].launches_per_step * args.steps,
-        "stage_ms": res["stage_ms"], "stage_gbs": stage_gbs,
+        "stage_ms": res["stage_ms"], "stage_gbs": stage_gbs, "kernels": ktab,
         "cg_iters": {"mean": float(res["iters"].mean()), "max": int(res["iters"].max()),
                      "min": int(res["iters"].min())},
         "graph": ({"ms_per_step": graph_ms, "value": Ntot / (graph_ms / 1e3)}
@@ -723,7 +793,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the per-scan comparison step")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay")
-    ap.add_argument("--no-autotune", action="store_true", help="use the plan's default tile shape")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time the tile shapes on the first scans and step with the fastest (default: the "
+                         "plan's own shape, the one the full-size parity tests run)")
     ap.add_argument("--no-oracle-error", action="store_true", help="skip the oracle comparison")
     ap.add_argument("--no-secondary", action="store_true", help="skip the 30 GHz section and the added rows")
     ap.add_argument("--no-psd", action="store_true", help="skip the noise-PSD step measurement")

@@ -174,13 +174,71 @@ tod_status tod_plan_status(tod_plan *p, int32_t *detscan_status);
 
 /* Launch schedule of the transform stages (gain, n_corr):
  * TOD_SCHED_PERSISTENT (default): every pass of a stage is one launch over
- * the tiles of all detscans (the n_corr draw is one cooperative launch);
+ * the tiles of all detscans (the n_corr draw: a fixed sequence of pass
+ * launches, its CG iterations past the third in one cooperative launch);
  * TOD_SCHED_PER_SCAN: the same kernels launched once per detscan (the
  * plain per-scan path, kept for comparison).  Results are identical: each
  * detscan's arithmetic does not depend on the others or on the launch. */
 #define TOD_SCHED_PERSISTENT 0
 #define TOD_SCHED_PER_SCAN   1
 tod_status tod_plan_set_schedule(tod_plan *p, int32_t schedule);
+
+/* Per-kernel timing (no counterpart in the paper; for measurement).  While
+ * on, every kernel launch of this plan's calls is bracketed by two CUDA
+ * events on the call's stream, recorded with the kernel's class below.
+ * tod_plan_set_kernel_timing(p, 1) clears the records and starts timing,
+ * (p, 0) stops it (records are kept).  tod_plan_kernel_times synchronises
+ * on the recorded events and writes, per class, the summed milliseconds
+ * (HOST double[TOD_KT_COUNT], may be NULL) and the number of launches (HOST
+ * int32[TOD_KT_COUNT], may be NULL).  The events cost a few microseconds
+ * per launch: time the headline separately.  Calls on one plan must not
+ * overlap while timing is on.  tod_kernel_name gives a class's kernel name
+ * (NULL outside [0, TOD_KT_COUNT)). */
+enum {
+    TOD_KT_DECODE = 0,        /* k_decode of the pointing (pix and psi: two launches) */
+    TOD_KT_DECODE_TOD,        /* k_decode of the compressed TOD */
+    TOD_KT_DECODE_FLAGS,      /* k_decode of the compressed flag words */
+    TOD_KT_PROJECT,           /* k_project */
+    TOD_KT_PROJECT64,         /* k_project64 */
+    TOD_KT_DET_SCALARS,       /* k_det_scalars */
+    TOD_KT_GAIN_COLS,         /* k_gain_cols */
+    TOD_KT_GAIN_ROWS,         /* k_gain_rows */
+    TOD_KT_GAIN_COLSINV,      /* k_gain_colsinv */
+    TOD_KT_GAIN_FIN,          /* k_gain_fin */
+    TOD_KT_TOEP_H,            /* k_toep_h */
+    TOD_KT_TOEP_DURBIN,       /* k_toep_durbin */
+    TOD_KT_NC_FLAG_COUNT,     /* k_nc_flag_count */
+    TOD_KT_NC_FLAG_SCAN,      /* k_nc_flag_scan */
+    TOD_KT_NC_FLAG_WRITE,     /* k_nc_flag_write */
+    TOD_KT_NC_INDEX,          /* k_nc_index */
+    TOD_KT_NC_RHS_COLS,       /* k_nc_rhs_cols */
+    TOD_KT_NC_RHS_ROWS,       /* k_nc_rhs_rows */
+    TOD_KT_NC_X0_COLS,        /* k_nc_x0_cols */
+    TOD_KT_NC_CG_INIT,        /* k_nc_cg_init */
+    TOD_KT_NC_SCATTER,        /* k_nc_scatter of a CG iteration */
+    TOD_KT_NC_FILTER,         /* k_nc_filter of a CG iteration */
+    TOD_KT_NC_GATHER,         /* k_nc_gather of a CG iteration */
+    TOD_KT_NC_UPDATE,         /* k_nc_update */
+    TOD_KT_NC_TAIL,           /* k_nc_tail (cooperative: the remaining CG iterations) */
+    TOD_KT_NC_SCATTER_FINAL,  /* k_nc_scatter of the correction x = x0 + B^-1 E y */
+    TOD_KT_NC_FILTER_FINAL,   /* k_nc_filter of the correction */
+    TOD_KT_NC_GATHER_FINAL,   /* k_nc_gather of the correction */
+    TOD_KT_NC_FINISH,         /* k_nc_finish */
+    TOD_KT_BIN,               /* k_bin */
+    TOD_KT_REDUCE,            /* k_reduce */
+    TOD_KT_COMBINE,           /* k_combine */
+    TOD_KT_SOLVE,             /* k_solve */
+    TOD_KT_CHI2_COLS,         /* k_chi2_cols */
+    TOD_KT_CHI2_ROWS,         /* k_chi2_rows */
+    TOD_KT_CHI2_COLSINV,      /* k_chi2_colsinv */
+    TOD_KT_CHI2_FIN,          /* k_chi2_fin and k_chi2_total */
+    TOD_KT_PSD_SUMS,          /* k_psd_sums */
+    TOD_KT_PSD_STEP,          /* k_psd_begin and k_psd_step */
+    TOD_KT_COUNT
+};
+const char *tod_kernel_name(int32_t id);
+tod_status tod_plan_set_kernel_timing(tod_plan *p, int32_t on);
+tod_status tod_plan_kernel_times(tod_plan *p, double *ms_out, int32_t *launches_out);
 
 /* A1 -- Huffman decode + undo differencing (Sect. 4.1).
  * pix_out int32[N], psi_out uint16[N] (device).  Bit-exact.  The pointing

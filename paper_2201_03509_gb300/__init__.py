@@ -73,7 +73,8 @@ SYMBOLS = ["tod_status_string", "tod_fft_length", "tod_huff_encode", "tod_huff_f
            "tod_combine_partials", "tod_solve_range", "tod_decode", "tod_project", "tod_sample_gain", "tod_sample_ncorr", "tod_bin",
            "tod_solve_maps", "tod_ncorr_static_setup", "tod_sample_ncorr_static", "tod_ncorr_prepare",
            "tod_sample_ncorr_prepared", "tod_sample_noise_psd", "tod_plan_set_ncorr_spectrum",
-           "tod_plan_attach_data", "tod_decode_data", "tod_sample_gain_smooth"]
+           "tod_plan_attach_data", "tod_decode_data", "tod_sample_gain_smooth", "tod_kernel_name",
+           "tod_plan_set_kernel_timing", "tod_plan_kernel_times"]
 
 
 def build(force: bool = False) -> str:
@@ -102,6 +103,10 @@ def lib():
         L.tod_plan_info.argtypes = [_P, _P, _P, _P, _P, _P]
         L.tod_plan_status.argtypes = [_P, _P]
         L.tod_plan_set_schedule.argtypes = [_P, _i32]
+        L.tod_kernel_name.argtypes = [_i32]
+        L.tod_kernel_name.restype = ctypes.c_char_p
+        L.tod_plan_set_kernel_timing.argtypes = [_P, _i32]
+        L.tod_plan_kernel_times.argtypes = [_P, _P, _P]
         L.tod_decode.argtypes = [_P, _P, _P, _P]
         L.tod_project.argtypes = [_P, _P, _P, _P, _P, _P, _P]
         L.tod_sample_gain.argtypes = [_P, _P, _P, _P, _P, Rng, _i32, _P, _P, _P, _P]
@@ -124,7 +129,7 @@ def lib():
         L.tod_decode_data.argtypes = [_P, _P, _P, _P]
         L.tod_sample_gain_smooth.argtypes = [_P, _P, _P, _P, Rng, _i32, _f64, _i32, _P, _P, _P]
         for name in SYMBOLS:
-            if name not in ("tod_status_string", "tod_fft_length", "tod_huff_free"):
+            if name not in ("tod_status_string", "tod_fft_length", "tod_huff_free", "tod_kernel_name"):
                 getattr(L, name).restype = _i32
         _lib = L
     return _lib
@@ -218,6 +223,16 @@ def ingest(band, data_streams: bool = False) -> dict:
     if data_streams:
         out.update(ingest_data(band, off))
     return out
+
+
+def kernel_names() -> list:
+    """The kernel classes of tod_plan_kernel_times, in id order."""
+    out = []
+    while True:
+        nm = lib().tod_kernel_name(len(out))
+        if nm is None:
+            return out
+        out.append(nm.decode())
 
 
 def kept_lengths(cfg) -> np.ndarray:
@@ -337,6 +352,20 @@ class Plan:
 
     def set_schedule(self, schedule: int):
         _check(lib().tod_plan_set_schedule(self._h, int(schedule)), "tod_plan_set_schedule")
+
+    def set_kernel_timing(self, on: bool):
+        """Bracket every kernel launch of this plan with CUDA events on its
+        stream (on: records cleared) or stop (records kept)."""
+        _check(lib().tod_plan_set_kernel_timing(self._h, 1 if on else 0), "tod_plan_set_kernel_timing")
+
+    def kernel_times(self) -> dict:
+        """{kernel name: (milliseconds, launches)} of the launches recorded
+        while timing was on (synchronises on their events)."""
+        names = kernel_names()
+        ms = np.zeros(len(names), np.float64)
+        n = np.zeros(len(names), np.int32)
+        _check(lib().tod_plan_kernel_times(self._h, ms.ctypes.data, n.ctypes.data), "tod_plan_kernel_times")
+        return {nm: (float(ms[i]), int(n[i])) for i, nm in enumerate(names) if n[i] > 0}
 
     def status(self, raise_on_error: bool = True) -> np.ndarray:
         st = np.zeros(self.nq, dtype=np.int32)

@@ -15,6 +15,31 @@
 
 using namespace tg;
 
+namespace tg {
+
+KScope::KScope(const Plan &p, int32_t id, cudaStream_t st) : st_(st)
+{
+    KTimer &k = p.kt;
+    if (!k.on) return;
+    while (k.pool.size() < k.used + 2) {
+        cudaEvent_t ev = nullptr;
+        if (cudaEventCreate(&ev) != cudaSuccess) return;     // untimed, never an error of the launch
+        k.pool.push_back(ev);
+    }
+    cudaEvent_t start = k.pool[k.used];
+    stop_ = k.pool[k.used + 1];
+    k.used += 2;
+    k.ids.push_back(id);
+    cudaEventRecord(start, st_);
+}
+
+KScope::~KScope()
+{
+    if (stop_) cudaEventRecord(stop_, st_);
+}
+
+}  // namespace tg
+
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
@@ -208,6 +233,7 @@ void free_plan(Plan *p)
     cudaGetDevice(&cur);
     cudaSetDevice(p->device);
     for (void *a : p->allocs) cudaFree(a);
+    for (cudaEvent_t ev : p->kt.pool) cudaEventDestroy(ev);
     cudaSetDevice(cur);
     delete p;
 }
@@ -912,6 +938,57 @@ tod_status tod_plan_destroy(tod_plan *pl)
 {
     if (!pl) return TOD_ERR_ARG;
     free_plan(reinterpret_cast<Plan *>(pl));
+    return TOD_OK;
+}
+
+static const char *const kKernelNames[TOD_KT_COUNT] = {
+    "k_decode", "k_decode_tod", "k_decode_flags", "k_project", "k_project64", "k_det_scalars",
+    "k_gain_cols", "k_gain_rows", "k_gain_colsinv", "k_gain_fin", "k_toep_h", "k_toep_durbin",
+    "k_nc_flag_count", "k_nc_flag_scan", "k_nc_flag_write", "k_nc_index", "k_nc_rhs_cols", "k_nc_rhs_rows",
+    "k_nc_x0_cols", "k_nc_cg_init", "k_nc_scatter", "k_nc_filter", "k_nc_gather", "k_nc_update", "k_nc_tail",
+    "k_nc_scatter_final", "k_nc_filter_final", "k_nc_gather_final", "k_nc_finish", "k_bin", "k_reduce",
+    "k_combine", "k_solve", "k_chi2_cols", "k_chi2_rows", "k_chi2_colsinv", "k_chi2_fin", "k_psd_sums",
+    "k_psd_step"};
+
+const char *tod_kernel_name(int32_t id)
+{
+    return (id >= 0 && id < TOD_KT_COUNT) ? kKernelNames[id] : nullptr;
+}
+
+tod_status tod_plan_set_kernel_timing(tod_plan *pl, int32_t on)
+{
+    if (!pl || (on != 0 && on != 1)) return TOD_ERR_ARG;
+    Plan *p = reinterpret_cast<Plan *>(pl);
+    if (on) {
+        p->kt.used = 0;
+        p->kt.ids.clear();
+    }
+    p->kt.on = on != 0;
+    return TOD_OK;
+}
+
+tod_status tod_plan_kernel_times(tod_plan *pl, double *ms_out, int32_t *launches_out)
+{
+    if (!pl) return TOD_ERR_ARG;
+    Plan *p = reinterpret_cast<Plan *>(pl);
+    DeviceGuard dg(p->device);
+    std::vector<double> ms(TOD_KT_COUNT, 0.0);
+    std::vector<int32_t> n(TOD_KT_COUNT, 0);
+    for (size_t i = 0; i < p->kt.ids.size(); ++i) {
+        cudaEvent_t a = p->kt.pool[2 * i], b = p->kt.pool[2 * i + 1];
+        cudaError_t e = cudaEventSynchronize(b);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+        if (e != cudaSuccess) return to_status(e);
+        const int32_t id = p->kt.ids[i];
+        if (id < 0 || id >= TOD_KT_COUNT) continue;
+        ms[id] += t;
+        ++n[id];
+    }
+    for (int i = 0; i < TOD_KT_COUNT; ++i) {
+        if (ms_out) ms_out[i] = ms[i];
+        if (launches_out) launches_out[i] = n[i];
+    }
     return TOD_OK;
 }
 

@@ -84,6 +84,16 @@ struct CgState {
 };
 enum : int32_t { CG_NONE = 0, CG_ACTIVE = 1, CG_DONE = 2, CG_ALLFLAG = 3, CG_OVER = 4 };
 
+// Per-kernel timing (tod_plan_set_kernel_timing): while on, every launch of
+// the plan's kernels is bracketed by two events on its stream, recorded with
+// the kernel's class (TOD_KT_*); tod_plan_kernel_times adds them up.
+struct KTimer {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;   // created on demand, reused after a reset
+    size_t used = 0;                 // events of the pool in use
+    std::vector<int32_t> ids;        // class of record i, events pool[2i], pool[2i+1]
+};
+
 struct Plan {
     int device = 0;
     int32_t nside = 0, npix = 0, ndet = 0, nscan = 0, nq = 0;
@@ -163,7 +173,25 @@ struct Plan {
     int32_t tile_pairs = 0;          // requested column pairs per tile (0 = choose)
     int64_t device_bytes = 0;
     std::vector<void *> allocs;
+    mutable KTimer kt;
 };
+
+// Brackets one launch on stream st with the class id's events while the
+// plan's timing is on (a no-op otherwise).
+class KScope {
+public:
+    KScope(const Plan &p, int32_t id, cudaStream_t st);
+    ~KScope();
+    KScope(const KScope &) = delete;
+    KScope &operator=(const KScope &) = delete;
+private:
+    cudaStream_t st_;
+    cudaEvent_t stop_ = nullptr;
+};
+#define TG_KT_CAT2(a, b) a##b
+#define TG_KT_CAT(a, b) TG_KT_CAT2(a, b)
+// the launch that follows in the same scope is timed as class id (needs p and st)
+#define KTIME(id) ::tg::KScope TG_KT_CAT(kt_scope_, __LINE__)(p, (id), st)
 
 // launchers (return cudaError_t of the launch)
 cudaError_t setup_decode_kernel();

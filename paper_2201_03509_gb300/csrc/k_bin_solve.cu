@@ -372,11 +372,17 @@ cudaError_t launch_bin(const Plan &p, const uint16_t *psi, const float *d, const
     a.ld_t = p.ld_t; a.ld_pos = p.ld_pos; a.pair_start = p.pair_start; a.pair_len = p.pair_len; a.pair_slot = p.pair_slot;
     a.tile_q = p.bin_tile_q; a.tile_r0 = p.bin_tile_r0; a.trig = p.trig; a.ndet = p.ndet; a.rec = p.rec;
     a.adjoint = false; a.y64 = nullptr;
-    if (p.nbin_tiles > 0) k_bin<<<p.nbin_tiles, BIN_T, 0, st>>>(a);
+    if (p.nbin_tiles > 0) {
+        KTIME(TOD_KT_BIN);
+        k_bin<<<p.nbin_tiles, BIN_T, 0, st>>>(a);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int nb = (p.npix + 255) / 256;
-    k_reduce<<<nb, 256, 0, st>>>(p.rec, p.pix_slot_off, p.npix, A, b, hits, part);
+    {
+        KTIME(TOD_KT_REDUCE);
+        k_reduce<<<nb, 256, 0, st>>>(p.rec, p.pix_slot_off, p.npix, A, b, hits, part);
+    }
     return cudaGetLastError();
 }
 
@@ -398,11 +404,17 @@ cudaError_t launch_project_adjoint(const Plan &p, const uint16_t *psi, const voi
     a.ld_t = p.ld_t; a.ld_pos = p.ld_pos; a.pair_start = p.pair_start; a.pair_len = p.pair_len; a.pair_slot = p.pair_slot;
     a.tile_q = p.bin_tile_q; a.tile_r0 = p.bin_tile_r0; a.trig = p.trig; a.ndet = p.ndet; a.rec = p.rec;
     a.adjoint = true; a.y64 = fp64 ? static_cast<const double *>(y) : nullptr;
-    if (p.nbin_tiles > 0) k_bin<<<p.nbin_tiles, BIN_T, 0, st>>>(a);
+    if (p.nbin_tiles > 0) {
+        KTIME(TOD_KT_BIN);
+        k_bin<<<p.nbin_tiles, BIN_T, 0, st>>>(a);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int nb = (p.npix + 255) / 256;
-    k_reduce<<<nb, 256, 0, st>>>(p.rec, p.pix_slot_off, p.npix, nullptr, out, nullptr, nullptr);
+    {
+        KTIME(TOD_KT_REDUCE);
+        k_reduce<<<nb, 256, 0, st>>>(p.rec, p.pix_slot_off, p.npix, nullptr, out, nullptr, nullptr);
+    }
     return cudaGetLastError();
 }
 
@@ -410,6 +422,7 @@ cudaError_t launch_solve(const Plan &p, const double *A, const double *b, const 
                          double rcond_min, double *map, float4 *map32, double *rcond,
                          uint8_t *valid, cudaStream_t st)
 {
+    KTIME(TOD_KT_SOLVE);
     return launch_solve_n(p.npix, A, b, hits, rcond_min, map, map32, rcond, valid, st);
 }
 

@@ -178,15 +178,22 @@ cudaError_t setup_decode_kernel()
 
 namespace {
 
+template <int KIND> constexpr int32_t kind_id() {
+    return KIND == DEC_TOD ? TOD_KT_DECODE_TOD : KIND == DEC_FLAG ? TOD_KT_DECODE_FLAGS : TOD_KT_DECODE;
+}
+
 template <typename OutT, int KIND>
 cudaError_t decode_into(const Plan &p, const HuffDev &h, const double *scale, uint32_t select, OutT *out,
                         cudaStream_t st)
 {
     if (h.ncta == 0) return cudaSuccess;
     const size_t smem = sizeof(int32_t) * (1 << DEC_LUTB);
-    k_decode<OutT, KIND><<<h.ncta, DEC_T, smem, st>>>(
-        h.words, h.word_off, h.nbits, h.blk_off, h.ckpt_bit, h.ckpt_val, h.blk_q, h.lut, h.lim, h.base,
-        h.canon_off, h.canon_vals, h.cta_scan, h.cta_blk0, h.cta_nblk, p.off, scale, select, out, p.status);
+    {
+        KTIME(kind_id<KIND>());
+        k_decode<OutT, KIND><<<h.ncta, DEC_T, smem, st>>>(
+            h.words, h.word_off, h.nbits, h.blk_off, h.ckpt_bit, h.ckpt_val, h.blk_q, h.lut, h.lim, h.base,
+            h.canon_off, h.canon_vals, h.cta_scan, h.cta_blk0, h.cta_nblk, p.off, scale, select, out, p.status);
+    }
     return cudaGetLastError();
 }
 
@@ -272,8 +279,11 @@ cudaError_t launch_project64(const Plan &p, const double *map, const int32_t *pi
                              const double *gain, double *s_out, cudaStream_t st)
 {
     if (p.ntile == 0) return cudaSuccess;
-    k_project64<<<p.ntile, 256, 0, st>>>(map, pix, psi, gain, p.trig, p.tile_q, p.tile_t0, p.off, p.npix,
-                                         s_out, p.status);
+    {
+        KTIME(TOD_KT_PROJECT64);
+        k_project64<<<p.ntile, 256, 0, st>>>(map, pix, psi, gain, p.trig, p.tile_q, p.tile_t0, p.off, p.npix,
+                                             s_out, p.status);
+    }
     return cudaGetLastError();
 }
 
@@ -281,8 +291,11 @@ cudaError_t launch_project(const Plan &p, const float4 *map, const int32_t *pix,
                            const double *gain, float *s_out, cudaStream_t st)
 {
     if (p.ntile == 0) return cudaSuccess;
-    k_project<<<p.ntile, 256, 0, st>>>(map, pix, psi, gain, p.trig, p.tile_q, p.tile_t0, p.off, p.npix,
-                                       s_out, p.status);
+    {
+        KTIME(TOD_KT_PROJECT);
+        k_project<<<p.ntile, 256, 0, st>>>(map, pix, psi, gain, p.trig, p.tile_q, p.tile_t0, p.off, p.npix,
+                                           s_out, p.status);
+    }
     return cudaGetLastError();
 }
 

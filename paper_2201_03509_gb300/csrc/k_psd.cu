@@ -198,15 +198,24 @@ cudaError_t launch_noise_psd(const Plan &p, const float *spec, const double *psd
                              double step_lnfk, double step_al, double *psd_out, int32_t *acc_out,
                              double *loglike_out, cudaStream_t st)
 {
-    k_psd_begin<<<(p.ndet + 31) / 32, 32, 0, st>>>(psd_in, p.psd_state, p.ndet, psd_out, acc_out);
+    {
+        KTIME(TOD_KT_PSD_STEP);
+        k_psd_begin<<<(p.ndet + 31) / 32, 32, 0, st>>>(psd_in, p.psd_state, p.ndet, psd_out, acc_out);
+    }
     cudaError_t e = cudaGetLastError();
     for (int s = -1; s < nsteps && e == cudaSuccess; ++s) {
         if (p.ntile > 0)
-            k_psd_sums<<<p.ntile, PSD_T, 0, st>>>(spec, p.off, p.tile_q, p.tile_t0, p.lnfs, p.lnk, p.psd_state,
-                                                  p.ndet, p.psd_part);
-        k_psd_step<<<p.ndet, PSD_T, 0, st>>>(s, nsteps, p.psd_part, p.tile_q, p.ntile, p.ndet, p.psd_state,
-                                             psd_in, p.psd_nmodes, p.psd_sumlnf, rng, step_lnfk, step_al,
-                                             psd_out, acc_out, loglike_out);
+            {
+                KTIME(TOD_KT_PSD_SUMS);
+                k_psd_sums<<<p.ntile, PSD_T, 0, st>>>(spec, p.off, p.tile_q, p.tile_t0, p.lnfs, p.lnk, p.psd_state,
+                                                      p.ndet, p.psd_part);
+            }
+        {
+            KTIME(TOD_KT_PSD_STEP);
+            k_psd_step<<<p.ndet, PSD_T, 0, st>>>(s, nsteps, p.psd_part, p.tile_q, p.ntile, p.ndet, p.psd_state,
+                                                 psd_in, p.psd_nmodes, p.psd_sumlnf, rng, step_lnfk, step_al,
+                                                 psd_out, acc_out, loglike_out);
+        }
         e = cudaGetLastError();
     }
     return e;

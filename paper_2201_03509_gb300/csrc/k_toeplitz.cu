@@ -128,10 +128,16 @@ k_toep_durbin(const float *__restrict__ htab, float *__restrict__ xtab, int32_t 
 cudaError_t launch_toeplitz_prep(const Plan &p, const double *psd, cudaStream_t st)
 {
     dim3 g(TOEP_LMAX / HD, p.ndet);
-    k_toep_h<<<g, HT, 0, st>>>(psd, p.ndet, p.toep_nref, p.fsamp, p.htab);
+    {
+        KTIME(TOD_KT_TOEP_H);
+        k_toep_h<<<g, HT, 0, st>>>(psd, p.ndet, p.toep_nref, p.fsamp, p.htab);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_toep_durbin<<<p.ndet, DT, 0, st>>>(p.htab, p.xtab, p.lvalid);
+    {
+        KTIME(TOD_KT_TOEP_DURBIN);
+        k_toep_durbin<<<p.ndet, DT, 0, st>>>(p.htab, p.xtab, p.lvalid);
+    }
     return cudaGetLastError();
 }
 

@@ -1875,18 +1875,33 @@ cudaError_t launch_tx_gain(const Plan &p, const float *d, const float *s, const 
     a.ndet = p.ndet; a.fsamp = p.fsamp; a.obase = p.h_off[q0]; a.Y = p.ybuf; a.part = p.part; a.qsc = p.qsc;
     const int c0 = p.h_col_off[q0], c1 = p.h_col_off[q1], r0 = p.h_row_off[q0], r1 = p.h_row_off[q1];
     const size_t sm = tx_smem_bytes(false);
-    k_det_scalars<<<(q1 - q0 + 127) / 128, 128, 0, st>>>(psd, nullptr, p.off, p.ndet, p.fsamp, q0, q1, p.qsc);
+    {
+        KTIME(TOD_KT_DET_SCALARS);
+        k_det_scalars<<<(q1 - q0 + 127) / 128, 128, 0, st>>>(psd, nullptr, p.off, p.ndet, p.fsamp, q0, q1, p.qsc);
+    }
     // column items' partials at part[4 c], row items' at part[4 (ncol + r)]
     double *cpart = p.part;
     double *rpart = p.part + 4 * static_cast<int64_t>(p.h_col_off[p.nq]);
     a.items = p.colitems; a.item0 = c0; a.nitems = c1 - c0; a.part = cpart;
-    k_gain_cols<<<grid_for(p, a.nitems), TX_T, sm, st>>>(a);
+    {
+        KTIME(TOD_KT_GAIN_COLS);
+        k_gain_cols<<<grid_for(p, a.nitems), TX_T, sm, st>>>(a);
+    }
     a.items = p.rowitems; a.item0 = r0; a.nitems = r1 - r0; a.part = rpart;
-    k_gain_rows<<<grid_for(p, a.nitems), TX_T, sm, st>>>(a);
+    {
+        KTIME(TOD_KT_GAIN_ROWS);
+        k_gain_rows<<<grid_for(p, a.nitems), TX_T, sm, st>>>(a);
+    }
     a.items = p.colitems; a.item0 = c0; a.nitems = c1 - c0; a.part = cpart;
-    k_gain_colsinv<<<grid_for(p, a.nitems), TX_T, sm, st>>>(a);
-    k_gain_fin<<<(q1 - q0 + 255) / 256, 256, 0, st>>>(rpart, cpart, p.row_off, p.col_off, q0, q1, 0, 0, rng, mode,
-                                                      g, mu, sig, p.status);
+    {
+        KTIME(TOD_KT_GAIN_COLSINV);
+        k_gain_colsinv<<<grid_for(p, a.nitems), TX_T, sm, st>>>(a);
+    }
+    {
+        KTIME(TOD_KT_GAIN_FIN);
+        k_gain_fin<<<(q1 - q0 + 255) / 256, 256, 0, st>>>(rpart, cpart, p.row_off, p.col_off, q0, q1, 0, 0, rng, mode,
+                                                          g, mu, sig, p.status);
+    }
     return cudaGetLastError();
 }
 
@@ -1907,13 +1922,25 @@ static cudaError_t chi2_range(const Plan &p, const float *d, const void *s, cons
     double *cpart = p.part;
     double *rpart = p.part + 4 * static_cast<int64_t>(p.h_col_off[p.nq]);
     a.items = p.colitems; a.item0 = c0; a.nitems = c1 - c0; a.part = cpart;
-    k_chi2_cols<V><<<grid_for(p, a.nitems), TX_T, sm, st>>>(a);
+    {
+        KTIME(TOD_KT_CHI2_COLS);
+        k_chi2_cols<V><<<grid_for(p, a.nitems), TX_T, sm, st>>>(a);
+    }
     a.items = p.rowitems; a.item0 = r0; a.nitems = r1 - r0; a.part = rpart;
-    k_chi2_rows<V><<<grid_for(p, a.nitems), TX_T, sm, st>>>(a);
+    {
+        KTIME(TOD_KT_CHI2_ROWS);
+        k_chi2_rows<V><<<grid_for(p, a.nitems), TX_T, sm, st>>>(a);
+    }
     a.items = p.colitems; a.item0 = c0; a.nitems = c1 - c0; a.part = cpart;
-    k_chi2_colsinv<V><<<grid_for(p, a.nitems), TX_T, sm, st>>>(a);
-    k_chi2_fin<<<(q1 - q0 + 255) / 256, 256, 0, st>>>(rpart, cpart, p.row_off, p.col_off, q0, q1, 0, 0, chi2_q, dgain,
-                                                       dpsd_q);
+    {
+        KTIME(TOD_KT_CHI2_COLSINV);
+        k_chi2_colsinv<V><<<grid_for(p, a.nitems), TX_T, sm, st>>>(a);
+    }
+    {
+        KTIME(TOD_KT_CHI2_FIN);
+        k_chi2_fin<<<(q1 - q0 + 255) / 256, 256, 0, st>>>(rpart, cpart, p.row_off, p.col_off, q0, q1, 0, 0, chi2_q, dgain,
+                                                           dpsd_q);
+    }
     return cudaGetLastError();
 }
 
@@ -1936,7 +1963,10 @@ cudaError_t launch_tx_chi2(const Plan &p, bool fp64, const float *d, const void 
         }
     }
     if (e != cudaSuccess) return e;
-    k_chi2_total<<<1, 1, 0, st>>>(chi2_q, dpsd_q, p.nq, p.ndet, total, dpsd_det);
+    {
+        KTIME(TOD_KT_CHI2_FIN);
+        k_chi2_total<<<1, 1, 0, st>>>(chi2_q, dpsd_q, p.nq, p.ndet, total, dpsd_det);
+    }
     return cudaGetLastError();
 }
 
@@ -1961,35 +1991,86 @@ cudaError_t launch_tx_ncorr(const Plan &p, const float *d, const float *s, const
     const int gq = std::min(nq, std::max(1, grid));
     // flag index (the chunked scan uses the same grid for count and write)
     const int gf = std::max(1, std::min(p.pass_grid, grid));
-    k_nc_flag_count<<<gf, TX_T, 0, st>>>(a);
-    k_nc_flag_scan<<<1, 1, 0, st>>>(a, gf);
-    k_nc_flag_write<<<gf, TX_T, 0, st>>>(a);
-    k_nc_index<<<gq, TX_T, 0, st>>>(a);
+    {
+        KTIME(TOD_KT_NC_FLAG_COUNT);
+        k_nc_flag_count<<<gf, TX_T, 0, st>>>(a);
+    }
+    {
+        KTIME(TOD_KT_NC_FLAG_SCAN);
+        k_nc_flag_scan<<<1, 1, 0, st>>>(a, gf);
+    }
+    {
+        KTIME(TOD_KT_NC_FLAG_WRITE);
+        k_nc_flag_write<<<gf, TX_T, 0, st>>>(a);
+    }
+    {
+        KTIME(TOD_KT_NC_INDEX);
+        k_nc_index<<<gq, TX_T, 0, st>>>(a);
+    }
     // x0 = B^{-1} b
-    k_nc_rhs_cols<<<gc, TX_T, s32, st>>>(a);
-    k_nc_rhs_rows<<<gr, TX_T, s32, st>>>(a);
-    k_nc_x0_cols<<<gc, TX_T, s32, st>>>(a);
+    {
+        KTIME(TOD_KT_NC_RHS_COLS);
+        k_nc_rhs_cols<<<gc, TX_T, s32, st>>>(a);
+    }
+    {
+        KTIME(TOD_KT_NC_RHS_ROWS);
+        k_nc_rhs_rows<<<gr, TX_T, s32, st>>>(a);
+    }
+    {
+        KTIME(TOD_KT_NC_X0_COLS);
+        k_nc_x0_cols<<<gc, TX_T, s32, st>>>(a);
+    }
     // CG on the Schur complement
-    k_nc_cg_init<<<gq, TX_T, sgb, st>>>(a);
+    {
+        KTIME(TOD_KT_NC_CG_INIT);
+        k_nc_cg_init<<<gq, TX_T, sgb, st>>>(a);
+    }
     int par = 0;
     for (int it = 0; it < NC_LAUNCHED_ITERS; ++it, par ^= 1) {
-        k_nc_scatter<false><<<gc, TX_T, s32, st>>>(a, par);
-        k_nc_filter<false><<<gr, TX_T, s32, st>>>(a, par);
-        k_nc_gather<false><<<gc, TX_T, s32, st>>>(a, par);
-        k_nc_update<<<gq, TX_T, sgb, st>>>(a, par);
+        {
+            KTIME(TOD_KT_NC_SCATTER);
+            k_nc_scatter<false><<<gc, TX_T, s32, st>>>(a, par);
+        }
+        {
+            KTIME(TOD_KT_NC_FILTER);
+            k_nc_filter<false><<<gr, TX_T, s32, st>>>(a, par);
+        }
+        {
+            KTIME(TOD_KT_NC_GATHER);
+            k_nc_gather<false><<<gc, TX_T, s32, st>>>(a, par);
+        }
+        {
+            KTIME(TOD_KT_NC_UPDATE);
+            k_nc_update<<<gq, TX_T, sgb, st>>>(a, par);
+        }
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int tail_par = par;
     void *args[] = {&a, &tail_par};
-    e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_nc_tail), dim3(std::max(1, std::min(grid, p.coop_grid))),
-                                    dim3(TX_T), args, sgb, st);
+    {
+        KTIME(TOD_KT_NC_TAIL);
+        e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_nc_tail),
+                                        dim3(std::max(1, std::min(grid, p.coop_grid))), dim3(TX_T), args, sgb, st);
+    }
     if (e != cudaSuccess) return e;
     // x = x0 + B^{-1} E y for every detscan that ran the CG
-    k_nc_scatter<true><<<gc, TX_T, s32, st>>>(a, 0);
-    k_nc_filter<true><<<gr, TX_T, s32, st>>>(a, 0);
-    k_nc_gather<true><<<gc, TX_T, s32, st>>>(a, 0);
-    k_nc_finish<<<(nq + 255) / 256, 256, 0, st>>>(a);
+    {
+        KTIME(TOD_KT_NC_SCATTER_FINAL);
+        k_nc_scatter<true><<<gc, TX_T, s32, st>>>(a, 0);
+    }
+    {
+        KTIME(TOD_KT_NC_FILTER_FINAL);
+        k_nc_filter<true><<<gr, TX_T, s32, st>>>(a, 0);
+    }
+    {
+        KTIME(TOD_KT_NC_GATHER_FINAL);
+        k_nc_gather<true><<<gc, TX_T, s32, st>>>(a, 0);
+    }
+    {
+        KTIME(TOD_KT_NC_FINISH);
+        k_nc_finish<<<(nq + 255) / 256, 256, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -176,7 +176,8 @@ class GibbsTODStep:
                                 self.cg_iters, self.cg_tol, self.cg_maxiter, hp)
         if lookahead:
             # the next step's pointing (the compressed streams do not change),
-            # decoded at low priority on the SMs the n_corr clusters leave idle
+            # decoded at low priority: its CTAs fill the SMs between the
+            # n_corr pass kernels' CTAs and in the draw's serial tails
             if self._pix_next is None:
                 self._pix_next = torch.empty_like(self.pix)
                 self._psi_next = torch.empty_like(self.psi)
