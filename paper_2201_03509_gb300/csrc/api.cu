@@ -6,6 +6,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <functional>
+#include <map>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <thread>
@@ -292,6 +294,72 @@ int tile_width(int P2, int m1, int tile_pairs)
     return tp;
 }
 
+// Shared-memory bank conflicts of the row FFTs of a row tile with nslot
+// rows at stride m2p: butterfly w of a Stockham pass (radix R after Ns
+// points) works on row w mod nslot, index j = w / nslot, reading elements
+// j + r L/R and writing (j / Ns) Ns R + j mod Ns + r Ns.  Returned: the mean
+// number of extra 8-byte wavefronts per half-warp access, over the first
+// eight warps' first two reads and writes of every pass.
+double row_bank_cost(int m2, int m2p, int nslot, const std::vector<int8_t> &radices)
+{
+    int Ns = 1;
+    double extra = 0.0;
+    int count = 0;
+    for (int R : radices) {
+        const int LR = m2 / R, total = nslot * LR;
+        for (int w0 = 0; w0 < std::min(total, TX_T); w0 += 32)
+            for (int half = 0; half < 32; half += 16)
+                for (int rd = 0; rd < 2; ++rd)
+                    for (int r = 0; r < 2; ++r) {
+                        int hits[16] = {0};
+                        int used = 0, worst = 0;
+                        for (int i = 0; i < 16; ++i) {
+                            const int w = w0 + half + i;
+                            if (w >= total) break;
+                            const int j = w / nslot, vec = w - j * nslot;
+                            int e;
+                            if (rd) e = j + r * LR;
+                            else { const int jq = j / Ns, k = j - jq * Ns; e = jq * Ns * R + k + r * Ns; }
+                            const int b = (vec * m2p + e) & 15;
+                            worst = std::max(worst, ++hits[b]);
+                            ++used;
+                        }
+                        if (used) { extra += worst - 1; ++count; }
+                    }
+        Ns *= R;
+    }
+    return count ? extra / count : 0.0;
+}
+
+// Row tile shape for row FFTs of length m2: TR row pairs, a power of two
+// (so a warp's butterflies spread evenly over the rows), and the row
+// stride m2p in [m2, m2 + 16] with the fewest bank conflicts; more row
+// pairs win unless they cost more than a quarter wavefront per access.
+void row_shape(int m2, int P1, const std::vector<int8_t> &radices, int &TR, int &m2p)
+{
+    // the shape depends on (m2, P1 up to 64) alone: remembered across lengths
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, std::pair<int, int>> seen;
+    const std::pair<int, int> key(m2, std::min(P1, 65));
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        const auto it = seen.find(key);
+        if (it != seen.end()) { TR = it->second.first; m2p = it->second.second; return; }
+    }
+    double best = 1e30;
+    TR = 1;
+    m2p = m2 | 1;
+    for (int tr = 1; tr <= 64 && 2 * tr * m2 <= TX_TILE; tr *= 2) {
+        if (tr > 1 && tr / 2 >= P1) break;          // more row pairs than the transform has
+        for (int p = m2; p <= m2 + 16 && 2 * tr * p <= TX_TILE; ++p) {
+            const double score = row_bank_cost(m2, p, 2 * tr, radices) - 0.25 * std::log2(static_cast<double>(tr));
+            if (score < best - 1e-12) { best = score; TR = tr; m2p = p; }
+        }
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    seen[key] = std::make_pair(TR, m2p);
+}
+
 // Split m = n/2 = m1 x m2 for the multi-pass transform.  A column tile holds
 // m1 rows of 2 TP columns and a row tile 2 TR rows of m2 (made odd), each at
 // most TX_TILE values.  Wide column tiles (TP up to 16: sample runs of 64
@@ -321,11 +389,11 @@ bool choose_tx_split(int n, int rmax, int tile_pairs, TxLen &out)
     const int m1 = bm1, m2 = m / m1;
     const auto r1 = radix_plan(m1, rmax), r2 = radix_plan(m2, rmax);
     std::memset(&out, 0, sizeof(out));
-    out.n = n; out.m = m; out.m1 = m1; out.m2 = m2; out.m2p = m2 | 1;
+    out.n = n; out.m = m; out.m1 = m1; out.m2 = m2;
     out.P1 = m1 / 2 + 1;
     out.P2 = (m2 + 1) / 2;
     out.TP = tile_width(out.P2, m1, tile_pairs);
-    out.TR = std::min(out.P1, TX_TILE / (2 * out.m2p));
+    row_shape(m2, out.P1, r2, out.TR, out.m2p);
     out.nr1 = static_cast<int32_t>(r1.size());
     out.nr2 = static_cast<int32_t>(r2.size());
     fill_stages(out.s1, r1, m1);

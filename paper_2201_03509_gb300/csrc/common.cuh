@@ -69,15 +69,31 @@ __device__ __forceinline__ u64x4 philox4x64(uint64_t c0, uint64_t c1, uint64_t c
 // Normals 2j, 2j+1 (j = 0..3) of a Philox block: 32-bit halves h (low half
 // of each word first) give uniforms u = ((h >> 9) + 1/2) 2^-23 (exact in
 // FP32), and the pair is sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).
+// FP32 on the SFU: ln u1 from lg2.approx (absolute error about 2^-22.6 in
+// log2 u1), or for 1 - u1 = v < 2^-10 from -v - v^2/2 (v exact, truncation
+// below 3e-7 relative), where a fixed absolute error would dominate;
+// sqrt(t) = t rsqrt.approx(t); the angle 2 pi u2 = pi + 2 pi (u2 - 1/2)
+// reduced to [-pi, pi) for sin/cos.approx (absolute error about 2^-20.9).
+// A normal's error stays near 1e-6 absolute, far inside the draws' FP32
+// transform budget.
 __device__ __forceinline__ float2 philox_normal_pair(const u64x4 &w, int j) {
     const uint64_t word = w.x[j];
     const uint32_t h0 = static_cast<uint32_t>(word), h1 = static_cast<uint32_t>(word >> 32);
     const float u1 = (static_cast<float>(h0 >> 9) + 0.5f) * 1.1920928955078125e-07f;  // 2^-23
+    const float v1 = (static_cast<float>(0x7FFFFFu - (h0 >> 9)) + 0.5f) * 1.1920928955078125e-07f;  // 1 - u1
     const float u2 = (static_cast<float>(h1 >> 9) + 0.5f) * 1.1920928955078125e-07f;
-    const float r = sqrtf(-2.0f * logf(u1));
-    float s, c;
-    sincospif(2.0f * u2, &s, &c);
-    return make_float2(r * c, r * s);
+    float lg;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"(u1));
+    const float lnu = v1 < 9.765625e-4f ? -v1 * fmaf(0.5f, v1, 1.0f) : 0.69314718055994531f * lg;
+    const float t = -2.0f * lnu;                       // > 0
+    float rs;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(t));
+    const float r = t * rs;
+    const float ang = 6.28318530717958648f * (u2 - 0.5f);
+    float sn, cs;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(sn) : "f"(ang));
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(cs) : "f"(ang));
+    return make_float2(-r * cs, -r * sn);
 }
 
 // The pair of normals (2i', 2i'+1) with i' = idx/2 of stream (q, purpose, it);

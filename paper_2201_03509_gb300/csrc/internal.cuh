@@ -61,7 +61,7 @@ constexpr int TX_GBMAX = 256;         // preconditioner gap blocks per detscan
 constexpr int TX_GBCAP = 2048;        // padded preconditioner elements staged per round
 
 struct alignas(16) TxLen {
-    int32_t n, m, m1, m2, m2p;        // m2p: row stride of a row tile (m2 made odd)
+    int32_t n, m, m1, m2, m2p;        // m2p: row stride of a row tile (>= m2, chosen against bank conflicts)
     int32_t P1, P2;                   // row pairs m1/2 + 1, column pairs (m2 + 1)/2
     int32_t TP, TR;                   // column pairs per column tile, row pairs per row tile
     int32_t nr1, nr2;                 // radix stages of the column and row FFTs

@@ -108,9 +108,30 @@ __device__ __forceinline__ void cta_share(int nitems, int &i0, int &i1) {
     i1 = min(nitems, i0 + per);
 }
 
-// (f_k / f_knee)^alpha at DCT mode k, FP32
+// The SFU's approximate base-2 logarithm and exponential and reciprocal
+// (PTX lg2/ex2/rcp.approx: absolute error about 2^-22 in the logarithm,
+// relative about 2^-22 in the others).  Used for the per-mode noise weights,
+// where their error (below 1e-6 relative in a weight) is far inside the
+// transforms' FP32 budget.
+__device__ __forceinline__ float sfu_lg2(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sfu_ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sfu_rcp(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// (f_k / f_knee)^alpha at DCT mode k >= 1, FP32 (fscale = fsamp / (2 n f_knee))
 __device__ __forceinline__ float tx_fpow(int k, float fscale, float alpha) {
-    return exp2f(alpha * log2f(static_cast<float>(k) * fscale));
+    return sfu_ex2(alpha * sfu_lg2(static_cast<float>(k) * fscale));
 }
 
 // twiddle block of a length: W_m1^i, W_m2^i, W_4n^{k1}, W_4n^{m1 k2},
@@ -590,8 +611,8 @@ __global__ void __launch_bounds__(TX_T, 3) k_gain_rows(GainTx a)
         Acc2 sa[1] = {{0.f, 0.f}};
         row_pass<float2, true>(X, b0, b1, a.Y, a.tw + X.L.twb, [](float2 *) {}, [&](int, int k, float2 S) {
             const int ka = k, kb = (k == 0) ? m : n - k;
-            const float wa = ka == 0 ? 0.f : 1.0f / (s2 * (1.0f + tx_fpow(ka, fscale, alpha)));
-            const float wb = 1.0f / (s2 * (1.0f + tx_fpow(kb, fscale, alpha)));
+            const float wa = ka == 0 ? 0.f : sfu_rcp(s2 * (1.0f + tx_fpow(ka, fscale, alpha)));
+            const float wb = sfu_rcp(s2 * (1.0f + tx_fpow(kb, fscale, alpha)));
             const float2 Wv = make_float2(S.x * wa, S.y * wb);
             acc_add_prod(sa[0], S.x, Wv.x);
             acc_add_prod(sa[0], S.y, Wv.y);
@@ -1283,8 +1304,8 @@ __device__ void nc_rhs_rows(const NcorrTx &a, const TxCtx &X, float2 *b0, float2
             const int ka = k, kb = (k == 0) ? m : n - k;
             const float ra = nc_r(ka, X), rb = nc_r(kb, X);
             float ba, bb;
-            if (allf) { ba = ka == 0 ? 0.f : s2 / ra; bb = s2 / rb; }
-            else { ba = s2 / (1.0f + ra); bb = s2 / (1.0f + rb); }
+            if (allf) { ba = ka == 0 ? 0.f : s2 * sfu_rcp(ra); bb = s2 * sfu_rcp(rb); }
+            else { ba = s2 * sfu_rcp(1.0f + ra); bb = s2 * sfu_rcp(1.0f + rb); }
             const float2 cb = make_float2(Yv.x + nu[e].x, Yv.y + nu[e].y);
             const float2 xs = make_float2(cb.x * ba, cb.y * bb);
             if (spec) { spec[ka] = xs.x; spec[kb] = xs.y; }
@@ -1366,11 +1387,12 @@ __device__ void nc_filter_rows(const NcorrTx &a, const TxCtx &X, float2 *b0, flo
         const int ka = k, kb = (k == 0) ? m : n - k;
         const float ra = nc_r(ka, X), rb = nc_r(kb, X);
         float2 r;
+        const float ia = sfu_rcp(1.0f + ra), ib = sfu_rcp(1.0f + rb);
         if (BETA) {
-            r = make_float2(Yv.x * (s2 / (1.0f + ra)), Yv.y * (s2 / (1.0f + rb)));
+            r = make_float2(Yv.x * (s2 * ia), Yv.y * (s2 * ib));
             if (spec) { spec[ka] += r.x; spec[kb] += r.y; }
         } else {
-            r = make_float2(Yv.x * (s2 * ra / (1.0f + ra)), Yv.y * (s2 * rb / (1.0f + rb)));
+            r = make_float2(Yv.x * (s2 * ra * ia), Yv.y * (s2 * rb * ib));
         }
         return r;
     });
