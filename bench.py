@@ -396,7 +396,7 @@ def measure_step(args, cfg, arr, ing, local, rank, ws, label="main"):
                 plain_ms=plain_ms, tuned=tuned, status_errors=int(np.count_nonzero(st)), lens=lens,
                 flagged=flagged,
                 comp_bytes=int(ing["pix_streams"]["words"].nbytes + ing["psi_streams"]["words"].nbytes),
-                npairs=int(getattr(plan, "npairs", 0) or 0))
+                npairs=int(plan.info()["nruns"]))
 
 
 def roofline_and_stages(res, peaks, peak_src):

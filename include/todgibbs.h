@@ -167,6 +167,10 @@ tod_status tod_plan_destroy(tod_plan *p);
 /* Sizes of the plan (host scalars; any pointer may be NULL). */
 tod_status tod_plan_info(const tod_plan *p, int64_t *nsamples, int32_t *ndetscan,
                          int32_t *npix, int32_t *tile_pairs, int64_t *device_bytes);
+/* Sizes of the plan's binning structure (host scalars; any pointer may be
+ * NULL): runs (the samples of one (detscan, pixel) pair; one record of 80
+ * bytes each per binning) and binning tiles. */
+tod_status tod_plan_binning_info(const tod_plan *p, int64_t *nruns, int32_t *ntiles);
 /* Synchronises the device, copies the per-detscan status words
  * (TOD_OK or an error code) into HOST int32[ndetscan] (may be NULL), clears
  * them, and returns the first error found (TOD_OK if none). */
@@ -219,6 +223,7 @@ enum {
     TOD_KT_NC_FILTER,         /* k_nc_filter of a CG iteration */
     TOD_KT_NC_GATHER,         /* k_nc_gather of a CG iteration */
     TOD_KT_NC_UPDATE,         /* k_nc_update */
+    TOD_KT_NC_LIST,           /* k_nc_list (the detscans a CG pass works on) */
     TOD_KT_NC_TAIL,           /* k_nc_tail (cooperative: the remaining CG iterations) */
     TOD_KT_NC_SCATTER_FINAL,  /* k_nc_scatter of the correction x = x0 + B^-1 E y */
     TOD_KT_NC_FILTER_FINAL,   /* k_nc_filter of the correction */

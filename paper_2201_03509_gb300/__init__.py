@@ -74,7 +74,7 @@ SYMBOLS = ["tod_status_string", "tod_fft_length", "tod_huff_encode", "tod_huff_f
            "tod_solve_maps", "tod_ncorr_static_setup", "tod_sample_ncorr_static", "tod_ncorr_prepare",
            "tod_sample_ncorr_prepared", "tod_sample_noise_psd", "tod_plan_set_ncorr_spectrum",
            "tod_plan_attach_data", "tod_decode_data", "tod_sample_gain_smooth", "tod_kernel_name",
-           "tod_plan_set_kernel_timing", "tod_plan_kernel_times"]
+           "tod_plan_set_kernel_timing", "tod_plan_kernel_times", "tod_plan_binning_info"]
 
 
 def build(force: bool = False) -> str:
@@ -107,6 +107,7 @@ def lib():
         L.tod_kernel_name.restype = ctypes.c_char_p
         L.tod_plan_set_kernel_timing.argtypes = [_P, _i32]
         L.tod_plan_kernel_times.argtypes = [_P, _P, _P]
+        L.tod_plan_binning_info.argtypes = [_P, _P, _P]
         L.tod_decode.argtypes = [_P, _P, _P, _P]
         L.tod_project.argtypes = [_P, _P, _P, _P, _P, _P, _P]
         L.tod_sample_gain.argtypes = [_P, _P, _P, _P, _P, Rng, _i32, _P, _P, _P, _P]
@@ -344,8 +345,10 @@ class Plan:
         ns, nq, npix, cs, nb = _i64(), _i32(), _i32(), _i32(), _i64()
         _check(lib().tod_plan_info(self._h, ctypes.byref(ns), ctypes.byref(nq), ctypes.byref(npix),
                                    ctypes.byref(cs), ctypes.byref(nb)), "tod_plan_info")
+        nr, nt = _i64(), _i32()
+        _check(lib().tod_plan_binning_info(self._h, ctypes.byref(nr), ctypes.byref(nt)), "tod_plan_binning_info")
         return dict(nsamples=ns.value, ndetscan=nq.value, npix=npix.value, tile_pairs=cs.value,
-                    device_bytes=nb.value)
+                    device_bytes=nb.value, nruns=nr.value, nbin_tiles=nt.value)
 
     SCHED_PERSISTENT = 0
     SCHED_PER_SCAN = 1

@@ -856,6 +856,8 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
         if ((e = dev_upload(*p, p->cgv, static_cast<float *>(nullptr), static_cast<size_t>(5 * p->cgcap))))
             return fail(e);
         if ((e = dev_upload(*p, p->cg_count, static_cast<int32_t *>(nullptr), 2))) return fail(e);
+        if ((e = dev_upload(*p, p->nclist, static_cast<int32_t *>(nullptr), 3 * static_cast<size_t>(p->nq) + 3)))
+            return fail(e);
         if ((e = dev_upload(*p, p->chi2_dpsd, static_cast<double *>(nullptr), 3 * static_cast<size_t>(p->nq))))
             return fail(e);
         if ((e = dev_upload(*p, p->qsc, static_cast<float4 *>(nullptr), 2 * static_cast<size_t>(p->nq))))
@@ -1013,7 +1015,7 @@ static const char *const kKernelNames[TOD_KT_COUNT] = {
     "k_decode", "k_decode_tod", "k_decode_flags", "k_project", "k_project64", "k_det_scalars",
     "k_gain_cols", "k_gain_rows", "k_gain_colsinv", "k_gain_fin", "k_toep_h", "k_toep_durbin",
     "k_nc_flag_count", "k_nc_flag_scan", "k_nc_flag_write", "k_nc_index", "k_nc_rhs_cols", "k_nc_rhs_rows",
-    "k_nc_x0_cols", "k_nc_cg_init", "k_nc_scatter", "k_nc_filter", "k_nc_gather", "k_nc_update", "k_nc_tail",
+    "k_nc_x0_cols", "k_nc_cg_init", "k_nc_scatter", "k_nc_filter", "k_nc_gather", "k_nc_update", "k_nc_list", "k_nc_tail",
     "k_nc_scatter_final", "k_nc_filter_final", "k_nc_gather_final", "k_nc_finish", "k_bin", "k_reduce",
     "k_combine", "k_solve", "k_chi2_cols", "k_chi2_rows", "k_chi2_colsinv", "k_chi2_fin", "k_psd_sums",
     "k_psd_step"};
@@ -1057,6 +1059,15 @@ tod_status tod_plan_kernel_times(tod_plan *pl, double *ms_out, int32_t *launches
         if (ms_out) ms_out[i] = ms[i];
         if (launches_out) launches_out[i] = n[i];
     }
+    return TOD_OK;
+}
+
+tod_status tod_plan_binning_info(const tod_plan *pl, int64_t *nruns, int32_t *ntiles)
+{
+    if (!pl) return TOD_ERR_ARG;
+    const Plan *p = reinterpret_cast<const Plan *>(pl);
+    if (nruns) *nruns = p->npairs;
+    if (ntiles) *ntiles = p->nbin_tiles;
     return TOD_OK;
 }
 

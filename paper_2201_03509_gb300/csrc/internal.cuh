@@ -166,6 +166,7 @@ struct Plan {
     float *cgv = nullptr;            // [5][cgcap] CG vectors y, r, p, q, z by flagged rank
     int64_t cgcap = 0;
     int32_t *cg_count = nullptr;     // [2] active detscans (alternating)
+    int32_t *nclist = nullptr;       // [3 nq + 3] detscans of a CG pass with their item counts
     double *chi2_dpsd = nullptr;     // [nq][3] per-detscan PSD terms of the chi^2 gradient
     float4 *qsc = nullptr;           // [nq][2] per-detscan FP32 noise scalars of the current call
     int32_t coop_grid = 0;           // co-resident CTAs of the cooperative n_corr kernel

@@ -971,7 +971,13 @@ struct NcorrTx {
     int64_t cgcap;
     int32_t *count;               // [2]
     float4 *qsc;                  // [nq][2] per-detscan FP32 scalars, written in the index phase
+    // the detscans a CG pass works on, in order, with the running counts of
+    // their column and row items: list[0] = n, then q[nq], col[nq + 1], row[nq + 1]
+    int32_t *list;
 };
+__device__ __forceinline__ int32_t *nl_q(const NcorrTx &a) { return a.list + 1; }
+__device__ __forceinline__ int32_t *nl_col(const NcorrTx &a) { return a.list + 1 + (a.q1 - a.q0); }
+__device__ __forceinline__ int32_t *nl_row(const NcorrTx &a) { return a.list + 2 + 2 * (a.q1 - a.q0); }
 
 struct CgVec { float *y, *r, *p, *q, *z; };
 __device__ __forceinline__ CgVec cg_vecs(const NcorrTx &a) {
@@ -1672,37 +1678,113 @@ __device__ void nc_cg_update(const NcorrTx &a, NcShared &S, int q, float *gb, in
 
 // ---------------------------------------------------------------------------
 // The n_corr kernels.  Each pass is its own launch over the tiles of the
-// launch range (skipping detscans that the pass does not concern); the CG
-// runs a fixed number of iterations as launches of their own, and a
+// launch range, or of the detscans a CG pass concerns (a list rebuilt after
+// every CG update); the CG runs a fixed number of iterations as launches of
+// their own (each returns at once when no detscan is iterating), and a
 // cooperative tail kernel finishes any detscan still iterating (grid
 // barriers between its passes; it returns at once when none is).
 // ---------------------------------------------------------------------------
-// Work items of the launch range: a contiguous share per CTA when every
-// detscan takes part (tiles of one length together), grid-stride when only
-// the detscans still iterating do (their tiles spread over every CTA).
-template <class Keep, class Fn>
-__device__ __forceinline__ void nc_items(const NcorrTx &a, TxCtx &X, bool rows, int &cur, Keep keep, Fn fn,
-                                         bool stride = false)
+// Every work item of the launch range, a contiguous share per CTA (tiles of
+// one length together).
+template <class Fn>
+__device__ __forceinline__ void nc_items(const NcorrTx &a, TxCtx &X, bool rows, int &cur, Fn fn)
 {
     const int2 *items = rows ? a.rowitems : a.colitems;
     const int j0 = rows ? a.row_off[a.q0] : a.col_off[a.q0];
     const int j1 = rows ? a.row_off[a.q1] : a.col_off[a.q1];
-    int i0, i1, step = 1;
+    int i0, i1;
     cta_share(j1 - j0, i0, i1);
-    if (stride) { i0 = blockIdx.x; i1 = j1 - j0; step = gridDim.x; }
-    for (int it = j0 + i0; it < j0 + i1; it += step) {
+    for (int it = j0 + i0; it < j0 + i1; ++it) {
         const int2 w = items[it];
-        const int md = a.cgs[w.x].mode;
-        if (!keep(md)) continue;
         tx_begin(X, a.txl, a.q_tx, a.off, w.x, w.y, a.off[a.q0], a.ndet, a.fsamp, a.psd, a.gain, cur, a.qsc);
-        if (threadIdx.x == 0) { X.mode = md; X.koff = a.cgs[w.x].koff; }
+        if (threadIdx.x == 0) { X.mode = a.cgs[w.x].mode; X.koff = a.cgs[w.x].koff; }
         __syncthreads();
         fn();
     }
 }
-__device__ __forceinline__ bool nc_all(int) { return true; }
-__device__ __forceinline__ bool nc_active(int md) { return md == CG_ACTIVE; }
-__device__ __forceinline__ bool nc_ran(int md) { return md == CG_DONE; }
+
+// The list of the launch range's detscans in CG mode `want` (ascending),
+// with exclusive running counts of their column and row items.  One CTA
+// (any multiple of 32 threads up to 1024) builds it.
+__device__ void nc_build_list(const NcorrTx &a, int want)
+{
+    __shared__ int s_w[32][3];
+    __shared__ int s_base[3], s_tot[3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) { s_base[0] = 0; s_base[1] = 0; s_base[2] = 0; }
+    __syncthreads();
+    int32_t *lq = nl_q(a), *lc = nl_col(a), *lr = nl_row(a);
+    for (int c0 = a.q0; c0 < a.q1; c0 += blockDim.x) {
+        const int q = c0 + threadIdx.x;
+        const bool in = q < a.q1 && a.cgs[q].mode == want;
+        int v[3] = {in ? 1 : 0, in ? a.col_off[q + 1] - a.col_off[q] : 0, in ? a.row_off[q + 1] - a.row_off[q] : 0};
+        int x[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            int t = v[k];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += u;
+            }
+            x[k] = t - v[k];                       // exclusive within the warp
+            if (lane == 31) s_w[warp][k] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) {                     // warp totals -> exclusive warp offsets
+            int acc = 0;
+            for (int w = 0; w < nw; ++w) { const int t = s_w[w][threadIdx.x]; s_w[w][threadIdx.x] = acc; acc += t; }
+            s_tot[threadIdx.x] = acc;
+        }
+        __syncthreads();
+        if (in) {
+            const int i = s_base[0] + s_w[warp][0] + x[0];
+            lq[i] = q;
+            lc[i] = s_base[1] + s_w[warp][1] + x[1];
+            lr[i] = s_base[2] + s_w[warp][2] + x[2];
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) s_base[threadIdx.x] += s_tot[threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        a.list[0] = s_base[0];
+        lc[s_base[0]] = s_base[1];
+        lr[s_base[0]] = s_base[2];
+    }
+}
+__global__ void __launch_bounds__(1024) k_nc_list(NcorrTx a, int want, int par)
+{
+    if (par >= 0 && *reinterpret_cast<volatile const int32_t *>(a.count + par) == 0) return;
+    nc_build_list(a, want);
+}
+
+// The listed detscans' column (or row) items, a contiguous share per CTA:
+// consecutive items of a CTA are mostly tiles of one detscan.
+template <class Fn>
+__device__ __forceinline__ void nc_list_items(const NcorrTx &a, TxCtx &X, bool rows, int &cur, Fn fn)
+{
+    const int n = *reinterpret_cast<volatile const int32_t *>(a.list);
+    if (n <= 0) return;
+    const int32_t *lq = nl_q(a), *lo = rows ? nl_row(a) : nl_col(a);
+    int i0, i1;
+    cta_share(lo[n], i0, i1);
+    if (i0 >= i1) return;
+    int pos = 0, hi = n - 1;                      // last detscan whose items start at or before i0
+    while (pos < hi) {
+        const int mid = (pos + hi + 1) >> 1;
+        if (lo[mid] <= i0) pos = mid; else hi = mid - 1;
+    }
+    for (int ii = i0; ii < i1; ++ii) {
+        while (lo[pos + 1] <= ii) ++pos;
+        const int q = lq[pos];
+        tx_begin(X, a.txl, a.q_tx, a.off, q, ii - lo[pos], a.off[a.q0], a.ndet, a.fsamp, a.psd, a.gain, cur, a.qsc);
+        if (threadIdx.x == 0) { X.mode = a.cgs[q].mode; X.koff = a.cgs[q].koff; }
+        __syncthreads();
+        fn();
+    }
+}
+
 
 __global__ void __launch_bounds__(TX_T) k_nc_flag_count(NcorrTx a)
 {
@@ -1736,7 +1818,7 @@ __global__ void __launch_bounds__(TX_T, 3) k_nc_rhs_cols(NcorrTx a)
     __shared__ TxCtx X;
     const uint64_t gi = a.rng.gibbs_iter_dev ? *a.rng.gibbs_iter_dev : a.rng.gibbs_iter;
     int cur = -1;
-    nc_items(a, X, false, cur, nc_all, [&] { nc_rhs_cols(a, X, tx_smem, tx_smem + TX_TILE, gi); });
+    nc_items(a, X, false, cur, [&] { nc_rhs_cols(a, X, tx_smem, tx_smem + TX_TILE, gi); });
 }
 __global__ void __launch_bounds__(TX_T, 3) k_nc_rhs_rows(NcorrTx a)
 {
@@ -1744,14 +1826,14 @@ __global__ void __launch_bounds__(TX_T, 3) k_nc_rhs_rows(NcorrTx a)
     __shared__ TxCtx X;
     const uint64_t gi = a.rng.gibbs_iter_dev ? *a.rng.gibbs_iter_dev : a.rng.gibbs_iter;
     int cur = -1;
-    nc_items(a, X, true, cur, nc_all, [&] { nc_rhs_rows(a, X, tx_smem, tx_smem + TX_TILE, gi); });
+    nc_items(a, X, true, cur, [&] { nc_rhs_rows(a, X, tx_smem, tx_smem + TX_TILE, gi); });
 }
 __global__ void __launch_bounds__(TX_T, 3) k_nc_x0_cols(NcorrTx a)
 {
     extern __shared__ __align__(16) float2 tx_smem[];
     __shared__ TxCtx X;
     int cur = -1;
-    nc_items(a, X, false, cur, nc_all, [&] { nc_x0_cols(a, X, tx_smem, tx_smem + TX_TILE); });
+    nc_items(a, X, false, cur, [&] { nc_x0_cols(a, X, tx_smem, tx_smem + TX_TILE); });
 }
 __global__ void __launch_bounds__(TX_T, 3) k_nc_cg_init(NcorrTx a)
 {
@@ -1775,8 +1857,7 @@ __global__ void __launch_bounds__(TX_T, 3) k_nc_scatter(NcorrTx a, int par)
     }
     const CgVec V = cg_vecs(a);
     int cur = -1;
-    if (FINAL) nc_items(a, X, false, cur, nc_ran, [&] { nc_scatter_cols(a, X, tx_smem, tx_smem + TX_TILE, V.y); }, true);
-    else nc_items(a, X, false, cur, nc_active, [&] { nc_scatter_cols(a, X, tx_smem, tx_smem + TX_TILE, V.p); }, true);
+    nc_list_items(a, X, false, cur, [&] { nc_scatter_cols(a, X, tx_smem, tx_smem + TX_TILE, FINAL ? V.y : V.p); });
 }
 template <bool FINAL>
 __global__ void __launch_bounds__(TX_T, 3) k_nc_filter(NcorrTx a, int par)
@@ -1785,8 +1866,7 @@ __global__ void __launch_bounds__(TX_T, 3) k_nc_filter(NcorrTx a, int par)
     __shared__ TxCtx X;
     if (!FINAL && *reinterpret_cast<volatile const int32_t *>(a.count + par) == 0) return;
     int cur = -1;
-    if (FINAL) nc_items(a, X, true, cur, nc_ran, [&] { nc_filter_rows<true>(a, X, tx_smem, tx_smem + TX_TILE); }, true);
-    else nc_items(a, X, true, cur, nc_active, [&] { nc_filter_rows<false>(a, X, tx_smem, tx_smem + TX_TILE); }, true);
+    nc_list_items(a, X, true, cur, [&] { nc_filter_rows<FINAL>(a, X, tx_smem, tx_smem + TX_TILE); });
 }
 template <bool FINAL>
 __global__ void __launch_bounds__(TX_T, 3) k_nc_gather(NcorrTx a, int par)
@@ -1796,20 +1876,28 @@ __global__ void __launch_bounds__(TX_T, 3) k_nc_gather(NcorrTx a, int par)
     if (!FINAL && *reinterpret_cast<volatile const int32_t *>(a.count + par) == 0) return;
     const CgVec V = cg_vecs(a);
     int cur = -1;
-    if (FINAL) nc_items(a, X, false, cur, nc_ran, [&] { nc_gather_cols<true>(a, X, tx_smem, tx_smem + TX_TILE, nullptr); }, true);
-    else nc_items(a, X, false, cur, nc_active, [&] { nc_gather_cols<false>(a, X, tx_smem, tx_smem + TX_TILE, V.q); }, true);
+    nc_list_items(a, X, false, cur,
+                  [&] { nc_gather_cols<FINAL>(a, X, tx_smem, tx_smem + TX_TILE, FINAL ? nullptr : V.q); });
+}
+// the listed (iterating) detscans' CG update
+__device__ __forceinline__ void nc_update_listed(const NcorrTx &a, NcShared &S, float *gb, int32_t *count_next)
+{
+    const int n = *reinterpret_cast<volatile const int32_t *>(a.list);
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        __syncthreads();
+        nc_cg_update(a, S, nl_q(a)[i], gb, count_next);
+    }
 }
 __global__ void __launch_bounds__(TX_T, 3) k_nc_update(NcorrTx a, int par)
 {
     extern __shared__ __align__(16) float2 tx_smem[];
     __shared__ NcShared S;
     if (*reinterpret_cast<volatile const int32_t *>(a.count + par) == 0) return;
-    for (int q = a.q0 + blockIdx.x; q < a.q1; q += gridDim.x) {
-        __syncthreads();
-        nc_cg_update(a, S, q, reinterpret_cast<float *>(tx_smem), a.count + (par ^ 1));
-    }
+    nc_update_listed(a, S, reinterpret_cast<float *>(tx_smem), a.count + (par ^ 1));
 }
-// The iterations left after the launched ones, in one cooperative launch.
+// The iterations left after the launched ones, in one cooperative launch:
+// the passes over the listed detscans with grid barriers between them, the
+// list rebuilt by CTA 0 after each update.
 __global__ void __launch_bounds__(TX_T, 2) k_nc_tail(NcorrTx a, int par)
 {
     extern __shared__ __align__(16) float2 tx_smem[];
@@ -1819,17 +1907,16 @@ __global__ void __launch_bounds__(TX_T, 2) k_nc_tail(NcorrTx a, int par)
     int cur = -1;
     for (;;) {
         if (*reinterpret_cast<volatile const int32_t *>(a.count + par) == 0) break;
+        if (blockIdx.x == 0) nc_build_list(a, CG_ACTIVE);
+        grid.sync();
         if (blockIdx.x == 0 && threadIdx.x == 0) a.count[par ^ 1] = 0;
-        nc_items(a, S.X, false, cur, nc_active, [&] { nc_scatter_cols(a, S.X, tx_smem, tx_smem + TX_TILE, V.p); }, true);
+        nc_list_items(a, S.X, false, cur, [&] { nc_scatter_cols(a, S.X, tx_smem, tx_smem + TX_TILE, V.p); });
         grid.sync();
-        nc_items(a, S.X, true, cur, nc_active, [&] { nc_filter_rows<false>(a, S.X, tx_smem, tx_smem + TX_TILE); }, true);
+        nc_list_items(a, S.X, true, cur, [&] { nc_filter_rows<false>(a, S.X, tx_smem, tx_smem + TX_TILE); });
         grid.sync();
-        nc_items(a, S.X, false, cur, nc_active, [&] { nc_gather_cols<false>(a, S.X, tx_smem, tx_smem + TX_TILE, V.q); }, true);
+        nc_list_items(a, S.X, false, cur, [&] { nc_gather_cols<false>(a, S.X, tx_smem, tx_smem + TX_TILE, V.q); });
         grid.sync();
-        for (int q = a.q0 + blockIdx.x; q < a.q1; q += gridDim.x) {
-            __syncthreads();
-            nc_cg_update(a, S, q, reinterpret_cast<float *>(tx_smem), a.count + (par ^ 1));
-        }
+        nc_update_listed(a, S, reinterpret_cast<float *>(tx_smem), a.count + (par ^ 1));
         grid.sync();
         par ^= 1;
     }
@@ -1849,7 +1936,7 @@ __global__ void k_nc_finish(NcorrTx a)
 // ===========================================================================
 static size_t tx_smem_bytes(bool fp64) { return (fp64 ? sizeof(double2) : sizeof(float2)) * 2 * TX_TILE; }
 constexpr size_t kGbBytes = 5 * TX_GBCAP * sizeof(float);           // preconditioner staging
-constexpr int NC_LAUNCHED_ITERS = 3;                                // CG iterations as separate launches
+constexpr int NC_LAUNCHED_ITERS = 8;                                // CG iterations as separate launches
 
 template <class K>
 static cudaError_t smem_attr(K k, size_t bytes) {
@@ -2005,7 +2092,7 @@ cudaError_t launch_tx_ncorr(const Plan &p, const float *d, const float *s, const
     a.maxit = maxit; a.x_out = x; a.iters = iters; a.status = p.status; a.spec_out = p.spec_out;
     a.xtab = p.use_prec ? p.xtab : nullptr; a.lvalid = p.lvalid;
     a.Y = sc.Y; a.wpre = sc.wpre; a.chunk = p.chunk; a.cgs = p.cgs; a.gblk = p.gblk; a.gnb = p.gnb;
-    a.cgv = sc.cgv; a.cgcap = sc.cgcap; a.count = p.cg_count; a.qsc = p.qsc;
+    a.cgv = sc.cgv; a.cgcap = sc.cgcap; a.count = p.cg_count; a.qsc = p.qsc; a.list = p.nclist;
     const size_t s32 = tx_smem_bytes(false), sgb = std::max(s32, kGbBytes);
     const int nq = q1 - q0;
     const int ncol = p.h_col_off[q1] - p.h_col_off[q0], nrow = p.h_row_off[q1] - p.h_row_off[q0];
@@ -2048,6 +2135,10 @@ cudaError_t launch_tx_ncorr(const Plan &p, const float *d, const float *s, const
         k_nc_cg_init<<<gq, TX_T, sgb, st>>>(a);
     }
     int par = 0;
+    {
+        KTIME(TOD_KT_NC_LIST);
+        k_nc_list<<<1, 1024, 0, st>>>(a, CG_ACTIVE, par);
+    }
     for (int it = 0; it < NC_LAUNCHED_ITERS; ++it, par ^= 1) {
         {
             KTIME(TOD_KT_NC_SCATTER);
@@ -2065,6 +2156,10 @@ cudaError_t launch_tx_ncorr(const Plan &p, const float *d, const float *s, const
             KTIME(TOD_KT_NC_UPDATE);
             k_nc_update<<<gq, TX_T, sgb, st>>>(a, par);
         }
+        {
+            KTIME(TOD_KT_NC_LIST);
+            k_nc_list<<<1, 1024, 0, st>>>(a, CG_ACTIVE, par ^ 1);
+        }
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -2076,6 +2171,10 @@ cudaError_t launch_tx_ncorr(const Plan &p, const float *d, const float *s, const
                                         dim3(std::max(1, std::min(grid, p.coop_grid))), dim3(TX_T), args, sgb, st);
     }
     if (e != cudaSuccess) return e;
+    {
+        KTIME(TOD_KT_NC_LIST);
+        k_nc_list<<<1, 1024, 0, st>>>(a, CG_DONE, -1);
+    }
     // x = x0 + B^{-1} E y for every detscan that ran the CG
     {
         KTIME(TOD_KT_NC_SCATTER_FINAL);

@@ -207,9 +207,10 @@ class GibbsTODStep:
         self._mark_d_done(stream)
 
     # decode x2, project, gain (scalars, three passes, draw), Toeplitz prep x2,
-    # n_corr (flag index 4, right-hand side 3, CG start, 3 launched CG
-    # iterations x 4, cooperative tail, correction 3, finish), bin + reduce, solve
-    LAUNCHES_PER_STEP = 2 + 1 + 5 + 2 + 25 + 2 + 1
+    # n_corr (flag index 4, right-hand side 3, CG start and its list, 8
+    # launched CG iterations x (3 passes, update, list), cooperative tail,
+    # list, correction 3, finish), bin + reduce, solve
+    LAUNCHES_PER_STEP = 2 + 1 + 5 + 2 + (4 + 3 + 2 + 8 * 5 + 1 + 1 + 3 + 1) + 2 + 1
     DATA_LAUNCHES = 2       # with data_streams: decode of the TOD and of the flags
 
     @property
