@@ -496,8 +496,9 @@ cudaError_t build_huff(Plan &p, HuffDev &d, const tod_huff_streams &h)
     return cudaSuccess;
 }
 
-// The n_corr draw over the whole band (one cooperative launch) or, with the
-// per-scan schedule, one launch per detscan.
+// The n_corr draw over the whole band (each pass one launch over every
+// detscan's tiles) or, with the per-scan schedule, one launch sequence per
+// detscan.
 cudaError_t ncorr_draw(const Plan &p, const float *d, const float *s, const double *gain, const uint32_t *flags,
                        const double *psd, tod_rng rng, int mode, float tol, int maxit, float *x, int32_t *iters,
                        cudaStream_t st)
@@ -505,12 +506,12 @@ cudaError_t ncorr_draw(const Plan &p, const float *d, const float *s, const doub
     const TxNcorrScratch sc = {p.ybuf, p.wpre, p.cgv, p.cgcap};
     if (p.schedule != TOD_SCHED_PER_SCAN)
         return launch_tx_ncorr(p, d, s, gain, flags, psd, rng, mode, tol, maxit, x, iters, st, 0, p.nq, sc,
-                               p.coop_grid);
+                               p.pass_grid);
     cudaError_t e = cudaSuccess;
     for (int q = 0; q < p.nq && e == cudaSuccess; ++q) {
         const int items = std::max(p.h_col_off[q + 1] - p.h_col_off[q], p.h_row_off[q + 1] - p.h_row_off[q]);
         e = launch_tx_ncorr(p, d, s, gain, flags, psd, rng, mode, tol, maxit, x, iters, st, q, q + 1, sc,
-                            std::min(p.coop_grid, std::max(1, items)));
+                            std::min(p.pass_grid, std::max(1, items)));
     }
     return e;
 }
@@ -846,7 +847,7 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
             return fail(e);
         if ((e = dev_upload(*p, p->wpre, static_cast<int64_t *>(nullptr), static_cast<size_t>(p->N / 32 + 3))))
             return fail(e);
-        if ((e = dev_upload(*p, p->chunk, static_cast<int64_t *>(nullptr), static_cast<size_t>(p->coop_grid + 1))))
+        if ((e = dev_upload(*p, p->chunk, static_cast<int64_t *>(nullptr), static_cast<size_t>(std::max(p->coop_grid, p->pass_grid) + 1))))
             return fail(e);
         if ((e = dev_upload(*p, p->cgs, static_cast<CgState *>(nullptr), static_cast<size_t>(p->nq)))) return fail(e);
         if ((e = dev_upload(*p, p->gblk, static_cast<int2 *>(nullptr), static_cast<size_t>(p->nq) * TX_GBMAX)))

@@ -231,7 +231,8 @@ struct TxNcorrScratch {
 cudaError_t setup_tx_kernels(Plan &p);
 cudaError_t launch_tx_gain(const Plan &p, const float *d, const float *s, const uint32_t *flags, const double *psd,
                            tod_rng rng, int mode, double *g, double *mu, double *sig, cudaStream_t st, int q0, int q1);
-// one cooperative launch over detscans [q0, q1) with `grid` CTAs (at most p.coop_grid)
+// the draw over detscans [q0, q1): pass kernels with at most `grid` CTAs
+// (at most p.pass_grid), the cooperative tail with at most p.coop_grid
 cudaError_t launch_tx_ncorr(const Plan &p, const float *d, const float *s, const double *gain,
                             const uint32_t *flags, const double *psd, tod_rng rng, int mode, float tol, int maxit,
                             float *x, int32_t *iters, cudaStream_t st, int q0, int q1, const TxNcorrScratch &sc,

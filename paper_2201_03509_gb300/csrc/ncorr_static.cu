@@ -121,9 +121,9 @@ tod_status tod_sample_ncorr_static(tod_plan *pl, const float *d, const float *s,
         int items = 0;
         for (int q = q0; q < q1; ++q)
             items = std::max(items, std::max(p->h_col_off[q + 1] - p->h_col_off[q], p->h_row_off[q + 1] - p->h_row_off[q]));
-        const int grid = std::min(p->coop_grid, std::max(1, (p->h_col_off[q1] - p->h_col_off[q0])));
+        const int grid = std::min(p->pass_grid, std::max(1, (p->h_col_off[q1] - p->h_col_off[q0])));
         e = launch_tx_ncorr(*p, d, s, gain, flags, psd, rng, mode, tol, maxit, ncorr_out, cg_iters_out, stream, q0,
-                            q1, sc, std::max(1, std::min(p->coop_grid, std::max(grid, items))));
+                            q1, sc, std::max(1, std::min(p->pass_grid, std::max(grid, items))));
         q0 = q1;
     }
     if (prev != p->device) cudaSetDevice(prev);
