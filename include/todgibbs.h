@@ -274,7 +274,10 @@ tod_status tod_decode(tod_plan *p, int32_t *pix_out, uint16_t *psi_out, cudaStre
  *   mu, sigma: DEVICE double[ndetscan]; prior: DEVICE double[ndet][2]
  *   (sigma_g > 0, alpha_g); gain_out: DEVICE double[ndetscan];
  *   cg_iters_out: DEVICE int32[ndet] or NULL.
- * TOD_ERR_ARG (host) when nscan > TOD_GAIN_SMOOTH_MAX_SCANS.
+ * TOD_ERR_ARG (host) when nscan > TOD_GAIN_SMOOTH_MAX_SCANS.  A detector
+ * whose prior has sigma_g not > 0 (or zero once squared in FP32), or a
+ * non-finite sigma_g or alpha_g, gets TOD_ERR_ARG in the status word of
+ * each of its detscans and gains of 0; the other detectors are drawn.
  * ------------------------------------------------------------------------- */
 #define TOD_GAIN_SMOOTH_MAX_SCANS 4096
 tod_status tod_sample_gain_smooth(tod_plan *p, const double *mu, const double *sigma, const double *prior,

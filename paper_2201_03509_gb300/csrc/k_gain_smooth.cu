@@ -123,6 +123,22 @@ __global__ void __launch_bounds__(GS_T) k_gain_smooth(GainSmoothArgs g)
     float *x = ph + S, *r = x + S, *z = r + S, *p = z + S, *q = p + S, *t = q + S;
     const int tid = threadIdx.x;
 
+    // the detector's prior: sigma_g > 0 (also after rounding to FP32, where
+    // the prior precision is held) and alpha_g finite, else every detscan of
+    // the detector is marked TOD_ERR_ARG and its gain set to 0
+    {
+        const double sgp = g.prior[2 * det], alp = g.prior[2 * det + 1];
+        const float sgf = static_cast<float>(sgp);
+        if (!(sgp > 0.0) || !isfinite(sgp) || !isfinite(alp) || !(sgf * sgf > 0.0f) || !isfinite(sgf * sgf)) {
+            for (int s = tid; s < S; s += GS_T) {
+                set_status(g.status, s * g.ndet + det, TOD_ERR_ARG);
+                g.gain_out[static_cast<int64_t>(s) * g.ndet + det] = 0.0;
+            }
+            if (tid == 0 && g.iters_out) g.iters_out[det] = 0;
+            return;
+        }
+    }
+
     // quarter wave in FP64 (m <= S), the rest by symmetry; the normalisation once
     for (int m = tid; m <= S; m += GS_T)
         cosT[cpad(m)] = static_cast<float>(cospi(static_cast<double>(m) / (2.0 * S)));

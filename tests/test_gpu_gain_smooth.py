@@ -130,7 +130,19 @@ def test_misuse():
     sigma[3] = 0.0
     with pytest.raises(tg.TodError):                         # marked on the device, raised by status
         _run(plan, mu, sigma, [(1e-3, -2.0)] * 2, 0)
+    # a bad prior (sigma_g of zero, below the FP32 range, or NaN; alpha_g
+    # infinite): every detscan of that detector is marked, the other detector runs
+    mu, sigma = _inputs(2, 8, 1)
     dev = torch.device("cuda:0")
+    t_mu, t_sig = torch.from_numpy(mu).to(dev), torch.from_numpy(sigma).to(dev)
+    for bad in ((0.0, -2.0), (1e-30, -2.0), (float("nan"), -2.0), (1e-3, float("inf"))):
+        t_pr = torch.tensor([bad, (1e-3, -2.0)], dtype=torch.float64, device=dev)
+        g = torch.full_like(t_mu, float("nan"))
+        plan.sample_gain_smooth(t_mu, t_sig, t_pr, tg.Rng(SEED, BAND, IT), 0, g)
+        st = plan.status(raise_on_error=False)
+        g = g.cpu().numpy()
+        assert np.all(st[0::2] == -1) and np.all(st[1::2] == 0), bad
+        assert np.all(g[0::2] == 0.0) and np.all(np.isfinite(g[1::2])), bad
     t = torch.zeros(16, dtype=torch.float64, device=dev)
     with pytest.raises(tg.TodError):                         # bad mode
         plan.sample_gain_smooth(t, t, t, tg.Rng(1, 0, 0), 7, t)
