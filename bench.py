@@ -654,6 +654,79 @@ def secondary_section(args, local):
     return out
 
 
+def sweep_section(args, local):
+    """The multi-band Gibbs sweep: the 30, 44 and 70 GHz-like bands of 1500
+    scans (7.2e9 samples per iteration) on one GPU, each band's step on its
+    own stream, `--sweep-iters` iterations carrying maps and noise
+    parameters (one Metropolis step of the noise PSD per iteration); the
+    first iteration is checked against the oracle on sampled detscans of
+    every band and is not timed."""
+    import torch
+    import synth
+    import oracle
+    import paper_2201_03509_gb300 as tg
+    from paper_2201_03509_gb300.sweep import BandChain, MultiBandSweep
+    t_set = time.time()
+    chains, keep = [], []
+    for b, name in enumerate(synth.SWEEP_BANDS):
+        cfg = synth.CONFIGS[name]
+        arr, ing = build_band(cfg)
+        plan = tg.Plan(cfg.nside, cfg.ndet, cfg.nscan, cfg.fsamp, ing["offsets"], ing["pix_streams"],
+                       ing["psi_streams"], device=local)
+        chains.append(BandChain(plan, arr.psd, ing["flag_words"], ing["tod"], arr.map_tqu, b,
+                                cg_tol=args.cg_tol, psd_steps=1))
+        keep.append((cfg, arr, ing))
+        torch.cuda.synchronize()
+    sw = MultiBandSweep(chains)
+    setup_s = time.time() - t_set
+    # iteration 0 (untimed): the truth map and noise parameters in, checked
+    sw.run(1, args.seed, it0=0)
+    errs = []
+    for (cfg, arr, ing), c in zip(keep, chains):
+        c.plan.status()
+        off = ing["offsets"]
+        lens = np.diff(off)
+        qs = sorted({0, int(np.argmax(lens)), len(lens) - 1})
+        g = c.step.gain.cpu().numpy()
+        e = {"band": cfg.name, "gain": 0.0, "ncorr": 0.0, "detscans": qs}
+        for q in qs:
+            a, bq = int(off[q]), int(off[q + 1])
+            n = bq - a
+            det = q % cfg.ndet
+            pr = oracle.decode_detscan(ing["pix_streams"], q, n, cfg.ndet)
+            qr = oracle.decode_detscan(ing["psi_streams"], q, n, cfg.ndet)
+            sref = oracle.project(arr.map_tqu, pr, qr)
+            s0, fk, al = arr.psd[det]
+            d = ing["tod"][a:bq].astype(np.float64)
+            M = (~ing["flags"][a:bq]).astype(np.float64)
+            P = oracle.noise_psd(n, cfg.fsamp, s0, fk, al)
+            rg, _, _ = oracle.sample_gain(sref, d, M, P, oracle.gain_normal(args.seed, c.band_id, q, 0))
+            x, _ = oracle.sample_ncorr(d, sref, rg, M, s0, fk, al, cfg.fsamp,
+                                       oracle.omega1(args.seed, c.band_id, q, 0, n),
+                                       oracle.omega2(args.seed, c.band_id, q, 0, n))
+            xg = c.step.ncorr[a:bq].cpu().numpy().astype(np.float64)
+            e["gain"] = max(e["gain"], abs(g[q] - rg) / abs(rg))
+            e["ncorr"] = max(e["ncorr"], float(np.linalg.norm(xg - x) / np.linalg.norm(x)))
+        errs.append(e)
+    del keep
+    sampler = ClockSampler(local)
+    sampler.start()
+    res = sw.run(args.sweep_iters, args.seed, it0=1)
+    clocks = sampler.stop()
+    for c in chains:
+        c.plan.status()
+    out = {"bands": [c.plan.info()["nsamples"] for c in chains], "band_names": list(synth.SWEEP_BANDS),
+           "iterations": args.sweep_iters, "samples_per_iteration": res["samples_per_iteration"],
+           "ms_per_iteration": res["ms"] / args.sweep_iters,
+           "value": res["samples_per_iteration"] * args.sweep_iters / (res["ms"] / 1e3), "unit": "samples/s",
+           "band_ms_to_last_iteration": res["band_ms"], "clocks": clocks, "setup_s": setup_s,
+           "psd_steps_per_iteration": 1, "oracle_error_first_iteration": errs,
+           "timing": "CUDA events on the caller's stream around all iterations; bands on their own streams"}
+    for c in chains:
+        c.plan.close()
+    return out
+
+
 def run_ours(args):
     import torch
     import synth
@@ -727,6 +800,10 @@ def run_ours(args):
     torch.cuda.empty_cache()
     if rank == 0 and ws == 1 and not args.no_secondary and args.workload != SECONDARY:
         out["secondary"] = secondary_section(args, local)
+    if rank == 0 and ws == 1 and args.sweep:
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        out["sweep"] = sweep_section(args, local)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, cfg, budget_s=args.cpu_seconds)
     if rank == 0:
@@ -790,6 +867,9 @@ def main():
     ap.add_argument("--cpu-detscans", type=int, default=64)
     ap.add_argument("--ref-detscans-per-step", type=int, default=1)
     ap.add_argument("--tune-scans", type=int, default=12)
+    ap.add_argument("--sweep", action="store_true",
+                    help="also run the 3-band (30/44/70 GHz-like, 7.2e9 samples) Gibbs sweep section")
+    ap.add_argument("--sweep-iters", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the per-scan comparison step")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay")

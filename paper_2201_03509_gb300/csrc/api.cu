@@ -400,6 +400,10 @@ bool choose_tx_split(int n, int rmax, int tile_pairs, TxLen &out)
     fill_stages(out.s2, r2, m2);
     out.f_m2 = make_fastdiv(static_cast<uint32_t>(m2));
     out.f_W = make_fastdiv(static_cast<uint32_t>(2 * out.TP));
+    out.lgW = 0;
+    while ((2 << out.lgW) <= 2 * out.TP) ++out.lgW;
+    out.lgS = 0;
+    while ((2 << out.lgS) <= 2 * out.TR) ++out.lgS;
     out.f_2TR = make_fastdiv(static_cast<uint32_t>(2 * out.TR));
     out.sq_fwd = std::sqrt(2.0 / n);
     out.s0_fwd = 1.0 / std::sqrt(static_cast<double>(n));

@@ -186,65 +186,67 @@ template <int R, bool INV, class V> struct RDft {
 
 // ---------------------------------------------------------------------------
 // One out-of-place Stockham pass (radix R after Ns points are done) over
-// nvec vectors of length L in shared memory: element e of vector c at
-// src[c * vs + e * es].  Butterfly w: vector-fast (w -> vector w mod nvec)
-// when vfast, else element-fast.  Pass twiddles W_L^{r k Lr/(Ns R)}... read
-// from tw (W_L^i, i < L, global).  NT threads; the caller synchronises.
-// Radices 16, 10, 9, 8, 6, 5, 4, 3, 2.
+// the 2^lgv vectors of length L of a tile in shared memory: element e of
+// vector c at c + e 2^lgv (COL: a tile of columns) or c * stride + e (rows).
+// Thread t keeps vector t mod 2^lgv (2^lgv divides NT) and takes the
+// butterflies j = t >> lgv, j + (NT >> lgv), ..; pass twiddles
+// W_L^{r k L/(Ns R)} (k = j mod Ns) from tw (W_L^i, i < L, global).  The
+// caller synchronises.  Radices 16, 10, 9, 8, 6, 5, 4, 3, 2.
 // ---------------------------------------------------------------------------
-template <int R, bool INV, int NT, class V>
+template <int R, bool INV, int NT, bool COL, class V>
 __device__ __forceinline__ void sp_pass(const V *__restrict__ src, V *__restrict__ dst, int L, const DctStage &st,
-                                        int nvec, const FastDiv &fnvec, int es, int vs, bool vfast,
-                                        const V *__restrict__ tw)
+                                        int lgv, int stride, const V *__restrict__ tw)
 {
     const int LR = L / R;
     const int Ns = st.Ns;
-    const int tstep = L / (Ns * R);
-    const int total = nvec * LR;
-    for (int w = threadIdx.x; w < total; w += NT) {
-        int vec, j;
-        if (vfast) { j = fdiv(w, fnvec); vec = w - j * nvec; }
-        else { vec = fdiv(w, st.fLR); j = w - vec * LR; }
-        const V *p = src + vec * vs + j * es;
+    const int tstep = fdiv(LR, st.fNs);                                             // L / (Ns R)
+    const int vec = threadIdx.x & ((1 << lgv) - 1);
+    const int es = COL ? (1 << lgv) : 1;
+    const int base = COL ? vec : vec * stride;
+    const V *s0 = src + base;
+    V *d0 = dst + base;
+    const int ls = LR * es, ns = Ns * es;
+    for (int j = threadIdx.x >> lgv; j < LR; j += NT >> lgv) {
+        const V *p = s0 + j * es;
         V v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = p[r * LR * es];
+        for (int r = 0; r < R; ++r) v[r] = p[r * ls];
         const int jq = fdiv(j, st.fNs);
         const int k = j - jq * Ns;
         if (Ns > 1) {
-            const int ks = k * tstep;
+            const int ts = k * tstep;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                V t = vld(tw + r * ks);
+                V t = vld(tw + r * ts);
                 if (INV) t.y = -t.y;
                 v[r] = vmul(v[r], t);
             }
         }
         RDft<R, INV, V>::run(v);
-        V *q = dst + vec * vs + (jq * Ns * R + k) * es;
+        V *q = d0 + (jq * Ns * R + k) * es;
 #pragma unroll
-        for (int r = 0; r < R; ++r) q[r * Ns * es] = v[r];
+        for (int r = 0; r < R; ++r) q[r * ns] = v[r];
     }
 }
 
 // All passes of a sub-transform, ping-ponging between the two tile buffers
 // (a barrier after each); returns the buffer holding the result.
-template <bool INV, int NT, class V>
-__device__ V *sp_transform(V *a, V *b, int L, const DctStage *stages, int nr, int nvec, const FastDiv &fnvec, int es,
-                           int vs, bool vfast, const V *__restrict__ tw)
+template <bool INV, int NT, bool COL, class V>
+__device__ V *sp_transform(V *a, V *b, int L, const DctStage *stages, int nr, int lgv, int stride,
+                           const V *__restrict__ tw)
 {
     for (int s = 0; s < nr; ++s) {
         const DctStage st = stages[s];
         switch (st.R) {
-        case 16: sp_pass<16, INV, NT>(a, b, L, st, nvec, fnvec, es, vs, vfast, tw); break;
-        case 10: sp_pass<10, INV, NT>(a, b, L, st, nvec, fnvec, es, vs, vfast, tw); break;
-        case 9: sp_pass<9, INV, NT>(a, b, L, st, nvec, fnvec, es, vs, vfast, tw); break;
-        case 8: sp_pass<8, INV, NT>(a, b, L, st, nvec, fnvec, es, vs, vfast, tw); break;
-        case 6: sp_pass<6, INV, NT>(a, b, L, st, nvec, fnvec, es, vs, vfast, tw); break;
-        case 5: sp_pass<5, INV, NT>(a, b, L, st, nvec, fnvec, es, vs, vfast, tw); break;
-        case 4: sp_pass<4, INV, NT>(a, b, L, st, nvec, fnvec, es, vs, vfast, tw); break;
-        case 3: sp_pass<3, INV, NT>(a, b, L, st, nvec, fnvec, es, vs, vfast, tw); break;
-        default: sp_pass<2, INV, NT>(a, b, L, st, nvec, fnvec, es, vs, vfast, tw); break;
+        case 16: sp_pass<16, INV, NT, COL>(a, b, L, st, lgv, stride, tw); break;
+        case 10: sp_pass<10, INV, NT, COL>(a, b, L, st, lgv, stride, tw); break;
+        case 9: sp_pass<9, INV, NT, COL>(a, b, L, st, lgv, stride, tw); break;
+        case 8: sp_pass<8, INV, NT, COL>(a, b, L, st, lgv, stride, tw); break;
+        case 6: sp_pass<6, INV, NT, COL>(a, b, L, st, lgv, stride, tw); break;
+        case 5: sp_pass<5, INV, NT, COL>(a, b, L, st, lgv, stride, tw); break;
+        case 4: sp_pass<4, INV, NT, COL>(a, b, L, st, lgv, stride, tw); break;
+        case 3: sp_pass<3, INV, NT, COL>(a, b, L, st, lgv, stride, tw); break;
+        default: sp_pass<2, INV, NT, COL>(a, b, L, st, lgv, stride, tw); break;
         }
         __syncthreads();
         V *t = a; a = b; b = t;

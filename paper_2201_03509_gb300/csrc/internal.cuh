@@ -65,7 +65,7 @@ struct alignas(16) TxLen {
     int32_t P1, P2;                   // row pairs m1/2 + 1, column pairs (m2 + 1)/2
     int32_t TP, TR;                   // column pairs per column tile, row pairs per row tile
     int32_t nr1, nr2;                 // radix stages of the column and row FFTs
-    int32_t pad0;
+    int16_t lgW, lgS;                 // log2 of the column tile's 2 TP columns and the row tile's 2 TR rows
     int64_t twb;                      // offset of this length's twiddle block
     FastDiv f_m2, f_W, f_2TR;         // divisions by m2, 2 TP, 2 TR
     int32_t pad1;

@@ -263,20 +263,19 @@ __device__ __forceinline__ void col_forward(const TxCtx &X, V *b0, V *b1, V *__r
     }
     __syncthreads();
     const TwB<V> T(twb, X.L);
-    V *R = sp_transform<false, TX_T>(b0, b1, m1, X.L.s1, X.L.nr1, W, X.L.f_W, W, 1, true, T.tw1);
+    V *R = sp_transform<false, TX_T, true>(b0, b1, m1, X.L.s1, X.L.nr1, X.L.lgW, 0, T.tw1);
     if (C.c < 0) return;
     V *Yq = Y + X.yb + C.c;
+    // W_m^{c k1} from the table at the first row of every TX_UNR rows, then
+    // by steps of W_m^{c rstep} (at most TX_UNR - 1 products from an exact value)
+    const V wstep = C.rstep < m1 ? T.w4(C.c * C.rstep) : vzero<V>();
     for (int k10 = C.r0; k10 < m1; k10 += TX_UNR * C.rstep) {
-        V w[TX_UNR];
+        V w = T.w4(C.c * k10);
 #pragma unroll
         for (int k = 0; k < TX_UNR; ++k) {
             const int k1 = k10 + k * C.rstep;
-            if (k1 < m1) w[k] = T.w4(C.c * k1);
-        }
-#pragma unroll
-        for (int k = 0; k < TX_UNR; ++k) {
-            const int k1 = k10 + k * C.rstep;
-            if (k1 < m1) Yq[static_cast<int64_t>(k1) * m2] = vmul(R[k1 * W + C.lc], w[k]);
+            if (k1 < m1) Yq[static_cast<int64_t>(k1) * m2] = vmul(R[k1 * W + C.lc], w);
+            if (k + 1 < TX_UNR) w = vmul(w, wstep);
         }
     }
 }
@@ -299,22 +298,20 @@ __device__ __forceinline__ void col_inverse(const TxCtx &X, V *b0, V *b1, const 
         const V *Yq = Y + X.yb + C.c;
         for (int k1 = C.r0; k1 < m1; k1 += C.rstep) cp_async(b0 + k1 * W + C.lc, Yq + static_cast<int64_t>(k1) * m2);
         cp_wait();
+        // the conjugate four-step twiddle, stepped as in the forward pass
+        const V wstep = C.rstep < m1 ? T.w4(C.c * C.rstep) : vzero<V>();
         for (int k10 = C.r0; k10 < m1; k10 += TX_UNR * C.rstep) {
-            V w[TX_UNR];
+            V w = T.w4(C.c * k10);
 #pragma unroll
             for (int k = 0; k < TX_UNR; ++k) {
                 const int k1 = k10 + k * C.rstep;
-                if (k1 < m1) w[k] = T.w4(C.c * k1);
-            }
-#pragma unroll
-            for (int k = 0; k < TX_UNR; ++k) {
-                const int k1 = k10 + k * C.rstep;
-                if (k1 < m1) b0[k1 * W + C.lc] = vmulc(b0[k1 * W + C.lc], w[k]);
+                if (k1 < m1) b0[k1 * W + C.lc] = vmulc(b0[k1 * W + C.lc], w);
+                if (k + 1 < TX_UNR) w = vmul(w, wstep);
             }
         }
     }
     __syncthreads();
-    V *R = sp_transform<true, TX_T>(b0, b1, m1, X.L.s1, X.L.nr1, W, X.L.f_W, W, 1, true, T.tw1);
+    V *R = sp_transform<true, TX_T, true>(b0, b1, m1, X.L.s1, X.L.nr1, X.L.lgW, 0, T.tw1);
     if (C.c < 0) return;
     for (int j10 = C.r0; j10 < G.m1h; j10 += TX_UNR * C.rstep) {
         decltype(ld(0, false)) D[TX_UNR];
@@ -358,15 +355,9 @@ struct RowGeo {
     }
 };
 
-// The split's twiddles of slot k = k1 + m1 k2: e1 = W_4n^k, e5 = W_4n^{5k}.
+// The split's twiddles of mode k: e1 = W_4n^k, e5 = W_4n^{5k} (for
+// k = k1 + m1 k2 the products of a per-row and a per-column table entry).
 template <class V> struct SplitTw { V e1, e5; };
-template <class V>
-__device__ __forceinline__ SplitTw<V> split_tw(const TwB<V> &T, int k1, int k2) {
-    SplitTw<V> t;
-    t.e1 = vmul(vld(T.sa1 + k1), vld(T.sb1 + k2));
-    t.e5 = vmul(vld(T.sa5 + k1), vld(T.sb5 + k2));
-    return t;
-}
 // Packed orthonormal coefficients of slot k from Z_k, Z_{m-k} (forward
 // half-split): W = e^{-i pi k/2n} A + e^{-i 5 pi k/2n} B.
 template <class V>
@@ -393,12 +384,26 @@ __device__ __forceinline__ V split_i(const SplitTw<V> &wk, const SplitTw<V> &wp,
     return vmake<V>(A.x - Bv.y, A.y + Bv.x);
 }
 
+// The split twiddles of mode m - k from those of mode k:
+// W_4n^{m-k} = W_4n^{n/2} conj(W_4n^k) = e^{-i pi/4} conj(e1) and
+// W_4n^{5(m-k)} = e^{-5 i pi/4} conj(e5).
+template <class V>
+__device__ __forceinline__ SplitTw<V> split_tw_mirror(const SplitTw<V> &w) {
+    typedef typename VecT<V>::S S;
+    const S h = static_cast<S>(0.70710678118654752440);
+    SplitTw<V> t;
+    t.e1 = vmake<V>(h * (w.e1.x - w.e1.y), -h * (w.e1.x + w.e1.y));     // (1 - i)/sqrt2 * conj(e1)
+    t.e5 = vmake<V>(h * (w.e5.y - w.e5.x), h * (w.e5.x + w.e5.y));      // (-1 + i)/sqrt2 * conj(e5)
+    return t;
+}
+
 // Row pass.  Loads the tile's rows from Y, forward row FFTs, then
 // pre(nubuf) (a second tile-sized buffer, or null when pre needs none; a
 // barrier follows), then for every packed slot:
 // Y' = f(e, k, Y) (e: tile element, k: slot, Y = (X_k, X_{n-k}) or (X_0, X_m));
 // with INV_BACK the inverse split and inverse row FFTs follow and the rows go
-// back to Y.
+// back to Y.  Rows are taken one at a time (their index is uniform over
+// the CTA), the threads over k2.
 template <class V, bool INV_BACK, class Pre, class F>
 __device__ __forceinline__ void row_pass(const TxCtx &X, V *b0, V *b1, V *__restrict__ Y, const V *__restrict__ twb,
                                          Pre pre, F f)
@@ -407,80 +412,75 @@ __device__ __forceinline__ void row_pass(const TxCtx &X, V *b0, V *b1, V *__rest
     const RowGeo G(X.L, X.blk);
     const int m1 = G.m1, m2 = G.m2, m2p = G.m2p;
     const int nslot = 2 * G.TR;
+    const int tid = threadIdx.x;
     V *Yq = Y + X.yb;
-    {
-        // element e = s m2 + k2, stepped by TX_T without divisions
-        int s = 0, k2 = threadIdx.x;
-        while (k2 >= m2) { k2 -= m2; ++s; }
-        for (; s < nslot;) {
-            const int r = G.row(s);
-            if (r < 0) b0[s * m2p + k2] = vzero<V>();
-            else cp_async(b0 + s * m2p + k2, Yq + static_cast<int64_t>(r) * m2 + k2);
-            k2 += TX_T;
-            while (k2 >= m2) { k2 -= m2; ++s; }
+    for (int sl = 0; sl < nslot; ++sl) {
+        const int r = G.row(sl);
+        V *dst = b0 + sl * m2p;
+        if (r < 0) {
+            for (int k2 = tid; k2 < m2; k2 += TX_T) dst[k2] = vzero<V>();
+        } else {
+            const V *src = Yq + static_cast<int64_t>(r) * m2;
+            for (int k2 = tid; k2 < m2; k2 += TX_T) cp_async(dst + k2, src + k2);
         }
     }
     cp_wait();
     __syncthreads();
     const TwB<V> T(twb, X.L);
-    V *R = sp_transform<false, TX_T>(b0, b1, m2, X.L.s2, X.L.nr2, nslot, X.L.f_2TR, 1, m2p, true, T.tw2);
+    V *R = sp_transform<false, TX_T, false>(b0, b1, m2, X.L.s2, X.L.nr2, X.L.lgS, m2p, T.tw2);
     V *Fr = R == b0 ? b1 : b0;
     pre(Fr);
     __syncthreads();
     const S sqf = static_cast<S>(X.L.sq_fwd), s0f = static_cast<S>(X.L.s0_fwd);
     const S sqi = static_cast<S>(X.L.sq_inv), s0i = static_cast<S>(X.L.s0_inv);
-    {
-        int pl = 0, k2 = threadIdx.x;
-        while (k2 >= m2) { k2 -= m2; ++pl; }
-        for (; pl < G.nr;) {
-            const int p = G.r0 + pl;
-            const int cnt = (p == 0) ? (m2 / 2 + 1) : ((2 * p == m1) ? (m2 + 1) / 2 : m2);
-            if (k2 < cnt) {
-                int ib, q1, q2;
-                if (p == 0) { q1 = 0; q2 = (k2 == 0) ? 0 : m2 - k2; ib = 2 * pl * m2p + q2; }
-                else { q1 = m1 - p; q2 = m2 - 1 - k2; ib = ((q1 == p) ? 2 * pl : 2 * pl + 1) * m2p + q2; }
-                const int ia = 2 * pl * m2p + k2;
-                const V Za = R[ia], Zb = R[ib];
-                if (p == 0 && k2 == 0) {
-                    V Yv = vmake<V>((Za.x + Za.y) * s0f, (Za.x - Za.y) * s0f);
-                    Yv = f(ia, 0, Yv);
-                    if (INV_BACK) {
-                        const S V0 = Yv.x * s0i, Vm = Yv.y * s0i;
-                        R[ia] = vmake<V>(static_cast<S>(0.5) * (V0 + Vm), static_cast<S>(0.5) * (V0 - Vm));
-                    }
-                } else {
-                    const SplitTw<V> wa = split_tw(T, p, k2);
-                    V Ya = split_f(wa, Za, Zb, sqf);
-                    Ya = f(ia, p + m1 * k2, Ya);
-                    if (ib != ia) {
-                        const SplitTw<V> wb = split_tw(T, q1, q2);
-                        V Yb = split_f(wb, Zb, Za, sqf);
-                        Yb = f(ib, q1 + m1 * q2, Yb);
-                        if (INV_BACK) {
-                            R[ib] = split_i(wb, wa, Yb, Ya, sqi);
-                            R[ia] = split_i(wa, wb, Ya, Yb, sqi);
-                        }
-                    } else if (INV_BACK) {
-                        R[ia] = split_i(wa, wa, Ya, Ya, sqi);
-                    }
+    for (int pl = 0; pl < G.nr; ++pl) {
+        const int p = G.r0 + pl;
+        const bool mid = 2 * p == m1;                 // the row pairs with itself
+        // elements (pl, k2) for k2 < cnt; each pairs with mode m - k
+        const int cnt = (p == 0) ? (m2 / 2 + 1) : (mid ? (m2 + 1) / 2 : m2);
+        const int rowa = 2 * pl * m2p, rowb = (p == 0 || mid) ? rowa : rowa + m2p;
+        const V a1 = vld(T.sa1 + p), a5 = vld(T.sa5 + p);
+        for (int k2 = tid; k2 < cnt; k2 += TX_T) {
+            const int q2 = (p == 0) ? (k2 == 0 ? 0 : m2 - k2) : m2 - 1 - k2;
+            const int ia = rowa + k2, ib = rowb + q2;
+            const V Za = R[ia], Zb = R[ib];
+            const int ka = p + m1 * k2;
+            if (ka == 0) {
+                V Yv = vmake<V>((Za.x + Za.y) * s0f, (Za.x - Za.y) * s0f);
+                Yv = f(ia, 0, Yv);
+                if (INV_BACK) {
+                    const S V0 = Yv.x * s0i, Vm = Yv.y * s0i;
+                    R[ia] = vmake<V>(static_cast<S>(0.5) * (V0 + Vm), static_cast<S>(0.5) * (V0 - Vm));
                 }
+                continue;
             }
-            k2 += TX_T;
-            while (k2 >= m2) { k2 -= m2; ++pl; }
+            SplitTw<V> wa;
+            wa.e1 = vmul(a1, vld(T.sb1 + k2));
+            wa.e5 = vmul(a5, vld(T.sb5 + k2));
+            V Ya = split_f(wa, Za, Zb, sqf);
+            Ya = f(ia, ka, Ya);
+            if (ib != ia) {
+                const SplitTw<V> wb = split_tw_mirror(wa);
+                V Yb = split_f(wb, Zb, Za, sqf);
+                Yb = f(ib, G.m - ka, Yb);
+                if (INV_BACK) {
+                    R[ib] = split_i(wb, wa, Yb, Ya, sqi);
+                    R[ia] = split_i(wa, wb, Ya, Yb, sqi);
+                }
+            } else if (INV_BACK) {
+                R[ia] = split_i(wa, wa, Ya, Ya, sqi);
+            }
         }
     }
     if (!INV_BACK) return;
     __syncthreads();
-    V *Ri = sp_transform<true, TX_T>(R, Fr, m2, X.L.s2, X.L.nr2, nslot, X.L.f_2TR, 1, m2p, true, T.tw2);
-    {
-        int s = 0, k2 = threadIdx.x;
-        while (k2 >= m2) { k2 -= m2; ++s; }
-        for (; s < nslot;) {
-            const int r = G.row(s);
-            if (r >= 0) Yq[static_cast<int64_t>(r) * m2 + k2] = Ri[s * m2p + k2];
-            k2 += TX_T;
-            while (k2 >= m2) { k2 -= m2; ++s; }
-        }
+    V *Ri = sp_transform<true, TX_T, false>(R, Fr, m2, X.L.s2, X.L.nr2, X.L.lgS, m2p, T.tw2);
+    for (int sl = 0; sl < nslot; ++sl) {
+        const int r = G.row(sl);
+        if (r < 0) continue;
+        const V *src = Ri + sl * m2p;
+        V *dst = Yq + static_cast<int64_t>(r) * m2;
+        for (int k2 = tid; k2 < m2; k2 += TX_T) dst[k2] = src[k2];
     }
 }
 

@@ -65,8 +65,10 @@ class BandConfig:
     seed: int = 20220110
 
 
-# Workloads of the benchmark suite: the 30 GHz band is the benchmark's, the
-# others are parity-test cases.
+# Workloads: the 70 GHz band is the benchmark's headline, the 30 GHz band
+# its secondary section; the three sweep bands (30/44/70 GHz-like, 1500
+# scans each, lengths the band's mean +-20 %) make the multi-band Gibbs
+# sweep; the rest are parity-test cases.
 CONFIGS = {
     "tiny": BandConfig(name="tiny: 1 det x 16 scans x 4096 @32.5Hz, Nside 16",
                        nside=16, ndet=1, nscan=16, fsamp=32.5, len_lo=4096, len_hi=4096,
@@ -81,11 +83,26 @@ CONFIGS = {
                         nside=1024, ndet=12, nscan=2000, fsamp=78.8, len_lo=150000, len_hi=300000,
                         fknee_lo=0.02, fknee_hi=0.2, alpha_lo=-2.0, alpha_hi=-1.0,
                         sigma0_jitter=0.2, flag_frac=0.02, seed=20220113),
+    "sweep30": BandConfig(name="sweep 30GHz-like: 4 det x 1500 scans x U[94k,140k] @32.5Hz, Nside 512",
+                          nside=512, ndet=4, nscan=1500, fsamp=32.5, len_lo=93600, len_hi=140400,
+                          fknee_lo=0.02, fknee_hi=0.2, alpha_lo=-2.0, alpha_hi=-1.0,
+                          sigma0_jitter=0.2, flag_frac=0.02, seed=20220115),
+    "sweep44": BandConfig(name="sweep 44GHz-like: 6 det x 1500 scans x U[136k,204k] @46.5Hz, Nside 512",
+                          nside=512, ndet=6, nscan=1500, fsamp=46.5, len_lo=136000, len_hi=204000,
+                          fknee_lo=0.02, fknee_hi=0.2, alpha_lo=-2.0, alpha_hi=-1.0,
+                          sigma0_jitter=0.2, flag_frac=0.02, seed=20220116),
+    "sweep70": BandConfig(name="sweep 70GHz-like: 12 det x 1500 scans x U[224k,336k] @78.8Hz, Nside 1024",
+                          nside=1024, ndet=12, nscan=1500, fsamp=78.8, len_lo=224000, len_hi=336000,
+                          fknee_lo=0.02, fknee_hi=0.2, alpha_lo=-2.0, alpha_hi=-1.0,
+                          sigma0_jitter=0.2, flag_frac=0.02, seed=20220117),
     "chi2": BandConfig(name="chi2: 4 det x 200 scans x 65536 @32.5Hz, Nside 256",
                        nside=256, ndet=4, nscan=200, fsamp=32.5, len_lo=65536, len_hi=65536,
                        fknee_lo=0.02, fknee_hi=0.2, alpha_lo=-2.0, alpha_hi=-1.0,
                        sigma0_jitter=0.2, flag_frac=0.0, seed=20220114),
 }
+
+
+SWEEP_BANDS = ("sweep30", "sweep44", "sweep70")
 
 
 def scaled(cfg: BandConfig, nscan: int | None = None, len_lo: int | None = None,
