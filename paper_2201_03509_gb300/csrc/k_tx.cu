@@ -223,16 +223,36 @@ struct ColThread {
     }
 };
 
+// The flag bits of a thread's units, loaded ahead of the transform (all
+// loads in flight together): bit 4i + u is sample u of the thread's i-th
+// unit (rows r0, r0 + rstep, ..; at most TX_TILE / 512 <= 8 units).  Zero
+// without flags (fl null) or for a thread without a column.
+__device__ __forceinline__ uint32_t unit_flags(const ColGeo &G, const ColThread &C, const uint32_t *__restrict__ fl,
+                                               int64_t o)
+{
+    uint32_t nib = 0;
+    if (!fl || C.c < 0) return nib;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int j1 = C.r0 + i * C.rstep;
+        const int j = j1 * G.m2 + C.c;
+        if (j1 < G.m1h && j <= G.m - 1 - j)
+            nib |= flag_bits(fl, o + 4 * static_cast<int64_t>(j), j == G.m - 1 - j ? 2 : 4) << (4 * i);
+    }
+    return nib;
+}
+
 // Forward column pass.  For every unit j <= m-1-j of the tile (the four
-// samples x_{4j..4j+3}, two at the centre j = m-1-j): D = ld(j, centre)
-// issues the unit's loads (TX_UNR units per thread at a time), then
-// put(D, j1, lc, c, j, jm, tile) writes z_j at (j1, lc) and z_{m-1-j} at
-// (m1-1-j1, lcol(m2-1-c)).  pre(tile) runs first (after the columns a
+// samples x_{4j..4j+3}, two at the centre j = m-1-j): D = ld(j, centre, fb)
+// issues the unit's loads (TX_UNR units per thread at a time; fb: the
+// unit's flag bits, from fl at sample o + 4j, read ahead), then
+// put(D, ea, eb, j, jm, tile, fb) writes z_j at tile element ea = (j1, lc) and
+// z_{m-1-j} at eb = (m1-1-j1, lcol(m2-1-c)).  pre(tile) runs first (after the columns a
 // ragged tile lacks are zeroed), with a barrier before the units.  Then
 // the column FFTs, the twiddle, and the tile out to Y.
 template <class V, class Pre, class Ld, class Put>
 __device__ __forceinline__ void col_forward(const TxCtx &X, V *b0, V *b1, V *__restrict__ Y, const V *__restrict__ twb,
-                                            Pre pre, Ld ld, Put put)
+                                            const uint32_t *__restrict__ fl, Pre pre, Ld ld, Put put)
 {
     const ColGeo G(X.L, X.blk);
     const ColThread C(G);
@@ -240,24 +260,26 @@ __device__ __forceinline__ void col_forward(const TxCtx &X, V *b0, V *b1, V *__r
     if (C.c < 0)
         for (int j1 = C.r0; j1 < m1; j1 += C.rstep) b0[j1 * W + C.lc] = vzero<V>();
     pre(b0);
+    const uint32_t fnib = unit_flags(G, C, fl, X.o);
     __syncthreads();
     if (C.c >= 0) {
-        for (int j10 = C.r0; j10 < G.m1h; j10 += TX_UNR * C.rstep) {
-            decltype(ld(0, false)) D[TX_UNR];
+        for (int j10 = C.r0, i0 = 0; j10 < G.m1h; j10 += TX_UNR * C.rstep, i0 += TX_UNR) {
+            decltype(ld(0, false, 0u)) D[TX_UNR];
             bool ok[TX_UNR];
 #pragma unroll
             for (int k = 0; k < TX_UNR; ++k) {
                 const int j1 = j10 + k * C.rstep;
                 const int j = j1 * m2 + C.c;
                 ok[k] = j1 < G.m1h && j <= G.m - 1 - j;
-                if (ok[k]) D[k] = ld(j, j == G.m - 1 - j);
+                if (ok[k]) D[k] = ld(j, j == G.m - 1 - j, (fnib >> (4 * (i0 + k))) & 15u);
             }
 #pragma unroll
             for (int k = 0; k < TX_UNR; ++k) {
                 if (!ok[k]) continue;
                 const int j1 = j10 + k * C.rstep;
                 const int j = j1 * m2 + C.c;
-                put(D[k], j1, C.lc, C.c, j, G.m - 1 - j, b0);
+                put(D[k], j1 * W + C.lc, (m1 - 1 - j1) * W + C.lpart, j, G.m - 1 - j, b0,
+                    (fnib >> (4 * (i0 + k))) & 15u);
             }
         }
     }
@@ -282,21 +304,25 @@ __device__ __forceinline__ void col_forward(const TxCtx &X, V *b0, V *b1, V *__r
 
 // Inverse column pass: the tile's Y values copied in asynchronously,
 // twiddled in place, inverse FFT of the columns; then for every unit
-// j <= m-1-j: D = ld(j, centre) (issued TX_UNR units at a time) and
-// out(D, j1, lc, c, j, jm, tile).
+// j <= m-1-j: D = ld(j, centre, fb) (issued TX_UNR units at a time) and
+// out(D, ea, eb, j, jm, tile, fb) with ea, eb, fb as for the forward pass
+// (the flag bits are read while the tile loads).
 template <class V, class Ld, class Out>
 __device__ __forceinline__ void col_inverse(const TxCtx &X, V *b0, V *b1, const V *__restrict__ Y,
-                                            const V *__restrict__ twb, Ld ld, Out out)
+                                            const V *__restrict__ twb, const uint32_t *__restrict__ fl, Ld ld,
+                                            Out out)
 {
     const ColGeo G(X.L, X.blk);
     const ColThread C(G);
     const int W = G.W, m1 = G.m1, m2 = G.m2;
     const TwB<V> T(twb, X.L);
+    uint32_t fnib = 0;
     if (C.c < 0) {
         for (int k1 = C.r0; k1 < m1; k1 += C.rstep) b0[k1 * W + C.lc] = vzero<V>();
     } else {
         const V *Yq = Y + X.yb + C.c;
         for (int k1 = C.r0; k1 < m1; k1 += C.rstep) cp_async(b0 + k1 * W + C.lc, Yq + static_cast<int64_t>(k1) * m2);
+        fnib = unit_flags(G, C, fl, X.o);
         cp_wait();
         // the conjugate four-step twiddle, stepped as in the forward pass
         const V wstep = C.rstep < m1 ? T.w4(C.c * C.rstep) : vzero<V>();
@@ -313,22 +339,22 @@ __device__ __forceinline__ void col_inverse(const TxCtx &X, V *b0, V *b1, const 
     __syncthreads();
     V *R = sp_transform<true, TX_T, true>(b0, b1, m1, X.L.s1, X.L.nr1, X.L.lgW, 0, T.tw1);
     if (C.c < 0) return;
-    for (int j10 = C.r0; j10 < G.m1h; j10 += TX_UNR * C.rstep) {
-        decltype(ld(0, false)) D[TX_UNR];
+    for (int j10 = C.r0, i0 = 0; j10 < G.m1h; j10 += TX_UNR * C.rstep, i0 += TX_UNR) {
+        decltype(ld(0, false, 0u)) D[TX_UNR];
         bool ok[TX_UNR];
 #pragma unroll
         for (int k = 0; k < TX_UNR; ++k) {
             const int j1 = j10 + k * C.rstep;
             const int j = j1 * m2 + C.c;
             ok[k] = j1 < G.m1h && j <= G.m - 1 - j;
-            if (ok[k]) D[k] = ld(j, j == G.m - 1 - j);
+            if (ok[k]) D[k] = ld(j, j == G.m - 1 - j, (fnib >> (4 * (i0 + k))) & 15u);
         }
 #pragma unroll
         for (int k = 0; k < TX_UNR; ++k) {
             if (!ok[k]) continue;
             const int j1 = j10 + k * C.rstep;
             const int j = j1 * m2 + C.c;
-            out(D[k], j1, C.lc, C.c, j, G.m - 1 - j, R);
+            out(D[k], j1 * W + C.lc, (m1 - 1 - j1) * W + C.lpart, j, G.m - 1 - j, R, (fnib >> (4 * (i0 + k))) & 15u);
         }
     }
 }
@@ -575,21 +601,14 @@ __global__ void __launch_bounds__(TX_T, 3) k_gain_cols(GainTx a)
         const int2 w = a.items[a.item0 + it];
         tx_begin(X, a.txl, a.q_tx, a.off, w.x, w.y, a.obase, a.ndet, a.fsamp, nullptr, nullptr, cur);
         const float *sq = a.s + X.o;
-        const int64_t o = X.o;
-        const ColGeo G(X.L, X.blk);
-        struct U4 { float4 v; uint32_t fb; };
-        col_forward(X, b0, b1, a.Y, a.tw + X.L.twb, [](float2 *) {},
-                    [&](int j, bool ctr) {
-                        const int64_t t = 4 * static_cast<int64_t>(j);
-                        return U4{ld4(sq, t, ctr), flag_bits(a.flags, o + t, ctr ? 2 : 4)};
-                    },
-                    [&](const U4 &D, int j1, int lc, int c, int j, int jm, float2 *U) {
-                        const uint32_t fb = D.fb;
-                        const float x0 = (fb & 1) ? 0.f : D.v.x, x1 = (fb & 2) ? 0.f : D.v.y;
-                        const float x2 = (fb & 4) ? 0.f : D.v.z, x3 = (fb & 8) ? 0.f : D.v.w;
-                        if (j == jm) { U[j1 * G.W + lc] = make_float2(x0, x1); return; }
-                        U[j1 * G.W + lc] = make_float2(x0, x2);
-                        U[(G.m1 - 1 - j1) * G.W + G.lcol(G.m2 - 1 - c)] = make_float2(x3, x1);
+        col_forward(X, b0, b1, a.Y, a.tw + X.L.twb, a.flags, [](float2 *) {},
+                    [&](int j, bool ctr, uint32_t) { return ld4(sq, 4 * static_cast<int64_t>(j), ctr); },
+                    [&](const float4 &v, int ea, int eb, int j, int jm, float2 *U, uint32_t fb) {
+                        const float x0 = (fb & 1) ? 0.f : v.x, x1 = (fb & 2) ? 0.f : v.y;
+                        const float x2 = (fb & 4) ? 0.f : v.z, x3 = (fb & 8) ? 0.f : v.w;
+                        if (j == jm) { U[ea] = make_float2(x0, x1); return; }
+                        U[ea] = make_float2(x0, x2);
+                        U[eb] = make_float2(x3, x1);
                     });
     }
 }
@@ -636,24 +655,18 @@ __global__ void __launch_bounds__(TX_T, 3) k_gain_colsinv(GainTx a)
         const int2 w = a.items[a.item0 + it];
         tx_begin(X, a.txl, a.q_tx, a.off, w.x, w.y, a.obase, a.ndet, a.fsamp, nullptr, nullptr, cur);
         const float *dq = a.d + X.o;
-        const int64_t o = X.o;
         Acc2 sb[1] = {{0.f, 0.f}};
-        const ColGeo G(X.L, X.blk);
-        struct U4 { float4 v; uint32_t fb; };
-        col_inverse(X, b0, b1, a.Y, a.tw + X.L.twb, [&](int j, bool ctr) {
-            const int64_t t = 4 * static_cast<int64_t>(j);
-            return U4{ld4(dq, t, ctr), flag_bits(a.flags, o + t, ctr ? 2 : 4)};
-        }, [&](const U4 &D, int j1, int lc, int c, int j, int jm, const float2 *U) {
+        col_inverse(X, b0, b1, a.Y, a.tw + X.L.twb, a.flags, [&](int j, bool ctr, uint32_t) {
+            return ld4(dq, 4 * static_cast<int64_t>(j), ctr);
+        }, [&](const float4 &dv, int ea, int eb, int j, int jm, const float2 *U, uint32_t fb) {
             const bool ctr = j == jm;
-            const float4 dv = D.v;
-            const uint32_t fb = D.fb;
-            const float2 za = U[j1 * G.W + lc];
+            const float2 za = U[ea];
             if (ctr) {
                 acc_add_prod(sb[0], (fb & 1) ? 0.f : dv.x, za.x);
                 acc_add_prod(sb[0], (fb & 2) ? 0.f : dv.y, za.y);
                 return;
             }
-            const float2 zb = U[(G.m1 - 1 - j1) * G.W + G.lcol(G.m2 - 1 - c)];
+            const float2 zb = U[eb];
             acc_add_prod(sb[0], (fb & 1) ? 0.f : dv.x, za.x);
             acc_add_prod(sb[0], (fb & 2) ? 0.f : dv.y, zb.y);
             acc_add_prod(sb[0], (fb & 4) ? 0.f : dv.z, za.y);
@@ -758,30 +771,27 @@ __global__ void __launch_bounds__(TX_T) k_chi2_cols(Chi2Tx<V> a)
         const double gq = a.gain[X.q];
         const float *dq = a.d + X.o;
         const int64_t o = X.o;
-        const ColGeo G(X.L, X.blk);
-        struct U4 { float4 dv; S sx[4]; uint32_t fb; };
-        col_forward(X, b0, b1, a.Y, a.tw + X.L.twb, [](V *) {},
-                    [&](int j, bool ctr) {
+        struct U4 { float4 dv; S sx[4]; };
+        col_forward(X, b0, b1, a.Y, a.tw + X.L.twb, a.flags, [](V *) {},
+                    [&](int j, bool ctr, uint32_t) {
                         const int64_t t = 4 * static_cast<int64_t>(j);
                         U4 D;
                         D.dv = ld4(dq, t, ctr);
                         ld4s<S>(a.s, o + t, ctr, D.sx);
-                        D.fb = flag_bits(a.flags, o + t, ctr ? 2 : 4);
                         return D;
                     },
-                    [&](const U4 &D, int j1, int lc, int c, int j, int jm, V *U) {
+                    [&](const U4 &D, int ea, int eb, int j, int jm, V *U, uint32_t fb) {
                         const bool ctr = j == jm;
                         const float4 dv = D.dv;
                         const struct { S x, y, z, w; } sv = {D.sx[0], D.sx[1], D.sx[2], D.sx[3]};
-                        const uint32_t fb = D.fb;
                         const S g = static_cast<S>(gq);
                         const S r0 = (fb & 1) ? S(0) : static_cast<S>(dv.x) - g * static_cast<S>(sv.x);
                         const S r1 = (fb & 2) ? S(0) : static_cast<S>(dv.y) - g * static_cast<S>(sv.y);
                         const S r2 = (fb & 4) ? S(0) : static_cast<S>(dv.z) - g * static_cast<S>(sv.z);
                         const S r3 = (fb & 8) ? S(0) : static_cast<S>(dv.w) - g * static_cast<S>(sv.w);
-                        if (ctr) { U[j1 * G.W + lc] = vmake<V>(r0, r1); return; }
-                        U[j1 * G.W + lc] = vmake<V>(r0, r2);
-                        U[(G.m1 - 1 - j1) * G.W + G.lcol(G.m2 - 1 - c)] = vmake<V>(r3, r1);
+                        if (ctr) { U[ea] = vmake<V>(r0, r1); return; }
+                        U[ea] = vmake<V>(r0, r2);
+                        U[eb] = vmake<V>(r3, r1);
                     });
     }
 }
@@ -859,21 +869,17 @@ __global__ void __launch_bounds__(TX_T) k_chi2_colsinv(Chi2Tx<V> a)
         tx_begin(X, a.txl, a.q_tx, a.off, w.x, w.y, a.obase, a.ndet, a.fsamp, nullptr, nullptr, cur);
         const int64_t o = X.o;
         double acc[1] = {0.0};
-        const ColGeo G(X.L, X.blk);
-        struct U4 { S sx[4]; uint32_t fb; };
-        col_inverse(X, b0, b1, a.Y, a.tw + X.L.twb, [&](int j, bool ctr) {
-            const int64_t t = 4 * static_cast<int64_t>(j);
+        struct U4 { S sx[4]; };
+        col_inverse(X, b0, b1, a.Y, a.tw + X.L.twb, a.flags, [&](int j, bool ctr, uint32_t) {
             U4 D;
-            ld4s<S>(a.s, o + t, ctr, D.sx);
-            D.fb = flag_bits(a.flags, o + t, ctr ? 2 : 4);
+            ld4s<S>(a.s, o + 4 * static_cast<int64_t>(j), ctr, D.sx);
             return D;
-        }, [&](const U4 &D, int j1, int lc, int c, int j, int jm, const V *U) {
+        }, [&](const U4 &D, int ea, int eb, int j, int jm, const V *U, uint32_t fb) {
             const bool ctr = j == jm;
             const int64_t t = 4 * static_cast<int64_t>(j);
             const S *sx = D.sx;
-            const uint32_t fb = D.fb;
-            const V za = U[j1 * G.W + lc];
-            const V zb = ctr ? za : U[(G.m1 - 1 - j1) * G.W + G.lcol(G.m2 - 1 - c)];
+            const V za = U[ea];
+            const V zb = ctr ? za : U[eb];
             S v[4] = {(fb & 1) ? S(0) : za.x, (fb & 2) ? S(0) : (ctr ? za.y : zb.y),
                       (fb & 4) ? S(0) : za.y, (fb & 8) ? S(0) : zb.x};
             const int cnt = ctr ? 2 : 4;
@@ -1188,12 +1194,11 @@ __device__ void nc_rhs_cols(const NcorrTx &a, const TxCtx &X, float2 *b0, float2
 {
     const bool draw = a.mode == TOD_MODE_DRAW;
     const float *dq = a.d + X.o, *sq = a.s + X.o;
-    const int64_t o = X.o;
     const float g = X.g, inv_s2 = X.inv_s2, inv_s = X.inv_s;
     const uint64_t q = static_cast<uint64_t>(X.q);
     const ColGeo G(X.L, X.blk);
-    struct U8 { float4 dv, sv; uint32_t fb; };
-    col_forward(X, b0, b1, a.Y, a.tw + X.L.twb,
+    struct U8 { float4 dv, sv; };
+    col_forward(X, b0, b1, a.Y, a.tw + X.L.twb, a.flags,
                 [&](float2 *U) {
                     // the tile's normals: one Philox block per thread, its four
                     // pairs to the tile elements whose index j falls in it
@@ -1225,22 +1230,19 @@ __device__ void nc_rhs_cols(const NcorrTx &a, const TxCtx &X, float2 *b0, float2
                         }
                     }
                 },
-                [&](int j, bool ctr) {
+                [&](int j, bool ctr, uint32_t) {
                     const int64_t t = 4 * static_cast<int64_t>(j);
-                    return U8{ld4(dq, t, ctr), ld4(sq, t, ctr), flag_bits(a.flags, o + t, ctr ? 2 : 4)};
+                    return U8{ld4(dq, t, ctr), ld4(sq, t, ctr)};
                 },
-                [&](const U8 &D, int j1, int lc, int c, int j, int jm, float2 *U) {
+                [&](const U8 &D, int ea, int eb, int j, int jm, float2 *U, uint32_t fb) {
                     const bool ctr = j == jm;
                     const float4 dv = D.dv, sv = D.sv;
-                    const uint32_t fb = D.fb;
-                    const int ea = j1 * G.W + lc;
                     const float2 wa = U[ea];
                     if (ctr) {
                         U[ea] = make_float2((fb & 1) ? 0.f : fmaf(dv.x - g * sv.x, inv_s2, wa.x * inv_s),
                                             (fb & 2) ? 0.f : fmaf(dv.y - g * sv.y, inv_s2, wa.y * inv_s));
                         return;
                     }
-                    const int eb = (G.m1 - 1 - j1) * G.W + G.lcol(G.m2 - 1 - c);
                     const float2 wb = U[eb];
                     // samples 4j, 4j+2 -> z_j = (v_{2j}, v_{2j+1}); 4j+3, 4j+1 -> z_{m-1-j}
                     U[ea] = make_float2((fb & 1) ? 0.f : fmaf(dv.x - g * sv.x, inv_s2, wa.x * inv_s),
@@ -1328,16 +1330,15 @@ __device__ void nc_x0_cols(const NcorrTx &a, const TxCtx &X, float2 *b0, float2 
     const int64_t o = X.o, obase = a.off[a.q0], w_lo = obase >> 5;
     float *r = a.cgv + a.cgcap;
     const ColGeo G(X.L, X.blk);
-    col_inverse(X, b0, b1, a.Y, a.tw + X.L.twb, [&](int j, bool ctr) {
-        return cg ? flag_bits(a.flags, o + 4 * static_cast<int64_t>(j), ctr ? 2 : 4) : 0u;
-    }, [&](uint32_t fbits, int j1, int lc, int c, int j, int jm, const float2 *U) {
+    col_inverse(X, b0, b1, a.Y, a.tw + X.L.twb, cg ? a.flags : nullptr, [&](int, bool, uint32_t) { return 0; },
+                [&](int, int ea, int eb, int j, int jm, const float2 *U, uint32_t fbits) {
         const bool ctr = j == jm;
         const int64_t t = 4 * static_cast<int64_t>(j);
-        const float2 za = U[j1 * G.W + lc];
+        const float2 za = U[ea];
         float v[4];
         if (ctr) { v[0] = za.x; v[1] = za.y; }
         else {
-            const float2 zb = U[(G.m1 - 1 - j1) * G.W + G.lcol(G.m2 - 1 - c)];
+            const float2 zb = U[eb];
             v[0] = za.x; v[1] = zb.y; v[2] = za.y; v[3] = zb.x;
         }
         reinterpret_cast<float2 *>(xq + t)[0] = make_float2(v[0], v[1]);
@@ -1359,11 +1360,10 @@ __device__ void nc_scatter_cols(const NcorrTx &a, const TxCtx &X, float2 *b0, fl
 {
     const int64_t o = X.o, obase = a.off[a.q0], w_lo = obase >> 5;
     const ColGeo G(X.L, X.blk);
-    col_forward(X, b0, b1, a.Y, a.tw + X.L.twb, [](float2 *) {},
-                [&](int j, bool ctr) {
+    col_forward(X, b0, b1, a.Y, a.tw + X.L.twb, a.flags, [](float2 *) {},
+                [&](int j, bool, uint32_t fb) {
                     // the unit's flagged entries of vec (a rank lookup only where flagged)
                     const int64_t t = 4 * static_cast<int64_t>(j);
-                    uint32_t fb = flag_bits(a.flags, o + t, ctr ? 2 : 4);
                     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
                     while (fb) {
                         const int u = __ffs(fb) - 1;
@@ -1373,11 +1373,11 @@ __device__ void nc_scatter_cols(const NcorrTx &a, const TxCtx &X, float2 *b0, fl
                     }
                     return v;
                 },
-                [&](const float4 &D, int j1, int lc, int c, int j, int jm, float2 *U) {
+                [&](const float4 &D, int ea, int eb, int j, int jm, float2 *U, uint32_t) {
                     const float v[4] = {D.x, D.y, D.z, D.w};
-                    if (j == jm) { U[j1 * G.W + lc] = make_float2(v[0], v[1]); return; }
-                    U[j1 * G.W + lc] = make_float2(v[0], v[2]);
-                    U[(G.m1 - 1 - j1) * G.W + G.lcol(G.m2 - 1 - c)] = make_float2(v[3], v[1]);
+                    if (j == jm) { U[ea] = make_float2(v[0], v[1]); return; }
+                    U[ea] = make_float2(v[0], v[2]);
+                    U[eb] = make_float2(v[3], v[1]);
                 });
 }
 
@@ -1411,35 +1411,34 @@ __device__ void nc_gather_cols(const NcorrTx &a, const TxCtx &X, float2 *b0, flo
     const int64_t o = X.o, obase = a.off[a.q0], w_lo = obase >> 5;
     float *xq = a.x_out + X.o;
     const ColGeo G(X.L, X.blk);
-    struct U4 { float4 x; uint32_t fb; };
-    col_inverse(X, b0, b1, a.Y, a.tw + X.L.twb, [&](int j, bool ctr) {
-        // ADD: the unit's x0; gather: its flag bits
-        const int64_t t = 4 * static_cast<int64_t>(j);
-        U4 D;
-        if (ADD) {      // x0 was written earlier in this launch: coherent loads, not the read-only path
+    col_inverse(X, b0, b1, a.Y, a.tw + X.L.twb, ADD ? nullptr : a.flags, [&](int j, bool ctr, uint32_t) {
+        // ADD: the unit's x0 (written earlier in this launch: coherent loads,
+        // not the read-only path); the gather needs only the flag bits
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ADD) {
+            const int64_t t = 4 * static_cast<int64_t>(j);
             const float2 a01 = reinterpret_cast<const float2 *>(xq + t)[0];
             const float2 a23 = ctr ? make_float2(0.f, 0.f) : reinterpret_cast<const float2 *>(xq + t + 2)[0];
-            D.x = make_float4(a01.x, a01.y, a23.x, a23.y);
-            D.fb = 0u;
+            x = make_float4(a01.x, a01.y, a23.x, a23.y);
         }
-        else { D.x = make_float4(0.f, 0.f, 0.f, 0.f); D.fb = flag_bits(a.flags, o + t, ctr ? 2 : 4); }
-        return D;
-    }, [&](const U4 &D, int j1, int lc, int c, int j, int jm, const float2 *U) {
+        return x;
+    }, [&](const float4 &x0, int ea, int eb, int j, int jm, const float2 *U, uint32_t fbits) {
+        if (!ADD && fbits == 0) return;          // no flagged sample in the unit
         const bool ctr = j == jm;
         const int64_t t = 4 * static_cast<int64_t>(j);
-        const float2 za = U[j1 * G.W + lc];
+        const float2 za = U[ea];
         float v[4];
         if (ctr) { v[0] = za.x; v[1] = za.y; }
         else {
-            const float2 zb = U[(G.m1 - 1 - j1) * G.W + G.lcol(G.m2 - 1 - c)];
+            const float2 zb = U[eb];
             v[0] = za.x; v[1] = zb.y; v[2] = za.y; v[3] = zb.x;
         }
         if (ADD) {
             float2 *p = reinterpret_cast<float2 *>(xq + t);
-            p[0] = make_float2(D.x.x + v[0], D.x.y + v[1]);
-            if (!ctr) p[1] = make_float2(D.x.z + v[2], D.x.w + v[3]);
+            p[0] = make_float2(x0.x + v[0], x0.y + v[1]);
+            if (!ctr) p[1] = make_float2(x0.z + v[2], x0.w + v[3]);
         } else {
-            uint32_t fb = D.fb;
+            uint32_t fb = fbits;
             while (fb) {
                 const int u = __ffs(fb) - 1;
                 fb &= fb - 1;
