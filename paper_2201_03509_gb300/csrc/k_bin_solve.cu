@@ -93,6 +93,14 @@ __device__ __forceinline__ void sums_store(const RunSums &r, double wA, double w
     rr[9] = static_cast<double>(r.hits);
 }
 
+// a - b of two double-words (two-sum on the heads, tails subtracted)
+__device__ __forceinline__ Acc2 acc_diff(const Acc2 &a, const Acc2 &b) {
+    Acc2 r = a;
+    acc_add(r, -b.s);
+    r.c = __fsub_rn(r.c, b.c);
+    return r;
+}
+
 __device__ __forceinline__ uint16_t psi_flag(const BinArgs &a, int64_t tg) {
     const uint32_t fb = a.flags ? (__ldg(a.flags + (tg >> 5)) >> (tg & 31)) & 1u : 0u;
     return static_cast<uint16_t>((__ldg(a.psi + tg) & 0x0FFF) | (fb << 15));
@@ -118,6 +126,7 @@ __global__ void __launch_bounds__(BIN_T) k_bin(BinArgs a)
     __shared__ float2 s_cs[BIN_TILE];
     __shared__ Acc2 s_red[BIN_T / 32][11];
     __shared__ int s_hits[BIN_T / 32];
+    __shared__ Acc2 s_out[BIN_T / 4][10];          // a quad's ten run outputs as double-words
     const int tile = blockIdx.x;
     const int q = a.tile_q[tile];
     const int r0 = a.tile_r0[tile], nr = a.tile_r0[tile + 1] - r0;
@@ -240,7 +249,28 @@ __global__ void __launch_bounds__(BIN_T) k_bin(BinArgs a)
             }
             rs.hits += __shfl_xor_sync(0xffffffffu, rs.hits, ofs);
         }
-        if (pr >= 0 && ql == 0) sums_store(rs, wA, wb, a.rec + static_cast<int64_t>(a.pair_slot[pr]) * 10);
+        // the ten outputs in FP64, spread over the quad's lanes (lane ql takes
+        // outputs ql, ql + 4, ql + 8: FP64 issues slowly on this part, so every
+        // lane of its warp instructions works); the b terms' d - x as double-words
+        if (pr >= 0 && ql == 0) {
+            Acc2 *o = s_out[quad];
+            o[0] = Acc2{static_cast<float>(rs.hits), 0.f};      // hits <= BIN_TILE: exact
+#pragma unroll
+            for (int k = 0; k < 5; ++k) o[1 + k] = rs.a[k];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) o[6 + k] = acc_diff(rs.a[5 + k], rs.a[8 + k]);
+            o[9] = o[0];
+        }
+        __syncwarp();
+        if (pr >= 0) {
+            double *rr = a.rec + static_cast<int64_t>(a.pair_slot[pr]) * 10;
+            for (int i = ql; i < 10; i += 4) {
+                const Acc2 v = s_out[quad][i];
+                const double w = i == 9 ? 1.0 : (i <= 5 ? wA : wb);
+                rr[i] = w * acc_value(v);
+            }
+        }
+        __syncwarp();
     }
 }
 

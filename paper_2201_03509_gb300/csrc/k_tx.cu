@@ -1410,7 +1410,6 @@ __device__ void nc_gather_cols(const NcorrTx &a, const TxCtx &X, float2 *b0, flo
 {
     const int64_t o = X.o, obase = a.off[a.q0], w_lo = obase >> 5;
     float *xq = a.x_out + X.o;
-    const ColGeo G(X.L, X.blk);
     col_inverse(X, b0, b1, a.Y, a.tw + X.L.twb, ADD ? nullptr : a.flags, [&](int j, bool ctr, uint32_t) {
         // ADD: the unit's x0 (written earlier in this launch: coherent loads,
         // not the read-only path); the gather needs only the flag bits
