@@ -301,12 +301,15 @@ k_reduce(const double *__restrict__ rec, const int64_t *__restrict__ pix_slot_of
     if (p >= npix) return;
     DD s[10];
 #pragma unroll
-    for (int i = 0; i < 10; ++i) s[i] = DD{0.0, 0.0};
+    for (int i = 0; i < 9; ++i) s[i] = DD{0.0, 0.0};
+    int nh = 0;                          // hits: an integer count, summed exactly as one
     for (int64_t k = pix_slot_off[p]; k < pix_slot_off[p + 1]; ++k) {
         const double *r = rec + k * 10;
 #pragma unroll
-        for (int i = 0; i < 10; ++i) dd_add(s[i], r[i]);
+        for (int i = 0; i < 9; ++i) dd_add(s[i], r[i]);
+        nh += static_cast<int>(r[9]);
     }
+    s[9] = DD{static_cast<double>(nh), 0.0};
     if (part) {          // the unrounded pairs (hi, lo) of the ten sums
         double *o = part + static_cast<int64_t>(p) * 20;
 #pragma unroll

@@ -410,19 +410,6 @@ __device__ __forceinline__ V split_i(const SplitTw<V> &wk, const SplitTw<V> &wp,
     return vmake<V>(A.x - Bv.y, A.y + Bv.x);
 }
 
-// The split twiddles of mode m - k from those of mode k:
-// W_4n^{m-k} = W_4n^{n/2} conj(W_4n^k) = e^{-i pi/4} conj(e1) and
-// W_4n^{5(m-k)} = e^{-5 i pi/4} conj(e5).
-template <class V>
-__device__ __forceinline__ SplitTw<V> split_tw_mirror(const SplitTw<V> &w) {
-    typedef typename VecT<V>::S S;
-    const S h = static_cast<S>(0.70710678118654752440);
-    SplitTw<V> t;
-    t.e1 = vmake<V>(h * (w.e1.x - w.e1.y), -h * (w.e1.x + w.e1.y));     // (1 - i)/sqrt2 * conj(e1)
-    t.e5 = vmake<V>(h * (w.e5.y - w.e5.x), h * (w.e5.x + w.e5.y));      // (-1 + i)/sqrt2 * conj(e5)
-    return t;
-}
-
 // Row pass.  Loads the tile's rows from Y, forward row FFTs, then
 // pre(nubuf) (a second tile-sized buffer, or null when pre needs none; a
 // barrier follows), then for every packed slot:
@@ -483,18 +470,38 @@ __device__ __forceinline__ void row_pass(const TxCtx &X, V *b0, V *b1, V *__rest
             SplitTw<V> wa;
             wa.e1 = vmul(a1, vld(T.sb1 + k2));
             wa.e5 = vmul(a5, vld(T.sb5 + k2));
-            V Ya = split_f(wa, Za, Zb, sqf);
+            if (ib == ia) {                           // the mode pairs with itself
+                V Ya = split_f(wa, Za, Zb, sqf);
+                Ya = f(ia, ka, Ya);
+                if (INV_BACK) R[ia] = split_i(wa, wa, Ya, Ya, sqi);
+                continue;
+            }
+            // Both slots of the pair at once (modes k and m - k, whose split
+            // twiddles are e1' = w conj(e1), e5' = -w conj(e5), w = e^{-i pi/4}):
+            // with P = e1 (Za + conj Zb), Q = e5 (-i)(Za - conj Zb),
+            // Y_k = (sq/2) conj(P + Q) and Y_{m-k} = (sq/2) conj(w) (P - Q).
+            const V sum = vmake<V>(Za.x + Zb.x, Za.y - Zb.y), dif = vmake<V>(Za.x - Zb.x, Za.y + Zb.y);
+            const V P = vmul(wa.e1, sum), Q = vmul(wa.e5, vmake<V>(dif.y, -dif.x));
+            const S hq = static_cast<S>(0.5) * sqf;
+            const S h = static_cast<S>(0.70710678118654752440);
+            const V pm = vsub(P, Q);
+            V Ya = vmake<V>(hq * (P.x + Q.x), -hq * (P.y + Q.y));
+            V Yb = vmake<V>(hq * h * (pm.x - pm.y), hq * h * (pm.x + pm.y));
             Ya = f(ia, ka, Ya);
-            if (ib != ia) {
-                const SplitTw<V> wb = split_tw_mirror(wa);
-                V Yb = split_f(wb, Zb, Za, sqf);
-                Yb = f(ib, G.m - ka, Yb);
-                if (INV_BACK) {
-                    R[ib] = split_i(wb, wa, Yb, Ya, sqi);
-                    R[ia] = split_i(wa, wb, Ya, Yb, sqi);
-                }
-            } else if (INV_BACK) {
-                R[ia] = split_i(wa, wa, Ya, Ya, sqi);
+            Yb = f(ib, G.m - ka, Yb);
+            if (INV_BACK) {
+                // U_a = (sqi/2) conj(Y_k) conj(e1), U_b = (sqi/2) conj(Y_{m-k}) conj(w) e1;
+                // S = U_a + conj(U_b), G = (U_a - conj(U_b)) conj(e4), e4 = e5 conj(e1);
+                // Z_k = S + i G, Z_{m-k} = conj(S) + i conj(G)
+                const S hi = static_cast<S>(0.5) * sqi;
+                const V Ua = vscale(vmulc(vconj(Ya), wa.e1), hi);
+                const V cb = vmul(vconj(Yb), wa.e1);
+                const V Ub = vscale(vmake<V>(h * (cb.x - cb.y), h * (cb.x + cb.y)), hi);
+                const V Sv = vmake<V>(Ua.x + Ub.x, Ua.y - Ub.y);
+                const V Dv = vmake<V>(Ua.x - Ub.x, Ua.y + Ub.y);
+                const V Gv = vmulc(Dv, vmulc(wa.e5, wa.e1));
+                R[ia] = vmake<V>(Sv.x - Gv.y, Sv.y + Gv.x);
+                R[ib] = vmake<V>(Sv.x + Gv.y, Gv.x - Sv.y);
             }
         }
     }
