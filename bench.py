@@ -123,16 +123,15 @@ def _peaks():
 # from an ncu capture of that kernel on a smaller case of the same band (the
 # summary under profiles/ gives the command and the figures); a full launch's
 # traffic is that ratio times its algorithmic bytes (every pass moves each
-# sample's values in proportion).  Valid only while the kernels' sources
+# sample's values in proportion).  Valid only while the kernel's sources
 # hash to the digest taken with it; otherwise the traffic is reported as null.
+TX_SOURCES = ["csrc/k_tx.cu", "csrc/fft_reg.cuh", "csrc/common.cuh", "csrc/internal.cuh"]
 KERNEL_TRAFFIC = {}
-TRAFFIC_SOURCES = ["csrc/k_tx.cu", "csrc/fft_reg.cuh", "csrc/common.cuh", "csrc/internal.cuh",
-                   "csrc/k_bin_solve.cu", "csrc/k_decode_project.cu"]
 
 
-def kernel_sources_digest() -> str | None:
+def sources_digest(sources) -> str | None:
     h = hashlib.sha256()
-    for rel in TRAFFIC_SOURCES:
+    for rel in sources:
         try:
             with open(os.path.join(ROOT, "paper_2201_03509_gb300", rel), "rb") as f:
                 h.update(f.read())
@@ -447,7 +446,7 @@ def roofline_and_stages(res, peaks, peak_src):
     ach = per_launch / (ms_launch / 1e3) / 1e9
     traffic = None
     tr = KERNEL_TRAFFIC.get(dom)
-    if tr and tr.get("sha256") and kernel_sources_digest() == tr["sha256"]:
+    if tr and tr.get("sha256") and sources_digest(tr["sources"]) == tr["sha256"]:
         traffic = tr["dram_per_algorithmic_byte"] * per_launch
     roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,
             "traffic": traffic, "traffic_unit": "bytes per launch", "launches_per_step": n,
@@ -567,6 +566,8 @@ def secondary_section(args, local):
     import paper_2201_03509_gb300 as tg
     from paper_2201_03509_gb300.step import GibbsTODStep
     cfg = synth.CONFIGS[SECONDARY]
+    if args.secondary_nscan:
+        cfg = synth.scaled(cfg, nscan=args.secondary_nscan)
     t_set = time.time()
     arr, ing = build_band(cfg)
     res = measure_step(args, cfg, arr, ing, local, 0, 1, label="secondary")
@@ -730,6 +731,8 @@ def sweep_section(args, local):
     sampler.start()
     res = sw.run(args.sweep_iters, args.seed, it0=1)
     clocks = sampler.stop()
+    # the same iterations with the bands taking turns (for comparison)
+    seq = sw.run(min(3, args.sweep_iters), args.seed, it0=1 + args.sweep_iters, concurrent=False)
     for c in chains:
         c.plan.status()
     out = {"bands": [c.plan.info()["nsamples"] for c in chains], "band_names": list(synth.SWEEP_BANDS),
@@ -737,6 +740,7 @@ def sweep_section(args, local):
            "ms_per_iteration": res["ms"] / args.sweep_iters,
            "value": res["samples_per_iteration"] * args.sweep_iters / (res["ms"] / 1e3), "unit": "samples/s",
            "band_ms_to_last_iteration": res["band_ms"], "clocks": clocks, "setup_s": setup_s,
+           "bands_in_turn_ms_per_iteration": seq["ms"] / min(3, args.sweep_iters),
            "psd_steps_per_iteration": 1, "oracle_error_first_iteration": errs,
            "timing": "CUDA events on the caller's stream around all iterations; bands on their own streams"}
     for c in chains:
@@ -879,6 +883,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=["lfi70", "lfi30"])
     ap.add_argument("--nscan", type=int, default=0, help="fewer scans (testing only)")
+    ap.add_argument("--secondary-nscan", type=int, default=0,
+                    help="fewer scans of the 30 GHz band in the secondary section (testing only)")
     ap.add_argument("--seed", type=int, default=2022)
     ap.add_argument("--cg-tol", type=float, default=1e-6)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)

@@ -73,12 +73,15 @@ class MultiBandSweep:
     def nsamples(self) -> int:
         return sum(c.nsamples for c in self.chains)
 
-    def run(self, n_iter: int, seed: int, it0: int = 0, mode: int = MODE_DRAW, on_iteration=None) -> dict:
+    def run(self, n_iter: int, seed: int, it0: int = 0, mode: int = MODE_DRAW, on_iteration=None,
+            concurrent: bool = True) -> dict:
         """Queue n_iter iterations of every band (iterations it0 ..
         it0 + n_iter - 1) and wait for them.  The caller's stream waits for
-        every band.  Returns the elapsed time and, per band, the time from the
-        start to the end of its last iteration (CUDA events).  on_iteration(k)
-        is called after iteration k is queued (e.g. to copy results out)."""
+        every band.  With concurrent=False each band's iteration waits for the
+        previous band's (the bands take turns on the GPU; same results).
+        Returns the elapsed time and, per band, the time from the start to
+        the end of its last iteration (CUDA events).  on_iteration(k) is
+        called after iteration k is queued (e.g. to copy results out)."""
         import torch
         cur = torch.cuda.current_stream()
         t0 = torch.cuda.Event(enable_timing=True)
@@ -86,7 +89,11 @@ class MultiBandSweep:
         for c in self.chains:
             c.stream.wait_event(t0)
         for k in range(n_iter):
-            for c in self.chains:
+            for i, c in enumerate(self.chains):
+                if not concurrent and (i or k):
+                    prev = torch.cuda.Event()
+                    prev.record(self.chains[i - 1].stream)
+                    c.stream.wait_event(prev)
                 c.enqueue(seed, it0 + k, mode)
             if on_iteration is not None:
                 on_iteration(k)
