@@ -183,20 +183,21 @@ def ncorr_algorithmic_bytes(lens, iters, flagged):
     return float(b.sum())
 
 
-def kernel_bytes(N, npix, npairs, comp_bytes, lens, iters, flagged):
+def kernel_bytes(N, npix, npairs, comp_bytes, lens, iters, flagged, launched=8):
     """Algorithmic HBM bytes of one step per kernel class (the names of
     tod_kernel_name).  Transforms: the column pass moves its inputs and the
     complex intermediate Y (4 B per sample), the row pass reads and writes
     Y, the inverse column pass reads Y and moves its outputs.  A CG pass
     touches only the detscans still iterating: iteration i of detscan q
     runs when q took more than i iterations; the cooperative tail runs the
-    iterations past the third; the correction passes run over every detscan
-    that ran the CG.  Small per-detscan kernels are left out."""
+    iterations past the `launched` ones (the CG iterations launched one by
+    one); the correction passes run over every detscan that ran the CG.
+    Small per-detscan kernels are left out."""
     lens = np.asarray(lens, np.float64)
     it = np.asarray(iters, np.float64)
     fl = np.asarray(flagged, bool)
-    act = [float(lens[fl & (it > i)].sum()) for i in range(3)]
-    tail = float((lens * np.maximum(it - 3, 0) * fl).sum())
+    act = [float(lens[fl & (it > i)].sum()) for i in range(launched)]
+    tail = float((lens * np.maximum(it - launched, 0) * fl).sum())
     ran = float(lens[fl & (it > 0)].sum())
     return {
         "k_decode": comp_bytes + 6.0 * N,
@@ -427,11 +428,12 @@ def roofline_and_stages(res, peaks, peak_src):
     stage_gbs = {k: (byts[k] / (stage_ms[k] / 1e3) / 1e9 if k in byts else None) for k in stage_ms}
     # kernel bytes averaged over the timed calls' own CG iteration counts
     kb = {}
+    kms = res["kernel_ms"]
+    launched = int(round(kms["k_nc_filter"][1])) if "k_nc_filter" in kms else 8
     for it in res["iters_kt"]:
         for nm, v in kernel_bytes(N, npix, res["npairs"], res["comp_bytes"], res["lens"], it,
-                                  res["flagged"]).items():
+                                  res["flagged"], launched).items():
             kb[nm] = kb.get(nm, 0.0) + v / len(res["iters_kt"])
-    kms = res["kernel_ms"]
     total = sum(ms for ms, _ in kms.values())
     table = {}
     for nm, (ms, n) in sorted(kms.items(), key=lambda x: -x[1][0]):

@@ -187,6 +187,18 @@ tod_status tod_plan_status(tod_plan *p, int32_t *detscan_status);
 #define TOD_SCHED_PER_SCAN   1
 tod_status tod_plan_set_schedule(tod_plan *p, int32_t schedule);
 
+/* Preconditioner of the n_corr CG (the Schur-complement solve of
+ * tod_sample_ncorr): TOD_PREC_NONE; TOD_PREC_BLOCKS, the exact inverses of
+ * the gap blocks' Toeplitz matrices; TOD_PREC_TWO_LEVEL (default), those
+ * plus a coarse correction over two vectors per gap block (indicator and
+ * ramp) in the balancing form.  The solution is the same to the CG
+ * tolerance; only the iteration count changes.  TOD_ERR_ARG for other
+ * values. */
+#define TOD_PREC_NONE      0
+#define TOD_PREC_BLOCKS    1
+#define TOD_PREC_TWO_LEVEL 2
+tod_status tod_plan_set_preconditioner(tod_plan *p, int32_t levels);
+
 /* Per-kernel timing (no counterpart in the paper; for measurement).  While
  * on, every kernel launch of this plan's calls is bracketed by two CUDA
  * events on the call's stream, recorded with the kernel's class below.
@@ -209,12 +221,15 @@ enum {
     TOD_KT_GAIN_ROWS,         /* k_gain_rows */
     TOD_KT_GAIN_COLSINV,      /* k_gain_colsinv */
     TOD_KT_GAIN_FIN,          /* k_gain_fin */
-    TOD_KT_TOEP_H,            /* k_toep_h */
+    TOD_KT_TOEP_KERNEL,       /* the gap kernel h(d) and its prefix sums: k_cz_fill, the k_cz_fft
+                                 passes (log2 of twice the reference length, halved, rounded up),
+                                 k_cz_tables */
     TOD_KT_TOEP_DURBIN,       /* k_toep_durbin */
     TOD_KT_NC_FLAG_COUNT,     /* k_nc_flag_count */
     TOD_KT_NC_FLAG_SCAN,      /* k_nc_flag_scan */
     TOD_KT_NC_FLAG_WRITE,     /* k_nc_flag_write */
     TOD_KT_NC_INDEX,          /* k_nc_index */
+    TOD_KT_NC_COARSE,         /* k_nc_coarse (the coarse correction of the preconditioner) */
     TOD_KT_NC_RHS_COLS,       /* k_nc_rhs_cols */
     TOD_KT_NC_RHS_ROWS,       /* k_nc_rhs_rows */
     TOD_KT_NC_X0_COLS,        /* k_nc_x0_cols */

@@ -16,10 +16,12 @@ import numpy as np
 from ._build import LIB as _LIB_PATH, build as _build_lib
 
 __all__ = ["build", "lib", "fft_length", "huff_encode", "ingest", "ingest_data", "pack_flags", "Plan", "Rng",
-           "TodError", "MODE_DRAW", "MODE_MEAN", "N_PSI", "CKPT_BLOCK"]
+           "TodError", "MODE_DRAW", "MODE_MEAN", "N_PSI", "CKPT_BLOCK", "PREC_NONE", "PREC_BLOCKS",
+           "PREC_TWO_LEVEL"]
 
 MODE_DRAW = 0
 MODE_MEAN = 1
+PREC_NONE, PREC_BLOCKS, PREC_TWO_LEVEL = 0, 1, 2      # n_corr CG preconditioner (set_preconditioner)
 N_PSI = 4096
 CKPT_BLOCK = 512
 
@@ -69,7 +71,8 @@ _lib = None
 
 SYMBOLS = ["tod_status_string", "tod_fft_length", "tod_huff_encode", "tod_huff_free",
            "tod_plan_create", "tod_plan_destroy", "tod_plan_info", "tod_plan_status",
-           "tod_plan_set_schedule", "tod_chi2", "tod_project_adjoint", "tod_project_f64", "tod_bin_partial",
+           "tod_plan_set_schedule", "tod_plan_set_preconditioner", "tod_chi2", "tod_project_adjoint",
+           "tod_project_f64", "tod_bin_partial",
            "tod_combine_partials", "tod_solve_range", "tod_decode", "tod_project", "tod_sample_gain", "tod_sample_ncorr", "tod_bin",
            "tod_solve_maps", "tod_ncorr_static_setup", "tod_sample_ncorr_static", "tod_ncorr_prepare",
            "tod_sample_ncorr_prepared", "tod_sample_noise_psd", "tod_plan_set_ncorr_spectrum",
@@ -103,6 +106,7 @@ def lib():
         L.tod_plan_info.argtypes = [_P, _P, _P, _P, _P, _P]
         L.tod_plan_status.argtypes = [_P, _P]
         L.tod_plan_set_schedule.argtypes = [_P, _i32]
+        L.tod_plan_set_preconditioner.argtypes = [_P, _i32]
         L.tod_kernel_name.argtypes = [_i32]
         L.tod_kernel_name.restype = ctypes.c_char_p
         L.tod_plan_set_kernel_timing.argtypes = [_P, _i32]
@@ -341,6 +345,18 @@ class Plan:
         except Exception:
             pass
 
+    @property
+    def toeplitz_prep_launches(self) -> int:
+        """Launches of tod_ncorr_prepare: the gap kernel (fill, the FFT
+        passes of length 2H, prefix tables) and the Durbin recursion, H the
+        power-of-two reference length (>= 1024) covering the longest
+        detscan."""
+        h = 1024
+        while h < int(np.diff(self.offsets).max()):
+            h *= 2
+        lg = (2 * h).bit_length() - 1
+        return 1 + (lg + 1) // 2 + 1 + 1
+
     def info(self) -> dict:
         ns, nq, npix, cs, nb = _i64(), _i32(), _i32(), _i32(), _i64()
         _check(lib().tod_plan_info(self._h, ctypes.byref(ns), ctypes.byref(nq), ctypes.byref(npix),
@@ -355,6 +371,11 @@ class Plan:
 
     def set_schedule(self, schedule: int):
         _check(lib().tod_plan_set_schedule(self._h, int(schedule)), "tod_plan_set_schedule")
+
+    def set_preconditioner(self, levels: int):
+        """PREC_NONE, PREC_BLOCKS or PREC_TWO_LEVEL (the default) for the
+        n_corr CG."""
+        _check(lib().tod_plan_set_preconditioner(self._h, int(levels)), "tod_plan_set_preconditioner")
 
     def set_kernel_timing(self, on: bool):
         """Bracket every kernel launch of this plan with CUDA events on its

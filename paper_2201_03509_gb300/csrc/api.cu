@@ -867,8 +867,27 @@ tod_status tod_plan_create(tod_plan **out, const tod_band_desc *band)
             return fail(e);
         if ((e = dev_upload(*p, p->qsc, static_cast<float4 *>(nullptr), 2 * static_cast<size_t>(p->nq))))
             return fail(e);
-        // Toeplitz preconditioner tables (per detector)
-        p->toep_nref = maxlen;
+        // Toeplitz preconditioner tables (per detector): the gap kernel at a
+        // power-of-two reference length covering every lag of every detscan
+        p->cz_href = 1024;
+        while (p->cz_href < maxlen) p->cz_href *= 2;
+        const size_t M2 = 2 * static_cast<size_t>(p->cz_href);
+        if ((e = dev_upload(*p, p->czfft, static_cast<float2 *>(nullptr), 2 * static_cast<size_t>(p->ndet) * M2)))
+            return fail(e);
+        if ((e = dev_upload(*p, p->cztab, static_cast<float4 *>(nullptr),
+                            static_cast<size_t>(p->ndet) * (static_cast<size_t>(p->cz_href) + 1))))
+            return fail(e);
+        // coarse correction: block positions, S Z rows for up to czcap
+        // flagged samples (3 % of the band; detscans past it run the
+        // one-level preconditioner), the factor of E per detscan
+        if ((e = dev_upload(*p, p->gbpos, static_cast<int32_t *>(nullptr), static_cast<size_t>(p->nq) * TX_GBMAX)))
+            return fail(e);
+        p->czcap = std::max<int64_t>(p->N / 32, 2 * static_cast<int64_t>(maxlen));
+        if ((e = dev_upload(*p, p->czsz, static_cast<float *>(nullptr), static_cast<size_t>(p->czcap) * TX_CZJ)))
+            return fail(e);
+        if ((e = dev_upload(*p, p->czl, static_cast<float *>(nullptr),
+                            static_cast<size_t>(p->nq) * 2 * TX_CBMAX * (TX_CZB + 1))))
+            return fail(e);
         if ((e = dev_upload(*p, p->htab, static_cast<float *>(nullptr), static_cast<size_t>(p->ndet) * TOEP_LMAX)))
             return fail(e);
         if ((e = dev_upload(*p, p->xtab, static_cast<float *>(nullptr),
@@ -1018,8 +1037,8 @@ tod_status tod_plan_destroy(tod_plan *pl)
 
 static const char *const kKernelNames[TOD_KT_COUNT] = {
     "k_decode", "k_decode_tod", "k_decode_flags", "k_project", "k_project64", "k_det_scalars",
-    "k_gain_cols", "k_gain_rows", "k_gain_colsinv", "k_gain_fin", "k_toep_h", "k_toep_durbin",
-    "k_nc_flag_count", "k_nc_flag_scan", "k_nc_flag_write", "k_nc_index", "k_nc_rhs_cols", "k_nc_rhs_rows",
+    "k_gain_cols", "k_gain_rows", "k_gain_colsinv", "k_gain_fin", "k_toep_kernel", "k_toep_durbin",
+    "k_nc_flag_count", "k_nc_flag_scan", "k_nc_flag_write", "k_nc_index", "k_nc_coarse", "k_nc_rhs_cols", "k_nc_rhs_rows",
     "k_nc_x0_cols", "k_nc_cg_init", "k_nc_scatter", "k_nc_filter", "k_nc_gather", "k_nc_update", "k_nc_list", "k_nc_tail",
     "k_nc_scatter_final", "k_nc_filter_final", "k_nc_gather_final", "k_nc_finish", "k_bin", "k_reduce",
     "k_combine", "k_solve", "k_chi2_cols", "k_chi2_rows", "k_chi2_colsinv", "k_chi2_fin", "k_psd_sums",
@@ -1111,6 +1130,15 @@ tod_status tod_plan_set_schedule(tod_plan *pl, int32_t schedule)
 {
     if (!pl || (schedule != TOD_SCHED_PERSISTENT && schedule != TOD_SCHED_PER_SCAN)) return TOD_ERR_ARG;
     reinterpret_cast<Plan *>(pl)->schedule = schedule;
+    return TOD_OK;
+}
+
+tod_status tod_plan_set_preconditioner(tod_plan *pl, int32_t levels)
+{
+    if (!pl || levels < TOD_PREC_NONE || levels > TOD_PREC_TWO_LEVEL) return TOD_ERR_ARG;
+    Plan *p = reinterpret_cast<Plan *>(pl);
+    p->use_prec = levels >= TOD_PREC_BLOCKS;
+    p->use_coarse = levels >= TOD_PREC_TWO_LEVEL;
     return TOD_OK;
 }
 

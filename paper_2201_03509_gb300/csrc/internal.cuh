@@ -59,6 +59,13 @@ constexpr int TX_TILE = 4096;         // complex values per tile buffer (two buf
 constexpr int TX_MAXR = 20;           // radix stages per sub-transform
 constexpr int TX_GBMAX = 256;         // preconditioner gap blocks per detscan
 constexpr int TX_GBCAP = 2048;        // padded preconditioner elements staged per round
+// Coarse correction of the preconditioner (two-level, balancing form): two
+// vectors per gap block (its indicator and its centred ramp); S Z kept for
+// the TX_CZW neighbouring blocks on either side of each block.
+constexpr int TX_CZW = 2;
+constexpr int TX_CZB = 2 * TX_CZW + 1;            // half-bandwidth of E = Z^T S Z (scalar rows)
+constexpr int TX_CZJ = 2 * (2 * TX_CZW + 1);      // S Z entries stored per flagged sample
+constexpr int TX_CBMAX = 64;                      // most blocks of a detscan with the coarse correction
 
 struct alignas(16) TxLen {
     int32_t n, m, m1, m2, m2p;        // m2p: row stride of a row tile (>= m2, chosen against bank conflicts)
@@ -80,7 +87,7 @@ struct CgState {
     int32_t K;                        // flagged samples
     int32_t it;                       // iterations done
     int32_t mode;                     // CG_* below
-    int32_t pad;
+    int32_t ncz;                      // blocks of the coarse correction (0: one-level preconditioner)
 };
 enum : int32_t { CG_NONE = 0, CG_ACTIVE = 1, CG_DONE = 2, CG_ALLFLAG = 3, CG_OVER = 4 };
 
@@ -117,8 +124,18 @@ struct Plan {
     float *htab = nullptr;           // [ndet][TOEP_LMAX] gap-kernel h(d)
     float *xtab = nullptr;           // [ndet][TOEP_LMAX (TOEP_LMAX+1)/2] T_L^{-1} e_1 per order
     int32_t *lvalid = nullptr;       // [ndet]
-    int32_t toep_nref = 0;
-    bool use_prec = true;
+    // coarse correction: the kernel h(d) at every lag below cz_href (a power
+    // of two >= the longest detscan), from one FFT of length 2 cz_href per
+    // detector, and its prefix sums
+    int32_t cz_href = 0;
+    float2 *czfft = nullptr;         // [2][ndet][2 cz_href] FFT work
+    float4 *cztab = nullptr;         // [ndet][cz_href + 1] (H, G) as FP32 pairs: H(x) = sum_{d<x} h(d), G: d h(d)
+    int32_t *gbpos = nullptr;        // [nq][TX_GBMAX] first sample (within the detscan) of each block
+    float *czsz = nullptr;           // [czcap][TX_CZJ] S Z entries by flagged rank
+    int64_t czcap = 0;
+    float *czl = nullptr;            // [nq][2 TX_CBMAX][TX_CZB + 1] banded Cholesky factor of E
+    bool use_prec = true;            // gap-block inverses (TOD_PREC_BLOCKS)
+    bool use_coarse = true;          // and the coarse correction (TOD_PREC_TWO_LEVEL)
     int32_t schedule = TOD_SCHED_PERSISTENT;
     int32_t nbin_tiles = 0;          // binning tiles (whole runs of one detscan)
     // noise PSD step

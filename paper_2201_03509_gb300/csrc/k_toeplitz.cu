@@ -4,11 +4,17 @@
 // symmetric Toeplitz matrix T_ij = h(|i-j|) with
 //   h(d) = (1/n) sum_{k>=1} gamma_k cos(pi k d / n),
 //   gamma_k = sigma0^2 r/(1+r),  r = (f_k/f_knee)^-alpha,  f_k = k f_samp/(2n).
-// One kernel evaluates h(d), d < TOEP_LMAX, per detector at a reference
-// length (the preconditioner only has to be symmetric positive definite; a
-// kernel shared by all detscans of a detector is close enough for 2-4 CG
-// iterations); a second runs the Durbin recursion (Golub & Van Loan,
-// Algorithm 4.7.1) in FP64 and stores, for every order L, the first column
+// The kernel is evaluated per detector at a reference length H (cz_href, a
+// power of two at least the longest detscan; the preconditioner only has to
+// be symmetric positive definite, and a kernel shared by all detscans of a
+// detector is close enough), at every lag d < H at once: h(d) is the real
+// part of the length-2H DFT of the even sequence a_k = gamma_k (k < H),
+// a_{2H-k} = gamma_k, a_H = 0, divided by 2H.  One FP32 Stockham FFT per
+// detector gives it; a scan then stores, for the coarse correction, the
+// prefix sums H(x) = sum_{d<x} h(d) and G(x) = sum_{d<x} d h(d) (FP64 sums
+// kept as FP32 pairs), and the first TOEP_LMAX lags for the gap blocks.
+// A second kernel runs the Durbin recursion (Golub & Van Loan, Algorithm
+// 4.7.1) in FP64 and stores, for every order L, the first column
 // x = T_L^{-1} e_1.  The CG then applies T_L^{-1} by the Gohberg-Semencul
 // formula T^{-1} = (L(x) L(x)^T - L(w) L(w)^T) / x_0, w = (0, x_{L-1}, ..,
 // x_1), L(v) the lower-triangular Toeplitz matrix with first column v.
@@ -17,45 +23,133 @@
 
 namespace tg {
 
-constexpr int HT = 256;     // threads per h block
-constexpr int HD = 8;       // lags per h block
+constexpr int CZ_FT = 256;      // threads per CTA of the fill and FFT passes
+constexpr int CZ_ST = 1024;     // threads of the prefix-table kernel (one CTA per detector)
 
-__global__ void __launch_bounds__(HT)
-k_toep_h(const double *__restrict__ psd, int ndet, int nref, double fsamp, float *__restrict__ htab)
+// a_k for k < 2H (gamma at f_k = k f_samp / (2H); a_0 = a_H = 0)
+__global__ void __launch_bounds__(CZ_FT)
+k_cz_fill(const double *__restrict__ psd, int href, double fsamp, float2 *__restrict__ a)
 {
     const int det = blockIdx.y;
-    const int d0 = blockIdx.x * HD;
+    const int M = 2 * href;
+    const int k = blockIdx.x * CZ_FT + threadIdx.x;
+    if (k >= M) return;
     const double sig0 = psd[3 * det], fk = psd[3 * det + 1], al = psd[3 * det + 2];
     const float s2 = static_cast<float>(sig0 * sig0);
-    const float fscale = static_cast<float>(fsamp / (2.0 * nref * fk));
+    const float fscale = static_cast<float>(fsamp / (2.0 * href * fk));
     const float mal = static_cast<float>(-al);
-    float acc[HD];
+    const int kk = k <= href ? k : M - k;
+    float g = 0.f;
+    if (kk > 0 && kk < href) {
+        const float r = exp2f(mal * log2f(static_cast<float>(kk) * fscale));
+        g = s2 / (1.0f + 1.0f / r);           // sigma0^2 r / (1 + r), also for r = 0 or inf
+    }
+    a[static_cast<int64_t>(det) * M + k] = make_float2(g, 0.f);
+}
+
+// One radix-R Stockham pass (forward DFT) over every detector's length-M
+// sequence, Ns points of each sub-transform already done (Ns, M powers of
+// two).  Thread j < M/R reads x[j + r M/R], twiddles by exp(-2 pi i r k /
+// (Ns R)), k = j mod Ns, and writes the R outputs to (j - k) R + k + r Ns.
+template <int R>
+__global__ void __launch_bounds__(CZ_FT)
+k_cz_fft(const float2 *__restrict__ src, float2 *__restrict__ dst, int M, int Ns)
+{
+    const int det = blockIdx.y;
+    const int MR = M / R;
+    const int j = blockIdx.x * CZ_FT + threadIdx.x;
+    if (j >= MR) return;
+    const float2 *x = src + static_cast<int64_t>(det) * M;
+    float2 *y = dst + static_cast<int64_t>(det) * M;
+    const int k = j & (Ns - 1);
+    float2 v[R];
 #pragma unroll
-    for (int i = 0; i < HD; ++i) acc[i] = 0.f;
-    const int two_n = 2 * nref;
-    for (int k = 1 + threadIdx.x; k < nref; k += HT) {
-        const float r = exp2f(mal * log2f(static_cast<float>(k) * fscale));
-        const float g = s2 * r / (1.0f + r);
+    for (int r = 0; r < R; ++r) v[r] = x[j + r * MR];
+    if (Ns > 1) {
 #pragma unroll
-        for (int i = 0; i < HD; ++i) {
-            const int d = d0 + i;
-            const int ph = static_cast<int>((static_cast<int64_t>(k) * d) % two_n);  // k d mod 2n
-            acc[i] = fmaf(g, cospif(static_cast<float>(ph) / static_cast<float>(nref)), acc[i]);
+        for (int r = 1; r < R; ++r) {
+            float sn, cs;
+            sincospif(-2.0f * static_cast<float>(r * k) / static_cast<float>(Ns * R), &sn, &cs);
+            v[r] = make_float2(v[r].x * cs - v[r].y * sn, v[r].x * sn + v[r].y * cs);
         }
     }
-    __shared__ float red[HT / 32][HD];
+    float2 o[R];
+    if constexpr (R == 2) {
+        o[0] = make_float2(v[0].x + v[1].x, v[0].y + v[1].y);
+        o[1] = make_float2(v[0].x - v[1].x, v[0].y - v[1].y);
+    } else {
+        const float2 a0 = make_float2(v[0].x + v[2].x, v[0].y + v[2].y);
+        const float2 a1 = make_float2(v[0].x - v[2].x, v[0].y - v[2].y);
+        const float2 a2 = make_float2(v[1].x + v[3].x, v[1].y + v[3].y);
+        const float2 a3 = make_float2(v[1].y - v[3].y, v[3].x - v[1].x);     // (v1 - v3) (-i)
+        o[0] = make_float2(a0.x + a2.x, a0.y + a2.y);
+        o[1] = make_float2(a1.x + a3.x, a1.y + a3.y);
+        o[2] = make_float2(a0.x - a2.x, a0.y - a2.y);
+        o[3] = make_float2(a1.x - a3.x, a1.y - a3.y);
+    }
+    const int base = (j - k) * R + k;
 #pragma unroll
-    for (int i = 0; i < HD; ++i) {
-        float v = acc[i];
-        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][i] = v;
+    for (int r = 0; r < R; ++r) y[base + r * Ns] = o[r];
+}
+
+__device__ __forceinline__ float4 cz_pack(double H, double G) {
+    const float hh = __double2float_rn(H), gh = __double2float_rn(G);
+    return make_float4(hh, __double2float_rn(H - static_cast<double>(hh)), gh,
+                       __double2float_rn(G - static_cast<double>(gh)));
+}
+
+// h(d) = Re X_d / 2H for d < H; tab[x] = (H(x), G(x)) for x <= H (FP64 sums
+// of the FP32 h values, as FP32 pairs); htab = the first TOEP_LMAX lags.
+// Each thread sums a stretch of H / CZ_ST lags; the stretches' sums are
+// scanned over the CTA.
+__global__ void __launch_bounds__(CZ_ST)
+k_cz_tables(const float2 *__restrict__ X, int href, float *__restrict__ htab, float4 *__restrict__ tab)
+{
+    const int det = blockIdx.x;
+    const int M = 2 * href;
+    const float2 *x = X + static_cast<int64_t>(det) * M;
+    float4 *t = tab + static_cast<int64_t>(det) * (href + 1);
+    const float inv = 1.0f / static_cast<float>(M);      // exact: M is a power of two
+    const int per = href / CZ_ST;
+    const int d0 = threadIdx.x * per;
+    double sh = 0.0, sg = 0.0;
+    for (int i = 0; i < per; ++i) {
+        const double h = static_cast<double>(x[d0 + i].x * inv);
+        sh += h;
+        sg += static_cast<double>(d0 + i) * h;
+    }
+    // exclusive scan of (sh, sg) over the CTA
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double ih = sh, ig = sg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double uh = __shfl_up_sync(0xffffffffu, ih, o), ug = __shfl_up_sync(0xffffffffu, ig, o);
+        if (lane >= o) { ih += uh; ig += ug; }
+    }
+    __shared__ double wh[CZ_ST / 32], wg[CZ_ST / 32];
+    if (lane == 31) { wh[warp] = ih; wg[warp] = ig; }
+    __syncthreads();
+    if (warp == 0) {
+        double vh = wh[lane], vg = wg[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double uh = __shfl_up_sync(0xffffffffu, vh, o), ug = __shfl_up_sync(0xffffffffu, vg, o);
+            if (lane >= o) { vh += uh; vg += ug; }
+        }
+        wh[lane] = vh - wh[lane];              // exclusive over the warps
+        wg[lane] = vg - wg[lane];
     }
     __syncthreads();
-    if (threadIdx.x < HD) {
-        float v = 0.f;
-        for (int w = 0; w < HT / 32; ++w) v += red[w][threadIdx.x];
-        htab[det * TOEP_LMAX + d0 + threadIdx.x] = v / static_cast<float>(nref);
+    double Hc = wh[warp] + (ih - sh), Gc = wg[warp] + (ig - sg);
+    for (int i = 0; i < per; ++i) {
+        const int d = d0 + i;
+        const float h32 = x[d].x * inv;
+        if (d < TOEP_LMAX) htab[det * TOEP_LMAX + d] = h32;
+        t[d] = cz_pack(Hc, Gc);
+        Hc += static_cast<double>(h32);
+        Gc += static_cast<double>(d) * static_cast<double>(h32);
     }
+    if (threadIdx.x == CZ_ST - 1) t[href] = cz_pack(Hc, Gc);
 }
 
 // One CTA per detector (FP64 issue is the bound, so the dot products use
@@ -127,10 +221,29 @@ k_toep_durbin(const float *__restrict__ htab, float *__restrict__ xtab, int32_t 
 
 cudaError_t launch_toeplitz_prep(const Plan &p, const double *psd, cudaStream_t st)
 {
-    dim3 g(TOEP_LMAX / HD, p.ndet);
+    const int M = 2 * p.cz_href;
+    float2 *buf[2] = {p.czfft, p.czfft + static_cast<int64_t>(p.ndet) * M};
     {
-        KTIME(TOD_KT_TOEP_H);
-        k_toep_h<<<g, HT, 0, st>>>(psd, p.ndet, p.toep_nref, p.fsamp, p.htab);
+        KTIME(TOD_KT_TOEP_KERNEL);
+        k_cz_fill<<<dim3((M + CZ_FT - 1) / CZ_FT, p.ndet), CZ_FT, 0, st>>>(psd, p.cz_href, p.fsamp, buf[0]);
+    }
+    int cur = 0, Ns = 1, lg = 0;
+    while ((1 << lg) < M) ++lg;
+    if (lg & 1) {
+        KTIME(TOD_KT_TOEP_KERNEL);
+        k_cz_fft<2><<<dim3((M / 2 + CZ_FT - 1) / CZ_FT, p.ndet), CZ_FT, 0, st>>>(buf[cur], buf[cur ^ 1], M, Ns);
+        cur ^= 1;
+        Ns *= 2;
+    }
+    while (Ns < M) {
+        KTIME(TOD_KT_TOEP_KERNEL);
+        k_cz_fft<4><<<dim3((M / 4 + CZ_FT - 1) / CZ_FT, p.ndet), CZ_FT, 0, st>>>(buf[cur], buf[cur ^ 1], M, Ns);
+        cur ^= 1;
+        Ns *= 4;
+    }
+    {
+        KTIME(TOD_KT_TOEP_KERNEL);
+        k_cz_tables<<<p.ndet, CZ_ST, 0, st>>>(buf[cur], p.cz_href, p.htab, p.cztab);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -973,6 +973,13 @@ struct NcorrTx {
     float *spec_out;
     const float *xtab;            // Toeplitz inverses' first columns per detector (null: no preconditioner)
     const int32_t *lvalid;
+    // coarse correction (null czsz: none)
+    const float4 *cztab;          // [ndet][href + 1] prefix sums of the gap kernel
+    int href;
+    int32_t *gbpos;               // [nq][TX_GBMAX] first sample of each block
+    float *czsz;                  // [czcap][TX_CZJ] S Z rows by flagged rank
+    int64_t czcap;
+    float *czl;                   // [nq][2 TX_CBMAX][TX_CZB + 1] factor of E
     // scratch
     float2 *Y;                    // launch-range intermediate
     int64_t *wpre;                // [range words + 1]
@@ -1168,7 +1175,7 @@ __device__ void nc_detscan_index(const NcorrTx &a, NcShared &S, int q)
     if (threadIdx.x == 0) {
         det_scalars_q(a.psd, a.gain, a.off, a.ndet, a.fsamp, q, a.qsc);
         CgState cs;
-        cs.rz = 0.0; cs.stop = 0.0; cs.koff = koff; cs.K = K; cs.it = 0; cs.pad = 0;
+        cs.rz = 0.0; cs.stop = 0.0; cs.koff = koff; cs.K = K; cs.it = 0; cs.ncz = 0;
         if (K == 0) cs.mode = CG_NONE;
         else if (K == n) cs.mode = CG_ALLFLAG;
         else if (koff + K > a.cgcap) cs.mode = CG_OVER;
@@ -1184,6 +1191,7 @@ __device__ void nc_detscan_index(const NcorrTx &a, NcShared &S, int q)
                     const int len = min(lmax, S.gend[g] - b0);
                     if (nb >= TX_GBMAX) { nb = -1; break; }
                     a.gblk[static_cast<int64_t>(q) * TX_GBMAX + nb] = make_int2(rank, len);
+                    if (a.gbpos) a.gbpos[static_cast<int64_t>(q) * TX_GBMAX + nb] = b0;
                     ++nb;
                     rank += len;
                 }
@@ -1459,7 +1467,7 @@ __device__ void nc_gather_cols(const NcorrTx &a, const TxCtx &X, float2 *b0, flo
 // tables, w = (0, x_{L-1}, .., x_1)), blocks staged in rounds of at most
 // TX_GBCAP padded floats.  Returns r.z (CTA total, every thread).  gb: five
 // TX_GBCAP float arrays.
-__device__ double nc_precond(const NcorrTx &a, NcShared &S, int q, const float *r, float *z, float *gb)
+__device__ double nc_precond_m1(const NcorrTx &a, NcShared &S, int q, const float *r, float *z, float *gb)
 {
     const int nb = a.gnb[q];
     const CgState &cs = a.cgs[q];
@@ -1605,6 +1613,325 @@ __device__ double nc_precond(const NcorrTx &a, NcShared &S, int q, const float *
             }
         }
         __syncthreads();
+    }
+    block_sums<1>(rz, S.red, S.out);
+    return S.out[0];
+}
+
+// ---------------------------------------------------------------------------
+// Coarse correction (two-level preconditioner, balancing form):
+//   M r = P^T M1 P r + Z E^{-1} Z^T r,  P = I - S Z E^{-1} Z^T,  E = Z^T S Z,
+// with M1 the gap-block inverses above and Z two vectors per gap block: its
+// indicator and its centred ramp (z(l) = (l - c) / c, c = (L - 1) / 2, over
+// the block's L samples; zero for L = 1).  M is symmetric positive definite
+// for any S Z and E^{-1} used consistently, so the CG converges to the same
+// solution; the correction takes out the smooth modes spread over several
+// gaps, which the block inverses leave to the iterations.  S Z is taken from
+// the Toeplitz kernel alone, (S Z)_{i,(b,s)} = sum_{j in b} h(|p_i - p_j|)
+// z_{b,s}(j), and only for the TX_CZW blocks either side of the row's own
+// block (farther terms dropped), so E is banded (half-bandwidth TX_CZB in
+// scalar rows) and one banded Cholesky factor per detscan applies E^{-1}.
+// The sums over a block come from prefix sums of h:
+//   sum_{delta=lo..hi} h(|delta|)       from H(x) = sum_{d<x} h(d),
+//   sum_{delta=lo..hi} delta h(|delta|) from G(x) = sum_{d<x} d h(d),
+// held as FP32 pairs and differenced in pair arithmetic (the differences of
+// far blocks cancel most of the prefix values).
+// ---------------------------------------------------------------------------
+constexpr int CZ_LROW = TX_CZB + 1;                   // factor row: 1 / L_ii, then L_{i,i-k}, k = 1..TX_CZB
+constexpr int CZ_FLOATS = 2 * TX_CBMAX * CZ_LROW + 3 * 2 * TX_CBMAX + TX_CBMAX * TX_CZJ + CZ_LROW * TX_CZB;
+
+__device__ __forceinline__ float cz_ramp(int l, int L) {
+    if (L < 2) return 0.f;
+    const float c = 0.5f * static_cast<float>(L - 1);
+    return (static_cast<float>(l) - c) * (1.0f / c);
+}
+
+// FP32 pair (hi + lo) arithmetic: Knuth's two-sum and an FMA two-product.
+struct F2 { float h, l; };
+__device__ __forceinline__ F2 f2_add(F2 x, F2 y) {
+    const float s = x.h + y.h;
+    const float bp = s - x.h;
+    float e = (x.h - (s - bp)) + (y.h - bp);
+    e += x.l + y.l;
+    const float h = s + e;
+    return {h, e - (h - s)};
+}
+__device__ __forceinline__ F2 f2_neg(F2 x) { return {-x.h, -x.l}; }
+__device__ __forceinline__ F2 f2_mulf(F2 x, float f) {
+    const float p = __fmul_rn(x.h, f);        // not contracted into the sum below
+    float e = fmaf(x.h, f, -p);
+    e = fmaf(x.l, f, e);
+    const float h = p + e;
+    return {h, e - (h - p)};
+}
+__device__ __forceinline__ F2 cz_H(const float4 *t, int x) { const float4 v = __ldg(t + x); return {v.x, v.y}; }
+__device__ __forceinline__ F2 cz_G(const float4 *t, int x) { const float4 v = __ldg(t + x); return {v.z, v.w}; }
+
+// (S Z) entries of the row at sample p for a block of L samples from s:
+// the indicator's sum over delta = p - j, and the ramp's.
+__device__ __forceinline__ float2 cz_entry(const float4 *__restrict__ t, int p, int s, int L) {
+    const int lo = p - (s + L - 1), hi = p - s;
+    F2 I, Mo;
+    if (lo >= 0) {
+        I = f2_add(cz_H(t, hi + 1), f2_neg(cz_H(t, lo)));
+        Mo = f2_add(cz_G(t, hi + 1), f2_neg(cz_G(t, lo)));
+    } else if (hi < 0) {
+        I = f2_add(cz_H(t, 1 - lo), f2_neg(cz_H(t, -hi)));
+        Mo = f2_add(cz_G(t, -hi), f2_neg(cz_G(t, 1 - lo)));
+    } else {
+        I = f2_add(f2_add(cz_H(t, hi + 1), cz_H(t, 1 - lo)), f2_neg(cz_H(t, 1)));
+        Mo = f2_add(cz_G(t, hi + 1), f2_neg(cz_G(t, 1 - lo)));
+    }
+    float ramp = 0.f;
+    if (L > 1) {
+        // sum_j (j - c_b) h = (p - c_b) I - Mo, c_b = s + (L - 1)/2
+        const float pc = 0.5f * static_cast<float>(2 * (p - s) - (L - 1));
+        const F2 v = f2_add(f2_mulf(I, pc), f2_neg(Mo));
+        ramp = (v.h + v.l) * (1.0f / (0.5f * static_cast<float>(L - 1)));
+    }
+    return make_float2(I.h + I.l, ramp);
+}
+
+// Builds the coarse correction of detscan q (after the index phase): S Z
+// rows, E, its banded Cholesky factor.  On success cgs[q].ncz = blocks.
+__device__ void nc_coarse_setup(const NcorrTx &a, int q)
+{
+    __shared__ int s_rank[TX_CBMAX], s_len[TX_CBMAX], s_pos[TX_CBMAX];
+    __shared__ float s_E[TX_CBMAX][4 * (2 * TX_CZW + 1)];
+    __shared__ double s_L[2 * TX_CBMAX][CZ_LROW];
+    __shared__ int s_ok;
+    const CgState cs = a.cgs[q];
+    const int nb = a.gnb[q];
+    if (cs.mode != CG_ACTIVE || nb < 1 || nb > TX_CBMAX || !a.czsz || cs.koff + cs.K > a.czcap) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int det = q % a.ndet;
+    const float4 *tab = a.cztab + static_cast<int64_t>(det) * (a.href + 1);
+    for (int b = threadIdx.x; b < nb; b += TX_T) {
+        const int2 bl = a.gblk[static_cast<int64_t>(q) * TX_GBMAX + b];
+        s_rank[b] = bl.x;
+        s_len[b] = bl.y;
+        s_pos[b] = a.gbpos[static_cast<int64_t>(q) * TX_GBMAX + b];
+    }
+    __syncthreads();
+    float *sz = a.czsz + cs.koff * TX_CZJ;
+    // S Z rows, one warp per block, with the block's rows of E: for the
+    // neighbour j and the row/column vector kinds (s', s), sum over the
+    // block's samples of z_{s'} (S Z)_s
+    for (int b = warp; b < nb; b += TX_T / 32) {
+        const int L = s_len[b];
+        float e[4 * (2 * TX_CZW + 1)];
+#pragma unroll
+        for (int k = 0; k < 4 * (2 * TX_CZW + 1); ++k) e[k] = 0.f;
+        for (int l = lane; l < L; l += 32) {
+            const int i = s_rank[b] + l, p = s_pos[b] + l;
+            const float zr = cz_ramp(l, L);
+            float2 *row = reinterpret_cast<float2 *>(sz + static_cast<int64_t>(i) * TX_CZJ);
+#pragma unroll
+            for (int j = 0; j < 2 * TX_CZW + 1; ++j) {
+                const int c = b - TX_CZW + j;
+                float2 v = make_float2(0.f, 0.f);
+                if (c >= 0 && c < nb) v = cz_entry(tab, p, s_pos[c], s_len[c]);
+                row[j] = v;
+                e[4 * j + 0] += v.x;
+                e[4 * j + 1] += v.y;
+                e[4 * j + 2] = fmaf(zr, v.x, e[4 * j + 2]);
+                e[4 * j + 3] = fmaf(zr, v.y, e[4 * j + 3]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4 * (2 * TX_CZW + 1); ++k) {
+            float v = e[k];
+            for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) s_E[b][k] = v;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // E(x, y), x = 2b + s', y = 2c + s: from block b's rows
+        // s_E[b][4 (c - b + W) + 2 s' + s], averaged with block c's
+        auto Exy = [&](int x, int y) -> double {
+            const int b = x >> 1, sp = x & 1, c = y >> 1, sc = y & 1;
+            if (b - c > TX_CZW || c - b > TX_CZW) return 0.0;
+            if ((sp && s_len[b] < 2) || (sc && s_len[c] < 2)) return x == y ? 1.0 : 0.0;
+            return 0.5 * (static_cast<double>(s_E[b][4 * (c - b + TX_CZW) + 2 * sp + sc]) +
+                          static_cast<double>(s_E[c][4 * (b - c + TX_CZW) + 2 * sc + sp]));
+        };
+        const int nc = 2 * nb;
+        int ok = 1;
+        for (int x = 0; x < nc && ok; ++x) {
+            double dsum = Exy(x, x);
+            for (int k = TX_CZB; k >= 1; --k) {
+                const int y = x - k;
+                double v = 0.0;
+                if (y >= 0) {
+                    v = Exy(x, y);
+                    // sum over m < y of L(x, m) L(y, m), both within the band
+                    for (int m = x - TX_CZB; m < y; ++m)
+                        if (m >= 0 && y - m <= TX_CZB) v -= s_L[x][x - m] * s_L[y][y - m];
+                    v /= s_L[y][0];
+                }
+                s_L[x][k] = v;
+                dsum -= v * v;
+            }
+            if (!(dsum > 1e-12 * fabs(Exy(x, x))) || !(dsum > 0.0)) ok = 0;
+            else s_L[x][0] = sqrt(dsum);
+        }
+        s_ok = ok;
+        if (ok) a.cgs[q].ncz = nb;
+    }
+    __syncthreads();
+    if (s_ok) {
+        float *Lq = a.czl + static_cast<int64_t>(q) * (2 * TX_CBMAX * CZ_LROW);
+        for (int i = threadIdx.x; i < 2 * nb * CZ_LROW; i += TX_T) {
+            const int x = i / CZ_LROW, k = i % CZ_LROW;
+            Lq[i] = k == 0 ? static_cast<float>(1.0 / s_L[x][0]) : static_cast<float>(s_L[x][k]);
+        }
+    }
+    __syncthreads();
+}
+
+// t = E^{-1} u with the banded factor staged in shared memory (rows of
+// CZ_LROW; rows nc .. nc + TX_CZB - 1 zero).  One thread.
+__device__ __forceinline__ void cz_solve(const float *L, int nc, const float *u, float *t)
+{
+    float w[TX_CZB];
+#pragma unroll
+    for (int k = 0; k < TX_CZB; ++k) w[k] = 0.f;
+    for (int x = 0; x < nc; ++x) {
+        const float *l = L + x * CZ_LROW;
+        float v = u[x];
+#pragma unroll
+        for (int k = 1; k <= TX_CZB; ++k) v = fmaf(-l[k], w[k - 1], v);
+        v *= l[0];
+#pragma unroll
+        for (int k = TX_CZB - 1; k > 0; --k) w[k] = w[k - 1];
+        w[0] = v;
+        t[x] = v;
+    }
+#pragma unroll
+    for (int k = 0; k < TX_CZB; ++k) w[k] = 0.f;
+    for (int x = nc - 1; x >= 0; --x) {
+        float v = t[x];
+#pragma unroll
+        for (int k = 1; k <= TX_CZB; ++k) v = fmaf(-L[(x + k) * CZ_LROW + k], w[k - 1], v);
+        v *= L[x * CZ_LROW];
+#pragma unroll
+        for (int k = TX_CZB - 1; k > 0; --k) w[k] = w[k - 1];
+        w[0] = v;
+        t[x] = v;
+    }
+}
+
+// z = M r (two-level when the detscan has a coarse correction, else the
+// block inverses alone).  Returns r.z (CTA total, every thread).  gb: the
+// five TX_GBCAP arrays of the block inverses, then CZ_FLOATS for the
+// coarse vectors.
+__device__ double nc_precond(const NcorrTx &a, NcShared &S, int q, const float *r, float *z, float *gb)
+{
+    const CgState cs = a.cgs[q];
+    const int nb = cs.ncz;
+    if (nb <= 0) return nc_precond_m1(a, S, q, r, z, gb);
+    const int nc = 2 * nb;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *cL = gb + 5 * TX_GBCAP;                      // [(nc + TX_CZB) rows][CZ_LROW]
+    float *ct = cL + (2 * TX_CBMAX + TX_CZB) * CZ_LROW;  // t = E^{-1} Z^T r
+    float *cu = ct + 2 * TX_CBMAX;                      // Z^T r, then (S Z)^T z1
+    float *cs2 = cu + 2 * TX_CBMAX;                     // t - E^{-1} (S Z)^T z1
+    float *cP = cs2 + 2 * TX_CBMAX;                     // [nb][TX_CZJ] per-block partial sums
+    const int2 *gbl = a.gblk + static_cast<int64_t>(q) * TX_GBMAX;
+    const float *Lq = a.czl + static_cast<int64_t>(q) * (2 * TX_CBMAX * CZ_LROW);
+    const float *sz = a.czsz + cs.koff * TX_CZJ;
+    for (int i = threadIdx.x; i < (nc + TX_CZB) * CZ_LROW; i += TX_T) cL[i] = i < nc * CZ_LROW ? Lq[i] : 0.f;
+    // Z^T r: one warp per block
+    for (int b = warp; b < nb; b += TX_T / 32) {
+        const int2 bl = gbl[b];
+        float s0 = 0.f, s1 = 0.f;
+        for (int l = lane; l < bl.y; l += 32) {
+            const float v = r[bl.x + l];
+            s0 += v;
+            s1 = fmaf(cz_ramp(l, bl.y), v, s1);
+        }
+        for (int o = 16; o; o >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        }
+        if (lane == 0) { cu[2 * b] = s0; cu[2 * b + 1] = s1; }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) cz_solve(cL, nc, cu, ct);
+    __syncthreads();
+    // w = r - (S Z) t, into z
+    for (int b = warp; b < nb; b += TX_T / 32) {
+        const int2 bl = gbl[b];
+        for (int l = lane; l < bl.y; l += 32) {
+            const int i = bl.x + l;
+            const float2 *row = reinterpret_cast<const float2 *>(sz + static_cast<int64_t>(i) * TX_CZJ);
+            float v = r[i];
+#pragma unroll
+            for (int j = 0; j < 2 * TX_CZW + 1; ++j) {
+                const int c = b - TX_CZW + j;
+                if (c >= 0 && c < nb) {
+                    const float2 e = row[j];
+                    v = fmaf(-e.x, ct[2 * c], v);
+                    v = fmaf(-e.y, ct[2 * c + 1], v);
+                }
+            }
+            z[i] = v;
+        }
+    }
+    __syncthreads();
+    // z1 = M1 w, in place
+    nc_precond_m1(a, S, q, z, z, gb);
+    __syncthreads();
+    // (S Z)^T z1: per block the sums over its rows of each stored column
+    for (int b = warp; b < nb; b += TX_T / 32) {
+        const int2 bl = gbl[b];
+        float e[TX_CZJ];
+#pragma unroll
+        for (int k = 0; k < TX_CZJ; ++k) e[k] = 0.f;
+        for (int l = lane; l < bl.y; l += 32) {
+            const int i = bl.x + l;
+            const float2 *row = reinterpret_cast<const float2 *>(sz + static_cast<int64_t>(i) * TX_CZJ);
+            const float zi = z[i];
+#pragma unroll
+            for (int j = 0; j < 2 * TX_CZW + 1; ++j) {
+                const float2 v = row[j];
+                e[2 * j] = fmaf(v.x, zi, e[2 * j]);
+                e[2 * j + 1] = fmaf(v.y, zi, e[2 * j + 1]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < TX_CZJ; ++k) {
+            float v = e[k];
+            for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) cP[b * TX_CZJ + k] = v;
+        }
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < nc; x += TX_T) {
+        const int c = x >> 1, sc = x & 1;
+        float v = 0.f;
+        for (int bp = max(0, c - TX_CZW); bp <= min(nb - 1, c + TX_CZW); ++bp)
+            v += cP[bp * TX_CZJ + 2 * (c - bp + TX_CZW) + sc];
+        cu[x] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cz_solve(cL, nc, cu, cs2);
+        for (int x = 0; x < nc; ++x) cs2[x] = ct[x] - cs2[x];
+    }
+    __syncthreads();
+    // z = z1 + Z (t - E^{-1} (S Z)^T z1);  r.z
+    Acc2 rz[1] = {{0.f, 0.f}};
+    for (int b = warp; b < nb; b += TX_T / 32) {
+        const int2 bl = gbl[b];
+        const float c0 = cs2[2 * b], c1 = cs2[2 * b + 1];
+        for (int l = lane; l < bl.y; l += 32) {
+            const int i = bl.x + l;
+            const float zi = z[i] + fmaf(c1, cz_ramp(l, bl.y), c0);
+            z[i] = zi;
+            acc_add_prod(rz[0], r[i], zi);
+        }
     }
     block_sums<1>(rz, S.red, S.out);
     return S.out[0];
@@ -1817,6 +2144,10 @@ __global__ void __launch_bounds__(TX_T) k_nc_index(NcorrTx a)
         __syncthreads();
     }
 }
+__global__ void __launch_bounds__(TX_T) k_nc_coarse(NcorrTx a)
+{
+    for (int q = a.q0 + blockIdx.x; q < a.q1; q += gridDim.x) nc_coarse_setup(a, q);
+}
 __global__ void __launch_bounds__(TX_T, 3) k_nc_rhs_cols(NcorrTx a)
 {
     extern __shared__ __align__(16) float2 tx_smem[];
@@ -1940,7 +2271,8 @@ __global__ void k_nc_finish(NcorrTx a)
 // launchers
 // ===========================================================================
 static size_t tx_smem_bytes(bool fp64) { return (fp64 ? sizeof(double2) : sizeof(float2)) * 2 * TX_TILE; }
-constexpr size_t kGbBytes = 5 * TX_GBCAP * sizeof(float);           // preconditioner staging
+constexpr size_t kGbBytes = (5 * TX_GBCAP + CZ_FLOATS) * sizeof(float);   // preconditioner staging
+static_assert(kGbBytes <= sizeof(float2) * 2 * TX_TILE, "the preconditioner staging fits the tile buffers");
 constexpr int NC_LAUNCHED_ITERS = 8;                                // CG iterations as separate launches
 
 template <class K>
@@ -2096,6 +2428,8 @@ cudaError_t launch_tx_ncorr(const Plan &p, const float *d, const float *s, const
     a.q0 = q0; a.q1 = q1; a.ndet = p.ndet; a.fsamp = p.fsamp; a.rng = rng; a.mode = mode; a.tol = tol;
     a.maxit = maxit; a.x_out = x; a.iters = iters; a.status = p.status; a.spec_out = p.spec_out;
     a.xtab = p.use_prec ? p.xtab : nullptr; a.lvalid = p.lvalid;
+    a.cztab = p.cztab; a.href = p.cz_href; a.gbpos = p.gbpos; a.czsz = (p.use_prec && p.use_coarse) ? p.czsz : nullptr;
+    a.czcap = p.czcap; a.czl = p.czl;
     a.Y = sc.Y; a.wpre = sc.wpre; a.chunk = p.chunk; a.cgs = p.cgs; a.gblk = p.gblk; a.gnb = p.gnb;
     a.cgv = sc.cgv; a.cgcap = sc.cgcap; a.count = p.cg_count; a.qsc = p.qsc; a.list = p.nclist;
     const size_t s32 = tx_smem_bytes(false), sgb = std::max(s32, kGbBytes);
@@ -2120,6 +2454,10 @@ cudaError_t launch_tx_ncorr(const Plan &p, const float *d, const float *s, const
     {
         KTIME(TOD_KT_NC_INDEX);
         k_nc_index<<<gq, TX_T, 0, st>>>(a);
+    }
+    {
+        KTIME(TOD_KT_NC_COARSE);
+        k_nc_coarse<<<gq, TX_T, 0, st>>>(a);
     }
     // x0 = B^{-1} b
     {

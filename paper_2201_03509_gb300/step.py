@@ -206,16 +206,18 @@ class GibbsTODStep:
             st.wait_stream(lo)
         self._mark_d_done(stream)
 
-    # decode x2, project, gain (scalars, three passes, draw), Toeplitz prep x2,
-    # n_corr (flag index 4, right-hand side 3, CG start and its list, 8
-    # launched CG iterations x (3 passes, update, list), cooperative tail,
-    # list, correction 3, finish), bin + reduce, solve
-    LAUNCHES_PER_STEP = 2 + 1 + 5 + 2 + (4 + 3 + 2 + 8 * 5 + 1 + 1 + 3 + 1) + 2 + 1
+    # decode x2, project, gain (scalars, three passes, draw), n_corr (flag
+    # index 4, coarse correction, right-hand side 3, CG start and its list,
+    # 8 launched CG iterations x (3 passes, update, list), cooperative tail,
+    # list, correction 3, finish), bin + reduce, solve; plus the
+    # preconditioner preparation (Plan.toeplitz_prep_launches)
+    LAUNCHES_PER_STEP = 2 + 1 + 5 + (4 + 1 + 3 + 2 + 8 * 5 + 1 + 1 + 3 + 1) + 2 + 1
     DATA_LAUNCHES = 2       # with data_streams: decode of the TOD and of the flags
 
     @property
     def launches_per_step(self) -> int:
-        return (self.LAUNCHES_PER_STEP + (self.DATA_LAUNCHES if self.data_streams else 0)
+        return (self.LAUNCHES_PER_STEP + self.plan.toeplitz_prep_launches
+                + (self.DATA_LAUNCHES if self.data_streams else 0)
                 + (1 if self.gain_prior is not None else 0))
 
     def capture(self, map32_in, seed: int, band: int = 0, mode: int = MODE_DRAW):
