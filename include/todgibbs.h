@@ -223,7 +223,7 @@ enum {
     TOD_KT_GAIN_FIN,          /* k_gain_fin */
     TOD_KT_TOEP_KERNEL,       /* the gap kernel h(d) and its prefix sums: k_cz_fill, the k_cz_fft
                                  passes (log2 of twice the reference length, halved, rounded up),
-                                 k_cz_tables */
+                                 k_cz_sums, k_cz_tables */
     TOD_KT_TOEP_DURBIN,       /* k_toep_durbin */
     TOD_KT_NC_FLAG_COUNT,     /* k_nc_flag_count */
     TOD_KT_NC_FLAG_SCAN,      /* k_nc_flag_scan */

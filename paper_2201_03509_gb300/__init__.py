@@ -348,14 +348,14 @@ class Plan:
     @property
     def toeplitz_prep_launches(self) -> int:
         """Launches of tod_ncorr_prepare: the gap kernel (fill, the FFT
-        passes of length 2H, prefix tables) and the Durbin recursion, H the
-        power-of-two reference length (>= 1024) covering the longest
-        detscan."""
+        passes of length 2H, chunk sums, prefix tables) and the Durbin
+        recursion, H the power-of-two reference length (>= 1024) covering
+        the longest detscan."""
         h = 1024
         while h < int(np.diff(self.offsets).max()):
             h *= 2
         lg = (2 * h).bit_length() - 1
-        return 1 + (lg + 1) // 2 + 1 + 1
+        return 1 + (lg + 1) // 2 + 2 + 1
 
     def info(self) -> dict:
         ns, nq, npix, cs, nb = _i64(), _i32(), _i32(), _i32(), _i64()

@@ -24,7 +24,7 @@
 namespace tg {
 
 constexpr int CZ_FT = 256;      // threads per CTA of the fill and FFT passes
-constexpr int CZ_ST = 1024;     // threads of the prefix-table kernel (one CTA per detector)
+constexpr int CZ_ST = 256;      // threads of the prefix-table kernels
 
 // a_k for k < 2H (gamma at f_k = k f_samp / (2H); a_0 = a_H = 0)
 __global__ void __launch_bounds__(CZ_FT)
@@ -100,25 +100,59 @@ __device__ __forceinline__ float4 cz_pack(double H, double G) {
 
 // h(d) = Re X_d / 2H for d < H; tab[x] = (H(x), G(x)) for x <= H (FP64 sums
 // of the FP32 h values, as FP32 pairs); htab = the first TOEP_LMAX lags.
-// Each thread sums a stretch of H / CZ_ST lags; the stretches' sums are
-// scanned over the CTA.
-__global__ void __launch_bounds__(CZ_ST)
-k_cz_tables(const float2 *__restrict__ X, int href, float *__restrict__ htab, float4 *__restrict__ tab)
-{
-    const int det = blockIdx.x;
-    const int M = 2 * href;
-    const float2 *x = X + static_cast<int64_t>(det) * M;
-    float4 *t = tab + static_cast<int64_t>(det) * (href + 1);
-    const float inv = 1.0f / static_cast<float>(M);      // exact: M is a power of two
-    const int per = href / CZ_ST;
-    const int d0 = threadIdx.x * per;
-    double sh = 0.0, sg = 0.0;
+// The lags of a detector are cut into chunks of CZ_ST threads x cz_per(H)
+// lags, one CTA each: k_cz_sums adds up every chunk, k_cz_tables scans
+// within its chunk from the sum of the chunks before it.
+__host__ __device__ __forceinline__ int cz_per(int href) { return href >= 64 * CZ_ST ? 64 : href / CZ_ST; }
+
+__device__ __forceinline__ void cz_stretch(const float2 *__restrict__ x, int d0, int per, float inv, double &sh,
+                                           double &sg) {
+    sh = 0.0;
+    sg = 0.0;
     for (int i = 0; i < per; ++i) {
         const double h = static_cast<double>(x[d0 + i].x * inv);
         sh += h;
         sg += static_cast<double>(d0 + i) * h;
     }
-    // exclusive scan of (sh, sg) over the CTA
+}
+
+__global__ void __launch_bounds__(CZ_ST)
+k_cz_sums(const float2 *__restrict__ X, int href, double2 *__restrict__ csum)
+{
+    const int det = blockIdx.y, nch = gridDim.x;
+    const int per = cz_per(href);
+    const float2 *x = X + static_cast<int64_t>(det) * 2 * href;
+    const float inv = 1.0f / static_cast<float>(2 * href);      // exact: a power of two
+    double sh, sg;
+    cz_stretch(x, (blockIdx.x * CZ_ST + threadIdx.x) * per, per, inv, sh, sg);
+    for (int o = 16; o; o >>= 1) {
+        sh += __shfl_xor_sync(0xffffffffu, sh, o);
+        sg += __shfl_xor_sync(0xffffffffu, sg, o);
+    }
+    __shared__ double wh[CZ_ST / 32], wg[CZ_ST / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { wh[warp] = sh; wg[warp] = sg; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double th = 0.0, tg_ = 0.0;
+        for (int w = 0; w < CZ_ST / 32; ++w) { th += wh[w]; tg_ += wg[w]; }
+        csum[det * nch + blockIdx.x] = make_double2(th, tg_);
+    }
+}
+
+__global__ void __launch_bounds__(CZ_ST)
+k_cz_tables(const float2 *__restrict__ X, int href, const double2 *__restrict__ csum, float *__restrict__ htab,
+            float4 *__restrict__ tab)
+{
+    const int det = blockIdx.y, ch = blockIdx.x, nch = gridDim.x;
+    const int per = cz_per(href);
+    const float2 *x = X + static_cast<int64_t>(det) * 2 * href;
+    float4 *t = tab + static_cast<int64_t>(det) * (href + 1);
+    const float inv = 1.0f / static_cast<float>(2 * href);
+    const int d0 = (ch * CZ_ST + threadIdx.x) * per;
+    double sh, sg;
+    cz_stretch(x, d0, per, inv, sh, sg);
+    // exclusive scan of (sh, sg) over the CTA, offset by the earlier chunks
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double ih = sh, ig = sg;
 #pragma unroll
@@ -127,20 +161,31 @@ k_cz_tables(const float2 *__restrict__ X, int href, float *__restrict__ htab, fl
         if (lane >= o) { ih += uh; ig += ug; }
     }
     __shared__ double wh[CZ_ST / 32], wg[CZ_ST / 32];
+    __shared__ double base[2];
     if (lane == 31) { wh[warp] = ih; wg[warp] = ig; }
+    if (threadIdx.x == 0) {
+        double bh = 0.0, bg = 0.0;
+        for (int c = 0; c < ch; ++c) { const double2 v = csum[det * nch + c]; bh += v.x; bg += v.y; }
+        base[0] = bh;
+        base[1] = bg;
+    }
     __syncthreads();
     if (warp == 0) {
-        double vh = wh[lane], vg = wg[lane];
+        constexpr int NW = CZ_ST / 32;
+        const double ownh = lane < NW ? wh[lane] : 0.0, owng = lane < NW ? wg[lane] : 0.0;
+        double vh = ownh, vg = owng;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const double uh = __shfl_up_sync(0xffffffffu, vh, o), ug = __shfl_up_sync(0xffffffffu, vg, o);
             if (lane >= o) { vh += uh; vg += ug; }
         }
-        wh[lane] = vh - wh[lane];              // exclusive over the warps
-        wg[lane] = vg - wg[lane];
+        if (lane < NW) {
+            wh[lane] = vh - ownh;              // exclusive over the warps
+            wg[lane] = vg - owng;
+        }
     }
     __syncthreads();
-    double Hc = wh[warp] + (ih - sh), Gc = wg[warp] + (ig - sg);
+    double Hc = base[0] + wh[warp] + (ih - sh), Gc = base[1] + wg[warp] + (ig - sg);
     for (int i = 0; i < per; ++i) {
         const int d = d0 + i;
         const float h32 = x[d].x * inv;
@@ -149,7 +194,7 @@ k_cz_tables(const float2 *__restrict__ X, int href, float *__restrict__ htab, fl
         Hc += static_cast<double>(h32);
         Gc += static_cast<double>(d) * static_cast<double>(h32);
     }
-    if (threadIdx.x == CZ_ST - 1) t[href] = cz_pack(Hc, Gc);
+    if (ch == nch - 1 && threadIdx.x == CZ_ST - 1) t[href] = cz_pack(Hc, Gc);
 }
 
 // One CTA per detector (FP64 issue is the bound, so the dot products use
@@ -241,9 +286,16 @@ cudaError_t launch_toeplitz_prep(const Plan &p, const double *psd, cudaStream_t 
         cur ^= 1;
         Ns *= 4;
     }
+    // chunk sums into the other FFT buffer (free after the last pass)
+    const int nch = p.cz_href / (CZ_ST * cz_per(p.cz_href));
+    double2 *csum = reinterpret_cast<double2 *>(buf[cur ^ 1]);
     {
         KTIME(TOD_KT_TOEP_KERNEL);
-        k_cz_tables<<<p.ndet, CZ_ST, 0, st>>>(buf[cur], p.cz_href, p.htab, p.cztab);
+        k_cz_sums<<<dim3(nch, p.ndet), CZ_ST, 0, st>>>(buf[cur], p.cz_href, csum);
+    }
+    {
+        KTIME(TOD_KT_TOEP_KERNEL);
+        k_cz_tables<<<dim3(nch, p.ndet), CZ_ST, 0, st>>>(buf[cur], p.cz_href, csum, p.htab, p.cztab);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
