@@ -126,7 +126,14 @@ def _peaks():
 # sample's values in proportion).  Valid only while the kernel's sources
 # hash to the digest taken with it; otherwise the traffic is reported as null.
 TX_SOURCES = ["csrc/k_tx.cu", "csrc/fft_reg.cuh", "csrc/common.cuh", "csrc/internal.cuh"]
-KERNEL_TRAFFIC = {}
+KERNEL_TRAFFIC = {
+    # profiles/k_tx_passes_lfi70_40scans.md: the first CG filter launch of the
+    # 480-detscan case (every detscan iterating: 8 x 104,686,200 algorithmic
+    # bytes) read 0.419450 GB and wrote 0.362361 GB of DRAM
+    "k_nc_filter": {"dram_per_algorithmic_byte": (0.419450e9 + 0.362361e9) / (8.0 * 104686200),
+                    "sources": TX_SOURCES,
+                    "sha256": "cb1f69f545b33dfc4b03532841d50262a1cfbbf09049919a52246a732ed58e2f"},
+}
 
 
 def sources_digest(sources) -> str | None:
@@ -339,10 +346,11 @@ def measure_step(args, cfg, arr, ing, local, rank, ws, label="main"):
             torch.cuda.synchronize()
             graph_ms = g0.elapsed_time(g1) / args.steps
             step.graph = None
+            step.graphs = []
         except Exception as ex:          # report, do not hide
             graph_ms = "capture failed: %s" % ex
-    # the eager step with the pointing decoded in-step, as the graph does
-    # (no next-step decode under the n_corr draw)
+    # the eager step with the pointing decoded in-step (no next-step decode
+    # under the n_corr draw)
     inline_ms = None
     if not args.no_graph and ws == 1:
         step.lookahead = False
