@@ -130,9 +130,10 @@ class GibbsTODStep:
         self._d_done = torch.cuda.Event()
         self._d_done.record(self._stream(stream))     # self.d is read by nothing queued after this
 
-    def run(self, map32_in, rng: Rng, mode: int = MODE_DRAW, stream=None):
+    def run(self, map32_in, rng: Rng, mode: int = MODE_DRAW, stream=None, gain_event=None):
         """Enqueue one step; the new map lands in self.map / self.map32.
-        Uses the detector data of a pending prefetch_tod() if there is one."""
+        Uses the detector data of a pending prefetch_tod() if there is one.
+        gain_event, if given, is recorded once the gains are drawn."""
         import torch
         self._take_prefetched(stream)
         p = self.plan
@@ -167,6 +168,8 @@ class GibbsTODStep:
             # every detector's scans drawn jointly from their conditionals and the prior
             p.sample_gain_smooth(self.mu, self.sigma, self.gain_prior, rng, mode, self.gain, self.gain_iters,
                                  stream=hp)
+        if gain_event is not None:
+            gain_event.record(hp)
         hp.wait_event(prepared)
         lookahead = self.lookahead
         if lookahead:
@@ -221,27 +224,96 @@ class GibbsTODStep:
                 + (1 if self.gain_prior is not None else 0))
 
     def capture(self, map32_in, seed: int, band: int = 0, mode: int = MODE_DRAW):
-        """Capture one step into a CUDA graph.  The Gibbs iteration is read by
-        the kernels from a device word, so replay(it) draws fresh numbers."""
+        """Capture the step into CUDA graphs.  The Gibbs iteration is read by
+        the kernels from a device word, so replay(it) draws fresh numbers.
+
+        With lookahead, two graphs are captured that take their pointing
+        from the two pix/psi pairs in turn and do not decode it; replay()
+        alternates between them, launches the graph on the high-priority
+        stream and, once the graph has drawn the gains (an event recorded
+        inside it), decodes the other pair (the next replay's pointing) with
+        eager launches on the low-priority stream beside the n_corr draw.
+        (A graph's kernels run at the priority of the stream it is launched
+        into, so a decode captured inside the graph would compete with the
+        draw at equal priority.)  Without lookahead one graph decodes
+        in-step."""
         import torch
         self.iter_dev = torch.zeros(1, dtype=torch.int64, device=self.d.device)
         self._rng_graph = Rng(seed, band, 0, self.iter_dev.data_ptr())
         self._map_graph = map32_in
-        # the captured step decodes its own pointing (no lookahead across replays)
-        saved_lookahead = self.lookahead
-        self.lookahead = False
         side = torch.cuda.Stream(device=self.d.device)
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):
             self.run(map32_in, self._rng_graph, mode)          # untimed first run off the capture
         torch.cuda.current_stream().wait_stream(side)
-        self.graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.graph):
-            self.run(map32_in, self._rng_graph, mode)
-        self.lookahead = saved_lookahead
+        lookahead = self.lookahead
+        self.graphs = []
+        self._graph_pairs = []
+        if lookahead:
+            p = self.plan
+            if self._pix_next is None:
+                self._pix_next = torch.empty_like(self.pix)
+                self._psi_next = torch.empty_like(self.psi)
+            if self.data_streams and self._d_next is None:
+                self._d_next = torch.empty_like(self.d)
+                self._flags_next = torch.empty_like(self.flags)
+            # both pairs decoded before the first replay
+            cur = torch.cuda.current_stream()
+            p.decode(self.pix, self.psi, cur)
+            p.decode(self._pix_next, self._psi_next, cur)
+            if self.data_streams:
+                p.decode_data(self.d, self.flags, cur)
+                p.decode_data(self._d_next, self._flags_next, cur)
+            self.lookahead = False
+        self._graph_gained = []
+        try:
+            for _ in range(2 if lookahead else 1):
+                ev = None
+                if lookahead:
+                    self._pointing_ready = True                 # run() swaps the pairs and does not decode
+                    try:
+                        ev = torch.cuda.Event(external=True)    # a record node the host can wait on
+                    except TypeError:
+                        ev = None
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g):
+                    self.run(map32_in, self._rng_graph, mode, gain_event=ev)
+                self.graphs.append(g)
+                self._graph_gained.append(ev)
+                # the pair this graph reads, and the other one (decoded beside it)
+                self._graph_pairs.append(((self._pix_next, self._psi_next, self._d_next, self._flags_next)))
+        finally:
+            self.lookahead = lookahead
+            self._pointing_ready = False
+        self._next_graph = 0
+        self.graph = self.graphs[0]
         return self.graph
 
     def replay(self, it: int):
         """Run the captured step at Gibbs iteration ``it`` (current stream)."""
+        import torch
         self.iter_dev.fill_(int(it))
-        self.graph.replay()
+        i = self._next_graph
+        g = self.graphs[i]
+        self._next_graph = (i + 1) % len(self.graphs)
+        if len(self.graphs) == 1:
+            g.replay()
+            return
+        cur = torch.cuda.current_stream(self.d.device)
+        hp, _, lo = self._streams()
+        hp.wait_stream(cur)
+        # the pair the other graph reads: free once everything queued so far
+        # is done; decoded after this replay's gain draw (else from its start)
+        pix, psi, d, fl = self._graph_pairs[i]
+        gained = self._graph_gained[i]
+        if gained is None:
+            gained = torch.cuda.Event()
+            gained.record(hp)
+        with torch.cuda.stream(hp):
+            g.replay()
+        lo.wait_event(gained)
+        self.plan.decode(pix, psi, lo)
+        if self.data_streams:
+            self.plan.decode_data(d, fl, lo)
+        cur.wait_stream(hp)
+        cur.wait_stream(lo)

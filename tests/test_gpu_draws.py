@@ -6,7 +6,8 @@
   the DCT basis and scaled by sqrt(phi_k + 1/sigma0^2), is N(0, 1) in every
   mode (the conditional covariance is C^T diag(1/(phi + 1/sigma0^2)) C);
 * a step captured as a CUDA graph and replayed at Gibbs iteration k gives
-  bit for bit what the eager step gives at k;
+  bit for bit what the eager step gives at k (with the pointing lookahead:
+  two graphs swapping the pointing buffers, replayed in turn);
 * steps whose detector data is prefetched into a second buffer on a copy
   stream give bit for bit the steps of plain copies;
 * the n_corr draw split in preparation (on a side stream) and prepared draw
@@ -96,6 +97,35 @@ def test_graph_replay_matches_eager_step(tiny):
     step.replay(6)
     torch.cuda.synchronize()
     assert not torch.equal(ref[0], step.gain)      # a fresh iteration draws fresh numbers
+    wl.plan.status()
+
+
+@pytest.mark.gpu
+def test_graph_replays_with_lookahead_match_eager_steps(tiny):
+    """With the pointing lookahead the step is captured as two graphs that
+    swap the pointing buffers; replays alternate between them and give bit
+    for bit the eager steps (which also decode ahead)."""
+    import torch
+    import paper_2201_03509_gb300 as tg
+    from paper_2201_03509_gb300.step import GibbsTODStep
+    wl = tiny
+    eager = GibbsTODStep(wl.plan, wl.band.psd, wl.ing["flag_words"])
+    eager.set_tod(wl.d32)
+    assert eager.lookahead
+    ref = []
+    for it in (5, 6, 7, 8):
+        eager.run(wl.t_map, tg.Rng(3, 0, it), tg.MODE_DRAW)
+        torch.cuda.synchronize()
+        ref.append([t.clone() for t in (eager.gain, eager.ncorr, eager.A, eager.map)])
+    step = GibbsTODStep(wl.plan, wl.band.psd, wl.ing["flag_words"])
+    step.set_tod(wl.d32)
+    step.capture(wl.t_map, 3, 0, tg.MODE_DRAW)
+    assert len(step.graphs) == 2
+    for k, it in enumerate((5, 6, 7, 8)):
+        step.replay(it)
+        torch.cuda.synchronize()
+        for a, b in zip(ref[k], (step.gain, step.ncorr, step.A, step.map)):
+            assert torch.equal(a, b), it
     wl.plan.status()
 
 

@@ -2,8 +2,9 @@
 C ABI against the FP64 oracle: gaps longer than the preconditioner's block
 (split into several Toeplitz blocks), gaps touching the first and the last
 sample, a detscan with every sample flagged, a single flagged sample, more
-gaps than the preconditioner takes (plain CG), detscans of a few dozen
-samples; and the per-detscan status words for an iteration cap of one and
+gaps than the preconditioner takes (plain CG), more gaps than the coarse
+correction takes (block inverses alone) and exactly as many, detscans of a
+few dozen samples; and the per-detscan status words for an iteration cap of one and
 for non-finite data."""
 import numpy as np
 import pytest
@@ -43,6 +44,10 @@ def _edge_mask(wl):
     seg(6, 4095, 4096) if n(6) >= 4096 else seg(6, n(6) - 1, n(6))
     seg(7, 2, 3)
     seg(7, 5, 6)
+    for k in range(100):                      # 100 gaps: block inverses without the coarse correction
+        seg(8, 40 + 30 * k, 43 + 30 * k)
+    for k in range(64):                       # 64 gaps: the most blocks with the coarse correction
+        seg(9, 40 + 40 * k, 40 + 40 * k + 2 + k % 7)
     return f
 
 
