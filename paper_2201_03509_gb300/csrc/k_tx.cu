@@ -1656,7 +1656,6 @@ __device__ __forceinline__ F2 f2_add(F2 x, F2 y) {
     const float h = s + e;
     return {h, e - (h - s)};
 }
-__device__ __forceinline__ F2 f2_neg(F2 x) { return {-x.h, -x.l}; }
 __device__ __forceinline__ F2 f2_mulf(F2 x, float f) {
     const float p = __fmul_rn(x.h, f);        // not contracted into the sum below
     float e = fmaf(x.h, f, -p);
@@ -1664,29 +1663,31 @@ __device__ __forceinline__ F2 f2_mulf(F2 x, float f) {
     const float h = p + e;
     return {h, e - (h - p)};
 }
-__device__ __forceinline__ F2 cz_H(const float4 *t, int x) { const float4 v = __ldg(t + x); return {v.x, v.y}; }
-__device__ __forceinline__ F2 cz_G(const float4 *t, int x) { const float4 v = __ldg(t + x); return {v.z, v.w}; }
 
 // (S Z) entries of the row at sample p for a block of L samples from s:
-// the indicator's sum over delta = p - j, and the ramp's.
+// the indicator's sum over delta = p - j, and the ramp's.  Each table
+// entry holds (H, G) at one x, loaded once.
 __device__ __forceinline__ float2 cz_entry(const float4 *__restrict__ t, int p, int s, int L) {
     const int lo = p - (s + L - 1), hi = p - s;
     F2 I, Mo;
     if (lo >= 0) {
-        I = f2_add(cz_H(t, hi + 1), f2_neg(cz_H(t, lo)));
-        Mo = f2_add(cz_G(t, hi + 1), f2_neg(cz_G(t, lo)));
+        const float4 A = __ldg(t + hi + 1), B = __ldg(t + lo);
+        I = f2_add(F2{A.x, A.y}, F2{-B.x, -B.y});
+        Mo = f2_add(F2{A.z, A.w}, F2{-B.z, -B.w});
     } else if (hi < 0) {
-        I = f2_add(cz_H(t, 1 - lo), f2_neg(cz_H(t, -hi)));
-        Mo = f2_add(cz_G(t, -hi), f2_neg(cz_G(t, 1 - lo)));
+        const float4 A = __ldg(t + 1 - lo), B = __ldg(t - hi);
+        I = f2_add(F2{A.x, A.y}, F2{-B.x, -B.y});
+        Mo = f2_add(F2{B.z, B.w}, F2{-A.z, -A.w});
     } else {
-        I = f2_add(f2_add(cz_H(t, hi + 1), cz_H(t, 1 - lo)), f2_neg(cz_H(t, 1)));
-        Mo = f2_add(cz_G(t, hi + 1), f2_neg(cz_G(t, 1 - lo)));
+        const float4 A = __ldg(t + hi + 1), B = __ldg(t + 1 - lo), C = __ldg(t + 1);
+        I = f2_add(f2_add(F2{A.x, A.y}, F2{B.x, B.y}), F2{-C.x, -C.y});
+        Mo = f2_add(F2{A.z, A.w}, F2{-B.z, -B.w});
     }
     float ramp = 0.f;
     if (L > 1) {
         // sum_j (j - c_b) h = (p - c_b) I - Mo, c_b = s + (L - 1)/2
         const float pc = 0.5f * static_cast<float>(2 * (p - s) - (L - 1));
-        const F2 v = f2_add(f2_mulf(I, pc), f2_neg(Mo));
+        const F2 v = f2_add(f2_mulf(I, pc), F2{-Mo.h, -Mo.l});
         ramp = (v.h + v.l) * (1.0f / (0.5f * static_cast<float>(L - 1)));
     }
     return make_float2(I.h + I.l, ramp);
@@ -1698,7 +1699,7 @@ __device__ void nc_coarse_setup(const NcorrTx &a, int q)
 {
     __shared__ int s_rank[TX_CBMAX], s_len[TX_CBMAX], s_pos[TX_CBMAX];
     __shared__ float s_E[TX_CBMAX][4 * (2 * TX_CZW + 1)];
-    __shared__ double s_L[2 * TX_CBMAX][CZ_LROW];
+    __shared__ float s_L[2 * TX_CBMAX][CZ_LROW];
     __shared__ int s_ok;
     const CgState cs = a.cgs[q];
     const int nb = a.gnb[q];
@@ -1746,35 +1747,44 @@ __device__ void nc_coarse_setup(const NcorrTx &a, int q)
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        // E(x, y), x = 2b + s', y = 2c + s: from block b's rows
-        // s_E[b][4 (c - b + W) + 2 s' + s], averaged with block c's
-        auto Exy = [&](int x, int y) -> double {
+    // E's lower band, s_L[x][k] = E(x, x - k), x = 2b + s', y = 2c + s: from
+    // block b's rows s_E[b][4 (c - b + W) + 2 s' + s], averaged with block
+    // c's; a ramp of a one-sample block is zero (its row of E set to the
+    // identity's)
+    const int nc = 2 * nb;
+    for (int i = threadIdx.x; i < nc * CZ_LROW; i += TX_T) {
+        const int x = i / CZ_LROW, k = i % CZ_LROW, y = x - k;
+        float v = 0.f;
+        if (y >= 0) {
             const int b = x >> 1, sp = x & 1, c = y >> 1, sc = y & 1;
-            if (b - c > TX_CZW || c - b > TX_CZW) return 0.0;
-            if ((sp && s_len[b] < 2) || (sc && s_len[c] < 2)) return x == y ? 1.0 : 0.0;
-            return 0.5 * (static_cast<double>(s_E[b][4 * (c - b + TX_CZW) + 2 * sp + sc]) +
-                          static_cast<double>(s_E[c][4 * (b - c + TX_CZW) + 2 * sc + sp]));
-        };
-        const int nc = 2 * nb;
+            if ((sp && s_len[b] < 2) || (sc && s_len[c] < 2)) v = x == y ? 1.f : 0.f;
+            else if (b - c <= TX_CZW)
+                v = 0.5f * (s_E[b][4 * (c - b + TX_CZW) + 2 * sp + sc] + s_E[c][4 * (b - c + TX_CZW) + 2 * sc + sp]);
+        }
+        s_L[x][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // banded Cholesky in place (FP32: E is a small, well-conditioned
+        // Gram matrix of smooth vectors); s_L[x][0] becomes 1 / L_xx
         int ok = 1;
         for (int x = 0; x < nc && ok; ++x) {
-            double dsum = Exy(x, x);
+            const float exx = s_L[x][0];
+            float dsum = exx;
             for (int k = TX_CZB; k >= 1; --k) {
                 const int y = x - k;
-                double v = 0.0;
+                float v = 0.f;
                 if (y >= 0) {
-                    v = Exy(x, y);
+                    v = s_L[x][k];
                     // sum over m < y of L(x, m) L(y, m), both within the band
-                    for (int m = x - TX_CZB; m < y; ++m)
-                        if (m >= 0 && y - m <= TX_CZB) v -= s_L[x][x - m] * s_L[y][y - m];
-                    v /= s_L[y][0];
+                    for (int m = max(0, x - TX_CZB); m < y; ++m) v = fmaf(-s_L[x][x - m], s_L[y][y - m], v);
+                    v *= s_L[y][0];
                 }
                 s_L[x][k] = v;
-                dsum -= v * v;
+                dsum = fmaf(-v, v, dsum);
             }
-            if (!(dsum > 1e-12 * fabs(Exy(x, x))) || !(dsum > 0.0)) ok = 0;
-            else s_L[x][0] = sqrt(dsum);
+            if (!(dsum > 1e-5f * fabsf(exx))) ok = 0;
+            else s_L[x][0] = rsqrtf(dsum);
         }
         s_ok = ok;
         if (ok) a.cgs[q].ncz = nb;
@@ -1782,10 +1792,7 @@ __device__ void nc_coarse_setup(const NcorrTx &a, int q)
     __syncthreads();
     if (s_ok) {
         float *Lq = a.czl + static_cast<int64_t>(q) * (2 * TX_CBMAX * CZ_LROW);
-        for (int i = threadIdx.x; i < 2 * nb * CZ_LROW; i += TX_T) {
-            const int x = i / CZ_LROW, k = i % CZ_LROW;
-            Lq[i] = k == 0 ? static_cast<float>(1.0 / s_L[x][0]) : static_cast<float>(s_L[x][k]);
-        }
+        for (int i = threadIdx.x; i < nc * CZ_LROW; i += TX_T) Lq[i] = s_L[i / CZ_LROW][i % CZ_LROW];
     }
     __syncthreads();
 }
