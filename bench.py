@@ -283,6 +283,27 @@ def measure_step(args, cfg, arr, ing, local, rank, ws, label="main"):
     elapsed = max_over_ranks(t0.elapsed_time(t1) / 1e3)
     iters = step.cg_iters.cpu().numpy()
 
+    # the same step captured in CUDA graphs (iteration read on the device),
+    # timed right after the eager steps
+    graph_ms = None
+    if not args.no_graph and ws == 1:
+        try:
+            step.capture(map_in, args.seed, 0, tg.MODE_DRAW)
+            for k in range(2):
+                step.replay(30_000 + k)
+            torch.cuda.synchronize()
+            g0, g1 = _event(), _event()
+            g0.record(stream)
+            for k in range(args.steps):
+                step.replay(40_000 + k)
+            g1.record(stream)
+            torch.cuda.synchronize()
+            graph_ms = g0.elapsed_time(g1) / args.steps
+            step.graph = None
+            step.graphs = []
+        except Exception as ex:          # report, do not hide
+            graph_ms = "capture failed: %s" % ex
+
     # per-stage times: the step's calls one by one on one stream with events
     # between them (the n_corr preparation, which the step overlaps with
     # decode, projection and gain, as its own stage), after the timed region
@@ -330,25 +351,6 @@ def measure_step(args, cfg, arr, ing, local, rank, ws, label="main"):
     iters_kt = [t.cpu().numpy() for t in its_kt]
     plan.status(raise_on_error=False)
 
-    # the same step captured in a CUDA graph (iteration read on the device)
-    graph_ms = None
-    if not args.no_graph and ws == 1:
-        try:
-            step.capture(map_in, args.seed, 0, tg.MODE_DRAW)
-            for k in range(2):
-                step.replay(30_000 + k)
-            torch.cuda.synchronize()
-            g0, g1 = _event(), _event()
-            g0.record(stream)
-            for k in range(args.steps):
-                step.replay(40_000 + k)
-            g1.record(stream)
-            torch.cuda.synchronize()
-            graph_ms = g0.elapsed_time(g1) / args.steps
-            step.graph = None
-            step.graphs = []
-        except Exception as ex:          # report, do not hide
-            graph_ms = "capture failed: %s" % ex
     # the eager step with the pointing decoded in-step (no next-step decode
     # under the n_corr draw)
     inline_ms = None

@@ -38,3 +38,26 @@ def test_reference_arm_other_ranks_do_no_work():
     p = _run({"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2"})
     assert p.returncode == 0, p.stderr[-2000:]
     assert p.stdout.strip() == ""
+
+
+def test_cg_pass_bytes_follow_the_launched_iterations():
+    """The algorithmic bytes of the CG passes: iteration i of a flagged
+    detscan runs in launch i while i < launched, the rest in the cooperative
+    tail; the correction passes cover every detscan that ran the CG."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    lens = np.array([100.0, 200.0, 300.0, 400.0])
+    iters = np.array([1, 3, 10, 0])
+    flagged = np.array([True, True, True, False])
+    kb = bench.kernel_bytes(1000, 10, 5, 0, lens, iters, flagged, launched=8)
+    # launched iterations: detscan 0 once, 1 three times, 2 eight times
+    act = 100 * 1 + 200 * 3 + 300 * 8
+    assert kb["k_nc_filter"] == 8.0 * act
+    assert kb["k_nc_scatter"] == 4.0 * act
+    assert kb["k_nc_gather"] == 4.125 * act
+    assert kb["k_nc_tail"] == 16.125 * 300 * 2
+    assert kb["k_nc_filter_final"] == 8.0 * (100 + 200 + 300)
+    kb3 = bench.kernel_bytes(1000, 10, 5, 0, lens, iters, flagged, launched=3)
+    assert kb3["k_nc_filter"] == 8.0 * (100 + 200 * 3 + 300 * 3)
+    assert kb3["k_nc_tail"] == 16.125 * 300 * 7
