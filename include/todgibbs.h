@@ -188,7 +188,10 @@ tod_status tod_plan_status(tod_plan *p, int32_t *detscan_status);
 tod_status tod_plan_set_schedule(tod_plan *p, int32_t schedule);
 
 /* Preconditioner of the n_corr CG (the Schur-complement solve of
- * tod_sample_ncorr): TOD_PREC_NONE; TOD_PREC_BLOCKS, the exact inverses of
+ * tod_sample_ncorr; the paper fills the gaps with FFTs inside a CG solver,
+ * Sect. 5, and states no preconditioner, so this is an implementation
+ * choice): TOD_PREC_NONE;
+ * TOD_PREC_BLOCKS, the exact inverses of
  * the gap blocks' Toeplitz matrices; TOD_PREC_TWO_LEVEL (default), those
  * plus a coarse correction over two vectors per gap block (indicator and
  * ramp) in the balancing form.  The solution is the same to the CG
