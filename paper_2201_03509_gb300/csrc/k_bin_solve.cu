@@ -12,7 +12,8 @@
 //             detscan's samples stay in L2 while its tiles run), then one
 //             thread sums each run.  Products of FP32 values are formed
 //             exactly and summed as FP32 double-words (FP64 accuracy at FP32
-//             issue rate); each run's sums are scaled by the detscan's
+//             issue rate), the residual d - x taken exactly as a
+//             double-word; each run's sums are scaled by the detscan's
 //             g^2/sigma0^2, g/sigma0^2 in FP64 and written at the run's rank.
 //             A run longer than a tile is summed by the whole CTA with a
 //             fixed-order tree.
@@ -56,14 +57,16 @@ __device__ __forceinline__ Acc2 acc_merge(const Acc2 &a, const Acc2 &b) {
     return r;
 }
 
-// the eleven per-run sums: 1 (as hits), c, s, cc, cs, ss, d, cd, sd, x, cx, sx
+// the per-run sums: 1 (as hits), c, s, cc, cs, ss, r, cr, sr with r = d - x
+// (taken exactly as a double-word: its head and tail)
+constexpr int NSUM = 8;
 struct RunSums {
-    Acc2 a[11];
+    Acc2 a[NSUM];
     int hits;
 };
 __device__ __forceinline__ void sums_zero(RunSums &r) {
 #pragma unroll
-    for (int i = 0; i < 11; ++i) r.a[i] = Acc2{0.f, 0.f};
+    for (int i = 0; i < NSUM; ++i) r.a[i] = Acc2{0.f, 0.f};
     r.hits = 0;
 }
 __device__ __forceinline__ void sums_add(RunSums &r, float2 cs, float dv, float xv) {
@@ -73,12 +76,18 @@ __device__ __forceinline__ void sums_add(RunSums &r, float2 cs, float dv, float 
     acc_add_prod(r.a[2], cs.x, cs.x);
     acc_add_prod(r.a[3], cs.x, cs.y);
     acc_add_prod(r.a[4], cs.y, cs.y);
-    acc_add(r.a[5], dv);
-    acc_add_prod(r.a[6], cs.x, dv);
-    acc_add_prod(r.a[7], cs.y, dv);
-    acc_add(r.a[8], xv);
-    acc_add_prod(r.a[9], cs.x, xv);
-    acc_add_prod(r.a[10], cs.y, xv);
+    // r = d - x exactly: head rh (rounded difference) and tail rl (two-sum)
+    const float rh = __fsub_rn(dv, xv);
+    const float bb = __fsub_rn(rh, dv);
+    const float rl = __fadd_rn(__fsub_rn(dv, __fsub_rn(rh, bb)), __fsub_rn(-xv, bb));
+    acc_add(r.a[5], rh);
+    r.a[5].c = __fadd_rn(r.a[5].c, rl);
+    // c r and s r: exact products of the heads, the tails' products (below
+    // 2^-24 of them) added to the compensation words
+    acc_add_prod(r.a[6], cs.x, rh);
+    r.a[6].c = __fmaf_rn(cs.x, rl, r.a[6].c);
+    acc_add_prod(r.a[7], cs.y, rh);
+    r.a[7].c = __fmaf_rn(cs.y, rl, r.a[7].c);
 }
 __device__ __forceinline__ void sums_store(const RunSums &r, double wA, double wb, double *rr) {
     rr[0] = wA * r.hits;
@@ -87,18 +96,10 @@ __device__ __forceinline__ void sums_store(const RunSums &r, double wA, double w
     rr[3] = wA * acc_value(r.a[2]);
     rr[4] = wA * acc_value(r.a[3]);
     rr[5] = wA * acc_value(r.a[4]);
-    rr[6] = wb * (acc_value(r.a[5]) - acc_value(r.a[8]));
-    rr[7] = wb * (acc_value(r.a[6]) - acc_value(r.a[9]));
-    rr[8] = wb * (acc_value(r.a[7]) - acc_value(r.a[10]));
+    rr[6] = wb * acc_value(r.a[5]);
+    rr[7] = wb * acc_value(r.a[6]);
+    rr[8] = wb * acc_value(r.a[7]);
     rr[9] = static_cast<double>(r.hits);
-}
-
-// a - b of two double-words (two-sum on the heads, tails subtracted)
-__device__ __forceinline__ Acc2 acc_diff(const Acc2 &a, const Acc2 &b) {
-    Acc2 r = a;
-    acc_add(r, -b.s);
-    r.c = __fsub_rn(r.c, b.c);
-    return r;
 }
 
 __device__ __forceinline__ uint16_t psi_flag(const BinArgs &a, int64_t tg) {
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(BIN_T) k_bin(BinArgs a)
 {
     __shared__ float s_d[BIN_TILE], s_x[BIN_TILE];
     __shared__ float2 s_cs[BIN_TILE];
-    __shared__ Acc2 s_red[BIN_T / 32][11];
+    __shared__ Acc2 s_red[BIN_T / 32][NSUM];
     __shared__ int s_hits[BIN_T / 32];
     __shared__ Acc2 s_out[BIN_T / 4][10];          // a quad's ten run outputs as double-words
     const int tile = blockIdx.x;
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(BIN_T) k_bin(BinArgs a)
 #pragma unroll
         for (int ofs = 16; ofs; ofs >>= 1) {
 #pragma unroll
-            for (int k = 0; k < 11; ++k) {
+            for (int k = 0; k < NSUM; ++k) {
                 Acc2 o2;
                 o2.s = __shfl_down_sync(0xffffffffu, r.a[k].s, ofs);
                 o2.c = __shfl_down_sync(0xffffffffu, r.a[k].c, ofs);
@@ -176,14 +177,14 @@ __global__ void __launch_bounds__(BIN_T) k_bin(BinArgs a)
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         if (lane == 0) {
 #pragma unroll
-            for (int k = 0; k < 11; ++k) s_red[warp][k] = r.a[k];
+            for (int k = 0; k < NSUM; ++k) s_red[warp][k] = r.a[k];
             s_hits[warp] = r.hits;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             for (int w = 1; w < BIN_T / 32; ++w) {
 #pragma unroll
-                for (int k = 0; k < 11; ++k) r.a[k] = acc_merge(r.a[k], s_red[w][k]);
+                for (int k = 0; k < NSUM; ++k) r.a[k] = acc_merge(r.a[k], s_red[w][k]);
                 r.hits += s_hits[w];
             }
             sums_store(r, wA, wb, a.rec + static_cast<int64_t>(a.pair_slot[r0]) * 10);
@@ -241,7 +242,7 @@ __global__ void __launch_bounds__(BIN_T) k_bin(BinArgs a)
 #pragma unroll
         for (int ofs = 1; ofs <= 2; ofs <<= 1) {
 #pragma unroll
-            for (int k = 0; k < 11; ++k) {
+            for (int k = 0; k < NSUM; ++k) {
                 Acc2 o2;
                 o2.s = __shfl_xor_sync(0xffffffffu, rs.a[k].s, ofs);
                 o2.c = __shfl_xor_sync(0xffffffffu, rs.a[k].c, ofs);
@@ -251,14 +252,14 @@ __global__ void __launch_bounds__(BIN_T) k_bin(BinArgs a)
         }
         // the ten outputs in FP64, spread over the quad's lanes (lane ql takes
         // outputs ql, ql + 4, ql + 8: FP64 issues slowly on this part, so every
-        // lane of its warp instructions works); the b terms' d - x as double-words
+        // lane of its warp instructions works)
         if (pr >= 0 && ql == 0) {
             Acc2 *o = s_out[quad];
             o[0] = Acc2{static_cast<float>(rs.hits), 0.f};      // hits <= BIN_TILE: exact
 #pragma unroll
             for (int k = 0; k < 5; ++k) o[1 + k] = rs.a[k];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) o[6 + k] = acc_diff(rs.a[5 + k], rs.a[8 + k]);
+            for (int k = 0; k < 3; ++k) o[6 + k] = rs.a[5 + k];
             o[9] = o[0];
         }
         __syncwarp();
