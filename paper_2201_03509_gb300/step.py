@@ -280,8 +280,8 @@ class GibbsTODStep:
                     self.run(map32_in, self._rng_graph, mode, gain_event=ev)
                 self.graphs.append(g)
                 self._graph_gained.append(ev)
-                # the pair this graph reads, and the other one (decoded beside it)
-                self._graph_pairs.append(((self._pix_next, self._psi_next, self._d_next, self._flags_next)))
+                # the pair this graph does not read: the other graph's, decoded beside this one
+                self._graph_pairs.append((self._pix_next, self._psi_next, self._d_next, self._flags_next))
         finally:
             self.lookahead = lookahead
             self._pointing_ready = False
