@@ -179,7 +179,7 @@ tod_status tod_plan_status(tod_plan *p, int32_t *detscan_status);
 /* Launch schedule of the transform stages (gain, n_corr):
  * TOD_SCHED_PERSISTENT (default): every pass of a stage is one launch over
  * the tiles of all detscans (the n_corr draw: a fixed sequence of pass
- * launches, its CG iterations past the third in one cooperative launch);
+ * launches, its CG iterations past the eighth in one cooperative launch);
  * TOD_SCHED_PER_SCAN: the same kernels launched once per detscan (the
  * plain per-scan path, kept for comparison).  Results are identical: each
  * detscan's arithmetic does not depend on the others or on the launch. */
