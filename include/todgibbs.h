@@ -366,7 +366,8 @@ tod_status tod_sample_gain(tod_plan *p, const float *d, const float *s,
  * n-1-(t-1)/2 for odd t); w2[k] is normal 2k (k < n/2), 2(n-k)+1 (k > n/2),
  * 0 (k = 0) or 1 (k = n/2) of the NC_W2 stream.  Gap-free detscans are solved
  * exactly in the DCT basis; flagged ones by conjugate gradients on the
- * flagged samples (Woodbury form), stopping at relative residual cg_tol
+ * flagged samples (Woodbury form; preconditioner: tod_plan_set_preconditioner),
+ * stopping at relative residual cg_tol
  * (<= 0: 1e-6) or cg_maxiter (<= 0: 500) iterations (then
  * TOD_ERR_NOT_CONVERGED).  ncorr_out float32[N]; cg_iters_out int32[ndetscan]
  * or NULL. */
@@ -383,9 +384,11 @@ tod_status tod_sample_ncorr(tod_plan *p, const float *d, const float *s,
  * not described): a scheduling convenience.  tod_sample_ncorr is exactly
  * tod_ncorr_prepare followed by tod_sample_ncorr_prepared on one stream.
  *   tod_ncorr_prepare builds, from psd (double[ndet][3], device), the
- *   per-detector gap preconditioner tables the plan holds (Toeplitz
- *   autocovariance of the CG operator at a reference length and its Durbin
- *   solutions), overwriting the previous ones.
+ *   per-detector gap preconditioner tables the plan holds (the Toeplitz
+ *   autocovariance of the CG operator at every lag of a power-of-two
+ *   reference length, by one FFT per detector, its prefix sums for the
+ *   coarse correction, and the Durbin solutions of its first 512 lags),
+ *   overwriting the previous ones.
  *   tod_sample_ncorr_prepared is tod_sample_ncorr (same arguments, results
  *   and errors) using those tables; psd must be the array they were built
  *   from.
